@@ -1,0 +1,587 @@
+/*
+ * FP64 reference ("oracle") for the FireANTs registration inner loop.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link, load or
+ * call this file: only tests/, __graft_entry__.smoke() and bench.py's CPU
+ * baseline leg use it.  It shares no code, header, table or constant
+ * generator with the CUDA library; it is written from the paper
+ * (arXiv 2404.01249, "FireANTs: Adaptive Riemannian Optimization for
+ * Multi-Scale Diffeomorphic Matching") and from the readings listed below.
+ *
+ * Everything is plain double precision.  Loops follow the definitions: no
+ * separable box sums, no sliding windows, no fusion.  The only structure
+ * beyond the definitions is the separable Gaussian (the method itself smooths
+ * with a separable Gaussian) and OpenMP over z-slices, which changes no
+ * arithmetic (per-slice partial sums are added in slice order).
+ *
+ * Conventions
+ *   volume  : [D][H][W] doubles, W fastest, index (z*H + y)*W + x.
+ *   field   : [3][D][H][W]; channel 0 is the z (D-axis) component,
+ *             channel 1 the y (H-axis), channel 2 the x (W-axis) component.
+ *   coordinates are voxel units of the current level; phi(x) = x + u(x).
+ *
+ * Readings of points the paper leaves open (each marked "reading" below):
+ *   R-interp  trilinear interpolation, samples outside the grid are zero
+ *             (u is extended by zero outside Omega, section Preliminaries).
+ *   R-kink    at integer coordinates the interpolant's derivative is taken in
+ *             the cell floor(p) (one-sided).
+ *   R-lncc    LNCC = squared local correlation over a w^3 box with zero
+ *             padding and fixed divisor n = w^3:
+ *               cross = S_IJ - S_I S_J / n, varI = S_II - S_I^2 / n,
+ *               varJ = S_JJ - S_J^2 / n, cc = cross^2 / (varI varJ + eps),
+ *               L = -(1/N) sum_x cc(x).
+ *   R-mse     L = (1/N) sum (J - I_f)^2 (the printed sum, normalised).
+ *   R-gauss   taps exp(-k^2 / 2 sigma^2), k in [-ceil(3 sigma), ceil(3 sigma)],
+ *             normalised to sum 1, zero padding; sigma == 0 is the identity.
+ *   R-adam    Kingma-Ba Adam with bias correction; t carries across levels.
+ *   R-step    eps_t = eta / (c_LP * max_x |d(x)|), c_LP = 2 (the Lipschitz
+ *             bound of the appendix "Limitations of Stationary Velocity
+ *             Fields" with voxel spacing 1); delta = -eps_t d; eps_t = 0 when
+ *             max |d| == 0.
+ *   R-pyr     level size max(1, floor(N_a / s)); Gaussian blur sigma = s/2 on
+ *             the fine grid, then trilinear align-corners sampling; s == 1 is
+ *             the identity.
+ *   R-up      level hand-off: trilinear align-corners; u scaled by
+ *             s_a = (Nf_a - 1)/(Nc_a - 1) per axis, m by 1/s_a and v by
+ *             1/s_a^2 (state kept fixed in normalised coordinates);
+ *             s_a = 1 when Nc_a == 1 or Nf_a == 1.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_OK 0
+#define OR_EINVAL 1
+
+#define IDX(z, y, x) (((size_t)(z) * (size_t)H + (size_t)(y)) * (size_t)W + (size_t)(x))
+
+static int in_grid(int z, int y, int x, int D, int H, int W) {
+    return z >= 0 && z < D && y >= 0 && y < H && x >= 0 && x < W;
+}
+
+/* Trilinear interpolant of vol at (pz, py, px) with zero outside the grid
+ * (reading R-interp) and its gradient with respect to the sample position
+ * (reading R-kink).  grad may be NULL. */
+static double trilinear(const double *vol, int D, int H, int W,
+                        double pz, double py, double px, double *grad) {
+    if (grad) grad[0] = grad[1] = grad[2] = 0.0;
+    if (isnan(pz) || isnan(py) || isnan(px)) {
+        if (grad) grad[0] = grad[1] = grad[2] = NAN;
+        return NAN;
+    }
+    /* every corner is outside: value and gradient are exactly zero */
+    if (pz < -1.0 || py < -1.0 || px < -1.0 ||
+        pz >= (double)D || py >= (double)H || px >= (double)W)
+        return 0.0;
+    double fz = floor(pz), fy = floor(py), fx = floor(px);
+    int z0 = (int)fz, y0 = (int)fy, x0 = (int)fx;
+    double tz = pz - fz, ty = py - fy, tx = px - fx;
+    double c[2][2][2];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int e = 0; e < 2; ++e) {
+                int z = z0 + a, y = y0 + b, x = x0 + e;
+                c[a][b][e] = in_grid(z, y, x, D, H, W) ? vol[IDX(z, y, x)] : 0.0;
+            }
+    double wz[2] = {1.0 - tz, tz}, wy[2] = {1.0 - ty, ty}, wx[2] = {1.0 - tx, tx};
+    double val = 0.0;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int e = 0; e < 2; ++e)
+                val += wz[a] * wy[b] * wx[e] * c[a][b][e];
+    if (grad) {
+        double gz = 0.0, gy = 0.0, gx = 0.0;
+        for (int b = 0; b < 2; ++b)
+            for (int e = 0; e < 2; ++e)
+                gz += (c[1][b][e] - c[0][b][e]) * wy[b] * wx[e];
+        for (int a = 0; a < 2; ++a)
+            for (int e = 0; e < 2; ++e)
+                gy += (c[a][1][e] - c[a][0][e]) * wz[a] * wx[e];
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b)
+                gx += (c[a][b][1] - c[a][b][0]) * wz[a] * wy[b];
+        grad[0] = gz; grad[1] = gy; grad[2] = gx;
+    }
+    return val;
+}
+
+/* Pointwise sample of a volume; exported so tests can probe the interpolant. */
+double or_sample(const double *vol, int D, int H, int W,
+                 double pz, double py, double px, double *grad3) {
+    return trilinear(vol, D, H, W, pz, py, px, grad3);
+}
+
+/* Warp (section Preliminaries: (I o phi)(x) = I(phi(x)), pushforward form of
+ * section "Alternative formulations"): J(x) = I_m(x + u(x)) and, if requested,
+ * gradJ(x) = (grad I_m)(x + u(x)), the interpolant's gradient at the sampled
+ * point (needed by the MSE gradient of section "Deformable Image Registration
+ * is a severely ill-conditioned problem" and by the LNCC chain rule). */
+int or_warp(const double *Im, int D, int H, int W, const double *u,
+            double *J, double *gradJ) {
+    if (D <= 0 || H <= 0 || W <= 0) return OR_EINVAL;
+    size_t N = (size_t)D * H * W;
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < D; ++z)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                size_t i = IDX(z, y, x);
+                double g[3];
+                double v = trilinear(Im, D, H, W, z + u[i], y + u[N + i], x + u[2 * N + i], g);
+                J[i] = v;
+                if (gradJ) {
+                    gradJ[i] = g[0];
+                    gradJ[N + i] = g[1];
+                    gradJ[2 * N + i] = g[2];
+                }
+            }
+    return OR_OK;
+}
+
+/* Adjoint of the warp with respect to the moving intensities: for a cotangent
+ * dJ on the fixed grid, dIm[k] = sum_x dJ(x) * w_k(x + u(x)) where w_k is the
+ * trilinear weight of voxel k.  This is the derivative a template update needs
+ * (the template is the moving image).  Serial scatter: exact order. */
+int or_warp_adjoint(const double *dJ, const double *u, int D, int H, int W,
+                    int Dm, int Hm, int Wm, double *dIm) {
+    if (D <= 0 || H <= 0 || W <= 0 || Dm <= 0 || Hm <= 0 || Wm <= 0) return OR_EINVAL;
+    size_t N = (size_t)D * H * W;
+    size_t Nm = (size_t)Dm * Hm * Wm;
+    memset(dIm, 0, Nm * sizeof(double));
+    for (int z = 0; z < D; ++z)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                size_t i = IDX(z, y, x);
+                double pz = z + u[i], py = y + u[N + i], px = x + u[2 * N + i];
+                if (isnan(pz) || isnan(py) || isnan(px)) continue;
+                if (pz < -1.0 || py < -1.0 || px < -1.0 ||
+                    pz >= (double)Dm || py >= (double)Hm || px >= (double)Wm)
+                    continue;
+                double fz = floor(pz), fy = floor(py), fx = floor(px);
+                int z0 = (int)fz, y0 = (int)fy, x0 = (int)fx;
+                double tz = pz - fz, ty = py - fy, tx = px - fx;
+                double wz[2] = {1.0 - tz, tz}, wy[2] = {1.0 - ty, ty}, wx[2] = {1.0 - tx, tx};
+                for (int a = 0; a < 2; ++a)
+                    for (int b = 0; b < 2; ++b)
+                        for (int e = 0; e < 2; ++e) {
+                            int zz = z0 + a, yy = y0 + b, xx = x0 + e;
+                            if (zz < 0 || zz >= Dm || yy < 0 || yy >= Hm || xx < 0 || xx >= Wm) continue;
+                            dIm[((size_t)zz * Hm + yy) * Wm + xx] += dJ[i] * wz[a] * wy[b] * wx[e];
+                        }
+            }
+    return OR_OK;
+}
+
+/* Window sum of v over the w^3 box centred at (z, y, x), zero padding. */
+static double box_at(const double *v, int D, int H, int W, int r, int z, int y, int x) {
+    double s = 0.0;
+    for (int dz = -r; dz <= r; ++dz)
+        for (int dy = -r; dy <= r; ++dy)
+            for (int dx = -r; dx <= r; ++dx) {
+                int zz = z + dz, yy = y + dy, xx = x + dx;
+                if (in_grid(zz, yy, xx, D, H, W)) s += v[IDX(zz, yy, xx)];
+            }
+    return s;
+}
+
+/* Box sum of a whole volume, straight from the definition (exported so that
+ * tests can check window extent against brute force). */
+int or_box_sum(const double *in, int D, int H, int W, int win, double *out) {
+    if (D <= 0 || H <= 0 || W <= 0 || win < 1 || (win % 2) == 0) return OR_EINVAL;
+    int r = win / 2;
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < D; ++z)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) out[IDX(z, y, x)] = box_at(in, D, H, W, r, z, y, x);
+    return OR_OK;
+}
+
+/* LNCC loss (reading R-lncc; the cost named in Eq. (image-reg) and tuned by
+ * its window in section "FireANTs enables rapid prototyping") and its
+ * analytic Gateaux derivative with respect to the warped image J and the
+ * fixed image I.
+ *
+ * With A = d cc / d S_IJ = 2 cross / Dn, B = d cc / d S_JJ = -cross^2 varI / Dn^2,
+ * C = d cc / d S_J = -A S_I / n - 2 B S_J / n (Dn = varI varJ + eps) and the
+ * mirrored B', C' for I, the chain rule through the window sums gives
+ *   dL/dJ(y) = -(1/N) sum_{x : y in win(x)} [A(x) I(y) + 2 B(x) J(y) + C(x)]
+ *   dL/dI(y) = -(1/N) sum_{x : y in win(x)} [A(x) J(y) + 2 B'(x) I(y) + C'(x)]
+ * and {x in grid : y in win(x)} = win(y) ∩ grid for the symmetric box.
+ *
+ * loss   : L (scalar).  cc (nullable): per-voxel cc.  dJ, dI (nullable). */
+int or_lncc(const double *I, const double *J, int D, int H, int W, int win, double cc_eps,
+            double *loss, double *cc, double *dJ, double *dI) {
+    if (D <= 0 || H <= 0 || W <= 0 || win < 1 || (win % 2) == 0 || cc_eps < 0.0) return OR_EINVAL;
+    size_t N = (size_t)D * H * W;
+    int r = win / 2;
+    double n = (double)win * win * win;
+    double *II = malloc(N * sizeof(double)), *JJ = malloc(N * sizeof(double)),
+           *IJ = malloc(N * sizeof(double));
+    double *A = malloc(N * sizeof(double)), *B = malloc(N * sizeof(double)),
+           *C = malloc(N * sizeof(double)), *Bp = malloc(N * sizeof(double)),
+           *Cp = malloc(N * sizeof(double));
+    double *slice = calloc((size_t)D, sizeof(double));
+    if (!II || !JJ || !IJ || !A || !B || !C || !Bp || !Cp || !slice) {
+        free(II); free(JJ); free(IJ); free(A); free(B); free(C); free(Bp); free(Cp); free(slice);
+        return OR_EINVAL;
+    }
+    for (size_t i = 0; i < N; ++i) {
+        II[i] = I[i] * I[i];
+        JJ[i] = J[i] * J[i];
+        IJ[i] = I[i] * J[i];
+    }
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < D; ++z) {
+        double acc = 0.0;
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                double sI = box_at(I, D, H, W, r, z, y, x);
+                double sJ = box_at(J, D, H, W, r, z, y, x);
+                double sII = box_at(II, D, H, W, r, z, y, x);
+                double sJJ = box_at(JJ, D, H, W, r, z, y, x);
+                double sIJ = box_at(IJ, D, H, W, r, z, y, x);
+                double cross = sIJ - sI * sJ / n;
+                double varI = sII - sI * sI / n;
+                double varJ = sJJ - sJ * sJ / n;
+                double den = varI * varJ + cc_eps;
+                double c = cross * cross / den;
+                size_t i = IDX(z, y, x);
+                if (cc) cc[i] = c;
+                acc += c;
+                A[i] = 2.0 * cross / den;
+                B[i] = -cross * cross * varI / (den * den);
+                Bp[i] = -cross * cross * varJ / (den * den);
+                C[i] = -A[i] * sI / n - 2.0 * B[i] * sJ / n;
+                Cp[i] = -A[i] * sJ / n - 2.0 * Bp[i] * sI / n;
+            }
+        slice[z] = acc;
+    }
+    double total = 0.0;
+    for (int z = 0; z < D; ++z) total += slice[z];
+    *loss = -total / (double)N;
+    if (dJ || dI) {
+#pragma omp parallel for schedule(static)
+        for (int z = 0; z < D; ++z)
+            for (int y = 0; y < H; ++y)
+                for (int x = 0; x < W; ++x) {
+                    size_t i = IDX(z, y, x);
+                    double sA = box_at(A, D, H, W, r, z, y, x);
+                    if (dJ) {
+                        double sB = box_at(B, D, H, W, r, z, y, x);
+                        double sC = box_at(C, D, H, W, r, z, y, x);
+                        dJ[i] = -(sA * I[i] + 2.0 * sB * J[i] + sC) / (double)N;
+                    }
+                    if (dI) {
+                        double sBp = box_at(Bp, D, H, W, r, z, y, x);
+                        double sCp = box_at(Cp, D, H, W, r, z, y, x);
+                        dI[i] = -(sA * J[i] + 2.0 * sBp * I[i] + sCp) / (double)N;
+                    }
+                }
+    }
+    free(II); free(JJ); free(IJ); free(A); free(B); free(C); free(Bp); free(Cp); free(slice);
+    return OR_OK;
+}
+
+/* MSE loss (reading R-mse of the cost in section "Deformable Image
+ * Registration is a severely ill-conditioned problem") and its derivative
+ * dL/dJ = 2 (J - I) / N, dL/dI = -dL/dJ. */
+int or_mse(const double *I, const double *J, int D, int H, int W,
+           double *loss, double *dJ, double *dI) {
+    if (D <= 0 || H <= 0 || W <= 0) return OR_EINVAL;
+    size_t N = (size_t)D * H * W;
+    double total = 0.0;
+    for (size_t i = 0; i < N; ++i) {
+        double e = J[i] - I[i];
+        total += e * e;
+        if (dJ) dJ[i] = 2.0 * e / (double)N;
+        if (dI) dI[i] = -2.0 * e / (double)N;
+    }
+    *loss = total / (double)N;
+    return OR_OK;
+}
+
+/* Gaussian taps (reading R-gauss).  Returns the radius R, fills taps[0..2R]
+ * (taps[k + R] is the weight of offset k); -1 if cap is too small. */
+int or_gauss_taps(double sigma, double *taps, int cap) {
+    if (!(sigma >= 0.0)) return -1;
+    if (sigma == 0.0) {
+        if (cap < 1) return -1;
+        taps[0] = 1.0;
+        return 0;
+    }
+    int R = (int)ceil(3.0 * sigma);
+    if (2 * R + 1 > cap) return -1;
+    double s = 0.0;
+    for (int k = -R; k <= R; ++k) {
+        taps[k + R] = exp(-(double)k * k / (2.0 * sigma * sigma));
+        s += taps[k + R];
+    }
+    for (int k = 0; k <= 2 * R; ++k) taps[k] /= s;
+    return R;
+}
+
+/* One axial pass of a 1-D correlation with zero padding. axis 0 = z, 1 = y, 2 = x. */
+static void axial_pass(const double *in, double *out, int D, int H, int W,
+                       const double *taps, int R, int axis) {
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < D; ++z)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                double s = 0.0;
+                for (int k = -R; k <= R; ++k) {
+                    int zz = z + (axis == 0 ? k : 0);
+                    int yy = y + (axis == 1 ? k : 0);
+                    int xx = x + (axis == 2 ? k : 0);
+                    if (in_grid(zz, yy, xx, D, H, W)) s += taps[k + R] * in[IDX(zz, yy, xx)];
+                }
+                out[IDX(z, y, x)] = s;
+            }
+}
+
+/* Separable Gaussian smoothing of C channels ([C][D][H][W]) with sigma in
+ * voxels (sigma_grad / sigma_warp of the hyper-parameter study, reading
+ * R-gauss).  in and out may alias. */
+int or_gauss_smooth(const double *in, double *out, int C, int D, int H, int W, double sigma) {
+    if (C <= 0 || D <= 0 || H <= 0 || W <= 0) return OR_EINVAL;
+    size_t N = (size_t)D * H * W;
+    double taps[4096];
+    int R = or_gauss_taps(sigma, taps, 4096);
+    if (R < 0) return OR_EINVAL;
+    if (R == 0) {
+        if (out != in) memmove(out, in, (size_t)C * N * sizeof(double));
+        return OR_OK;
+    }
+    double *a = malloc(N * sizeof(double)), *b = malloc(N * sizeof(double));
+    if (!a || !b) { free(a); free(b); return OR_EINVAL; }
+    for (int c = 0; c < C; ++c) {
+        axial_pass(in + (size_t)c * N, a, D, H, W, taps, R, 2);
+        axial_pass(a, b, D, H, W, taps, R, 1);
+        axial_pass(b, out + (size_t)c * N, D, H, W, taps, R, 0);
+    }
+    free(a); free(b);
+    return OR_OK;
+}
+
+/* Adam (section "Adaptive optimization on diffeomorphisms", Algorithm 1 step
+ * "Update (v_d', optstate)"; constants of reading R-adam) applied to the
+ * descent directions, which all live in the tangent space at identity:
+ *   m <- b1 m + (1-b1) g,  v <- b2 v + (1-b2) g^2,
+ *   d = (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps).
+ * t is the step number after increment (t >= 1). */
+int or_adam(const double *g, double *m, double *v, double *d, size_t n, int t,
+            double b1, double b2, double eps) {
+    if (t < 1) return OR_EINVAL;
+    double bc1 = 1.0 - pow(b1, t), bc2 = 1.0 - pow(b2, t);
+    for (size_t i = 0; i < n; ++i) {
+        m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+        v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+        d[i] = (m[i] / bc1) / (sqrt(v[i] / bc2) + eps);
+    }
+    return OR_OK;
+}
+
+/* max_x |d(x)|_2 over a 3-channel field: the quantity that bounds the
+ * Lipschitz constant in the appendix "Limitations of Stationary Velocity
+ * Fields".  Returns NaN if any component is NaN. */
+double or_max_norm(const double *d, int D, int H, int W) {
+    size_t N = (size_t)D * H * W;
+    double mx = 0.0;
+    for (size_t i = 0; i < N; ++i) {
+        double s = d[i] * d[i] + d[N + i] * d[N + i] + d[2 * N + i] * d[2 * N + i];
+        double nrm = sqrt(s);
+        if (isnan(nrm)) return NAN;
+        if (nrm > mx) mx = nrm;
+    }
+    return mx;
+}
+
+/* Step scaling (appendix "Limitations of Stationary Velocity Fields", reading
+ * R-step): delta = -eta / (c_LP max|d|) * d.  Returns the step size eps_t. */
+double or_step_scale(const double *d, double *delta, int D, int H, int W, double eta, double c_lp) {
+    size_t N = (size_t)D * H * W;
+    double mx = or_max_norm(d, D, H, W);
+    double e = (mx > 0.0) ? eta / (c_lp * mx) : 0.0;
+    if (isnan(mx)) e = NAN;
+    for (size_t i = 0; i < 3 * N; ++i) delta[i] = -e * d[i];
+    return e;
+}
+
+/* Compositive retraction update (section "Minimizing the Eulerian
+ * differential": phi_{t+1} = phi_t o (id + eta_t v_d); Algorithm 1):
+ *   phi'(x) = phi(x + delta(x))  =>  u'(x) = delta(x) + u(x + delta(x)),
+ * u interpolated trilinearly with zero outside (reading R-interp).
+ * out must not alias u. */
+int or_compose(const double *u, const double *delta, double *out, int D, int H, int W) {
+    if (D <= 0 || H <= 0 || W <= 0 || out == u) return OR_EINVAL;
+    size_t N = (size_t)D * H * W;
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < D; ++z)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                size_t i = IDX(z, y, x);
+                double pz = z + delta[i], py = y + delta[N + i], px = x + delta[2 * N + i];
+                for (int c = 0; c < 3; ++c)
+                    out[(size_t)c * N + i] =
+                        delta[(size_t)c * N + i] + trilinear(u + (size_t)c * N, D, H, W, pz, py, px, NULL);
+            }
+    return OR_OK;
+}
+
+/* Size of a pyramid level (reading R-pyr). */
+int or_level_size(int n, int s) {
+    int m = (s > 0) ? n / s : 0;
+    return m < 1 ? 1 : m;
+}
+
+/* Align-corners source coordinate of destination index i when resampling
+ * an axis of length n_src onto one of length n_dst. */
+static double ac_coord(int i, int n_src, int n_dst) {
+    if (n_dst <= 1 || n_src <= 1) return 0.0;
+    return (double)i * (double)(n_src - 1) / (double)(n_dst - 1);
+}
+
+/* Trilinear align-corners resampling of C channels from (Ds,Hs,Ws) onto
+ * (Dd,Hd,Wd); all sample points lie inside the source grid. */
+static void resample_ac(const double *src, int C, int Ds, int Hs, int Ws,
+                        double *dst, int Dd, int Hd, int Wd) {
+    size_t Ns = (size_t)Ds * Hs * Ws, Nd = (size_t)Dd * Hd * Wd;
+    for (int c = 0; c < C; ++c) {
+#pragma omp parallel for schedule(static)
+        for (int z = 0; z < Dd; ++z)
+            for (int y = 0; y < Hd; ++y)
+                for (int x = 0; x < Wd; ++x)
+                    dst[(size_t)c * Nd + ((size_t)z * Hd + y) * Wd + x] =
+                        trilinear(src + (size_t)c * Ns, Ds, Hs, Ws, ac_coord(z, Ds, Dd),
+                                  ac_coord(y, Hs, Hd), ac_coord(x, Ws, Wd), NULL);
+    }
+}
+
+/* Pyramid level (section "Interpolation strategies for multi-scale
+ * registration"; Algorithm 1 "downsample(I, s_l)"; reading R-pyr): Gaussian
+ * blur sigma = s/2 then trilinear align-corners sampling to
+ * (max(1, D/s), max(1, H/s), max(1, W/s)). */
+int or_downsample(const double *I, int D, int H, int W, int s, double *out) {
+    if (D <= 0 || H <= 0 || W <= 0 || s < 1) return OR_EINVAL;
+    size_t N = (size_t)D * H * W;
+    if (s == 1) {
+        memmove(out, I, N * sizeof(double));
+        return OR_OK;
+    }
+    double *blur = malloc(N * sizeof(double));
+    if (!blur) return OR_EINVAL;
+    int rc = or_gauss_smooth(I, blur, 1, D, H, W, 0.5 * (double)s);
+    if (rc != OR_OK) { free(blur); return rc; }
+    resample_ac(blur, 1, D, H, W, out, or_level_size(D, s), or_level_size(H, s), or_level_size(W, s));
+    free(blur);
+    return OR_OK;
+}
+
+/* Per-axis voxel-unit scale factor of the level hand-off (reading R-up). */
+static double up_scale(int nc, int nf) {
+    if (nc <= 1 || nf <= 1) return 1.0;
+    return (double)(nf - 1) / (double)(nc - 1);
+}
+
+/* Level hand-off of a 3-channel field (section "Interpolation strategies":
+ * trilinear upsampling of phi and of the optimiser state m, nu; Algorithm 1
+ * "Upsample(phi, s_{l+1})").  power = 1 multiplies channel a by s_a (the
+ * displacement u), power = -1 divides by s_a (the first moment m), power = -2
+ * divides by s_a^2 (the second moment nu); reading R-up. */
+int or_upsample_field(const double *src, int Dc, int Hc, int Wc,
+                      double *dst, int Df, int Hf, int Wf, int power) {
+    if (Dc <= 0 || Hc <= 0 || Wc <= 0 || Df <= 0 || Hf <= 0 || Wf <= 0) return OR_EINVAL;
+    if (power != 1 && power != -1 && power != -2) return OR_EINVAL;
+    size_t Nf = (size_t)Df * Hf * Wf;
+    resample_ac(src, 3, Dc, Hc, Wc, dst, Df, Hf, Wf);
+    double s[3] = {up_scale(Dc, Df), up_scale(Hc, Hf), up_scale(Wc, Wf)};
+    for (int c = 0; c < 3; ++c) {
+        double f = power == 1 ? s[c] : (power == -1 ? 1.0 / s[c] : 1.0 / (s[c] * s[c]));
+        for (size_t i = 0; i < Nf; ++i) dst[(size_t)c * Nf + i] *= f;
+    }
+    return OR_OK;
+}
+
+/* Hyper-parameters of Algorithm 1 plus the smoothing widths of the grid
+ * study and the Adam constants.  Plain struct, mirrored in oracle/__init__.py. */
+typedef struct {
+    int n_levels;
+    int scales[8];
+    int iters[8];
+    double lr;          /* eta */
+    double sigma_grad;
+    double sigma_warp;
+    int window;         /* LNCC box width w (odd) */
+    int loss;           /* 0 = LNCC, 1 = MSE */
+    double beta1, beta2, adam_eps;
+    double cc_eps;
+    double c_lp;        /* Lipschitz-bound factor of reading R-step (2) */
+} or_params;
+
+static int loss_and_grad(const or_params *p, const double *If, const double *J,
+                         int D, int H, int W, double *L, double *dJ) {
+    if (p->loss == 0) return or_lncc(If, J, D, H, W, p->window, p->cc_eps, L, NULL, dJ, NULL);
+    return or_mse(If, J, D, H, W, L, dJ, NULL);
+}
+
+/* Algorithm 1 (FireANTs), Jacobian-free descent direction (section
+ * "Jacobian-Free Eulerian Descent"), with the per-iteration order
+ *   warp -> loss and dL/dphi -> Gaussian(sigma_grad) -> Adam -> step scale
+ *   -> compose -> Gaussian(sigma_warp).
+ * u_out receives the finest-level displacement (level size of the last
+ * scale); final_loss receives L(phi_final) on the last level;
+ * loss_trace (nullable, sum(iters) entries) receives the loss of every
+ * iteration before its update. */
+int or_register(const double *If, const double *Im, int D, int H, int W, const or_params *p,
+                double *u_out, double *final_loss, double *loss_trace) {
+    if (D <= 0 || H <= 0 || W <= 0 || !p || p->n_levels < 1 || p->n_levels > 8) return OR_EINVAL;
+    for (int l = 0; l < p->n_levels; ++l)
+        if (p->scales[l] < 1 || p->iters[l] < 0) return OR_EINVAL;
+    int t = 0, pd = 0, ph = 0, pw = 0, trace_i = 0;
+    double *u = NULL, *m = NULL, *v = NULL;
+    for (int l = 0; l < p->n_levels; ++l) {
+        int s = p->scales[l];
+        int d = or_level_size(D, s), h = or_level_size(H, s), w = or_level_size(W, s);
+        size_t N = (size_t)d * h * w;
+        double *fl = malloc(N * sizeof(double)), *ml = malloc(N * sizeof(double));
+        double *nu = calloc(3 * N, sizeof(double)), *nm = calloc(3 * N, sizeof(double)),
+               *nv = calloc(3 * N, sizeof(double));
+        double *J = malloc(N * sizeof(double)), *gJ = malloc(3 * N * sizeof(double)),
+               *dJ = malloc(N * sizeof(double)), *g = malloc(3 * N * sizeof(double)),
+               *dir = malloc(3 * N * sizeof(double)), *tmp = malloc(3 * N * sizeof(double));
+        if (!fl || !ml || !nu || !nm || !nv || !J || !gJ || !dJ || !g || !dir || !tmp) return OR_EINVAL;
+        or_downsample(If, D, H, W, s, fl);
+        or_downsample(Im, D, H, W, s, ml);
+        if (l > 0) {   /* Algorithm 1: phi <- Upsample(phi), state likewise */
+            or_upsample_field(u, pd, ph, pw, nu, d, h, w, 1);
+            or_upsample_field(m, pd, ph, pw, nm, d, h, w, -1);
+            or_upsample_field(v, pd, ph, pw, nv, d, h, w, -2);
+        }
+        free(u); free(m); free(v);
+        u = nu; m = nm; v = nv;
+        pd = d; ph = h; pw = w;
+        for (int it = 0; it < p->iters[l]; ++it) {
+            double L;
+            or_warp(ml, d, h, w, u, J, gJ);
+            loss_and_grad(p, fl, J, d, h, w, &L, dJ);
+            if (loss_trace) loss_trace[trace_i++] = L;
+            for (int c = 0; c < 3; ++c)          /* dL/dphi(x) = dL/dJ(x) grad I_m(phi(x)) */
+                for (size_t i = 0; i < N; ++i) g[(size_t)c * N + i] = dJ[i] * gJ[(size_t)c * N + i];
+            or_gauss_smooth(g, g, 3, d, h, w, p->sigma_grad);
+            ++t;
+            or_adam(g, m, v, dir, 3 * N, t, p->beta1, p->beta2, p->adam_eps);
+            or_step_scale(dir, dir, d, h, w, p->lr, p->c_lp);
+            or_compose(u, dir, tmp, d, h, w);
+            or_gauss_smooth(tmp, u, 3, d, h, w, p->sigma_warp);
+        }
+        if (l == p->n_levels - 1) {
+            double L;
+            or_warp(ml, d, h, w, u, J, NULL);
+            loss_and_grad(p, fl, J, d, h, w, &L, NULL);
+            *final_loss = L;
+            memcpy(u_out, u, 3 * N * sizeof(double));
+        }
+        free(fl); free(ml); free(J); free(gJ); free(dJ); free(g); free(dir); free(tmp);
+    }
+    free(u); free(m); free(v);
+    return OR_OK;
+}
