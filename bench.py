@@ -1,0 +1,346 @@
+#!/usr/bin/env python3
+"""Benchmark of whole multi-scale registrations (Algorithm 1) on the
+brain-MRI-shaped synthetic pair: 160x192x224 Voronoi volumes, scales
+{4, 2, 1} x iterations {200, 100, 50}, LNCC window 5, lr 0.5,
+sigma_grad 1, sigma_warp 0.5.  One step = one whole registration of one pair
+(pyramid, all levels, final loss) with the inputs resident in HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--mode fused|plain]
+    python bench.py --impl reference     # the FP64 oracle on the host cores
+
+Prints one JSON line (rank 0).  Under torchrun each rank registers its own
+pair (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="voronoi_brain_160x192x224", shape=(160, 192, 224), scales=(4, 2, 1),
+                iters=(200, 100, 50), window=5, lr=0.5, sigma_grad=1.0, sigma_warp=0.5,
+                cc_eps=1e-5)
+METRIC = "voxel-iters/s"
+L2_BYTES = 129 * 1024 * 1024
+HBM_FALLBACK_GBS = 6800.0
+# algorithmic bytes per voxel of one launch of each timed kernel (fp32
+# storage)
+ALGO_BYTES = {
+    "fused_grad_adam": 4 * (3 + 3 + 3 + 3 + 3 + 3),  # g (halo), m, v read; m, v, d written
+    "fused_warp_lncc": 4 * (3 + 1 + 1 + 3),          # u, I_f, I_m read; A, B, C written
+    "fused_lncc_grad": 4 * (3 + 3 + 1 + 1 + 3),      # A, B, C, u, I_f, I_m read; g written
+    "fused_compose": 4 * (3 + 3 + 3),                # d, u read; u written
+    "plain_iteration": 80,                           # whole plain iteration (I_f, I_m, u, m, v)
+}
+
+
+def level_size(n, s):
+    return max(1, n // s)
+
+
+def voxel_iters(shape, scales, iters):
+    tot = 0
+    for s, t in zip(scales, iters):
+        n = 1
+        for a in shape:
+            n *= level_size(a, s)
+        tot += n * t
+    return tot
+
+
+def rank_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+    FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus = (bus_id or "").lower()
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r.split(",") for r in out.strip().splitlines() if r.count(",") >= 9]
+        rows = [[c.strip() for c in r] for r in rows]
+        if not rows:
+            return None
+        buses = {r[1].lower() for r in rows}
+        if len(buses) > 1 and self.bus:
+            rows = [r for r in rows if r[1].lower().endswith(self.bus[-12:])] or rows
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[6 + k] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# --------------------------------------------------------------- oracle leg
+def oracle_sample(f, m, iters: int):
+    """Times the FP64 oracle on `iters` finest-level iterations of the pair
+    (plus its final-loss evaluation); returns (seconds, voxel-iterations, threads)."""
+    threads = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(threads))
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.register(f, m, [1], [iters], lr=WORKLOAD["lr"], sigma_grad=WORKLOAD["sigma_grad"],
+                    sigma_warp=WORKLOAD["sigma_warp"], window=WORKLOAD["window"],
+                    cc_eps=WORKLOAD["cc_eps"])
+    dt = time.perf_counter() - t0
+    return dt, iters * int(np.prod(f.shape)), int(os.environ["OMP_NUM_THREADS"])
+
+
+def run_reference(args):
+    rank, world, _ = rank_env()
+    if rank != 0:
+        return 0
+    from paper_2404_01249_gb300 import synth
+    f, m, _ = synth.voronoi_pair(shape=WORKLOAD["shape"], seed=1000)
+    for _ in range(args.warmup):
+        oracle_sample(f, m, 1)
+    times, units = [], 0
+    for _ in range(args.steps):
+        dt, vi, threads = oracle_sample(f, m, 1)
+        times.append(dt)
+        units += vi
+    total = sum(times)
+    val = units / total
+    sample = ("1 finest-level iteration (scale 1, 160x192x224) of the pair plus the oracle's "
+              "final-loss evaluation per step")
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": METRIC, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(args, world),
+            "cpu_baseline": {"value": val, "unit": METRIC, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": METRIC, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def config_dict(args, world):
+    return {"workload": WORKLOAD["name"], "shape": list(WORKLOAD["shape"]),
+            "scales": list(WORKLOAD["scales"]), "iters": list(WORKLOAD["iters"]),
+            "window": WORKLOAD["window"], "lr": WORKLOAD["lr"],
+            "sigma_grad": WORKLOAD["sigma_grad"], "sigma_warp": WORKLOAD["sigma_warp"],
+            "loss": "lncc", "mode": args.mode, "pairs_per_rank": 1, "world_size": world,
+            "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"}
+
+
+def traffic_from_profile(kernel: str, n_voxels: int):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        e = d[kernel]
+        src = os.path.join(ROOT, "paper_2404_01249_gb300", "csrc", e["source"])
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if sha != e["source_sha"]:
+            return None
+        return float(e["dram_bytes_per_voxel"]) * n_voxels
+    except Exception:
+        return None
+
+
+# --------------------------------------------------------------- GPU leg
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2404_01249_gb300 import build, fa, synth
+
+    rank, world, local = rank_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    fa.load()
+    shape = WORKLOAD["shape"]
+    f, m, _ = synth.voronoi_pair(shape=shape, seed=1000 + rank)
+    params = fa.RegParams(scales=WORKLOAD["scales"], iters=WORKLOAD["iters"],
+                          window=WORKLOAD["window"], lr=WORKLOAD["lr"],
+                          sigma_grad=WORKLOAD["sigma_grad"], sigma_warp=WORKLOAD["sigma_warp"],
+                          cc_eps=WORKLOAD["cc_eps"], mode=args.mode)
+    fixed = torch.from_numpy(f).to(dev)
+    moving = torch.from_numpy(m).to(dev)
+    ws = fa.workspace(fa.fa_register_workspace_size(shape, params), dev)
+    u = torch.empty((3,) + shape, device=dev)
+    loss = torch.empty((), device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        fa.fa_register(fixed, moving, params, ws=ws, sync=False, u_out=u, loss_out=loss)
+    torch.cuda.synchronize()
+
+    # kernel timer: the dominant kernel on the finest level, every step
+    fin = len(WORKLOAD["scales"]) - 1
+    kid = fa.FA_K_PLAIN_ANY if args.mode == "plain" else fa.FA_K_FUSED_GRAD_ADAM
+    kname = "plain_iteration" if args.mode == "plain" else "fused_grad_adam"
+    cap = WORKLOAD["iters"][fin] * args.steps
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(cap)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(cap)]
+    timer = fa.make_timer(kid, fin, ev0, ev1)
+    step0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    step1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(dev).pci_bus_id  # type: ignore[attr-defined]
+    except Exception:
+        pass
+    clocks = ClockSampler(str(bus) if bus is not None else None)
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = fa.fa_launch_count()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        step0[k].record(stream)
+        fa.fa_register(fixed, moving, params, ws=ws, sync=False, u_out=u, loss_out=loss,
+                       timer=timer)
+        step1[k].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    launches = fa.fa_launch_count() - launches0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    fa.fa_ws_status(ws)
+    step_ms = [a.elapsed_time(b) for a, b in zip(step0, step1)]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    vi = voxel_iters(shape, WORKLOAD["scales"], WORKLOAD["iters"])
+    value = world * vi * args.steps / (total_ms / 1e3)
+
+    # dominant kernel roofline (finest level launches of every timed step)
+    kt = [ev0[i].elapsed_time(ev1[i]) for i in range(timer.count)]
+    n_fine = int(np.prod([level_size(a, WORKLOAD["scales"][fin]) for a in shape]))
+    peak, peak_kind = measured_peak()
+    algo = ALGO_BYTES[kname] * n_fine
+    avg_ms = float(np.mean(kt)) if kt else float("nan")
+    achieved = algo / (avg_ms / 1e3) / 1e9
+    traffic = traffic_from_profile(kname, n_fine)
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "algo_bytes": algo, "avg_launch_ms": avg_ms,
+                "launches_timed": len(kt)}
+
+    # end to end: host buffers in, displacement and loss out
+    fh = torch.from_numpy(f).pin_memory()
+    mh = torch.from_numpy(m).pin_memory()
+    uh = torch.empty((3,) + shape, dtype=torch.float32).pin_memory()
+    lh = torch.empty((), dtype=torch.float32).pin_memory()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    fd = torch.empty_like(fixed)
+    md = torch.empty_like(moving)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        fd.copy_(fh, non_blocking=True)
+        md.copy_(mh, non_blocking=True)
+        fa.fa_register(fd, md, params, ws=ws, sync=False, u_out=u, loss_out=loss)
+        uh.copy_(u, non_blocking=True)
+        lh.copy_(loss, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": world * vi * args.steps / (e2e_ms / 1e3), "unit": METRIC,
+           "h2d_bytes_per_step": 2 * f.nbytes, "d2h_bytes_per_step": uh.numel() * 4 + 4,
+           "final_lncc": -float(lh)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "s_per_pair": total_ms / args.steps / 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_dict(args, world), "wall_s": wall, "roofline": roofline,
+                "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
+                "final_lncc": -float(loss)}
+        if world == 1 and not args.no_cpu_baseline:
+            dt, units, threads = oracle_sample(f, m, args.cpu_iters)
+            line["cpu_baseline"] = {
+                "value": units / dt, "unit": METRIC, "cores": threads, "kind": "oracle",
+                "sample": f"{args.cpu_iters} finest-level iteration(s) (scale 1, 160x192x224) "
+                          "of the same pair plus the oracle's final-loss evaluation"}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="fused", choices=["fused", "plain"])
+    ap.add_argument("--cpu-iters", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

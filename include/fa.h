@@ -1,0 +1,248 @@
+/*
+ * libfa -- GB300 (sm_103a) inner loop of FireANTs' multi-scale Riemannian
+ * Adam diffeomorphic registration (arXiv 2404.01249).
+ *
+ * C ABI.  Every pointer to voxel data is a DEVICE pointer owned by the
+ * caller; every other pointer (descriptors, parameters, host results) is a
+ * HOST pointer.  Streams are passed as `void *` holding a cudaStream_t
+ * (NULL = the legacy default stream).  Calls are asynchronous on that stream
+ * unless stated otherwise.  Argument, shape and dtype errors are returned
+ * before anything is launched; libfa never allocates device memory: scratch
+ * space is a caller-provided workspace whose size the *_workspace_size
+ * queries return.  No exceptions cross the ABI; fa_last_error() gives a
+ * thread-local message for the last failing call.
+ *
+ * Layout.  A volume is [D][H][W], W fastest.  A 3-channel field is
+ * [3][D][H][W] (structure of arrays); channel 0 is the z (D-axis)
+ * component, 1 the y (H-axis), 2 the x (W-axis) component, in voxels of the
+ * grid it lives on.  The map is phi(x) = x + u(x).  Samples outside the grid
+ * read as zero (u is extended by zero outside the domain, section
+ * "Preliminaries" of the paper).
+ *
+ * Arithmetic is FP32 on the GPU.  LNCC window sums are accumulated exactly
+ * in 64-bit fixed point, so the E[I^2] - E[I]^2 cancellation does not lose
+ * precision.  No FP64 runs on the GPU.
+ */
+#ifndef FA_H
+#define FA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FA_OK = 0,
+    FA_ERR_INVALID = 1,     /* null pointer, bad parameter value            */
+    FA_ERR_SHAPE = 2,       /* inconsistent or unsupported shapes           */
+    FA_ERR_DTYPE = 3,       /* unsupported element type                     */
+    FA_ERR_CUDA = 4,        /* a CUDA runtime call failed                   */
+    FA_ERR_NONFINITE = 5,   /* device status word: NaN/Inf in a loss or step */
+    FA_ERR_TIMEOUT = 6,     /* device status word: a bounded wait gave up   */
+    FA_ERR_UNSUPPORTED = 7, /* valid request this build does not implement  */
+    FA_ERR_WORKSPACE = 8    /* workspace missing, too small or misaligned   */
+} fa_status;
+
+typedef enum { FA_F32 = 0, FA_BF16 = 1, FA_F16 = 2 } fa_dtype;
+
+typedef enum { FA_LOSS_LNCC = 0, FA_LOSS_MSE = 1 } fa_loss;
+
+/* Kernel schedule used by fa_register: FA_MODE_FUSED (three fused kernels per
+ * iteration) or FA_MODE_PLAIN (one kernel per operation, intermediates in
+ * HBM; the baseline the fused form is measured against).  Both compute the
+ * same arithmetic. */
+typedef enum { FA_MODE_FUSED = 0, FA_MODE_PLAIN = 1 } fa_mode;
+
+/* Descriptor of a caller-owned device buffer holding C channels of a
+ * D x H x W grid, contiguous [C][D][H][W]. */
+typedef struct {
+    void *data;
+    int32_t dtype; /* fa_dtype */
+    int32_t C, D, H, W;
+} fa_vol;
+
+/* Hyper-parameters of Algorithm 1 ("FireANTs"): scales s_l and iterations
+ * T_l per level (coarsest first), learning rate eta, the Gaussian widths
+ * sigma_grad / sigma_warp of the hyper-parameter study, the LNCC window, the
+ * loss, Adam constants (Kingma & Ba, as cited for the adaptive optimiser),
+ * the LNCC stabiliser cc_eps and the factor c_lp of the step-size rule
+ * eps_t = eta / (c_lp max|d|) of the appendix "Limitations of Stationary
+ * Velocity Fields" (c_lp = 2: the bound LP(v) <= sup 2|v| / |dx|). */
+typedef struct {
+    int32_t n_levels;     /* 1..8 */
+    int32_t scales[8];    /* downsampling factor per level, >= 1 */
+    int32_t iters[8];     /* iterations per level, >= 0 */
+    float lr;             /* eta, > 0 */
+    float sigma_grad;     /* >= 0, voxels of the level; 0 = no smoothing */
+    float sigma_warp;     /* >= 0 */
+    int32_t window;       /* odd LNCC box width, 1..15 */
+    int32_t loss;         /* fa_loss */
+    float beta1, beta2, adam_eps;
+    float cc_eps;         /* >= 0 */
+    float c_lp;           /* > 0 */
+    int32_t mode;         /* fa_mode */
+    int32_t storage;      /* fa_dtype of images and fields inside fa_register (FA_F32) */
+} fa_params;
+
+/* Fills p with: 3 levels {4,2,1} x {200,100,50}, lr 0.5, sigma_grad 1,
+ * sigma_warp 0.5, window 5, LNCC, Adam (0.9, 0.999, 1e-8), cc_eps 1e-5,
+ * c_lp 2, fused mode, FP32 storage. */
+fa_status fa_params_default(fa_params *p);
+
+const char *fa_status_str(fa_status s);
+/* Message of the last failing call made by this host thread ("" if none). */
+const char *fa_last_error(void);
+
+/* Number of kernels this library has launched in this process (all threads);
+ * benchmarks difference it around a timed region. */
+uint64_t fa_launch_count(void);
+
+/* ---------------------------------------------------------------------------
+ * Building blocks.  Each is one step of the per-iteration loop; fa_register
+ * chains them (or their fused forms) for whole registrations.
+ * ------------------------------------------------------------------------- */
+
+/* Warp (section "Preliminaries": (I o phi)(x) = I(phi(x)); pushforward form
+ * of section "Alternative formulations for Eulerian differential"):
+ *   out(x) = moving(x + u(x)), trilinear, zero outside the grid;
+ *   grad_opt(x) = gradient of the trilinear interpolant of `moving` at
+ *   x + u(x) (derivative inside the cell floor(x + u), one-sided at integer
+ *   coordinates); may be NULL.
+ * moving: C=1; u: C=3; out: C=1; grad_opt: C=3; all on one D x H x W grid,
+ * FA_F32.  No workspace. */
+fa_status fa_warp(const fa_vol *moving, const fa_vol *u, fa_vol *out, fa_vol *grad_opt,
+                  void *stream);
+
+/* Bytes of workspace fa_lncc_fwd_bwd needs for a D x H x W grid. */
+size_t fa_lncc_workspace_size(int32_t D, int32_t H, int32_t W);
+
+/* LNCC loss (the local normalised cross-correlation cost named with
+ * Eq. (image-reg); window size is its hyper-parameter) and its Gateaux
+ * derivatives (section "Jacobian-Free Eulerian Descent").  Definition:
+ * box window of width `window` (odd), zero padding, fixed divisor
+ * n = window^3; cross = S_IJ - S_I S_J / n, var_I = S_II - S_I^2 / n,
+ * var_J = S_JJ - S_J^2 / n, cc = cross^2 / (var_I var_J + cc_eps),
+ * L = -(1/N) sum_x cc(x).
+ *   loss_dev         device float, receives L (may be NULL)
+ *   dL_dwarped_opt   C=1, receives dL/dJ (may be NULL)
+ *   dL_dfixed_opt    C=1, receives dL/dI (may be NULL)
+ * fixed, warped: C=1, FA_F32, same grid.  window in 1..15.  Workspace of
+ * fa_lncc_workspace_size bytes, 256-byte aligned. */
+fa_status fa_lncc_fwd_bwd(const fa_vol *fixed, const fa_vol *warped, int32_t window,
+                          float cc_eps, float *loss_dev, fa_vol *dL_dwarped_opt,
+                          fa_vol *dL_dfixed_opt, void *ws, size_t ws_bytes, void *stream);
+
+/* MSE loss L = (1/N) sum (J - I)^2 (the squared-intensity cost of section
+ * "Deformable Image Registration is a severely ill-conditioned problem",
+ * normalised by N) and dL/dJ = 2 (J - I) / N, dL/dI = -dL/dJ.  Same argument
+ * conventions as fa_lncc_fwd_bwd; workspace of fa_lncc_workspace_size. */
+fa_status fa_mse_fwd_bwd(const fa_vol *fixed, const fa_vol *warped, float *loss_dev,
+                         fa_vol *dL_dwarped_opt, fa_vol *dL_dfixed_opt, void *ws,
+                         size_t ws_bytes, void *stream);
+
+/* Bytes of workspace fa_gauss_smooth needs for C channels of D x H x W. */
+size_t fa_gauss_workspace_size(int32_t C, int32_t D, int32_t H, int32_t W);
+
+/* Separable Gaussian smoothing of each channel (sigma_grad / sigma_warp of
+ * the hyper-parameter study, in voxels): taps exp(-k^2 / 2 sigma^2) for
+ * |k| <= ceil(3 sigma), normalised to sum 1, zero padding.  sigma = 0 copies.
+ * in, out: same C, D, H, W, FA_F32; in == out is allowed.  sigma <= 10. */
+fa_status fa_gauss_smooth(const fa_vol *in, fa_vol *out, float sigma, void *ws,
+                          size_t ws_bytes, void *stream);
+
+/* Bytes of workspace fa_radam_step needs for a D x H x W grid. */
+size_t fa_radam_workspace_size(int32_t D, int32_t H, int32_t W);
+
+/* One Riemannian Adam step (section "Adaptive optimization on
+ * diffeomorphisms"; Algorithm 1 optimiser update and compositive update):
+ *   m <- b1 m + (1-b1) g;  v <- b2 v + (1-b2) g^2;
+ *   d = (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + adam_eps);
+ *   eps_t = lr / (c_lp max_x |d(x)|)  (0 if the max is 0);  delta = -eps_t d;
+ *   u_out(x) = delta(x) + u_in(x + delta(x))   (phi <- phi o (id + delta)).
+ * u_in, u_out, m, v, g: C=3, FA_F32, same grid; u_out must not alias u_in.
+ * t >= 1 is the step number after increment.  Uses p->beta1, beta2,
+ * adam_eps, lr, c_lp.  eps_t_dev (device float, may be NULL) receives eps_t.
+ * A non-finite max|d| sets the workspace status word (see fa_ws_status). */
+fa_status fa_radam_step(const fa_vol *u_in, fa_vol *u_out, fa_vol *m, fa_vol *v,
+                        const fa_vol *g, int32_t t, const fa_params *p, float *eps_t_dev,
+                        void *ws, size_t ws_bytes, void *stream);
+
+/* Pyramid level (Algorithm 1 "downsample(I, s)"; section "Interpolation
+ * strategies for multi-scale registration"): Gaussian blur with sigma = s/2
+ * on the input grid, then trilinear align-corners sampling onto the output
+ * grid, whose size must be max(1, floor(N_a / s)) per axis.  s = 1 copies.
+ * img, out: C=1, FA_F32.  Workspace of fa_gauss_workspace_size(1, D, H, W). */
+fa_status fa_pyramid_level(const fa_vol *img, int32_t s, fa_vol *out, void *ws,
+                           size_t ws_bytes, void *stream);
+
+/* Level hand-off (section "Interpolation strategies": trilinear upsampling
+ * of phi and of the optimiser state m, nu; Algorithm 1 "Upsample"):
+ * trilinear align-corners resampling of a 3-channel field from `coarse` onto
+ * `fine`, then channel a is multiplied by s_a^power with
+ * s_a = (Nf_a - 1) / (Nc_a - 1) (1 when either size is 1):
+ * power = 1 for the displacement u, -1 for the first moment m, -2 for the
+ * second moment nu.  C=3, FA_F32.  No workspace. */
+fa_status fa_upsample_field(const fa_vol *coarse, fa_vol *fine, int32_t power, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Whole registration (Algorithm 1 with the Jacobian-free direction).
+ * Per iteration: warp -> loss and dL/dphi -> Gaussian(sigma_grad) -> Adam ->
+ * step scaling -> compose -> Gaussian(sigma_warp).  Levels run coarsest
+ * first; u, m, nu are handed off with fa_upsample_field's rule; the Adam
+ * step counter carries across levels.
+ * ------------------------------------------------------------------------- */
+
+/* Bytes of workspace fa_register needs for a D x H x W pair. */
+size_t fa_register_workspace_size(int32_t D, int32_t H, int32_t W, const fa_params *p);
+
+/* fixed, moving: C=1, FA_F32, same D x H x W.  u_out: C=3 on the grid of the
+ * last level (max(1, floor(N_a / s_last))).  final_loss_dev (device float,
+ * may be NULL) receives the loss at the final map on the last level
+ * (for LNCC that is -mean cc).  If final_loss_host is not NULL the call
+ * waits for the stream, stores that loss there and returns
+ * FA_ERR_NONFINITE / FA_ERR_TIMEOUT if the device status word is set;
+ * otherwise it returns after enqueueing (read the status with fa_ws_status).
+ * Workspace of fa_register_workspace_size bytes, 256-byte aligned. */
+fa_status fa_register(const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
+                      fa_vol *u_out, float *final_loss_dev, float *final_loss_host, void *ws,
+                      size_t ws_bytes, void *stream);
+
+/* Waits for `stream` and returns the status word that kernels recorded in a
+ * workspace used by fa_register, fa_radam_step or fa_lncc_fwd_bwd
+ * (FA_OK, FA_ERR_NONFINITE or FA_ERR_TIMEOUT). */
+fa_status fa_ws_status(const void *ws, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Kernel timing for benchmarks.  When `timer` is not NULL, fa_register_timed
+ * records a pair of CUDA events (caller-created cudaEvent_t handles) around
+ * every launch of kernel `kernel_id` on level `level` (-1: every level), in
+ * order, until `capacity` pairs are used; `count` receives the number of
+ * pairs recorded.  Elapsed times are then read with cudaEventElapsedTime.
+ * ------------------------------------------------------------------------- */
+typedef enum {
+    FA_K_FUSED_WARP_LNCC = 0,   /* fused: warp + LNCC forward (coefficients)     */
+    FA_K_FUSED_GRAD_ADAM = 1,   /* fused: LNCC backward + Gaussian(g) + Adam     */
+    FA_K_FUSED_COMPOSE = 2,     /* fused: compose + Gaussian(u)                   */
+    FA_K_PLAIN_ANY = 3          /* plain mode: every kernel of the iteration     */
+} fa_kernel_id;
+
+typedef struct {
+    int32_t kernel_id;
+    int32_t level;
+    int32_t capacity;
+    int32_t count;
+    void **start_events;
+    void **stop_events;
+} fa_kernel_timer;
+
+fa_status fa_register_timed(const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
+                            fa_vol *u_out, float *final_loss_dev, float *final_loss_host,
+                            void *ws, size_t ws_bytes, void *stream, fa_kernel_timer *timer);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FA_H */

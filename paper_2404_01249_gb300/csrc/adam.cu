@@ -1,0 +1,158 @@
+// Adam on the Jacobian-free descent directions (section "Adaptive
+// optimization on diffeomorphisms"), the step size eps_t = lr / (c_lp
+// max|d|) of the appendix "Limitations of Stationary Velocity Fields", and
+// the compositive update phi <- phi o (id + delta) (section "Minimizing the
+// Eulerian differential", Algorithm 1).  Plain per-op kernels.
+#include <math.h>
+
+#include "ops.h"
+#include "validate.h"
+
+namespace fa {
+
+__global__ void __launch_bounds__(256) k_adam(const float *__restrict__ g, float *__restrict__ m,
+                                              float *__restrict__ v, float *__restrict__ d,
+                                              long long N, AdamConsts c, WsHeader *h,
+                                              int parity) {
+    __shared__ float red[32];
+    float nrm2 = 0.0f;
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    bool bad = false;
+    if (i < N) {
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            long long k = ch * N + i;
+            float gv = g[k];
+            float mv = fmaf(c.b1, m[k], (1.0f - c.b1) * gv);
+            float vv = fmaf(c.b2, v[k], (1.0f - c.b2) * gv * gv);
+            m[k] = mv;
+            v[k] = vv;
+            float dv = (mv / c.bc1) / (sqrtf(vv / c.bc2) + c.eps);
+            d[k] = dv;
+            nrm2 = fmaf(dv, dv, nrm2);
+        }
+        if (!(nrm2 <= 3.4e38f)) {
+            bad = true;
+            nrm2 = 0.0f;
+        }
+    }
+    if (bad) status_set(&h->status, ST_NONFINITE);
+    block_max_to(&h->step_max_bits[parity], sqrtf(nrm2), red);
+}
+
+__global__ void __launch_bounds__(256) k_compose(const float *__restrict__ u,
+                                                 const float *__restrict__ d,
+                                                 float *__restrict__ uo, int D, int H, int W,
+                                                 float lr, float c_lp, WsHeader *h, int parity,
+                                                 float *eps_out) {
+    int x = blockIdx.x * 32 + threadIdx.x;
+    int y = blockIdx.y * 8 + threadIdx.y;
+    int z = blockIdx.z;
+    float mx = __uint_as_float(h->step_max_bits[parity]);
+    float e = (mx > 0.0f) ? lr / (c_lp * mx) : 0.0f;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 &&
+        threadIdx.y == 0) {
+        h->step_max_bits[parity ^ 1] = 0u;  // slot of the next iteration
+        h->eps_t = e;
+        if (eps_out) *eps_out = e;
+    }
+    if (x >= W || y >= H) return;
+    long long N = (long long)D * H * W;
+    long long i = ((long long)z * H + y) * W + x;
+    float dz = -e * d[i], dy = -e * d[N + i], dx = -e * d[2 * N + i];
+    float gz, gy, gx;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        float s = tri_sample<false>(u + ch * N, D, H, W, z, y, x, dz, dy, dx, gz, gy, gx);
+        float dc = ch == 0 ? dz : (ch == 1 ? dy : dx);
+        uo[ch * N + i] = dc + s;
+    }
+}
+
+cudaError_t launch_adam(const float *g, float *m, float *v, float *d, long long N, AdamConsts c,
+                        WsHeader *h, int parity, cudaStream_t s) {
+    long long blocks = (N + 255) / 256;
+    k_adam<<<(unsigned)blocks, 256, 0, s>>>(g, m, v, d, N, c, h, parity); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compose(const float *u_in, const float *d, float *u_out, Dims dm, float lr,
+                           float c_lp, WsHeader *h, int parity, float *eps_out, cudaStream_t s) {
+    VoxGrid g(dm.D, dm.H, dm.W);
+    k_compose<<<g.grid, g.block, 0, s>>>(u_in, d, u_out, dm.D, dm.H, dm.W, lr, c_lp, h, parity,
+                                         eps_out); note_launch();
+    return cudaGetLastError();
+}
+
+AdamConsts adam_consts(const fa_params *p, int t) {
+    AdamConsts c;
+    c.b1 = p->beta1;
+    c.b2 = p->beta2;
+    c.eps = p->adam_eps;
+    c.bc1 = (float)(1.0 - pow((double)p->beta1, (double)t));
+    c.bc2 = (float)(1.0 - pow((double)p->beta2, (double)t));
+    return c;
+}
+
+fa_status check_adam_params(const fa_params *p, const char *who) {
+    if (!p) {
+        set_error("%s: params are NULL", who);
+        return FA_ERR_INVALID;
+    }
+    if (!(p->beta1 >= 0.0f && p->beta1 < 1.0f) || !(p->beta2 >= 0.0f && p->beta2 < 1.0f) ||
+        !(p->adam_eps >= 0.0f) || !(p->lr > 0.0f && p->lr < 1e30f) ||
+        !(p->c_lp > 0.0f && p->c_lp < 1e30f)) {
+        set_error("%s: need 0 <= beta < 1, adam_eps >= 0, lr > 0, c_lp > 0", who);
+        return FA_ERR_INVALID;
+    }
+    return FA_OK;
+}
+
+}  // namespace fa
+
+extern "C" size_t fa_radam_workspace_size(int32_t D, int32_t H, int32_t W) {
+    if (D < 1 || H < 1 || W < 1) return 0;
+    fa::WsCarver c(nullptr, ~size_t(0));
+    c.take<fa::WsHeader>(1);
+    c.take<float>(3 * (size_t)D * H * W);
+    return c.off;
+}
+
+extern "C" fa_status fa_radam_step(const fa_vol *u_in, fa_vol *u_out, fa_vol *m, fa_vol *v,
+                                   const fa_vol *g, int32_t t, const fa_params *p,
+                                   float *eps_t_dev, void *ws, size_t ws_bytes, void *stream) {
+    using namespace fa;
+    clear_error();
+    FA_TRY(check_vol(u_in, "u_in", 3));
+    FA_TRY(check_vol(u_out, "u_out", 3));
+    FA_TRY(check_vol(m, "m", 3));
+    FA_TRY(check_vol(v, "v", 3));
+    FA_TRY(check_vol(g, "g", 3));
+    FA_TRY(same_grid(u_in, u_out, "u_in", "u_out"));
+    FA_TRY(same_grid(u_in, m, "u_in", "m"));
+    FA_TRY(same_grid(u_in, v, "u_in", "v"));
+    FA_TRY(same_grid(u_in, g, "u_in", "g"));
+    if (u_in->data == u_out->data) {
+        set_error("fa_radam_step: u_out must not alias u_in");
+        return FA_ERR_INVALID;
+    }
+    if (t < 1) {
+        set_error("fa_radam_step: t must be >= 1");
+        return FA_ERR_INVALID;
+    }
+    FA_TRY(check_adam_params(p, "fa_radam_step"));
+    FA_TRY(check_ws(ws, ws_bytes, fa_radam_workspace_size(u_in->D, u_in->H, u_in->W),
+                    "fa_radam_step"));
+    cudaStream_t s = (cudaStream_t)stream;
+    Dims d{u_in->D, u_in->H, u_in->W};
+    WsCarver c(ws, ws_bytes);
+    WsHeader *h = c.take<WsHeader>(1);
+    float *dir = c.take<float>(3 * d.N());
+    int parity = t & 1;
+    FA_CUDA_TRY(launch_header_reset(h, s));
+    FA_CUDA_TRY(launch_adam((const float *)g->data, (float *)m->data, (float *)v->data, dir, d.N(),
+                            adam_consts(p, t), h, parity, s));
+    FA_CUDA_TRY(launch_compose((const float *)u_in->data, dir, (float *)u_out->data, d, p->lr,
+                               p->c_lp, h, parity, eps_t_dev, s));
+    return FA_OK;
+}

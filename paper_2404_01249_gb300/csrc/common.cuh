@@ -1,0 +1,228 @@
+// Shared device helpers of libfa (sm_103a).  Nothing here is numerical
+// policy beyond what fa.h states: trilinear sampling with zero outside the
+// grid, fixed-point scaling for exact window sums, status-word bits.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fa.h"
+
+namespace fa {
+
+// ---------------------------------------------------------------- host side
+void set_error(const char *fmt, ...);
+void clear_error();
+fa_status cuda_fail(cudaError_t e, const char *where);
+// Counts kernel launches made by this library (read with fa_launch_count).
+void note_launch();
+
+#define FA_CUDA_TRY(expr)                                           \
+    do {                                                            \
+        cudaError_t _e = (expr);                                    \
+        if (_e != cudaSuccess) return ::fa::cuda_fail(_e, #expr);   \
+    } while (0)
+
+#define FA_TRY(expr)                        \
+    do {                                    \
+        fa_status _s = (expr);              \
+        if (_s != FA_OK) return _s;         \
+    } while (0)
+
+// Device status word bits (FA_ERR_NONFINITE / FA_ERR_TIMEOUT on the host).
+enum : unsigned { ST_NONFINITE = 1u, ST_TIMEOUT = 2u };
+
+// Workspace header, at offset 0 of every workspace libfa uses.  256 bytes.
+struct WsHeader {
+    unsigned status;           // sticky status bits of this call
+    unsigned absmax_bits[2];   // max |I|, max |J| (float bits, non-negative)
+    unsigned coef_max_bits[8]; // max |coefficient| per LNCC adjoint channel
+    unsigned step_max_bits[2]; // max_x |d(x)| per iteration parity (float bits)
+    unsigned pad0;
+    unsigned long long loss_acc; // sum of cc (or squared error) in 2^-32 fixed point
+    float loss;                // final loss of the last reduction
+    float eps_t;               // last step size
+    unsigned char pad[256 - 4 - 8 - 32 - 8 - 4 - 8 - 8];
+};
+static_assert(sizeof(WsHeader) == 256, "header must be 256 bytes");
+
+// Carves 256-byte aligned regions from a caller workspace.
+struct WsCarver {
+    char *base;
+    size_t cap, off;
+    bool ok;
+    WsCarver(void *b, size_t c) : base((char *)b), cap(c), off(0), ok(true) {}
+    template <class T>
+    T *take(size_t count) {
+        size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+        if (off + bytes > cap) {
+            ok = false;
+            return nullptr;
+        }
+        T *p = base ? (T *)(base + off) : nullptr;
+        off += bytes;
+        return p;
+    }
+};
+
+// -------------------------------------------------------------- device side
+__device__ __forceinline__ void status_set(unsigned *st, unsigned bits) { atomicOr(st, bits); }
+
+// Non-negative floats order like their bit patterns.
+__device__ __forceinline__ void atomic_max_nonneg(unsigned *slot, float v) {
+    atomicMax(slot, __float_as_uint(v));
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide max of non-negative values, then one atomic per block.
+// Every thread of the block must call it.
+__device__ __forceinline__ void block_max_to(unsigned *slot, float v, float *red /*>=32*/) {
+    int lane = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    int nthr = blockDim.x * blockDim.y * blockDim.z;
+    v = warp_max(v);
+    if ((lane & 31) == 0) red[lane >> 5] = v;
+    __syncthreads();
+    if (lane < 32) {
+        float w = (lane < (nthr + 31) / 32) ? red[lane] : 0.0f;
+        w = warp_max(w);
+        if (lane == 0 && w > 0.0f) atomic_max_nonneg(slot, w);
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void block_sum_to(unsigned long long *slot, unsigned long long v,
+                                             unsigned long long *red /*>=32*/) {
+    int lane = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    int nthr = blockDim.x * blockDim.y * blockDim.z;
+    v = warp_sum_u64(v);
+    if ((lane & 31) == 0) red[lane >> 5] = v;
+    __syncthreads();
+    if (lane < 32) {
+        unsigned long long w = (lane < (nthr + 31) / 32) ? red[lane] : 0ull;
+        w = warp_sum_u64(w);
+        if (lane == 0 && w) atomicAdd(slot, w);
+    }
+    __syncthreads();
+}
+
+// Trilinear sample of v at (z + uz, y + uy, x + ux) with zero outside the
+// grid.  The cell is floor of the position (integer part taken from u so the
+// fraction keeps full precision); gradients are the interpolant's partial
+// derivatives inside that cell.  NaN displacement gives NaN; a displacement
+// of magnitude >= 2^20 voxels samples outside (zero).
+template <bool GRAD>
+__device__ __forceinline__ float tri_sample(const float *__restrict__ v, int D, int H, int W,
+                                            int z, int y, int x, float uz, float uy, float ux,
+                                            float &gz, float &gy, float &gx) {
+    gz = gy = gx = 0.0f;
+    const float LIM = 1048576.0f;
+    if (!(fabsf(uz) < LIM && fabsf(uy) < LIM && fabsf(ux) < LIM)) {
+        if (isnan(uz) || isnan(uy) || isnan(ux)) {
+            gz = gy = gx = __int_as_float(0x7fc00000);
+            return __int_as_float(0x7fc00000);
+        }
+        return 0.0f;
+    }
+    float fz = floorf(uz), fy = floorf(uy), fx = floorf(ux);
+    int iz = z + (int)fz, iy = y + (int)fy, ix = x + (int)fx;
+    float tz = uz - fz, ty = uy - fy, tx = ux - fx;
+    if (iz < -1 || iz >= D || iy < -1 || iy >= H || ix < -1 || ix >= W) return 0.0f;
+    const bool z0 = iz >= 0, z1 = iz + 1 < D;
+    const bool y0 = iy >= 0, y1 = iy + 1 < H;
+    const bool x0 = ix >= 0, x1 = ix + 1 < W;
+    const long long HW = (long long)H * W;
+    const long long b = (long long)iz * HW + (long long)iy * W + ix;
+    float c000 = (z0 && y0 && x0) ? __ldg(v + b) : 0.0f;
+    float c001 = (z0 && y0 && x1) ? __ldg(v + b + 1) : 0.0f;
+    float c010 = (z0 && y1 && x0) ? __ldg(v + b + W) : 0.0f;
+    float c011 = (z0 && y1 && x1) ? __ldg(v + b + W + 1) : 0.0f;
+    float c100 = (z1 && y0 && x0) ? __ldg(v + b + HW) : 0.0f;
+    float c101 = (z1 && y0 && x1) ? __ldg(v + b + HW + 1) : 0.0f;
+    float c110 = (z1 && y1 && x0) ? __ldg(v + b + HW + W) : 0.0f;
+    float c111 = (z1 && y1 && x1) ? __ldg(v + b + HW + W + 1) : 0.0f;
+    float c00 = fmaf(tx, c001 - c000, c000);
+    float c01 = fmaf(tx, c011 - c010, c010);
+    float c10 = fmaf(tx, c101 - c100, c100);
+    float c11 = fmaf(tx, c111 - c110, c110);
+    float c0 = fmaf(ty, c01 - c00, c00);
+    float c1 = fmaf(ty, c11 - c10, c10);
+    if (GRAD) {
+        gz = c1 - c0;
+        gy = fmaf(tz, (c11 - c10) - (c01 - c00), c01 - c00);
+        float d00 = c001 - c000, d01 = c011 - c010, d10 = c101 - c100, d11 = c111 - c110;
+        float d0 = fmaf(ty, d01 - d00, d00), d1 = fmaf(ty, d11 - d10, d10);
+        gx = fmaf(tz, d1 - d0, d0);
+    }
+    return fmaf(tz, c1 - c0, c0);
+}
+
+// ---------------------------------------------------------- fixed point
+// Window sums of images run in 64-bit integers: values are quantised as
+// q = rint(v * 2^s) with |q| <= 2^b, b = floor((62 - ceil(log2 n)) / 2) for
+// an n-voxel window, so every sum of n products stays below 2^62 and is
+// exact (associative, order-independent).
+__host__ __device__ inline int fixed_bits_for_window(int window) {
+    long long n = (long long)window * window * window;
+    int lg = 0;
+    while ((1ll << lg) < n) ++lg;
+    return (62 - lg) / 2;
+}
+
+// Exponent s with max|v| * 2^s <= 2^bits (0 if amax is 0 or not finite).
+__device__ __forceinline__ int fixed_shift(float amax, int bits) {
+    if (!(amax > 0.0f) || !(amax <= 3.4e38f)) return 0;
+    int e;
+    frexpf(amax, &e);  // amax = m 2^e, m in [0.5, 1)  =>  amax < 2^e
+    int s = bits - e;
+    return s < -126 ? -126 : (s > 127 ? 127 : s);
+}
+
+// q = rint(v * scale) with scale = pow2f(s) (exact scaling).
+__device__ __forceinline__ long long quantize(float v, float scale) {
+    return __float2ll_rn(v * scale);
+}
+
+// int64 -> (hi, lo) floats with hi + lo == x exactly for |x| < 2^48.
+__device__ __forceinline__ void i64_to_ff(long long x, float &hi, float &lo) {
+    hi = __ll2float_rn(x);
+    lo = __ll2float_rn(x - __float2ll_rn(hi));
+}
+
+// Signed 128-bit a*b - c*d converted to float: one rounding of the exact
+// integer when it fits in 62 bits, otherwise a right shift (floor, relative
+// truncation below 2^-54) first.
+__device__ __forceinline__ float i128_diff_to_float(long long a, long long b, long long c,
+                                                    long long d) {
+    __int128 r = (__int128)a * b - (__int128)c * d;
+    __int128 m = r < 0 ? -r : r;
+    int sh = 0;
+    while ((m >> sh) >= ((__int128)1 << 62)) sh += 8;
+    float f = __ll2float_rn((long long)(r >> sh));
+    return sh ? ldexpf(f, sh) : f;
+}
+
+// 2^s as a float for s in [-126, 127] (clamped).
+__device__ __forceinline__ float pow2f(int s) {
+    s = s < -126 ? -126 : (s > 127 ? 127 : s);
+    return __int_as_float((127 + s) << 23);
+}
+
+// Launch geometry for voxel-parallel kernels: 32 x 8 threads per (x, y)
+// tile, one grid layer per z-slice.
+struct VoxGrid {
+    dim3 block, grid;
+    VoxGrid(int D, int H, int W) : block(32, 8, 1), grid((W + 31) / 32, (H + 7) / 8, D) {}
+};
+
+}  // namespace fa

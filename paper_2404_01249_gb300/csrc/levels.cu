@@ -1,0 +1,125 @@
+// Pyramid levels (Algorithm 1 "downsample"; section "Interpolation strategies
+// for multi-scale registration") and the trilinear level hand-off of u, m, nu
+// (Algorithm 1 "Upsample").  Align-corners: index i of an n_dst axis samples
+// source coordinate i (n_src - 1) / (n_dst - 1).
+#include "ops.h"
+#include "validate.h"
+
+namespace fa {
+
+__device__ __forceinline__ float ac_coord(int i, int ns, int nd) {
+    if (nd <= 1 || ns <= 1) return 0.0f;
+    return (float)(i * (ns - 1)) / (float)(nd - 1);  // both exact; one rounding
+}
+
+struct Scale3 {
+    float s[3];
+};
+
+__global__ void __launch_bounds__(256) k_resample(const float *__restrict__ src, int Ds, int Hs,
+                                                  int Ws, float *__restrict__ dst, int Dd, int Hd,
+                                                  int Wd, int C, Scale3 sc) {
+    int x = blockIdx.x * 32 + threadIdx.x;
+    int y = blockIdx.y * 8 + threadIdx.y;
+    int z = blockIdx.z;
+    if (x >= Wd || y >= Hd) return;
+    long long Ns = (long long)Ds * Hs * Ws, Nd = (long long)Dd * Hd * Wd;
+    long long i = ((long long)z * Hd + y) * Wd + x;
+    float cz = ac_coord(z, Ds, Dd), cy = ac_coord(y, Hs, Hd), cx = ac_coord(x, Ws, Wd);
+    float gz, gy, gx;
+    for (int c = 0; c < C; ++c) {
+        float v = tri_sample<false>(src + c * Ns, Ds, Hs, Ws, 0, 0, 0, cz, cy, cx, gz, gy, gx);
+        dst[c * Nd + i] = v * sc.s[c];
+    }
+}
+
+cudaError_t launch_resample(const float *src, Dims ds, float *dst, Dims dd, int C,
+                            const float *scale3, cudaStream_t s) {
+    Scale3 sc;
+    for (int c = 0; c < 3; ++c) sc.s[c] = scale3 ? scale3[c] : 1.0f;
+    VoxGrid g(dd.D, dd.H, dd.W);
+    k_resample<<<g.grid, g.block, 0, s>>>(src, ds.D, ds.H, ds.W, dst, dd.D, dd.H, dd.W, C, sc); note_launch();
+    return cudaGetLastError();
+}
+
+int level_size(int n, int s) {
+    int m = s > 0 ? n / s : 0;
+    return m < 1 ? 1 : m;
+}
+
+// Per-axis hand-off factor s_a^power, s_a = (nf - 1) / (nc - 1) (1 if degenerate).
+void handoff_scales(Dims c, Dims f, int power, float out[3]) {
+    int nc[3] = {c.D, c.H, c.W}, nf[3] = {f.D, f.H, f.W};
+    for (int a = 0; a < 3; ++a) {
+        double s = (nc[a] <= 1 || nf[a] <= 1) ? 1.0 : (double)(nf[a] - 1) / (double)(nc[a] - 1);
+        double v = power == 1 ? s : (power == -1 ? 1.0 / s : 1.0 / (s * s));
+        out[a] = (float)v;
+    }
+}
+
+// Blur (sigma = s / 2) then resample; t1, t2: N floats of the input grid.
+cudaError_t launch_pyramid_level(const float *img, Dims d, int s, float *out, Dims dl, float *t1,
+                                 float *t2, cudaStream_t st) {
+    if (s == 1) return cudaMemcpyAsync(out, img, sizeof(float) * d.N(), cudaMemcpyDeviceToDevice, st);
+    GaussTaps t;
+    if (!make_gauss_taps(0.5f * (float)s, &t)) return cudaErrorInvalidValue;
+    cudaError_t e;
+    if ((e = launch_gauss_axis(img, t1, 1, d, t, 0, st)) != cudaSuccess) return e;
+    if ((e = launch_gauss_axis(t1, t2, 1, d, t, 1, st)) != cudaSuccess) return e;
+    if ((e = launch_gauss_axis(t2, t1, 1, d, t, 2, st)) != cudaSuccess) return e;
+    return launch_resample(t1, d, out, dl, 1, nullptr, st);
+}
+
+}  // namespace fa
+
+extern "C" fa_status fa_pyramid_level(const fa_vol *img, int32_t s, fa_vol *out, void *ws,
+                                      size_t ws_bytes, void *stream) {
+    using namespace fa;
+    clear_error();
+    FA_TRY(check_vol(img, "img", 1));
+    FA_TRY(check_vol(out, "out", 1));
+    if (s < 1 || 0.5f * (float)s > kMaxSigma) {
+        set_error("fa_pyramid_level: scale must be in 1..%d (got %d)", (int)(2 * kMaxSigma),
+                  (int)s);
+        return FA_ERR_INVALID;
+    }
+    Dims d{img->D, img->H, img->W};
+    Dims dl{level_size(d.D, s), level_size(d.H, s), level_size(d.W, s)};
+    if (out->D != dl.D || out->H != dl.H || out->W != dl.W) {
+        set_error("fa_pyramid_level: out must be %dx%dx%d for scale %d", dl.D, dl.H, dl.W, (int)s);
+        return FA_ERR_SHAPE;
+    }
+    size_t need = s == 1 ? 0 : fa_gauss_workspace_size(1, d.D, d.H, d.W);
+    FA_TRY(check_ws(ws, ws_bytes, need, "fa_pyramid_level"));
+    float *t1 = nullptr, *t2 = nullptr;
+    if (s > 1) {
+        WsCarver c(ws, ws_bytes);
+        t1 = c.take<float>(d.N());
+        t2 = c.take<float>(d.N());
+    }
+    FA_CUDA_TRY(launch_pyramid_level((const float *)img->data, d, s, (float *)out->data, dl, t1, t2,
+                                     (cudaStream_t)stream));
+    return FA_OK;
+}
+
+extern "C" fa_status fa_upsample_field(const fa_vol *coarse, fa_vol *fine, int32_t power,
+                                       void *stream) {
+    using namespace fa;
+    clear_error();
+    FA_TRY(check_vol(coarse, "coarse", 3));
+    FA_TRY(check_vol(fine, "fine", 3));
+    if (power != 1 && power != -1 && power != -2) {
+        set_error("fa_upsample_field: power must be 1, -1 or -2");
+        return FA_ERR_INVALID;
+    }
+    if (coarse->data == fine->data) {
+        set_error("fa_upsample_field: fine must not alias coarse");
+        return FA_ERR_INVALID;
+    }
+    Dims c{coarse->D, coarse->H, coarse->W}, f{fine->D, fine->H, fine->W};
+    float sc[3];
+    handoff_scales(c, f, power, sc);
+    FA_CUDA_TRY(launch_resample((const float *)coarse->data, c, (float *)fine->data, f, 3, sc,
+                                (cudaStream_t)stream));
+    return FA_OK;
+}

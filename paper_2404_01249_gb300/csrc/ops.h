@@ -1,0 +1,84 @@
+// Internal launchers shared by the entry points and the registration driver.
+// Every launcher enqueues on `s` and returns the launch error (if any).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace fa {
+
+struct Dims {
+    int D, H, W;
+    long long N() const { return (long long)D * H * W; }
+};
+
+// Gaussian taps of the method (exp(-k^2 / 2 sigma^2), |k| <= ceil(3 sigma),
+// normalised); computed on the host in double, rounded to float.
+struct GaussTaps {
+    int R;          // radius; 0 = identity
+    float w[64];    // w[k + R]
+};
+bool make_gauss_taps(float sigma, GaussTaps *t);
+constexpr float kMaxSigma = 10.0f;
+
+// ---- warp (warp.cu)
+cudaError_t launch_warp(const float *Im, const float *u, float *J, float *grad, Dims d,
+                        cudaStream_t s);
+
+// ---- plain LNCC / MSE (lncc.cu)
+// Header fields used: absmax_bits, coef_max_bits, loss_acc, status.
+struct LnccBuffers {
+    long long *p0, *p1;   // [5][N] int64 each
+    float *coef;          // [5][N]: A, B, C, B', C'
+};
+size_t lncc_plain_bytes(long long N);
+cudaError_t launch_absmax2(const float *I, const float *J, long long N, WsHeader *h,
+                           cudaStream_t s);
+// Forward: coefficients and loss accumulator.  want_dI selects B', C'.
+cudaError_t launch_lncc_forward(const float *I, const float *J, Dims d, int window, float cc_eps,
+                                bool want_dI, WsHeader *h, LnccBuffers b, cudaStream_t s);
+// Backward: dJ = dL/dJ (may be NULL), dI = dL/dI (may be NULL),
+// g = dL/dJ * grad (3 channels, may be NULL; needs grad).
+cudaError_t launch_lncc_backward(const float *I, const float *J, const float *grad, Dims d,
+                                 int window, WsHeader *h, LnccBuffers b, float *dJ, float *dI,
+                                 float *g, cudaStream_t s);
+long long mse_partials_count(Dims d);  // floats of `partials` launch_mse needs
+cudaError_t launch_mse(const float *I, const float *J, const float *grad, Dims d, WsHeader *h,
+                       float *partials, float *dJ, float *dI, float *g, cudaStream_t s);
+// loss_out = sign * loss_acc * 2^-32 / N; also stored in h->loss.
+cudaError_t launch_loss_finalize(WsHeader *h, long long N, float sign, float *loss_out,
+                                 cudaStream_t s);
+cudaError_t launch_header_reset(WsHeader *h, cudaStream_t s);
+
+// ---- Gaussian (gauss.cu)
+cudaError_t launch_gauss_axis(const float *in, float *out, int C, Dims d, const GaussTaps &t,
+                              int axis, cudaStream_t s);
+// Three passes in -> t1 -> t2 -> out (t1, t2: C*N floats each).  R == 0 copies.
+cudaError_t launch_gauss3(const float *in, float *out, float *t1, float *t2, int C, Dims d,
+                          const GaussTaps &t, cudaStream_t s);
+
+// ---- Adam, step scale, compose (adam.cu)
+struct AdamConsts {
+    float b1, b2, eps, bc1, bc2;  // bc = 1 - beta^t
+};
+AdamConsts adam_consts(const fa_params *p, int t);
+fa_status check_adam_params(const fa_params *p, const char *who);
+// d = Adam direction; block max of |d| into h->step_max_bits[parity].
+cudaError_t launch_adam(const float *g, float *m, float *v, float *d, long long N, AdamConsts c,
+                        WsHeader *h, int parity, cudaStream_t s);
+// u_out = delta + u_in o (id + delta), delta = -lr / (c_lp max) d; resets the
+// other parity's max slot; eps_t to h->eps_t and eps_out (if not NULL).
+cudaError_t launch_compose(const float *u_in, const float *d, float *u_out, Dims dm, float lr,
+                           float c_lp, WsHeader *h, int parity, float *eps_out, cudaStream_t s);
+
+// ---- pyramid and hand-off (levels.cu)
+// dst channel c = scale[c] * trilinear align-corners resample of src channel c
+cudaError_t launch_resample(const float *src, Dims ds, float *dst, Dims dd, int C,
+                            const float *scale3, cudaStream_t s);
+
+int level_size(int n, int s);
+void handoff_scales(Dims c, Dims f, int power, float out[3]);
+cudaError_t launch_pyramid_level(const float *img, Dims d, int s, float *out, Dims dl, float *t1,
+                                 float *t2, cudaStream_t st);
+
+}  // namespace fa

@@ -1,0 +1,326 @@
+// Whole registration (Algorithm 1, Jacobian-free direction): pyramid, level
+// loop, iteration loop, level hand-off, final loss.  Host-side driver; every
+// step runs in this library's kernels.
+#include <math.h>
+#include <string.h>
+
+#include "ops.h"
+#include "register.h"
+#include "validate.h"
+
+namespace fa {
+
+static fa_status check_params(const fa_params *p) {
+    if (!p) {
+        set_error("params are NULL");
+        return FA_ERR_INVALID;
+    }
+    if (p->n_levels < 1 || p->n_levels > 8) {
+        set_error("n_levels must be in 1..8 (got %d)", (int)p->n_levels);
+        return FA_ERR_INVALID;
+    }
+    for (int l = 0; l < p->n_levels; ++l) {
+        if (p->scales[l] < 1 || 0.5f * (float)p->scales[l] > kMaxSigma || p->iters[l] < 0) {
+            set_error("level %d: scale must be in 1..%d and iterations >= 0", l,
+                      (int)(2 * kMaxSigma));
+            return FA_ERR_INVALID;
+        }
+    }
+    if (p->loss != FA_LOSS_LNCC && p->loss != FA_LOSS_MSE) {
+        set_error("loss must be FA_LOSS_LNCC or FA_LOSS_MSE");
+        return FA_ERR_INVALID;
+    }
+    if (p->loss == FA_LOSS_LNCC &&
+        (p->window < 1 || p->window > 15 || (p->window % 2) == 0)) {
+        set_error("window must be odd and in 1..15 (got %d)", (int)p->window);
+        return FA_ERR_INVALID;
+    }
+    if (!(p->cc_eps >= 0.0f && p->cc_eps < 3e38f)) {
+        set_error("cc_eps must be finite and >= 0");
+        return FA_ERR_INVALID;
+    }
+    GaussTaps t;
+    if (!make_gauss_taps(p->sigma_grad, &t) || !make_gauss_taps(p->sigma_warp, &t)) {
+        set_error("sigma_grad and sigma_warp must be in [0, %g]", (double)kMaxSigma);
+        return FA_ERR_INVALID;
+    }
+    if (p->mode != FA_MODE_FUSED && p->mode != FA_MODE_PLAIN) {
+        set_error("mode must be FA_MODE_FUSED or FA_MODE_PLAIN");
+        return FA_ERR_INVALID;
+    }
+    if (p->storage != FA_F32) {
+        set_error("storage dtype %d is not supported by fa_register", (int)p->storage);
+        return FA_ERR_UNSUPPORTED;
+    }
+    return check_adam_params(p, "fa_register");
+}
+
+// Workspace plan; with base == nullptr only sizes are computed.
+struct Plan {
+    Dims full;
+    Dims lvl[8];
+    long long nmax;
+    WsHeader *h;
+    float *If[8], *Im[8];
+    float *u[2], *m[2], *v[2];
+    float *J, *grad, *g, *dir, *t1, *t2;
+    LnccBuffers lb;
+    float *partials;
+    FusedBuffers fb;
+    size_t bytes;
+    bool ok;
+};
+
+static void make_plan(Plan &P, void *base, size_t cap, Dims full, const fa_params *p) {
+    P.full = full;
+    P.nmax = 0;
+    for (int l = 0; l < p->n_levels; ++l) {
+        int s = p->scales[l];
+        P.lvl[l] = Dims{level_size(full.D, s), level_size(full.H, s), level_size(full.W, s)};
+        if (P.lvl[l].N() > P.nmax) P.nmax = P.lvl[l].N();
+    }
+    long long n = P.nmax;
+    WsCarver c(base, cap);
+    P.h = c.take<WsHeader>(1);
+    for (int l = 0; l < p->n_levels; ++l) {
+        if (p->scales[l] == 1) {
+            P.If[l] = P.Im[l] = nullptr;  // the inputs themselves
+        } else {
+            P.If[l] = c.take<float>(P.lvl[l].N());
+            P.Im[l] = c.take<float>(P.lvl[l].N());
+        }
+    }
+    for (int k = 0; k < 2; ++k) {
+        P.u[k] = c.take<float>(3 * n);
+        P.m[k] = c.take<float>(3 * n);
+        P.v[k] = c.take<float>(3 * n);
+    }
+    long long tmp = 3 * n > full.N() ? 3 * n : full.N();
+    P.t1 = c.take<float>(tmp);
+    P.t2 = c.take<float>(tmp);
+    P.J = c.take<float>(n);
+    P.grad = c.take<float>(3 * n);
+    P.g = c.take<float>(3 * n);
+    P.dir = c.take<float>(3 * n);
+    Dims dmax{1, 1, (int)n};
+    long long np = 0;
+    for (int l = 0; l < p->n_levels; ++l) {
+        long long k = mse_partials_count(P.lvl[l]);
+        if (k > np) np = k;
+    }
+    (void)dmax;
+    P.partials = c.take<float>(np);
+    memset(&P.lb, 0, sizeof(P.lb));
+    memset(&P.fb, 0, sizeof(P.fb));
+    if (p->mode == FA_MODE_PLAIN) {
+        P.lb.p0 = c.take<long long>(5 * n);
+        P.lb.p1 = c.take<long long>(5 * n);
+        P.lb.coef = c.take<float>(5 * n);
+    } else {
+        fused_carve(c, n, &P.fb);
+    }
+    P.bytes = c.off;
+    P.ok = c.ok;
+}
+
+// Bytes [offsetof(coef_max_bits), offsetof(loss) ) are per-iteration state.
+static cudaError_t iter_reset(WsHeader *h, cudaStream_t s) {
+    size_t a = offsetof(WsHeader, coef_max_bits), b = offsetof(WsHeader, loss);
+    return cudaMemsetAsync((char *)h + a, 0, b - a, s);
+}
+
+struct Timer {
+    fa_kernel_timer *t;
+    int level;
+    bool on(int kernel_id) const {
+        return t && t->kernel_id == kernel_id && (t->level < 0 || t->level == level) &&
+               t->count < t->capacity;
+    }
+    cudaError_t start(int kernel_id, cudaStream_t s) const {
+        if (!on(kernel_id)) return cudaSuccess;
+        return cudaEventRecord((cudaEvent_t)t->start_events[t->count], s);
+    }
+    cudaError_t stop(int kernel_id, cudaStream_t s) const {
+        if (!on(kernel_id)) return cudaSuccess;
+        cudaError_t e = cudaEventRecord((cudaEvent_t)t->stop_events[t->count], s);
+        t->count++;
+        return e;
+    }
+};
+
+// One plain-mode iteration: u <- G_warp(compose(u, step(Adam(G_grad(dL/du))))).
+static fa_status plain_iteration(Plan &P, const fa_params *p, int l, const float *If,
+                                 const float *Im, float *u, float *u_alt, float *m, float *v,
+                                 int t, const GaussTaps &tg, const GaussTaps &tw, Timer &tm,
+                                 cudaStream_t s) {
+    Dims d = P.lvl[l];
+    long long N = d.N();
+    FA_CUDA_TRY(tm.start(FA_K_PLAIN_ANY, s));
+    FA_CUDA_TRY(iter_reset(P.h, s));
+    FA_CUDA_TRY(launch_warp(Im, u, P.J, P.grad, d, s));
+    if (p->loss == FA_LOSS_LNCC) {
+        FA_CUDA_TRY(launch_lncc_forward(If, P.J, d, p->window, p->cc_eps, false, P.h, P.lb, s));
+        FA_CUDA_TRY(launch_lncc_backward(If, P.J, P.grad, d, p->window, P.h, P.lb, nullptr,
+                                         nullptr, P.g, s));
+    } else {
+        FA_CUDA_TRY(launch_mse(If, P.J, P.grad, d, P.h, P.partials, nullptr, nullptr, P.g, s));
+    }
+    FA_CUDA_TRY(launch_gauss3(P.g, P.g, P.t1, P.t2, 3, d, tg, s));
+    int parity = t & 1;
+    FA_CUDA_TRY(launch_adam(P.g, m, v, P.dir, N, adam_consts(p, t), P.h, parity, s));
+    FA_CUDA_TRY(launch_compose(u, P.dir, u_alt, d, p->lr, p->c_lp, P.h, parity, nullptr, s));
+    FA_CUDA_TRY(launch_gauss3(u_alt, u, P.t1, P.t2, 3, d, tw, s));
+    FA_CUDA_TRY(tm.stop(FA_K_PLAIN_ANY, s));
+    return FA_OK;
+}
+
+static fa_status final_loss(Plan &P, const fa_params *p, int l, const float *If, const float *Im,
+                            const float *u, float *loss_dev, cudaStream_t s) {
+    Dims d = P.lvl[l];
+    FA_CUDA_TRY(iter_reset(P.h, s));
+    FA_CUDA_TRY(launch_warp(Im, u, P.J, nullptr, d, s));
+    if (p->loss == FA_LOSS_LNCC) {
+        if (p->mode == FA_MODE_PLAIN) {
+            FA_CUDA_TRY(launch_lncc_forward(If, P.J, d, p->window, p->cc_eps, false, P.h, P.lb, s));
+        } else {
+            FA_CUDA_TRY(fused_lncc_forward_only(If, P.J, d, p->window, p->cc_eps, P.h, P.fb, s));
+        }
+        FA_CUDA_TRY(launch_loss_finalize(P.h, d.N(), -1.0f, loss_dev, s));
+    } else {
+        FA_CUDA_TRY(launch_mse(If, P.J, nullptr, d, P.h, P.partials, nullptr, nullptr, nullptr, s));
+        if (loss_dev)
+            FA_CUDA_TRY(
+                cudaMemcpyAsync(loss_dev, &P.h->loss, sizeof(float), cudaMemcpyDeviceToDevice, s));
+    }
+    return FA_OK;
+}
+
+fa_status register_impl(const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
+                        fa_vol *u_out, float *final_loss_dev, float *final_loss_host, void *ws,
+                        size_t ws_bytes, cudaStream_t s, fa_kernel_timer *timer) {
+    FA_TRY(check_params(p));
+    FA_TRY(check_vol(fixed, "fixed", 1));
+    FA_TRY(check_vol(moving, "moving", 1));
+    FA_TRY(same_grid(fixed, moving, "fixed", "moving"));
+    FA_TRY(check_vol(u_out, "u_out", 3));
+    Dims full{fixed->D, fixed->H, fixed->W};
+    int L = p->n_levels - 1;
+    Dims last{level_size(full.D, p->scales[L]), level_size(full.H, p->scales[L]),
+              level_size(full.W, p->scales[L])};
+    if (u_out->D != last.D || u_out->H != last.H || u_out->W != last.W) {
+        set_error("u_out must be 3 x %d x %d x %d (the last level's grid)", last.D, last.H, last.W);
+        return FA_ERR_SHAPE;
+    }
+    Plan P;
+    make_plan(P, nullptr, ~size_t(0), full, p);
+    FA_TRY(check_ws(ws, ws_bytes, P.bytes, "fa_register"));
+    make_plan(P, ws, ws_bytes, full, p);
+    if (timer) {
+        if (timer->capacity < 0 || (timer->capacity > 0 && (!timer->start_events || !timer->stop_events))) {
+            set_error("fa_register_timed: bad timer");
+            return FA_ERR_INVALID;
+        }
+        timer->count = 0;
+    }
+    const float *If0 = (const float *)fixed->data, *Im0 = (const float *)moving->data;
+    GaussTaps tg, tw;
+    make_gauss_taps(p->sigma_grad, &tg);
+    make_gauss_taps(p->sigma_warp, &tw);
+    FA_CUDA_TRY(launch_header_reset(P.h, s));
+    // pyramid (once per level)
+    for (int l = 0; l < p->n_levels; ++l) {
+        if (p->scales[l] == 1) continue;
+        FA_CUDA_TRY(launch_pyramid_level(If0, full, p->scales[l], P.If[l], P.lvl[l], P.t1, P.t2, s));
+        FA_CUDA_TRY(launch_pyramid_level(Im0, full, p->scales[l], P.Im[l], P.lvl[l], P.t1, P.t2, s));
+    }
+    int cur = 0, t = 0;
+    for (int l = 0; l < p->n_levels; ++l) {
+        Dims d = P.lvl[l];
+        const float *If = p->scales[l] == 1 ? If0 : P.If[l];
+        const float *Im = p->scales[l] == 1 ? Im0 : P.Im[l];
+        if (l == 0) {
+            size_t b = sizeof(float) * 3 * d.N();
+            FA_CUDA_TRY(cudaMemsetAsync(P.u[cur], 0, b, s));
+            FA_CUDA_TRY(cudaMemsetAsync(P.m[cur], 0, b, s));
+            FA_CUDA_TRY(cudaMemsetAsync(P.v[cur], 0, b, s));
+        } else {
+            Dims c = P.lvl[l - 1];
+            float su[3], sm[3], sv[3];
+            handoff_scales(c, d, 1, su);
+            handoff_scales(c, d, -1, sm);
+            handoff_scales(c, d, -2, sv);
+            int nx = cur ^ 1;
+            FA_CUDA_TRY(launch_resample(P.u[cur], c, P.u[nx], d, 3, su, s));
+            FA_CUDA_TRY(launch_resample(P.m[cur], c, P.m[nx], d, 3, sm, s));
+            FA_CUDA_TRY(launch_resample(P.v[cur], c, P.v[nx], d, 3, sv, s));
+            cur = nx;
+        }
+        // fixed-point scale of this level's images (max |I_f|, max |I_m|)
+        FA_CUDA_TRY(cudaMemsetAsync(P.h->absmax_bits, 0, sizeof(P.h->absmax_bits), s));
+        FA_CUDA_TRY(launch_absmax2(If, Im, d.N(), P.h, s));
+        Timer tm{timer, l};
+        for (int it = 0; it < p->iters[l]; ++it) {
+            ++t;
+            if (p->mode == FA_MODE_PLAIN) {
+                FA_TRY(plain_iteration(P, p, l, If, Im, P.u[cur], P.u[cur ^ 1], P.m[cur], P.v[cur],
+                                       t, tg, tw, tm, s));
+            } else {
+                FusedIter fi;
+                fi.If = If;
+                fi.Im = Im;
+                fi.u = P.u[cur];
+                fi.u_alt = P.u[cur ^ 1];
+                fi.m = P.m[cur];
+                fi.v = P.v[cur];
+                fi.t = t;
+                FA_TRY(fused_iteration(P.fb, P.h, p, P.lvl[l], fi, tg, tw, tm.t, l, s));
+                // the fused compose writes u_alt: swap roles
+                float *tmpu = P.u[cur];
+                P.u[cur] = P.u[cur ^ 1];
+                P.u[cur ^ 1] = tmpu;
+            }
+        }
+        if (l == L) {
+            FA_TRY(final_loss(P, p, l, If, Im, P.u[cur], final_loss_dev, s));
+            FA_CUDA_TRY(cudaMemcpyAsync(u_out->data, P.u[cur], sizeof(float) * 3 * d.N(),
+                                        cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    if (final_loss_host) {
+        FA_CUDA_TRY(cudaStreamSynchronize(s));
+        FA_CUDA_TRY(cudaMemcpy(final_loss_host, &P.h->loss, sizeof(float), cudaMemcpyDeviceToHost));
+        return fa_ws_status(ws, s);
+    }
+    return FA_OK;
+}
+
+size_t register_ws_bytes(int D, int H, int W, const fa_params *p) {
+    if (D < 1 || H < 1 || W < 1 || check_params(p) != FA_OK) return 0;
+    Plan P;
+    make_plan(P, nullptr, ~size_t(0), Dims{D, H, W}, p);
+    return P.bytes;
+}
+
+}  // namespace fa
+
+extern "C" size_t fa_register_workspace_size(int32_t D, int32_t H, int32_t W, const fa_params *p) {
+    fa::clear_error();
+    return fa::register_ws_bytes(D, H, W, p);
+}
+
+extern "C" fa_status fa_register(const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
+                                 fa_vol *u_out, float *final_loss_dev, float *final_loss_host,
+                                 void *ws, size_t ws_bytes, void *stream) {
+    fa::clear_error();
+    return fa::register_impl(fixed, moving, p, u_out, final_loss_dev, final_loss_host, ws,
+                             ws_bytes, (cudaStream_t)stream, nullptr);
+}
+
+extern "C" fa_status fa_register_timed(const fa_vol *fixed, const fa_vol *moving,
+                                       const fa_params *p, fa_vol *u_out, float *final_loss_dev,
+                                       float *final_loss_host, void *ws, size_t ws_bytes,
+                                       void *stream, fa_kernel_timer *timer) {
+    fa::clear_error();
+    return fa::register_impl(fixed, moving, p, u_out, final_loss_dev, final_loss_host, ws,
+                             ws_bytes, (cudaStream_t)stream, timer);
+}

@@ -1,0 +1,32 @@
+// Fused-path interface used by the registration driver (register.cu).
+#pragma once
+#include "ops.h"
+
+namespace fa {
+
+// Scratch of the fused iteration (carved from the registration workspace).
+struct FusedBuffers {
+    float *coef;   // [3][N]: A, B, C of the LNCC adjoint
+    float *g;      // [3][N]: dL/dphi before smoothing
+    float *dir;    // [3][N]: Adam direction d
+    float *J;      // [N]    : warped image (final loss only)
+};
+void fused_carve(WsCarver &c, long long n, FusedBuffers *fb);
+
+struct FusedIter {
+    const float *If, *Im;
+    float *u, *u_alt, *m, *v;  // u_alt receives the updated displacement
+    int t;
+};
+
+fa_status fused_iteration(FusedBuffers &fb, WsHeader *h, const fa_params *p, Dims d,
+                          const FusedIter &it, const GaussTaps &tg, const GaussTaps &tw,
+                          fa_kernel_timer *timer, int level, cudaStream_t s);
+cudaError_t fused_lncc_forward_only(const float *If, const float *J, Dims d, int window,
+                                    float cc_eps, WsHeader *h, FusedBuffers &fb, cudaStream_t s);
+
+fa_status register_impl(const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
+                        fa_vol *u_out, float *final_loss_dev, float *final_loss_host, void *ws,
+                        size_t ws_bytes, cudaStream_t s, fa_kernel_timer *timer);
+
+}  // namespace fa

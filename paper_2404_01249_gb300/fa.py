@@ -1,0 +1,315 @@
+"""Thin ctypes binding of libfa (include/fa.h).
+
+Argument marshalling only: torch tensors provide device memory and the
+current CUDA stream; every step runs in libfa's kernels.  Each function has
+the name of the C entry point it calls.  If the library is missing the call
+raises; there is no fallback implementation.
+
+Layouts: volumes are float32 CUDA tensors [D, H, W] (or [1, D, H, W]);
+fields are [3, D, H, W] with channel 0 the z component, in voxels.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+from typing import Optional, Sequence
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libfa.so")
+
+FA_OK = 0
+STATUS_NAMES = {0: "FA_OK", 1: "FA_ERR_INVALID", 2: "FA_ERR_SHAPE", 3: "FA_ERR_DTYPE",
+                4: "FA_ERR_CUDA", 5: "FA_ERR_NONFINITE", 6: "FA_ERR_TIMEOUT",
+                7: "FA_ERR_UNSUPPORTED", 8: "FA_ERR_WORKSPACE"}
+FA_F32, FA_BF16, FA_F16 = 0, 1, 2
+FA_LOSS_LNCC, FA_LOSS_MSE = 0, 1
+FA_MODE_FUSED, FA_MODE_PLAIN = 0, 1
+FA_K_FUSED_WARP_LNCC, FA_K_FUSED_GRAD_ADAM, FA_K_FUSED_COMPOSE, FA_K_PLAIN_ANY = 0, 1, 2, 3
+
+EXPORTED = ["fa_params_default", "fa_status_str", "fa_last_error", "fa_warp",
+            "fa_lncc_workspace_size", "fa_lncc_fwd_bwd", "fa_mse_fwd_bwd",
+            "fa_gauss_workspace_size", "fa_gauss_smooth", "fa_radam_workspace_size",
+            "fa_radam_step", "fa_pyramid_level", "fa_upsample_field",
+            "fa_register_workspace_size", "fa_register", "fa_ws_status", "fa_register_timed",
+            "fa_launch_count"]
+
+
+class FAError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Vol(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("dtype", ctypes.c_int32), ("C", ctypes.c_int32),
+                ("D", ctypes.c_int32), ("H", ctypes.c_int32), ("W", ctypes.c_int32)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("n_levels", ctypes.c_int32), ("scales", ctypes.c_int32 * 8),
+                ("iters", ctypes.c_int32 * 8), ("lr", ctypes.c_float),
+                ("sigma_grad", ctypes.c_float), ("sigma_warp", ctypes.c_float),
+                ("window", ctypes.c_int32), ("loss", ctypes.c_int32), ("beta1", ctypes.c_float),
+                ("beta2", ctypes.c_float), ("adam_eps", ctypes.c_float),
+                ("cc_eps", ctypes.c_float), ("c_lp", ctypes.c_float), ("mode", ctypes.c_int32),
+                ("storage", ctypes.c_int32)]
+
+
+class KernelTimer(ctypes.Structure):
+    _fields_ = [("kernel_id", ctypes.c_int32), ("level", ctypes.c_int32),
+                ("capacity", ctypes.c_int32), ("count", ctypes.c_int32),
+                ("start_events", ctypes.POINTER(ctypes.c_void_p)),
+                ("stop_events", ctypes.POINTER(ctypes.c_void_p))]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads libfa.so (built by paper_2404_01249_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libfa is not built ({path} missing); run "
+                           "`python -m paper_2404_01249_gb300.build` or __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, V, vp, sz, i32, f32 = (ctypes.POINTER(Params), ctypes.POINTER(Vol), ctypes.c_void_p,
+                              ctypes.c_size_t, ctypes.c_int32, ctypes.c_float)
+    fp = ctypes.POINTER(ctypes.c_float)
+    sig = {
+        "fa_params_default": (i32, [P]),
+        "fa_status_str": (ctypes.c_char_p, [i32]),
+        "fa_last_error": (ctypes.c_char_p, []),
+        "fa_launch_count": (ctypes.c_uint64, []),
+        "fa_warp": (i32, [V, V, V, V, vp]),
+        "fa_lncc_workspace_size": (sz, [i32, i32, i32]),
+        "fa_lncc_fwd_bwd": (i32, [V, V, i32, f32, vp, V, V, vp, sz, vp]),
+        "fa_mse_fwd_bwd": (i32, [V, V, vp, V, V, vp, sz, vp]),
+        "fa_gauss_workspace_size": (sz, [i32, i32, i32, i32]),
+        "fa_gauss_smooth": (i32, [V, V, f32, vp, sz, vp]),
+        "fa_radam_workspace_size": (sz, [i32, i32, i32]),
+        "fa_radam_step": (i32, [V, V, V, V, V, i32, P, vp, vp, sz, vp]),
+        "fa_pyramid_level": (i32, [V, i32, V, vp, sz, vp]),
+        "fa_upsample_field": (i32, [V, V, i32, vp]),
+        "fa_register_workspace_size": (sz, [i32, i32, i32, P]),
+        "fa_register": (i32, [V, V, P, V, vp, fp, vp, sz, vp]),
+        "fa_ws_status": (i32, [vp, vp]),
+        "fa_register_timed": (i32, [V, V, P, V, vp, fp, vp, sz, vp,
+                                    ctypes.POINTER(KernelTimer)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != FA_OK:
+        raise FAError(status, load().fa_last_error().decode())
+
+
+def _stream() -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _vol(t: Optional[torch.Tensor], C: int):
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError("expected a contiguous float32 CUDA tensor")
+    shp = tuple(t.shape)
+    if C == 1 and len(shp) == 3:
+        shp = (1,) + shp
+    if len(shp) != 4 or shp[0] != C:
+        raise ValueError(f"expected shape [{C}, D, H, W], got {tuple(t.shape)}")
+    return ctypes.byref(Vol(t.data_ptr(), FA_F32, C, shp[1], shp[2], shp[3]))
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def workspace(nbytes: int, device=None) -> torch.Tensor:
+    """Caller-owned scratch buffer (torch allocations are 256-byte aligned)."""
+    ws = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device or "cuda")
+    assert ws.data_ptr() % 256 == 0
+    return ws
+
+
+@dataclasses.dataclass
+class RegParams:
+    scales: Sequence[int] = (4, 2, 1)
+    iters: Sequence[int] = (200, 100, 50)
+    lr: float = 0.5
+    sigma_grad: float = 1.0
+    sigma_warp: float = 0.5
+    window: int = 5
+    loss: str = "lncc"
+    beta1: float = 0.9
+    beta2: float = 0.999
+    adam_eps: float = 1e-8
+    cc_eps: float = 1e-5
+    c_lp: float = 2.0
+    mode: str = "fused"
+
+    def to_c(self) -> Params:
+        p = Params()
+        _check(load().fa_params_default(ctypes.byref(p)))
+        if len(self.scales) != len(self.iters) or not 1 <= len(self.scales) <= 8:
+            raise ValueError("1..8 levels with one iteration count each")
+        p.n_levels = len(self.scales)
+        for k, (s, t) in enumerate(zip(self.scales, self.iters)):
+            p.scales[k] = int(s)
+            p.iters[k] = int(t)
+        p.lr, p.sigma_grad, p.sigma_warp = self.lr, self.sigma_grad, self.sigma_warp
+        p.window = int(self.window)
+        p.loss = {"lncc": FA_LOSS_LNCC, "mse": FA_LOSS_MSE}[self.loss]
+        p.beta1, p.beta2, p.adam_eps = self.beta1, self.beta2, self.adam_eps
+        p.cc_eps, p.c_lp = self.cc_eps, self.c_lp
+        p.mode = {"fused": FA_MODE_FUSED, "plain": FA_MODE_PLAIN}[self.mode]
+        p.storage = FA_F32
+        return p
+
+
+def level_size(n: int, s: int) -> int:
+    return max(1, n // s)
+
+
+# ------------------------------------------------------------------ entry points
+
+def fa_warp(moving: torch.Tensor, u: torch.Tensor, want_grad: bool = True, out=None, grad=None):
+    D, H, W = moving.shape[-3:]
+    out = out if out is not None else torch.empty((D, H, W), device=moving.device)
+    if want_grad and grad is None:
+        grad = torch.empty((3, D, H, W), device=moving.device)
+    _check(load().fa_warp(_vol(moving, 1), _vol(u, 3), _vol(out, 1),
+                          _vol(grad, 3) if want_grad else None, _stream()))
+    return (out, grad) if want_grad else out
+
+
+def fa_lncc_fwd_bwd(fixed, warped, window: int = 5, cc_eps: float = 1e-5, want_dJ: bool = True,
+                    want_dI: bool = False, ws: Optional[torch.Tensor] = None):
+    D, H, W = fixed.shape[-3:]
+    lib = load()
+    need = lib.fa_lncc_workspace_size(D, H, W)
+    ws = ws if ws is not None else workspace(need, fixed.device)
+    loss = torch.empty((), device=fixed.device)
+    dJ = torch.empty((D, H, W), device=fixed.device) if want_dJ else None
+    dI = torch.empty((D, H, W), device=fixed.device) if want_dI else None
+    _check(lib.fa_lncc_fwd_bwd(_vol(fixed, 1), _vol(warped, 1), window, cc_eps, _ptr(loss),
+                               _vol(dJ, 1), _vol(dI, 1), _ptr(ws), ws.numel(), _stream()))
+    return dict(loss=loss, dJ=dJ, dI=dI)
+
+
+def fa_mse_fwd_bwd(fixed, warped, want_dJ: bool = True, want_dI: bool = False):
+    D, H, W = fixed.shape[-3:]
+    lib = load()
+    ws = workspace(lib.fa_lncc_workspace_size(D, H, W), fixed.device)
+    loss = torch.empty((), device=fixed.device)
+    dJ = torch.empty((D, H, W), device=fixed.device) if want_dJ else None
+    dI = torch.empty((D, H, W), device=fixed.device) if want_dI else None
+    _check(lib.fa_mse_fwd_bwd(_vol(fixed, 1), _vol(warped, 1), _ptr(loss), _vol(dJ, 1),
+                              _vol(dI, 1), _ptr(ws), ws.numel(), _stream()))
+    return dict(loss=loss, dJ=dJ, dI=dI)
+
+
+def fa_gauss_smooth(x: torch.Tensor, sigma: float, out=None):
+    squeeze = x.dim() == 3
+    xx = x.unsqueeze(0) if squeeze else x
+    C, D, H, W = xx.shape
+    out = out if out is not None else torch.empty_like(xx)
+    out4 = out.view(C, D, H, W)
+    lib = load()
+    ws = workspace(lib.fa_gauss_workspace_size(C, D, H, W), x.device)
+    _check(lib.fa_gauss_smooth(_vol(xx, C), _vol(out4, C), sigma, _ptr(ws), ws.numel(),
+                               _stream()))
+    return out4[0] if squeeze else out4
+
+
+def fa_radam_step(u_in, m, v, g, t: int, params: RegParams, u_out=None):
+    """Updates m, v in place; returns (u_out, eps_t as a 0-dim CUDA tensor)."""
+    D, H, W = u_in.shape[-3:]
+    lib = load()
+    u_out = u_out if u_out is not None else torch.empty_like(u_in)
+    eps_t = torch.empty((), device=u_in.device)
+    ws = workspace(lib.fa_radam_workspace_size(D, H, W), u_in.device)
+    p = params.to_c()
+    _check(lib.fa_radam_step(_vol(u_in, 3), _vol(u_out, 3), _vol(m, 3), _vol(v, 3), _vol(g, 3),
+                             t, ctypes.byref(p), _ptr(eps_t), _ptr(ws), ws.numel(), _stream()))
+    return u_out, eps_t
+
+
+def fa_pyramid_level(img: torch.Tensor, s: int):
+    D, H, W = img.shape[-3:]
+    out = torch.empty((level_size(D, s), level_size(H, s), level_size(W, s)), device=img.device)
+    lib = load()
+    ws = workspace(lib.fa_gauss_workspace_size(1, D, H, W), img.device)
+    _check(lib.fa_pyramid_level(_vol(img, 1), s, _vol(out, 1), _ptr(ws), ws.numel(), _stream()))
+    return out
+
+
+def fa_upsample_field(coarse: torch.Tensor, shape, power: int):
+    fine = torch.empty((3,) + tuple(shape), device=coarse.device)
+    _check(load().fa_upsample_field(_vol(coarse, 3), _vol(fine, 3), power, _stream()))
+    return fine
+
+
+def fa_register_workspace_size(shape, params: RegParams) -> int:
+    p = params.to_c()
+    n = load().fa_register_workspace_size(*[int(s) for s in shape], ctypes.byref(p))
+    if n == 0:
+        _check(1)
+    return n
+
+
+def fa_register(fixed, moving, params: RegParams, ws: Optional[torch.Tensor] = None,
+                sync: bool = True, u_out=None, loss_out=None, timer: Optional[KernelTimer] = None):
+    """Whole registration.  Returns dict(u=[3, d, h, w] tensor of the last
+    level, loss=0-dim CUDA tensor, final_loss=float or None if sync=False)."""
+    D, H, W = fixed.shape[-3:]
+    p = params.to_c()
+    lib = load()
+    need = lib.fa_register_workspace_size(D, H, W, ctypes.byref(p))
+    if need == 0:
+        _check(lib.fa_register_workspace_size(D, H, W, ctypes.byref(p)) or 1)
+    ws = ws if ws is not None else workspace(need, fixed.device)
+    s = params.scales[-1]
+    if u_out is None:
+        u_out = torch.empty((3, level_size(D, s), level_size(H, s), level_size(W, s)),
+                            device=fixed.device)
+    loss = loss_out if loss_out is not None else torch.empty((), device=fixed.device)
+    host = ctypes.c_float() if sync else None
+    args = (_vol(fixed, 1), _vol(moving, 1), ctypes.byref(p), _vol(u_out, 3), _ptr(loss),
+            ctypes.byref(host) if sync else None, _ptr(ws), ws.numel(), _stream())
+    if timer is None:
+        _check(lib.fa_register(*args))
+    else:
+        _check(lib.fa_register_timed(*args, ctypes.byref(timer)))
+    return dict(u=u_out, loss=loss, final_loss=host.value if sync else None)
+
+
+def fa_launch_count() -> int:
+    return int(load().fa_launch_count())
+
+
+def fa_ws_status(ws: torch.Tensor):
+    _check(load().fa_ws_status(_ptr(ws), _stream()))
+
+
+def make_timer(kernel_id: int, level: int, events_start, events_stop) -> KernelTimer:
+    """Timer over caller-created torch.cuda.Event objects (enable_timing=True)."""
+    n = len(events_start)
+    for e in list(events_start) + list(events_stop):
+        e.record()  # torch creates the underlying cudaEvent_t on first record
+    st = (ctypes.c_void_p * n)(*[ctypes.c_void_p(e.cuda_event) for e in events_start])
+    sp = (ctypes.c_void_p * n)(*[ctypes.c_void_p(e.cuda_event) for e in events_stop])
+    t = KernelTimer(kernel_id, level, n, 0, ctypes.cast(st, ctypes.POINTER(ctypes.c_void_p)),
+                    ctypes.cast(sp, ctypes.POINTER(ctypes.c_void_p)))
+    t._keep = (st, sp)
+    return t

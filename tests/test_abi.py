@@ -1,0 +1,90 @@
+"""The C ABI library builds, loads on a machine without a GPU, exports every
+entry point include/fa.h declares, and validates arguments on the host
+before touching the device."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "fa.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fa_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    import torch  # noqa: F401  (loads the CUDA runtime the library links against)
+    from paper_2404_01249_gb300 import build, fa
+    build.build()
+    return fa.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2404_01249_gb300 import fa
+    decl = declared_functions()
+    assert len(decl) >= 17
+    for name in decl:
+        assert hasattr(lib, name), name
+    assert sorted(fa.EXPORTED) == decl
+
+
+def test_params_default_and_status_strings(lib):
+    from paper_2404_01249_gb300 import fa
+    p = fa.Params()
+    assert lib.fa_params_default(ctypes.byref(p)) == 0
+    assert p.n_levels == 3 and list(p.scales[:3]) == [4, 2, 1] and list(p.iters[:3]) == [200, 100, 50]
+    assert p.window == 5 and abs(p.lr - 0.5) < 1e-7 and abs(p.c_lp - 2.0) < 1e-7
+    for s in range(9):
+        assert lib.fa_status_str(s)
+    assert lib.fa_params_default(None) == 1
+
+
+def test_workspace_queries(lib):
+    from paper_2404_01249_gb300 import fa
+    n = 160 * 192 * 224
+    assert lib.fa_lncc_workspace_size(160, 192, 224) >= 100 * n
+    assert lib.fa_gauss_workspace_size(3, 160, 192, 224) >= 24 * n
+    assert lib.fa_lncc_workspace_size(0, 1, 1) == 0
+    p = fa.RegParams().to_c()
+    assert lib.fa_register_workspace_size(160, 192, 224, ctypes.byref(p)) > 0
+    p.window = 4
+    assert lib.fa_register_workspace_size(160, 192, 224, ctypes.byref(p)) == 0
+
+
+def _vol(ptr, C, D, H, W, dtype=0):
+    from paper_2404_01249_gb300 import fa
+    return ctypes.byref(fa.Vol(ptr, dtype, C, D, H, W))
+
+
+def test_host_validation_rejects_before_launch(lib):
+    # fake (never dereferenced) device addresses: validation fails first
+    a = 1 << 20
+    ok1 = lambda: _vol(a, 1, 4, 5, 6)
+    assert lib.fa_warp(None, _vol(a, 3, 4, 5, 6), ok1(), None, None) == 1
+    assert lib.fa_warp(ok1(), _vol(a, 1, 4, 5, 6), ok1(), None, None) == 2   # u needs C=3
+    assert lib.fa_warp(ok1(), _vol(a, 3, 4, 5, 7), ok1(), None, None) == 2   # grid mismatch
+    assert lib.fa_warp(ok1(), _vol(a, 3, 4, 5, 6, dtype=1), ok1(), None, None) == 3
+    assert b"share a grid" in lib.fa_last_error() or lib.fa_last_error()
+    assert lib.fa_lncc_fwd_bwd(ok1(), ok1(), 4, 1e-5, None, None, None, None, 0, None) == 1
+    assert lib.fa_lncc_fwd_bwd(ok1(), ok1(), 5, 1e-5, None, None, None, None, 0, None) == 8
+    assert lib.fa_gauss_smooth(_vol(a, 3, 4, 5, 6), _vol(a, 3, 4, 5, 6), 11.0, None, 0, None) == 1
+    assert lib.fa_upsample_field(_vol(a, 3, 2, 2, 2), _vol(a + 4096, 3, 4, 4, 4), 2, None) == 1
+    from paper_2404_01249_gb300 import fa
+    p = fa.RegParams(mode="plain").to_c()
+    assert lib.fa_radam_step(_vol(a, 3, 4, 5, 6), _vol(a, 3, 4, 5, 6), _vol(a, 3, 4, 5, 6),
+                             _vol(a, 3, 4, 5, 6), _vol(a, 3, 4, 5, 6), 1, ctypes.byref(p), None,
+                             None, 0, None) == 1   # u_out aliases u_in
+    # u_out on the wrong grid, then a missing workspace
+    assert lib.fa_register(ok1(), ok1(), ctypes.byref(p), _vol(a, 3, 4, 5, 7), None, None, None,
+                           0, None) == 2
+    assert lib.fa_register(ok1(), ok1(), ctypes.byref(p), _vol(a, 3, 4, 5, 6), None, None, None,
+                           0, None) == 8
+    assert lib.fa_pyramid_level(_vol(a, 1, 8, 8, 8), 2, _vol(a, 1, 3, 4, 4), None, 0, None) == 2

@@ -1,0 +1,178 @@
+"""Parity of every libfa kernel entry point with the FP64 oracle (same seeded
+inputs; the oracle reads the float32 inputs as doubles).  Bar: max-abs error
+over max-abs reference <= 1e-5 for FP32 arithmetic."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2404_01249_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def rel(a, b):
+    a = a.detach().cpu().double().numpy() if torch.is_tensor(a) else np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    den = np.abs(b).max()
+    return float(np.abs(a - b).max() / (den if den > 0 else 1.0))
+
+
+@pytest.fixture(scope="module")
+def fa():
+    from paper_2404_01249_gb300 import build, fa
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    fa.load()
+    return fa
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def voronoi(shape, seed=1000):
+    f, m, _ = synth.voronoi_pair(shape=shape, seed=seed)
+    return f, m
+
+
+def smooth_field(shape, max_disp, seed):
+    return synth.random_field(shape, 3.0, max_disp, seed)
+
+
+SHAPES = [(19, 37, 45), (40, 48, 56), (1, 9, 70), (5, 3, 2)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_warp(fa, orc, shape):
+    f, m = voronoi(shape) if min(shape) > 3 else (None, np.random.default_rng(1).random(shape))
+    img = m.astype(np.float32)
+    u = smooth_field(shape, 4.0, 5)
+    J, g = fa.fa_warp(cuda(img), cuda(u))
+    Jr, gr = orc.warp(img, u)
+    assert rel(J, Jr) < TOL
+    assert rel(g, gr) < TOL
+
+
+def test_warp_outside_and_identity(fa, orc):
+    shape = (6, 7, 8)
+    img = np.random.default_rng(2).random(shape).astype(np.float32)
+    u = np.zeros((3,) + shape, np.float32)
+    J = fa.fa_warp(cuda(img), cuda(u), want_grad=False)
+    assert torch.equal(J.cpu(), torch.from_numpy(img))
+    u[:] = 50.0  # everything outside
+    J, g = fa.fa_warp(cuda(img), cuda(u))
+    assert float(J.abs().max()) == 0.0 and float(g.abs().max()) == 0.0
+    u[0] = 1.0
+    u[1] = -2.0
+    u[2] = 3.0
+    J = fa.fa_warp(cuda(img), cuda(u), want_grad=False)
+    assert np.array_equal(J.cpu().numpy(), orc.warp(img, u, want_grad=False).astype(np.float32))
+
+
+@pytest.mark.parametrize("window", [3, 5, 7])
+@pytest.mark.parametrize("shape", [(19, 37, 45), (40, 48, 56)])
+def test_lncc_fwd_bwd(fa, orc, shape, window):
+    f, m = voronoi(shape, seed=11)
+    out = fa.fa_lncc_fwd_bwd(cuda(f), cuda(m), window, 1e-5, want_dJ=True, want_dI=True)
+    ref = orc.lncc(f, m, window, np.float32(1e-5), want_dI=True)
+    assert abs(float(out["loss"]) - ref["loss"]) <= TOL * abs(ref["loss"])
+    assert rel(out["dJ"], ref["dJ"]) < TOL
+    assert rel(out["dI"], ref["dI"]) < TOL
+
+
+def test_lncc_eps_zero_and_single_outputs(fa, orc):
+    shape = (12, 17, 33)
+    r = np.random.default_rng(3)
+    f = r.random(shape).astype(np.float32)
+    m = r.random(shape).astype(np.float32)
+    for want_dJ, want_dI in [(True, False), (False, True)]:
+        out = fa.fa_lncc_fwd_bwd(cuda(f), cuda(m), 5, 0.0, want_dJ=want_dJ, want_dI=want_dI)
+        ref = orc.lncc(f, m, 5, 0.0, want_dI=True)
+        assert abs(float(out["loss"]) - ref["loss"]) <= TOL * abs(ref["loss"])
+        if want_dJ:
+            assert rel(out["dJ"], ref["dJ"]) < TOL
+        if want_dI:
+            assert rel(out["dI"], ref["dI"]) < TOL
+
+
+def test_lncc_self_is_one(fa):
+    f, _ = voronoi((20, 24, 28), seed=12)
+    out = fa.fa_lncc_fwd_bwd(cuda(f), cuda(f), 5, 0.0, want_dJ=True)
+    assert abs(float(out["loss"]) + 1.0) < 1e-6
+    assert float(out["dJ"].abs().max()) * f.size < 1e-3
+
+
+def test_mse(fa, orc):
+    shape = (19, 37, 45)
+    f, m = voronoi(shape, seed=13)
+    out = fa.fa_mse_fwd_bwd(cuda(f), cuda(m), want_dI=True)
+    ref = orc.mse(f, m)
+    assert abs(float(out["loss"]) - ref["loss"]) <= TOL * ref["loss"]
+    assert rel(out["dJ"], ref["dJ"]) < TOL
+    assert rel(out["dI"], ref["dI"]) < TOL
+
+
+@pytest.mark.parametrize("sigma", [0.0, 0.5, 1.0, 2.0, 6.0])
+def test_gauss(fa, orc, sigma):
+    shape = (19, 37, 45)
+    x = np.random.default_rng(4).standard_normal((3,) + shape).astype(np.float32)
+    y = fa.fa_gauss_smooth(cuda(x), sigma)
+    assert rel(y, orc.gauss_smooth(x, sigma)) < TOL
+    xin = cuda(x)
+    fa.fa_gauss_smooth(xin, sigma, out=xin)  # in place
+    assert rel(xin, orc.gauss_smooth(x, sigma)) < TOL
+
+
+def test_radam_step(fa, orc):
+    shape = (19, 37, 45)
+    r = np.random.default_rng(5)
+    u = smooth_field(shape, 2.0, 6)
+    m = (r.standard_normal((3,) + shape) * 1e-6).astype(np.float32)
+    v = (r.random((3,) + shape) * 1e-12).astype(np.float32)
+    g = (r.standard_normal((3,) + shape) * 1e-6).astype(np.float32)
+    params = fa.RegParams(lr=0.5)
+    mt, vt = cuda(m), cuda(v)
+    for t in (1, 7):
+        mt, vt = cuda(m), cuda(v)
+        u_out, eps = fa.fa_radam_step(cuda(u), mt, vt, cuda(g), t, params)
+        f32 = lambda x: float(np.float32(x))
+        d, mr, vr = orc.adam(g, m, v, t, f32(0.9), f32(0.999), f32(1e-8))
+        delta, er = orc.step_scale(d, 0.5, 2.0)
+        ur = orc.compose(u, delta)
+        assert rel(mt, mr) < TOL and rel(vt, vr) < TOL
+        assert abs(float(eps) - er) <= TOL * er
+        assert rel(u_out, ur) < TOL
+
+
+@pytest.mark.parametrize("s", [1, 2, 3, 4])
+def test_pyramid_level(fa, orc, s):
+    shape = (19, 37, 45)
+    f, _ = voronoi(shape, seed=14)
+    y = fa.fa_pyramid_level(cuda(f), s)
+    assert rel(y, orc.downsample(f, s)) < TOL
+
+
+@pytest.mark.parametrize("power", [1, -1, -2])
+def test_upsample_field(fa, orc, power):
+    c = smooth_field((10, 12, 14), 1.5, 7)
+    fine = (19, 24, 28)
+    y = fa.fa_upsample_field(cuda(c), fine, power)
+    assert rel(y, orc.upsample_field(c, fine, power)) < TOL
+
+
+def test_full_size_warp_and_lncc(fa, orc):
+    """160x192x224 (brain-MRI shape): warp and LNCC forward/backward in the
+    launch configuration fa_register uses, against the oracle on the whole
+    volume."""
+    shape = (160, 192, 224)
+    f, m, psi = synth.voronoi_pair(shape=shape, seed=1000)
+    u = (-0.5 * psi).astype(np.float32)
+    J, g = fa.fa_warp(cuda(m), cuda(u))
+    Jr, gr = orc.warp(m, u)
+    assert rel(J, Jr) < TOL and rel(g, gr) < TOL
+    Jn = J.cpu().numpy()
+    out = fa.fa_lncc_fwd_bwd(cuda(f), J, 5, 1e-5)
+    ref = orc.lncc(f, Jn, 5, np.float32(1e-5))
+    assert abs(float(out["loss"]) - ref["loss"]) <= TOL * abs(ref["loss"])
+    assert rel(out["dJ"], ref["dJ"]) < TOL
