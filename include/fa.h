@@ -134,6 +134,22 @@ fa_status fa_lncc_fwd_bwd(const fa_vol *fixed, const fa_vol *warped, int32_t win
                           float cc_eps, float *loss_dev, fa_vol *dL_dwarped_opt,
                           fa_vol *dL_dfixed_opt, void *ws, size_t ws_bytes, void *stream);
 
+/* Same computation and arguments as fa_lncc_fwd_bwd, for callers that
+ * cannot allocate device memory (code where cudaMalloc is forbidden or
+ * unavailable, e.g. inside another library's allocation-free section, a
+ * plugin host that owns every device allocation, or a loop that must never
+ * enter the allocator).  No workspace argument: scratch is a 64 MiB array
+ * built into the library, held by every GPU that loads it until exit, so the
+ * grid may hold at most 671,084 voxels (larger grids return FA_ERR_SHAPE
+ * before any launch).  The first call on each device looks up the array's
+ * address with that device current; make it before any stream capture.
+ * All calls share the array (each clears what must start at zero); calls
+ * that overlap on the GPU race and must be serialised by the caller.  No
+ * counterpart in the paper: an integration convenience of this library. */
+fa_status fa_lncc_fwd_bwd_noalloc(const fa_vol *fixed, const fa_vol *warped, int32_t window,
+                                  float cc_eps, float *loss_dev, fa_vol *dL_dwarped_opt,
+                                  fa_vol *dL_dfixed_opt, void *stream);
+
 /* MSE loss L = (1/N) sum (J - I)^2 (the squared-intensity cost of section
  * "Deformable Image Registration is a severely ill-conditioned problem",
  * normalised by N) and dL/dJ = 2 (J - I) / N, dL/dI = -dL/dJ.  Same argument

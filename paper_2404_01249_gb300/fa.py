@@ -34,7 +34,7 @@ EXPORTED = ["fa_params_default", "fa_status_str", "fa_last_error", "fa_warp",
             "fa_gauss_workspace_size", "fa_gauss_smooth", "fa_radam_workspace_size",
             "fa_radam_step", "fa_pyramid_level", "fa_upsample_field",
             "fa_register_workspace_size", "fa_register", "fa_ws_status", "fa_register_timed",
-            "fa_launch_count"]
+            "fa_launch_count", "fa_lncc_fwd_bwd_noalloc"]
 
 
 class FAError(RuntimeError):
@@ -88,6 +88,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "fa_warp": (i32, [V, V, V, V, vp]),
         "fa_lncc_workspace_size": (sz, [i32, i32, i32]),
         "fa_lncc_fwd_bwd": (i32, [V, V, i32, f32, vp, V, V, vp, sz, vp]),
+        "fa_lncc_fwd_bwd_noalloc": (i32, [V, V, i32, f32, vp, V, V, vp]),
         "fa_mse_fwd_bwd": (i32, [V, V, vp, V, V, vp, sz, vp]),
         "fa_gauss_workspace_size": (sz, [i32, i32, i32, i32]),
         "fa_gauss_smooth": (i32, [V, V, f32, vp, sz, vp]),
