@@ -36,12 +36,14 @@ HBM_FALLBACK_GBS = 6800.0
 # algorithmic bytes per voxel of one launch of each timed kernel (fp32
 # storage)
 ALGO_BYTES = {
-    "fused_grad_adam": 4 * (3 + 3 + 3 + 3 + 3 + 3),  # g (halo), m, v read; m, v, d written
     "fused_warp_lncc": 4 * (3 + 1 + 1 + 3),          # u, I_f, I_m read; A, B, C written
     "fused_lncc_grad": 4 * (3 + 3 + 1 + 1 + 3),      # A, B, C, u, I_f, I_m read; g written
+    "fused_smooth_adam": 4 * (3 + 3 + 3 + 3 + 3 + 3),  # g, m, v read; m, v, d written
     "fused_compose": 4 * (3 + 3 + 3),                # d, u read; u written
     "plain_iteration": 80,                           # whole plain iteration (I_f, I_m, u, m, v)
 }
+KERNEL_IDS = {"fused_warp_lncc": 0, "fused_lncc_grad": 1, "fused_smooth_adam": 2,
+              "fused_compose": 3, "plain_iteration": 4}
 
 
 def level_size(n, s):
@@ -221,8 +223,8 @@ def run_gpu(args):
 
     # kernel timer: the dominant kernel on the finest level, every step
     fin = len(WORKLOAD["scales"]) - 1
-    kid = fa.FA_K_PLAIN_ANY if args.mode == "plain" else fa.FA_K_FUSED_GRAD_ADAM
-    kname = "plain_iteration" if args.mode == "plain" else "fused_grad_adam"
+    kname = "plain_iteration" if args.mode == "plain" else args.kernel
+    kid = KERNEL_IDS[kname]
     cap = WORKLOAD["iters"][fin] * args.steps
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(cap)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(cap)]
@@ -335,8 +337,22 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="fused", choices=["fused", "plain"])
     ap.add_argument("--cpu-iters", type=int, default=2)
+    ap.add_argument("--kernel", default="fused_warp_lncc", choices=sorted(ALGO_BYTES),
+                    help="fused kernel whose finest-level launches are timed for the roofline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scales", type=int, nargs="+", default=None,
+                    help="override the pyramid scales (profiling runs; changes the workload)")
+    ap.add_argument("--iters", type=int, nargs="+", default=None,
+                    help="override the iterations per level (profiling runs)")
     args = ap.parse_args()
+    if args.scales is not None or args.iters is not None:
+        sc = tuple(args.scales or WORKLOAD["scales"])
+        it = tuple(args.iters or WORKLOAD["iters"])
+        if len(sc) != len(it):
+            ap.error("--scales and --iters need the same length")
+        WORKLOAD.update(scales=sc, iters=it,
+                        name=WORKLOAD["name"] + "_scales" + "-".join(map(str, sc)) +
+                        "_iters" + "-".join(map(str, it)))
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

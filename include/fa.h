@@ -49,7 +49,7 @@ typedef enum { FA_F32 = 0, FA_BF16 = 1, FA_F16 = 2 } fa_dtype;
 
 typedef enum { FA_LOSS_LNCC = 0, FA_LOSS_MSE = 1 } fa_loss;
 
-/* Kernel schedule used by fa_register: FA_MODE_FUSED (three fused kernels per
+/* Kernel schedule used by fa_register: FA_MODE_FUSED (four fused kernels per
  * iteration) or FA_MODE_PLAIN (one kernel per operation, intermediates in
  * HBM; the baseline the fused form is measured against).  Both compute the
  * same arithmetic. */
@@ -238,10 +238,11 @@ fa_status fa_ws_status(const void *ws, void *stream);
  * pairs recorded.  Elapsed times are then read with cudaEventElapsedTime.
  * ------------------------------------------------------------------------- */
 typedef enum {
-    FA_K_FUSED_WARP_LNCC = 0,   /* fused: warp + LNCC forward (coefficients)     */
-    FA_K_FUSED_GRAD_ADAM = 1,   /* fused: LNCC backward + Gaussian(g) + Adam     */
-    FA_K_FUSED_COMPOSE = 2,     /* fused: compose + Gaussian(u)                   */
-    FA_K_PLAIN_ANY = 3          /* plain mode: every kernel of the iteration     */
+    FA_K_FUSED_WARP_LNCC = 0,   /* fused: warp + LNCC forward (coefficients, loss)    */
+    FA_K_FUSED_LNCC_GRAD = 1,   /* fused: LNCC adjoint sums + warp gradient -> dL/du  */
+    FA_K_FUSED_SMOOTH_ADAM = 2, /* fused: Gaussian(sigma_grad) + Adam + max |d|       */
+    FA_K_FUSED_COMPOSE = 3,     /* fused: compose + Gaussian(sigma_warp)              */
+    FA_K_PLAIN_ANY = 4          /* plain mode: every kernel of one iteration          */
 } fa_kernel_id;
 
 typedef struct {

@@ -117,66 +117,101 @@ __device__ __forceinline__ void block_sum_to(unsigned long long *slot, unsigned 
 }
 
 // Trilinear sample of v at (z + uz, y + uy, x + ux) with zero outside the
-// grid.  The cell is floor of the position (integer part taken from u so the
-// fraction keeps full precision); gradients are the interpolant's partial
-// derivatives inside that cell.  NaN displacement gives NaN; a displacement
-// of magnitude >= 2^20 voxels samples outside (zero).
-template <bool GRAD>
-__device__ __forceinline__ float tri_sample(const float *__restrict__ v, int D, int H, int W,
-                                            int z, int y, int x, float uz, float uy, float ux,
-                                            float &gz, float &gy, float &gx) {
-    gz = gy = gx = 0.0f;
+// grid, split in two halves so that the eight corner loads can be issued
+// early and consumed later.  The cell is floor of the position (integer
+// part taken from u so the fraction keeps full precision); gradients are the
+// interpolant's partial derivatives inside that cell.  NaN displacement
+// gives NaN; a displacement of magnitude >= 2^20 voxels samples outside.
+struct TriPending {
+    float c000, c001, c010, c011, c100, c101, c110, c111;
+    float tz, ty, tx;
+};
+
+__device__ __forceinline__ void tri_issue(TriPending &p, const float *__restrict__ v, int D,
+                                          int H, int W, int z, int y, int x, float uz, float uy,
+                                          float ux) {
+    p.c000 = p.c001 = p.c010 = p.c011 = p.c100 = p.c101 = p.c110 = p.c111 = 0.0f;
+    p.tz = p.ty = p.tx = 0.0f;
     const float LIM = 1048576.0f;
     if (!(fabsf(uz) < LIM && fabsf(uy) < LIM && fabsf(ux) < LIM)) {
-        if (isnan(uz) || isnan(uy) || isnan(ux)) {
-            gz = gy = gx = __int_as_float(0x7fc00000);
-            return __int_as_float(0x7fc00000);
-        }
-        return 0.0f;
+        if (isnan(uz) || isnan(uy) || isnan(ux)) p.c000 = __int_as_float(0x7fc00000);
+        p.tz = p.ty = p.tx = isnan(uz) || isnan(uy) || isnan(ux) ? __int_as_float(0x7fc00000) : 0.0f;
+        return;
     }
     float fz = floorf(uz), fy = floorf(uy), fx = floorf(ux);
     int iz = z + (int)fz, iy = y + (int)fy, ix = x + (int)fx;
-    float tz = uz - fz, ty = uy - fy, tx = ux - fx;
-    if (iz < -1 || iz >= D || iy < -1 || iy >= H || ix < -1 || ix >= W) return 0.0f;
+    p.tz = uz - fz;
+    p.ty = uy - fy;
+    p.tx = ux - fx;
+    if (iz < -1 || iz >= D || iy < -1 || iy >= H || ix < -1 || ix >= W) return;
     const bool z0 = iz >= 0, z1 = iz + 1 < D;
     const bool y0 = iy >= 0, y1 = iy + 1 < H;
     const bool x0 = ix >= 0, x1 = ix + 1 < W;
     const long long HW = (long long)H * W;
     const long long b = (long long)iz * HW + (long long)iy * W + ix;
-    float c000 = (z0 && y0 && x0) ? __ldg(v + b) : 0.0f;
-    float c001 = (z0 && y0 && x1) ? __ldg(v + b + 1) : 0.0f;
-    float c010 = (z0 && y1 && x0) ? __ldg(v + b + W) : 0.0f;
-    float c011 = (z0 && y1 && x1) ? __ldg(v + b + W + 1) : 0.0f;
-    float c100 = (z1 && y0 && x0) ? __ldg(v + b + HW) : 0.0f;
-    float c101 = (z1 && y0 && x1) ? __ldg(v + b + HW + 1) : 0.0f;
-    float c110 = (z1 && y1 && x0) ? __ldg(v + b + HW + W) : 0.0f;
-    float c111 = (z1 && y1 && x1) ? __ldg(v + b + HW + W + 1) : 0.0f;
-    float c00 = fmaf(tx, c001 - c000, c000);
-    float c01 = fmaf(tx, c011 - c010, c010);
-    float c10 = fmaf(tx, c101 - c100, c100);
-    float c11 = fmaf(tx, c111 - c110, c110);
+    if (z0 && y0 && x0) p.c000 = __ldg(v + b);
+    if (z0 && y0 && x1) p.c001 = __ldg(v + b + 1);
+    if (z0 && y1 && x0) p.c010 = __ldg(v + b + W);
+    if (z0 && y1 && x1) p.c011 = __ldg(v + b + W + 1);
+    if (z1 && y0 && x0) p.c100 = __ldg(v + b + HW);
+    if (z1 && y0 && x1) p.c101 = __ldg(v + b + HW + 1);
+    if (z1 && y1 && x0) p.c110 = __ldg(v + b + HW + W);
+    if (z1 && y1 && x1) p.c111 = __ldg(v + b + HW + W + 1);
+}
+
+template <bool GRAD>
+__device__ __forceinline__ float tri_finish(const TriPending &p, float &gz, float &gy, float &gx) {
+    const float tz = p.tz, ty = p.ty, tx = p.tx;
+    float c00 = fmaf(tx, p.c001 - p.c000, p.c000);
+    float c01 = fmaf(tx, p.c011 - p.c010, p.c010);
+    float c10 = fmaf(tx, p.c101 - p.c100, p.c100);
+    float c11 = fmaf(tx, p.c111 - p.c110, p.c110);
     float c0 = fmaf(ty, c01 - c00, c00);
     float c1 = fmaf(ty, c11 - c10, c10);
     if (GRAD) {
         gz = c1 - c0;
         gy = fmaf(tz, (c11 - c10) - (c01 - c00), c01 - c00);
-        float d00 = c001 - c000, d01 = c011 - c010, d10 = c101 - c100, d11 = c111 - c110;
+        float d00 = p.c001 - p.c000, d01 = p.c011 - p.c010, d10 = p.c101 - p.c100,
+              d11 = p.c111 - p.c110;
         float d0 = fmaf(ty, d01 - d00, d00), d1 = fmaf(ty, d11 - d10, d10);
         gx = fmaf(tz, d1 - d0, d0);
+    } else {
+        gz = gy = gx = 0.0f;
     }
     return fmaf(tz, c1 - c0, c0);
 }
 
+template <bool GRAD>
+__device__ __forceinline__ float tri_sample(const float *__restrict__ v, int D, int H, int W,
+                                            int z, int y, int x, float uz, float uy, float ux,
+                                            float &gz, float &gy, float &gx) {
+    TriPending p;
+    tri_issue(p, v, D, H, W, z, y, x, uz, uy, ux);
+    return tri_finish<GRAD>(p, gz, gy, gx);
+}
+
 // ---------------------------------------------------------- fixed point
 // Window sums of images run in 64-bit integers: values are quantised as
-// q = rint(v * 2^s) with |q| <= 2^b, b = floor((62 - ceil(log2 n)) / 2) for
-// an n-voxel window, so every sum of n products stays below 2^62 and is
-// exact (associative, order-independent).
-__host__ __device__ inline int fixed_bits_for_window(int window) {
+// q = rint(v * 2^s) with |q| <= 2^b (b from lncc_image_bits), so every sum
+// is exact (associative, order-independent).
+
+// Image bits used by every LNCC path: with |q| <= 2^b every 3-D window sum
+// of n products stays below 2^62 (b = floor((62 - ceil(log2 n)) / 2)); the
+// numerators n S_II - S_I^2 are then formed exactly in 128-bit integers.
+__host__ __device__ inline int lncc_image_bits(int window) {
     long long n = (long long)window * window * window;
     int lg = 0;
     while ((1ll << lg) < n) ++lg;
     return (62 - lg) / 2;
+}
+
+// Bits of the quantised LNCC adjoint coefficients: 3-D sums stay below 2^47
+// so that they convert to float-float exactly.
+__host__ __device__ inline int lncc_coef_bits(int window) {
+    long long n = (long long)window * window * window;
+    int lg = 0;
+    while ((1ll << lg) < n) ++lg;
+    return 47 - lg;
 }
 
 // Exponent s with max|v| * 2^s <= 2^bits (0 if amax is 0 or not finite).
@@ -199,17 +234,17 @@ __device__ __forceinline__ void i64_to_ff(long long x, float &hi, float &lo) {
     lo = __ll2float_rn(x - __float2ll_rn(hi));
 }
 
-// Signed 128-bit a*b - c*d converted to float: one rounding of the exact
-// integer when it fits in 62 bits, otherwise a right shift (floor, relative
-// truncation below 2^-54) first.
-__device__ __forceinline__ float i128_diff_to_float(long long a, long long b, long long c,
-                                                    long long d) {
-    __int128 r = (__int128)a * b - (__int128)c * d;
-    __int128 m = r < 0 ? -r : r;
-    int sh = 0;
-    while ((m >> sh) >= ((__int128)1 << 62)) sh += 8;
-    float f = __ll2float_rn((long long)(r >> sh));
-    return sh ? ldexpf(f, sh) : f;
+// n a - b c for int64 operands, formed exactly in 128 bits and rounded to
+// float (one rounding when the result fits 64 bits; otherwise the two halves
+// are scaled and added, within one float ulp).
+__device__ __forceinline__ float diff_i128_to_float(long long n, long long a, long long b,
+                                                    long long c) {
+    const __int128 r = (__int128)n * a - (__int128)b * c;
+    const long long hi = (long long)(r >> 64);
+    const unsigned long long lo = (unsigned long long)r;
+    if (hi == 0) return __ull2float_rn(lo);
+    if (hi == -1 && (long long)lo < 0) return __ll2float_rn((long long)lo);
+    return fmaf(__ll2float_rn(hi), 18446744073709551616.0f, __ull2float_rn(lo));
 }
 
 // 2^s as a float for s in [-126, 127] (clamped).

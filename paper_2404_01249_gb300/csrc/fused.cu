@@ -1,26 +1,1072 @@
 // Fused per-iteration kernels of fa_register (FA_MODE_FUSED).
+//
+// One iteration of Algorithm 1 (Jacobian-free direction) is four launches:
+//   K1 k_lncc_fwd       LNCC forward on J = I_m o phi: exact int64 window
+//                       sums, cc, the adjoint coefficients A, B, C, the loss
+//                       accumulator and the coefficient maxima.
+//   K2 k_lncc_grad      adjoint window sums of A, B, C; J and grad I_m o phi
+//                       at the output voxel; g = dL/dJ grad.
+//   K3 k_smooth_adam    Gaussian(sigma_grad) of g, Adam update of m, nu, the
+//                       direction d and the grid max |d|.
+//   K4 k_compose        delta = -eps_t d, u' = delta + u o (id + delta),
+//                       Gaussian(sigma_warp) of u', and J = I_m o (id + u) of
+//                       the new map for the next iteration's K1.
+// The grid max of K3 is a global dependency, so K4 cannot join K3; the
+// adjoint window sums need A, B, C around every output, so K2 cannot join K1
+// without recomputing a much wider halo.
+//
+// Every kernel marches along z ("2.5-D" tiling): a CTA owns a 32 x TY tile of
+// (x, y) columns and a slab of TZ output planes.  Plane inputs (tile plus
+// halo) arrive through a three-stage cp.async pipeline two planes ahead of
+// the plane being reduced; the plane is reduced along x and then y in shared
+// memory, and the last 2R + 1 in-plane results per output column sit in a
+// shared-memory ring from which the z-reduction reads.  No intermediate of
+// the separable sums goes to HBM; halo re-reads hit L2.
+#include <math.h>
+
+#include <mutex>
+
 #include "register.h"
 #include "validate.h"
 
 namespace fa {
+
+namespace {
+
+constexpr int FX = 32;  // tile width along x (one warp)
+constexpr int NST = 3;  // cp.async pipeline stages
+
+__device__ __forceinline__ void cp4(void *dst, const float *src, bool ok) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src),
+                 "r"(ok ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Issues the copies of C channel planes of a [C][D][H][W] field onto a
+// [C][RY][RX] shared tile whose (0, 0) is voxel (ybase, xbase) of plane zp;
+// outside the grid the tile reads zero.  Thread t copies positions
+// k = t, t + NT, ... (the consumers that read only their own positions need
+// no barrier after the wait).
+template <int C, int RY, int RX, int NT>
+__device__ __forceinline__ void load_tile(float *dst, const float *src, long long N, int D, int H,
+                                          int W, int zp, int ybase, int xbase, int tid) {
+    const bool zok = zp >= 0 && zp < D;
+    for (int k = tid; k < RY * RX; k += NT) {
+        const int ry = k / RX, rx = k - ry * RX;
+        const int y = ybase + ry, x = xbase + rx;
+        const bool ok = zok && y >= 0 && y < H && x >= 0 && x < W;
+        const long long i = ok ? ((long long)zp * H + y) * W + x : 0;
+#pragma unroll
+        for (int c = 0; c < C; ++c) cp4(dst + c * RY * RX + k, src + c * N + i, ok);
+    }
+}
+
+// Copies C channels at this thread's OPT output voxels of plane z.
+template <int C, int NT, int OPT, int NW>
+__device__ __forceinline__ void load_outputs(float *dst, const float *src, long long N, int D,
+                                             int H, int W, int z, int y0, int x0, int wy, int tx,
+                                             int tid) {
+    constexpr int NOUT = NT * OPT;
+#pragma unroll
+    for (int o = 0; o < OPT; ++o) {
+        const int y = y0 + wy + NW * o, x = x0 + tx;
+        const bool ok = z >= 0 && z < D && y < H && x < W;
+        const long long i = ok ? ((long long)z * H + y) * W + x : 0;
+#pragma unroll
+        for (int c = 0; c < C; ++c) cp4(dst + c * NOUT + o * NT + tid, src + c * N + i, ok);
+    }
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void ff_add(float &h, float &l, float bh, float bl) {
+    float s, e;
+    two_sum(h, bh, s, e);
+    e += l + bl;
+    h = s + e;
+    l = e - (h - s);
+}
+
+__device__ __forceinline__ void ff_mul_f(float a, float xh, float xl, float &h, float &l) {
+    h = a * xh;
+    l = fmaf(a, xh, -h);
+    l = fmaf(a, xl, l);
+}
+
+// ====================================================================== K1
+template <int R, int NW, int OPT>
+struct K1S {
+    static constexpr int NT = FX * NW, TY = NW * OPT, RX = FX + 2 * R, RY = TY + 2 * R;
+    static constexpr int NR = RX * RY, NS = 2 * R + 1, NOUT = NT * OPT;
+    static constexpr size_t o_ring = 0;                                     // [NS][5][NOUT] int64
+    static constexpr size_t o_xL = o_ring + (size_t)NS * 5 * NOUT * 8;      // [5][RY][FX] int64
+    static constexpr size_t o_q = o_xL + (size_t)5 * RY * FX * 8;           // [2][NR] int32
+    static constexpr size_t o_st = o_q + (size_t)2 * NR * 4;                // [NST][2][NR] f32
+    static constexpr size_t bytes = o_st + (size_t)NST * 2 * NR * 4;
+};
+
+template <int R, int NW, int OPT>
+__global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const float *__restrict__ If,
+                                                     const float *__restrict__ J,
+                                                     float *__restrict__ coef,
+                                                     WsHeader *__restrict__ h, int D, int H, int W,
+                                                     int TZ, int bits, float cc_eps, int window,
+                                                     int write_coef) {
+    using S = K1S<R, NW, OPT>;
+    constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, NR = S::NR, NS = S::NS,
+                  NOUT = S::NOUT;
+    extern __shared__ __align__(16) unsigned char smem[];
+    long long *ring = (long long *)(smem + S::o_ring);
+    long long *xL = (long long *)(smem + S::o_xL);
+    int *qI = (int *)(smem + S::o_q), *qJ = qI + NR;
+    float *st = (float *)(smem + S::o_st);
+    __shared__ float redf[32];
+    __shared__ unsigned long long redu[32];
+
+    const int tx = threadIdx.x, wy = threadIdx.y, tid = wy * FX + tx;
+    const int x0 = blockIdx.x * FX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+    const int zend = min(z0 + TZ, D);
+    const long long N = (long long)D * H * W, HW = (long long)H * W;
+    const float amax =
+        fmaxf(__uint_as_float(h->absmax_bits[0]), __uint_as_float(h->absmax_bits[1]));
+    const int sh = fixed_shift(amax, bits);
+    const float scale = pow2f(sh), inv_s = pow2f(-sh);
+    const long long n = (long long)window * window * window;
+    const float nf = (float)n, inv_nf = 1.0f / nf;
+
+    for (int k = tid; k < NS * 5 * NOUT; k += NT) ring[k] = 0;
+    long long acc[OPT][5];
+#pragma unroll
+    for (int o = 0; o < OPT; ++o)
+#pragma unroll
+        for (int c = 0; c < 5; ++c) acc[o][c] = 0;
+
+    const int zs = z0 - R, np = zend - z0 + 2 * R;
+    auto issue = [&](int i) {
+        if (i < np) {
+            float *dst = st + (i % NST) * 2 * NR;
+            load_tile<1, RY, RX, NT>(dst, If, N, D, H, W, zs + i, y0 - R, x0 - R, tid);
+            load_tile<1, RY, RX, NT>(dst + NR, J, N, D, H, W, zs + i, y0 - R, x0 - R, tid);
+        }
+        cp_commit();
+    };
+    issue(0);
+    issue(1);
+
+    unsigned long long qcc = 0;
+    float mA = 0.f, mB = 0.f, mC = 0.f;
+    bool bad = false;
+    int slot = 0;
+    for (int i = 0; i < np; ++i) {
+        const int zp = zs + i;
+        issue(i + 2);
+        cp_wait<2>();
+        long long P[OPT][5];
+        if (zp >= 0 && zp < D) {
+            const float *sI = st + (i % NST) * 2 * NR, *sJ = sI + NR;
+            for (int k = tid; k < NR; k += NT) {  // own copies: no barrier needed
+                qI[k] = __float2int_rn(sI[k] * scale);
+                qJ[k] = __float2int_rn(sJ[k] * scale);
+            }
+            __syncthreads();
+            for (int k = tid; k < RY * FX; k += NT) {
+                const int ry = k >> 5, ox = k & 31;
+                const int *a = qI + ry * RX + ox, *b = qJ + ry * RX + ox;
+                long long s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0;
+#pragma unroll
+                for (int t = 0; t <= 2 * R; ++t) {
+                    const int va = a[t], vb = b[t];
+                    s1 += va;
+                    s2 += vb;
+                    s3 += (long long)va * va;
+                    s4 += (long long)vb * vb;
+                    s5 += (long long)va * vb;
+                }
+                xL[k] = s1;
+                xL[RY * FX + k] = s2;
+                xL[2 * RY * FX + k] = s3;
+                xL[3 * RY * FX + k] = s4;
+                xL[4 * RY * FX + k] = s5;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int o = 0; o < OPT; ++o) {
+                const int ty = wy + NW * o;
+#pragma unroll
+                for (int c = 0; c < 5; ++c) {
+                    long long sum = 0;
+#pragma unroll
+                    for (int t = 0; t <= 2 * R; ++t) sum += xL[c * RY * FX + (ty + t) * FX + tx];
+                    P[o][c] = sum;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int o = 0; o < OPT; ++o)
+#pragma unroll
+                for (int c = 0; c < 5; ++c) P[o][c] = 0;
+        }
+#pragma unroll
+        for (int o = 0; o < OPT; ++o) {
+            const int idx = o * NT + tid;
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                long long *r = ring + (slot * 5 + c) * NOUT + idx;
+                acc[o][c] += P[o][c] - *r;
+                *r = P[o][c];
+            }
+        }
+        slot = (slot + 1 == NS) ? 0 : slot + 1;
+        const int z = zp - R;
+        if (z >= z0 && z < zend) {
+#pragma unroll
+            for (int o = 0; o < OPT; ++o) {
+                const int y = y0 + wy + NW * o, x = x0 + tx;
+                if (y >= H || x >= W) continue;
+                const long long a1 = acc[o][0], a2 = acc[o][1];
+                const float varI = diff_i128_to_float(n, acc[o][2], a1, a1) * inv_s * inv_s * inv_nf;
+                const float varJ = diff_i128_to_float(n, acc[o][3], a2, a2) * inv_s * inv_s * inv_nf;
+                const float cross = diff_i128_to_float(n, acc[o][4], a1, a2) * inv_s * inv_s * inv_nf;
+                const float den = fmaf(varI, varJ, cc_eps);
+                const float cc = cross * cross / den;
+                if (cc >= 0.0f && cc <= 2.0f)
+                    qcc += (unsigned long long)__float2ull_rn(cc * 4294967296.0f);
+                else
+                    bad = true;
+                if (write_coef) {
+                    const float SIf = __ll2float_rn(a1) * inv_s, SJf = __ll2float_rn(a2) * inv_s;
+                    const float A = 2.0f * cross / den;
+                    const float B = -cc * varI / den;
+                    const float C = -(A * SIf + 2.0f * B * SJf) / nf;
+                    const long long gi = (long long)z * HW + (long long)y * W + x;
+                    coef[gi] = A;
+                    coef[N + gi] = B;
+                    coef[2 * N + gi] = C;
+                    mA = fmaxf(mA, fabsf(A));
+                    mB = fmaxf(mB, fabsf(B));
+                    mC = fmaxf(mC, fabsf(C));
+                }
+            }
+        }
+    }
+    cp_wait<0>();
+    if (bad) status_set(&h->status, ST_NONFINITE);
+    block_sum_to(&h->loss_acc, qcc, redu);
+    if (write_coef) {
+        block_max_to(&h->coef_max_bits[0], mA, redf);
+        block_max_to(&h->coef_max_bits[1], mB, redf);
+        block_max_to(&h->coef_max_bits[2], mC, redf);
+    }
+}
+
+// ====================================================================== K2
+template <int R, int NW, int OPT>
+struct K2S {
+    static constexpr int NT = FX * NW, TY = NW * OPT, RX = FX + 2 * R, RY = TY + 2 * R;
+    static constexpr int NR = RX * RY, NS = 2 * R + 1, NOUT = NT * OPT;
+    static constexpr size_t o_ring = 0;
+    static constexpr size_t o_xL = o_ring + (size_t)NS * 3 * NOUT * 8;
+    static constexpr size_t o_q = o_xL + (size_t)3 * RY * FX * 8;
+    static constexpr size_t o_st = o_q + (size_t)3 * NR * 8;
+    static constexpr size_t o_ost = o_st + (size_t)NST * 3 * NR * 4;
+    static constexpr size_t bytes = o_ost + (size_t)NST * 4 * NOUT * 4;
+};
+
+template <int R, int NW, int OPT>
+__global__ void __launch_bounds__(FX *NW) k_lncc_grad(const float *__restrict__ If,
+                                                      const float *__restrict__ Im,
+                                                      const float *__restrict__ u,
+                                                      const float *__restrict__ coef,
+                                                      const WsHeader *__restrict__ h,
+                                                      float *__restrict__ g, int D, int H, int W,
+                                                      int TZ, int cbits) {
+    using S = K2S<R, NW, OPT>;
+    constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, NR = S::NR, NS = S::NS,
+                  NOUT = S::NOUT;
+    extern __shared__ __align__(16) unsigned char smem[];
+    long long *ring = (long long *)(smem + S::o_ring);
+    long long *xL = (long long *)(smem + S::o_xL);
+    long long *q = (long long *)(smem + S::o_q);
+    float *st = (float *)(smem + S::o_st);
+    float *ost = (float *)(smem + S::o_ost);
+
+    const int tx = threadIdx.x, wy = threadIdx.y, tid = wy * FX + tx;
+    const int x0 = blockIdx.x * FX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+    const int zend = min(z0 + TZ, D);
+    const long long N = (long long)D * H * W, HW = (long long)H * W;
+    float qs[3], us[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int e = fixed_shift(__uint_as_float(h->coef_max_bits[c]), cbits);
+        qs[c] = pow2f(e);
+        us[c] = pow2f(-e);
+    }
+    const float inv_n = 1.0f / (float)N;
+
+    for (int k = tid; k < NS * 3 * NOUT; k += NT) ring[k] = 0;
+    long long acc[OPT][3];
+#pragma unroll
+    for (int o = 0; o < OPT; ++o)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[o][c] = 0;
+
+    const int zs = z0 - R, np = zend - z0 + 2 * R;
+    auto issue = [&](int i) {
+        if (i < np) {
+            const int zp = zs + i, zo = zp - R;
+            load_tile<3, RY, RX, NT>(st + (i % NST) * 3 * NR, coef, N, D, H, W, zp, y0 - R, x0 - R,
+                                     tid);
+            if (zo >= z0 && zo < zend) {
+                float *o = ost + (i % NST) * 4 * NOUT;
+                load_outputs<3, NT, OPT, NW>(o, u, N, D, H, W, zo, y0, x0, wy, tx, tid);
+                load_outputs<1, NT, OPT, NW>(o + 3 * NOUT, If, N, D, H, W, zo, y0, x0, wy, tx, tid);
+            }
+        }
+        cp_commit();
+    };
+    issue(0);
+    issue(1);
+
+    int slot = 0;
+    for (int i = 0; i < np; ++i) {
+        const int zp = zs + i, zo = zp - R;
+        issue(i + 2);
+        cp_wait<2>();
+        const bool out = zo >= z0 && zo < zend;
+        // warp gathers for this plane's outputs, consumed after the reductions
+        TriPending tp[OPT];
+        float Iv[OPT];
+        if (out) {
+            const float *o = ost + (i % NST) * 4 * NOUT;
+#pragma unroll
+            for (int k = 0; k < OPT; ++k) {
+                const int idx = k * NT + tid, y = y0 + wy + NW * k, x = x0 + tx;
+                tri_issue(tp[k], Im, D, H, W, zo, y, x, o[idx], o[NOUT + idx], o[2 * NOUT + idx]);
+                Iv[k] = o[3 * NOUT + idx];
+            }
+        }
+        long long P[OPT][3];
+        if (zp >= 0 && zp < D) {
+            const float *s = st + (i % NST) * 3 * NR;
+            for (int k = tid; k < NR; k += NT) {  // own copies
+                q[k] = quantize(s[k], qs[0]);
+                q[NR + k] = quantize(s[NR + k], qs[1]);
+                q[2 * NR + k] = quantize(s[2 * NR + k], qs[2]);
+            }
+            __syncthreads();
+            for (int k = tid; k < RY * FX; k += NT) {
+                const int ry = k >> 5, ox = k & 31;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const long long *src = q + c * NR + ry * RX + ox;
+                    long long sum = 0;
+#pragma unroll
+                    for (int t = 0; t <= 2 * R; ++t) sum += src[t];
+                    xL[c * RY * FX + k] = sum;
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int o = 0; o < OPT; ++o) {
+                const int ty = wy + NW * o;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    long long sum = 0;
+#pragma unroll
+                    for (int t = 0; t <= 2 * R; ++t) sum += xL[c * RY * FX + (ty + t) * FX + tx];
+                    P[o][c] = sum;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int o = 0; o < OPT; ++o)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) P[o][c] = 0;
+        }
+#pragma unroll
+        for (int o = 0; o < OPT; ++o) {
+            const int idx = o * NT + tid;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                long long *r = ring + (slot * 3 + c) * NOUT + idx;
+                acc[o][c] += P[o][c] - *r;
+                *r = P[o][c];
+            }
+        }
+        slot = (slot + 1 == NS) ? 0 : slot + 1;
+        if (out) {
+#pragma unroll
+            for (int o = 0; o < OPT; ++o) {
+                const int y = y0 + wy + NW * o, x = x0 + tx;
+                if (y >= H || x >= W) continue;
+                const long long gi = (long long)zo * HW + (long long)y * W + x;
+                float gz, gy, gx;
+                const float Jv = tri_finish<true>(tp[o], gz, gy, gx);
+                float ah, al, bh, bl, ch, cl, rh, rl, th, tl;
+                i64_to_ff(acc[o][0], ah, al);
+                i64_to_ff(acc[o][1], bh, bl);
+                i64_to_ff(acc[o][2], ch, cl);
+                ff_mul_f(Iv[o], ah * us[0], al * us[0], rh, rl);       // I SA
+                ff_mul_f(2.0f * Jv, bh * us[1], bl * us[1], th, tl);   // 2 J SB
+                ff_add(rh, rl, th, tl);
+                ff_add(rh, rl, ch * us[2], cl * us[2]);                // + SC
+                const float dj = -(rh + rl) * inv_n;
+                g[gi] = dj * gz;
+                g[N + gi] = dj * gy;
+                g[2 * N + gi] = dj * gx;
+            }
+        }
+    }
+    cp_wait<0>();
+}
+
+// MSE: g = 2 (J - I) / N * grad I_m o phi (pointwise).
+__global__ void __launch_bounds__(256) k_fused_mse_grad(const float *__restrict__ If,
+                                                        const float *__restrict__ Im,
+                                                        const float *__restrict__ u,
+                                                        float *__restrict__ g, int D, int H,
+                                                        int W) {
+    int x = blockIdx.x * 32 + threadIdx.x;
+    int y = blockIdx.y * 8 + threadIdx.y;
+    int z = blockIdx.z;
+    if (x >= W || y >= H) return;
+    long long N = (long long)D * H * W;
+    long long i = ((long long)z * H + y) * W + x;
+    float gz, gy, gx;
+    float Jv = tri_sample<true>(Im, D, H, W, z, y, x, __ldg(u + i), __ldg(u + N + i),
+                                __ldg(u + 2 * N + i), gz, gy, gx);
+    float dj = 2.0f * (Jv - __ldg(If + i)) / (float)N;
+    g[i] = dj * gz;
+    g[N + i] = dj * gy;
+    g[2 * N + i] = dj * gx;
+}
+
+// ====================================================== separable Gaussian
+// x pass of a [3][RY][RX] plane onto [3][RY][FX], then this thread's y pass.
+template <int RG, int RY, int RX, int NT, int NW, int OPT>
+__device__ __forceinline__ void gauss_xy(const float *pl, float *xb, const GaussTaps &t, int tid,
+                                         int wy, int tx, float Q[OPT][3]) {
+    for (int k = tid; k < RY * FX; k += NT) {
+        const int ry = k >> 5, ox = k & 31;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float *src = pl + c * RY * RX + ry * RX + ox;
+            float s = 0.0f;
+#pragma unroll
+            for (int j = 0; j <= 2 * RG; ++j) s = fmaf(t.w[j], src[j], s);
+            xb[c * RY * FX + k] = s;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int o = 0; o < OPT; ++o) {
+        const int ty = wy + NW * o;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float s = 0.0f;
+#pragma unroll
+            for (int j = 0; j <= 2 * RG; ++j)
+                s = fmaf(t.w[j], xb[c * RY * FX + (ty + j) * FX + tx], s);
+            Q[o][c] = s;
+        }
+    }
+}
+
+// z pass from the ring: oldest slot holds plane z - RG.
+template <int RG, int NOUT>
+__device__ __forceinline__ float gauss_z(const float *ring, const GaussTaps &t, int oldest, int c,
+                                         int idx) {
+    constexpr int NS = 2 * RG + 1;
+    float s = 0.0f;
+    int sl = oldest;
+#pragma unroll
+    for (int j = 0; j <= 2 * RG; ++j) {
+        s = fmaf(t.w[j], ring[(sl * 3 + c) * NOUT + idx], s);
+        sl = (sl + 1 == NS) ? 0 : sl + 1;
+    }
+    return s;
+}
+
+// ====================================================================== K3
+template <int RG, int NW, int OPT>
+struct K3S {
+    static constexpr int NT = FX * NW, TY = NW * OPT, RX = FX + 2 * RG, RY = TY + 2 * RG;
+    static constexpr int NR = RX * RY, NS = 2 * RG + 1, NOUT = NT * OPT;
+    static constexpr size_t o_ring = 0;
+    static constexpr size_t o_xb = o_ring + (size_t)NS * 3 * NOUT * 4;
+    static constexpr size_t o_st = o_xb + (size_t)3 * RY * FX * 4;
+    static constexpr size_t o_mv = o_st + (size_t)NST * 3 * NR * 4;
+    static constexpr size_t bytes = o_mv + (size_t)NST * 6 * NOUT * 4;
+};
+
+template <int RG, int NW, int OPT>
+__global__ void __launch_bounds__(FX *NW) k_smooth_adam(const float *__restrict__ g,
+                                                        float *__restrict__ m,
+                                                        float *__restrict__ v,
+                                                        float *__restrict__ dir,
+                                                        WsHeader *__restrict__ h, int D, int H,
+                                                        int W, int TZ, GaussTaps t, AdamConsts ac,
+                                                        int parity) {
+    using S = K3S<RG, NW, OPT>;
+    constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, NR = S::NR, NS = S::NS,
+                  NOUT = S::NOUT;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *ring = (float *)(smem + S::o_ring);
+    float *xb = (float *)(smem + S::o_xb);
+    float *st = (float *)(smem + S::o_st);
+    float *mvs = (float *)(smem + S::o_mv);
+    __shared__ float redf[32];
+
+    const int tx = threadIdx.x, wy = threadIdx.y, tid = wy * FX + tx;
+    const int x0 = blockIdx.x * FX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+    const int zend = min(z0 + TZ, D);
+    const long long N = (long long)D * H * W, HW = (long long)H * W;
+    for (int k = tid; k < NS * 3 * NOUT; k += NT) ring[k] = 0.0f;
+
+    const int zs = z0 - RG, np = zend - z0 + 2 * RG;
+    auto issue = [&](int i) {
+        if (i < np) {
+            const int zp = zs + i, zo = zp - RG;
+            load_tile<3, RY, RX, NT>(st + (i % NST) * 3 * NR, g, N, D, H, W, zp, y0 - RG, x0 - RG,
+                                     tid);
+            if (zo >= z0 && zo < zend) {
+                float *o = mvs + (i % NST) * 6 * NOUT;
+                load_outputs<3, NT, OPT, NW>(o, m, N, D, H, W, zo, y0, x0, wy, tx, tid);
+                load_outputs<3, NT, OPT, NW>(o + 3 * NOUT, v, N, D, H, W, zo, y0, x0, wy, tx, tid);
+            }
+        }
+        cp_commit();
+    };
+    issue(0);
+    issue(1);
+
+    float mx = 0.0f;
+    bool bad = false;
+    int slot = 0;
+    for (int i = 0; i < np; ++i) {
+        const int zp = zs + i, zo = zp - RG;
+        issue(i + 2);
+        cp_wait<2>();
+        float Q[OPT][3];
+        if (zp >= 0 && zp < D) {
+            __syncthreads();  // the x pass reads neighbours' copies
+            gauss_xy<RG, RY, RX, NT, NW, OPT>(st + (i % NST) * 3 * NR, xb, t, tid, wy, tx, Q);
+        } else {
+#pragma unroll
+            for (int o = 0; o < OPT; ++o) Q[o][0] = Q[o][1] = Q[o][2] = 0.0f;
+        }
+#pragma unroll
+        for (int o = 0; o < OPT; ++o)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ring[(slot * 3 + c) * NOUT + o * NT + tid] = Q[o][c];
+        const int oldest = (slot + 1 == NS) ? 0 : slot + 1;
+        slot = oldest;
+        if (zo >= z0 && zo < zend) {
+            const float *mv = mvs + (i % NST) * 6 * NOUT;
+#pragma unroll
+            for (int o = 0; o < OPT; ++o) {
+                const int y = y0 + wy + NW * o, x = x0 + tx;
+                if (y >= H || x >= W) continue;
+                const int idx = o * NT + tid;
+                const long long gi = (long long)zo * HW + (long long)y * W + x;
+                float nrm2 = 0.0f;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float s = gauss_z<RG, NOUT>(ring, t, oldest, c, idx);
+                    const float mvv = fmaf(ac.b1, mv[c * NOUT + idx], (1.0f - ac.b1) * s);
+                    const float vvv = fmaf(ac.b2, mv[(3 + c) * NOUT + idx], (1.0f - ac.b2) * s * s);
+                    m[c * N + gi] = mvv;
+                    v[c * N + gi] = vvv;
+                    const float dv = (mvv / ac.bc1) / (sqrtf(vvv / ac.bc2) + ac.eps);
+                    dir[c * N + gi] = dv;
+                    nrm2 = fmaf(dv, dv, nrm2);
+                }
+                if (nrm2 <= 3.4e38f)
+                    mx = fmaxf(mx, sqrtf(nrm2));
+                else
+                    bad = true;
+            }
+        }
+    }
+    cp_wait<0>();
+    if (bad) status_set(&h->status, ST_NONFINITE);
+    block_max_to(&h->step_max_bits[parity], mx, redf);
+}
+
+// ====================================================================== K4
+// SU: u is staged in shared memory (planes z-1..z+1, halo RG + 1); valid when
+// the step is shorter than one voxel (lr / c_lp < 1).
+template <int RG, int NW, int OPT, bool SU>
+struct K4S {
+    static constexpr int NT = FX * NW, TY = NW * OPT, RX = FX + 2 * RG, RY = TY + 2 * RG;
+    static constexpr int NR = RX * RY, NS = 2 * RG + 1, NOUT = NT * OPT;
+    static constexpr int URX = RX + 2, URY = RY + 2, NRU = URX * URY, NSU = 5;
+    static constexpr size_t o_ring = 0;
+    static constexpr size_t o_xb = o_ring + (size_t)NS * 3 * NOUT * 4;
+    static constexpr size_t o_up = o_xb + (size_t)3 * RY * FX * 4;
+    static constexpr size_t o_dst = o_up + (size_t)3 * NR * 4;
+    static constexpr size_t o_ust = o_dst + (size_t)NST * 3 * NR * 4;
+    static constexpr size_t bytes = o_ust + (SU ? (size_t)NSU * 3 * NRU * 4 : 0);
+};
+
+template <int RG, int NW, int OPT, bool SU>
+__global__ void __launch_bounds__(FX *NW) k_compose(const float *__restrict__ u,
+                                                    const float *__restrict__ dir,
+                                                    float *__restrict__ uo,
+                                                    const float *__restrict__ Im,
+                                                    float *__restrict__ Jout,
+                                                    WsHeader *__restrict__ h, int D, int H, int W,
+                                                    int TZ, GaussTaps t, float lr, float c_lp,
+                                                    int parity) {
+    using S = K4S<RG, NW, OPT, SU>;
+    constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, NR = S::NR, NS = S::NS,
+                  NOUT = S::NOUT, URX = S::URX, URY = S::URY, NRU = S::NRU, NSU = S::NSU;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *ring = (float *)(smem + S::o_ring);
+    float *xb = (float *)(smem + S::o_xb);
+    float *up = (float *)(smem + S::o_up);
+    float *dst = (float *)(smem + S::o_dst);
+    float *ust = (float *)(smem + S::o_ust);
+
+    const int tx = threadIdx.x, wy = threadIdx.y, tid = wy * FX + tx;
+    const int x0 = blockIdx.x * FX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+    const int zend = min(z0 + TZ, D);
+    const long long N = (long long)D * H * W, HW = (long long)H * W;
+    const float mxd = __uint_as_float(h->step_max_bits[parity]);
+    const float e = (mxd > 0.0f) ? lr / (c_lp * mxd) : 0.0f;
+    for (int k = tid; k < NS * 3 * NOUT; k += NT) ring[k] = 0.0f;
+
+    const int zs = z0 - RG, np = zend - z0 + 2 * RG;
+    // u plane q lives in stage (q - (zs - 1)) % NSU
+    auto issue_u = [&](int q) {
+        load_tile<3, URY, URX, NT>(ust + ((q - (zs - 1)) % NSU) * 3 * NRU, u, N, D, H, W, q,
+                                   y0 - RG - 1, x0 - RG - 1, tid);
+    };
+    auto issue = [&](int i) {
+        if (i < np) {
+            load_tile<3, RY, RX, NT>(dst + (i % NST) * 3 * NR, dir, N, D, H, W, zs + i, y0 - RG,
+                                     x0 - RG, tid);
+            if (SU) issue_u(zs + i + 1);
+        }
+        cp_commit();
+    };
+    if (SU) {
+        issue_u(zs - 1);
+        issue_u(zs);
+    }
+    issue(0);  // the u planes above join group 0
+    issue(1);
+
+    TriPending jp[OPT];
+    long long jidx[OPT];
+    bool jlive[OPT];
+#pragma unroll
+    for (int o = 0; o < OPT; ++o) jlive[o] = false;
+
+    int slot = 0;
+    for (int i = 0; i < np; ++i) {
+        const int zp = zs + i, zo = zp - RG;
+        issue(i + 2);
+        cp_wait<2>();
+        float Q[OPT][3];
+        if (zp >= 0 && zp < D) {
+            if (SU) __syncthreads();  // u stages hold neighbours' copies
+            const float *ds = dst + (i % NST) * 3 * NR;
+            const float *um = ust + ((zp - 1 - (zs - 1)) % NSU) * 3 * NRU;
+            const float *u0 = ust + ((zp - (zs - 1)) % NSU) * 3 * NRU;
+            const float *u1 = ust + ((zp + 1 - (zs - 1)) % NSU) * 3 * NRU;
+            for (int k = tid; k < NR; k += NT) {
+                const int ry = k / RX, rx = k - ry * RX;
+                const int y = y0 - RG + ry, x = x0 - RG + rx;
+                float a = 0.f, b = 0.f, c = 0.f;
+                if (y >= 0 && y < H && x >= 0 && x < W) {
+                    const float dz = -e * ds[k], dy = -e * ds[NR + k], dx = -e * ds[2 * NR + k];
+                    if (SU) {
+                        // cell corners lie within one voxel: planes zp-1..zp+1
+                        if (dz > -1.0f && dz < 1.0f && dy > -1.0f && dy < 1.0f && dx > -1.0f &&
+                            dx < 1.0f) {
+                            const float fz = floorf(dz), fy = floorf(dy), fx = floorf(dx);
+                            const float tz = dz - fz, ty = dy - fy, tx2 = dx - fx;
+                            const float *pa = fz < 0.0f ? um : u0;
+                            const float *pb = fz < 0.0f ? u0 : u1;
+                            const int b0 = (ry + 1 + (int)fy) * URX + (rx + 1 + (int)fx);
+                            float r[3];
+#pragma unroll
+                            for (int ch = 0; ch < 3; ++ch) {
+                                const float *A = pa + ch * NRU, *B = pb + ch * NRU;
+                                const float c00 = fmaf(tx2, A[b0 + 1] - A[b0], A[b0]);
+                                const float c01 = fmaf(tx2, A[b0 + URX + 1] - A[b0 + URX], A[b0 + URX]);
+                                const float c10 = fmaf(tx2, B[b0 + 1] - B[b0], B[b0]);
+                                const float c11 = fmaf(tx2, B[b0 + URX + 1] - B[b0 + URX], B[b0 + URX]);
+                                const float c0 = fmaf(ty, c01 - c00, c00);
+                                const float c1 = fmaf(ty, c11 - c10, c10);
+                                r[ch] = fmaf(tz, c1 - c0, c0);
+                            }
+                            a = dz + r[0];
+                            b = dy + r[1];
+                            c = dx + r[2];
+                        } else {
+                            a = b = c = __int_as_float(0x7fc00000);  // impossible step: flag it
+                        }
+                    } else {
+                        float gz, gy, gx;
+                        a = dz + tri_sample<false>(u, D, H, W, zp, y, x, dz, dy, dx, gz, gy, gx);
+                        b = dy + tri_sample<false>(u + N, D, H, W, zp, y, x, dz, dy, dx, gz, gy, gx);
+                        c = dx + tri_sample<false>(u + 2 * N, D, H, W, zp, y, x, dz, dy, dx, gz, gy,
+                                                   gx);
+                    }
+                }
+                up[k] = a;
+                up[NR + k] = b;
+                up[2 * NR + k] = c;
+            }
+            __syncthreads();
+            gauss_xy<RG, RY, RX, NT, NW, OPT>(up, xb, t, tid, wy, tx, Q);
+        } else {
+#pragma unroll
+            for (int o = 0; o < OPT; ++o) Q[o][0] = Q[o][1] = Q[o][2] = 0.0f;
+        }
+#pragma unroll
+        for (int o = 0; o < OPT; ++o)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ring[(slot * 3 + c) * NOUT + o * NT + tid] = Q[o][c];
+        const int oldest = (slot + 1 == NS) ? 0 : slot + 1;
+        slot = oldest;
+        if (zo >= z0 && zo < zend) {
+#pragma unroll
+            for (int o = 0; o < OPT; ++o) {
+                // finish the previous plane's warped value first (its loads have landed)
+                if (jlive[o]) {
+                    float gz, gy, gx;
+                    Jout[jidx[o]] = tri_finish<false>(jp[o], gz, gy, gx);
+                    jlive[o] = false;
+                }
+                const int y = y0 + wy + NW * o, x = x0 + tx;
+                if (y >= H || x >= W) continue;
+                const int idx = o * NT + tid;
+                const long long gi = (long long)zo * HW + (long long)y * W + x;
+                const float a = gauss_z<RG, NOUT>(ring, t, oldest, 0, idx);
+                const float b = gauss_z<RG, NOUT>(ring, t, oldest, 1, idx);
+                const float c = gauss_z<RG, NOUT>(ring, t, oldest, 2, idx);
+                uo[gi] = a;
+                uo[N + gi] = b;
+                uo[2 * N + gi] = c;
+                tri_issue(jp[o], Im, D, H, W, zo, y, x, a, b, c);  // J of the new map
+                jidx[o] = gi;
+                jlive[o] = true;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < OPT; ++o)
+        if (jlive[o]) {
+            float gz, gy, gx;
+            Jout[jidx[o]] = tri_finish<false>(jp[o], gz, gy, gx);
+        }
+    cp_wait<0>();
+    // per-iteration header fields for the next iteration (nobody else reads them now)
+    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && tid == 0) {
+        for (int c = 0; c < 8; ++c) h->coef_max_bits[c] = 0u;
+        h->step_max_bits[parity ^ 1] = 0u;
+        h->loss_acc = 0ull;
+        h->eps_t = e;
+    }
+}
+
+// ================================================================ launching
+
+std::mutex g_mu;
+int g_num_sms = 0;
+
+int num_sms() {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (g_num_sms == 0) {
+        int dev = 0, n = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
+            g_num_sms = n;
+        else
+            g_num_sms = 152;
+    }
+    return g_num_sms;
+}
+
+// Slab depth TZ minimising (waves x planes per CTA) for a z-marching kernel.
+int choose_tz(int D, int tiles_xy, int halo, int ctas_per_sm) {
+    const long long slots = (long long)num_sms() * (ctas_per_sm > 0 ? ctas_per_sm : 1);
+    int best = D;
+    long long bestcost = -1;
+    for (int tz = 1; tz <= D && tz <= 64; ++tz) {
+        const long long ctas = (long long)tiles_xy * ((D + tz - 1) / tz);
+        const long long waves = (ctas + slots - 1) / slots;
+        const long long cost = waves * (tz + 2 * halo);
+        if (bestcost < 0 || cost < bestcost) {
+            bestcost = cost;
+            best = tz;
+        }
+    }
+    return best;
+}
+
+// Per-kernel launch preparation: opt into the dynamic shared memory once and
+// query the resident CTAs per SM.
+template <class K>
+int prepare(K kernel, size_t smem, int threads) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess ||
+        n < 1)
+        n = 1;
+    return n;
+}
+
+struct LaunchGeom {
+    dim3 grid, block;
+    int tz;
+};
+
+// occ: resident CTAs per SM of the kernel (queried once per instantiation).
+inline LaunchGeom geometry(int occ, int nw, int ty, int halo, Dims d) {
+    LaunchGeom g;
+    const int gx = (d.W + FX - 1) / FX, gy = (d.H + ty - 1) / ty;
+    g.tz = choose_tz(d.D, gx * gy, halo, occ);
+    g.grid = dim3(gx, gy, (d.D + g.tz - 1) / g.tz);
+    g.block = dim3(FX, nw);
+    return g;
+}
+
+// tile shapes (warps per CTA, outputs per thread along y)
+constexpr int K1_NW = 8, K1_OPT = 1;
+constexpr int K2_NW = 8, K2_OPT = 1;
+constexpr int K3_NW = 8, K3_OPT = 1;
+constexpr int K4_NW = 8, K4_OPT = 1;
+
+template <int R>
+cudaError_t launch_k1(const float *If, const float *J, float *coef, WsHeader *h, Dims d,
+                      int window, float cc_eps, bool wc, cudaStream_t s) {
+    using S = K1S<R, K1_NW, K1_OPT>;
+    auto kern = k_lncc_fwd<R, K1_NW, K1_OPT>;
+    static const int occ = prepare(kern, S::bytes, S::NT);
+    LaunchGeom g = geometry(occ, K1_NW, S::TY, R, d);
+    kern<<<g.grid, g.block, S::bytes, s>>>(If, J, coef, h, d.D, d.H, d.W, g.tz,
+                                           lncc_image_bits(window), cc_eps, window, wc ? 1 : 0);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <int R>
+cudaError_t launch_k2(const float *If, const float *Im, const float *u, const float *coef,
+                      const WsHeader *h, float *g, Dims d, int window, cudaStream_t s) {
+    using S = K2S<R, K2_NW, K2_OPT>;
+    auto kern = k_lncc_grad<R, K2_NW, K2_OPT>;
+    static const int occ = prepare(kern, S::bytes, S::NT);
+    LaunchGeom gg = geometry(occ, K2_NW, S::TY, R, d);
+    kern<<<gg.grid, gg.block, S::bytes, s>>>(If, Im, u, coef, h, g, d.D, d.H, d.W, gg.tz,
+                                             lncc_coef_bits(window));
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <int RG>
+cudaError_t launch_k3(const float *g, float *m, float *v, float *dir, WsHeader *h, Dims d,
+                      const GaussTaps &t, AdamConsts ac, int parity, cudaStream_t s) {
+    using S = K3S<RG, K3_NW, K3_OPT>;
+    auto kern = k_smooth_adam<RG, K3_NW, K3_OPT>;
+    static const int occ = prepare(kern, S::bytes, S::NT);
+    LaunchGeom gg = geometry(occ, K3_NW, S::TY, RG, d);
+    kern<<<gg.grid, gg.block, S::bytes, s>>>(g, m, v, dir, h, d.D, d.H, d.W, gg.tz, t, ac, parity);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <int RG, bool SU>
+cudaError_t launch_k4(const float *u, const float *dir, float *uo, const float *Im, float *J,
+                      WsHeader *h, Dims d, const GaussTaps &t, float lr, float c_lp, int parity,
+                      cudaStream_t s) {
+    using S = K4S<RG, K4_NW, K4_OPT, SU>;
+    auto kern = k_compose<RG, K4_NW, K4_OPT, SU>;
+    static const int occ = prepare(kern, S::bytes, S::NT);
+    LaunchGeom gg = geometry(occ, K4_NW, S::TY, RG, d);
+    kern<<<gg.grid, gg.block, S::bytes, s>>>(u, dir, uo, Im, J, h, d.D, d.H, d.W, gg.tz, t, lr,
+                                             c_lp, parity);
+    note_launch();
+    return cudaGetLastError();
+}
+
+#define FA_CASE(n, call) \
+    case n: {            \
+        constexpr int RR = n; \
+        return call;     \
+    }
+
+cudaError_t dispatch_k1(const float *If, const float *J, float *coef, WsHeader *h, Dims d,
+                        int window, float cc_eps, bool wc, cudaStream_t s) {
+    switch (window / 2) {
+        FA_CASE(0, (launch_k1<RR>(If, J, coef, h, d, window, cc_eps, wc, s)))
+        FA_CASE(1, (launch_k1<RR>(If, J, coef, h, d, window, cc_eps, wc, s)))
+        FA_CASE(2, (launch_k1<RR>(If, J, coef, h, d, window, cc_eps, wc, s)))
+        FA_CASE(3, (launch_k1<RR>(If, J, coef, h, d, window, cc_eps, wc, s)))
+        FA_CASE(4, (launch_k1<RR>(If, J, coef, h, d, window, cc_eps, wc, s)))
+        FA_CASE(5, (launch_k1<RR>(If, J, coef, h, d, window, cc_eps, wc, s)))
+        FA_CASE(6, (launch_k1<RR>(If, J, coef, h, d, window, cc_eps, wc, s)))
+        FA_CASE(7, (launch_k1<RR>(If, J, coef, h, d, window, cc_eps, wc, s)))
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t dispatch_k2(const float *If, const float *Im, const float *u, const float *coef,
+                        const WsHeader *h, float *g, Dims d, int window, cudaStream_t s) {
+    switch (window / 2) {
+        FA_CASE(0, (launch_k2<RR>(If, Im, u, coef, h, g, d, window, s)))
+        FA_CASE(1, (launch_k2<RR>(If, Im, u, coef, h, g, d, window, s)))
+        FA_CASE(2, (launch_k2<RR>(If, Im, u, coef, h, g, d, window, s)))
+        FA_CASE(3, (launch_k2<RR>(If, Im, u, coef, h, g, d, window, s)))
+        FA_CASE(4, (launch_k2<RR>(If, Im, u, coef, h, g, d, window, s)))
+        FA_CASE(5, (launch_k2<RR>(If, Im, u, coef, h, g, d, window, s)))
+        FA_CASE(6, (launch_k2<RR>(If, Im, u, coef, h, g, d, window, s)))
+        FA_CASE(7, (launch_k2<RR>(If, Im, u, coef, h, g, d, window, s)))
+    }
+    return cudaErrorInvalidValue;
+}
+
+constexpr int kMaxFusedRG = 6;
+
+cudaError_t dispatch_k3(const float *g, float *m, float *v, float *dir, WsHeader *h, Dims d,
+                        const GaussTaps &t, AdamConsts ac, int parity, cudaStream_t s) {
+    switch (t.R) {
+        FA_CASE(0, (launch_k3<RR>(g, m, v, dir, h, d, t, ac, parity, s)))
+        FA_CASE(1, (launch_k3<RR>(g, m, v, dir, h, d, t, ac, parity, s)))
+        FA_CASE(2, (launch_k3<RR>(g, m, v, dir, h, d, t, ac, parity, s)))
+        FA_CASE(3, (launch_k3<RR>(g, m, v, dir, h, d, t, ac, parity, s)))
+        FA_CASE(4, (launch_k3<RR>(g, m, v, dir, h, d, t, ac, parity, s)))
+        FA_CASE(5, (launch_k3<RR>(g, m, v, dir, h, d, t, ac, parity, s)))
+        FA_CASE(6, (launch_k3<RR>(g, m, v, dir, h, d, t, ac, parity, s)))
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t dispatch_k4(const float *u, const float *dir, float *uo, const float *Im, float *J,
+                        WsHeader *h, Dims d, const GaussTaps &t, float lr, float c_lp, int parity,
+                        bool su, cudaStream_t s) {
+    if (su) {
+        switch (t.R) {
+            FA_CASE(0, (launch_k4<RR, true>(u, dir, uo, Im, J, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(1, (launch_k4<RR, true>(u, dir, uo, Im, J, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(2, (launch_k4<RR, true>(u, dir, uo, Im, J, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(3, (launch_k4<RR, true>(u, dir, uo, Im, J, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(4, (launch_k4<RR, true>(u, dir, uo, Im, J, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(5, (launch_k4<RR, true>(u, dir, uo, Im, J, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(6, (launch_k4<RR, true>(u, dir, uo, Im, J, h, d, t, lr, c_lp, parity, s)))
+        }
+    } else {
+        switch (t.R) {
+            FA_CASE(0, (launch_k4<RR, false>(u, dir, uo, Im, J, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(1, (launch_k4<RR, false>(u, dir, uo, Im, J, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(2, (launch_k4<RR, false>(u, dir, uo, Im, J, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(3, (launch_k4<RR, false>(u, dir, uo, Im, J, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(4, (launch_k4<RR, false>(u, dir, uo, Im, J, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(5, (launch_k4<RR, false>(u, dir, uo, Im, J, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(6, (launch_k4<RR, false>(u, dir, uo, Im, J, h, d, t, lr, c_lp, parity, s)))
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+#undef FA_CASE
+
+struct KTimer {
+    fa_kernel_timer *t;
+    int level;
+    bool on(int id) const {
+        return t && t->kernel_id == id && (t->level < 0 || t->level == level) &&
+               t->count < t->capacity;
+    }
+};
+
+}  // namespace
 
 void fused_carve(WsCarver &c, long long n, FusedBuffers *fb) {
     fb->coef = c.take<float>(3 * n);
     fb->g = c.take<float>(3 * n);
     fb->dir = c.take<float>(3 * n);
     fb->J = c.take<float>(n);
+    fb->t1 = c.take<float>(3 * n);
+    fb->t2 = c.take<float>(3 * n);
 }
 
-fa_status fused_iteration(FusedBuffers &, WsHeader *, const fa_params *, Dims, const FusedIter &,
-                          const GaussTaps &, const GaussTaps &, fa_kernel_timer *, int,
-                          cudaStream_t) {
-    set_error("fused mode is not built yet");
-    return FA_ERR_UNSUPPORTED;
+cudaError_t fused_level_start(const float *Im, const float *u, Dims d, FusedBuffers &fb,
+                              cudaStream_t s) {
+    return launch_warp(Im, u, fb.J, nullptr, d, s);
 }
 
-cudaError_t fused_lncc_forward_only(const float *, const float *, Dims, int, float, WsHeader *,
-                                    FusedBuffers &, cudaStream_t) {
-    return cudaErrorNotSupported;
+fa_status fused_iteration(FusedBuffers &fb, WsHeader *h, const fa_params *p, Dims d,
+                          const FusedIter &it, const GaussTaps &tg, const GaussTaps &tw,
+                          fa_kernel_timer *timer, int level, cudaStream_t s) {
+    KTimer kt{timer, level};
+    auto start = [&](int id) -> cudaError_t {
+        return kt.on(id) ? cudaEventRecord((cudaEvent_t)timer->start_events[timer->count], s)
+                         : cudaSuccess;
+    };
+    auto stop = [&](int id) -> cudaError_t {
+        if (!kt.on(id)) return cudaSuccess;
+        cudaError_t e = cudaEventRecord((cudaEvent_t)timer->stop_events[timer->count], s);
+        timer->count++;
+        return e;
+    };
+    const int parity = it.t & 1;
+    if (p->loss == FA_LOSS_LNCC) {
+        FA_CUDA_TRY(start(FA_K_FUSED_WARP_LNCC));
+        FA_CUDA_TRY(dispatch_k1(it.If, fb.J, fb.coef, h, d, p->window, p->cc_eps, true, s));
+        FA_CUDA_TRY(stop(FA_K_FUSED_WARP_LNCC));
+        FA_CUDA_TRY(start(FA_K_FUSED_LNCC_GRAD));
+        FA_CUDA_TRY(dispatch_k2(it.If, it.Im, it.u, fb.coef, h, fb.g, d, p->window, s));
+        FA_CUDA_TRY(stop(FA_K_FUSED_LNCC_GRAD));
+    } else {
+        VoxGrid gg(d.D, d.H, d.W);
+        FA_CUDA_TRY(start(FA_K_FUSED_LNCC_GRAD));
+        k_fused_mse_grad<<<gg.grid, gg.block, 0, s>>>(it.If, it.Im, it.u, fb.g, d.D, d.H, d.W);
+        note_launch();
+        FA_CUDA_TRY(cudaGetLastError());
+        FA_CUDA_TRY(stop(FA_K_FUSED_LNCC_GRAD));
+    }
+    // Gaussians wider than the fused kernels' rings run as separable passes
+    // around the identity-width fused kernel.
+    static const GaussTaps ident = [] {
+        GaussTaps t;
+        make_gauss_taps(0.0f, &t);
+        return t;
+    }();
+    const bool wide_g = tg.R > kMaxFusedRG, wide_w = tw.R > kMaxFusedRG;
+    // the compose reads u from shared memory when every step is under a voxel
+    const bool su = (double)p->lr / (double)p->c_lp < 0.999;
+    if (wide_g) FA_CUDA_TRY(launch_gauss3(fb.g, fb.g, fb.t1, fb.t2, 3, d, tg, s));
+    FA_CUDA_TRY(start(FA_K_FUSED_SMOOTH_ADAM));
+    FA_CUDA_TRY(dispatch_k3(fb.g, it.m, it.v, fb.dir, h, d, wide_g ? ident : tg,
+                            adam_consts(p, it.t), parity, s));
+    FA_CUDA_TRY(stop(FA_K_FUSED_SMOOTH_ADAM));
+    FA_CUDA_TRY(start(FA_K_FUSED_COMPOSE));
+    FA_CUDA_TRY(dispatch_k4(it.u, fb.dir, it.u_alt, it.Im, fb.J, h, d, wide_w ? ident : tw, p->lr,
+                            p->c_lp, parity, su, s));
+    FA_CUDA_TRY(stop(FA_K_FUSED_COMPOSE));
+    if (wide_w) {
+        FA_CUDA_TRY(launch_gauss3(it.u_alt, it.u_alt, fb.t1, fb.t2, 3, d, tw, s));
+        FA_CUDA_TRY(launch_warp(it.Im, it.u_alt, fb.J, nullptr, d, s));  // J of the smoothed map
+    }
+    return FA_OK;
+}
+
+cudaError_t fused_lncc_forward_only(const float *If, const float *J, Dims d, int window,
+                                    float cc_eps, WsHeader *h, cudaStream_t s) {
+    return dispatch_k1(If, J, nullptr, h, d, window, cc_eps, false, s);
 }
 
 }  // namespace fa

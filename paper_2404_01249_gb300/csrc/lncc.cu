@@ -13,9 +13,9 @@
 //   dL/dJ(y) = -(1/N) sum_{x in win(y)} [A(x) I(y) + 2 B(x) J(y) + C(x)].
 //
 // Precision: images are quantised to b-bit fixed point (b from the window,
-// see fixed_bits_for_window) and all window sums are exact int64 sums; the
+// see lncc_image_bits) and all window sums are exact int64 sums; the
 // variance / covariance numerators n S_II - S_I^2 are formed exactly in
-// 128-bit integers before one rounding to float.  The adjoint window sums
+// 128-bit integers before rounding to float.  The adjoint window sums
 // quantise A, B, C to 2^-(47 - ceil(log2 n)) of their maxima and are exact
 // int64 sums too; the final I SA + 2 J SB + SC is combined in float-float.
 #include "ops.h"
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(256) k_lncc_coef(const long long *__restrict__
     long long N = (long long)D * H * W;
     long long i = ((long long)z * H + y) * W + x;
     const long long n = (long long)window * window * window;
-    const float nf = (float)n;
+    const float nf = (float)n, inv_nf = 1.0f / nf;
     float amax = fmaxf(__uint_as_float(h->absmax_bits[0]), __uint_as_float(h->absmax_bits[1]));
     int s = fixed_shift(amax, bits);
     float inv_s = pow2f(-s);
@@ -157,9 +157,9 @@ __global__ void __launch_bounds__(256) k_lncc_coef(const long long *__restrict__
     if (live) {
         long long sI = S[i], sJ = S[N + i], sII = S[2 * N + i], sJJ = S[3 * N + i],
                   sIJ = S[4 * N + i];
-        float varI = i128_diff_to_float(n, sII, sI, sI) * inv_s * inv_s / nf;
-        float varJ = i128_diff_to_float(n, sJJ, sJ, sJ) * inv_s * inv_s / nf;
-        float cross = i128_diff_to_float(n, sIJ, sI, sJ) * inv_s * inv_s / nf;
+        float varI = diff_i128_to_float(n, sII, sI, sI) * inv_s * inv_s * inv_nf;
+        float varJ = diff_i128_to_float(n, sJJ, sJ, sJ) * inv_s * inv_s * inv_nf;
+        float cross = diff_i128_to_float(n, sIJ, sI, sJ) * inv_s * inv_s * inv_nf;
         float SIf = __ll2float_rn(sI) * inv_s, SJf = __ll2float_rn(sJ) * inv_s;
         float den = fmaf(varI, varJ, cc_eps);
         float cc = cross * cross / den;
@@ -404,7 +404,7 @@ static void box_yz(long long *a, long long *b, Dims d, int R, cudaStream_t s) {
 cudaError_t launch_lncc_forward(const float *I, const float *J, Dims d, int window, float cc_eps,
                                 bool want_dI, WsHeader *h, LnccBuffers b, cudaStream_t s) {
     int R = window / 2;
-    int bits = fixed_bits_for_window(window);
+    int bits = lncc_image_bits(window);
     FA_DISPATCH_R(R, xpass_img<RR>(I, J, h, b.p0, d, bits, s));
     box_yz<5>(b.p0, b.p1, d, R, s);
     VoxGrid g(d.D, d.H, d.W);
@@ -423,7 +423,7 @@ cudaError_t launch_lncc_backward(const float *I, const float *J, const float *gr
                                  int window, WsHeader *h, LnccBuffers b, float *dJ, float *dI,
                                  float *g, cudaStream_t s) {
     int R = window / 2;
-    int cbits = 47 - log2_ceil_window(window);
+    int cbits = lncc_coef_bits(window);
     bool wantJ = dJ || g;
     int4 sel;
     int nc;

@@ -178,12 +178,13 @@ static fa_status final_loss(Plan &P, const fa_params *p, int l, const float *If,
                             const float *u, float *loss_dev, cudaStream_t s) {
     Dims d = P.lvl[l];
     FA_CUDA_TRY(iter_reset(P.h, s));
-    FA_CUDA_TRY(launch_warp(Im, u, P.J, nullptr, d, s));
+    if (p->mode == FA_MODE_PLAIN || p->loss != FA_LOSS_LNCC)
+        FA_CUDA_TRY(launch_warp(Im, u, P.J, nullptr, d, s));
     if (p->loss == FA_LOSS_LNCC) {
         if (p->mode == FA_MODE_PLAIN) {
             FA_CUDA_TRY(launch_lncc_forward(If, P.J, d, p->window, p->cc_eps, false, P.h, P.lb, s));
         } else {
-            FA_CUDA_TRY(fused_lncc_forward_only(If, P.J, d, p->window, p->cc_eps, P.h, P.fb, s));
+            FA_CUDA_TRY(fused_lncc_forward_only(If, P.fb.J, d, p->window, p->cc_eps, P.h, s));
         }
         FA_CUDA_TRY(launch_loss_finalize(P.h, d.N(), -1.0f, loss_dev, s));
     } else {
@@ -259,6 +260,7 @@ fa_status register_impl(const fa_vol *fixed, const fa_vol *moving, const fa_para
         FA_CUDA_TRY(cudaMemsetAsync(P.h->absmax_bits, 0, sizeof(P.h->absmax_bits), s));
         FA_CUDA_TRY(launch_absmax2(If, Im, d.N(), P.h, s));
         Timer tm{timer, l};
+        if (p->mode == FA_MODE_FUSED) FA_CUDA_TRY(fused_level_start(Im, P.u[cur], d, P.fb, s));
         for (int it = 0; it < p->iters[l]; ++it) {
             ++t;
             if (p->mode == FA_MODE_PLAIN) {

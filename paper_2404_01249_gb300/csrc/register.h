@@ -9,7 +9,8 @@ struct FusedBuffers {
     float *coef;   // [3][N]: A, B, C of the LNCC adjoint
     float *g;      // [3][N]: dL/dphi before smoothing
     float *dir;    // [3][N]: Adam direction d
-    float *J;      // [N]    : warped image (final loss only)
+    float *J;      // [N]    : warped image I_m o phi of the current map
+    float *t1, *t2;  // [3][N]: separable passes when a Gaussian is wider than the fused kernels take
 };
 void fused_carve(WsCarver &c, long long n, FusedBuffers *fb);
 
@@ -22,8 +23,13 @@ struct FusedIter {
 fa_status fused_iteration(FusedBuffers &fb, WsHeader *h, const fa_params *p, Dims d,
                           const FusedIter &it, const GaussTaps &tg, const GaussTaps &tw,
                           fa_kernel_timer *timer, int level, cudaStream_t s);
+// J = I_m o (id + u) for the first fused iteration of a level (later
+// iterations get J from the compose kernel).
+cudaError_t fused_level_start(const float *Im, const float *u, Dims d, FusedBuffers &fb,
+                              cudaStream_t s);
+// LNCC loss accumulator only (no coefficients) for the warped image J.
 cudaError_t fused_lncc_forward_only(const float *If, const float *J, Dims d, int window,
-                                    float cc_eps, WsHeader *h, FusedBuffers &fb, cudaStream_t s);
+                                    float cc_eps, WsHeader *h, cudaStream_t s);
 
 fa_status register_impl(const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
                         fa_vol *u_out, float *final_loss_dev, float *final_loss_host, void *ws,

@@ -27,7 +27,8 @@ STATUS_NAMES = {0: "FA_OK", 1: "FA_ERR_INVALID", 2: "FA_ERR_SHAPE", 3: "FA_ERR_D
 FA_F32, FA_BF16, FA_F16 = 0, 1, 2
 FA_LOSS_LNCC, FA_LOSS_MSE = 0, 1
 FA_MODE_FUSED, FA_MODE_PLAIN = 0, 1
-FA_K_FUSED_WARP_LNCC, FA_K_FUSED_GRAD_ADAM, FA_K_FUSED_COMPOSE, FA_K_PLAIN_ANY = 0, 1, 2, 3
+(FA_K_FUSED_WARP_LNCC, FA_K_FUSED_LNCC_GRAD, FA_K_FUSED_SMOOTH_ADAM, FA_K_FUSED_COMPOSE,
+ FA_K_PLAIN_ANY) = 0, 1, 2, 3, 4
 
 EXPORTED = ["fa_params_default", "fa_status_str", "fa_last_error", "fa_warp",
             "fa_lncc_workspace_size", "fa_lncc_fwd_bwd", "fa_mse_fwd_bwd",

@@ -40,7 +40,7 @@ def c1_oracle(orc):
     return f, m, r
 
 
-@pytest.mark.parametrize("mode", ["plain"])
+@pytest.mark.parametrize("mode", ["plain", "fused"])
 def test_c1_matches_oracle(fa, c1_oracle, mode):
     f, m, ref = c1_oracle
     out = fa.fa_register(cuda(f), cuda(m), fa.RegParams(mode=mode, **C1))
@@ -48,41 +48,79 @@ def test_c1_matches_oracle(fa, c1_oracle, mode):
     assert mean_disp_diff(out["u"], ref["u"]) < 0.05
 
 
-def test_zero_iterations_is_identity(fa, orc):
+@pytest.mark.parametrize("mode", ["plain", "fused"])
+def test_zero_iterations_is_identity(fa, orc, mode):
     f, m, _ = synth.blobs_pair(shape=(12, 14, 16), sigma=2.0)
-    out = fa.fa_register(cuda(f), cuda(m), fa.RegParams(scales=(2, 1), iters=(0, 0), mode="plain"))
+    out = fa.fa_register(cuda(f), cuda(m), fa.RegParams(scales=(2, 1), iters=(0, 0), mode=mode))
     assert float(out["u"].abs().max()) == 0.0
     ref = orc.lncc(f, m, 5, np.float32(1e-5), want_dJ=False)["loss"]
     assert abs(out["final_loss"] - ref) < 1e-5
 
 
-def test_mse_single_level(fa, orc):
+@pytest.mark.parametrize("mode", ["plain", "fused"])
+def test_mse_single_level(fa, orc, mode):
     f, m, _ = synth.blobs_pair(shape=(16, 16, 16), sigma=2.0, max_disp=1.0)
     out = fa.fa_register(cuda(f), cuda(m), fa.RegParams(scales=(1,), iters=(30,), loss="mse",
-                                                         mode="plain"))
+                                                         mode=mode))
     ref = orc.register(f, m, [1], [30], loss="mse", cc_eps=0.0, beta1=float(np.float32(0.9)),
                        beta2=float(np.float32(0.999)), adam_eps=float(np.float32(1e-8)))
     assert abs(out["final_loss"] - ref["final_loss"]) < 1e-3 * max(1.0, abs(ref["final_loss"]))
     assert mean_disp_diff(out["u"], ref["u"]) < 0.05
 
 
-def test_nonfinite_input_is_reported(fa):
+@pytest.mark.parametrize("mode", ["plain", "fused"])
+def test_nonfinite_input_is_reported(fa, mode):
     f, m, _ = synth.blobs_pair(shape=(8, 8, 8), sigma=2.0)
     m[3, 3, 3] = np.nan
     with pytest.raises(fa.FAError) as e:
-        fa.fa_register(cuda(f), cuda(m), fa.RegParams(scales=(1,), iters=(3,), mode="plain"))
+        fa.fa_register(cuda(f), cuda(m), fa.RegParams(scales=(1,), iters=(3,), mode=mode))
     assert e.value.status == 5
 
 
-def test_tiny_and_degenerate_grids(fa, orc):
+@pytest.mark.parametrize("mode", ["plain", "fused"])
+def test_tiny_and_degenerate_grids(fa, orc, mode):
     for shape in [(1, 1, 1), (1, 4, 9), (3, 2, 5)]:
         r = np.random.default_rng(9)
         f = r.random(shape).astype(np.float32)
         m = r.random(shape).astype(np.float32)
-        p = fa.RegParams(scales=(2, 1), iters=(3, 2), mode="plain")
+        p = fa.RegParams(scales=(2, 1), iters=(3, 2), mode=mode)
         out = fa.fa_register(cuda(f), cuda(m), p)
         ref = orc.register(f, m, [2, 1], [3, 2], cc_eps=float(np.float32(1e-5)),
                            beta1=float(np.float32(0.9)), beta2=float(np.float32(0.999)),
                            adam_eps=float(np.float32(1e-8)))
         assert abs(out["final_loss"] - ref["final_loss"]) < 1e-3
         assert mean_disp_diff(out["u"], ref["u"]) < 0.05
+
+
+@pytest.mark.parametrize("kw", [
+    dict(),                                         # the brain workload's hyper-parameters
+    dict(window=7, sigma_grad=2.0, sigma_warp=0.0),  # wider window, no warp smoothing
+    dict(window=3, sigma_grad=3.0, sigma_warp=2.5),  # Gaussians wider than the fused rings
+    dict(loss="mse", sigma_grad=0.5),
+])
+def test_fused_equals_plain(fa, kw):
+    """Both schedules compute the same arithmetic in the same order, so their
+    results agree to float32 rounding over a whole multi-level run on a
+    ragged brain-shaped grid."""
+    f, m, _ = synth.voronoi_pair(shape=(37, 45, 53), seed=31)
+    base = dict(scales=(2, 1), iters=(15, 8))
+    base.update(kw)
+    a = fa.fa_register(cuda(f), cuda(m), fa.RegParams(mode="plain", **base))
+    b = fa.fa_register(cuda(f), cuda(m), fa.RegParams(mode="fused", **base))
+    assert abs(a["final_loss"] - b["final_loss"]) < 1e-5
+    assert float((a["u"] - b["u"]).abs().max()) < 1e-4
+
+
+def test_fused_brain_level_against_oracle(fa, orc):
+    """One level of the brain workload at scale 4 (40x48x56, 200 iterations)
+    against the oracle: final LNCC within 1e-3 and mean displacement
+    difference below 0.05 voxel."""
+    f, m, _ = synth.voronoi_pair(shape=(160, 192, 224), seed=1000)
+    fl = orc.downsample(f, 4).astype(np.float32)
+    ml = orc.downsample(m, 4).astype(np.float32)
+    out = fa.fa_register(cuda(fl), cuda(ml), fa.RegParams(scales=(1,), iters=(200,), mode="fused"))
+    f32 = lambda x: float(np.float32(x))
+    ref = orc.register(fl, ml, [1], [200], cc_eps=f32(1e-5), beta1=f32(0.9), beta2=f32(0.999),
+                       adam_eps=f32(1e-8))
+    assert abs(out["final_loss"] - ref["final_loss"]) < 1e-3
+    assert mean_disp_diff(out["u"], ref["u"]) < 0.05
