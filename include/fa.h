@@ -140,7 +140,7 @@ fa_status fa_lncc_fwd_bwd(const fa_vol *fixed, const fa_vol *warped, int32_t win
  * plugin host that owns every device allocation, or a loop that must never
  * enter the allocator).  No workspace argument: scratch is a 64 MiB array
  * built into the library, held by every GPU that loads it until exit, so the
- * grid may hold at most 671,084 voxels (larger grids return FA_ERR_SHAPE
+ * grid may hold at most 621,376 voxels (larger grids return FA_ERR_SHAPE
  * before any launch).  The first call on each device looks up the array's
  * address with that device current; make it before any stream capture.
  * All calls share the array (each clears what must start at zero); calls

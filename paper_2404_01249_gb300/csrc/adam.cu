@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(256) k_adam(const float *__restrict__ g, float
             float vv = fmaf(c.b2, v[k], (1.0f - c.b2) * gv * gv);
             m[k] = mv;
             v[k] = vv;
-            float dv = (mv / c.bc1) / (sqrtf(vv / c.bc2) + c.eps);
+            float dv = (mv * c.rbc1) / (sqrtf(vv * c.rbc2) + c.eps);
             d[k] = dv;
             nrm2 = fmaf(dv, dv, nrm2);
         }
@@ -89,8 +89,8 @@ AdamConsts adam_consts(const fa_params *p, int t) {
     c.b1 = p->beta1;
     c.b2 = p->beta2;
     c.eps = p->adam_eps;
-    c.bc1 = (float)(1.0 - pow((double)p->beta1, (double)t));
-    c.bc2 = (float)(1.0 - pow((double)p->beta2, (double)t));
+    c.rbc1 = (float)(1.0 / (1.0 - pow((double)p->beta1, (double)t)));
+    c.rbc2 = (float)(1.0 / (1.0 - pow((double)p->beta2, (double)t)));
     return c;
 }
 

@@ -247,6 +247,53 @@ __device__ __forceinline__ float diff_i128_to_float(long long n, long long a, lo
     return fmaf(__ll2float_rn(hi), 18446744073709551616.0f, __ull2float_rn(lo));
 }
 
+// ---------------------------------------------------------- float-float
+__device__ __forceinline__ void ff_two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void ff_add(float &h, float &l, float bh, float bl) {
+    float s, e;
+    ff_two_sum(h, bh, s, e);
+    e += l + bl;
+    h = s + e;
+    l = e - (h - s);
+}
+
+// (hi, lo) of a * (xh + xl) for a float a and a float-float x.
+__device__ __forceinline__ void ff_mul_f(float a, float xh, float xl, float &h, float &l) {
+    h = a * xh;
+    l = fmaf(a, xh, -h);
+    l = fmaf(a, xl, l);
+}
+
+// Adjoint coefficient C = -(A S_I + 2 B S_J) / n of the LNCC gradient as a
+// float-float pair, from the exact window sums (scaled by 2^s, inv_s = 2^-s)
+// and the rounded float A, B.  Forming C from the same rounded A, B that are
+// summed keeps I(y) sum A + sum C free of their rounding; the pair keeps the
+// ~2^-44 relative accuracy the cancellation between those two sums needs.
+__device__ __forceinline__ void lncc_c_ff(float A, float B, long long sI, long long sJ,
+                                          float inv_s, float nf, float inv_nf, float &ch,
+                                          float &cl) {
+    float ih, il, jh, jl;
+    i64_to_ff(sI, ih, il);
+    i64_to_ff(sJ, jh, jl);
+    ih *= inv_s;
+    il *= inv_s;
+    jh *= inv_s;
+    jl *= inv_s;
+    const float i1 = ih * inv_nf, i2 = (fmaf(-i1, nf, ih) + il) * inv_nf;  // mean of I
+    const float j1 = jh * inv_nf, j2 = (fmaf(-j1, nf, jh) + jl) * inv_nf;  // mean of J
+    float ph, pl, th, tl;
+    ff_mul_f(A, i1, i2, ph, pl);
+    ff_mul_f(2.0f * B, j1, j2, th, tl);
+    ff_add(ph, pl, th, tl);
+    ch = -ph;
+    cl = -pl;
+}
+
 // 2^s as a float for s in [-126, 127] (clamped).
 __device__ __forceinline__ float pow2f(int s) {
     s = s < -126 ? -126 : (s > 127 ? 127 : s);

@@ -22,6 +22,12 @@
 // memory, and the last 2R + 1 in-plane results per output column sit in a
 // shared-memory ring from which the z-reduction reads.  No intermediate of
 // the separable sums goes to HBM; halo re-reads hit L2.
+//
+// Thread layout: warp w of NW covers region rows w, w + NW, ...; lane l
+// covers columns l and l + 32.  All trip counts are compile-time, the
+// in-plane offsets of a thread's positions are computed once per CTA, and a
+// thread consumes exactly the stage positions it copied itself wherever
+// possible, so those reads need no barrier.
 #include <math.h>
 
 #include <mutex>
@@ -34,12 +40,17 @@ namespace fa {
 namespace {
 
 constexpr int FX = 32;  // tile width along x (one warp)
-constexpr int NST = 3;  // cp.async pipeline stages
 
 __device__ __forceinline__ void cp4(void *dst, const float *src, bool ok) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src),
                  "r"(ok ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp8(void *dst, const void *src, bool ok) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src),
+                 "r"(ok ? 8 : 0)
                  : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
@@ -48,88 +59,112 @@ __device__ __forceinline__ void cp_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Issues the copies of C channel planes of a [C][D][H][W] field onto a
-// [C][RY][RX] shared tile whose (0, 0) is voxel (ybase, xbase) of plane zp;
-// outside the grid the tile reads zero.  Thread t copies positions
-// k = t, t + NT, ... (the consumers that read only their own positions need
-// no barrier after the wait).
-template <int C, int RY, int RX, int NT>
-__device__ __forceinline__ void load_tile(float *dst, const float *src, long long N, int D, int H,
-                                          int W, int zp, int ybase, int xbase, int tid) {
-    const bool zok = zp >= 0 && zp < D;
-    for (int k = tid; k < RY * RX; k += NT) {
-        const int ry = k / RX, rx = k - ry * RX;
-        const int y = ybase + ry, x = xbase + rx;
-        const bool ok = zok && y >= 0 && y < H && x >= 0 && x < W;
-        const long long i = ok ? ((long long)zp * H + y) * W + x : 0;
+// A thread's positions in an RY x RX region (RX <= 64).
+template <int RY, int RX, int NW>
+struct Region {
+    static constexpr int NJ = (RY + NW - 1) / NW;  // row slots
+    static constexpr int NC = (RX + 31) / 32;      // column slots
+    static constexpr int NP = NJ * NC;
+    int off[NP];  // y W + x inside the grid, -1 outside the grid, -2 outside the region
+    int sbase;    // shared index of slot (0, 0): wy RX + tx
+
+    __device__ __forceinline__ void init(int wy, int tx, int ybase, int xbase, int H, int W) {
+        sbase = wy * RX + tx;
 #pragma unroll
-        for (int c = 0; c < C; ++c) cp4(dst + c * RY * RX + k, src + c * N + i, ok);
+        for (int j = 0; j < NJ; ++j)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int ry = wy + NW * j, rx = tx + 32 * c;
+                const int y = ybase + ry, x = xbase + rx;
+                int o = -2;
+                if (ry < RY && rx < RX) o = (y >= 0 && y < H && x >= 0 && x < W) ? y * W + x : -1;
+                off[j * NC + c] = o;
+            }
     }
+    static __device__ __forceinline__ int sofs(int j, int c) { return NW * j * RX + 32 * c; }
+};
+
+// Copies C channels of plane zp onto [C][RY][RX] shared floats (zero outside).
+template <int C, int RY, int RX, int NW>
+__device__ __forceinline__ void load_plane(float *dst, const float *src, long long N,
+                                           long long zoff, bool zok,
+                                           const Region<RY, RX, NW> &rg) {
+    using G = Region<RY, RX, NW>;
+#pragma unroll
+    for (int j = 0; j < G::NJ; ++j)
+#pragma unroll
+        for (int c = 0; c < G::NC; ++c) {
+            const int o = rg.off[j * G::NC + c];
+            if (o == -2) continue;
+            const bool ok = zok && o >= 0;
+            const float *s = src + (ok ? zoff + o : 0);
+            float *d = dst + rg.sbase + G::sofs(j, c);
+#pragma unroll
+            for (int ch = 0; ch < C; ++ch) cp4(d + ch * RY * RX, s + ch * N, ok);
+        }
 }
 
-// Copies C channels at this thread's OPT output voxels of plane z.
-template <int C, int NT, int OPT, int NW>
-__device__ __forceinline__ void load_outputs(float *dst, const float *src, long long N, int D,
-                                             int H, int W, int z, int y0, int x0, int wy, int tx,
-                                             int tid) {
-    constexpr int NOUT = NT * OPT;
+// A thread's OPT output voxels of the 32 x TY tile.
+template <int OPT>
+struct Outs {
+    int off[OPT];  // y W + x, -1 outside the grid
+    __device__ __forceinline__ void init(int wy, int tx, int y0, int x0, int NW, int H, int W) {
+#pragma unroll
+        for (int o = 0; o < OPT; ++o) {
+            const int y = y0 + wy + NW * o, x = x0 + tx;
+            off[o] = (y < H && x < W) ? y * W + x : -1;
+        }
+    }
+};
+
+template <int C, int OPT, int NOUT>
+__device__ __forceinline__ void load_outs(float *dst, const float *src, long long N,
+                                          long long zoff, const Outs<OPT> &ou, int tid, int NT) {
 #pragma unroll
     for (int o = 0; o < OPT; ++o) {
-        const int y = y0 + wy + NW * o, x = x0 + tx;
-        const bool ok = z >= 0 && z < D && y < H && x < W;
-        const long long i = ok ? ((long long)z * H + y) * W + x : 0;
+        const bool ok = ou.off[o] >= 0;
+        const float *s = src + (ok ? zoff + ou.off[o] : 0);
 #pragma unroll
-        for (int c = 0; c < C; ++c) cp4(dst + c * NOUT + o * NT + tid, src + c * N + i, ok);
+        for (int ch = 0; ch < C; ++ch) cp4(dst + ch * NOUT + o * NT + tid, s + ch * N, ok);
     }
-}
-
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-    s = a + b;
-    float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-
-__device__ __forceinline__ void ff_add(float &h, float &l, float bh, float bl) {
-    float s, e;
-    two_sum(h, bh, s, e);
-    e += l + bl;
-    h = s + e;
-    l = e - (h - s);
-}
-
-__device__ __forceinline__ void ff_mul_f(float a, float xh, float xl, float &h, float &l) {
-    h = a * xh;
-    l = fmaf(a, xh, -h);
-    l = fmaf(a, xl, l);
 }
 
 // ====================================================================== K1
-template <int R, int NW, int OPT>
+// Box channels: J, J^2, I J (the fixed image's S_I and var_I come
+// precomputed per level).
+template <int R, int NW, int OPT, int NSTG>
 struct K1S {
     static constexpr int NT = FX * NW, TY = NW * OPT, RX = FX + 2 * R, RY = TY + 2 * R;
     static constexpr int NR = RX * RY, NS = 2 * R + 1, NOUT = NT * OPT;
-    static constexpr size_t o_ring = 0;                                     // [NS][5][NOUT] int64
-    static constexpr size_t o_xL = o_ring + (size_t)NS * 5 * NOUT * 8;      // [5][RY][FX] int64
-    static constexpr size_t o_q = o_xL + (size_t)5 * RY * FX * 8;           // [2][NR] int32
-    static constexpr size_t o_st = o_q + (size_t)2 * NR * 4;                // [NST][2][NR] f32
-    static constexpr size_t bytes = o_st + (size_t)NST * 2 * NR * 4;
+    static constexpr size_t o_ring = 0;                                   // [NS][3][NOUT] int64
+    static constexpr size_t o_xL = o_ring + (size_t)NS * 3 * NOUT * 8;    // [3][RY][FX] int64
+    static constexpr size_t o_os = o_xL + (size_t)3 * RY * FX * 8;        // [NSTG][NOUT] int64 S_I
+    static constexpr size_t o_q = o_os + (size_t)NSTG * NOUT * 8;         // [2][NR] int32
+    static constexpr size_t o_st = o_q + (size_t)2 * NR * 4;              // [NSTG][2][NR] f32
+    static constexpr size_t o_ov = o_st + (size_t)NSTG * 2 * NR * 4;      // [NSTG][NOUT] f32 var_I
+    static constexpr size_t bytes = o_ov + (size_t)NSTG * NOUT * 4;
 };
 
-template <int R, int NW, int OPT>
+template <int R, int NW, int OPT, int NSTG>
 __global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const float *__restrict__ If,
                                                      const float *__restrict__ J,
+                                                     const long long *__restrict__ SIg,
+                                                     const float *__restrict__ varIg,
                                                      float *__restrict__ coef,
                                                      WsHeader *__restrict__ h, int D, int H, int W,
                                                      int TZ, int bits, float cc_eps, int window,
                                                      int write_coef) {
-    using S = K1S<R, NW, OPT>;
+    using S = K1S<R, NW, OPT, NSTG>;
+    using G = Region<S::RY, S::RX, NW>;
     constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, NR = S::NR, NS = S::NS,
                   NOUT = S::NOUT;
     extern __shared__ __align__(16) unsigned char smem[];
     long long *ring = (long long *)(smem + S::o_ring);
     long long *xL = (long long *)(smem + S::o_xL);
+    long long *os = (long long *)(smem + S::o_os);
     int *qI = (int *)(smem + S::o_q), *qJ = qI + NR;
     float *st = (float *)(smem + S::o_st);
+    float *ov = (float *)(smem + S::o_ov);
     __shared__ float redf[32];
     __shared__ unsigned long long redu[32];
 
@@ -143,25 +178,41 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const float *__restrict__ I
     const float scale = pow2f(sh), inv_s = pow2f(-sh);
     const long long n = (long long)window * window * window;
     const float nf = (float)n, inv_nf = 1.0f / nf;
+    G rg;
+    rg.init(wy, tx, y0 - R, x0 - R, H, W);
+    Outs<OPT> ou;
+    ou.init(wy, tx, y0, x0, NW, H, W);
 
-    for (int k = tid; k < NS * 5 * NOUT; k += NT) ring[k] = 0;
-    long long acc[OPT][5];
+    for (int k = tid; k < NS * 3 * NOUT; k += NT) ring[k] = 0;
+    long long acc[OPT][3];
 #pragma unroll
     for (int o = 0; o < OPT; ++o)
 #pragma unroll
-        for (int c = 0; c < 5; ++c) acc[o][c] = 0;
+        for (int c = 0; c < 3; ++c) acc[o][c] = 0;
 
     const int zs = z0 - R, np = zend - z0 + 2 * R;
     auto issue = [&](int i) {
         if (i < np) {
-            float *dst = st + (i % NST) * 2 * NR;
-            load_tile<1, RY, RX, NT>(dst, If, N, D, H, W, zs + i, y0 - R, x0 - R, tid);
-            load_tile<1, RY, RX, NT>(dst + NR, J, N, D, H, W, zs + i, y0 - R, x0 - R, tid);
+            const int zp = zs + i, zo = zp - R;
+            const bool zok = zp >= 0 && zp < D;
+            float *dst = st + (i % NSTG) * 2 * NR;
+            load_plane<1, RY, RX, NW>(dst, If, N, (long long)zp * HW, zok, rg);
+            load_plane<1, RY, RX, NW>(dst + NR, J, N, (long long)zp * HW, zok, rg);
+            if (zo >= z0 && zo < zend) {
+                const long long zoff = (long long)zo * HW;
+#pragma unroll
+                for (int o = 0; o < OPT; ++o) {
+                    const bool ok = ou.off[o] >= 0;
+                    const long long gi = ok ? zoff + ou.off[o] : 0;
+                    cp8(os + (i % NSTG) * NOUT + o * NT + tid, SIg + gi, ok);
+                    cp4(ov + (i % NSTG) * NOUT + o * NT + tid, varIg + gi, ok);
+                }
+            }
         }
         cp_commit();
     };
-    issue(0);
-    issue(1);
+#pragma unroll
+    for (int k = 0; k < NSTG - 1; ++k) issue(k);
 
     unsigned long long qcc = 0;
     float mA = 0.f, mB = 0.f, mC = 0.f;
@@ -169,44 +220,49 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const float *__restrict__ I
     int slot = 0;
     for (int i = 0; i < np; ++i) {
         const int zp = zs + i;
-        issue(i + 2);
-        cp_wait<2>();
-        long long P[OPT][5];
+        issue(i + NSTG - 1);
+        cp_wait<NSTG - 1>();
+        long long P[OPT][3];
         if (zp >= 0 && zp < D) {
-            const float *sI = st + (i % NST) * 2 * NR, *sJ = sI + NR;
-            for (int k = tid; k < NR; k += NT) {  // own copies: no barrier needed
-                qI[k] = __float2int_rn(sI[k] * scale);
-                qJ[k] = __float2int_rn(sJ[k] * scale);
-            }
+            const float *sI = st + (i % NSTG) * 2 * NR, *sJ = sI + NR;
+#pragma unroll
+            for (int j = 0; j < G::NJ; ++j)
+#pragma unroll
+                for (int c = 0; c < G::NC; ++c) {  // own copies: no barrier needed
+                    if (rg.off[j * G::NC + c] == -2) continue;
+                    const int k = rg.sbase + G::sofs(j, c);
+                    qI[k] = __float2int_rn(sI[k] * scale);
+                    qJ[k] = __float2int_rn(sJ[k] * scale);
+                }
             __syncthreads();
-            for (int k = tid; k < RY * FX; k += NT) {
-                const int ry = k >> 5, ox = k & 31;
-                const int *a = qI + ry * RX + ox, *b = qJ + ry * RX + ox;
-                long long s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0;
+#pragma unroll
+            for (int j = 0; j < G::NJ; ++j) {
+                const int ry = wy + NW * j;
+                if (ry >= RY) continue;
+                const int *a = qI + ry * RX + tx, *b = qJ + ry * RX + tx;
+                int s2 = 0;
+                long long s4 = 0, s5 = 0;
 #pragma unroll
                 for (int t = 0; t <= 2 * R; ++t) {
                     const int va = a[t], vb = b[t];
-                    s1 += va;
                     s2 += vb;
-                    s3 += (long long)va * va;
                     s4 += (long long)vb * vb;
                     s5 += (long long)va * vb;
                 }
-                xL[k] = s1;
-                xL[RY * FX + k] = s2;
-                xL[2 * RY * FX + k] = s3;
-                xL[3 * RY * FX + k] = s4;
-                xL[4 * RY * FX + k] = s5;
+                long long *xo = xL + ry * FX + tx;
+                xo[0] = s2;
+                xo[RY * FX] = s4;
+                xo[2 * RY * FX] = s5;
             }
             __syncthreads();
 #pragma unroll
             for (int o = 0; o < OPT; ++o) {
-                const int ty = wy + NW * o;
+                const long long *xi = xL + (wy + NW * o) * FX + tx;
 #pragma unroll
-                for (int c = 0; c < 5; ++c) {
+                for (int c = 0; c < 3; ++c) {
                     long long sum = 0;
 #pragma unroll
-                    for (int t = 0; t <= 2 * R; ++t) sum += xL[c * RY * FX + (ty + t) * FX + tx];
+                    for (int t = 0; t <= 2 * R; ++t) sum += xi[c * RY * FX + t * FX];
                     P[o][c] = sum;
                 }
             }
@@ -214,47 +270,49 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const float *__restrict__ I
 #pragma unroll
             for (int o = 0; o < OPT; ++o)
 #pragma unroll
-                for (int c = 0; c < 5; ++c) P[o][c] = 0;
+                for (int c = 0; c < 3; ++c) P[o][c] = 0;
         }
+        long long *rb = ring + slot * 3 * NOUT + tid;
 #pragma unroll
-        for (int o = 0; o < OPT; ++o) {
-            const int idx = o * NT + tid;
+        for (int o = 0; o < OPT; ++o)
 #pragma unroll
-            for (int c = 0; c < 5; ++c) {
-                long long *r = ring + (slot * 5 + c) * NOUT + idx;
+            for (int c = 0; c < 3; ++c) {
+                long long *r = rb + c * NOUT + o * NT;
                 acc[o][c] += P[o][c] - *r;
                 *r = P[o][c];
             }
-        }
         slot = (slot + 1 == NS) ? 0 : slot + 1;
         const int z = zp - R;
         if (z >= z0 && z < zend) {
+            const long long zoff = (long long)z * HW;
 #pragma unroll
             for (int o = 0; o < OPT; ++o) {
-                const int y = y0 + wy + NW * o, x = x0 + tx;
-                if (y >= H || x >= W) continue;
-                const long long a1 = acc[o][0], a2 = acc[o][1];
-                const float varI = diff_i128_to_float(n, acc[o][2], a1, a1) * inv_s * inv_s * inv_nf;
-                const float varJ = diff_i128_to_float(n, acc[o][3], a2, a2) * inv_s * inv_s * inv_nf;
-                const float cross = diff_i128_to_float(n, acc[o][4], a1, a2) * inv_s * inv_s * inv_nf;
+                if (ou.off[o] < 0) continue;
+                const long long a1 = os[(i % NSTG) * NOUT + o * NT + tid];  // own copy
+                const float varI = ov[(i % NSTG) * NOUT + o * NT + tid];
+                const long long a2 = acc[o][0];
+                const float varJ = diff_i128_to_float(n, acc[o][1], a2, a2) * inv_s * inv_s * inv_nf;
+                const float cross = diff_i128_to_float(n, acc[o][2], a1, a2) * inv_s * inv_s * inv_nf;
                 const float den = fmaf(varI, varJ, cc_eps);
-                const float cc = cross * cross / den;
+                const float rden = 1.0f / den;
+                const float cc = cross * cross * rden;
                 if (cc >= 0.0f && cc <= 2.0f)
                     qcc += (unsigned long long)__float2ull_rn(cc * 4294967296.0f);
                 else
                     bad = true;
                 if (write_coef) {
-                    const float SIf = __ll2float_rn(a1) * inv_s, SJf = __ll2float_rn(a2) * inv_s;
-                    const float A = 2.0f * cross / den;
-                    const float B = -cc * varI / den;
-                    const float C = -(A * SIf + 2.0f * B * SJf) / nf;
-                    const long long gi = (long long)z * HW + (long long)y * W + x;
-                    coef[gi] = A;
-                    coef[N + gi] = B;
-                    coef[2 * N + gi] = C;
+                    const float A = 2.0f * cross * rden;
+                    const float B = -cc * varI * rden;
+                    float Ch, Cl;
+                    lncc_c_ff(A, B, a1, a2, inv_s, nf, inv_nf, Ch, Cl);
+                    float *cp = coef + zoff + ou.off[o];
+                    cp[0] = A;
+                    cp[N] = B;
+                    cp[2 * N] = Ch;
+                    cp[3 * N] = Cl;
                     mA = fmaxf(mA, fabsf(A));
                     mB = fmaxf(mB, fabsf(B));
-                    mC = fmaxf(mC, fabsf(C));
+                    mC = fmaxf(mC, fabsf(Ch));
                 }
             }
         }
@@ -270,7 +328,7 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const float *__restrict__ I
 }
 
 // ====================================================================== K2
-template <int R, int NW, int OPT>
+template <int R, int NW, int OPT, int NSTG>
 struct K2S {
     static constexpr int NT = FX * NW, TY = NW * OPT, RX = FX + 2 * R, RY = TY + 2 * R;
     static constexpr int NR = RX * RY, NS = 2 * R + 1, NOUT = NT * OPT;
@@ -278,11 +336,12 @@ struct K2S {
     static constexpr size_t o_xL = o_ring + (size_t)NS * 3 * NOUT * 8;
     static constexpr size_t o_q = o_xL + (size_t)3 * RY * FX * 8;
     static constexpr size_t o_st = o_q + (size_t)3 * NR * 8;
-    static constexpr size_t o_ost = o_st + (size_t)NST * 3 * NR * 4;
-    static constexpr size_t bytes = o_ost + (size_t)NST * 4 * NOUT * 4;
+    static constexpr size_t o_ost = o_st + (size_t)NSTG * 4 * NR * 4;
+    static constexpr size_t bytes = o_ost + (size_t)NSTG * 4 * NOUT * 4;
 };
 
-template <int R, int NW, int OPT>
+// coef holds A, B and C as a float-float pair (C hi, C lo).
+template <int R, int NW, int OPT, int NSTG>
 __global__ void __launch_bounds__(FX *NW) k_lncc_grad(const float *__restrict__ If,
                                                       const float *__restrict__ Im,
                                                       const float *__restrict__ u,
@@ -290,7 +349,8 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_grad(const float *__restrict__ 
                                                       const WsHeader *__restrict__ h,
                                                       float *__restrict__ g, int D, int H, int W,
                                                       int TZ, int cbits) {
-    using S = K2S<R, NW, OPT>;
+    using S = K2S<R, NW, OPT, NSTG>;
+    using G = Region<S::RY, S::RX, NW>;
     constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, NR = S::NR, NS = S::NS,
                   NOUT = S::NOUT;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -312,6 +372,10 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_grad(const float *__restrict__ 
         us[c] = pow2f(-e);
     }
     const float inv_n = 1.0f / (float)N;
+    G rg;
+    rg.init(wy, tx, y0 - R, x0 - R, H, W);
+    Outs<OPT> ou;
+    ou.init(wy, tx, y0, x0, NW, H, W);
 
     for (int k = tid; k < NS * 3 * NOUT; k += NT) ring[k] = 0;
     long long acc[OPT][3];
@@ -324,66 +388,73 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_grad(const float *__restrict__ 
     auto issue = [&](int i) {
         if (i < np) {
             const int zp = zs + i, zo = zp - R;
-            load_tile<3, RY, RX, NT>(st + (i % NST) * 3 * NR, coef, N, D, H, W, zp, y0 - R, x0 - R,
-                                     tid);
+            load_plane<4, RY, RX, NW>(st + (i % NSTG) * 4 * NR, coef, N, (long long)zp * HW,
+                                      zp >= 0 && zp < D, rg);
             if (zo >= z0 && zo < zend) {
-                float *o = ost + (i % NST) * 4 * NOUT;
-                load_outputs<3, NT, OPT, NW>(o, u, N, D, H, W, zo, y0, x0, wy, tx, tid);
-                load_outputs<1, NT, OPT, NW>(o + 3 * NOUT, If, N, D, H, W, zo, y0, x0, wy, tx, tid);
+                float *o = ost + (i % NSTG) * 4 * NOUT;
+                load_outs<3, OPT, NOUT>(o, u, N, (long long)zo * HW, ou, tid, NT);
+                load_outs<1, OPT, NOUT>(o + 3 * NOUT, If, N, (long long)zo * HW, ou, tid, NT);
             }
         }
         cp_commit();
     };
-    issue(0);
-    issue(1);
+#pragma unroll
+    for (int k = 0; k < NSTG - 1; ++k) issue(k);
 
     int slot = 0;
     for (int i = 0; i < np; ++i) {
         const int zp = zs + i, zo = zp - R;
-        issue(i + 2);
-        cp_wait<2>();
+        issue(i + NSTG - 1);
+        cp_wait<NSTG - 1>();
         const bool out = zo >= z0 && zo < zend;
-        // warp gathers for this plane's outputs, consumed after the reductions
+        // gathers for this plane's outputs, consumed after the reductions
         TriPending tp[OPT];
         float Iv[OPT];
         if (out) {
-            const float *o = ost + (i % NST) * 4 * NOUT;
+            const float *o = ost + (i % NSTG) * 4 * NOUT + tid;
 #pragma unroll
             for (int k = 0; k < OPT; ++k) {
-                const int idx = k * NT + tid, y = y0 + wy + NW * k, x = x0 + tx;
-                tri_issue(tp[k], Im, D, H, W, zo, y, x, o[idx], o[NOUT + idx], o[2 * NOUT + idx]);
-                Iv[k] = o[3 * NOUT + idx];
+                tri_issue(tp[k], Im, D, H, W, zo, y0 + wy + NW * k, x0 + tx, o[k * NT],
+                          o[NOUT + k * NT], o[2 * NOUT + k * NT]);
+                Iv[k] = o[3 * NOUT + k * NT];
             }
         }
         long long P[OPT][3];
         if (zp >= 0 && zp < D) {
-            const float *s = st + (i % NST) * 3 * NR;
-            for (int k = tid; k < NR; k += NT) {  // own copies
-                q[k] = quantize(s[k], qs[0]);
-                q[NR + k] = quantize(s[NR + k], qs[1]);
-                q[2 * NR + k] = quantize(s[2 * NR + k], qs[2]);
-            }
+            const float *s = st + (i % NSTG) * 4 * NR;
+#pragma unroll
+            for (int j = 0; j < G::NJ; ++j)
+#pragma unroll
+                for (int c = 0; c < G::NC; ++c) {  // own copies
+                    if (rg.off[j * G::NC + c] == -2) continue;
+                    const int k = rg.sbase + G::sofs(j, c);
+                    q[k] = quantize(s[k], qs[0]);
+                    q[NR + k] = quantize(s[NR + k], qs[1]);
+                    q[2 * NR + k] = quantize(s[2 * NR + k], qs[2]) + quantize(s[3 * NR + k], qs[2]);
+                }
             __syncthreads();
-            for (int k = tid; k < RY * FX; k += NT) {
-                const int ry = k >> 5, ox = k & 31;
+#pragma unroll
+            for (int j = 0; j < G::NJ; ++j) {
+                const int ry = wy + NW * j;
+                if (ry >= RY) continue;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const long long *src = q + c * NR + ry * RX + ox;
+                    const long long *src = q + c * NR + ry * RX + tx;
                     long long sum = 0;
 #pragma unroll
                     for (int t = 0; t <= 2 * R; ++t) sum += src[t];
-                    xL[c * RY * FX + k] = sum;
+                    xL[c * RY * FX + ry * FX + tx] = sum;
                 }
             }
             __syncthreads();
 #pragma unroll
             for (int o = 0; o < OPT; ++o) {
-                const int ty = wy + NW * o;
+                const long long *xi = xL + (wy + NW * o) * FX + tx;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     long long sum = 0;
 #pragma unroll
-                    for (int t = 0; t <= 2 * R; ++t) sum += xL[c * RY * FX + (ty + t) * FX + tx];
+                    for (int t = 0; t <= 2 * R; ++t) sum += xi[c * RY * FX + t * FX];
                     P[o][c] = sum;
                 }
             }
@@ -393,23 +464,21 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_grad(const float *__restrict__ 
 #pragma unroll
                 for (int c = 0; c < 3; ++c) P[o][c] = 0;
         }
+        long long *rb = ring + slot * 3 * NOUT + tid;
 #pragma unroll
-        for (int o = 0; o < OPT; ++o) {
-            const int idx = o * NT + tid;
+        for (int o = 0; o < OPT; ++o)
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                long long *r = ring + (slot * 3 + c) * NOUT + idx;
+                long long *r = rb + c * NOUT + o * NT;
                 acc[o][c] += P[o][c] - *r;
                 *r = P[o][c];
             }
-        }
         slot = (slot + 1 == NS) ? 0 : slot + 1;
         if (out) {
+            const long long zoff = (long long)zo * HW;
 #pragma unroll
             for (int o = 0; o < OPT; ++o) {
-                const int y = y0 + wy + NW * o, x = x0 + tx;
-                if (y >= H || x >= W) continue;
-                const long long gi = (long long)zo * HW + (long long)y * W + x;
+                if (ou.off[o] < 0) continue;
                 float gz, gy, gx;
                 const float Jv = tri_finish<true>(tp[o], gz, gy, gx);
                 float ah, al, bh, bl, ch, cl, rh, rl, th, tl;
@@ -421,9 +490,10 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_grad(const float *__restrict__ 
                 ff_add(rh, rl, th, tl);
                 ff_add(rh, rl, ch * us[2], cl * us[2]);                // + SC
                 const float dj = -(rh + rl) * inv_n;
-                g[gi] = dj * gz;
-                g[N + gi] = dj * gy;
-                g[2 * N + gi] = dj * gx;
+                float *gp = g + zoff + ou.off[o];
+                gp[0] = dj * gz;
+                gp[N] = dj * gy;
+                gp[2 * N] = dj * gx;
             }
         }
     }
@@ -452,64 +522,75 @@ __global__ void __launch_bounds__(256) k_fused_mse_grad(const float *__restrict_
 }
 
 // ====================================================== separable Gaussian
-// x pass of a [3][RY][RX] plane onto [3][RY][FX], then this thread's y pass.
-template <int RG, int RY, int RX, int NT, int NW, int OPT>
-__device__ __forceinline__ void gauss_xy(const float *pl, float *xb, const GaussTaps &t, int tid,
-                                         int wy, int tx, float Q[OPT][3]) {
-    for (int k = tid; k < RY * FX; k += NT) {
-        const int ry = k >> 5, ox = k & 31;
+// x pass of a [3][RY][RX] plane onto [3][RY][FX] and this thread's y pass.
+template <int RG, int RY, int RX, int NW, int OPT>
+__device__ __forceinline__ void gauss_xy(const float *pl, float *xb, const GaussTaps &t, int wy,
+                                         int tx, float Q[OPT][3]) {
+    constexpr int NJ = (RY + NW - 1) / NW;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const int ry = wy + NW * j;
+        if (ry >= RY) continue;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const float *src = pl + c * RY * RX + ry * RX + ox;
+            const float *src = pl + c * RY * RX + ry * RX + tx;
             float s = 0.0f;
 #pragma unroll
-            for (int j = 0; j <= 2 * RG; ++j) s = fmaf(t.w[j], src[j], s);
-            xb[c * RY * FX + k] = s;
+            for (int k = 0; k <= 2 * RG; ++k) s = fmaf(t.w[k], src[k], s);
+            xb[c * RY * FX + ry * FX + tx] = s;
         }
     }
     __syncthreads();
 #pragma unroll
     for (int o = 0; o < OPT; ++o) {
-        const int ty = wy + NW * o;
+        const float *xi = xb + (wy + NW * o) * FX + tx;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             float s = 0.0f;
 #pragma unroll
-            for (int j = 0; j <= 2 * RG; ++j)
-                s = fmaf(t.w[j], xb[c * RY * FX + (ty + j) * FX + tx], s);
+            for (int k = 0; k <= 2 * RG; ++k) s = fmaf(t.w[k], xi[c * RY * FX + k * FX], s);
             Q[o][c] = s;
         }
     }
 }
 
-// z pass from the ring: oldest slot holds plane z - RG.
-template <int RG, int NOUT>
-__device__ __forceinline__ float gauss_z(const float *ring, const GaussTaps &t, int oldest, int c,
-                                         int idx) {
-    constexpr int NS = 2 * RG + 1;
-    float s = 0.0f;
-    int sl = oldest;
+// Ring of the last NS in-plane results, every slot stored twice (k, k + NS)
+// so that the z window is contiguous.  Writes plane results at `slot` and
+// returns the first slot of the window (oldest plane first).
+template <int NS, int OPT, int NOUT, int NT>
+__device__ __forceinline__ int ring_push(float *ring, int slot, int tid, const float Q[OPT][3]) {
 #pragma unroll
-    for (int j = 0; j <= 2 * RG; ++j) {
-        s = fmaf(t.w[j], ring[(sl * 3 + c) * NOUT + idx], s);
-        sl = (sl + 1 == NS) ? 0 : sl + 1;
-    }
+    for (int o = 0; o < OPT; ++o)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float v = Q[o][c];
+            ring[(slot * 3 + c) * NOUT + o * NT + tid] = v;
+            ring[((slot + NS) * 3 + c) * NOUT + o * NT + tid] = v;
+        }
+    return slot + 1;  // window slots slot+1 .. slot+NS
+}
+
+template <int RG, int NOUT>
+__device__ __forceinline__ float gauss_z(const float *win, const GaussTaps &t, int c) {
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k <= 2 * RG; ++k) s = fmaf(t.w[k], win[(k * 3 + c) * NOUT], s);
     return s;
 }
 
 // ====================================================================== K3
-template <int RG, int NW, int OPT>
+template <int RG, int NW, int OPT, int NSTG>
 struct K3S {
     static constexpr int NT = FX * NW, TY = NW * OPT, RX = FX + 2 * RG, RY = TY + 2 * RG;
     static constexpr int NR = RX * RY, NS = 2 * RG + 1, NOUT = NT * OPT;
     static constexpr size_t o_ring = 0;
-    static constexpr size_t o_xb = o_ring + (size_t)NS * 3 * NOUT * 4;
+    static constexpr size_t o_xb = o_ring + (size_t)2 * NS * 3 * NOUT * 4;
     static constexpr size_t o_st = o_xb + (size_t)3 * RY * FX * 4;
-    static constexpr size_t o_mv = o_st + (size_t)NST * 3 * NR * 4;
-    static constexpr size_t bytes = o_mv + (size_t)NST * 6 * NOUT * 4;
+    static constexpr size_t o_mv = o_st + (size_t)NSTG * 3 * NR * 4;
+    static constexpr size_t bytes = o_mv + (size_t)NSTG * 6 * NOUT * 4;
 };
 
-template <int RG, int NW, int OPT>
+template <int RG, int NW, int OPT, int NSTG>
 __global__ void __launch_bounds__(FX *NW) k_smooth_adam(const float *__restrict__ g,
                                                         float *__restrict__ m,
                                                         float *__restrict__ v,
@@ -517,7 +598,8 @@ __global__ void __launch_bounds__(FX *NW) k_smooth_adam(const float *__restrict_
                                                         WsHeader *__restrict__ h, int D, int H,
                                                         int W, int TZ, GaussTaps t, AdamConsts ac,
                                                         int parity) {
-    using S = K3S<RG, NW, OPT>;
+    using S = K3S<RG, NW, OPT, NSTG>;
+    using G = Region<S::RY, S::RX, NW>;
     constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, NR = S::NR, NS = S::NS,
                   NOUT = S::NOUT;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -531,63 +613,64 @@ __global__ void __launch_bounds__(FX *NW) k_smooth_adam(const float *__restrict_
     const int x0 = blockIdx.x * FX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
     const int zend = min(z0 + TZ, D);
     const long long N = (long long)D * H * W, HW = (long long)H * W;
-    for (int k = tid; k < NS * 3 * NOUT; k += NT) ring[k] = 0.0f;
+    G rg;
+    rg.init(wy, tx, y0 - RG, x0 - RG, H, W);
+    Outs<OPT> ou;
+    ou.init(wy, tx, y0, x0, NW, H, W);
+    for (int k = tid; k < 2 * NS * 3 * NOUT; k += NT) ring[k] = 0.0f;
 
     const int zs = z0 - RG, np = zend - z0 + 2 * RG;
     auto issue = [&](int i) {
         if (i < np) {
             const int zp = zs + i, zo = zp - RG;
-            load_tile<3, RY, RX, NT>(st + (i % NST) * 3 * NR, g, N, D, H, W, zp, y0 - RG, x0 - RG,
-                                     tid);
+            load_plane<3, RY, RX, NW>(st + (i % NSTG) * 3 * NR, g, N, (long long)zp * HW,
+                                      zp >= 0 && zp < D, rg);
             if (zo >= z0 && zo < zend) {
-                float *o = mvs + (i % NST) * 6 * NOUT;
-                load_outputs<3, NT, OPT, NW>(o, m, N, D, H, W, zo, y0, x0, wy, tx, tid);
-                load_outputs<3, NT, OPT, NW>(o + 3 * NOUT, v, N, D, H, W, zo, y0, x0, wy, tx, tid);
+                float *o = mvs + (i % NSTG) * 6 * NOUT;
+                load_outs<3, OPT, NOUT>(o, m, N, (long long)zo * HW, ou, tid, NT);
+                load_outs<3, OPT, NOUT>(o + 3 * NOUT, v, N, (long long)zo * HW, ou, tid, NT);
             }
         }
         cp_commit();
     };
-    issue(0);
-    issue(1);
+#pragma unroll
+    for (int k = 0; k < NSTG - 1; ++k) issue(k);
 
     float mx = 0.0f;
     bool bad = false;
     int slot = 0;
     for (int i = 0; i < np; ++i) {
         const int zp = zs + i, zo = zp - RG;
-        issue(i + 2);
-        cp_wait<2>();
+        issue(i + NSTG - 1);
+        cp_wait<NSTG - 1>();
         float Q[OPT][3];
         if (zp >= 0 && zp < D) {
             __syncthreads();  // the x pass reads neighbours' copies
-            gauss_xy<RG, RY, RX, NT, NW, OPT>(st + (i % NST) * 3 * NR, xb, t, tid, wy, tx, Q);
+            gauss_xy<RG, RY, RX, NW, OPT>(st + (i % NSTG) * 3 * NR, xb, t, wy, tx, Q);
         } else {
 #pragma unroll
             for (int o = 0; o < OPT; ++o) Q[o][0] = Q[o][1] = Q[o][2] = 0.0f;
         }
-#pragma unroll
-        for (int o = 0; o < OPT; ++o)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) ring[(slot * 3 + c) * NOUT + o * NT + tid] = Q[o][c];
-        const int oldest = (slot + 1 == NS) ? 0 : slot + 1;
-        slot = oldest;
+        const int wbase = ring_push<NS, OPT, NOUT, NT>(ring, slot, tid, Q);
+        slot = (slot + 1 == NS) ? 0 : slot + 1;
         if (zo >= z0 && zo < zend) {
-            const float *mv = mvs + (i % NST) * 6 * NOUT;
+            const float *mv = mvs + (i % NSTG) * 6 * NOUT + tid;
+            const long long zoff = (long long)zo * HW;
 #pragma unroll
             for (int o = 0; o < OPT; ++o) {
-                const int y = y0 + wy + NW * o, x = x0 + tx;
-                if (y >= H || x >= W) continue;
-                const int idx = o * NT + tid;
-                const long long gi = (long long)zo * HW + (long long)y * W + x;
+                if (ou.off[o] < 0) continue;
+                const float *win = ring + wbase * 3 * NOUT + o * NT + tid;
+                const long long gi = zoff + ou.off[o];
                 float nrm2 = 0.0f;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float s = gauss_z<RG, NOUT>(ring, t, oldest, c, idx);
-                    const float mvv = fmaf(ac.b1, mv[c * NOUT + idx], (1.0f - ac.b1) * s);
-                    const float vvv = fmaf(ac.b2, mv[(3 + c) * NOUT + idx], (1.0f - ac.b2) * s * s);
+                    const float s = gauss_z<RG, NOUT>(win, t, c);
+                    const float mvv = fmaf(ac.b1, mv[c * NOUT + o * NT], (1.0f - ac.b1) * s);
+                    const float vvv =
+                        fmaf(ac.b2, mv[(3 + c) * NOUT + o * NT], (1.0f - ac.b2) * s * s);
                     m[c * N + gi] = mvv;
                     v[c * N + gi] = vvv;
-                    const float dv = (mvv / ac.bc1) / (sqrtf(vvv / ac.bc2) + ac.eps);
+                    const float dv = (mvv * ac.rbc1) / (sqrtf(vvv * ac.rbc2) + ac.eps);
                     dir[c * N + gi] = dv;
                     nrm2 = fmaf(dv, dv, nrm2);
                 }
@@ -606,20 +689,21 @@ __global__ void __launch_bounds__(FX *NW) k_smooth_adam(const float *__restrict_
 // ====================================================================== K4
 // SU: u is staged in shared memory (planes z-1..z+1, halo RG + 1); valid when
 // the step is shorter than one voxel (lr / c_lp < 1).
-template <int RG, int NW, int OPT, bool SU>
+template <int RG, int NW, int OPT, bool SU, int NSTG>
 struct K4S {
     static constexpr int NT = FX * NW, TY = NW * OPT, RX = FX + 2 * RG, RY = TY + 2 * RG;
     static constexpr int NR = RX * RY, NS = 2 * RG + 1, NOUT = NT * OPT;
-    static constexpr int URX = RX + 2, URY = RY + 2, NRU = URX * URY, NSU = 5;
+    // u planes z-1, z, z+1 in use plus NSTG - 1 in flight
+    static constexpr int URX = RX + 2, URY = RY + 2, NRU = URX * URY, NSU = NSTG + 2;
     static constexpr size_t o_ring = 0;
-    static constexpr size_t o_xb = o_ring + (size_t)NS * 3 * NOUT * 4;
+    static constexpr size_t o_xb = o_ring + (size_t)2 * NS * 3 * NOUT * 4;
     static constexpr size_t o_up = o_xb + (size_t)3 * RY * FX * 4;
     static constexpr size_t o_dst = o_up + (size_t)3 * NR * 4;
-    static constexpr size_t o_ust = o_dst + (size_t)NST * 3 * NR * 4;
+    static constexpr size_t o_ust = o_dst + (size_t)NSTG * 3 * NR * 4;
     static constexpr size_t bytes = o_ust + (SU ? (size_t)NSU * 3 * NRU * 4 : 0);
 };
 
-template <int RG, int NW, int OPT, bool SU>
+template <int RG, int NW, int OPT, bool SU, int NSTG>
 __global__ void __launch_bounds__(FX *NW) k_compose(const float *__restrict__ u,
                                                     const float *__restrict__ dir,
                                                     float *__restrict__ uo,
@@ -628,7 +712,9 @@ __global__ void __launch_bounds__(FX *NW) k_compose(const float *__restrict__ u,
                                                     WsHeader *__restrict__ h, int D, int H, int W,
                                                     int TZ, GaussTaps t, float lr, float c_lp,
                                                     int parity) {
-    using S = K4S<RG, NW, OPT, SU>;
+    using S = K4S<RG, NW, OPT, SU, NSTG>;
+    using G = Region<S::RY, S::RX, NW>;
+    using GU = Region<S::URY, S::URX, NW>;
     constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, NR = S::NR, NS = S::NS,
                   NOUT = S::NOUT, URX = S::URX, URY = S::URY, NRU = S::NRU, NSU = S::NSU;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -644,19 +730,26 @@ __global__ void __launch_bounds__(FX *NW) k_compose(const float *__restrict__ u,
     const long long N = (long long)D * H * W, HW = (long long)H * W;
     const float mxd = __uint_as_float(h->step_max_bits[parity]);
     const float e = (mxd > 0.0f) ? lr / (c_lp * mxd) : 0.0f;
-    for (int k = tid; k < NS * 3 * NOUT; k += NT) ring[k] = 0.0f;
+    G rg;
+    rg.init(wy, tx, y0 - RG, x0 - RG, H, W);
+    GU rgu;
+    if (SU) rgu.init(wy, tx, y0 - RG - 1, x0 - RG - 1, H, W);
+    Outs<OPT> ou;
+    ou.init(wy, tx, y0, x0, NW, H, W);
+    for (int k = tid; k < 2 * NS * 3 * NOUT; k += NT) ring[k] = 0.0f;
 
     const int zs = z0 - RG, np = zend - z0 + 2 * RG;
     // u plane q lives in stage (q - (zs - 1)) % NSU
     auto issue_u = [&](int q) {
-        load_tile<3, URY, URX, NT>(ust + ((q - (zs - 1)) % NSU) * 3 * NRU, u, N, D, H, W, q,
-                                   y0 - RG - 1, x0 - RG - 1, tid);
+        load_plane<3, URY, URX, NW>(ust + ((q - (zs - 1)) % NSU) * 3 * NRU, u, N,
+                                    (long long)q * HW, q >= 0 && q < D, rgu);
     };
     auto issue = [&](int i) {
         if (i < np) {
-            load_tile<3, RY, RX, NT>(dst + (i % NST) * 3 * NR, dir, N, D, H, W, zs + i, y0 - RG,
-                                     x0 - RG, tid);
-            if (SU) issue_u(zs + i + 1);
+            const int zp = zs + i;
+            load_plane<3, RY, RX, NW>(dst + (i % NSTG) * 3 * NR, dir, N, (long long)zp * HW,
+                                      zp >= 0 && zp < D, rg);
+            if (SU) issue_u(zp + 1);
         }
         cp_commit();
     };
@@ -664,8 +757,8 @@ __global__ void __launch_bounds__(FX *NW) k_compose(const float *__restrict__ u,
         issue_u(zs - 1);
         issue_u(zs);
     }
-    issue(0);  // the u planes above join group 0
-    issue(1);
+#pragma unroll
+    for (int k = 0; k < NSTG - 1; ++k) issue(k);  // the u planes above join group 0
 
     TriPending jp[OPT];
     long long jidx[OPT];
@@ -676,73 +769,77 @@ __global__ void __launch_bounds__(FX *NW) k_compose(const float *__restrict__ u,
     int slot = 0;
     for (int i = 0; i < np; ++i) {
         const int zp = zs + i, zo = zp - RG;
-        issue(i + 2);
-        cp_wait<2>();
+        issue(i + NSTG - 1);
+        cp_wait<NSTG - 1>();
         float Q[OPT][3];
         if (zp >= 0 && zp < D) {
             if (SU) __syncthreads();  // u stages hold neighbours' copies
-            const float *ds = dst + (i % NST) * 3 * NR;
+            const float *ds = dst + (i % NSTG) * 3 * NR;
             const float *um = ust + ((zp - 1 - (zs - 1)) % NSU) * 3 * NRU;
             const float *u0 = ust + ((zp - (zs - 1)) % NSU) * 3 * NRU;
             const float *u1 = ust + ((zp + 1 - (zs - 1)) % NSU) * 3 * NRU;
-            for (int k = tid; k < NR; k += NT) {
-                const int ry = k / RX, rx = k - ry * RX;
-                const int y = y0 - RG + ry, x = x0 - RG + rx;
-                float a = 0.f, b = 0.f, c = 0.f;
-                if (y >= 0 && y < H && x >= 0 && x < W) {
-                    const float dz = -e * ds[k], dy = -e * ds[NR + k], dx = -e * ds[2 * NR + k];
-                    if (SU) {
-                        // cell corners lie within one voxel: planes zp-1..zp+1
-                        if (dz > -1.0f && dz < 1.0f && dy > -1.0f && dy < 1.0f && dx > -1.0f &&
-                            dx < 1.0f) {
-                            const float fz = floorf(dz), fy = floorf(dy), fx = floorf(dx);
-                            const float tz = dz - fz, ty = dy - fy, tx2 = dx - fx;
-                            const float *pa = fz < 0.0f ? um : u0;
-                            const float *pb = fz < 0.0f ? u0 : u1;
-                            const int b0 = (ry + 1 + (int)fy) * URX + (rx + 1 + (int)fx);
-                            float r[3];
 #pragma unroll
-                            for (int ch = 0; ch < 3; ++ch) {
-                                const float *A = pa + ch * NRU, *B = pb + ch * NRU;
-                                const float c00 = fmaf(tx2, A[b0 + 1] - A[b0], A[b0]);
-                                const float c01 = fmaf(tx2, A[b0 + URX + 1] - A[b0 + URX], A[b0 + URX]);
-                                const float c10 = fmaf(tx2, B[b0 + 1] - B[b0], B[b0]);
-                                const float c11 = fmaf(tx2, B[b0 + URX + 1] - B[b0 + URX], B[b0 + URX]);
-                                const float c0 = fmaf(ty, c01 - c00, c00);
-                                const float c1 = fmaf(ty, c11 - c10, c10);
-                                r[ch] = fmaf(tz, c1 - c0, c0);
+            for (int j = 0; j < G::NJ; ++j)
+#pragma unroll
+                for (int cc = 0; cc < G::NC; ++cc) {  // own copies of d
+                    const int o = rg.off[j * G::NC + cc];
+                    if (o == -2) continue;
+                    const int k = rg.sbase + G::sofs(j, cc);
+                    float a = 0.f, b = 0.f, c = 0.f;
+                    if (o >= 0) {
+                        const float dz = -e * ds[k], dy = -e * ds[NR + k], dx = -e * ds[2 * NR + k];
+                        if (SU) {
+                            // cell corners lie within one voxel: planes zp-1..zp+1
+                            if (dz > -1.0f && dz < 1.0f && dy > -1.0f && dy < 1.0f &&
+                                dx > -1.0f && dx < 1.0f) {
+                                const float fz = floorf(dz), fy = floorf(dy), fx = floorf(dx);
+                                const float tz = dz - fz, ty = dy - fy, tx2 = dx - fx;
+                                const float *pa = fz < 0.0f ? um : u0;
+                                const float *pb = fz < 0.0f ? u0 : u1;
+                                const int ry = wy + NW * j, rx = tx + 32 * cc;
+                                const int b0 = (ry + 1 + (int)fy) * URX + (rx + 1 + (int)fx);
+                                float r[3];
+#pragma unroll
+                                for (int ch = 0; ch < 3; ++ch) {
+                                    const float *A = pa + ch * NRU + b0, *B = pb + ch * NRU + b0;
+                                    const float c00 = fmaf(tx2, A[1] - A[0], A[0]);
+                                    const float c01 = fmaf(tx2, A[URX + 1] - A[URX], A[URX]);
+                                    const float c10 = fmaf(tx2, B[1] - B[0], B[0]);
+                                    const float c11 = fmaf(tx2, B[URX + 1] - B[URX], B[URX]);
+                                    const float c0 = fmaf(ty, c01 - c00, c00);
+                                    const float c1 = fmaf(ty, c11 - c10, c10);
+                                    r[ch] = fmaf(tz, c1 - c0, c0);
+                                }
+                                a = dz + r[0];
+                                b = dy + r[1];
+                                c = dx + r[2];
+                            } else {
+                                a = b = c = __int_as_float(0x7fc00000);  // impossible step: flag it
                             }
-                            a = dz + r[0];
-                            b = dy + r[1];
-                            c = dx + r[2];
                         } else {
-                            a = b = c = __int_as_float(0x7fc00000);  // impossible step: flag it
+                            const int y = y0 - RG + wy + NW * j, x = x0 - RG + tx + 32 * cc;
+                            float gz, gy, gx;
+                            a = dz + tri_sample<false>(u, D, H, W, zp, y, x, dz, dy, dx, gz, gy, gx);
+                            b = dy + tri_sample<false>(u + N, D, H, W, zp, y, x, dz, dy, dx, gz, gy,
+                                                       gx);
+                            c = dx + tri_sample<false>(u + 2 * N, D, H, W, zp, y, x, dz, dy, dx, gz,
+                                                       gy, gx);
                         }
-                    } else {
-                        float gz, gy, gx;
-                        a = dz + tri_sample<false>(u, D, H, W, zp, y, x, dz, dy, dx, gz, gy, gx);
-                        b = dy + tri_sample<false>(u + N, D, H, W, zp, y, x, dz, dy, dx, gz, gy, gx);
-                        c = dx + tri_sample<false>(u + 2 * N, D, H, W, zp, y, x, dz, dy, dx, gz, gy,
-                                                   gx);
                     }
+                    up[k] = a;
+                    up[NR + k] = b;
+                    up[2 * NR + k] = c;
                 }
-                up[k] = a;
-                up[NR + k] = b;
-                up[2 * NR + k] = c;
-            }
             __syncthreads();
-            gauss_xy<RG, RY, RX, NT, NW, OPT>(up, xb, t, tid, wy, tx, Q);
+            gauss_xy<RG, RY, RX, NW, OPT>(up, xb, t, wy, tx, Q);
         } else {
 #pragma unroll
             for (int o = 0; o < OPT; ++o) Q[o][0] = Q[o][1] = Q[o][2] = 0.0f;
         }
-#pragma unroll
-        for (int o = 0; o < OPT; ++o)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) ring[(slot * 3 + c) * NOUT + o * NT + tid] = Q[o][c];
-        const int oldest = (slot + 1 == NS) ? 0 : slot + 1;
-        slot = oldest;
+        const int wbase = ring_push<NS, OPT, NOUT, NT>(ring, slot, tid, Q);
+        slot = (slot + 1 == NS) ? 0 : slot + 1;
         if (zo >= z0 && zo < zend) {
+            const long long zoff = (long long)zo * HW;
 #pragma unroll
             for (int o = 0; o < OPT; ++o) {
                 // finish the previous plane's warped value first (its loads have landed)
@@ -751,17 +848,16 @@ __global__ void __launch_bounds__(FX *NW) k_compose(const float *__restrict__ u,
                     Jout[jidx[o]] = tri_finish<false>(jp[o], gz, gy, gx);
                     jlive[o] = false;
                 }
-                const int y = y0 + wy + NW * o, x = x0 + tx;
-                if (y >= H || x >= W) continue;
-                const int idx = o * NT + tid;
-                const long long gi = (long long)zo * HW + (long long)y * W + x;
-                const float a = gauss_z<RG, NOUT>(ring, t, oldest, 0, idx);
-                const float b = gauss_z<RG, NOUT>(ring, t, oldest, 1, idx);
-                const float c = gauss_z<RG, NOUT>(ring, t, oldest, 2, idx);
+                if (ou.off[o] < 0) continue;
+                const float *win = ring + wbase * 3 * NOUT + o * NT + tid;
+                const long long gi = zoff + ou.off[o];
+                const float a = gauss_z<RG, NOUT>(win, t, 0);
+                const float b = gauss_z<RG, NOUT>(win, t, 1);
+                const float c = gauss_z<RG, NOUT>(win, t, 2);
                 uo[gi] = a;
                 uo[N + gi] = b;
                 uo[2 * N + gi] = c;
-                tri_issue(jp[o], Im, D, H, W, zo, y, x, a, b, c);  // J of the new map
+                tri_issue(jp[o], Im, D, H, W, zo, y0 + wy + NW * o, x0 + tx, a, b, c);
                 jidx[o] = gi;
                 jlive[o] = true;
             }
@@ -818,8 +914,8 @@ int choose_tz(int D, int tiles_xy, int halo, int ctas_per_sm) {
     return best;
 }
 
-// Per-kernel launch preparation: opt into the dynamic shared memory once and
-// query the resident CTAs per SM.
+// Opts the kernel into its dynamic shared memory and returns its resident
+// CTAs per SM (called once per kernel instantiation).
 template <class K>
 int prepare(K kernel, size_t smem, int threads) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -835,7 +931,6 @@ struct LaunchGeom {
     int tz;
 };
 
-// occ: resident CTAs per SM of the kernel (queried once per instantiation).
 inline LaunchGeom geometry(int occ, int nw, int ty, int halo, Dims d) {
     LaunchGeom g;
     const int gx = (d.W + FX - 1) / FX, gy = (d.H + ty - 1) / ty;
@@ -845,20 +940,21 @@ inline LaunchGeom geometry(int occ, int nw, int ty, int halo, Dims d) {
     return g;
 }
 
-// tile shapes (warps per CTA, outputs per thread along y)
-constexpr int K1_NW = 8, K1_OPT = 1;
-constexpr int K2_NW = 8, K2_OPT = 1;
-constexpr int K3_NW = 8, K3_OPT = 1;
-constexpr int K4_NW = 8, K4_OPT = 1;
+// tile shapes (warps per CTA, outputs per thread along y) and pipeline depth
+constexpr int K1_NW = 8, K1_OPT = 1, K1_ST = 3;
+constexpr int K2_NW = 8, K2_OPT = 1, K2_ST = 2;
+constexpr int K3_NW = 8, K3_OPT = 1, K3_ST = 2;
+constexpr int K4_NW = 8, K4_OPT = 1, K4_ST = 2;
 
 template <int R>
-cudaError_t launch_k1(const float *If, const float *J, float *coef, WsHeader *h, Dims d,
-                      int window, float cc_eps, bool wc, cudaStream_t s) {
-    using S = K1S<R, K1_NW, K1_OPT>;
-    auto kern = k_lncc_fwd<R, K1_NW, K1_OPT>;
+cudaError_t launch_k1(const float *If, const float *J, const long long *sI, const float *varI,
+                      float *coef, WsHeader *h, Dims d, int window, float cc_eps, bool wc,
+                      cudaStream_t s) {
+    using S = K1S<R, K1_NW, K1_OPT, K1_ST>;
+    auto kern = k_lncc_fwd<R, K1_NW, K1_OPT, K1_ST>;
     static const int occ = prepare(kern, S::bytes, S::NT);
     LaunchGeom g = geometry(occ, K1_NW, S::TY, R, d);
-    kern<<<g.grid, g.block, S::bytes, s>>>(If, J, coef, h, d.D, d.H, d.W, g.tz,
+    kern<<<g.grid, g.block, S::bytes, s>>>(If, J, sI, varI, coef, h, d.D, d.H, d.W, g.tz,
                                            lncc_image_bits(window), cc_eps, window, wc ? 1 : 0);
     note_launch();
     return cudaGetLastError();
@@ -867,8 +963,8 @@ cudaError_t launch_k1(const float *If, const float *J, float *coef, WsHeader *h,
 template <int R>
 cudaError_t launch_k2(const float *If, const float *Im, const float *u, const float *coef,
                       const WsHeader *h, float *g, Dims d, int window, cudaStream_t s) {
-    using S = K2S<R, K2_NW, K2_OPT>;
-    auto kern = k_lncc_grad<R, K2_NW, K2_OPT>;
+    using S = K2S<R, K2_NW, K2_OPT, K2_ST>;
+    auto kern = k_lncc_grad<R, K2_NW, K2_OPT, K2_ST>;
     static const int occ = prepare(kern, S::bytes, S::NT);
     LaunchGeom gg = geometry(occ, K2_NW, S::TY, R, d);
     kern<<<gg.grid, gg.block, S::bytes, s>>>(If, Im, u, coef, h, g, d.D, d.H, d.W, gg.tz,
@@ -880,8 +976,8 @@ cudaError_t launch_k2(const float *If, const float *Im, const float *u, const fl
 template <int RG>
 cudaError_t launch_k3(const float *g, float *m, float *v, float *dir, WsHeader *h, Dims d,
                       const GaussTaps &t, AdamConsts ac, int parity, cudaStream_t s) {
-    using S = K3S<RG, K3_NW, K3_OPT>;
-    auto kern = k_smooth_adam<RG, K3_NW, K3_OPT>;
+    using S = K3S<RG, K3_NW, K3_OPT, K3_ST>;
+    auto kern = k_smooth_adam<RG, K3_NW, K3_OPT, K3_ST>;
     static const int occ = prepare(kern, S::bytes, S::NT);
     LaunchGeom gg = geometry(occ, K3_NW, S::TY, RG, d);
     kern<<<gg.grid, gg.block, S::bytes, s>>>(g, m, v, dir, h, d.D, d.H, d.W, gg.tz, t, ac, parity);
@@ -893,8 +989,8 @@ template <int RG, bool SU>
 cudaError_t launch_k4(const float *u, const float *dir, float *uo, const float *Im, float *J,
                       WsHeader *h, Dims d, const GaussTaps &t, float lr, float c_lp, int parity,
                       cudaStream_t s) {
-    using S = K4S<RG, K4_NW, K4_OPT, SU>;
-    auto kern = k_compose<RG, K4_NW, K4_OPT, SU>;
+    using S = K4S<RG, K4_NW, K4_OPT, SU, K4_ST>;
+    auto kern = k_compose<RG, K4_NW, K4_OPT, SU, K4_ST>;
     static const int occ = prepare(kern, S::bytes, S::NT);
     LaunchGeom gg = geometry(occ, K4_NW, S::TY, RG, d);
     kern<<<gg.grid, gg.block, S::bytes, s>>>(u, dir, uo, Im, J, h, d.D, d.H, d.W, gg.tz, t, lr,
@@ -903,23 +999,24 @@ cudaError_t launch_k4(const float *u, const float *dir, float *uo, const float *
     return cudaGetLastError();
 }
 
-#define FA_CASE(n, call) \
-    case n: {            \
+#define FA_CASE(n, call)      \
+    case n: {                 \
         constexpr int RR = n; \
-        return call;     \
+        return call;          \
     }
 
-cudaError_t dispatch_k1(const float *If, const float *J, float *coef, WsHeader *h, Dims d,
-                        int window, float cc_eps, bool wc, cudaStream_t s) {
+cudaError_t dispatch_k1(const float *If, const float *J, const long long *sI, const float *varI,
+                        float *coef, WsHeader *h, Dims d, int window, float cc_eps, bool wc,
+                        cudaStream_t s) {
     switch (window / 2) {
-        FA_CASE(0, (launch_k1<RR>(If, J, coef, h, d, window, cc_eps, wc, s)))
-        FA_CASE(1, (launch_k1<RR>(If, J, coef, h, d, window, cc_eps, wc, s)))
-        FA_CASE(2, (launch_k1<RR>(If, J, coef, h, d, window, cc_eps, wc, s)))
-        FA_CASE(3, (launch_k1<RR>(If, J, coef, h, d, window, cc_eps, wc, s)))
-        FA_CASE(4, (launch_k1<RR>(If, J, coef, h, d, window, cc_eps, wc, s)))
-        FA_CASE(5, (launch_k1<RR>(If, J, coef, h, d, window, cc_eps, wc, s)))
-        FA_CASE(6, (launch_k1<RR>(If, J, coef, h, d, window, cc_eps, wc, s)))
-        FA_CASE(7, (launch_k1<RR>(If, J, coef, h, d, window, cc_eps, wc, s)))
+        FA_CASE(0, (launch_k1<RR>(If, J, sI, varI, coef, h, d, window, cc_eps, wc, s)))
+        FA_CASE(1, (launch_k1<RR>(If, J, sI, varI, coef, h, d, window, cc_eps, wc, s)))
+        FA_CASE(2, (launch_k1<RR>(If, J, sI, varI, coef, h, d, window, cc_eps, wc, s)))
+        FA_CASE(3, (launch_k1<RR>(If, J, sI, varI, coef, h, d, window, cc_eps, wc, s)))
+        FA_CASE(4, (launch_k1<RR>(If, J, sI, varI, coef, h, d, window, cc_eps, wc, s)))
+        FA_CASE(5, (launch_k1<RR>(If, J, sI, varI, coef, h, d, window, cc_eps, wc, s)))
+        FA_CASE(6, (launch_k1<RR>(If, J, sI, varI, coef, h, d, window, cc_eps, wc, s)))
+        FA_CASE(7, (launch_k1<RR>(If, J, sI, varI, coef, h, d, window, cc_eps, wc, s)))
     }
     return cudaErrorInvalidValue;
 }
@@ -995,16 +1092,24 @@ struct KTimer {
 }  // namespace
 
 void fused_carve(WsCarver &c, long long n, FusedBuffers *fb) {
-    fb->coef = c.take<float>(3 * n);
-    fb->g = c.take<float>(3 * n);
+    fb->coef = c.take<float>(4 * n);  // also the first int64 scratch of the fixed statistics
+    fb->g = c.take<float>(4 * n);     // also the second one
     fb->dir = c.take<float>(3 * n);
     fb->J = c.take<float>(n);
     fb->t1 = c.take<float>(3 * n);
     fb->t2 = c.take<float>(3 * n);
+    fb->sI = c.take<long long>(n);
+    fb->varI = c.take<float>(n);
 }
 
-cudaError_t fused_level_start(const float *Im, const float *u, Dims d, FusedBuffers &fb,
+cudaError_t fused_level_start(const float *If, const float *Im, const float *u, Dims d,
+                              const fa_params *p, const WsHeader *h, FusedBuffers &fb,
                               cudaStream_t s) {
+    if (p->loss == FA_LOSS_LNCC) {
+        cudaError_t e = launch_fixed_stats(If, d, p->window, h, (long long *)fb.coef,
+                                           (long long *)fb.g, fb.sI, fb.varI, s);
+        if (e != cudaSuccess) return e;
+    }
     return launch_warp(Im, u, fb.J, nullptr, d, s);
 }
 
@@ -1025,7 +1130,8 @@ fa_status fused_iteration(FusedBuffers &fb, WsHeader *h, const fa_params *p, Dim
     const int parity = it.t & 1;
     if (p->loss == FA_LOSS_LNCC) {
         FA_CUDA_TRY(start(FA_K_FUSED_WARP_LNCC));
-        FA_CUDA_TRY(dispatch_k1(it.If, fb.J, fb.coef, h, d, p->window, p->cc_eps, true, s));
+        FA_CUDA_TRY(dispatch_k1(it.If, fb.J, fb.sI, fb.varI, fb.coef, h, d, p->window, p->cc_eps,
+                                true, s));
         FA_CUDA_TRY(stop(FA_K_FUSED_WARP_LNCC));
         FA_CUDA_TRY(start(FA_K_FUSED_LNCC_GRAD));
         FA_CUDA_TRY(dispatch_k2(it.If, it.Im, it.u, fb.coef, h, fb.g, d, p->window, s));
@@ -1064,9 +1170,9 @@ fa_status fused_iteration(FusedBuffers &fb, WsHeader *h, const fa_params *p, Dim
     return FA_OK;
 }
 
-cudaError_t fused_lncc_forward_only(const float *If, const float *J, Dims d, int window,
+cudaError_t fused_lncc_forward_only(const float *If, const FusedBuffers &fb, Dims d, int window,
                                     float cc_eps, WsHeader *h, cudaStream_t s) {
-    return dispatch_k1(If, J, nullptr, h, d, window, cc_eps, false, s);
+    return dispatch_k1(If, fb.J, fb.sI, fb.varI, nullptr, h, d, window, cc_eps, false, s);
 }
 
 }  // namespace fa

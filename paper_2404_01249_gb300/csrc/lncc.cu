@@ -23,27 +23,6 @@
 
 namespace fa {
 
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-    s = a + b;
-    float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-
-__device__ __forceinline__ void ff_add(float &h, float &l, float bh, float bl) {
-    float s, e;
-    two_sum(h, bh, s, e);
-    e += l + bl;
-    h = s + e;
-    l = e - (h - s);
-}
-
-// (hi, lo) of a * (xh + xl) for a float a and an exact float-float x.
-__device__ __forceinline__ void ff_mul_f(float a, float xh, float xl, float &h, float &l) {
-    h = a * xh;
-    l = fmaf(a, xh, -h);
-    l = fmaf(a, xl, l);
-}
-
 __host__ __device__ inline int log2_ceil_window(int window) {
     long long n = (long long)window * window * window;
     int lg = 0;
@@ -160,20 +139,23 @@ __global__ void __launch_bounds__(256) k_lncc_coef(const long long *__restrict__
         float varI = diff_i128_to_float(n, sII, sI, sI) * inv_s * inv_s * inv_nf;
         float varJ = diff_i128_to_float(n, sJJ, sJ, sJ) * inv_s * inv_s * inv_nf;
         float cross = diff_i128_to_float(n, sIJ, sI, sJ) * inv_s * inv_s * inv_nf;
-        float SIf = __ll2float_rn(sI) * inv_s, SJf = __ll2float_rn(sJ) * inv_s;
         float den = fmaf(varI, varJ, cc_eps);
-        float cc = cross * cross / den;
-        A = 2.0f * cross / den;
-        B = -cc * varI / den;
-        Cc = -(A * SIf + 2.0f * B * SJf) / nf;
+        float rden = 1.0f / den;
+        float cc = cross * cross * rden;
+        A = 2.0f * cross * rden;
+        B = -cc * varI * rden;
+        float clo;
+        lncc_c_ff(A, B, sI, sJ, inv_s, nf, inv_nf, Cc, clo);
         coef[i] = A;
         coef[N + i] = B;
         coef[2 * N + i] = Cc;
+        coef[3 * N + i] = clo;
         if (WANT_DI) {
-            Bp = -cc * varJ / den;
-            Cp = -(A * SJf + 2.0f * Bp * SIf) / nf;
-            coef[3 * N + i] = Bp;
-            coef[4 * N + i] = Cp;
+            Bp = -cc * varJ * rden;
+            lncc_c_ff(A, Bp, sJ, sI, inv_s, nf, inv_nf, Cp, clo);
+            coef[4 * N + i] = Bp;
+            coef[5 * N + i] = Cp;
+            coef[6 * N + i] = clo;
         }
         if (cc >= 0.0f && cc <= 2.0f) {
             qcc = (unsigned long long)__float2ull_rn(cc * 4294967296.0f);
@@ -191,28 +173,37 @@ __global__ void __launch_bounds__(256) k_lncc_coef(const long long *__restrict__
     }
 }
 
-// x-window sums of the quantised adjoint coefficients: channels sel[0..NC)
+// x-window sums of the quantised adjoint coefficients.  Output channel c
+// quantises coef[hi[c]] (+ coef[lo[c]] when lo[c] >= 0, the low half of a
+// float-float coefficient) with the scale of coef_max_bits[mx[c]].
+struct CoefSel {
+    int hi[4], lo[4], mx[4];
+};
+
 template <int NC, int R>
 __global__ void __launch_bounds__(256) k_coef_xpass(const float *__restrict__ coef,
                                                     const WsHeader *__restrict__ h,
                                                     long long *__restrict__ p, int D, int H,
-                                                    int W, int cbits, int4 sel) {
+                                                    int W, int cbits, CoefSel sel) {
     int x = blockIdx.x * 32 + threadIdx.x;
     int y = blockIdx.y * 8 + threadIdx.y;
     int z = blockIdx.z;
     if (x >= W || y >= H) return;
     long long N = (long long)D * H * W;
     long long row = ((long long)z * H + y) * W;
-    const int chan[4] = {sel.x, sel.y, sel.z, sel.w};
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        const float *src = coef + chan[c] * N + row;
-        float sc = pow2f(fixed_shift(__uint_as_float(h->coef_max_bits[chan[c]]), cbits));
+        const float *src = coef + sel.hi[c] * N + row;
+        const float *lo = sel.lo[c] >= 0 ? coef + sel.lo[c] * N + row : nullptr;
+        float sc = pow2f(fixed_shift(__uint_as_float(h->coef_max_bits[sel.mx[c]]), cbits));
         long long acc = 0;
 #pragma unroll
         for (int k = -R; k <= R; ++k) {
             int xx = x + k;
-            if (xx >= 0 && xx < W) acc += quantize(__ldg(src + xx), sc);
+            if (xx >= 0 && xx < W) {
+                acc += quantize(__ldg(src + xx), sc);
+                if (lo) acc += quantize(__ldg(lo + xx), sc);
+            }
         }
         p[c * N + row + x] = acc;
     }
@@ -344,14 +335,68 @@ __global__ void k_partials_finalize(const float *partials, long long nb, long lo
     }
 }
 
+// Window statistics of the fixed image alone (constant during a level): the
+// exact sum S_I and the rounded variance var_I, both as the LNCC kernels
+// compute them.
+template <int R>
+__global__ void __launch_bounds__(256) k_fixed_xpass(const float *__restrict__ I,
+                                                     const WsHeader *__restrict__ h,
+                                                     long long *__restrict__ p, int D, int H,
+                                                     int W, int bits) {
+    int x = blockIdx.x * 32 + threadIdx.x;
+    int y = blockIdx.y * 8 + threadIdx.y;
+    int z = blockIdx.z;
+    if (x >= W || y >= H) return;
+    long long N = (long long)D * H * W;
+    long long row = ((long long)z * H + y) * W;
+    float sc = image_scale(h, bits);
+    long long sI = 0, sII = 0;
+#pragma unroll
+    for (int k = -R; k <= R; ++k) {
+        int xx = x + k;
+        if (xx < 0 || xx >= W) continue;
+        long long qi = quantize(__ldg(I + row + xx), sc);
+        sI += qi;
+        sII += qi * qi;
+    }
+    p[row + x] = sI;
+    p[N + row + x] = sII;
+}
+
+__global__ void __launch_bounds__(256) k_fixed_finalize(const long long *__restrict__ S,
+                                                        const WsHeader *__restrict__ h,
+                                                        long long *__restrict__ sI_out,
+                                                        float *__restrict__ varI_out, int D,
+                                                        int H, int W, int window, int bits) {
+    int x = blockIdx.x * 32 + threadIdx.x;
+    int y = blockIdx.y * 8 + threadIdx.y;
+    int z = blockIdx.z;
+    if (x >= W || y >= H) return;
+    long long N = (long long)D * H * W;
+    long long i = ((long long)z * H + y) * W + x;
+    const long long n = (long long)window * window * window;
+    const float inv_nf = 1.0f / (float)n;
+    float amax = fmaxf(__uint_as_float(h->absmax_bits[0]), __uint_as_float(h->absmax_bits[1]));
+    float inv_s = pow2f(-fixed_shift(amax, bits));
+    long long sI = S[i], sII = S[N + i];
+    sI_out[i] = sI;
+    varI_out[i] = diff_i128_to_float(n, sII, sI, sI) * inv_s * inv_s * inv_nf;
+}
+
 // ---------------------------------------------------------------- launchers
+
+LnccBuffers lncc_carve(WsCarver &c, long long N) {
+    LnccBuffers b;
+    b.p0 = c.take<long long>(5 * N);
+    b.p1 = c.take<long long>(5 * N);
+    b.coef = c.take<float>(7 * N);
+    return b;
+}
 
 size_t lncc_plain_bytes(long long N) {
     WsCarver c(nullptr, ~size_t(0));
     c.take<WsHeader>(1);
-    c.take<long long>(5 * N);
-    c.take<long long>(5 * N);
-    c.take<float>(5 * N);
+    lncc_carve(c, N);
     return c.off;
 }
 
@@ -376,7 +421,7 @@ static void xpass_img(const float *I, const float *J, WsHeader *h, long long *p,
 
 template <int NC, int R>
 static void xpass_coef(const float *coef, const WsHeader *h, long long *p, Dims d, int cbits,
-                       int4 sel, cudaStream_t s) {
+                       CoefSel sel, cudaStream_t s) {
     VoxGrid g(d.D, d.H, d.W);
     k_coef_xpass<NC, R><<<g.grid, g.block, 0, s>>>(coef, h, p, d.D, d.H, d.W, cbits, sel); note_launch();
 }
@@ -425,16 +470,19 @@ cudaError_t launch_lncc_backward(const float *I, const float *J, const float *gr
     int R = window / 2;
     int cbits = lncc_coef_bits(window);
     bool wantJ = dJ || g;
-    int4 sel;
+    // coefficient channels: 0 A, 1 B, 2/3 C (hi/lo), 4 B', 5/6 C' (hi/lo);
+    // maxima: 0 A, 1 B, 2 C, 3 B', 4 C'
+    const CoefSel cA{{0, 0, 0, 0}, {-1, -1, -1, -1}, {0, 0, 0, 0}};
+    CoefSel sel = cA;
     int nc;
     if (wantJ && dI) {
-        sel = make_int4(0, 1, 2, 3);  // SA, SB, SC, SB' (+ SC' in a second pass)
+        sel = CoefSel{{0, 1, 2, 4}, {-1, -1, 3, -1}, {0, 1, 2, 3}};  // SA, SB, SC, SB'
         nc = 5;
     } else if (wantJ) {
-        sel = make_int4(0, 1, 2, 0);
+        sel = CoefSel{{0, 1, 2, 0}, {-1, -1, 3, -1}, {0, 1, 2, 0}};
         nc = 3;
     } else {
-        sel = make_int4(0, 3, 4, 0);
+        sel = CoefSel{{0, 4, 5, 0}, {-1, -1, 6, -1}, {0, 3, 4, 0}};  // SA, SB', SC'
         nc = 3;
     }
     if (nc == 3) {
@@ -443,8 +491,8 @@ cudaError_t launch_lncc_backward(const float *I, const float *J, const float *gr
     } else {
         FA_DISPATCH_R(R, (xpass_coef<4, RR>(b.coef, h, b.p0, d, cbits, sel, s)));
         long long N = d.N();
-        FA_DISPATCH_R(R, (xpass_coef<1, RR>(b.coef, h, b.p0 + 4 * N, d, cbits,
-                                            make_int4(4, 0, 0, 0), s)));
+        const CoefSel sc5{{5, 0, 0, 0}, {6, -1, -1, -1}, {4, 0, 0, 0}};  // SC'
+        FA_DISPATCH_R(R, (xpass_coef<1, RR>(b.coef, h, b.p0 + 4 * N, d, cbits, sc5, s)));
         box_yz<5>(b.p0, b.p1, d, R, s);
     }
     VoxGrid gg(d.D, d.H, d.W);
@@ -464,6 +512,21 @@ cudaError_t launch_mse(const float *I, const float *J, const float *grad, Dims d
     long long nb = mse_partials_count(d);
     k_mse<<<gg.grid, gg.block, 0, s>>>(I, J, grad, dJ, dI, g, partials, d.D, d.H, d.W); note_launch();
     k_partials_finalize<<<1, 256, 0, s>>>(partials, nb, d.N(), h, nullptr); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fixed_stats(const float *I, Dims d, int window, const WsHeader *h,
+                               long long *p0, long long *p1, long long *sI, float *varI,
+                               cudaStream_t s) {
+    int R = window / 2;
+    int bits = lncc_image_bits(window);
+    VoxGrid g(d.D, d.H, d.W);
+    FA_DISPATCH_R(R, (k_fixed_xpass<RR><<<g.grid, g.block, 0, s>>>(I, h, p0, d.D, d.H, d.W, bits)));
+    note_launch();
+    k_box_axis<2, 1><<<g.grid, g.block, 0, s>>>(p0, p1, d.D, d.H, d.W, R); note_launch();
+    k_box_axis<2, 2><<<g.grid, g.block, 0, s>>>(p1, p0, d.D, d.H, d.W, R); note_launch();
+    k_fixed_finalize<<<g.grid, g.block, 0, s>>>(p0, h, sI, varI, d.D, d.H, d.W, window, bits);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -521,10 +584,7 @@ extern "C" fa_status fa_lncc_fwd_bwd(const fa_vol *fixed, const fa_vol *warped, 
     long long N = d.N();
     WsCarver c(ws, ws_bytes);
     WsHeader *h = c.take<WsHeader>(1);
-    LnccBuffers b;
-    b.p0 = c.take<long long>(5 * N);
-    b.p1 = c.take<long long>(5 * N);
-    b.coef = c.take<float>(5 * N);
+    LnccBuffers b = lncc_carve(c, N);
     const float *I = (const float *)fixed->data, *J = (const float *)warped->data;
     FA_CUDA_TRY(launch_header_reset(h, s));
     FA_CUDA_TRY(launch_absmax2(I, J, N, h, s));

@@ -12,8 +12,8 @@
 //
 // Limits and rules for callers:
 //  * the grid may hold at most as many voxels as fit the scratch (the
-//    same bytes fa_lncc_workspace_size reports: at most 671,084 voxels, e.g.
-//    80 x 96 x 87); larger grids are rejected with FA_ERR_SHAPE before
+//    same bytes fa_lncc_workspace_size reports: at most 621,376 voxels, e.g.
+//    80 x 96 x 80); larger grids are rejected with FA_ERR_SHAPE before
 //    anything is launched;
 //  * the first call on each device looks up the array's device address
 //    (cudaGetSymbolAddress, with that device current); make that first call
@@ -91,7 +91,7 @@ extern "C" fa_status fa_lncc_fwd_bwd_noalloc(const fa_vol *fixed, const fa_vol *
     size_t need = lncc_plain_bytes(N);
     if (need > kNoAllocScratchBytes) {
         set_error("fa_lncc_fwd_bwd_noalloc: a %dx%dx%d grid needs %zu bytes of scratch but the "
-                  "built-in scratch holds %zu (at most 671084 voxels); use fa_lncc_fwd_bwd with a "
+                  "built-in scratch holds %zu (at most 621376 voxels); use fa_lncc_fwd_bwd with a "
                   "workspace",
                   d.D, d.H, d.W, need, kNoAllocScratchBytes);
         return FA_ERR_SHAPE;
@@ -101,10 +101,7 @@ extern "C" fa_status fa_lncc_fwd_bwd_noalloc(const fa_vol *fixed, const fa_vol *
     cudaStream_t s = (cudaStream_t)stream;
     WsCarver c(scratch, kNoAllocScratchBytes);
     WsHeader *h = c.take<WsHeader>(1);
-    LnccBuffers b;
-    b.p0 = c.take<long long>(5 * N);
-    b.p1 = c.take<long long>(5 * N);
-    b.coef = c.take<float>(5 * N);
+    LnccBuffers b = lncc_carve(c, N);
     const float *I = (const float *)fixed->data, *J = (const float *)warped->data;
     FA_CUDA_TRY(launch_header_reset(h, s));  // loss accumulator, maxima, status start at zero
     FA_CUDA_TRY(launch_absmax2(I, J, N, h, s));

@@ -29,9 +29,10 @@ cudaError_t launch_warp(const float *Im, const float *u, float *J, float *grad, 
 // Header fields used: absmax_bits, coef_max_bits, loss_acc, status.
 struct LnccBuffers {
     long long *p0, *p1;   // [5][N] int64 each
-    float *coef;          // [5][N]: A, B, C, B', C'
+    float *coef;          // [7][N]: A, B, C hi, C lo, B', C' hi, C' lo
 };
 size_t lncc_plain_bytes(long long N);
+LnccBuffers lncc_carve(WsCarver &c, long long N);  // the plain-path scratch of an N-voxel grid
 cudaError_t launch_absmax2(const float *I, const float *J, long long N, WsHeader *h,
                            cudaStream_t s);
 // Forward: coefficients and loss accumulator.  want_dI selects B', C'.
@@ -45,6 +46,11 @@ cudaError_t launch_lncc_backward(const float *I, const float *J, const float *gr
 long long mse_partials_count(Dims d);  // floats of `partials` launch_mse needs
 cudaError_t launch_mse(const float *I, const float *J, const float *grad, Dims d, WsHeader *h,
                        float *partials, float *dJ, float *dI, float *g, cudaStream_t s);
+// Exact window sum S_I and rounded variance of the fixed image (p0, p1:
+// 2N int64 scratch each).
+cudaError_t launch_fixed_stats(const float *I, Dims d, int window, const WsHeader *h,
+                               long long *p0, long long *p1, long long *sI, float *varI,
+                               cudaStream_t s);
 // loss_out = sign * loss_acc * 2^-32 / N; also stored in h->loss.
 cudaError_t launch_loss_finalize(WsHeader *h, long long N, float sign, float *loss_out,
                                  cudaStream_t s);
@@ -59,7 +65,7 @@ cudaError_t launch_gauss3(const float *in, float *out, float *t1, float *t2, int
 
 // ---- Adam, step scale, compose (adam.cu)
 struct AdamConsts {
-    float b1, b2, eps, bc1, bc2;  // bc = 1 - beta^t
+    float b1, b2, eps, rbc1, rbc2;  // rbc = 1 / (1 - beta^t)
 };
 AdamConsts adam_consts(const fa_params *p, int t);
 fa_status check_adam_params(const fa_params *p, const char *who);

@@ -113,9 +113,7 @@ static void make_plan(Plan &P, void *base, size_t cap, Dims full, const fa_param
     memset(&P.lb, 0, sizeof(P.lb));
     memset(&P.fb, 0, sizeof(P.fb));
     if (p->mode == FA_MODE_PLAIN) {
-        P.lb.p0 = c.take<long long>(5 * n);
-        P.lb.p1 = c.take<long long>(5 * n);
-        P.lb.coef = c.take<float>(5 * n);
+        P.lb = lncc_carve(c, n);
     } else {
         fused_carve(c, n, &P.fb);
     }
@@ -184,7 +182,7 @@ static fa_status final_loss(Plan &P, const fa_params *p, int l, const float *If,
         if (p->mode == FA_MODE_PLAIN) {
             FA_CUDA_TRY(launch_lncc_forward(If, P.J, d, p->window, p->cc_eps, false, P.h, P.lb, s));
         } else {
-            FA_CUDA_TRY(fused_lncc_forward_only(If, P.fb.J, d, p->window, p->cc_eps, P.h, s));
+            FA_CUDA_TRY(fused_lncc_forward_only(If, P.fb, d, p->window, p->cc_eps, P.h, s));
         }
         FA_CUDA_TRY(launch_loss_finalize(P.h, d.N(), -1.0f, loss_dev, s));
     } else {
@@ -260,7 +258,8 @@ fa_status register_impl(const fa_vol *fixed, const fa_vol *moving, const fa_para
         FA_CUDA_TRY(cudaMemsetAsync(P.h->absmax_bits, 0, sizeof(P.h->absmax_bits), s));
         FA_CUDA_TRY(launch_absmax2(If, Im, d.N(), P.h, s));
         Timer tm{timer, l};
-        if (p->mode == FA_MODE_FUSED) FA_CUDA_TRY(fused_level_start(Im, P.u[cur], d, P.fb, s));
+        if (p->mode == FA_MODE_FUSED)
+            FA_CUDA_TRY(fused_level_start(If, Im, P.u[cur], d, p, P.h, P.fb, s));
         for (int it = 0; it < p->iters[l]; ++it) {
             ++t;
             if (p->mode == FA_MODE_PLAIN) {

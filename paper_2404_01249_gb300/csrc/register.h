@@ -6,11 +6,13 @@ namespace fa {
 
 // Scratch of the fused iteration (carved from the registration workspace).
 struct FusedBuffers {
-    float *coef;   // [3][N]: A, B, C of the LNCC adjoint
+    float *coef;   // [4][N]: A, B, C hi, C lo of the LNCC adjoint
     float *g;      // [3][N]: dL/dphi before smoothing
     float *dir;    // [3][N]: Adam direction d
     float *J;      // [N]    : warped image I_m o phi of the current map
     float *t1, *t2;  // [3][N]: separable passes when a Gaussian is wider than the fused kernels take
+    long long *sI; // [N]    : exact window sum of the level's fixed image
+    float *varI;   // [N]    : its window variance
 };
 void fused_carve(WsCarver &c, long long n, FusedBuffers *fb);
 
@@ -23,12 +25,14 @@ struct FusedIter {
 fa_status fused_iteration(FusedBuffers &fb, WsHeader *h, const fa_params *p, Dims d,
                           const FusedIter &it, const GaussTaps &tg, const GaussTaps &tw,
                           fa_kernel_timer *timer, int level, cudaStream_t s);
-// J = I_m o (id + u) for the first fused iteration of a level (later
-// iterations get J from the compose kernel).
-cudaError_t fused_level_start(const float *Im, const float *u, Dims d, FusedBuffers &fb,
+// Per-level set-up of the fused path: the fixed image's window statistics
+// (LNCC) and J = I_m o (id + u) for the first iteration (later iterations
+// get J from the compose kernel).  Needs the level's image maxima in h.
+cudaError_t fused_level_start(const float *If, const float *Im, const float *u, Dims d,
+                              const fa_params *p, const WsHeader *h, FusedBuffers &fb,
                               cudaStream_t s);
-// LNCC loss accumulator only (no coefficients) for the warped image J.
-cudaError_t fused_lncc_forward_only(const float *If, const float *J, Dims d, int window,
+// LNCC loss accumulator only (no coefficients) for the warped image fb.J.
+cudaError_t fused_lncc_forward_only(const float *If, const FusedBuffers &fb, Dims d, int window,
                                     float cc_eps, WsHeader *h, cudaStream_t s);
 
 fa_status register_impl(const fa_vol *fixed, const fa_vol *moving, const fa_params *p,

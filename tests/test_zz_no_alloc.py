@@ -60,4 +60,4 @@ def test_noalloc_rejects_grids_beyond_its_scratch(fa):
     with pytest.raises(fa.FAError) as e:
         call_noalloc(fa, big, big, 5, 1e-5)
     assert e.value.status == 2
-    assert "671084" in str(e.value)
+    assert "621376" in str(e.value)
