@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(256) k_adam(const float *__restrict__ g, float
             float vv = fmaf(c.b2, v[k], (1.0f - c.b2) * gv * gv);
             m[k] = mv;
             v[k] = vv;
-            float dv = (mv * c.rbc1) / (sqrtf(vv * c.rbc2) + c.eps);
+            float dv = adam_dir(mv, vv, c.rbc1, c.rbc2, c.eps);
             d[k] = dv;
             nrm2 = fmaf(dv, dv, nrm2);
         }

@@ -294,6 +294,15 @@ __device__ __forceinline__ void lncc_c_ff(float A, float B, long long sI, long l
     cl = -pl;
 }
 
+// Adam direction d = (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps) with the
+// bias corrections passed as reciprocals; square root and quotient use the
+// hardware approximations (a few ulp).
+__device__ __forceinline__ float adam_dir(float m, float v, float rbc1, float rbc2, float eps) {
+    const float vh = v * rbc2;
+    const float sq = vh > 0.0f ? vh * rsqrtf(vh) : 0.0f;
+    return __fdividef(m * rbc1, sq + eps);
+}
+
 // 2^s as a float for s in [-126, 127] (clamped).
 __device__ __forceinline__ float pow2f(int s) {
     s = s < -126 ? -126 : (s > 127 ? 127 : s);

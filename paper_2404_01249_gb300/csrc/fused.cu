@@ -59,17 +59,22 @@ __device__ __forceinline__ void cp_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// A thread's positions in an RY x RX region (RX <= 64).
-template <int RY, int RX, int NW>
+// Row stride of an RX-wide shared region: a multiple of 4 elements, so that
+// 16-byte vector loads of a row start aligned.
+constexpr int pad4(int x) { return (x + 3) & ~3; }
+
+// A thread's positions in an RY x RX region (RX <= 64) stored with row
+// stride RXP.
+template <int RY, int RX, int NW, int RXP = pad4(RX)>
 struct Region {
     static constexpr int NJ = (RY + NW - 1) / NW;  // row slots
     static constexpr int NC = (RX + 31) / 32;      // column slots
     static constexpr int NP = NJ * NC;
     int off[NP];  // y W + x inside the grid, -1 outside the grid, -2 outside the region
-    int sbase;    // shared index of slot (0, 0): wy RX + tx
+    int sbase;    // shared index of slot (0, 0): wy RXP + tx
 
     __device__ __forceinline__ void init(int wy, int tx, int ybase, int xbase, int H, int W) {
-        sbase = wy * RX + tx;
+        sbase = wy * RXP + tx;
 #pragma unroll
         for (int j = 0; j < NJ; ++j)
 #pragma unroll
@@ -81,15 +86,15 @@ struct Region {
                 off[j * NC + c] = o;
             }
     }
-    static __device__ __forceinline__ int sofs(int j, int c) { return NW * j * RX + 32 * c; }
+    static __device__ __forceinline__ int sofs(int j, int c) { return NW * j * RXP + 32 * c; }
 };
 
-// Copies C channels of plane zp onto [C][RY][RX] shared floats (zero outside).
-template <int C, int RY, int RX, int NW>
+// Copies C channels of plane zp onto [C][RY][RXP] shared floats (zero outside).
+template <int C, int RY, int RX, int NW, int RXP>
 __device__ __forceinline__ void load_plane(float *dst, const float *src, long long N,
                                            long long zoff, bool zok,
-                                           const Region<RY, RX, NW> &rg) {
-    using G = Region<RY, RX, NW>;
+                                           const Region<RY, RX, NW, RXP> &rg) {
+    using G = Region<RY, RX, NW, RXP>;
 #pragma unroll
     for (int j = 0; j < G::NJ; ++j)
 #pragma unroll
@@ -100,7 +105,7 @@ __device__ __forceinline__ void load_plane(float *dst, const float *src, long lo
             const float *s = src + (ok ? zoff + o : 0);
             float *d = dst + rg.sbase + G::sofs(j, c);
 #pragma unroll
-            for (int ch = 0; ch < C; ++ch) cp4(d + ch * RY * RX, s + ch * N, ok);
+            for (int ch = 0; ch < C; ++ch) cp4(d + ch * RY * RXP, s + ch * N, ok);
         }
 }
 
@@ -129,18 +134,150 @@ __device__ __forceinline__ void load_outs(float *dst, const float *src, long lon
     }
 }
 
+// ------------------------------------------------- register-blocked x passes
+// A work item is (channel, row, group of 4 adjacent output columns); items
+// are spread over all threads.  Rows are read with 16-byte shared loads.
+
+// Gaussian x pass: pl [C][RY][RXP] -> xb [C][RY][FX].
+template <int RG, int C, int RY, int RXP, int NT>
+__device__ __forceinline__ void gauss_x4(const float *pl, float *xb, const GaussTaps &t, int tid) {
+    constexpr int ITEMS = C * RY * 8, NL = (4 + 2 * RG + 3) / 4;
+    static_assert(28 + 4 * NL <= RXP, "row too short for the vector loads");
+#pragma unroll
+    for (int j = 0; j < (ITEMS + NT - 1) / NT; ++j) {
+        const int it = tid + j * NT;
+        if (ITEMS % NT != 0 && it >= ITEMS) break;
+        const int k = it & 7, rest = it >> 3, ry = rest % RY, c = rest / RY;
+        const float4 *src = (const float4 *)(pl + (c * RY + ry) * RXP + 4 * k);
+        float v[4 * NL];
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            const float4 q = src[l];
+            v[4 * l] = q.x;
+            v[4 * l + 1] = q.y;
+            v[4 * l + 2] = q.z;
+            v[4 * l + 3] = q.w;
+        }
+        float o[4];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            float a = 0.0f;
+#pragma unroll
+            for (int tt = 0; tt <= 2 * RG; ++tt) a = fmaf(t.w[tt], v[jj + tt], a);
+            o[jj] = a;
+        }
+        *(float4 *)(xb + (c * RY + ry) * FX + 4 * k) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+}
+
+// Sliding window sums of 4 adjacent outputs from 4 + 2R values.
+template <int R, class T>
+__device__ __forceinline__ void slide4(const T *p, T s[4]) {
+    T a = 0;
+#pragma unroll
+    for (int t = 0; t <= 2 * R; ++t) a += p[t];
+    s[0] = a;
+#pragma unroll
+    for (int jj = 1; jj < 4; ++jj) {
+        a += p[2 * R + jj] - p[jj - 1];
+        s[jj] = a;
+    }
+}
+
+__device__ __forceinline__ void store_ll4(long long *d, const long long s[4]) {
+    ((longlong2 *)d)[0] = make_longlong2(s[0], s[1]);
+    ((longlong2 *)d)[1] = make_longlong2(s[2], s[3]);
+}
+
+// LNCC forward x pass on quantised planes qI, qJ [RY][RXP] (int32) ->
+// xL [3][RY][FX] int64: channel 0 sum J, 1 sum J^2, 2 sum I J.
+template <int R, int RY, int RXP, int NT>
+__device__ __forceinline__ void box_x4_fwd(const int *qI, const int *qJ, long long *xL, int tid) {
+    constexpr int ITEMS = 3 * RY * 8, NL = (4 + 2 * R + 3) / 4, NV = 4 + 2 * R;
+    static_assert(28 + 4 * NL <= RXP, "row too short for the vector loads");
+#pragma unroll
+    for (int j = 0; j < (ITEMS + NT - 1) / NT; ++j) {
+        const int it = tid + j * NT;
+        if (ITEMS % NT != 0 && it >= ITEMS) break;
+        const int k = it & 7, rest = it >> 3, ry = rest % RY, c = rest / RY;
+        int vj[4 * NL], vi[4 * NL];
+        const int4 *sj = (const int4 *)(qJ + ry * RXP + 4 * k);
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            const int4 q = sj[l];
+            vj[4 * l] = q.x;
+            vj[4 * l + 1] = q.y;
+            vj[4 * l + 2] = q.z;
+            vj[4 * l + 3] = q.w;
+        }
+        long long out[4];
+        if (c == 0) {
+            int s4[4];
+            slide4<R, int>(vj, s4);
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) out[jj] = s4[jj];
+        } else {
+            if (c == 2) {
+                const int4 *si = (const int4 *)(qI + ry * RXP + 4 * k);
+#pragma unroll
+                for (int l = 0; l < NL; ++l) {
+                    const int4 q = si[l];
+                    vi[4 * l] = q.x;
+                    vi[4 * l + 1] = q.y;
+                    vi[4 * l + 2] = q.z;
+                    vi[4 * l + 3] = q.w;
+                }
+            } else {
+#pragma unroll
+                for (int l = 0; l < 4 * NL; ++l) vi[l] = vj[l];
+            }
+            long long pr[NV];
+#pragma unroll
+            for (int t = 0; t < NV; ++t) pr[t] = (long long)vi[t] * vj[t];
+            slide4<R, long long>(pr, out);
+        }
+        store_ll4(xL + (c * RY + ry) * FX + 4 * k, out);
+    }
+}
+
+// LNCC adjoint x pass on quantised coefficients q [3][RY][RXP] (int64) ->
+// xL [3][RY][FX].
+template <int R, int RY, int RXP, int NT>
+__device__ __forceinline__ void box_x4_adj(const long long *q, long long *xL, int tid) {
+    constexpr int ITEMS = 3 * RY * 8, NL = (4 + 2 * R + 1) / 2, NV = 4 + 2 * R;
+    static_assert(28 + 2 * NL <= RXP, "row too short for the vector loads");
+#pragma unroll
+    for (int j = 0; j < (ITEMS + NT - 1) / NT; ++j) {
+        const int it = tid + j * NT;
+        if (ITEMS % NT != 0 && it >= ITEMS) break;
+        const int k = it & 7, rest = it >> 3, ry = rest % RY, c = rest / RY;
+        const longlong2 *src = (const longlong2 *)(q + (c * RY + ry) * RXP + 4 * k);
+        long long v[2 * NL];
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            const longlong2 a = src[l];
+            v[2 * l] = a.x;
+            v[2 * l + 1] = a.y;
+        }
+        long long out[4];
+        slide4<R, long long>(v, out);
+        (void)NV;
+        store_ll4(xL + (c * RY + ry) * FX + 4 * k, out);
+    }
+}
+
 // ====================================================================== K1
 // Box channels: J, J^2, I J (the fixed image's S_I and var_I come
 // precomputed per level).
 template <int R, int NW, int OPT, int NSTG>
 struct K1S {
     static constexpr int NT = FX * NW, TY = NW * OPT, RX = FX + 2 * R, RY = TY + 2 * R;
-    static constexpr int NR = RX * RY, NS = 2 * R + 1, NOUT = NT * OPT;
+    static constexpr int RXP = pad4(RX), NR = RXP * RY, NS = 2 * R + 1, NOUT = NT * OPT;
     static constexpr size_t o_ring = 0;                                   // [NS][3][NOUT] int64
     static constexpr size_t o_xL = o_ring + (size_t)NS * 3 * NOUT * 8;    // [3][RY][FX] int64
     static constexpr size_t o_os = o_xL + (size_t)3 * RY * FX * 8;        // [NSTG][NOUT] int64 S_I
-    static constexpr size_t o_q = o_os + (size_t)NSTG * NOUT * 8;         // [2][NR] int32
-    static constexpr size_t o_st = o_q + (size_t)2 * NR * 4;              // [NSTG][2][NR] f32
+    static constexpr size_t o_q = o_os + (size_t)NSTG * NOUT * 8;         // [2][RY][RXP] int32
+    static constexpr size_t o_st = o_q + (size_t)2 * NR * 4;              // [NSTG][2][RY][RXP] f32
     static constexpr size_t o_ov = o_st + (size_t)NSTG * 2 * NR * 4;      // [NSTG][NOUT] f32 var_I
     static constexpr size_t bytes = o_ov + (size_t)NSTG * NOUT * 4;
 };
@@ -155,9 +292,9 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const float *__restrict__ I
                                                      int TZ, int bits, float cc_eps, int window,
                                                      int write_coef) {
     using S = K1S<R, NW, OPT, NSTG>;
-    using G = Region<S::RY, S::RX, NW>;
-    constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, NR = S::NR, NS = S::NS,
-                  NOUT = S::NOUT;
+    using G = Region<S::RY, S::RX, NW, S::RXP>;
+    constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, RXP = S::RXP, NR = S::NR,
+                  NS = S::NS, NOUT = S::NOUT;
     extern __shared__ __align__(16) unsigned char smem[];
     long long *ring = (long long *)(smem + S::o_ring);
     long long *xL = (long long *)(smem + S::o_xL);
@@ -196,8 +333,8 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const float *__restrict__ I
             const int zp = zs + i, zo = zp - R;
             const bool zok = zp >= 0 && zp < D;
             float *dst = st + (i % NSTG) * 2 * NR;
-            load_plane<1, RY, RX, NW>(dst, If, N, (long long)zp * HW, zok, rg);
-            load_plane<1, RY, RX, NW>(dst + NR, J, N, (long long)zp * HW, zok, rg);
+            load_plane<1, RY, RX, NW, RXP>(dst, If, N, (long long)zp * HW, zok, rg);
+            load_plane<1, RY, RX, NW, RXP>(dst + NR, J, N, (long long)zp * HW, zok, rg);
             if (zo >= z0 && zo < zend) {
                 const long long zoff = (long long)zo * HW;
 #pragma unroll
@@ -235,25 +372,7 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const float *__restrict__ I
                     qJ[k] = __float2int_rn(sJ[k] * scale);
                 }
             __syncthreads();
-#pragma unroll
-            for (int j = 0; j < G::NJ; ++j) {
-                const int ry = wy + NW * j;
-                if (ry >= RY) continue;
-                const int *a = qI + ry * RX + tx, *b = qJ + ry * RX + tx;
-                int s2 = 0;
-                long long s4 = 0, s5 = 0;
-#pragma unroll
-                for (int t = 0; t <= 2 * R; ++t) {
-                    const int va = a[t], vb = b[t];
-                    s2 += vb;
-                    s4 += (long long)vb * vb;
-                    s5 += (long long)va * vb;
-                }
-                long long *xo = xL + ry * FX + tx;
-                xo[0] = s2;
-                xo[RY * FX] = s4;
-                xo[2 * RY * FX] = s5;
-            }
+            box_x4_fwd<R, RY, RXP, NT>(qI, qJ, xL, tid);
             __syncthreads();
 #pragma unroll
             for (int o = 0; o < OPT; ++o) {
@@ -294,7 +413,7 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const float *__restrict__ I
                 const float varJ = diff_i128_to_float(n, acc[o][1], a2, a2) * inv_s * inv_s * inv_nf;
                 const float cross = diff_i128_to_float(n, acc[o][2], a1, a2) * inv_s * inv_s * inv_nf;
                 const float den = fmaf(varI, varJ, cc_eps);
-                const float rden = 1.0f / den;
+                const float rden = __frcp_rn(den);
                 const float cc = cross * cross * rden;
                 if (cc >= 0.0f && cc <= 2.0f)
                     qcc += (unsigned long long)__float2ull_rn(cc * 4294967296.0f);
@@ -331,7 +450,7 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const float *__restrict__ I
 template <int R, int NW, int OPT, int NSTG>
 struct K2S {
     static constexpr int NT = FX * NW, TY = NW * OPT, RX = FX + 2 * R, RY = TY + 2 * R;
-    static constexpr int NR = RX * RY, NS = 2 * R + 1, NOUT = NT * OPT;
+    static constexpr int RXP = pad4(RX), NR = RXP * RY, NS = 2 * R + 1, NOUT = NT * OPT;
     static constexpr size_t o_ring = 0;
     static constexpr size_t o_xL = o_ring + (size_t)NS * 3 * NOUT * 8;
     static constexpr size_t o_q = o_xL + (size_t)3 * RY * FX * 8;
@@ -350,9 +469,9 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_grad(const float *__restrict__ 
                                                       float *__restrict__ g, int D, int H, int W,
                                                       int TZ, int cbits) {
     using S = K2S<R, NW, OPT, NSTG>;
-    using G = Region<S::RY, S::RX, NW>;
-    constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, NR = S::NR, NS = S::NS,
-                  NOUT = S::NOUT;
+    using G = Region<S::RY, S::RX, NW, S::RXP>;
+    constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, RXP = S::RXP, NR = S::NR,
+                  NS = S::NS, NOUT = S::NOUT;
     extern __shared__ __align__(16) unsigned char smem[];
     long long *ring = (long long *)(smem + S::o_ring);
     long long *xL = (long long *)(smem + S::o_xL);
@@ -388,8 +507,8 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_grad(const float *__restrict__ 
     auto issue = [&](int i) {
         if (i < np) {
             const int zp = zs + i, zo = zp - R;
-            load_plane<4, RY, RX, NW>(st + (i % NSTG) * 4 * NR, coef, N, (long long)zp * HW,
-                                      zp >= 0 && zp < D, rg);
+            load_plane<4, RY, RX, NW, RXP>(st + (i % NSTG) * 4 * NR, coef, N, (long long)zp * HW,
+                                           zp >= 0 && zp < D, rg);
             if (zo >= z0 && zo < zend) {
                 float *o = ost + (i % NSTG) * 4 * NOUT;
                 load_outs<3, OPT, NOUT>(o, u, N, (long long)zo * HW, ou, tid, NT);
@@ -433,19 +552,7 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_grad(const float *__restrict__ 
                     q[2 * NR + k] = quantize(s[2 * NR + k], qs[2]) + quantize(s[3 * NR + k], qs[2]);
                 }
             __syncthreads();
-#pragma unroll
-            for (int j = 0; j < G::NJ; ++j) {
-                const int ry = wy + NW * j;
-                if (ry >= RY) continue;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const long long *src = q + c * NR + ry * RX + tx;
-                    long long sum = 0;
-#pragma unroll
-                    for (int t = 0; t <= 2 * R; ++t) sum += src[t];
-                    xL[c * RY * FX + ry * FX + tx] = sum;
-                }
-            }
+            box_x4_adj<R, RY, RXP, NT>(q, xL, tid);
             __syncthreads();
 #pragma unroll
             for (int o = 0; o < OPT; ++o) {
@@ -522,24 +629,11 @@ __global__ void __launch_bounds__(256) k_fused_mse_grad(const float *__restrict_
 }
 
 // ====================================================== separable Gaussian
-// x pass of a [3][RY][RX] plane onto [3][RY][FX] and this thread's y pass.
-template <int RG, int RY, int RX, int NW, int OPT>
+// x pass of a [3][RY][RXP] plane onto [3][RY][FX] and this thread's y pass.
+template <int RG, int RY, int RXP, int NW, int OPT>
 __device__ __forceinline__ void gauss_xy(const float *pl, float *xb, const GaussTaps &t, int wy,
                                          int tx, float Q[OPT][3]) {
-    constexpr int NJ = (RY + NW - 1) / NW;
-#pragma unroll
-    for (int j = 0; j < NJ; ++j) {
-        const int ry = wy + NW * j;
-        if (ry >= RY) continue;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float *src = pl + c * RY * RX + ry * RX + tx;
-            float s = 0.0f;
-#pragma unroll
-            for (int k = 0; k <= 2 * RG; ++k) s = fmaf(t.w[k], src[k], s);
-            xb[c * RY * FX + ry * FX + tx] = s;
-        }
-    }
+    gauss_x4<RG, 3, RY, RXP, FX * NW>(pl, xb, t, wy * FX + tx);
     __syncthreads();
 #pragma unroll
     for (int o = 0; o < OPT; ++o) {
@@ -582,7 +676,7 @@ __device__ __forceinline__ float gauss_z(const float *win, const GaussTaps &t, i
 template <int RG, int NW, int OPT, int NSTG>
 struct K3S {
     static constexpr int NT = FX * NW, TY = NW * OPT, RX = FX + 2 * RG, RY = TY + 2 * RG;
-    static constexpr int NR = RX * RY, NS = 2 * RG + 1, NOUT = NT * OPT;
+    static constexpr int RXP = pad4(RX), NR = RXP * RY, NS = 2 * RG + 1, NOUT = NT * OPT;
     static constexpr size_t o_ring = 0;
     static constexpr size_t o_xb = o_ring + (size_t)2 * NS * 3 * NOUT * 4;
     static constexpr size_t o_st = o_xb + (size_t)3 * RY * FX * 4;
@@ -599,9 +693,9 @@ __global__ void __launch_bounds__(FX *NW) k_smooth_adam(const float *__restrict_
                                                         int W, int TZ, GaussTaps t, AdamConsts ac,
                                                         int parity) {
     using S = K3S<RG, NW, OPT, NSTG>;
-    using G = Region<S::RY, S::RX, NW>;
-    constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, NR = S::NR, NS = S::NS,
-                  NOUT = S::NOUT;
+    using G = Region<S::RY, S::RX, NW, S::RXP>;
+    constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, RXP = S::RXP, NR = S::NR,
+                  NS = S::NS, NOUT = S::NOUT;
     extern __shared__ __align__(16) unsigned char smem[];
     float *ring = (float *)(smem + S::o_ring);
     float *xb = (float *)(smem + S::o_xb);
@@ -623,8 +717,8 @@ __global__ void __launch_bounds__(FX *NW) k_smooth_adam(const float *__restrict_
     auto issue = [&](int i) {
         if (i < np) {
             const int zp = zs + i, zo = zp - RG;
-            load_plane<3, RY, RX, NW>(st + (i % NSTG) * 3 * NR, g, N, (long long)zp * HW,
-                                      zp >= 0 && zp < D, rg);
+            load_plane<3, RY, RX, NW, RXP>(st + (i % NSTG) * 3 * NR, g, N, (long long)zp * HW,
+                                           zp >= 0 && zp < D, rg);
             if (zo >= z0 && zo < zend) {
                 float *o = mvs + (i % NSTG) * 6 * NOUT;
                 load_outs<3, OPT, NOUT>(o, m, N, (long long)zo * HW, ou, tid, NT);
@@ -646,7 +740,7 @@ __global__ void __launch_bounds__(FX *NW) k_smooth_adam(const float *__restrict_
         float Q[OPT][3];
         if (zp >= 0 && zp < D) {
             __syncthreads();  // the x pass reads neighbours' copies
-            gauss_xy<RG, RY, RX, NW, OPT>(st + (i % NSTG) * 3 * NR, xb, t, wy, tx, Q);
+            gauss_xy<RG, RY, RXP, NW, OPT>(st + (i % NSTG) * 3 * NR, xb, t, wy, tx, Q);
         } else {
 #pragma unroll
             for (int o = 0; o < OPT; ++o) Q[o][0] = Q[o][1] = Q[o][2] = 0.0f;
@@ -670,7 +764,7 @@ __global__ void __launch_bounds__(FX *NW) k_smooth_adam(const float *__restrict_
                         fmaf(ac.b2, mv[(3 + c) * NOUT + o * NT], (1.0f - ac.b2) * s * s);
                     m[c * N + gi] = mvv;
                     v[c * N + gi] = vvv;
-                    const float dv = (mvv * ac.rbc1) / (sqrtf(vvv * ac.rbc2) + ac.eps);
+                    const float dv = adam_dir(mvv, vvv, ac.rbc1, ac.rbc2, ac.eps);
                     dir[c * N + gi] = dv;
                     nrm2 = fmaf(dv, dv, nrm2);
                 }
@@ -692,9 +786,10 @@ __global__ void __launch_bounds__(FX *NW) k_smooth_adam(const float *__restrict_
 template <int RG, int NW, int OPT, bool SU, int NSTG>
 struct K4S {
     static constexpr int NT = FX * NW, TY = NW * OPT, RX = FX + 2 * RG, RY = TY + 2 * RG;
-    static constexpr int NR = RX * RY, NS = 2 * RG + 1, NOUT = NT * OPT;
+    static constexpr int RXP = pad4(RX), NR = RXP * RY, NS = 2 * RG + 1, NOUT = NT * OPT;
     // u planes z-1, z, z+1 in use plus NSTG - 1 in flight
-    static constexpr int URX = RX + 2, URY = RY + 2, NRU = URX * URY, NSU = NSTG + 2;
+    static constexpr int URX = RX + 2, URY = RY + 2, URXP = pad4(URX), NRU = URXP * URY,
+                         NSU = NSTG + 2;
     static constexpr size_t o_ring = 0;
     static constexpr size_t o_xb = o_ring + (size_t)2 * NS * 3 * NOUT * 4;
     static constexpr size_t o_up = o_xb + (size_t)3 * RY * FX * 4;
@@ -713,10 +808,11 @@ __global__ void __launch_bounds__(FX *NW) k_compose(const float *__restrict__ u,
                                                     int TZ, GaussTaps t, float lr, float c_lp,
                                                     int parity) {
     using S = K4S<RG, NW, OPT, SU, NSTG>;
-    using G = Region<S::RY, S::RX, NW>;
-    using GU = Region<S::URY, S::URX, NW>;
-    constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, NR = S::NR, NS = S::NS,
-                  NOUT = S::NOUT, URX = S::URX, URY = S::URY, NRU = S::NRU, NSU = S::NSU;
+    using G = Region<S::RY, S::RX, NW, S::RXP>;
+    using GU = Region<S::URY, S::URX, NW, S::URXP>;
+    constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, RXP = S::RXP, NR = S::NR,
+                  NS = S::NS, NOUT = S::NOUT, URX = S::URX, URY = S::URY, URXP = S::URXP,
+                  NRU = S::NRU, NSU = S::NSU;
     extern __shared__ __align__(16) unsigned char smem[];
     float *ring = (float *)(smem + S::o_ring);
     float *xb = (float *)(smem + S::o_xb);
@@ -741,14 +837,14 @@ __global__ void __launch_bounds__(FX *NW) k_compose(const float *__restrict__ u,
     const int zs = z0 - RG, np = zend - z0 + 2 * RG;
     // u plane q lives in stage (q - (zs - 1)) % NSU
     auto issue_u = [&](int q) {
-        load_plane<3, URY, URX, NW>(ust + ((q - (zs - 1)) % NSU) * 3 * NRU, u, N,
-                                    (long long)q * HW, q >= 0 && q < D, rgu);
+        load_plane<3, URY, URX, NW, URXP>(ust + ((q - (zs - 1)) % NSU) * 3 * NRU, u, N,
+                                          (long long)q * HW, q >= 0 && q < D, rgu);
     };
     auto issue = [&](int i) {
         if (i < np) {
             const int zp = zs + i;
-            load_plane<3, RY, RX, NW>(dst + (i % NSTG) * 3 * NR, dir, N, (long long)zp * HW,
-                                      zp >= 0 && zp < D, rg);
+            load_plane<3, RY, RX, NW, RXP>(dst + (i % NSTG) * 3 * NR, dir, N,
+                                           (long long)zp * HW, zp >= 0 && zp < D, rg);
             if (SU) issue_u(zp + 1);
         }
         cp_commit();
@@ -797,15 +893,15 @@ __global__ void __launch_bounds__(FX *NW) k_compose(const float *__restrict__ u,
                                 const float *pa = fz < 0.0f ? um : u0;
                                 const float *pb = fz < 0.0f ? u0 : u1;
                                 const int ry = wy + NW * j, rx = tx + 32 * cc;
-                                const int b0 = (ry + 1 + (int)fy) * URX + (rx + 1 + (int)fx);
+                                const int b0 = (ry + 1 + (int)fy) * URXP + (rx + 1 + (int)fx);
                                 float r[3];
 #pragma unroll
                                 for (int ch = 0; ch < 3; ++ch) {
                                     const float *A = pa + ch * NRU + b0, *B = pb + ch * NRU + b0;
                                     const float c00 = fmaf(tx2, A[1] - A[0], A[0]);
-                                    const float c01 = fmaf(tx2, A[URX + 1] - A[URX], A[URX]);
+                                    const float c01 = fmaf(tx2, A[URXP + 1] - A[URXP], A[URXP]);
                                     const float c10 = fmaf(tx2, B[1] - B[0], B[0]);
-                                    const float c11 = fmaf(tx2, B[URX + 1] - B[URX], B[URX]);
+                                    const float c11 = fmaf(tx2, B[URXP + 1] - B[URXP], B[URXP]);
                                     const float c0 = fmaf(ty, c01 - c00, c00);
                                     const float c1 = fmaf(ty, c11 - c10, c10);
                                     r[ch] = fmaf(tz, c1 - c0, c0);
@@ -831,7 +927,7 @@ __global__ void __launch_bounds__(FX *NW) k_compose(const float *__restrict__ u,
                     up[2 * NR + k] = c;
                 }
             __syncthreads();
-            gauss_xy<RG, RY, RX, NW, OPT>(up, xb, t, wy, tx, Q);
+            gauss_xy<RG, RY, RXP, NW, OPT>(up, xb, t, wy, tx, Q);
         } else {
 #pragma unroll
             for (int o = 0; o < OPT; ++o) Q[o][0] = Q[o][1] = Q[o][2] = 0.0f;

@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(256) k_lncc_coef(const long long *__restrict__
         float varJ = diff_i128_to_float(n, sJJ, sJ, sJ) * inv_s * inv_s * inv_nf;
         float cross = diff_i128_to_float(n, sIJ, sI, sJ) * inv_s * inv_s * inv_nf;
         float den = fmaf(varI, varJ, cc_eps);
-        float rden = 1.0f / den;
+        float rden = __frcp_rn(den);
         float cc = cross * cross * rden;
         A = 2.0f * cross * rden;
         B = -cc * varI * rden;
