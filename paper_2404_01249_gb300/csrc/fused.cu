@@ -2,8 +2,10 @@
 //
 // One iteration of Algorithm 1 (Jacobian-free direction) is four launches:
 //   K1 k_lncc_fwd       LNCC forward on J = I_m o phi: exact int64 window
-//                       sums, cc, the adjoint coefficients A, B, C, the loss
-//                       accumulator and the coefficient maxima.
+//                       sums of J, J^2 and I J (the fixed image's window sum
+//                       and variance come precomputed per level), cc, the
+//                       adjoint coefficients A, B, C, the loss accumulator and
+//                       the coefficient maxima.
 //   K2 k_lncc_grad      adjoint window sums of A, B, C; J and grad I_m o phi
 //                       at the output voxel; g = dL/dJ grad.
 //   K3 k_smooth_adam    Gaussian(sigma_grad) of g, Adam update of m, nu, the
@@ -16,18 +18,24 @@
 // without recomputing a much wider halo.
 //
 // Every kernel marches along z ("2.5-D" tiling): a CTA owns a 32 x TY tile of
-// (x, y) columns and a slab of TZ output planes.  Plane inputs (tile plus
-// halo) arrive through a three-stage cp.async pipeline two planes ahead of
-// the plane being reduced; the plane is reduced along x and then y in shared
-// memory, and the last 2R + 1 in-plane results per output column sit in a
-// shared-memory ring from which the z-reduction reads.  No intermediate of
-// the separable sums goes to HBM; halo re-reads hit L2.
+// (x, y) columns and a slab of TZ output planes.  A plane's inputs (the tile
+// plus its halo, and the operands of the plane's outputs) arrive NSTG - 1
+// planes ahead of use.  When the grid width is a multiple of 4 they come as
+// TMA tile copies issued by one thread and completed on an mbarrier (zero
+// fill outside the grid); otherwise each thread copies its own positions with
+// cp.async.  A plane is reduced along x (register-blocked, 16-byte shared
+// loads) and then y in shared memory; the last 2R + 1 in-plane results per
+// output column sit in a shared-memory ring from which the z reduction reads.
+// No intermediate of the separable sums goes to HBM; halo re-reads hit L2.
 //
-// Thread layout: warp w of NW covers region rows w, w + NW, ...; lane l
-// covers columns l and l + 32.  All trip counts are compile-time, the
-// in-plane offsets of a thread's positions are computed once per CTA, and a
-// thread consumes exactly the stage positions it copied itself wherever
-// possible, so those reads need no barrier.
+// Shared plane layout: [C][RY][BXW] with BXW = 32 + 2 XB and XB = R rounded
+// up to a multiple of 4.  Column c holds x = x0 - XB + c and row r holds
+// y = y0 - R + r, so that a TMA box starts on a 16-byte boundary.
+//
+// Every wait on a TMA barrier is bounded; a wait that gives up sets
+// ST_TIMEOUT in the status word, waits (bounded again) for the CTA's copies
+// in flight and ends the CTA, and later CTAs that see the bit return at once.
+#include <cuda.h>
 #include <math.h>
 
 #include <mutex>
@@ -41,15 +49,21 @@ namespace {
 
 constexpr int FX = 32;  // tile width along x (one warp)
 
-__device__ __forceinline__ void cp4(void *dst, const float *src, bool ok) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src),
+__host__ __device__ constexpr int halo4(int r) { return (r + 3) / 4 * 4; }
+__host__ __device__ constexpr size_t al128(size_t b) { return (b + 127) & ~size_t(127); }
+
+__device__ __forceinline__ unsigned su32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// ----------------------------------------------------------- cp.async path
+__device__ __forceinline__ void cp4(void *dst, const void *src, bool ok) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(su32(dst)), "l"(src),
                  "r"(ok ? 4 : 0)
                  : "memory");
 }
 __device__ __forceinline__ void cp8(void *dst, const void *src, bool ok) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src),
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(su32(dst)), "l"(src),
                  "r"(ok ? 8 : 0)
                  : "memory");
 }
@@ -59,22 +73,76 @@ __device__ __forceinline__ void cp_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Row stride of an RX-wide shared region: a multiple of 4 elements, so that
-// 16-byte vector loads of a row start aligned.
-constexpr int pad4(int x) { return (x + 3) & ~3; }
+// ---------------------------------------------------------------- TMA path
+__device__ __forceinline__ void mbar_init(unsigned long long *b) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(b)) : "memory");
+}
+// Makes initialised barriers visible to the TMA unit.
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// The arrival of the one expected thread, announcing `bytes` of copies.
+__device__ __forceinline__ void mbar_expect(unsigned long long *b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(su32(b)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned long long *b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Waits for the phase of parity `parity` to complete; gives up after about
+// 2^28 SM cycles (0.13 s at 2 GHz; a tile copy takes microseconds).
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity) {
+    if (mbar_try(b, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try(b, parity))
+        if (clock64() - t0 > (1ll << 28)) return false;
+    return true;
+}
+// One tile copy of a rank-4 map ([C][D][H][W]) into shared memory.
+__device__ __forceinline__ void tma4(void *dst, const CUtensorMap *m, int x, int y, int z, int c,
+                                     unsigned long long *b) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(su32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(m)), "r"(x), "r"(y), "r"(z), "r"(c),
+        "r"(su32(b))
+        : "memory");
+}
 
-// A thread's positions in an RY x RX region (RX <= 64) stored with row
-// stride RXP.
-template <int RY, int RX, int NW, int RXP = pad4(RX)>
+// Tensor maps of one launch (the ones a kernel does not use stay zero).
+struct alignas(64) Maps {
+    CUtensorMap a, b, c, d;
+};
+
+// Uniform early exit of a CTA when an earlier CTA reported a timeout.
+__device__ __forceinline__ bool timed_out(const WsHeader *h, int tid, int *flag) {
+    if (tid == 0) *flag = (int)(*(volatile const unsigned *)&h->status & ST_TIMEOUT);
+    __syncthreads();
+    return *flag != 0;
+}
+
+// --------------------------------------------- cp.async position mapping
+// A thread's positions in the RY x RX logical region of a plane (RX <= 64):
+// warp w covers rows w, w + NW, ...; lane l covers columns l and l + 32.
+// Logical column rx is stored at column rx + COFF of a BXW-wide row.
+template <int RY, int RX, int NW, int BXW, int COFF>
 struct Region {
-    static constexpr int NJ = (RY + NW - 1) / NW;  // row slots
-    static constexpr int NC = (RX + 31) / 32;      // column slots
-    static constexpr int NP = NJ * NC;
-    int off[NP];  // y W + x inside the grid, -1 outside the grid, -2 outside the region
-    int sbase;    // shared index of slot (0, 0): wy RXP + tx
-
+    static constexpr int NJ = (RY + NW - 1) / NW;
+    static constexpr int NC = (RX + 31) / 32;
+    int off[NJ * NC];  // y W + x inside the grid, -1 outside the grid, -2 outside the region
+    int sbase;
     __device__ __forceinline__ void init(int wy, int tx, int ybase, int xbase, int H, int W) {
-        sbase = wy * RXP + tx;
+        sbase = wy * BXW + tx + COFF;
 #pragma unroll
         for (int j = 0; j < NJ; ++j)
 #pragma unroll
@@ -86,69 +154,73 @@ struct Region {
                 off[j * NC + c] = o;
             }
     }
-    static __device__ __forceinline__ int sofs(int j, int c) { return NW * j * RXP + 32 * c; }
+    static __device__ __forceinline__ int sofs(int j, int c) { return NW * j * BXW + 32 * c; }
+    // C channels of plane zoff / W H (zero outside the grid) -> [C][RY][BXW]
+    template <int C>
+    __device__ __forceinline__ void load(float *dst, const float *src, long long N, long long zoff,
+                                         bool zok) const {
+#pragma unroll
+        for (int j = 0; j < NJ; ++j)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int o = off[j * NC + c];
+                if (o == -2) continue;
+                const bool ok = zok && o >= 0;
+                const float *s = src + (ok ? zoff + o : 0);
+                float *d = dst + sbase + sofs(j, c);
+#pragma unroll
+                for (int ch = 0; ch < C; ++ch) cp4(d + ch * RY * BXW, s + ch * N, ok);
+            }
+    }
 };
 
-// Copies C channels of plane zp onto [C][RY][RXP] shared floats (zero outside).
-template <int C, int RY, int RX, int NW, int RXP>
-__device__ __forceinline__ void load_plane(float *dst, const float *src, long long N,
-                                           long long zoff, bool zok,
-                                           const Region<RY, RX, NW, RXP> &rg) {
-    using G = Region<RY, RX, NW, RXP>;
-#pragma unroll
-    for (int j = 0; j < G::NJ; ++j)
-#pragma unroll
-        for (int c = 0; c < G::NC; ++c) {
-            const int o = rg.off[j * G::NC + c];
-            if (o == -2) continue;
-            const bool ok = zok && o >= 0;
-            const float *s = src + (ok ? zoff + o : 0);
-            float *d = dst + rg.sbase + G::sofs(j, c);
-#pragma unroll
-            for (int ch = 0; ch < C; ++ch) cp4(d + ch * RY * RXP, s + ch * N, ok);
-        }
-}
-
-// A thread's OPT output voxels of the 32 x TY tile.
-template <int OPT>
+// This thread's OPT output voxels; its slot o of a [C][TY][32] output tile is
+// o NT + tid (the layout a {32, TY, 1, C} TMA box lands in).
+template <int OPT, int NW>
 struct Outs {
+    static constexpr int NT = 32 * NW, NOUT = OPT * NT;
     int off[OPT];  // y W + x, -1 outside the grid
-    __device__ __forceinline__ void init(int wy, int tx, int y0, int x0, int NW, int H, int W) {
+    __device__ __forceinline__ void init(int wy, int tx, int y0, int x0, int H, int W) {
 #pragma unroll
         for (int o = 0; o < OPT; ++o) {
             const int y = y0 + wy + NW * o, x = x0 + tx;
             off[o] = (y < H && x < W) ? y * W + x : -1;
         }
     }
-};
-
-template <int C, int OPT, int NOUT>
-__device__ __forceinline__ void load_outs(float *dst, const float *src, long long N,
-                                          long long zoff, const Outs<OPT> &ou, int tid, int NT) {
+    template <int C, class T>
+    __device__ __forceinline__ void load(T *dst, const T *src, long long N, long long zoff,
+                                         int tid) const {
 #pragma unroll
-    for (int o = 0; o < OPT; ++o) {
-        const bool ok = ou.off[o] >= 0;
-        const float *s = src + (ok ? zoff + ou.off[o] : 0);
+        for (int o = 0; o < OPT; ++o) {
+            const bool ok = off[o] >= 0;
+            const T *s = src + (ok ? zoff + off[o] : 0);
 #pragma unroll
-        for (int ch = 0; ch < C; ++ch) cp4(dst + ch * NOUT + o * NT + tid, s + ch * N, ok);
+            for (int ch = 0; ch < C; ++ch) {
+                if (sizeof(T) == 8)
+                    cp8(dst + ch * NOUT + o * NT + tid, s + ch * N, ok);
+                else
+                    cp4(dst + ch * NOUT + o * NT + tid, s + ch * N, ok);
+            }
+        }
     }
-}
+};
 
 // ------------------------------------------------- register-blocked x passes
 // A work item is (channel, row, group of 4 adjacent output columns); items
-// are spread over all threads.  Rows are read with 16-byte shared loads.
+// are spread over all threads.  The taps of output column ox start at plane
+// column ox + COFF; rows are read with 16-byte shared loads from column 4k.
 
-// Gaussian x pass: pl [C][RY][RXP] -> xb [C][RY][FX].
-template <int RG, int C, int RY, int RXP, int NT>
+// Gaussian x pass: pl [C][RY][BXW] -> xb [C][RY][FX].
+template <int RG, int C, int RY, int BXW, int COFF, int NT>
 __device__ __forceinline__ void gauss_x4(const float *pl, float *xb, const GaussTaps &t, int tid) {
-    constexpr int ITEMS = C * RY * 8, NL = (4 + 2 * RG + 3) / 4;
-    static_assert(28 + 4 * NL <= RXP, "row too short for the vector loads");
+    constexpr int ITEMS = C * RY * 8, NL = (4 + COFF + 2 * RG + 3) / 4;
+    static_assert(28 + 4 * NL <= BXW, "row too short for the vector loads");
 #pragma unroll
     for (int j = 0; j < (ITEMS + NT - 1) / NT; ++j) {
         const int it = tid + j * NT;
         if (ITEMS % NT != 0 && it >= ITEMS) break;
         const int k = it & 7, rest = it >> 3, ry = rest % RY, c = rest / RY;
-        const float4 *src = (const float4 *)(pl + (c * RY + ry) * RXP + 4 * k);
+        const float4 *src = (const float4 *)(pl + (c * RY + ry) * BXW + 4 * k);
         float v[4 * NL];
 #pragma unroll
         for (int l = 0; l < NL; ++l) {
@@ -163,7 +235,7 @@ __device__ __forceinline__ void gauss_x4(const float *pl, float *xb, const Gauss
         for (int jj = 0; jj < 4; ++jj) {
             float a = 0.0f;
 #pragma unroll
-            for (int tt = 0; tt <= 2 * RG; ++tt) a = fmaf(t.w[tt], v[jj + tt], a);
+            for (int tt = 0; tt <= 2 * RG; ++tt) a = fmaf(t.w[tt], v[jj + COFF + tt], a);
             o[jj] = a;
         }
         *(float4 *)(xb + (c * RY + ry) * FX + 4 * k) = make_float4(o[0], o[1], o[2], o[3]);
@@ -189,19 +261,19 @@ __device__ __forceinline__ void store_ll4(long long *d, const long long s[4]) {
     ((longlong2 *)d)[1] = make_longlong2(s[2], s[3]);
 }
 
-// LNCC forward x pass on quantised planes qI, qJ [RY][RXP] (int32) ->
+// LNCC forward x pass on quantised planes qI, qJ [RY][BXW] (int32) ->
 // xL [3][RY][FX] int64: channel 0 sum J, 1 sum J^2, 2 sum I J.
-template <int R, int RY, int RXP, int NT>
+template <int R, int RY, int BXW, int COFF, int NT>
 __device__ __forceinline__ void box_x4_fwd(const int *qI, const int *qJ, long long *xL, int tid) {
-    constexpr int ITEMS = 3 * RY * 8, NL = (4 + 2 * R + 3) / 4, NV = 4 + 2 * R;
-    static_assert(28 + 4 * NL <= RXP, "row too short for the vector loads");
+    constexpr int ITEMS = 3 * RY * 8, NL = (4 + COFF + 2 * R + 3) / 4, NV = 4 + 2 * R;
+    static_assert(28 + 4 * NL <= BXW, "row too short for the vector loads");
 #pragma unroll
     for (int j = 0; j < (ITEMS + NT - 1) / NT; ++j) {
         const int it = tid + j * NT;
         if (ITEMS % NT != 0 && it >= ITEMS) break;
         const int k = it & 7, rest = it >> 3, ry = rest % RY, c = rest / RY;
         int vj[4 * NL], vi[4 * NL];
-        const int4 *sj = (const int4 *)(qJ + ry * RXP + 4 * k);
+        const int4 *sj = (const int4 *)(qJ + ry * BXW + 4 * k);
 #pragma unroll
         for (int l = 0; l < NL; ++l) {
             const int4 q = sj[l];
@@ -213,12 +285,12 @@ __device__ __forceinline__ void box_x4_fwd(const int *qI, const int *qJ, long lo
         long long out[4];
         if (c == 0) {
             int s4[4];
-            slide4<R, int>(vj, s4);
+            slide4<R, int>(vj + COFF, s4);
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj) out[jj] = s4[jj];
         } else {
             if (c == 2) {
-                const int4 *si = (const int4 *)(qI + ry * RXP + 4 * k);
+                const int4 *si = (const int4 *)(qI + ry * BXW + 4 * k);
 #pragma unroll
                 for (int l = 0; l < NL; ++l) {
                     const int4 q = si[l];
@@ -233,25 +305,25 @@ __device__ __forceinline__ void box_x4_fwd(const int *qI, const int *qJ, long lo
             }
             long long pr[NV];
 #pragma unroll
-            for (int t = 0; t < NV; ++t) pr[t] = (long long)vi[t] * vj[t];
+            for (int tt = 0; tt < NV; ++tt) pr[tt] = (long long)vi[tt + COFF] * vj[tt + COFF];
             slide4<R, long long>(pr, out);
         }
         store_ll4(xL + (c * RY + ry) * FX + 4 * k, out);
     }
 }
 
-// LNCC adjoint x pass on quantised coefficients q [3][RY][RXP] (int64) ->
+// LNCC adjoint x pass on quantised coefficients q [3][RY][BXW] (int64) ->
 // xL [3][RY][FX].
-template <int R, int RY, int RXP, int NT>
+template <int R, int RY, int BXW, int COFF, int NT>
 __device__ __forceinline__ void box_x4_adj(const long long *q, long long *xL, int tid) {
-    constexpr int ITEMS = 3 * RY * 8, NL = (4 + 2 * R + 1) / 2, NV = 4 + 2 * R;
-    static_assert(28 + 2 * NL <= RXP, "row too short for the vector loads");
+    constexpr int ITEMS = 3 * RY * 8, NL = (4 + COFF + 2 * R + 1) / 2;
+    static_assert(28 + 2 * NL <= BXW, "row too short for the vector loads");
 #pragma unroll
     for (int j = 0; j < (ITEMS + NT - 1) / NT; ++j) {
         const int it = tid + j * NT;
         if (ITEMS % NT != 0 && it >= ITEMS) break;
         const int k = it & 7, rest = it >> 3, ry = rest % RY, c = rest / RY;
-        const longlong2 *src = (const longlong2 *)(q + (c * RY + ry) * RXP + 4 * k);
+        const longlong2 *src = (const longlong2 *)(q + (c * RY + ry) * BXW + 4 * k);
         long long v[2 * NL];
 #pragma unroll
         for (int l = 0; l < NL; ++l) {
@@ -260,30 +332,111 @@ __device__ __forceinline__ void box_x4_adj(const long long *q, long long *xL, in
             v[2 * l + 1] = a.y;
         }
         long long out[4];
-        slide4<R, long long>(v, out);
-        (void)NV;
+        slide4<R, long long>(v + COFF, out);
         store_ll4(xL + (c * RY + ry) * FX + 4 * k, out);
     }
 }
 
+// y pass of this thread's outputs from xL [C][RY][FX].
+template <int R, int RY, int NW, int OPT>
+__device__ __forceinline__ void box_y3(const long long *xL, int wy, int tx, long long P[OPT][3]) {
+#pragma unroll
+    for (int o = 0; o < OPT; ++o) {
+        const long long *xi = xL + (wy + NW * o) * FX + tx;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            long long sum = 0;
+#pragma unroll
+            for (int t = 0; t <= 2 * R; ++t) sum += xi[c * RY * FX + t * FX];
+            P[o][c] = sum;
+        }
+    }
+}
+
+template <int RG, int RY, int NW, int OPT>
+__device__ __forceinline__ void gauss_y3(const float *xb, const GaussTaps &t, int wy, int tx,
+                                         float Q[OPT][3]) {
+#pragma unroll
+    for (int o = 0; o < OPT; ++o) {
+        const float *xi = xb + (wy + NW * o) * FX + tx;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float s = 0.0f;
+#pragma unroll
+            for (int k = 0; k <= 2 * RG; ++k) s = fmaf(t.w[k], xi[c * RY * FX + k * FX], s);
+            Q[o][c] = s;
+        }
+    }
+}
+
+// Running z window sums: ring of the last NS plane results per output.
+template <int NS, int OPT, int NOUT, int NT>
+__device__ __forceinline__ void zslide(long long *ring, int slot, int tid,
+                                       const long long P[OPT][3], long long acc[OPT][3]) {
+    long long *rb = ring + slot * 3 * NOUT + tid;
+#pragma unroll
+    for (int o = 0; o < OPT; ++o)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            long long *r = rb + c * NOUT + o * NT;
+            acc[o][c] += P[o][c] - *r;
+            *r = P[o][c];
+        }
+}
+
+// Ring of the last NS in-plane results, every slot stored twice (k, k + NS)
+// so that the z window is contiguous.  Returns the first slot of the window
+// (oldest plane first).
+template <int NS, int OPT, int NOUT, int NT>
+__device__ __forceinline__ int ring_push(float *ring, int slot, int tid, const float Q[OPT][3]) {
+#pragma unroll
+    for (int o = 0; o < OPT; ++o)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float v = Q[o][c];
+            ring[(slot * 3 + c) * NOUT + o * NT + tid] = v;
+            ring[((slot + NS) * 3 + c) * NOUT + o * NT + tid] = v;
+        }
+    return slot + 1;
+}
+
+template <int RG, int NOUT>
+__device__ __forceinline__ float gauss_z(const float *win, const GaussTaps &t, int c) {
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k <= 2 * RG; ++k) s = fmaf(t.w[k], win[(k * 3 + c) * NOUT], s);
+    return s;
+}
+
+// Bounded wait, by thread 0, for the copies of planes i .. i + NSTG - 1 that
+// may still be in flight when a CTA stops early.
+template <int NSTG>
+__device__ __forceinline__ void drain(unsigned long long *bar, int i, int np) {
+    for (int j = i; j < i + NSTG && j < np; ++j) mbar_wait(bar + j % NSTG, (unsigned)(j / NSTG) & 1u);
+}
+
 // ====================================================================== K1
-// Box channels: J, J^2, I J (the fixed image's S_I and var_I come
-// precomputed per level).
 template <int R, int NW, int OPT, int NSTG>
 struct K1S {
     static constexpr int NT = FX * NW, TY = NW * OPT, RX = FX + 2 * R, RY = TY + 2 * R;
-    static constexpr int RXP = pad4(RX), NR = RXP * RY, NS = 2 * R + 1, NOUT = NT * OPT;
-    static constexpr size_t o_ring = 0;                                   // [NS][3][NOUT] int64
-    static constexpr size_t o_xL = o_ring + (size_t)NS * 3 * NOUT * 8;    // [3][RY][FX] int64
-    static constexpr size_t o_os = o_xL + (size_t)3 * RY * FX * 8;        // [NSTG][NOUT] int64 S_I
-    static constexpr size_t o_q = o_os + (size_t)NSTG * NOUT * 8;         // [2][RY][RXP] int32
-    static constexpr size_t o_st = o_q + (size_t)2 * NR * 4;              // [NSTG][2][RY][RXP] f32
-    static constexpr size_t o_ov = o_st + (size_t)NSTG * 2 * NR * 4;      // [NSTG][NOUT] f32 var_I
-    static constexpr size_t bytes = o_ov + (size_t)NSTG * NOUT * 4;
+    static constexpr int XB = halo4(R), BXW = FX + 2 * XB, COFF = XB - R;
+    static constexpr int NR = BXW * RY, NS = 2 * R + 1, NOUT = NT * OPT;
+    static constexpr size_t plane = al128((size_t)NR * 4);  // I_f plane, then J plane
+    static constexpr size_t st_bytes = 2 * plane;
+    static constexpr size_t ost_bytes = al128((size_t)NOUT * 12);  // S_I (int64), var_I
+    static constexpr unsigned tx_plane = 2u * NR * 4, tx_out = NOUT * 12u;
+    static constexpr size_t o_st = 0;
+    static constexpr size_t o_ost = o_st + st_bytes * NSTG;
+    static constexpr size_t o_ring = o_ost + ost_bytes * NSTG;           // [NS][3][NOUT] int64
+    static constexpr size_t o_xL = o_ring + (size_t)NS * 3 * NOUT * 8;   // [3][RY][FX] int64
+    static constexpr size_t o_q = o_xL + (size_t)3 * RY * FX * 8;        // [2][RY][BXW] int32
+    static constexpr size_t o_bar = al128(o_q + (size_t)2 * NR * 4);
+    static constexpr size_t bytes = o_bar + 8 * NSTG;
 };
 
-template <int R, int NW, int OPT, int NSTG>
-__global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const float *__restrict__ If,
+template <int R, int NW, int OPT, int NSTG, bool TMA>
+__global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const __grid_constant__ Maps maps,
+                                                     const float *__restrict__ If,
                                                      const float *__restrict__ J,
                                                      const long long *__restrict__ SIg,
                                                      const float *__restrict__ varIg,
@@ -292,18 +445,20 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const float *__restrict__ I
                                                      int TZ, int bits, float cc_eps, int window,
                                                      int write_coef) {
     using S = K1S<R, NW, OPT, NSTG>;
-    using G = Region<S::RY, S::RX, NW, S::RXP>;
-    constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, RXP = S::RXP, NR = S::NR,
-                  NS = S::NS, NOUT = S::NOUT;
-    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, BXW = S::BXW, COFF = S::COFF,
+                  XB = S::XB, NR = S::NR, NS = S::NS, NOUT = S::NOUT;
+    constexpr int CS = (int)(S::plane / 4);
+    using G = Region<RY, RX, NW, BXW, COFF>;
+    extern __shared__ __align__(128) unsigned char smem[];
     long long *ring = (long long *)(smem + S::o_ring);
     long long *xL = (long long *)(smem + S::o_xL);
-    long long *os = (long long *)(smem + S::o_os);
     int *qI = (int *)(smem + S::o_q), *qJ = qI + NR;
-    float *st = (float *)(smem + S::o_st);
-    float *ov = (float *)(smem + S::o_ov);
+    unsigned long long *bar = (unsigned long long *)(smem + S::o_bar);
     __shared__ float redf[32];
     __shared__ unsigned long long redu[32];
+    __shared__ int flag;
+    auto stage = [&](int s) { return (float *)(smem + S::o_st + S::st_bytes * s); };
+    auto ostage = [&](int s) { return (long long *)(smem + S::o_ost + S::ost_bytes * s); };
 
     const int tx = threadIdx.x, wy = threadIdx.y, tid = wy * FX + tx;
     const int x0 = blockIdx.x * FX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
@@ -316,11 +471,16 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const float *__restrict__ I
     const long long n = (long long)window * window * window;
     const float nf = (float)n, inv_nf = 1.0f / nf;
     G rg;
-    rg.init(wy, tx, y0 - R, x0 - R, H, W);
-    Outs<OPT> ou;
-    ou.init(wy, tx, y0, x0, NW, H, W);
-
+    if (!TMA) rg.init(wy, tx, y0 - R, x0 - R, H, W);
+    Outs<OPT, NW> ou;
+    ou.init(wy, tx, y0, x0, H, W);
+    if (TMA && tid == 0) {
+        for (int k = 0; k < NSTG; ++k) mbar_init(bar + k);
+        mbar_init_fence();
+    }
     for (int k = tid; k < NS * 3 * NOUT; k += NT) ring[k] = 0;
+    if (timed_out(h, tid, &flag)) return;
+
     long long acc[OPT][3];
 #pragma unroll
     for (int o = 0; o < OPT; ++o)
@@ -329,24 +489,31 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const float *__restrict__ I
 
     const int zs = z0 - R, np = zend - z0 + 2 * R;
     auto issue = [&](int i) {
-        if (i < np) {
-            const int zp = zs + i, zo = zp - R;
-            const bool zok = zp >= 0 && zp < D;
-            float *dst = st + (i % NSTG) * 2 * NR;
-            load_plane<1, RY, RX, NW, RXP>(dst, If, N, (long long)zp * HW, zok, rg);
-            load_plane<1, RY, RX, NW, RXP>(dst + NR, J, N, (long long)zp * HW, zok, rg);
-            if (zo >= z0 && zo < zend) {
-                const long long zoff = (long long)zo * HW;
-#pragma unroll
-                for (int o = 0; o < OPT; ++o) {
-                    const bool ok = ou.off[o] >= 0;
-                    const long long gi = ok ? zoff + ou.off[o] : 0;
-                    cp8(os + (i % NSTG) * NOUT + o * NT + tid, SIg + gi, ok);
-                    cp4(ov + (i % NSTG) * NOUT + o * NT + tid, varIg + gi, ok);
+        const int zp = zs + i, zo = zp - R, s = i % NSTG;
+        const bool out = zo >= z0 && zo < zend;
+        if (TMA) {
+            if (tid == 0 && i < np) {
+                mbar_expect(bar + s, S::tx_plane + (out ? S::tx_out : 0u));
+                tma4(stage(s), &maps.a, x0 - XB, y0 - R, zp, 0, bar + s);
+                tma4(stage(s) + CS, &maps.b, x0 - XB, y0 - R, zp, 0, bar + s);
+                if (out) {
+                    tma4(ostage(s), &maps.c, x0, y0, zo, 0, bar + s);
+                    tma4(ostage(s) + NOUT, &maps.d, x0, y0, zo, 0, bar + s);
                 }
             }
+        } else {
+            if (i < np) {
+                const bool zok = zp >= 0 && zp < D;
+                rg.template load<1>(stage(s), If, N, (long long)zp * HW, zok);
+                rg.template load<1>(stage(s) + CS, J, N, (long long)zp * HW, zok);
+                if (out) {
+                    ou.template load<1, long long>(ostage(s), SIg, N, (long long)zo * HW, tid);
+                    ou.template load<1, float>((float *)(ostage(s) + NOUT), varIg, N,
+                                               (long long)zo * HW, tid);
+                }
+            }
+            cp_commit();
         }
-        cp_commit();
     };
 #pragma unroll
     for (int k = 0; k < NSTG - 1; ++k) issue(k);
@@ -354,64 +521,74 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const float *__restrict__ I
     unsigned long long qcc = 0;
     float mA = 0.f, mB = 0.f, mC = 0.f;
     bool bad = false;
-    int slot = 0;
+    int fail = -1, slot = 0;
     for (int i = 0; i < np; ++i) {
-        const int zp = zs + i;
+        const int zp = zs + i, z = zp - R, s = i % NSTG;
         issue(i + NSTG - 1);
-        cp_wait<NSTG - 1>();
-        long long P[OPT][3];
-        if (zp >= 0 && zp < D) {
-            const float *sI = st + (i % NSTG) * 2 * NR, *sJ = sI + NR;
+        bool ok = true;
+        if (TMA)
+            ok = mbar_wait(bar + s, (unsigned)(i / NSTG) & 1u);
+        else
+            cp_wait<NSTG - 1>();
+        const bool out = z >= z0 && z < zend;
+        // the outputs' operands, read before the barrier that frees the stage
+        long long a1[OPT];
+        float vI[OPT];
+        if (out) {
+            const long long *od = ostage(s);
 #pragma unroll
-            for (int j = 0; j < G::NJ; ++j)
-#pragma unroll
-                for (int c = 0; c < G::NC; ++c) {  // own copies: no barrier needed
-                    if (rg.off[j * G::NC + c] == -2) continue;
-                    const int k = rg.sbase + G::sofs(j, c);
+            for (int o = 0; o < OPT; ++o) {
+                a1[o] = od[o * NT + tid];
+                vI[o] = ((const float *)(od + NOUT))[o * NT + tid];
+            }
+        }
+        const bool zin = zp >= 0 && zp < D;
+        if (zin) {
+            const float *sI = stage(s), *sJ = sI + CS;
+            if (TMA) {
+                for (int k = tid; k < NR; k += NT) {
                     qI[k] = __float2int_rn(sI[k] * scale);
                     qJ[k] = __float2int_rn(sJ[k] * scale);
                 }
-            __syncthreads();
-            box_x4_fwd<R, RY, RXP, NT>(qI, qJ, xL, tid);
-            __syncthreads();
+            } else {
 #pragma unroll
-            for (int o = 0; o < OPT; ++o) {
-                const long long *xi = xL + (wy + NW * o) * FX + tx;
+                for (int j = 0; j < G::NJ; ++j)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    long long sum = 0;
-#pragma unroll
-                    for (int t = 0; t <= 2 * R; ++t) sum += xi[c * RY * FX + t * FX];
-                    P[o][c] = sum;
-                }
+                    for (int c = 0; c < G::NC; ++c) {  // own copies
+                        if (rg.off[j * G::NC + c] == -2) continue;
+                        const int k = rg.sbase + G::sofs(j, c);
+                        qI[k] = __float2int_rn(sI[k] * scale);
+                        qJ[k] = __float2int_rn(sJ[k] * scale);
+                    }
             }
+        }
+        if (__syncthreads_or(!ok)) {
+            fail = i;
+            break;
+        }
+        long long P[OPT][3];
+        if (zin) {
+            box_x4_fwd<R, RY, BXW, COFF, NT>(qI, qJ, xL, tid);
+            __syncthreads();
+            box_y3<R, RY, NW, OPT>(xL, wy, tx, P);
         } else {
 #pragma unroll
             for (int o = 0; o < OPT; ++o)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) P[o][c] = 0;
         }
-        long long *rb = ring + slot * 3 * NOUT + tid;
-#pragma unroll
-        for (int o = 0; o < OPT; ++o)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                long long *r = rb + c * NOUT + o * NT;
-                acc[o][c] += P[o][c] - *r;
-                *r = P[o][c];
-            }
+        zslide<NS, OPT, NOUT, NT>(ring, slot, tid, P, acc);
         slot = (slot + 1 == NS) ? 0 : slot + 1;
-        const int z = zp - R;
-        if (z >= z0 && z < zend) {
+        if (out) {
             const long long zoff = (long long)z * HW;
 #pragma unroll
             for (int o = 0; o < OPT; ++o) {
                 if (ou.off[o] < 0) continue;
-                const long long a1 = os[(i % NSTG) * NOUT + o * NT + tid];  // own copy
-                const float varI = ov[(i % NSTG) * NOUT + o * NT + tid];
                 const long long a2 = acc[o][0];
+                const float varI = vI[o];
                 const float varJ = diff_i128_to_float(n, acc[o][1], a2, a2) * inv_s * inv_s * inv_nf;
-                const float cross = diff_i128_to_float(n, acc[o][2], a1, a2) * inv_s * inv_s * inv_nf;
+                const float cross =
+                    diff_i128_to_float(n, acc[o][2], a1[o], a2) * inv_s * inv_s * inv_nf;
                 const float den = fmaf(varI, varJ, cc_eps);
                 const float rden = __frcp_rn(den);
                 const float cc = cross * cross * rden;
@@ -423,7 +600,7 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const float *__restrict__ I
                     const float A = 2.0f * cross * rden;
                     const float B = -cc * varI * rden;
                     float Ch, Cl;
-                    lncc_c_ff(A, B, a1, a2, inv_s, nf, inv_nf, Ch, Cl);
+                    lncc_c_ff(A, B, a1[o], a2, inv_s, nf, inv_nf, Ch, Cl);
                     float *cp = coef + zoff + ou.off[o];
                     cp[0] = A;
                     cp[N] = B;
@@ -436,7 +613,14 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const float *__restrict__ I
             }
         }
     }
-    cp_wait<0>();
+    if (fail >= 0) {  // a tile copy never landed
+        if (tid == 0) {
+            status_set(&h->status, ST_TIMEOUT);
+            drain<NSTG>(bar, fail, np);
+        }
+        return;
+    }
+    if (!TMA) cp_wait<0>();
     if (bad) status_set(&h->status, ST_NONFINITE);
     block_sum_to(&h->loss_acc, qcc, redu);
     if (write_coef) {
@@ -447,37 +631,45 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const float *__restrict__ I
 }
 
 // ====================================================================== K2
+// coef holds A, B and C as a float-float pair (C hi, C lo): [4][N].
 template <int R, int NW, int OPT, int NSTG>
 struct K2S {
     static constexpr int NT = FX * NW, TY = NW * OPT, RX = FX + 2 * R, RY = TY + 2 * R;
-    static constexpr int RXP = pad4(RX), NR = RXP * RY, NS = 2 * R + 1, NOUT = NT * OPT;
-    static constexpr size_t o_ring = 0;
+    static constexpr int XB = halo4(R), BXW = FX + 2 * XB, COFF = XB - R;
+    static constexpr int NR = BXW * RY, NS = 2 * R + 1, NOUT = NT * OPT;
+    static constexpr size_t st_bytes = al128((size_t)4 * NR * 4);    // A, B, C hi, C lo
+    static constexpr size_t ost_bytes = al128((size_t)4 * NOUT * 4);  // u (3), I_f
+    static constexpr unsigned tx_plane = 4u * NR * 4, tx_out = 4u * NOUT * 4;
+    static constexpr size_t o_st = 0;
+    static constexpr size_t o_ost = o_st + st_bytes * NSTG;
+    static constexpr size_t o_ring = o_ost + ost_bytes * NSTG;
     static constexpr size_t o_xL = o_ring + (size_t)NS * 3 * NOUT * 8;
     static constexpr size_t o_q = o_xL + (size_t)3 * RY * FX * 8;
-    static constexpr size_t o_st = o_q + (size_t)3 * NR * 8;
-    static constexpr size_t o_ost = o_st + (size_t)NSTG * 4 * NR * 4;
-    static constexpr size_t bytes = o_ost + (size_t)NSTG * 4 * NOUT * 4;
+    static constexpr size_t o_bar = al128(o_q + (size_t)3 * NR * 8);
+    static constexpr size_t bytes = o_bar + 8 * NSTG;
 };
 
-// coef holds A, B and C as a float-float pair (C hi, C lo).
-template <int R, int NW, int OPT, int NSTG>
-__global__ void __launch_bounds__(FX *NW) k_lncc_grad(const float *__restrict__ If,
+template <int R, int NW, int OPT, int NSTG, bool TMA>
+__global__ void __launch_bounds__(FX *NW) k_lncc_grad(const __grid_constant__ Maps maps,
+                                                      const float *__restrict__ If,
                                                       const float *__restrict__ Im,
                                                       const float *__restrict__ u,
                                                       const float *__restrict__ coef,
-                                                      const WsHeader *__restrict__ h,
+                                                      WsHeader *__restrict__ h,
                                                       float *__restrict__ g, int D, int H, int W,
                                                       int TZ, int cbits) {
     using S = K2S<R, NW, OPT, NSTG>;
-    using G = Region<S::RY, S::RX, NW, S::RXP>;
-    constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, RXP = S::RXP, NR = S::NR,
-                  NS = S::NS, NOUT = S::NOUT;
-    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, BXW = S::BXW, COFF = S::COFF,
+                  XB = S::XB, NR = S::NR, NS = S::NS, NOUT = S::NOUT;
+    using G = Region<RY, RX, NW, BXW, COFF>;
+    extern __shared__ __align__(128) unsigned char smem[];
     long long *ring = (long long *)(smem + S::o_ring);
     long long *xL = (long long *)(smem + S::o_xL);
     long long *q = (long long *)(smem + S::o_q);
-    float *st = (float *)(smem + S::o_st);
-    float *ost = (float *)(smem + S::o_ost);
+    unsigned long long *bar = (unsigned long long *)(smem + S::o_bar);
+    __shared__ int flag;
+    auto stage = [&](int s) { return (float *)(smem + S::o_st + S::st_bytes * s); };
+    auto ostage = [&](int s) { return (float *)(smem + S::o_ost + S::ost_bytes * s); };
 
     const int tx = threadIdx.x, wy = threadIdx.y, tid = wy * FX + tx;
     const int x0 = blockIdx.x * FX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
@@ -492,11 +684,15 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_grad(const float *__restrict__ 
     }
     const float inv_n = 1.0f / (float)N;
     G rg;
-    rg.init(wy, tx, y0 - R, x0 - R, H, W);
-    Outs<OPT> ou;
-    ou.init(wy, tx, y0, x0, NW, H, W);
-
+    if (!TMA) rg.init(wy, tx, y0 - R, x0 - R, H, W);
+    Outs<OPT, NW> ou;
+    ou.init(wy, tx, y0, x0, H, W);
+    if (TMA && tid == 0) {
+        for (int k = 0; k < NSTG; ++k) mbar_init(bar + k);
+        mbar_init_fence();
+    }
     for (int k = tid; k < NS * 3 * NOUT; k += NT) ring[k] = 0;
+    if (timed_out(h, tid, &flag)) return;
     long long acc[OPT][3];
 #pragma unroll
     for (int o = 0; o < OPT; ++o)
@@ -505,32 +701,47 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_grad(const float *__restrict__ 
 
     const int zs = z0 - R, np = zend - z0 + 2 * R;
     auto issue = [&](int i) {
-        if (i < np) {
-            const int zp = zs + i, zo = zp - R;
-            load_plane<4, RY, RX, NW, RXP>(st + (i % NSTG) * 4 * NR, coef, N, (long long)zp * HW,
-                                           zp >= 0 && zp < D, rg);
-            if (zo >= z0 && zo < zend) {
-                float *o = ost + (i % NSTG) * 4 * NOUT;
-                load_outs<3, OPT, NOUT>(o, u, N, (long long)zo * HW, ou, tid, NT);
-                load_outs<1, OPT, NOUT>(o + 3 * NOUT, If, N, (long long)zo * HW, ou, tid, NT);
+        const int zp = zs + i, zo = zp - R, s = i % NSTG;
+        const bool out = zo >= z0 && zo < zend;
+        if (TMA) {
+            if (tid == 0 && i < np) {
+                mbar_expect(bar + s, S::tx_plane + (out ? S::tx_out : 0u));
+                tma4(stage(s), &maps.a, x0 - XB, y0 - R, zp, 0, bar + s);
+                if (out) {
+                    tma4(ostage(s), &maps.b, x0, y0, zo, 0, bar + s);
+                    tma4(ostage(s) + 3 * NOUT, &maps.c, x0, y0, zo, 0, bar + s);
+                }
             }
+        } else {
+            if (i < np) {
+                rg.template load<4>(stage(s), coef, N, (long long)zp * HW, zp >= 0 && zp < D);
+                if (out) {
+                    ou.template load<3, float>(ostage(s), u, N, (long long)zo * HW, tid);
+                    ou.template load<1, float>(ostage(s) + 3 * NOUT, If, N, (long long)zo * HW,
+                                               tid);
+                }
+            }
+            cp_commit();
         }
-        cp_commit();
     };
 #pragma unroll
     for (int k = 0; k < NSTG - 1; ++k) issue(k);
 
-    int slot = 0;
+    int fail = -1, slot = 0;
     for (int i = 0; i < np; ++i) {
-        const int zp = zs + i, zo = zp - R;
+        const int zp = zs + i, zo = zp - R, s = i % NSTG;
         issue(i + NSTG - 1);
-        cp_wait<NSTG - 1>();
+        bool ok = true;
+        if (TMA)
+            ok = mbar_wait(bar + s, (unsigned)(i / NSTG) & 1u);
+        else
+            cp_wait<NSTG - 1>();
         const bool out = zo >= z0 && zo < zend;
         // gathers for this plane's outputs, consumed after the reductions
         TriPending tp[OPT];
         float Iv[OPT];
-        if (out) {
-            const float *o = ost + (i % NSTG) * 4 * NOUT + tid;
+        if (out && ok) {
+            const float *o = ostage(s) + tid;
 #pragma unroll
             for (int k = 0; k < OPT; ++k) {
                 tri_issue(tp[k], Im, D, H, W, zo, y0 + wy + NW * k, x0 + tx, o[k * NT],
@@ -538,48 +749,42 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_grad(const float *__restrict__ 
                 Iv[k] = o[3 * NOUT + k * NT];
             }
         }
-        long long P[OPT][3];
-        if (zp >= 0 && zp < D) {
-            const float *s = st + (i % NSTG) * 4 * NR;
+        const bool zin = zp >= 0 && zp < D;
+        if (zin) {
+            const float *sp = stage(s);
+            auto quant = [&](int k) {
+                q[k] = quantize(sp[k], qs[0]);
+                q[NR + k] = quantize(sp[NR + k], qs[1]);
+                q[2 * NR + k] = quantize(sp[2 * NR + k], qs[2]) + quantize(sp[3 * NR + k], qs[2]);
+            };
+            if (TMA) {
+                for (int k = tid; k < NR; k += NT) quant(k);
+            } else {
 #pragma unroll
-            for (int j = 0; j < G::NJ; ++j)
+                for (int j = 0; j < G::NJ; ++j)
 #pragma unroll
-                for (int c = 0; c < G::NC; ++c) {  // own copies
-                    if (rg.off[j * G::NC + c] == -2) continue;
-                    const int k = rg.sbase + G::sofs(j, c);
-                    q[k] = quantize(s[k], qs[0]);
-                    q[NR + k] = quantize(s[NR + k], qs[1]);
-                    q[2 * NR + k] = quantize(s[2 * NR + k], qs[2]) + quantize(s[3 * NR + k], qs[2]);
-                }
-            __syncthreads();
-            box_x4_adj<R, RY, RXP, NT>(q, xL, tid);
-            __syncthreads();
-#pragma unroll
-            for (int o = 0; o < OPT; ++o) {
-                const long long *xi = xL + (wy + NW * o) * FX + tx;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    long long sum = 0;
-#pragma unroll
-                    for (int t = 0; t <= 2 * R; ++t) sum += xi[c * RY * FX + t * FX];
-                    P[o][c] = sum;
-                }
+                    for (int c = 0; c < G::NC; ++c) {  // own copies
+                        if (rg.off[j * G::NC + c] == -2) continue;
+                        quant(rg.sbase + G::sofs(j, c));
+                    }
             }
+        }
+        if (__syncthreads_or(!ok)) {
+            fail = i;
+            break;
+        }
+        long long P[OPT][3];
+        if (zin) {
+            box_x4_adj<R, RY, BXW, COFF, NT>(q, xL, tid);
+            __syncthreads();
+            box_y3<R, RY, NW, OPT>(xL, wy, tx, P);
         } else {
 #pragma unroll
             for (int o = 0; o < OPT; ++o)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) P[o][c] = 0;
         }
-        long long *rb = ring + slot * 3 * NOUT + tid;
-#pragma unroll
-        for (int o = 0; o < OPT; ++o)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                long long *r = rb + c * NOUT + o * NT;
-                acc[o][c] += P[o][c] - *r;
-                *r = P[o][c];
-            }
+        zslide<NS, OPT, NOUT, NT>(ring, slot, tid, P, acc);
         slot = (slot + 1 == NS) ? 0 : slot + 1;
         if (out) {
             const long long zoff = (long long)zo * HW;
@@ -592,10 +797,10 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_grad(const float *__restrict__ 
                 i64_to_ff(acc[o][0], ah, al);
                 i64_to_ff(acc[o][1], bh, bl);
                 i64_to_ff(acc[o][2], ch, cl);
-                ff_mul_f(Iv[o], ah * us[0], al * us[0], rh, rl);       // I SA
-                ff_mul_f(2.0f * Jv, bh * us[1], bl * us[1], th, tl);   // 2 J SB
+                ff_mul_f(Iv[o], ah * us[0], al * us[0], rh, rl);      // I SA
+                ff_mul_f(2.0f * Jv, bh * us[1], bl * us[1], th, tl);  // 2 J SB
                 ff_add(rh, rl, th, tl);
-                ff_add(rh, rl, ch * us[2], cl * us[2]);                // + SC
+                ff_add(rh, rl, ch * us[2], cl * us[2]);               // + SC
                 const float dj = -(rh + rl) * inv_n;
                 float *gp = g + zoff + ou.off[o];
                 gp[0] = dj * gz;
@@ -604,7 +809,14 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_grad(const float *__restrict__ 
             }
         }
     }
-    cp_wait<0>();
+    if (fail >= 0) {
+        if (tid == 0) {
+            status_set(&h->status, ST_TIMEOUT);
+            drain<NSTG>(bar, fail, np);
+        }
+        return;
+    }
+    if (!TMA) cp_wait<0>();
 }
 
 // MSE: g = 2 (J - I) / N * grad I_m o phi (pointwise).
@@ -628,64 +840,26 @@ __global__ void __launch_bounds__(256) k_fused_mse_grad(const float *__restrict_
     g[2 * N + i] = dj * gx;
 }
 
-// ====================================================== separable Gaussian
-// x pass of a [3][RY][RXP] plane onto [3][RY][FX] and this thread's y pass.
-template <int RG, int RY, int RXP, int NW, int OPT>
-__device__ __forceinline__ void gauss_xy(const float *pl, float *xb, const GaussTaps &t, int wy,
-                                         int tx, float Q[OPT][3]) {
-    gauss_x4<RG, 3, RY, RXP, FX * NW>(pl, xb, t, wy * FX + tx);
-    __syncthreads();
-#pragma unroll
-    for (int o = 0; o < OPT; ++o) {
-        const float *xi = xb + (wy + NW * o) * FX + tx;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            float s = 0.0f;
-#pragma unroll
-            for (int k = 0; k <= 2 * RG; ++k) s = fmaf(t.w[k], xi[c * RY * FX + k * FX], s);
-            Q[o][c] = s;
-        }
-    }
-}
-
-// Ring of the last NS in-plane results, every slot stored twice (k, k + NS)
-// so that the z window is contiguous.  Writes plane results at `slot` and
-// returns the first slot of the window (oldest plane first).
-template <int NS, int OPT, int NOUT, int NT>
-__device__ __forceinline__ int ring_push(float *ring, int slot, int tid, const float Q[OPT][3]) {
-#pragma unroll
-    for (int o = 0; o < OPT; ++o)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float v = Q[o][c];
-            ring[(slot * 3 + c) * NOUT + o * NT + tid] = v;
-            ring[((slot + NS) * 3 + c) * NOUT + o * NT + tid] = v;
-        }
-    return slot + 1;  // window slots slot+1 .. slot+NS
-}
-
-template <int RG, int NOUT>
-__device__ __forceinline__ float gauss_z(const float *win, const GaussTaps &t, int c) {
-    float s = 0.0f;
-#pragma unroll
-    for (int k = 0; k <= 2 * RG; ++k) s = fmaf(t.w[k], win[(k * 3 + c) * NOUT], s);
-    return s;
-}
-
 // ====================================================================== K3
 template <int RG, int NW, int OPT, int NSTG>
 struct K3S {
     static constexpr int NT = FX * NW, TY = NW * OPT, RX = FX + 2 * RG, RY = TY + 2 * RG;
-    static constexpr int RXP = pad4(RX), NR = RXP * RY, NS = 2 * RG + 1, NOUT = NT * OPT;
-    static constexpr size_t o_ring = 0;
+    static constexpr int XB = halo4(RG), BXW = FX + 2 * XB, COFF = XB - RG;
+    static constexpr int NR = BXW * RY, NS = 2 * RG + 1, NOUT = NT * OPT;
+    static constexpr size_t st_bytes = al128((size_t)3 * NR * 4);    // g
+    static constexpr size_t ost_bytes = al128((size_t)6 * NOUT * 4);  // m, v
+    static constexpr unsigned tx_plane = 3u * NR * 4, tx_out = 6u * NOUT * 4;
+    static constexpr size_t o_st = 0;
+    static constexpr size_t o_ost = o_st + st_bytes * NSTG;
+    static constexpr size_t o_ring = o_ost + ost_bytes * NSTG;
     static constexpr size_t o_xb = o_ring + (size_t)2 * NS * 3 * NOUT * 4;
-    static constexpr size_t o_st = o_xb + (size_t)3 * RY * FX * 4;
-    static constexpr size_t o_mv = o_st + (size_t)NSTG * 3 * NR * 4;
-    static constexpr size_t bytes = o_mv + (size_t)NSTG * 6 * NOUT * 4;
+    static constexpr size_t o_bar = al128(o_xb + (size_t)3 * RY * FX * 4);
+    static constexpr size_t bytes = o_bar + 8 * NSTG;
 };
 
-template <int RG, int NW, int OPT, int NSTG>
-__global__ void __launch_bounds__(FX *NW) k_smooth_adam(const float *__restrict__ g,
+template <int RG, int NW, int OPT, int NSTG, bool TMA>
+__global__ void __launch_bounds__(FX *NW) k_smooth_adam(const __grid_constant__ Maps maps,
+                                                        const float *__restrict__ g,
                                                         float *__restrict__ m,
                                                         float *__restrict__ v,
                                                         float *__restrict__ dir,
@@ -693,62 +867,100 @@ __global__ void __launch_bounds__(FX *NW) k_smooth_adam(const float *__restrict_
                                                         int W, int TZ, GaussTaps t, AdamConsts ac,
                                                         int parity) {
     using S = K3S<RG, NW, OPT, NSTG>;
-    using G = Region<S::RY, S::RX, NW, S::RXP>;
-    constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, RXP = S::RXP, NR = S::NR,
-                  NS = S::NS, NOUT = S::NOUT;
-    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, BXW = S::BXW, COFF = S::COFF,
+                  XB = S::XB, NS = S::NS, NOUT = S::NOUT;
+    using G = Region<RY, RX, NW, BXW, COFF>;
+    extern __shared__ __align__(128) unsigned char smem[];
     float *ring = (float *)(smem + S::o_ring);
     float *xb = (float *)(smem + S::o_xb);
-    float *st = (float *)(smem + S::o_st);
-    float *mvs = (float *)(smem + S::o_mv);
+    unsigned long long *bar = (unsigned long long *)(smem + S::o_bar);
     __shared__ float redf[32];
+    __shared__ int flag;
+    auto stage = [&](int s) { return (float *)(smem + S::o_st + S::st_bytes * s); };
+    auto ostage = [&](int s) { return (float *)(smem + S::o_ost + S::ost_bytes * s); };
 
     const int tx = threadIdx.x, wy = threadIdx.y, tid = wy * FX + tx;
     const int x0 = blockIdx.x * FX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
     const int zend = min(z0 + TZ, D);
     const long long N = (long long)D * H * W, HW = (long long)H * W;
     G rg;
-    rg.init(wy, tx, y0 - RG, x0 - RG, H, W);
-    Outs<OPT> ou;
-    ou.init(wy, tx, y0, x0, NW, H, W);
+    if (!TMA) rg.init(wy, tx, y0 - RG, x0 - RG, H, W);
+    Outs<OPT, NW> ou;
+    ou.init(wy, tx, y0, x0, H, W);
+    if (TMA && tid == 0) {
+        for (int k = 0; k < NSTG; ++k) mbar_init(bar + k);
+        mbar_init_fence();
+    }
     for (int k = tid; k < 2 * NS * 3 * NOUT; k += NT) ring[k] = 0.0f;
+    if (timed_out(h, tid, &flag)) return;
 
     const int zs = z0 - RG, np = zend - z0 + 2 * RG;
     auto issue = [&](int i) {
-        if (i < np) {
-            const int zp = zs + i, zo = zp - RG;
-            load_plane<3, RY, RX, NW, RXP>(st + (i % NSTG) * 3 * NR, g, N, (long long)zp * HW,
-                                           zp >= 0 && zp < D, rg);
-            if (zo >= z0 && zo < zend) {
-                float *o = mvs + (i % NSTG) * 6 * NOUT;
-                load_outs<3, OPT, NOUT>(o, m, N, (long long)zo * HW, ou, tid, NT);
-                load_outs<3, OPT, NOUT>(o + 3 * NOUT, v, N, (long long)zo * HW, ou, tid, NT);
+        const int zp = zs + i, zo = zp - RG, s = i % NSTG;
+        const bool out = zo >= z0 && zo < zend;
+        if (TMA) {
+            if (tid == 0 && i < np) {
+                mbar_expect(bar + s, S::tx_plane + (out ? S::tx_out : 0u));
+                tma4(stage(s), &maps.a, x0 - XB, y0 - RG, zp, 0, bar + s);
+                if (out) {
+                    tma4(ostage(s), &maps.b, x0, y0, zo, 0, bar + s);
+                    tma4(ostage(s) + 3 * NOUT, &maps.c, x0, y0, zo, 0, bar + s);
+                }
             }
+        } else {
+            if (i < np) {
+                rg.template load<3>(stage(s), g, N, (long long)zp * HW, zp >= 0 && zp < D);
+                if (out) {
+                    ou.template load<3, float>(ostage(s), m, N, (long long)zo * HW, tid);
+                    ou.template load<3, float>(ostage(s) + 3 * NOUT, v, N, (long long)zo * HW,
+                                               tid);
+                }
+            }
+            cp_commit();
         }
-        cp_commit();
     };
 #pragma unroll
     for (int k = 0; k < NSTG - 1; ++k) issue(k);
 
     float mx = 0.0f;
     bool bad = false;
-    int slot = 0;
+    int fail = -1, slot = 0;
     for (int i = 0; i < np; ++i) {
-        const int zp = zs + i, zo = zp - RG;
+        const int zp = zs + i, zo = zp - RG, s = i % NSTG;
         issue(i + NSTG - 1);
-        cp_wait<NSTG - 1>();
+        bool ok = true;
+        if (TMA)
+            ok = mbar_wait(bar + s, (unsigned)(i / NSTG) & 1u);
+        else
+            cp_wait<NSTG - 1>();
+        const bool out = zo >= z0 && zo < zend;
+        float mo[OPT][3], vo[OPT][3];
+        if (out) {
+            const float *od = ostage(s) + tid;
+#pragma unroll
+            for (int o = 0; o < OPT; ++o)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    mo[o][c] = od[c * NOUT + o * NT];
+                    vo[o][c] = od[(3 + c) * NOUT + o * NT];
+                }
+        }
+        if (__syncthreads_or(!ok)) {  // also: the x pass reads neighbours' copies
+            fail = i;
+            break;
+        }
         float Q[OPT][3];
         if (zp >= 0 && zp < D) {
-            __syncthreads();  // the x pass reads neighbours' copies
-            gauss_xy<RG, RY, RXP, NW, OPT>(st + (i % NSTG) * 3 * NR, xb, t, wy, tx, Q);
+            gauss_x4<RG, 3, RY, BXW, COFF, NT>(stage(s), xb, t, tid);
+            __syncthreads();
+            gauss_y3<RG, RY, NW, OPT>(xb, t, wy, tx, Q);
         } else {
 #pragma unroll
             for (int o = 0; o < OPT; ++o) Q[o][0] = Q[o][1] = Q[o][2] = 0.0f;
         }
         const int wbase = ring_push<NS, OPT, NOUT, NT>(ring, slot, tid, Q);
         slot = (slot + 1 == NS) ? 0 : slot + 1;
-        if (zo >= z0 && zo < zend) {
-            const float *mv = mvs + (i % NSTG) * 6 * NOUT + tid;
+        if (out) {
             const long long zoff = (long long)zo * HW;
 #pragma unroll
             for (int o = 0; o < OPT; ++o) {
@@ -758,10 +970,9 @@ __global__ void __launch_bounds__(FX *NW) k_smooth_adam(const float *__restrict_
                 float nrm2 = 0.0f;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float s = gauss_z<RG, NOUT>(win, t, c);
-                    const float mvv = fmaf(ac.b1, mv[c * NOUT + o * NT], (1.0f - ac.b1) * s);
-                    const float vvv =
-                        fmaf(ac.b2, mv[(3 + c) * NOUT + o * NT], (1.0f - ac.b2) * s * s);
+                    const float sg = gauss_z<RG, NOUT>(win, t, c);
+                    const float mvv = fmaf(ac.b1, mo[o][c], (1.0f - ac.b1) * sg);
+                    const float vvv = fmaf(ac.b2, vo[o][c], (1.0f - ac.b2) * sg * sg);
                     m[c * N + gi] = mvv;
                     v[c * N + gi] = vvv;
                     const float dv = adam_dir(mvv, vvv, ac.rbc1, ac.rbc2, ac.eps);
@@ -775,7 +986,14 @@ __global__ void __launch_bounds__(FX *NW) k_smooth_adam(const float *__restrict_
             }
         }
     }
-    cp_wait<0>();
+    if (fail >= 0) {
+        if (tid == 0) {
+            status_set(&h->status, ST_TIMEOUT);
+            drain<NSTG>(bar, fail, np);
+        }
+        return;
+    }
+    if (!TMA) cp_wait<0>();
     if (bad) status_set(&h->status, ST_NONFINITE);
     block_max_to(&h->step_max_bits[parity], mx, redf);
 }
@@ -786,20 +1004,26 @@ __global__ void __launch_bounds__(FX *NW) k_smooth_adam(const float *__restrict_
 template <int RG, int NW, int OPT, bool SU, int NSTG>
 struct K4S {
     static constexpr int NT = FX * NW, TY = NW * OPT, RX = FX + 2 * RG, RY = TY + 2 * RG;
-    static constexpr int RXP = pad4(RX), NR = RXP * RY, NS = 2 * RG + 1, NOUT = NT * OPT;
-    // u planes z-1, z, z+1 in use plus NSTG - 1 in flight
-    static constexpr int URX = RX + 2, URY = RY + 2, URXP = pad4(URX), NRU = URXP * URY,
-                         NSU = NSTG + 2;
-    static constexpr size_t o_ring = 0;
+    static constexpr int XB = halo4(RG), BXW = FX + 2 * XB, COFF = XB - RG;
+    static constexpr int NR = BXW * RY, NS = 2 * RG + 1, NOUT = NT * OPT;
+    // u planes z-1, z, z+1 in use plus NSTG - 1 in flight, halo RG + 1
+    static constexpr int URX = RX + 2, URY = RY + 2, UXB = halo4(RG + 1), UBXW = FX + 2 * UXB;
+    static constexpr int UCOFF = UXB - RG - 1, NRU = UBXW * URY, NSU = NSTG + 2;
+    static constexpr size_t st_bytes = al128((size_t)3 * NR * 4);    // d
+    static constexpr size_t ust_bytes = al128((size_t)3 * NRU * 4);  // u
+    static constexpr unsigned tx_plane = 3u * NR * 4, tx_u = 3u * NRU * 4;
+    static constexpr size_t o_st = 0;
+    static constexpr size_t o_ust = o_st + st_bytes * NSTG;
+    static constexpr size_t o_ring = o_ust + (SU ? ust_bytes * NSU : 0);
     static constexpr size_t o_xb = o_ring + (size_t)2 * NS * 3 * NOUT * 4;
     static constexpr size_t o_up = o_xb + (size_t)3 * RY * FX * 4;
-    static constexpr size_t o_dst = o_up + (size_t)3 * NR * 4;
-    static constexpr size_t o_ust = o_dst + (size_t)NSTG * 3 * NR * 4;
-    static constexpr size_t bytes = o_ust + (SU ? (size_t)NSU * 3 * NRU * 4 : 0);
+    static constexpr size_t o_bar = al128(o_up + (size_t)3 * NR * 4);
+    static constexpr size_t bytes = o_bar + 8 * (NSTG + 1);
 };
 
-template <int RG, int NW, int OPT, bool SU, int NSTG>
-__global__ void __launch_bounds__(FX *NW) k_compose(const float *__restrict__ u,
+template <int RG, int NW, int OPT, bool SU, int NSTG, bool TMA>
+__global__ void __launch_bounds__(FX *NW) k_compose(const __grid_constant__ Maps maps,
+                                                    const float *__restrict__ u,
                                                     const float *__restrict__ dir,
                                                     float *__restrict__ uo,
                                                     const float *__restrict__ Im,
@@ -808,17 +1032,19 @@ __global__ void __launch_bounds__(FX *NW) k_compose(const float *__restrict__ u,
                                                     int TZ, GaussTaps t, float lr, float c_lp,
                                                     int parity) {
     using S = K4S<RG, NW, OPT, SU, NSTG>;
-    using G = Region<S::RY, S::RX, NW, S::RXP>;
-    using GU = Region<S::URY, S::URX, NW, S::URXP>;
-    constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, RXP = S::RXP, NR = S::NR,
-                  NS = S::NS, NOUT = S::NOUT, URX = S::URX, URY = S::URY, URXP = S::URXP,
-                  NRU = S::NRU, NSU = S::NSU;
-    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, BXW = S::BXW, COFF = S::COFF,
+                  XB = S::XB, NR = S::NR, NS = S::NS, NOUT = S::NOUT, URX = S::URX,
+                  URY = S::URY, UXB = S::UXB, UBXW = S::UBXW, UCOFF = S::UCOFF, NRU = S::NRU,
+                  NSU = S::NSU;
+    using G = Region<RY, RX, NW, BXW, COFF>;
+    using GU = Region<URY, URX, NW, UBXW, UCOFF>;
+    extern __shared__ __align__(128) unsigned char smem[];
     float *ring = (float *)(smem + S::o_ring);
     float *xb = (float *)(smem + S::o_xb);
     float *up = (float *)(smem + S::o_up);
-    float *dst = (float *)(smem + S::o_dst);
-    float *ust = (float *)(smem + S::o_ust);
+    unsigned long long *bar = (unsigned long long *)(smem + S::o_bar);
+    __shared__ int flag;
+    auto stage = [&](int s) { return (float *)(smem + S::o_st + S::st_bytes * s); };
 
     const int tx = threadIdx.x, wy = threadIdx.y, tid = wy * FX + tx;
     const int x0 = blockIdx.x * FX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
@@ -827,34 +1053,62 @@ __global__ void __launch_bounds__(FX *NW) k_compose(const float *__restrict__ u,
     const float mxd = __uint_as_float(h->step_max_bits[parity]);
     const float e = (mxd > 0.0f) ? lr / (c_lp * mxd) : 0.0f;
     G rg;
-    rg.init(wy, tx, y0 - RG, x0 - RG, H, W);
     GU rgu;
-    if (SU) rgu.init(wy, tx, y0 - RG - 1, x0 - RG - 1, H, W);
-    Outs<OPT> ou;
-    ou.init(wy, tx, y0, x0, NW, H, W);
+    if (!TMA) {
+        rg.init(wy, tx, y0 - RG, x0 - RG, H, W);
+        if (SU) rgu.init(wy, tx, y0 - RG - 1, x0 - RG - 1, H, W);
+    }
+    Outs<OPT, NW> ou;
+    ou.init(wy, tx, y0, x0, H, W);
+    if (TMA && tid == 0) {
+        for (int k = 0; k <= NSTG; ++k) mbar_init(bar + k);
+        mbar_init_fence();
+    }
     for (int k = tid; k < 2 * NS * 3 * NOUT; k += NT) ring[k] = 0.0f;
+    if (timed_out(h, tid, &flag)) return;
 
     const int zs = z0 - RG, np = zend - z0 + 2 * RG;
-    // u plane q lives in stage (q - (zs - 1)) % NSU
-    auto issue_u = [&](int q) {
-        load_plane<3, URY, URX, NW, URXP>(ust + ((q - (zs - 1)) % NSU) * 3 * NRU, u, N,
-                                          (long long)q * HW, q >= 0 && q < D, rgu);
+    // u plane q lives in u stage (q - (zs - 1)) % NSU
+    auto uslot = [&](int q) {
+        return (float *)(smem + S::o_ust + S::ust_bytes * ((q - (zs - 1)) % NSU));
     };
+    // group i: d plane zs + i and u plane zs + i + 1
     auto issue = [&](int i) {
-        if (i < np) {
-            const int zp = zs + i;
-            load_plane<3, RY, RX, NW, RXP>(dst + (i % NSTG) * 3 * NR, dir, N,
-                                           (long long)zp * HW, zp >= 0 && zp < D, rg);
-            if (SU) issue_u(zp + 1);
+        const int zp = zs + i, s = i % NSTG;
+        if (TMA) {
+            if (tid == 0 && i < np) {
+                mbar_expect(bar + s, S::tx_plane + (SU ? S::tx_u : 0u));
+                tma4(stage(s), &maps.a, x0 - XB, y0 - RG, zp, 0, bar + s);
+                if (SU) tma4(uslot(zp + 1), &maps.b, x0 - UXB, y0 - RG - 1, zp + 1, 0, bar + s);
+            }
+        } else {
+            if (i < np) {
+                rg.template load<3>(stage(s), dir, N, (long long)zp * HW, zp >= 0 && zp < D);
+                if (SU)
+                    rgu.template load<3>(uslot(zp + 1), u, N, (long long)(zp + 1) * HW,
+                                         zp + 1 >= 0 && zp + 1 < D);
+            }
+            cp_commit();
         }
-        cp_commit();
     };
+    // u planes zs - 1 and zs: barrier NSTG (TMA), or cp.async group 0
     if (SU) {
-        issue_u(zs - 1);
-        issue_u(zs);
+        if (TMA) {
+            if (tid == 0) {
+                mbar_expect(bar + NSTG, 2u * S::tx_u);
+                tma4(uslot(zs - 1), &maps.b, x0 - UXB, y0 - RG - 1, zs - 1, 0, bar + NSTG);
+                tma4(uslot(zs), &maps.b, x0 - UXB, y0 - RG - 1, zs, 0, bar + NSTG);
+            }
+        } else {
+            rgu.template load<3>(uslot(zs - 1), u, N, (long long)(zs - 1) * HW,
+                                 zs - 1 >= 0 && zs - 1 < D);
+            rgu.template load<3>(uslot(zs), u, N, (long long)zs * HW, zs >= 0 && zs < D);
+        }
     }
 #pragma unroll
-    for (int k = 0; k < NSTG - 1; ++k) issue(k);  // the u planes above join group 0
+    for (int k = 0; k < NSTG - 1; ++k) issue(k);
+    bool ok0 = true;
+    if (SU && TMA) ok0 = mbar_wait(bar + NSTG, 0u);
 
     TriPending jp[OPT];
     long long jidx[OPT];
@@ -862,27 +1116,34 @@ __global__ void __launch_bounds__(FX *NW) k_compose(const float *__restrict__ u,
 #pragma unroll
     for (int o = 0; o < OPT; ++o) jlive[o] = false;
 
-    int slot = 0;
+    int fail = -1, slot = 0;
     for (int i = 0; i < np; ++i) {
-        const int zp = zs + i, zo = zp - RG;
+        const int zp = zs + i, zo = zp - RG, s = i % NSTG;
         issue(i + NSTG - 1);
-        cp_wait<NSTG - 1>();
+        bool ok = ok0;
+        if (TMA)
+            ok = mbar_wait(bar + s, (unsigned)(i / NSTG) & 1u) && ok;
+        else
+            cp_wait<NSTG - 1>();
+        if (__syncthreads_or(!ok)) {  // the stages hold neighbours' copies
+            fail = i;
+            break;
+        }
         float Q[OPT][3];
         if (zp >= 0 && zp < D) {
-            if (SU) __syncthreads();  // u stages hold neighbours' copies
-            const float *ds = dst + (i % NSTG) * 3 * NR;
-            const float *um = ust + ((zp - 1 - (zs - 1)) % NSU) * 3 * NRU;
-            const float *u0 = ust + ((zp - (zs - 1)) % NSU) * 3 * NRU;
-            const float *u1 = ust + ((zp + 1 - (zs - 1)) % NSU) * 3 * NRU;
+            const float *ds = stage(s);
+            const float *um = uslot(zp - 1), *u0 = uslot(zp), *u1 = uslot(zp + 1);
+            // u' on the RY x RX region, at the plane layout's columns
 #pragma unroll
             for (int j = 0; j < G::NJ; ++j)
 #pragma unroll
-                for (int cc = 0; cc < G::NC; ++cc) {  // own copies of d
-                    const int o = rg.off[j * G::NC + cc];
-                    if (o == -2) continue;
-                    const int k = rg.sbase + G::sofs(j, cc);
+                for (int cc = 0; cc < G::NC; ++cc) {
+                    const int ry = wy + NW * j, rx = tx + 32 * cc;
+                    if (ry >= RY || rx >= RX) continue;
+                    const int y = y0 - RG + ry, x = x0 - RG + rx;
+                    const int k = ry * BXW + rx + COFF;
                     float a = 0.f, b = 0.f, c = 0.f;
-                    if (o >= 0) {
+                    if (y >= 0 && y < H && x >= 0 && x < W) {
                         const float dz = -e * ds[k], dy = -e * ds[NR + k], dx = -e * ds[2 * NR + k];
                         if (SU) {
                             // cell corners lie within one voxel: planes zp-1..zp+1
@@ -892,16 +1153,15 @@ __global__ void __launch_bounds__(FX *NW) k_compose(const float *__restrict__ u,
                                 const float tz = dz - fz, ty = dy - fy, tx2 = dx - fx;
                                 const float *pa = fz < 0.0f ? um : u0;
                                 const float *pb = fz < 0.0f ? u0 : u1;
-                                const int ry = wy + NW * j, rx = tx + 32 * cc;
-                                const int b0 = (ry + 1 + (int)fy) * URXP + (rx + 1 + (int)fx);
+                                const int b0 = (ry + 1 + (int)fy) * UBXW + (rx + 1 + (int)fx) + UCOFF;
                                 float r[3];
 #pragma unroll
                                 for (int ch = 0; ch < 3; ++ch) {
                                     const float *A = pa + ch * NRU + b0, *B = pb + ch * NRU + b0;
                                     const float c00 = fmaf(tx2, A[1] - A[0], A[0]);
-                                    const float c01 = fmaf(tx2, A[URXP + 1] - A[URXP], A[URXP]);
+                                    const float c01 = fmaf(tx2, A[UBXW + 1] - A[UBXW], A[UBXW]);
                                     const float c10 = fmaf(tx2, B[1] - B[0], B[0]);
-                                    const float c11 = fmaf(tx2, B[URXP + 1] - B[URXP], B[URXP]);
+                                    const float c11 = fmaf(tx2, B[UBXW + 1] - B[UBXW], B[UBXW]);
                                     const float c0 = fmaf(ty, c01 - c00, c00);
                                     const float c1 = fmaf(ty, c11 - c10, c10);
                                     r[ch] = fmaf(tz, c1 - c0, c0);
@@ -913,7 +1173,6 @@ __global__ void __launch_bounds__(FX *NW) k_compose(const float *__restrict__ u,
                                 a = b = c = __int_as_float(0x7fc00000);  // impossible step: flag it
                             }
                         } else {
-                            const int y = y0 - RG + wy + NW * j, x = x0 - RG + tx + 32 * cc;
                             float gz, gy, gx;
                             a = dz + tri_sample<false>(u, D, H, W, zp, y, x, dz, dy, dx, gz, gy, gx);
                             b = dy + tri_sample<false>(u + N, D, H, W, zp, y, x, dz, dy, dx, gz, gy,
@@ -927,7 +1186,9 @@ __global__ void __launch_bounds__(FX *NW) k_compose(const float *__restrict__ u,
                     up[2 * NR + k] = c;
                 }
             __syncthreads();
-            gauss_xy<RG, RY, RXP, NW, OPT>(up, xb, t, wy, tx, Q);
+            gauss_x4<RG, 3, RY, BXW, COFF, NT>(up, xb, t, tid);
+            __syncthreads();
+            gauss_y3<RG, RY, NW, OPT>(xb, t, wy, tx, Q);
         } else {
 #pragma unroll
             for (int o = 0; o < OPT; ++o) Q[o][0] = Q[o][1] = Q[o][2] = 0.0f;
@@ -959,13 +1220,21 @@ __global__ void __launch_bounds__(FX *NW) k_compose(const float *__restrict__ u,
             }
         }
     }
+    if (fail >= 0) {
+        if (tid == 0) {
+            status_set(&h->status, ST_TIMEOUT);
+            if (SU && !ok0) mbar_wait(bar + NSTG, 0u);
+            drain<NSTG>(bar, fail, np);
+        }
+        return;
+    }
 #pragma unroll
     for (int o = 0; o < OPT; ++o)
         if (jlive[o]) {
             float gz, gy, gx;
             Jout[jidx[o]] = tri_finish<false>(jp[o], gz, gy, gx);
         }
-    cp_wait<0>();
+    if (!TMA) cp_wait<0>();
     // per-iteration header fields for the next iteration (nobody else reads them now)
     if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && tid == 0) {
         for (int c = 0; c < 8; ++c) h->coef_max_bits[c] = 0u;
@@ -1036,35 +1305,131 @@ inline LaunchGeom geometry(int occ, int nw, int ty, int halo, Dims d) {
     return g;
 }
 
-// tile shapes (warps per CTA, outputs per thread along y) and pipeline depth
-constexpr int K1_NW = 8, K1_OPT = 1, K1_ST = 3;
-constexpr int K2_NW = 8, K2_OPT = 1, K2_ST = 2;
-constexpr int K3_NW = 8, K3_OPT = 1, K3_ST = 2;
-constexpr int K4_NW = 8, K4_OPT = 1, K4_ST = 2;
+// ------------------------------------------------------------- tensor maps
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return (EncodeTiledFn)p;
+    }();
+    return fn;
+}
+
+struct MapKey {
+    const void *base;
+    int esize, D, H, W, C, bx, by, bc;
+    bool operator==(const MapKey &o) const {
+        return base == o.base && esize == o.esize && D == o.D && H == o.H && W == o.W &&
+               C == o.C && bx == o.bx && by == o.by && bc == o.bc;
+    }
+};
+
+// Map of a [C][D][H][W] field of 4- or 8-byte elements with a {bx, by, 1, bc}
+// box, zero fill outside the field.  Encoded maps are kept per host thread
+// (a launch sequence reuses a handful of buffers).  False when the field
+// does not meet TMA's alignment rules (row pitch a multiple of 16 bytes).
+bool tmap(CUtensorMap *m, const void *base, int esize, Dims d, int C, int bx, int by, int bc) {
+    constexpr int kCache = 64;
+    thread_local MapKey keys[kCache];
+    thread_local CUtensorMap maps[kCache];
+    thread_local int used = 0, next = 0;
+    const MapKey key{base, esize, d.D, d.H, d.W, C, bx, by, bc};
+    for (int i = 0; i < used; ++i)
+        if (keys[i] == key) {
+            *m = maps[i];
+            return true;
+        }
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    if (((uintptr_t)base & 15u) != 0 || ((long long)d.W * esize) % 16 != 0 ||
+        (d.N() * esize) % 16 != 0)
+        return false;
+    cuuint64_t dims[4] = {(cuuint64_t)d.W, (cuuint64_t)d.H, (cuuint64_t)d.D, (cuuint64_t)C};
+    cuuint64_t strides[3] = {(cuuint64_t)d.W * esize, (cuuint64_t)d.W * d.H * esize,
+                             (cuuint64_t)d.N() * esize};
+    cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1u, (cuuint32_t)bc};
+    cuuint32_t es[4] = {1u, 1u, 1u, 1u};
+    CUtensorMap tm;
+    CUresult r = fn(&tm, esize == 8 ? CU_TENSOR_MAP_DATA_TYPE_INT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                    4, const_cast<void *>(base), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+    const int slot = used < kCache ? used++ : (next++ % kCache);
+    keys[slot] = key;
+    maps[slot] = tm;
+    *m = tm;
+    return true;
+}
+
+// tile shapes (warps per CTA, outputs per thread along y) and pipeline depths
+// of the TMA and of the cp.async variant
+constexpr int K1_NW = 8, K1_OPT = 1, K1_ST_TMA = 3, K1_ST_CP = 3;
+constexpr int K2_NW = 8, K2_OPT = 1, K2_ST_TMA = 3, K2_ST_CP = 2;
+constexpr int K3_NW = 8, K3_OPT = 1, K3_ST_TMA = 3, K3_ST_CP = 2;
+constexpr int K4_NW = 8, K4_OPT = 1, K4_ST_TMA = 3, K4_ST_CP = 2;
 
 template <int R>
 cudaError_t launch_k1(const float *If, const float *J, const long long *sI, const float *varI,
                       float *coef, WsHeader *h, Dims d, int window, float cc_eps, bool wc,
                       cudaStream_t s) {
-    using S = K1S<R, K1_NW, K1_OPT, K1_ST>;
-    auto kern = k_lncc_fwd<R, K1_NW, K1_OPT, K1_ST>;
-    static const int occ = prepare(kern, S::bytes, S::NT);
-    LaunchGeom g = geometry(occ, K1_NW, S::TY, R, d);
-    kern<<<g.grid, g.block, S::bytes, s>>>(If, J, sI, varI, coef, h, d.D, d.H, d.W, g.tz,
-                                           lncc_image_bits(window), cc_eps, window, wc ? 1 : 0);
+    const int bits = lncc_image_bits(window);
+    Maps mp{};
+    using ST = K1S<R, K1_NW, K1_OPT, K1_ST_TMA>;
+    const bool tma = tmap(&mp.a, If, 4, d, 1, ST::BXW, ST::RY, 1) &&
+                     tmap(&mp.b, J, 4, d, 1, ST::BXW, ST::RY, 1) &&
+                     tmap(&mp.c, sI, 8, d, 1, FX, ST::TY, 1) &&
+                     tmap(&mp.d, varI, 4, d, 1, FX, ST::TY, 1);
+    if (tma) {
+        auto kern = k_lncc_fwd<R, K1_NW, K1_OPT, K1_ST_TMA, true>;
+        static const int occ = prepare(kern, ST::bytes, ST::NT);
+        LaunchGeom g = geometry(occ, K1_NW, ST::TY, R, d);
+        kern<<<g.grid, g.block, ST::bytes, s>>>(mp, If, J, sI, varI, coef, h, d.D, d.H, d.W, g.tz,
+                                                bits, cc_eps, window, wc ? 1 : 0);
+    } else {
+        using SC = K1S<R, K1_NW, K1_OPT, K1_ST_CP>;
+        auto kern = k_lncc_fwd<R, K1_NW, K1_OPT, K1_ST_CP, false>;
+        static const int occ = prepare(kern, SC::bytes, SC::NT);
+        LaunchGeom g = geometry(occ, K1_NW, SC::TY, R, d);
+        kern<<<g.grid, g.block, SC::bytes, s>>>(mp, If, J, sI, varI, coef, h, d.D, d.H, d.W, g.tz,
+                                                bits, cc_eps, window, wc ? 1 : 0);
+    }
     note_launch();
     return cudaGetLastError();
 }
 
 template <int R>
 cudaError_t launch_k2(const float *If, const float *Im, const float *u, const float *coef,
-                      const WsHeader *h, float *g, Dims d, int window, cudaStream_t s) {
-    using S = K2S<R, K2_NW, K2_OPT, K2_ST>;
-    auto kern = k_lncc_grad<R, K2_NW, K2_OPT, K2_ST>;
-    static const int occ = prepare(kern, S::bytes, S::NT);
-    LaunchGeom gg = geometry(occ, K2_NW, S::TY, R, d);
-    kern<<<gg.grid, gg.block, S::bytes, s>>>(If, Im, u, coef, h, g, d.D, d.H, d.W, gg.tz,
-                                             lncc_coef_bits(window));
+                      WsHeader *h, float *g, Dims d, int window, cudaStream_t s) {
+    const int cb = lncc_coef_bits(window);
+    Maps mp{};
+    using ST = K2S<R, K2_NW, K2_OPT, K2_ST_TMA>;
+    const bool tma = tmap(&mp.a, coef, 4, d, 4, ST::BXW, ST::RY, 4) &&
+                     tmap(&mp.b, u, 4, d, 3, FX, ST::TY, 3) &&
+                     tmap(&mp.c, If, 4, d, 1, FX, ST::TY, 1);
+    if (tma) {
+        auto kern = k_lncc_grad<R, K2_NW, K2_OPT, K2_ST_TMA, true>;
+        static const int occ = prepare(kern, ST::bytes, ST::NT);
+        LaunchGeom gg = geometry(occ, K2_NW, ST::TY, R, d);
+        kern<<<gg.grid, gg.block, ST::bytes, s>>>(mp, If, Im, u, coef, h, g, d.D, d.H, d.W, gg.tz,
+                                                  cb);
+    } else {
+        using SC = K2S<R, K2_NW, K2_OPT, K2_ST_CP>;
+        auto kern = k_lncc_grad<R, K2_NW, K2_OPT, K2_ST_CP, false>;
+        static const int occ = prepare(kern, SC::bytes, SC::NT);
+        LaunchGeom gg = geometry(occ, K2_NW, SC::TY, R, d);
+        kern<<<gg.grid, gg.block, SC::bytes, s>>>(mp, If, Im, u, coef, h, g, d.D, d.H, d.W, gg.tz,
+                                                  cb);
+    }
     note_launch();
     return cudaGetLastError();
 }
@@ -1072,11 +1437,25 @@ cudaError_t launch_k2(const float *If, const float *Im, const float *u, const fl
 template <int RG>
 cudaError_t launch_k3(const float *g, float *m, float *v, float *dir, WsHeader *h, Dims d,
                       const GaussTaps &t, AdamConsts ac, int parity, cudaStream_t s) {
-    using S = K3S<RG, K3_NW, K3_OPT, K3_ST>;
-    auto kern = k_smooth_adam<RG, K3_NW, K3_OPT, K3_ST>;
-    static const int occ = prepare(kern, S::bytes, S::NT);
-    LaunchGeom gg = geometry(occ, K3_NW, S::TY, RG, d);
-    kern<<<gg.grid, gg.block, S::bytes, s>>>(g, m, v, dir, h, d.D, d.H, d.W, gg.tz, t, ac, parity);
+    Maps mp{};
+    using ST = K3S<RG, K3_NW, K3_OPT, K3_ST_TMA>;
+    const bool tma = tmap(&mp.a, g, 4, d, 3, ST::BXW, ST::RY, 3) &&
+                     tmap(&mp.b, m, 4, d, 3, FX, ST::TY, 3) &&
+                     tmap(&mp.c, v, 4, d, 3, FX, ST::TY, 3);
+    if (tma) {
+        auto kern = k_smooth_adam<RG, K3_NW, K3_OPT, K3_ST_TMA, true>;
+        static const int occ = prepare(kern, ST::bytes, ST::NT);
+        LaunchGeom gg = geometry(occ, K3_NW, ST::TY, RG, d);
+        kern<<<gg.grid, gg.block, ST::bytes, s>>>(mp, g, m, v, dir, h, d.D, d.H, d.W, gg.tz, t, ac,
+                                                  parity);
+    } else {
+        using SC = K3S<RG, K3_NW, K3_OPT, K3_ST_CP>;
+        auto kern = k_smooth_adam<RG, K3_NW, K3_OPT, K3_ST_CP, false>;
+        static const int occ = prepare(kern, SC::bytes, SC::NT);
+        LaunchGeom gg = geometry(occ, K3_NW, SC::TY, RG, d);
+        kern<<<gg.grid, gg.block, SC::bytes, s>>>(mp, g, m, v, dir, h, d.D, d.H, d.W, gg.tz, t, ac,
+                                                  parity);
+    }
     note_launch();
     return cudaGetLastError();
 }
@@ -1085,12 +1464,24 @@ template <int RG, bool SU>
 cudaError_t launch_k4(const float *u, const float *dir, float *uo, const float *Im, float *J,
                       WsHeader *h, Dims d, const GaussTaps &t, float lr, float c_lp, int parity,
                       cudaStream_t s) {
-    using S = K4S<RG, K4_NW, K4_OPT, SU, K4_ST>;
-    auto kern = k_compose<RG, K4_NW, K4_OPT, SU, K4_ST>;
-    static const int occ = prepare(kern, S::bytes, S::NT);
-    LaunchGeom gg = geometry(occ, K4_NW, S::TY, RG, d);
-    kern<<<gg.grid, gg.block, S::bytes, s>>>(u, dir, uo, Im, J, h, d.D, d.H, d.W, gg.tz, t, lr,
-                                             c_lp, parity);
+    Maps mp{};
+    using ST = K4S<RG, K4_NW, K4_OPT, SU, K4_ST_TMA>;
+    const bool tma = tmap(&mp.a, dir, 4, d, 3, ST::BXW, ST::RY, 3) &&
+                     (!SU || tmap(&mp.b, u, 4, d, 3, ST::UBXW, ST::URY, 3));
+    if (tma) {
+        auto kern = k_compose<RG, K4_NW, K4_OPT, SU, K4_ST_TMA, true>;
+        static const int occ = prepare(kern, ST::bytes, ST::NT);
+        LaunchGeom gg = geometry(occ, K4_NW, ST::TY, RG, d);
+        kern<<<gg.grid, gg.block, ST::bytes, s>>>(mp, u, dir, uo, Im, J, h, d.D, d.H, d.W, gg.tz,
+                                                  t, lr, c_lp, parity);
+    } else {
+        using SC = K4S<RG, K4_NW, K4_OPT, SU, K4_ST_CP>;
+        auto kern = k_compose<RG, K4_NW, K4_OPT, SU, K4_ST_CP, false>;
+        static const int occ = prepare(kern, SC::bytes, SC::NT);
+        LaunchGeom gg = geometry(occ, K4_NW, SC::TY, RG, d);
+        kern<<<gg.grid, gg.block, SC::bytes, s>>>(mp, u, dir, uo, Im, J, h, d.D, d.H, d.W, gg.tz,
+                                                  t, lr, c_lp, parity);
+    }
     note_launch();
     return cudaGetLastError();
 }
@@ -1118,7 +1509,7 @@ cudaError_t dispatch_k1(const float *If, const float *J, const long long *sI, co
 }
 
 cudaError_t dispatch_k2(const float *If, const float *Im, const float *u, const float *coef,
-                        const WsHeader *h, float *g, Dims d, int window, cudaStream_t s) {
+                        WsHeader *h, float *g, Dims d, int window, cudaStream_t s) {
     switch (window / 2) {
         FA_CASE(0, (launch_k2<RR>(If, Im, u, coef, h, g, d, window, s)))
         FA_CASE(1, (launch_k2<RR>(If, Im, u, coef, h, g, d, window, s)))

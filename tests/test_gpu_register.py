@@ -79,7 +79,9 @@ def test_nonfinite_input_is_reported(fa, mode):
 
 @pytest.mark.parametrize("mode", ["plain", "fused"])
 def test_tiny_and_degenerate_grids(fa, orc, mode):
-    for shape in [(1, 1, 1), (1, 4, 9), (3, 2, 5)]:
+    # widths that are multiples of 4 take the tile-copy (TMA) path with boxes
+    # larger than the grid; the others take the per-thread copy path
+    for shape in [(1, 1, 1), (1, 4, 9), (3, 2, 5), (2, 3, 4), (5, 6, 8)]:
         r = np.random.default_rng(9)
         f = r.random(shape).astype(np.float32)
         m = r.random(shape).astype(np.float32)
@@ -92,17 +94,19 @@ def test_tiny_and_degenerate_grids(fa, orc, mode):
         assert mean_disp_diff(out["u"], ref["u"]) < 0.05
 
 
+@pytest.mark.parametrize("shape", [(37, 45, 53), (40, 48, 56)])
 @pytest.mark.parametrize("kw", [
     dict(),                                         # the brain workload's hyper-parameters
     dict(window=7, sigma_grad=2.0, sigma_warp=0.0),  # wider window, no warp smoothing
     dict(window=3, sigma_grad=3.0, sigma_warp=2.5),  # Gaussians wider than the fused rings
     dict(loss="mse", sigma_grad=0.5),
 ])
-def test_fused_equals_plain(fa, kw):
+def test_fused_equals_plain(fa, kw, shape):
     """Both schedules compute the same arithmetic in the same order, so their
     results agree to float32 rounding over a whole multi-level run on a
-    ragged brain-shaped grid."""
-    f, m, _ = synth.voronoi_pair(shape=(37, 45, 53), seed=31)
+    brain-shaped grid: ragged (per-thread copies) and with widths that are
+    multiples of 4 (tile copies)."""
+    f, m, _ = synth.voronoi_pair(shape=shape, seed=31)
     base = dict(scales=(2, 1), iters=(15, 8))
     base.update(kw)
     a = fa.fa_register(cuda(f), cuda(m), fa.RegParams(mode="plain", **base))
