@@ -33,17 +33,20 @@ WORKLOAD = dict(name="voronoi_brain_160x192x224", shape=(160, 192, 224), scales=
 METRIC = "voxel-iters/s"
 L2_BYTES = 129 * 1024 * 1024
 HBM_FALLBACK_GBS = 6800.0
-# algorithmic bytes per voxel of one launch of each timed kernel (fp32
-# storage)
+# algorithmic bytes per voxel of one launch of each timed kernel: every input
+# field read once, every output field written once (fp32 storage, S_I int64)
 ALGO_BYTES = {
-    "fused_warp_lncc": 4 * (3 + 1 + 1 + 3),          # u, I_f, I_m read; A, B, C written
-    "fused_lncc_grad": 4 * (3 + 3 + 1 + 1 + 3),      # A, B, C, u, I_f, I_m read; g written
-    "fused_smooth_adam": 4 * (3 + 3 + 3 + 3 + 3 + 3),  # g, m, v read; m, v, d written
-    "fused_compose": 4 * (3 + 3 + 3),                # d, u read; u written
-    "plain_iteration": 80,                           # whole plain iteration (I_f, I_m, u, m, v)
+    "fused_warp_lncc": 4 + 4 + 8 + 4 + 16,      # I_f, J, S_I, var_I read; A, B, C hi/lo written
+    "fused_lncc_grad": 16 + 12 + 4 + 4 + 12,    # A, B, C hi/lo, u, I_f, I_m read; g written
+    "fused_smooth_adam": 12 * 3 + 12 * 3,       # g, m, v read; m, v, d written
+    "fused_compose": 12 + 12 + 4 + 12 + 4,      # d, u, I_m read; u', J written
+    "plain_iteration": 80,                      # whole iteration: I_f, I_m, u, m, v once
 }
+# the whole path per voxel-iteration: read I_f, I_m, u, m, v, write u, m, v
+PATH_BYTES = 80
 KERNEL_IDS = {"fused_warp_lncc": 0, "fused_lncc_grad": 1, "fused_smooth_adam": 2,
               "fused_compose": 3, "plain_iteration": 4}
+FUSED_KERNELS = ("fused_warp_lncc", "fused_lncc_grad", "fused_smooth_adam", "fused_compose")
 
 
 def level_size(n, s):
@@ -221,14 +224,22 @@ def run_gpu(args):
         fa.fa_register(fixed, moving, params, ws=ws, sync=False, u_out=u, loss_out=loss)
     torch.cuda.synchronize()
 
-    # kernel timer: the dominant kernel on the finest level, every step
+    # kernel timers on the finest level: the fused kernels take turns, one
+    # kernel per timed step (plain mode: the whole plain iteration)
     fin = len(WORKLOAD["scales"]) - 1
-    kname = "plain_iteration" if args.mode == "plain" else args.kernel
-    kid = KERNEL_IDS[kname]
-    cap = WORKLOAD["iters"][fin] * args.steps
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(cap)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(cap)]
-    timer = fa.make_timer(kid, fin, ev0, ev1)
+    if args.mode == "plain":
+        knames = ["plain_iteration"]
+    elif args.kernel == "dominant":
+        knames = list(FUSED_KERNELS)
+    else:
+        knames = [args.kernel]
+    timers = {}
+    for j, kn in enumerate(knames):
+        nsteps = len(range(j, args.steps, len(knames)))
+        cap = max(1, WORKLOAD["iters"][fin] * nsteps)
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(cap)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(cap)]
+        timers[kn] = (fa.make_timer(KERNEL_IDS[kn], fin, ev0, ev1), ev0, ev1)
     step0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     step1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     bus = None
@@ -248,7 +259,7 @@ def run_gpu(args):
         flush.zero_()
         step0[k].record(stream)
         fa.fa_register(fixed, moving, params, ws=ws, sync=False, u_out=u, loss_out=loss,
-                       timer=timer)
+                       timer=timers[knames[k % len(knames)]][0])
         step1[k].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
@@ -266,18 +277,33 @@ def run_gpu(args):
     vi = voxel_iters(shape, WORKLOAD["scales"], WORKLOAD["iters"])
     value = world * vi * args.steps / (total_ms / 1e3)
 
-    # dominant kernel roofline (finest level launches of every timed step)
-    kt = [ev0[i].elapsed_time(ev1[i]) for i in range(timer.count)]
+    # per-kernel rooflines from the finest-level launches of the timed steps;
+    # the reported one is the kernel with the longest average launch (each
+    # runs once per iteration)
     n_fine = int(np.prod([level_size(a, WORKLOAD["scales"][fin]) for a in shape]))
     peak, peak_kind = measured_peak()
-    algo = ALGO_BYTES[kname] * n_fine
-    avg_ms = float(np.mean(kt)) if kt else float("nan")
-    achieved = algo / (avg_ms / 1e3) / 1e9
-    traffic = traffic_from_profile(kname, n_fine)
-    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
-                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "algo_bytes": algo, "avg_launch_ms": avg_ms,
-                "launches_timed": len(kt)}
+    kernels = {}
+    for kn, (tm, ev0, ev1) in timers.items():
+        kt = [ev0[i].elapsed_time(ev1[i]) for i in range(tm.count)]
+        if not kt:
+            continue
+        avg_ms = float(np.mean(kt))
+        algo = ALGO_BYTES[kn] * n_fine
+        achieved = algo / (avg_ms / 1e3) / 1e9
+        kernels[kn] = {"avg_launch_ms": avg_ms, "launches_timed": len(kt), "algo_bytes": algo,
+                       "achieved": achieved, "frac": achieved / peak,
+                       "traffic": traffic_from_profile(kn, n_fine)}
+    kname = max(kernels, key=lambda k: kernels[k]["avg_launch_ms"])
+    kd = kernels[kname]
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": kd["achieved"], "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": kd["frac"],
+                "traffic": kd["traffic"], "algo_bytes": kd["algo_bytes"],
+                "avg_launch_ms": kd["avg_launch_ms"], "launches_timed": kd["launches_timed"],
+                "all_kernels": {k: {"avg_launch_ms": round(v["avg_launch_ms"], 4),
+                                    "frac": round(v["frac"], 4)} for k, v in kernels.items()},
+                "path": {"bytes_per_voxel_iter": PATH_BYTES,
+                         "achieved": PATH_BYTES * vi * args.steps / (total_ms / 1e3) / 1e9,
+                         "frac": PATH_BYTES * vi * args.steps / (total_ms / 1e3) / 1e9 / peak}}
 
     # end to end: host buffers in, displacement and loss out
     fh = torch.from_numpy(f).pin_memory()
@@ -337,8 +363,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="fused", choices=["fused", "plain"])
     ap.add_argument("--cpu-iters", type=int, default=2)
-    ap.add_argument("--kernel", default="fused_warp_lncc", choices=sorted(ALGO_BYTES),
-                    help="fused kernel whose finest-level launches are timed for the roofline")
+    ap.add_argument("--kernel", default="dominant", choices=["dominant"] + sorted(ALGO_BYTES),
+                    help="kernel whose finest-level launches are timed for the roofline "
+                         "(dominant: all four fused kernels, one per timed step)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--scales", type=int, nargs="+", default=None,
                     help="override the pyramid scales (profiling runs; changes the workload)")
