@@ -384,28 +384,31 @@ __device__ __forceinline__ void zslide(long long *ring, int slot, int tid,
         }
 }
 
-// Ring of the last NS in-plane results, every slot stored twice (k, k + NS)
-// so that the z window is contiguous.  Returns the first slot of the window
-// (oldest plane first).
+// Ring of the last NS in-plane results of this thread's outputs, [NS][3][NOUT]
+// floats; slot `newest` holds the current plane.
 template <int NS, int OPT, int NOUT, int NT>
-__device__ __forceinline__ int ring_push(float *ring, int slot, int tid, const float Q[OPT][3]) {
+__device__ __forceinline__ void ring_put(float *ring, int newest, int tid, const float Q[OPT][3]) {
 #pragma unroll
     for (int o = 0; o < OPT; ++o)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float v = Q[o][c];
-            ring[(slot * 3 + c) * NOUT + o * NT + tid] = v;
-            ring[((slot + NS) * 3 + c) * NOUT + o * NT + tid] = v;
-        }
-    return slot + 1;
+        for (int c = 0; c < 3; ++c) ring[(newest * 3 + c) * NOUT + o * NT + tid] = Q[o][c];
 }
 
+// Weighted z window of all three channels of one output: tap k takes the
+// plane k - R of the window, i.e. ring slot (newest + 1 + k) mod NS.
 template <int RG, int NOUT>
-__device__ __forceinline__ float gauss_z(const float *win, const GaussTaps &t, int c) {
-    float s = 0.0f;
+__device__ __forceinline__ void gauss_z3(const float *ring_o, int newest, const GaussTaps &t,
+                                         float out[3]) {
+    constexpr int NS = 2 * RG + 1;
+    out[0] = out[1] = out[2] = 0.0f;
 #pragma unroll
-    for (int k = 0; k <= 2 * RG; ++k) s = fmaf(t.w[k], win[(k * 3 + c) * NOUT], s);
-    return s;
+    for (int k = 0; k < NS; ++k) {
+        int j = newest + 1 + k;
+        j = j >= NS ? j - NS : j;
+        const float *r = ring_o + j * 3 * NOUT;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) out[c] = fmaf(t.w[k], r[c * NOUT], out[c]);
+    }
 }
 
 // Bounded wait, by thread 0, for the copies of planes i .. i + NSTG - 1 that
@@ -852,7 +855,7 @@ struct K3S {
     static constexpr size_t o_st = 0;
     static constexpr size_t o_ost = o_st + st_bytes * NSTG;
     static constexpr size_t o_ring = o_ost + ost_bytes * NSTG;
-    static constexpr size_t o_xb = o_ring + (size_t)2 * NS * 3 * NOUT * 4;
+    static constexpr size_t o_xb = o_ring + (size_t)NS * 3 * NOUT * 4;
     static constexpr size_t o_bar = al128(o_xb + (size_t)3 * RY * FX * 4);
     static constexpr size_t bytes = o_bar + 8 * NSTG;
 };
@@ -891,7 +894,7 @@ __global__ void __launch_bounds__(FX *NW) k_smooth_adam(const __grid_constant__ 
         for (int k = 0; k < NSTG; ++k) mbar_init(bar + k);
         mbar_init_fence();
     }
-    for (int k = tid; k < 2 * NS * 3 * NOUT; k += NT) ring[k] = 0.0f;
+    for (int k = tid; k < NS * 3 * NOUT; k += NT) ring[k] = 0.0f;
     if (timed_out(h, tid, &flag)) return;
 
     const int zs = z0 - RG, np = zend - z0 + 2 * RG;
@@ -958,19 +961,21 @@ __global__ void __launch_bounds__(FX *NW) k_smooth_adam(const __grid_constant__ 
 #pragma unroll
             for (int o = 0; o < OPT; ++o) Q[o][0] = Q[o][1] = Q[o][2] = 0.0f;
         }
-        const int wbase = ring_push<NS, OPT, NOUT, NT>(ring, slot, tid, Q);
+        ring_put<NS, OPT, NOUT, NT>(ring, slot, tid, Q);
+        const int newest = slot;
         slot = (slot + 1 == NS) ? 0 : slot + 1;
         if (out) {
             const long long zoff = (long long)zo * HW;
 #pragma unroll
             for (int o = 0; o < OPT; ++o) {
                 if (ou.off[o] < 0) continue;
-                const float *win = ring + wbase * 3 * NOUT + o * NT + tid;
+                float sz[3];
+                gauss_z3<RG, NOUT>(ring + o * NT + tid, newest, t, sz);
                 const long long gi = zoff + ou.off[o];
                 float nrm2 = 0.0f;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float sg = gauss_z<RG, NOUT>(win, t, c);
+                    const float sg = sz[c];
                     const float mvv = fmaf(ac.b1, mo[o][c], (1.0f - ac.b1) * sg);
                     const float vvv = fmaf(ac.b2, vo[o][c], (1.0f - ac.b2) * sg * sg);
                     m[c * N + gi] = mvv;
@@ -1015,7 +1020,7 @@ struct K4S {
     static constexpr size_t o_st = 0;
     static constexpr size_t o_ust = o_st + st_bytes * NSTG;
     static constexpr size_t o_ring = o_ust + (SU ? ust_bytes * NSU : 0);
-    static constexpr size_t o_xb = o_ring + (size_t)2 * NS * 3 * NOUT * 4;
+    static constexpr size_t o_xb = o_ring + (size_t)NS * 3 * NOUT * 4;
     static constexpr size_t o_up = o_xb + (size_t)3 * RY * FX * 4;
     static constexpr size_t o_bar = al128(o_up + (size_t)3 * NR * 4);
     static constexpr size_t bytes = o_bar + 8 * (NSTG + 1);
@@ -1064,7 +1069,7 @@ __global__ void __launch_bounds__(FX *NW) k_compose(const __grid_constant__ Maps
         for (int k = 0; k <= NSTG; ++k) mbar_init(bar + k);
         mbar_init_fence();
     }
-    for (int k = tid; k < 2 * NS * 3 * NOUT; k += NT) ring[k] = 0.0f;
+    for (int k = tid; k < NS * 3 * NOUT; k += NT) ring[k] = 0.0f;
     if (timed_out(h, tid, &flag)) return;
 
     const int zs = z0 - RG, np = zend - z0 + 2 * RG;
@@ -1193,7 +1198,8 @@ __global__ void __launch_bounds__(FX *NW) k_compose(const __grid_constant__ Maps
 #pragma unroll
             for (int o = 0; o < OPT; ++o) Q[o][0] = Q[o][1] = Q[o][2] = 0.0f;
         }
-        const int wbase = ring_push<NS, OPT, NOUT, NT>(ring, slot, tid, Q);
+        ring_put<NS, OPT, NOUT, NT>(ring, slot, tid, Q);
+        const int newest = slot;
         slot = (slot + 1 == NS) ? 0 : slot + 1;
         if (zo >= z0 && zo < zend) {
             const long long zoff = (long long)zo * HW;
@@ -1206,11 +1212,10 @@ __global__ void __launch_bounds__(FX *NW) k_compose(const __grid_constant__ Maps
                     jlive[o] = false;
                 }
                 if (ou.off[o] < 0) continue;
-                const float *win = ring + wbase * 3 * NOUT + o * NT + tid;
+                float sz[3];
+                gauss_z3<RG, NOUT>(ring + o * NT + tid, newest, t, sz);
                 const long long gi = zoff + ou.off[o];
-                const float a = gauss_z<RG, NOUT>(win, t, 0);
-                const float b = gauss_z<RG, NOUT>(win, t, 1);
-                const float c = gauss_z<RG, NOUT>(win, t, 2);
+                const float a = sz[0], b = sz[1], c = sz[2];
                 uo[gi] = a;
                 uo[N + gi] = b;
                 uo[2 * N + gi] = c;
@@ -1284,6 +1289,8 @@ int choose_tz(int D, int tiles_xy, int halo, int ctas_per_sm) {
 template <class K>
 int prepare(K kernel, size_t smem, int threads) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         (int)cudaSharedmemCarveoutMaxShared);
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess ||
         n < 1)
@@ -1374,9 +1381,9 @@ bool tmap(CUtensorMap *m, const void *base, int esize, Dims d, int C, int bx, in
 // tile shapes (warps per CTA, outputs per thread along y) and pipeline depths
 // of the TMA and of the cp.async variant
 constexpr int K1_NW = 8, K1_OPT = 1, K1_ST_TMA = 3, K1_ST_CP = 3;
-constexpr int K2_NW = 8, K2_OPT = 1, K2_ST_TMA = 3, K2_ST_CP = 2;
-constexpr int K3_NW = 8, K3_OPT = 1, K3_ST_TMA = 3, K3_ST_CP = 2;
-constexpr int K4_NW = 8, K4_OPT = 1, K4_ST_TMA = 3, K4_ST_CP = 2;
+constexpr int K2_NW = 8, K2_OPT = 1, K2_ST_TMA = 2, K2_ST_CP = 2;
+constexpr int K3_NW = 8, K3_OPT = 1, K3_ST_TMA = 2, K3_ST_CP = 2;
+constexpr int K4_NW = 8, K4_OPT = 1, K4_ST_TMA = 2, K4_ST_CP = 2;
 
 template <int R>
 cudaError_t launch_k1(const float *If, const float *J, const long long *sI, const float *varI,
