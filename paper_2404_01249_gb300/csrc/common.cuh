@@ -206,12 +206,13 @@ __host__ __device__ inline int lncc_image_bits(int window) {
 }
 
 // Bits of the quantised LNCC adjoint coefficients: 3-D sums stay below 2^47
-// so that they convert to float-float exactly.
+// so that they convert to float-float exactly, and every quantised value
+// stays below 2^41 (the range of quantize below).
 __host__ __device__ inline int lncc_coef_bits(int window) {
     long long n = (long long)window * window * window;
     int lg = 0;
     while ((1ll << lg) < n) ++lg;
-    return 47 - lg;
+    return 47 - lg < 41 ? 47 - lg : 41;
 }
 
 // Exponent s with max|v| * 2^s <= 2^bits (0 if amax is 0 or not finite).
@@ -223,15 +224,36 @@ __device__ __forceinline__ int fixed_shift(float amax, int bits) {
     return s < -126 ? -126 : (s > 127 ? 127 : s);
 }
 
-// q = rint(v * scale) with scale = pow2f(s) (exact scaling).
+// q = rint(v * scale) (round half to even) for |v * scale| < 2^42, scale a
+// power of two.  Built from FP32 adds instead of the 64-bit float-to-integer
+// conversion, which issues at a small fraction of the ALU rate on sm_103:
+// adding and subtracting 1.5 * 2^43 rounds x to a multiple of 2^20, the
+// remainder (exact, |r| <= 2^19) is rounded by adding 1.5 * 2^23, and both
+// integers are read from the bits of floats in the binade [2^23, 2^24).
 __device__ __forceinline__ long long quantize(float v, float scale) {
-    return __float2ll_rn(v * scale);
+    const float x = v * scale;
+    const float M43 = 13194139533312.0f, M23 = 12582912.0f;
+    const float h = __fsub_rn(__fadd_rn(x, M43), M43);
+    const float r = __fsub_rn(x, h);
+    const int k = __float_as_int(__fmaf_rn(h, 9.5367431640625e-07f, M23)) - 0x4B400000;
+    const int l = __float_as_int(__fadd_rn(r, M23)) - 0x4B400000;
+    return ((long long)k << 20) + l;
+}
+
+// Exact int64 value of an integer-valued float with |f| < 2^63, from its bits.
+__device__ __forceinline__ long long float_int_to_ll(float f) {
+    const unsigned b = __float_as_uint(f);
+    const int ex = (int)((b >> 23) & 0xffu) - 150;
+    const long long m = (long long)((b & 0x7fffffu) | 0x800000u);
+    long long r = ex >= 0 ? (m << (ex & 63)) : (m >> ((-ex) & 63));
+    r = (b & 0x7fffffffu) ? r : 0;
+    return (b >> 31) ? -r : r;
 }
 
 // int64 -> (hi, lo) floats with hi + lo == x exactly for |x| < 2^48.
 __device__ __forceinline__ void i64_to_ff(long long x, float &hi, float &lo) {
     hi = __ll2float_rn(x);
-    lo = __ll2float_rn(x - __float2ll_rn(hi));
+    lo = __ll2float_rn(x - float_int_to_ll(hi));
 }
 
 // n a - b c for int64 operands, formed exactly in 128 bits and rounded to

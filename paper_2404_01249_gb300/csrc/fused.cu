@@ -1138,57 +1138,58 @@ __global__ void __launch_bounds__(FX *NW) k_compose(const __grid_constant__ Maps
         if (zp >= 0 && zp < D) {
             const float *ds = stage(s);
             const float *um = uslot(zp - 1), *u0 = uslot(zp), *u1 = uslot(zp + 1);
-            // u' on the RY x RX region, at the plane layout's columns
+            // u' on the RY x RX region (positions spread over all threads),
+            // at the plane layout's columns
+            constexpr int NP = RY * RX;
 #pragma unroll
-            for (int j = 0; j < G::NJ; ++j)
+            for (int j = 0; j < (NP + NT - 1) / NT; ++j) {
+                const int pidx = tid + j * NT;
+                if (NP % NT != 0 && pidx >= NP) break;
+                const int ry = pidx / RX, rx = pidx - ry * RX;
+                const int y = y0 - RG + ry, x = x0 - RG + rx;
+                const int k = ry * BXW + rx + COFF;
+                float a = 0.f, b = 0.f, c = 0.f;
+                if (y >= 0 && y < H && x >= 0 && x < W) {
+                    const float dz = -e * ds[k], dy = -e * ds[NR + k], dx = -e * ds[2 * NR + k];
+                    if (SU) {
+                        // cell corners lie within one voxel: planes zp-1..zp+1
+                        if (dz > -1.0f && dz < 1.0f && dy > -1.0f && dy < 1.0f &&
+                            dx > -1.0f && dx < 1.0f) {
+                            const float fz = floorf(dz), fy = floorf(dy), fx = floorf(dx);
+                            const float tz = dz - fz, ty = dy - fy, tx2 = dx - fx;
+                            const float *pa = fz < 0.0f ? um : u0;
+                            const float *pb = fz < 0.0f ? u0 : u1;
+                            const int b0 = (ry + 1 + (int)fy) * UBXW + (rx + 1 + (int)fx) + UCOFF;
+                            float r[3];
 #pragma unroll
-                for (int cc = 0; cc < G::NC; ++cc) {
-                    const int ry = wy + NW * j, rx = tx + 32 * cc;
-                    if (ry >= RY || rx >= RX) continue;
-                    const int y = y0 - RG + ry, x = x0 - RG + rx;
-                    const int k = ry * BXW + rx + COFF;
-                    float a = 0.f, b = 0.f, c = 0.f;
-                    if (y >= 0 && y < H && x >= 0 && x < W) {
-                        const float dz = -e * ds[k], dy = -e * ds[NR + k], dx = -e * ds[2 * NR + k];
-                        if (SU) {
-                            // cell corners lie within one voxel: planes zp-1..zp+1
-                            if (dz > -1.0f && dz < 1.0f && dy > -1.0f && dy < 1.0f &&
-                                dx > -1.0f && dx < 1.0f) {
-                                const float fz = floorf(dz), fy = floorf(dy), fx = floorf(dx);
-                                const float tz = dz - fz, ty = dy - fy, tx2 = dx - fx;
-                                const float *pa = fz < 0.0f ? um : u0;
-                                const float *pb = fz < 0.0f ? u0 : u1;
-                                const int b0 = (ry + 1 + (int)fy) * UBXW + (rx + 1 + (int)fx) + UCOFF;
-                                float r[3];
-#pragma unroll
-                                for (int ch = 0; ch < 3; ++ch) {
-                                    const float *A = pa + ch * NRU + b0, *B = pb + ch * NRU + b0;
-                                    const float c00 = fmaf(tx2, A[1] - A[0], A[0]);
-                                    const float c01 = fmaf(tx2, A[UBXW + 1] - A[UBXW], A[UBXW]);
-                                    const float c10 = fmaf(tx2, B[1] - B[0], B[0]);
-                                    const float c11 = fmaf(tx2, B[UBXW + 1] - B[UBXW], B[UBXW]);
-                                    const float c0 = fmaf(ty, c01 - c00, c00);
-                                    const float c1 = fmaf(ty, c11 - c10, c10);
-                                    r[ch] = fmaf(tz, c1 - c0, c0);
-                                }
-                                a = dz + r[0];
-                                b = dy + r[1];
-                                c = dx + r[2];
-                            } else {
-                                a = b = c = __int_as_float(0x7fc00000);  // impossible step: flag it
+                            for (int ch = 0; ch < 3; ++ch) {
+                                const float *A = pa + ch * NRU + b0, *B = pb + ch * NRU + b0;
+                                const float c00 = fmaf(tx2, A[1] - A[0], A[0]);
+                                const float c01 = fmaf(tx2, A[UBXW + 1] - A[UBXW], A[UBXW]);
+                                const float c10 = fmaf(tx2, B[1] - B[0], B[0]);
+                                const float c11 = fmaf(tx2, B[UBXW + 1] - B[UBXW], B[UBXW]);
+                                const float c0 = fmaf(ty, c01 - c00, c00);
+                                const float c1 = fmaf(ty, c11 - c10, c10);
+                                r[ch] = fmaf(tz, c1 - c0, c0);
                             }
+                            a = dz + r[0];
+                            b = dy + r[1];
+                            c = dx + r[2];
                         } else {
-                            float gz, gy, gx;
-                            a = dz + tri_sample<false>(u, D, H, W, zp, y, x, dz, dy, dx, gz, gy, gx);
-                            b = dy + tri_sample<false>(u + N, D, H, W, zp, y, x, dz, dy, dx, gz, gy,
-                                                       gx);
-                            c = dx + tri_sample<false>(u + 2 * N, D, H, W, zp, y, x, dz, dy, dx, gz,
-                                                       gy, gx);
+                            a = b = c = __int_as_float(0x7fc00000);  // impossible step: flag it
                         }
+                    } else {
+                        float gz, gy, gx;
+                        a = dz + tri_sample<false>(u, D, H, W, zp, y, x, dz, dy, dx, gz, gy, gx);
+                        b = dy + tri_sample<false>(u + N, D, H, W, zp, y, x, dz, dy, dx, gz, gy,
+                                                   gx);
+                        c = dx + tri_sample<false>(u + 2 * N, D, H, W, zp, y, x, dz, dy, dx, gz,
+                                                   gy, gx);
                     }
-                    up[k] = a;
-                    up[NR + k] = b;
-                    up[2 * NR + k] = c;
+                }
+                up[k] = a;
+                up[NR + k] = b;
+                up[2 * NR + k] = c;
                 }
             __syncthreads();
             gauss_x4<RG, 3, RY, BXW, COFF, NT>(up, xb, t, tid);
