@@ -147,16 +147,17 @@ __device__ __forceinline__ void tri_issue(TriPending &p, const float *__restrict
     const bool z0 = iz >= 0, z1 = iz + 1 < D;
     const bool y0 = iy >= 0, y1 = iy + 1 < H;
     const bool x0 = ix >= 0, x1 = ix + 1 < W;
-    const long long HW = (long long)H * W;
-    const long long b = (long long)iz * HW + (long long)iy * W + ix;
-    if (z0 && y0 && x0) p.c000 = __ldg(v + b);
-    if (z0 && y0 && x1) p.c001 = __ldg(v + b + 1);
-    if (z0 && y1 && x0) p.c010 = __ldg(v + b + W);
-    if (z0 && y1 && x1) p.c011 = __ldg(v + b + W + 1);
-    if (z1 && y0 && x0) p.c100 = __ldg(v + b + HW);
-    if (z1 && y0 && x1) p.c101 = __ldg(v + b + HW + 1);
-    if (z1 && y1 && x0) p.c110 = __ldg(v + b + HW + W);
-    if (z1 && y1 && x1) p.c111 = __ldg(v + b + HW + W + 1);
+    // 32-bit offsets: grids hold fewer than 2^31 voxels and iz >= -1
+    const int b = (iz * H + iy) * W + ix;
+    const float *q0 = v + b, *q1 = q0 + H * W;
+    if (z0 && y0 && x0) p.c000 = __ldg(q0);
+    if (z0 && y0 && x1) p.c001 = __ldg(q0 + 1);
+    if (z0 && y1 && x0) p.c010 = __ldg(q0 + W);
+    if (z0 && y1 && x1) p.c011 = __ldg(q0 + W + 1);
+    if (z1 && y0 && x0) p.c100 = __ldg(q1);
+    if (z1 && y0 && x1) p.c101 = __ldg(q1 + 1);
+    if (z1 && y1 && x0) p.c110 = __ldg(q1 + W);
+    if (z1 && y1 && x1) p.c111 = __ldg(q1 + W + 1);
 }
 
 template <bool GRAD>

@@ -124,10 +124,24 @@ struct alignas(64) Maps {
     CUtensorMap a, b, c, d;
 };
 
-// Uniform early exit of a CTA when an earlier CTA reported a timeout.
+// Programmatic dependent launch: the fused kernels are launched so that a
+// kernel's CTAs may start while the previous kernel in the stream finishes.
+// Everything before pdl_wait() touches no data the previous kernel writes;
+// pdl_wait() returns once that kernel has completed and its writes are
+// visible.  pdl_trigger() lets the next kernel begin launching once every
+// CTA of this one has started.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+// Waits for the previous kernel, then exits the CTA uniformly when an earlier
+// CTA reported a timeout.
 __device__ __forceinline__ bool timed_out(const WsHeader *h, int tid, int *flag) {
+    pdl_wait();
     if (tid == 0) *flag = (int)(*(volatile const unsigned *)&h->status & ST_TIMEOUT);
     __syncthreads();
+    pdl_trigger();
     return *flag != 0;
 }
 
@@ -467,10 +481,6 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const __grid_constant__ Map
     const int x0 = blockIdx.x * FX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
     const int zend = min(z0 + TZ, D);
     const long long N = (long long)D * H * W, HW = (long long)H * W;
-    const float amax =
-        fmaxf(__uint_as_float(h->absmax_bits[0]), __uint_as_float(h->absmax_bits[1]));
-    const int sh = fixed_shift(amax, bits);
-    const float scale = pow2f(sh), inv_s = pow2f(-sh);
     const long long n = (long long)window * window * window;
     const float nf = (float)n, inv_nf = 1.0f / nf;
     G rg;
@@ -483,6 +493,10 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const __grid_constant__ Map
     }
     for (int k = tid; k < NS * 3 * NOUT; k += NT) ring[k] = 0;
     if (timed_out(h, tid, &flag)) return;
+    const float amax =
+        fmaxf(__uint_as_float(h->absmax_bits[0]), __uint_as_float(h->absmax_bits[1]));
+    const int sh = fixed_shift(amax, bits);
+    const float scale = pow2f(sh), inv_s = pow2f(-sh);
 
     long long acc[OPT][3];
 #pragma unroll
@@ -596,7 +610,7 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const __grid_constant__ Map
                 const float rden = __frcp_rn(den);
                 const float cc = cross * cross * rden;
                 if (cc >= 0.0f && cc <= 2.0f)
-                    qcc += (unsigned long long)__float2ull_rn(cc * 4294967296.0f);
+                    qcc += (unsigned long long)quantize(cc, 4294967296.0f);  // cc in [0, 2]
                 else
                     bad = true;
                 if (write_coef) {
@@ -678,13 +692,6 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_grad(const __grid_constant__ Ma
     const int x0 = blockIdx.x * FX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
     const int zend = min(z0 + TZ, D);
     const long long N = (long long)D * H * W, HW = (long long)H * W;
-    float qs[3], us[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const int e = fixed_shift(__uint_as_float(h->coef_max_bits[c]), cbits);
-        qs[c] = pow2f(e);
-        us[c] = pow2f(-e);
-    }
     const float inv_n = 1.0f / (float)N;
     G rg;
     if (!TMA) rg.init(wy, tx, y0 - R, x0 - R, H, W);
@@ -696,6 +703,13 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_grad(const __grid_constant__ Ma
     }
     for (int k = tid; k < NS * 3 * NOUT; k += NT) ring[k] = 0;
     if (timed_out(h, tid, &flag)) return;
+    float qs[3], us[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int e = fixed_shift(__uint_as_float(h->coef_max_bits[c]), cbits);
+        qs[c] = pow2f(e);
+        us[c] = pow2f(-e);
+    }
     long long acc[OPT][3];
 #pragma unroll
     for (int o = 0; o < OPT; ++o)
@@ -1055,8 +1069,6 @@ __global__ void __launch_bounds__(FX *NW) k_compose(const __grid_constant__ Maps
     const int x0 = blockIdx.x * FX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
     const int zend = min(z0 + TZ, D);
     const long long N = (long long)D * H * W, HW = (long long)H * W;
-    const float mxd = __uint_as_float(h->step_max_bits[parity]);
-    const float e = (mxd > 0.0f) ? lr / (c_lp * mxd) : 0.0f;
     G rg;
     GU rgu;
     if (!TMA) {
@@ -1071,6 +1083,8 @@ __global__ void __launch_bounds__(FX *NW) k_compose(const __grid_constant__ Maps
     }
     for (int k = tid; k < NS * 3 * NOUT; k += NT) ring[k] = 0.0f;
     if (timed_out(h, tid, &flag)) return;
+    const float mxd = __uint_as_float(h->step_max_bits[parity]);
+    const float e = (mxd > 0.0f) ? lr / (c_lp * mxd) : 0.0f;
 
     const int zs = z0 - RG, np = zend - z0 + 2 * RG;
     // u plane q lives in u stage (q - (zs - 1)) % NSU
@@ -1304,6 +1318,23 @@ struct LaunchGeom {
     int tz;
 };
 
+// Launch with programmatic stream serialization (see pdl_wait).
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), const LaunchGeom &g, size_t smem, cudaStream_t s,
+                       Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g.grid;
+    cfg.blockDim = g.block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 inline LaunchGeom geometry(int occ, int nw, int ty, int halo, Dims d) {
     LaunchGeom g;
     const int gx = (d.W + FX - 1) / FX, gy = (d.H + ty - 1) / ty;
@@ -1392,6 +1423,7 @@ cudaError_t launch_k1(const float *If, const float *J, const long long *sI, cons
                       cudaStream_t s) {
     const int bits = lncc_image_bits(window);
     Maps mp{};
+    cudaError_t le;
     using ST = K1S<R, K1_NW, K1_OPT, K1_ST_TMA>;
     const bool tma = tmap(&mp.a, If, 4, d, 1, ST::BXW, ST::RY, 1) &&
                      tmap(&mp.b, J, 4, d, 1, ST::BXW, ST::RY, 1) &&
@@ -1401,18 +1433,18 @@ cudaError_t launch_k1(const float *If, const float *J, const long long *sI, cons
         auto kern = k_lncc_fwd<R, K1_NW, K1_OPT, K1_ST_TMA, true>;
         static const int occ = prepare(kern, ST::bytes, ST::NT);
         LaunchGeom g = geometry(occ, K1_NW, ST::TY, R, d);
-        kern<<<g.grid, g.block, ST::bytes, s>>>(mp, If, J, sI, varI, coef, h, d.D, d.H, d.W, g.tz,
+        le = launch_pdl(kern, g, ST::bytes, s, mp, If, J, sI, varI, coef, h, d.D, d.H, d.W, g.tz,
                                                 bits, cc_eps, window, wc ? 1 : 0);
     } else {
         using SC = K1S<R, K1_NW, K1_OPT, K1_ST_CP>;
         auto kern = k_lncc_fwd<R, K1_NW, K1_OPT, K1_ST_CP, false>;
         static const int occ = prepare(kern, SC::bytes, SC::NT);
         LaunchGeom g = geometry(occ, K1_NW, SC::TY, R, d);
-        kern<<<g.grid, g.block, SC::bytes, s>>>(mp, If, J, sI, varI, coef, h, d.D, d.H, d.W, g.tz,
+        le = launch_pdl(kern, g, SC::bytes, s, mp, If, J, sI, varI, coef, h, d.D, d.H, d.W, g.tz,
                                                 bits, cc_eps, window, wc ? 1 : 0);
     }
     note_launch();
-    return cudaGetLastError();
+    return le;
 }
 
 template <int R>
@@ -1420,6 +1452,7 @@ cudaError_t launch_k2(const float *If, const float *Im, const float *u, const fl
                       WsHeader *h, float *g, Dims d, int window, cudaStream_t s) {
     const int cb = lncc_coef_bits(window);
     Maps mp{};
+    cudaError_t le;
     using ST = K2S<R, K2_NW, K2_OPT, K2_ST_TMA>;
     const bool tma = tmap(&mp.a, coef, 4, d, 4, ST::BXW, ST::RY, 4) &&
                      tmap(&mp.b, u, 4, d, 3, FX, ST::TY, 3) &&
@@ -1428,24 +1461,25 @@ cudaError_t launch_k2(const float *If, const float *Im, const float *u, const fl
         auto kern = k_lncc_grad<R, K2_NW, K2_OPT, K2_ST_TMA, true>;
         static const int occ = prepare(kern, ST::bytes, ST::NT);
         LaunchGeom gg = geometry(occ, K2_NW, ST::TY, R, d);
-        kern<<<gg.grid, gg.block, ST::bytes, s>>>(mp, If, Im, u, coef, h, g, d.D, d.H, d.W, gg.tz,
+        le = launch_pdl(kern, gg, ST::bytes, s, mp, If, Im, u, coef, h, g, d.D, d.H, d.W, gg.tz,
                                                   cb);
     } else {
         using SC = K2S<R, K2_NW, K2_OPT, K2_ST_CP>;
         auto kern = k_lncc_grad<R, K2_NW, K2_OPT, K2_ST_CP, false>;
         static const int occ = prepare(kern, SC::bytes, SC::NT);
         LaunchGeom gg = geometry(occ, K2_NW, SC::TY, R, d);
-        kern<<<gg.grid, gg.block, SC::bytes, s>>>(mp, If, Im, u, coef, h, g, d.D, d.H, d.W, gg.tz,
+        le = launch_pdl(kern, gg, SC::bytes, s, mp, If, Im, u, coef, h, g, d.D, d.H, d.W, gg.tz,
                                                   cb);
     }
     note_launch();
-    return cudaGetLastError();
+    return le;
 }
 
 template <int RG>
 cudaError_t launch_k3(const float *g, float *m, float *v, float *dir, WsHeader *h, Dims d,
                       const GaussTaps &t, AdamConsts ac, int parity, cudaStream_t s) {
     Maps mp{};
+    cudaError_t le;
     using ST = K3S<RG, K3_NW, K3_OPT, K3_ST_TMA>;
     const bool tma = tmap(&mp.a, g, 4, d, 3, ST::BXW, ST::RY, 3) &&
                      tmap(&mp.b, m, 4, d, 3, FX, ST::TY, 3) &&
@@ -1454,18 +1488,18 @@ cudaError_t launch_k3(const float *g, float *m, float *v, float *dir, WsHeader *
         auto kern = k_smooth_adam<RG, K3_NW, K3_OPT, K3_ST_TMA, true>;
         static const int occ = prepare(kern, ST::bytes, ST::NT);
         LaunchGeom gg = geometry(occ, K3_NW, ST::TY, RG, d);
-        kern<<<gg.grid, gg.block, ST::bytes, s>>>(mp, g, m, v, dir, h, d.D, d.H, d.W, gg.tz, t, ac,
+        le = launch_pdl(kern, gg, ST::bytes, s, mp, g, m, v, dir, h, d.D, d.H, d.W, gg.tz, t, ac,
                                                   parity);
     } else {
         using SC = K3S<RG, K3_NW, K3_OPT, K3_ST_CP>;
         auto kern = k_smooth_adam<RG, K3_NW, K3_OPT, K3_ST_CP, false>;
         static const int occ = prepare(kern, SC::bytes, SC::NT);
         LaunchGeom gg = geometry(occ, K3_NW, SC::TY, RG, d);
-        kern<<<gg.grid, gg.block, SC::bytes, s>>>(mp, g, m, v, dir, h, d.D, d.H, d.W, gg.tz, t, ac,
+        le = launch_pdl(kern, gg, SC::bytes, s, mp, g, m, v, dir, h, d.D, d.H, d.W, gg.tz, t, ac,
                                                   parity);
     }
     note_launch();
-    return cudaGetLastError();
+    return le;
 }
 
 template <int RG, bool SU>
@@ -1473,6 +1507,7 @@ cudaError_t launch_k4(const float *u, const float *dir, float *uo, const float *
                       WsHeader *h, Dims d, const GaussTaps &t, float lr, float c_lp, int parity,
                       cudaStream_t s) {
     Maps mp{};
+    cudaError_t le;
     using ST = K4S<RG, K4_NW, K4_OPT, SU, K4_ST_TMA>;
     const bool tma = tmap(&mp.a, dir, 4, d, 3, ST::BXW, ST::RY, 3) &&
                      (!SU || tmap(&mp.b, u, 4, d, 3, ST::UBXW, ST::URY, 3));
@@ -1480,18 +1515,18 @@ cudaError_t launch_k4(const float *u, const float *dir, float *uo, const float *
         auto kern = k_compose<RG, K4_NW, K4_OPT, SU, K4_ST_TMA, true>;
         static const int occ = prepare(kern, ST::bytes, ST::NT);
         LaunchGeom gg = geometry(occ, K4_NW, ST::TY, RG, d);
-        kern<<<gg.grid, gg.block, ST::bytes, s>>>(mp, u, dir, uo, Im, J, h, d.D, d.H, d.W, gg.tz,
+        le = launch_pdl(kern, gg, ST::bytes, s, mp, u, dir, uo, Im, J, h, d.D, d.H, d.W, gg.tz,
                                                   t, lr, c_lp, parity);
     } else {
         using SC = K4S<RG, K4_NW, K4_OPT, SU, K4_ST_CP>;
         auto kern = k_compose<RG, K4_NW, K4_OPT, SU, K4_ST_CP, false>;
         static const int occ = prepare(kern, SC::bytes, SC::NT);
         LaunchGeom gg = geometry(occ, K4_NW, SC::TY, RG, d);
-        kern<<<gg.grid, gg.block, SC::bytes, s>>>(mp, u, dir, uo, Im, J, h, d.D, d.H, d.W, gg.tz,
+        le = launch_pdl(kern, gg, SC::bytes, s, mp, u, dir, uo, Im, J, h, d.D, d.H, d.W, gg.tz,
                                                   t, lr, c_lp, parity);
     }
     note_launch();
-    return cudaGetLastError();
+    return le;
 }
 
 #define FA_CASE(n, call)      \

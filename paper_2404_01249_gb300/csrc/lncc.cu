@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(256) k_lncc_coef(const long long *__restrict__
             coef[6 * N + i] = clo;
         }
         if (cc >= 0.0f && cc <= 2.0f) {
-            qcc = (unsigned long long)__float2ull_rn(cc * 4294967296.0f);
+            qcc = (unsigned long long)quantize(cc, 4294967296.0f);  // cc in [0, 2]
         } else {
             status_set(&h->status, ST_NONFINITE);
         }
