@@ -83,7 +83,9 @@ typedef struct {
     float cc_eps;         /* >= 0 */
     float c_lp;           /* > 0 */
     int32_t mode;         /* fa_mode */
-    int32_t storage;      /* fa_dtype of images and fields inside fa_register (FA_F32) */
+    int32_t storage;      /* fa_dtype of the fixed and moving images given to fa_register:
+                             FA_F32, FA_BF16 or FA_F16 (16-bit images are widened once
+                             to FP32 copies in the workspace; all arithmetic is FP32) */
 } fa_params;
 
 /* Fills p with: 3 levels {4,2,1} x {200,100,50}, lr 0.5, sigma_grad 1,
@@ -213,7 +215,7 @@ fa_status fa_upsample_field(const fa_vol *coarse, fa_vol *fine, int32_t power, v
 /* Bytes of workspace fa_register needs for a D x H x W pair. */
 size_t fa_register_workspace_size(int32_t D, int32_t H, int32_t W, const fa_params *p);
 
-/* fixed, moving: C=1, FA_F32, same D x H x W.  u_out: C=3 on the grid of the
+/* fixed, moving: C=1, dtype p->storage, same D x H x W.  u_out: C=3 FA_F32 on the grid of the
  * last level (max(1, floor(N_a / s_last))).  final_loss_dev (device float,
  * may be NULL) receives the loss at the final map on the last level
  * (for LNCC that is -mean cc).  If final_loss_host is not NULL the call
@@ -224,6 +226,52 @@ size_t fa_register_workspace_size(int32_t D, int32_t H, int32_t W, const fa_para
 fa_status fa_register(const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
                       fa_vol *u_out, float *final_loss_dev, float *final_loss_host, void *ws,
                       size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Differentiation of the warp + LNCC loss (the Gateaux derivative of section
+ * "Jacobian-free Eulerian descent" plus the adjoints with respect to both
+ * images).  L = LNCC(I_f, I_m o (id + u)) exactly as fa_lncc_fwd_bwd
+ * defines it; dL_du = dL/dJ * grad I_m(phi) (C=3); dL_dfixed = dL/dI_f;
+ * dL_dmoving(p) = sum_x dL/dJ(x) w_p(x), w_p the trilinear weight of voxel
+ * p at x + u(x) (zero outside), accumulated in 2^-40-relative fixed point
+ * with integer atomics (order-independent).  Every output may be NULL.
+ * All volumes FA_F32 on one grid.  Workspace of
+ * fa_warp_lncc_adjoint_workspace_size bytes, 256-byte aligned. */
+size_t fa_warp_lncc_adjoint_workspace_size(int32_t D, int32_t H, int32_t W);
+fa_status fa_warp_lncc_adjoint(const fa_vol *fixed, const fa_vol *moving, const fa_vol *u,
+                               int32_t window, float cc_eps, float *loss_dev, fa_vol *dL_du_opt,
+                               fa_vol *dL_dfixed_opt, fa_vol *dL_dmoving_opt, void *ws,
+                               size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Many registrations in one call (no counterpart in the paper's text beyond
+ * the independence of registrations in Algorithm 1; the paper's own
+ * hyper-parameter sweeps run many such registrations, section "Results:
+ * Runtime and Memory Efficiency Analysis").
+ *
+ * Job j = pair * n_cfg + cfg registers fixed[pair] to moving[pair] with
+ * cfgs[cfg] (every field of fa_register's parameters may differ between
+ * sets, including the pyramid).  Pairs may have different grids.
+ * u_out[j] (C=3) is on the last level's grid of that job; final_loss_dev
+ * (n_pairs * n_cfg device floats, may be NULL) receives each job's final
+ * loss; status_dev (n_pairs * n_cfg device uint32, may be NULL) receives
+ * each job's device status bits (1: non-finite value, 2: a bounded wait gave
+ * up; 0: ok).
+ *
+ * Jobs run on `concurrency` (1..32) internal streams of the current device,
+ * forked from `stream` with events and joined back into it: work enqueued
+ * on `stream` afterwards sees every job's results.  Slot k of the workspace
+ * (fa_register_batched_workspace_size bytes, 256-byte aligned) serves jobs
+ * k, k + concurrency, ... in order.  Every job's arguments are checked
+ * before anything is enqueued.  The call returns after enqueueing.  The
+ * internal streams are created on first use and kept until the process
+ * exits; make the first call before a stream capture. */
+size_t fa_register_batched_workspace_size(int32_t n_pairs, const fa_vol *fixed, int32_t n_cfg,
+                                          const fa_params *cfgs, int32_t concurrency);
+fa_status fa_register_batched(int32_t n_pairs, const fa_vol *fixed, const fa_vol *moving,
+                              int32_t n_cfg, const fa_params *cfgs, fa_vol *u_out,
+                              float *final_loss_dev, uint32_t *status_dev, int32_t concurrency,
+                              void *ws, size_t ws_bytes, void *stream);
 
 /* Waits for `stream` and returns the status word that kernels recorded in a
  * workspace used by fa_register, fa_radam_step or fa_lncc_fwd_bwd

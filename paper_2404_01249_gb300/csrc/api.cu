@@ -30,6 +30,10 @@ fa_status cuda_fail(cudaError_t e, const char *where) {
 }
 
 fa_status check_vol(const fa_vol *v, const char *name, int C) {
+    return check_vol_dtype(v, name, C, FA_F32);
+}
+
+fa_status check_vol_dtype(const fa_vol *v, const char *name, int C, int dtype) {
     if (!v) {
         set_error("%s: descriptor is NULL", name);
         return FA_ERR_INVALID;
@@ -38,8 +42,8 @@ fa_status check_vol(const fa_vol *v, const char *name, int C) {
         set_error("%s: data pointer is NULL", name);
         return FA_ERR_INVALID;
     }
-    if (v->dtype != FA_F32) {
-        set_error("%s: dtype %d not supported here (FA_F32 only)", name, (int)v->dtype);
+    if (v->dtype != dtype) {
+        set_error("%s: dtype %d not supported here (expected %d)", name, (int)v->dtype, dtype);
         return FA_ERR_DTYPE;
     }
     if (v->C != C || v->D < 1 || v->H < 1 || v->W < 1) {

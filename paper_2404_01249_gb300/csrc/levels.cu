@@ -2,6 +2,9 @@
 // for multi-scale registration") and the trilinear level hand-off of u, m, nu
 // (Algorithm 1 "Upsample").  Align-corners: index i of an n_dst axis samples
 // source coordinate i (n_src - 1) / (n_dst - 1).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "ops.h"
 #include "validate.h"
 
@@ -68,6 +71,25 @@ cudaError_t launch_pyramid_level(const float *img, Dims d, int s, float *out, Di
     if ((e = launch_gauss_axis(t1, t2, 1, d, t, 1, st)) != cudaSuccess) return e;
     if ((e = launch_gauss_axis(t2, t1, 1, d, t, 2, st)) != cudaSuccess) return e;
     return launch_resample(t1, d, out, dl, 1, nullptr, st);
+}
+
+// 16-bit input images widened to FP32 (exact for both formats).
+__global__ void __launch_bounds__(256) k_widen(const unsigned short *__restrict__ src, int dtype,
+                                               float *__restrict__ dst, long long n) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const unsigned short b = src[i];
+        dst[i] = dtype == FA_BF16 ? __uint_as_float((unsigned)b << 16)
+                                  : __half2float(__ushort_as_half(b));
+    }
+}
+
+cudaError_t launch_widen(const void *src, int dtype, float *dst, long long n, cudaStream_t s) {
+    const long long blocks = (n + 255) / 256;
+    k_widen<<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, s>>>(
+        (const unsigned short *)src, dtype, dst, n);
+    note_launch();
+    return cudaGetLastError();
 }
 
 }  // namespace fa

@@ -87,4 +87,7 @@ void handoff_scales(Dims c, Dims f, int power, float out[3]);
 cudaError_t launch_pyramid_level(const float *img, Dims d, int s, float *out, Dims dl, float *t1,
                                  float *t2, cudaStream_t st);
 
+// dst[i] = src[i] widened to FP32 (src FA_BF16 or FA_F16; exact).
+cudaError_t launch_widen(const void *src, int dtype, float *dst, long long n, cudaStream_t s);
+
 }  // namespace fa

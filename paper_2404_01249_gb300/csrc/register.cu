@@ -48,8 +48,8 @@ static fa_status check_params(const fa_params *p) {
         set_error("mode must be FA_MODE_FUSED or FA_MODE_PLAIN");
         return FA_ERR_INVALID;
     }
-    if (p->storage != FA_F32) {
-        set_error("storage dtype %d is not supported by fa_register", (int)p->storage);
+    if (p->storage != FA_F32 && p->storage != FA_BF16 && p->storage != FA_F16) {
+        set_error("storage must be FA_F32, FA_BF16 or FA_F16 (got %d)", (int)p->storage);
         return FA_ERR_UNSUPPORTED;
     }
     return check_adam_params(p, "fa_register");
@@ -62,6 +62,7 @@ struct Plan {
     long long nmax;
     WsHeader *h;
     float *If[8], *Im[8];
+    float *If0, *Im0;  // FP32 copies of 16-bit input images (else nullptr)
     float *u[2], *m[2], *v[2];
     float *J, *grad, *g, *dir, *t1, *t2;
     LnccBuffers lb;
@@ -82,6 +83,11 @@ static void make_plan(Plan &P, void *base, size_t cap, Dims full, const fa_param
     long long n = P.nmax;
     WsCarver c(base, cap);
     P.h = c.take<WsHeader>(1);
+    P.If0 = P.Im0 = nullptr;
+    if (p->storage != FA_F32) {
+        P.If0 = c.take<float>(full.N());
+        P.Im0 = c.take<float>(full.N());
+    }
     for (int l = 0; l < p->n_levels; ++l) {
         if (p->scales[l] == 1) {
             P.If[l] = P.Im[l] = nullptr;  // the inputs themselves
@@ -194,12 +200,11 @@ static fa_status final_loss(Plan &P, const fa_params *p, int l, const float *If,
     return FA_OK;
 }
 
-fa_status register_impl(const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
-                        fa_vol *u_out, float *final_loss_dev, float *final_loss_host, void *ws,
-                        size_t ws_bytes, cudaStream_t s, fa_kernel_timer *timer) {
+fa_status register_check(const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
+                         const fa_vol *u_out) {
     FA_TRY(check_params(p));
-    FA_TRY(check_vol(fixed, "fixed", 1));
-    FA_TRY(check_vol(moving, "moving", 1));
+    FA_TRY(check_vol_dtype(fixed, "fixed", 1, p->storage));
+    FA_TRY(check_vol_dtype(moving, "moving", 1, p->storage));
     FA_TRY(same_grid(fixed, moving, "fixed", "moving"));
     FA_TRY(check_vol(u_out, "u_out", 3));
     Dims full{fixed->D, fixed->H, fixed->W};
@@ -210,6 +215,15 @@ fa_status register_impl(const fa_vol *fixed, const fa_vol *moving, const fa_para
         set_error("u_out must be 3 x %d x %d x %d (the last level's grid)", last.D, last.H, last.W);
         return FA_ERR_SHAPE;
     }
+    return FA_OK;
+}
+
+fa_status register_impl(const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
+                        fa_vol *u_out, float *final_loss_dev, float *final_loss_host, void *ws,
+                        size_t ws_bytes, cudaStream_t s, fa_kernel_timer *timer) {
+    FA_TRY(register_check(fixed, moving, p, u_out));
+    Dims full{fixed->D, fixed->H, fixed->W};
+    const int L = p->n_levels - 1;
     Plan P;
     make_plan(P, nullptr, ~size_t(0), full, p);
     FA_TRY(check_ws(ws, ws_bytes, P.bytes, "fa_register"));
@@ -222,6 +236,12 @@ fa_status register_impl(const fa_vol *fixed, const fa_vol *moving, const fa_para
         timer->count = 0;
     }
     const float *If0 = (const float *)fixed->data, *Im0 = (const float *)moving->data;
+    if (p->storage != FA_F32) {  // 16-bit images: widened once, exactly
+        FA_CUDA_TRY(launch_widen(fixed->data, p->storage, P.If0, full.N(), s));
+        FA_CUDA_TRY(launch_widen(moving->data, p->storage, P.Im0, full.N(), s));
+        If0 = P.If0;
+        Im0 = P.Im0;
+    }
     GaussTaps tg, tw;
     make_gauss_taps(p->sigma_grad, &tg);
     make_gauss_taps(p->sigma_warp, &tw);

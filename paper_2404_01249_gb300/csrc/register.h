@@ -35,6 +35,11 @@ cudaError_t fused_level_start(const float *If, const float *Im, const float *u, 
 cudaError_t fused_lncc_forward_only(const float *If, const FusedBuffers &fb, Dims d, int window,
                                     float cc_eps, WsHeader *h, cudaStream_t s);
 
+// Argument checks of fa_register (no launch).
+fa_status register_check(const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
+                         const fa_vol *u_out);
+size_t register_ws_bytes(int D, int H, int W, const fa_params *p);
+
 fa_status register_impl(const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
                         fa_vol *u_out, float *final_loss_dev, float *final_loss_host, void *ws,
                         size_t ws_bytes, cudaStream_t s, fa_kernel_timer *timer);

@@ -21,6 +21,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libfa.so")
 
 FA_OK = 0
+FA_ERR_INVALID = 1
 STATUS_NAMES = {0: "FA_OK", 1: "FA_ERR_INVALID", 2: "FA_ERR_SHAPE", 3: "FA_ERR_DTYPE",
                 4: "FA_ERR_CUDA", 5: "FA_ERR_NONFINITE", 6: "FA_ERR_TIMEOUT",
                 7: "FA_ERR_UNSUPPORTED", 8: "FA_ERR_WORKSPACE"}
@@ -35,7 +36,9 @@ EXPORTED = ["fa_params_default", "fa_status_str", "fa_last_error", "fa_warp",
             "fa_gauss_workspace_size", "fa_gauss_smooth", "fa_radam_workspace_size",
             "fa_radam_step", "fa_pyramid_level", "fa_upsample_field",
             "fa_register_workspace_size", "fa_register", "fa_ws_status", "fa_register_timed",
-            "fa_launch_count", "fa_lncc_fwd_bwd_noalloc"]
+            "fa_launch_count", "fa_lncc_fwd_bwd_noalloc", "fa_register_batched_workspace_size",
+            "fa_register_batched", "fa_warp_lncc_adjoint_workspace_size",
+            "fa_warp_lncc_adjoint"]
 
 
 class FAError(RuntimeError):
@@ -102,6 +105,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "fa_ws_status": (i32, [vp, vp]),
         "fa_register_timed": (i32, [V, V, P, V, vp, fp, vp, sz, vp,
                                     ctypes.POINTER(KernelTimer)]),
+        "fa_register_batched_workspace_size": (sz, [i32, V, i32, P, i32]),
+        "fa_register_batched": (i32, [i32, V, V, i32, P, V, vp, vp, i32, vp, sz, vp]),
+        "fa_warp_lncc_adjoint_workspace_size": (sz, [i32, i32, i32]),
+        "fa_warp_lncc_adjoint": (i32, [V, V, V, i32, f32, vp, V, V, V, vp, sz, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -120,17 +127,21 @@ def _stream() -> ctypes.c_void_p:
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-def _vol(t: Optional[torch.Tensor], C: int):
+_DTYPES = {torch.float32: FA_F32, torch.bfloat16: FA_BF16, torch.float16: FA_F16}
+
+
+def _vol(t: Optional[torch.Tensor], C: int, half_ok: bool = False):
     if t is None:
         return None
-    if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
-        raise ValueError("expected a contiguous float32 CUDA tensor")
+    ok = (torch.float32, torch.bfloat16, torch.float16) if half_ok else (torch.float32,)
+    if not t.is_cuda or t.dtype not in ok or not t.is_contiguous():
+        raise ValueError(f"expected a contiguous CUDA tensor of dtype {ok}")
     shp = tuple(t.shape)
     if C == 1 and len(shp) == 3:
         shp = (1,) + shp
     if len(shp) != 4 or shp[0] != C:
         raise ValueError(f"expected shape [{C}, D, H, W], got {tuple(t.shape)}")
-    return ctypes.byref(Vol(t.data_ptr(), FA_F32, C, shp[1], shp[2], shp[3]))
+    return ctypes.byref(Vol(t.data_ptr(), _DTYPES[t.dtype], C, shp[1], shp[2], shp[3]))
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -276,6 +287,7 @@ def fa_register(fixed, moving, params: RegParams, ws: Optional[torch.Tensor] = N
     level, loss=0-dim CUDA tensor, final_loss=float or None if sync=False)."""
     D, H, W = fixed.shape[-3:]
     p = params.to_c()
+    p.storage = _DTYPES.get(fixed.dtype, FA_F32)  # 16-bit images are widened in the workspace
     lib = load()
     need = lib.fa_register_workspace_size(D, H, W, ctypes.byref(p))
     if need == 0:
@@ -287,13 +299,82 @@ def fa_register(fixed, moving, params: RegParams, ws: Optional[torch.Tensor] = N
                             device=fixed.device)
     loss = loss_out if loss_out is not None else torch.empty((), device=fixed.device)
     host = ctypes.c_float() if sync else None
-    args = (_vol(fixed, 1), _vol(moving, 1), ctypes.byref(p), _vol(u_out, 3), _ptr(loss),
+    args = (_vol(fixed, 1, True), _vol(moving, 1, True), ctypes.byref(p), _vol(u_out, 3), _ptr(loss),
             ctypes.byref(host) if sync else None, _ptr(ws), ws.numel(), _stream())
     if timer is None:
         _check(lib.fa_register(*args))
     else:
         _check(lib.fa_register_timed(*args, ctypes.byref(timer)))
     return dict(u=u_out, loss=loss, final_loss=host.value if sync else None)
+
+
+def _vol_struct(t: torch.Tensor, C: int, half_ok: bool = False) -> Vol:
+    _vol(t, C, half_ok)  # validation
+    shp = tuple(t.shape) if t.dim() == 4 else (1,) + tuple(t.shape)
+    return Vol(t.data_ptr(), _DTYPES[t.dtype], C, shp[1], shp[2], shp[3])
+
+
+def fa_register_batched(fixed: list, moving: list, params: list, concurrency: int = 4,
+                        ws: Optional[torch.Tensor] = None, sync: bool = True):
+    """Registers every pair under every parameter set (job = pair * len(params)
+    + set) concurrently.  Returns a list of dicts (u, loss tensor, final_loss
+    and status when sync=True), one per job."""
+    n_pairs, n_cfg = len(fixed), len(params)
+    if len(moving) != n_pairs:
+        raise ValueError("fixed and moving need the same number of volumes")
+    lib = load()
+    dev = fixed[0].device
+    fv = (Vol * n_pairs)(*[_vol_struct(t, 1, True) for t in fixed])
+    mv = (Vol * n_pairs)(*[_vol_struct(t, 1, True) for t in moving])
+    if len({t.dtype for t in list(fixed) + list(moving)}) != 1:
+        raise ValueError("all images of one batched call share a dtype")
+    cs = [q.to_c() for q in params]
+    for c in cs:
+        c.storage = _DTYPES[fixed[0].dtype]
+    pc = (Params * n_cfg)(*cs)
+    need = lib.fa_register_batched_workspace_size(n_pairs, fv, n_cfg, pc, concurrency)
+    if need == 0:
+        raise FAError(FA_ERR_INVALID, lib.fa_last_error().decode())
+    ws = ws if ws is not None else workspace(need, dev)
+    outs = []
+    for i in range(n_pairs):
+        D, H, W = fixed[i].shape[-3:]
+        for q in params:
+            s = q.scales[-1]
+            outs.append(torch.empty((3, level_size(D, s), level_size(H, s), level_size(W, s)),
+                                    device=dev))
+    uv = (Vol * len(outs))(*[_vol_struct(t, 3) for t in outs])
+    loss = torch.empty(len(outs), device=dev)
+    status = torch.zeros(len(outs), dtype=torch.int32, device=dev)
+    _check(lib.fa_register_batched(n_pairs, fv, mv, n_cfg, pc, uv, _ptr(loss), _ptr(status),
+                                   concurrency, _ptr(ws), ws.numel(), _stream()))
+    res = [dict(u=u, loss=loss[j]) for j, u in enumerate(outs)]
+    if sync:
+        torch.cuda.current_stream().synchronize()
+        lh, sh = loss.cpu().tolist(), status.cpu().tolist()
+        for j, r in enumerate(res):
+            r["final_loss"], r["status"] = lh[j], sh[j]
+    return res
+
+
+def fa_warp_lncc_adjoint(fixed, moving, u, window: int = 5, cc_eps: float = 1e-5,
+                         want_u: bool = True, want_fixed: bool = True, want_moving: bool = True,
+                         ws: Optional[torch.Tensor] = None):
+    """L = LNCC(fixed, moving o (id + u)) and its derivatives.  Returns
+    dict(loss=0-dim tensor, dL_du, dL_dfixed, dL_dmoving) (None where not
+    wanted); asynchronous on the current stream."""
+    D, H, W = fixed.shape[-3:]
+    lib = load()
+    need = lib.fa_warp_lncc_adjoint_workspace_size(D, H, W)
+    ws = ws if ws is not None else workspace(need, fixed.device)
+    loss = torch.empty((), device=fixed.device)
+    du = torch.empty((3, D, H, W), device=fixed.device) if want_u else None
+    dfx = torch.empty((D, H, W), device=fixed.device) if want_fixed else None
+    dmv = torch.empty((D, H, W), device=fixed.device) if want_moving else None
+    _check(lib.fa_warp_lncc_adjoint(_vol(fixed, 1), _vol(moving, 1), _vol(u, 3), int(window),
+                                    float(cc_eps), _ptr(loss), _vol(du, 3), _vol(dfx, 1),
+                                    _vol(dmv, 1), _ptr(ws), ws.numel(), _stream()))
+    return dict(loss=loss, dL_du=du, dL_dfixed=dfx, dL_dmoving=dmv)
 
 
 def fa_launch_count() -> int:

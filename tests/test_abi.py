@@ -88,3 +88,24 @@ def test_host_validation_rejects_before_launch(lib):
     assert lib.fa_register(ok1(), ok1(), ctypes.byref(p), _vol(a, 3, 4, 5, 6), None, None, None,
                            0, None) == 8
     assert lib.fa_pyramid_level(_vol(a, 1, 8, 8, 8), 2, _vol(a, 1, 3, 4, 4), None, 0, None) == 2
+
+
+def test_batched_validation_before_launch(lib):
+    from paper_2404_01249_gb300 import fa
+    a = 1 << 20
+    p = fa.RegParams(scales=(2, 1), iters=(3, 2)).to_c()
+    cfgs = (fa.Params * 1)(p)
+    fx = (fa.Vol * 2)(fa.Vol(a, 0, 1, 8, 9, 10), fa.Vol(a, 0, 1, 12, 6, 4))
+    assert lib.fa_register_batched_workspace_size(0, fx, 1, cfgs, 2) == 0
+    assert lib.fa_register_batched_workspace_size(2, fx, 1, cfgs, 0) == 0
+    assert lib.fa_register_batched_workspace_size(2, fx, 1, cfgs, 33) == 0
+    one = lib.fa_register_workspace_size(8, 9, 10, ctypes.byref(p))
+    two = lib.fa_register_workspace_size(12, 6, 4, ctypes.byref(p))
+    got = lib.fa_register_batched_workspace_size(2, fx, 1, cfgs, 2)
+    assert got >= 2 * max(one, two) and got % 256 == 0
+    # a job whose u_out is on the wrong grid is rejected before anything runs
+    uo = (fa.Vol * 2)(fa.Vol(a, 0, 3, 8, 9, 10), fa.Vol(a, 0, 3, 12, 6, 5))
+    st = lib.fa_register_batched(2, fx, fx, 1, cfgs, uo, None, None, 2, None, 0, None)
+    assert st == 2
+    assert b"pair 1, parameter set 0" in lib.fa_last_error()
+    assert lib.fa_register_batched(0, fx, fx, 1, cfgs, uo, None, None, 2, None, 0, None) == 1

@@ -1,0 +1,101 @@
+"""fa_warp_lncc_adjoint and the autograd wrapper against the oracle: the loss,
+dL/du = dL/dJ grad I_m(phi), dL/dI_f and the warp adjoint dL/dI_m (oracle:
+lncc + warp + warp_adjoint in FP64).  Bar: max-abs error over max-abs
+reference <= 1e-5."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2404_01249_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def fa():
+    from paper_2404_01249_gb300 import build, fa
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    fa.load()
+    return fa
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def rel(a, b):
+    a = a.detach().cpu().double().numpy()
+    b = np.asarray(b, np.float64)
+    den = np.abs(b).max()
+    return float(np.abs(a - b).max() / (den if den > 0 else 1.0))
+
+
+@pytest.mark.parametrize("shape,window", [((20, 24, 28), 5), ((17, 31, 22), 3),
+                                          ((12, 16, 40), 7)])
+def test_adjoint_matches_oracle(fa, orc, shape, window):
+    f, m, _ = synth.voronoi_pair(shape=shape, seed=321)
+    u = synth.random_field(shape, 3.0, 2.5, seed=9).astype(np.float32)
+    r = fa.fa_warp_lncc_adjoint(cuda(f), cuda(m), cuda(u), window, 1e-5)
+    # the oracle's LNCC runs on the warped image the GPU computes (fa_warp is
+    # the same kernel), its gradient and warp adjoint in FP64
+    J, _ = fa.fa_warp(cuda(m), cuda(u))
+    Jr, gr = orc.warp(m, u)
+    assert rel(J, Jr) < TOL
+    ref = orc.lncc(f, J.cpu().numpy(), window, np.float32(1e-5), want_dJ=True, want_dI=True)
+    assert abs(float(r["loss"]) - ref["loss"]) <= TOL * abs(ref["loss"])
+    assert rel(r["dL_dfixed"], ref["dI"]) < TOL
+    assert rel(r["dL_du"], ref["dJ"][None] * gr) < TOL
+    assert rel(r["dL_dmoving"], orc.warp_adjoint(ref["dJ"], u, shape)) < TOL
+
+
+def test_adjoint_outputs_are_optional_and_deterministic(fa):
+    shape = (16, 20, 24)
+    f, m, _ = synth.voronoi_pair(shape=shape, seed=5)
+    u = cuda(synth.random_field(shape, 3.0, 2.0, seed=4))
+    a = fa.fa_warp_lncc_adjoint(cuda(f), cuda(m), u, 5, 1e-5)
+    b = fa.fa_warp_lncc_adjoint(cuda(f), cuda(m), u, 5, 1e-5, want_u=False, want_fixed=False)
+    c = fa.fa_warp_lncc_adjoint(cuda(f), cuda(m), u, 5, 1e-5)
+    assert b["dL_du"] is None and b["dL_dfixed"] is None
+    assert torch.equal(a["dL_dmoving"], b["dL_dmoving"])
+    assert torch.equal(a["dL_dmoving"], c["dL_dmoving"])   # order-independent scatter
+    assert float(a["loss"]) == float(b["loss"])
+
+
+def test_autograd_function(fa):
+    from paper_2404_01249_gb300.autograd import warp_lncc
+    shape = (14, 18, 22)
+    f, m, _ = synth.voronoi_pair(shape=shape, seed=8)
+    u0 = synth.random_field(shape, 3.0, 1.5, seed=3)
+    fx = cuda(f).requires_grad_(True)
+    mv = cuda(m).requires_grad_(True)
+    u = cuda(u0).requires_grad_(True)
+    loss = 3.0 * warp_lncc(fx, mv, u, 5, 1e-5)
+    loss.backward()
+    r = fa.fa_warp_lncc_adjoint(cuda(f), cuda(m), cuda(u0), 5, 1e-5)
+    assert torch.allclose(fx.grad, 3.0 * r["dL_dfixed"], rtol=0, atol=0)
+    assert torch.allclose(mv.grad, 3.0 * r["dL_dmoving"], rtol=0, atol=0)
+    assert torch.allclose(u.grad, 3.0 * r["dL_du"], rtol=0, atol=0)
+    # only what is asked for is computed
+    u2 = cuda(u0).requires_grad_(True)
+    warp_lncc(cuda(f), cuda(m), u2).backward()
+    assert u2.grad is not None
+
+
+def test_template_gradient_on_gpu_matches_oracle(fa, orc):
+    from paper_2404_01249_gb300.template import template_gradient
+    shape = (12, 14, 16)
+    T, _, _ = synth.voronoi_pair(shape=shape, seed=60)
+    subs = [synth.voronoi_pair(shape=shape, seed=61 + i)[1] for i in range(3)]
+    us = [synth.random_field(shape, 3.0, 1.0, seed=70 + i).astype(np.float32) for i in range(3)]
+    loss, g = template_gradient(cuda(T), [cuda(s) for s in subs], [cuda(u) for u in us])
+    ref_g = np.zeros(shape)
+    ref_l = 0.0
+    for s, u in zip(subs, us):
+        J, _ = fa.fa_warp(cuda(T), cuda(u))
+        r = orc.lncc(s, J.cpu().numpy(), 5, np.float32(1e-5), want_dJ=True)
+        ref_g += orc.warp_adjoint(r["dJ"], u, shape)
+        ref_l += r["loss"]
+    assert rel(g, ref_g / 3) < TOL
+    assert abs(float(loss) - ref_l / 3) < 1e-5

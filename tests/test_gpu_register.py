@@ -128,3 +128,16 @@ def test_fused_brain_level_against_oracle(fa, orc):
                        adam_eps=f32(1e-8))
     assert abs(out["final_loss"] - ref["final_loss"]) < 1e-3
     assert mean_disp_diff(out["u"], ref["u"]) < 0.05
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
+def test_16bit_images_equal_fp32_of_the_rounded_images(fa, dtype):
+    """16-bit images are widened exactly, so registering them equals
+    registering their FP32 values bit for bit (and inherits the FP32 path's
+    parity with the oracle)."""
+    f, m, _ = synth.voronoi_pair(shape=(24, 28, 32), seed=77)
+    fh, mh = cuda(f).to(dtype), cuda(m).to(dtype)
+    p = fa.RegParams(scales=(2, 1), iters=(10, 5))
+    a = fa.fa_register(fh, mh, p)
+    b = fa.fa_register(fh.float().contiguous(), mh.float().contiguous(), p)
+    assert torch.equal(a["u"], b["u"]) and a["final_loss"] == b["final_loss"]
