@@ -875,7 +875,7 @@ struct K3S {
 };
 
 template <int RG, int NW, int OPT, int NSTG, bool TMA>
-__global__ void __launch_bounds__(FX *NW) k_smooth_adam(const __grid_constant__ Maps maps,
+__global__ void __launch_bounds__(FX *NW, 1024 / (FX * NW)) k_smooth_adam(const __grid_constant__ Maps maps,
                                                         const float *__restrict__ g,
                                                         float *__restrict__ m,
                                                         float *__restrict__ v,
@@ -1041,7 +1041,7 @@ struct K4S {
 };
 
 template <int RG, int NW, int OPT, bool SU, int NSTG, bool TMA>
-__global__ void __launch_bounds__(FX *NW) k_compose(const __grid_constant__ Maps maps,
+__global__ void __launch_bounds__(FX *NW, 1024 / (FX * NW)) k_compose(const __grid_constant__ Maps maps,
                                                     const float *__restrict__ u,
                                                     const float *__restrict__ dir,
                                                     float *__restrict__ uo,
@@ -1415,7 +1415,7 @@ bool tmap(CUtensorMap *m, const void *base, int esize, Dims d, int C, int bx, in
 constexpr int K1_NW = 8, K1_OPT = 1, K1_ST_TMA = 3, K1_ST_CP = 3;
 constexpr int K2_NW = 8, K2_OPT = 1, K2_ST_TMA = 2, K2_ST_CP = 2;
 constexpr int K3_NW = 8, K3_OPT = 1, K3_ST_TMA = 2, K3_ST_CP = 2;
-constexpr int K4_NW = 8, K4_OPT = 1, K4_ST_TMA = 2, K4_ST_CP = 2;
+constexpr int K4_NW = 16, K4_OPT = 1, K4_ST_TMA = 2, K4_ST_CP = 2;
 
 template <int R>
 cudaError_t launch_k1(const float *If, const float *J, const long long *sI, const float *varI,
