@@ -220,26 +220,33 @@ def run_gpu(args):
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    for _ in range(args.warmup):
-        fa.fa_register(fixed, moving, params, ws=ws, sync=False, u_out=u, loss_out=loss)
-    torch.cuda.synchronize()
-
-    # kernel timers on the finest level: the fused kernels take turns, one
-    # kernel per timed step (plain mode: the whole plain iteration)
+    # kernel timers on the finest level, inside the recorded graph: fused mode
+    # times all four fused kernels (launch order K1 K2 K3 K4 per iteration),
+    # plain mode the whole plain iteration.  Two timers alternate between
+    # steps so that one step's events are read before they are recorded again.
     fin = len(WORKLOAD["scales"]) - 1
     if args.mode == "plain":
-        knames = ["plain_iteration"]
-    elif args.kernel == "dominant":
-        knames = list(FUSED_KERNELS)
+        knames, kid = ["plain_iteration"], fa.FA_K_PLAIN_ANY
     else:
-        knames = [args.kernel]
-    timers = {}
-    for j, kn in enumerate(knames):
-        nsteps = len(range(j, args.steps, len(knames)))
-        cap = max(1, WORKLOAD["iters"][fin] * nsteps)
+        knames, kid = list(FUSED_KERNELS), fa.FA_K_FUSED_ALL
+    cap = WORKLOAD["iters"][fin] * len(knames)
+    timers = []
+    for _ in range(2):
         ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(cap)]
         ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(cap)]
-        timers[kn] = (fa.make_timer(KERNEL_IDS[kn], fin, ev0, ev1), ev0, ev1)
+        timers.append((fa.make_timer(kid, fin, ev0, ev1), ev0, ev1))
+    ktimes = {k: [] for k in knames}
+
+    def harvest(j):
+        tm, ev0, ev1 = timers[j]
+        for i in range(tm.count):
+            ktimes[knames[i % len(knames)]].append(ev0[i].elapsed_time(ev1[i]))
+
+    # warm-up (records the graphs of both timers when W >= 2)
+    for w in range(args.warmup):
+        fa.fa_register(fixed, moving, params, ws=ws, sync=False, u_out=u, loss_out=loss,
+                       timer=timers[w % 2][0])
+    torch.cuda.synchronize()
     step0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     step1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     bus = None
@@ -259,9 +266,13 @@ def run_gpu(args):
         flush.zero_()
         step0[k].record(stream)
         fa.fa_register(fixed, moving, params, ws=ws, sync=False, u_out=u, loss_out=loss,
-                       timer=timers[knames[k % len(knames)]][0])
+                       timer=timers[k % 2][0])
         step1[k].record(stream)
+        if k >= 1:  # step k is queued: read step k-1's kernel events
+            step1[k - 1].synchronize()
+            harvest((k - 1) % 2)
     torch.cuda.synchronize()
+    harvest((args.steps - 1) % 2)
     wall = time.perf_counter() - t0
     launches = fa.fa_launch_count() - launches0
     if world > 1:
@@ -283,8 +294,7 @@ def run_gpu(args):
     n_fine = int(np.prod([level_size(a, WORKLOAD["scales"][fin]) for a in shape]))
     peak, peak_kind = measured_peak()
     kernels = {}
-    for kn, (tm, ev0, ev1) in timers.items():
-        kt = [ev0[i].elapsed_time(ev1[i]) for i in range(tm.count)]
+    for kn, kt in ktimes.items():
         if not kt:
             continue
         avg_ms = float(np.mean(kt))
@@ -314,6 +324,9 @@ def run_gpu(args):
     e1 = torch.cuda.Event(enable_timing=True)
     fd = torch.empty_like(fixed)
     md = torch.empty_like(moving)
+    fd.copy_(fh)
+    md.copy_(mh)
+    fa.fa_register(fd, md, params, ws=ws, sync=False, u_out=u, loss_out=loss)  # records its graph
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -355,6 +368,67 @@ def run_gpu(args):
     return 0
 
 
+# ------------------------------------------------------- batched throughput
+def run_batched(args):
+    """Throughput of many independent registrations in one fa_register_batched
+    call: `--batched P` pairs of uneven brain-like grids (each axis uniform
+    in [96,192] x [112,224] x [96,192]) x 9 parameter sets (lr {0.25, 0.5, 1}
+    x sigma_grad {0.5, 1, 2}), scales {4,2,1} x iterations {200,100,50}.
+    A step is the whole batch.  Also times the same batch with one stream
+    (concurrency 1) once, for comparison."""
+    import torch
+    from paper_2404_01249_gb300 import build, fa, synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    build.build()
+    fa.load()
+    shapes = synth.uneven_shapes(n=args.batched, seed=3000)
+    pairs = [synth.voronoi_pair(shape=sh, seed=1000 + i) for i, sh in enumerate(shapes)]
+    fixed = [torch.from_numpy(p[0]).to(dev) for p in pairs]
+    moving = [torch.from_numpy(p[1]).to(dev) for p in pairs]
+    cfgs = [fa.RegParams(scales=WORKLOAD["scales"], iters=WORKLOAD["iters"], lr=lr, sigma_grad=sg,
+                         sigma_warp=WORKLOAD["sigma_warp"], window=WORKLOAD["window"])
+            for lr in (0.25, 0.5, 1.0) for sg in (0.5, 1.0, 2.0)]
+    vi = sum(voxel_iters(sh, WORKLOAD["scales"], WORKLOAD["iters"]) for sh in shapes) * len(cfgs)
+    n_jobs = len(shapes) * len(cfgs)
+
+    def step(conc):
+        return fa.fa_register_batched(fixed, moving, cfgs, concurrency=conc, sync=False)
+
+    for _ in range(args.warmup):
+        step(args.concurrency)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(None)
+    clocks.start()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(args.concurrency)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    e0.record(stream)
+    step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms1 = e0.elapsed_time(e1)
+    line = {"metric": METRIC, "value": vi / (ms / 1e3), "unit": METRIC, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"uneven_brain_batch_{len(shapes)}x{len(cfgs)}",
+                       "shapes": [list(x) for x in shapes], "scales": list(WORKLOAD["scales"]),
+                       "iters": list(WORKLOAD["iters"]), "lr": [0.25, 0.5, 1.0],
+                       "sigma_grad": [0.5, 1.0, 2.0], "concurrency": args.concurrency,
+                       "l2": "inputs of the batch exceed L2"},
+            "registrations_per_s": n_jobs / (ms / 1e3),
+            "ms_per_step_concurrency_1": ms1, "clocks": clk}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -363,10 +437,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="fused", choices=["fused", "plain"])
     ap.add_argument("--cpu-iters", type=int, default=2)
-    ap.add_argument("--kernel", default="dominant", choices=["dominant"] + sorted(ALGO_BYTES),
-                    help="kernel whose finest-level launches are timed for the roofline "
-                         "(dominant: all four fused kernels, one per timed step)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched", type=int, default=0, metavar="P",
+                    help="time fa_register_batched on P uneven pairs x 9 parameter sets instead")
+    ap.add_argument("--concurrency", type=int, default=8, help="streams of --batched")
     ap.add_argument("--scales", type=int, nargs="+", default=None,
                     help="override the pyramid scales (profiling runs; changes the workload)")
     ap.add_argument("--iters", type=int, nargs="+", default=None,
@@ -382,6 +456,8 @@ def main():
                         "_iters" + "-".join(map(str, it)))
     if args.impl == "reference":
         return run_reference(args)
+    if args.batched:
+        return run_batched(args)
     return run_gpu(args)
 
 

@@ -86,11 +86,16 @@ typedef struct {
     int32_t storage;      /* fa_dtype of the fixed and moving images given to fa_register:
                              FA_F32, FA_BF16 or FA_F16 (16-bit images are widened once
                              to FP32 copies in the workspace; all arithmetic is FP32) */
+    int32_t graph;        /* 1: fa_register records its whole launch sequence as a CUDA
+                             graph on first use (stream capture on a private stream) and
+                             replays it when called again with identical arguments
+                             (pointers, shapes, parameters, workspace, timer); up to 64
+                             graphs are kept per process.  0: launch kernel by kernel. */
 } fa_params;
 
 /* Fills p with: 3 levels {4,2,1} x {200,100,50}, lr 0.5, sigma_grad 1,
  * sigma_warp 0.5, window 5, LNCC, Adam (0.9, 0.999, 1e-8), cc_eps 1e-5,
- * c_lp 2, fused mode, FP32 storage. */
+ * c_lp 2, fused mode, FP32 storage, graph replay on. */
 fa_status fa_params_default(fa_params *p);
 
 const char *fa_status_str(fa_status s);
@@ -284,13 +289,17 @@ fa_status fa_ws_status(const void *ws, void *stream);
  * every launch of kernel `kernel_id` on level `level` (-1: every level), in
  * order, until `capacity` pairs are used; `count` receives the number of
  * pairs recorded.  Elapsed times are then read with cudaEventElapsedTime.
+ * With p->graph set, the event records are part of the recorded graph: a
+ * replay records the same events again (read them before the next replay
+ * of the same call), and `count` is set to the recorded number.
  * ------------------------------------------------------------------------- */
 typedef enum {
     FA_K_FUSED_WARP_LNCC = 0,   /* fused: warp + LNCC forward (coefficients, loss)    */
     FA_K_FUSED_LNCC_GRAD = 1,   /* fused: LNCC adjoint sums + warp gradient -> dL/du  */
     FA_K_FUSED_SMOOTH_ADAM = 2, /* fused: Gaussian(sigma_grad) + Adam + max |d|       */
     FA_K_FUSED_COMPOSE = 3,     /* fused: compose + Gaussian(sigma_warp)              */
-    FA_K_PLAIN_ANY = 4          /* plain mode: every kernel of one iteration          */
+    FA_K_PLAIN_ANY = 4,         /* plain mode: every kernel of one iteration          */
+    FA_K_FUSED_ALL = 5          /* fused: each of the four kernels above, launch order */
 } fa_kernel_id;
 
 typedef struct {

@@ -14,6 +14,8 @@ static thread_local char g_err[512];
 static std::atomic<unsigned long long> g_launches{0};
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+unsigned long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 void set_error(const char *fmt, ...) {
     va_list ap;
@@ -133,6 +135,7 @@ fa_status fa_params_default(fa_params *p) {
     p->c_lp = 2.0f;
     p->mode = FA_MODE_FUSED;
     p->storage = FA_F32;
+    p->graph = 1;
     return FA_OK;
 }
 

@@ -14,8 +14,11 @@ namespace fa {
 void set_error(const char *fmt, ...);
 void clear_error();
 fa_status cuda_fail(cudaError_t e, const char *where);
-// Counts kernel launches made by this library (read with fa_launch_count).
+// Counts kernel launches made by this library (read with fa_launch_count);
+// a replayed graph adds the kernels it holds.
 void note_launch();
+void note_launches(unsigned long long n);
+unsigned long long launches_so_far();
 
 #define FA_CUDA_TRY(expr)                                           \
     do {                                                            \

@@ -1614,8 +1614,8 @@ struct KTimer {
     fa_kernel_timer *t;
     int level;
     bool on(int id) const {
-        return t && t->kernel_id == id && (t->level < 0 || t->level == level) &&
-               t->count < t->capacity;
+        return t && (t->kernel_id == id || (t->kernel_id == FA_K_FUSED_ALL && id <= 3)) &&
+               (t->level < 0 || t->level == level) && t->count < t->capacity;
     }
 };
 
@@ -1648,12 +1648,14 @@ fa_status fused_iteration(FusedBuffers &fb, WsHeader *h, const fa_params *p, Dim
                           fa_kernel_timer *timer, int level, cudaStream_t s) {
     KTimer kt{timer, level};
     auto start = [&](int id) -> cudaError_t {
-        return kt.on(id) ? cudaEventRecord((cudaEvent_t)timer->start_events[timer->count], s)
+        return kt.on(id) ? cudaEventRecordWithFlags((cudaEvent_t)timer->start_events[timer->count], s,
+                                                    cudaEventRecordExternal)
                          : cudaSuccess;
     };
     auto stop = [&](int id) -> cudaError_t {
         if (!kt.on(id)) return cudaSuccess;
-        cudaError_t e = cudaEventRecord((cudaEvent_t)timer->stop_events[timer->count], s);
+        cudaError_t e = cudaEventRecordWithFlags((cudaEvent_t)timer->stop_events[timer->count], s,
+                                                 cudaEventRecordExternal);
         timer->count++;
         return e;
     };

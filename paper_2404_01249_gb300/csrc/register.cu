@@ -4,6 +4,10 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
+#include <string>
+#include <vector>
+
 #include "ops.h"
 #include "register.h"
 #include "validate.h"
@@ -142,11 +146,13 @@ struct Timer {
     }
     cudaError_t start(int kernel_id, cudaStream_t s) const {
         if (!on(kernel_id)) return cudaSuccess;
-        return cudaEventRecord((cudaEvent_t)t->start_events[t->count], s);
+        return cudaEventRecordWithFlags((cudaEvent_t)t->start_events[t->count], s,
+                                        cudaEventRecordExternal);
     }
     cudaError_t stop(int kernel_id, cudaStream_t s) const {
         if (!on(kernel_id)) return cudaSuccess;
-        cudaError_t e = cudaEventRecord((cudaEvent_t)t->stop_events[t->count], s);
+        cudaError_t e = cudaEventRecordWithFlags((cudaEvent_t)t->stop_events[t->count], s,
+                                                 cudaEventRecordExternal);
         t->count++;
         return e;
     }
@@ -218,23 +224,15 @@ fa_status register_check(const fa_vol *fixed, const fa_vol *moving, const fa_par
     return FA_OK;
 }
 
-fa_status register_impl(const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
-                        fa_vol *u_out, float *final_loss_dev, float *final_loss_host, void *ws,
-                        size_t ws_bytes, cudaStream_t s, fa_kernel_timer *timer) {
-    FA_TRY(register_check(fixed, moving, p, u_out));
+// Everything one registration enqueues on stream s (arguments checked).
+static fa_status enqueue_registration(const fa_vol *fixed, const fa_vol *moving,
+                                      const fa_params *p, fa_vol *u_out, float *final_loss_dev,
+                                      void *ws, size_t ws_bytes, cudaStream_t s,
+                                      fa_kernel_timer *timer) {
     Dims full{fixed->D, fixed->H, fixed->W};
     const int L = p->n_levels - 1;
     Plan P;
-    make_plan(P, nullptr, ~size_t(0), full, p);
-    FA_TRY(check_ws(ws, ws_bytes, P.bytes, "fa_register"));
     make_plan(P, ws, ws_bytes, full, p);
-    if (timer) {
-        if (timer->capacity < 0 || (timer->capacity > 0 && (!timer->start_events || !timer->stop_events))) {
-            set_error("fa_register_timed: bad timer");
-            return FA_ERR_INVALID;
-        }
-        timer->count = 0;
-    }
     const float *If0 = (const float *)fixed->data, *Im0 = (const float *)moving->data;
     if (p->storage != FA_F32) {  // 16-bit images: widened once, exactly
         FA_CUDA_TRY(launch_widen(fixed->data, p->storage, P.If0, full.N(), s));
@@ -307,9 +305,165 @@ fa_status register_impl(const fa_vol *fixed, const fa_vol *moving, const fa_para
                                         cudaMemcpyDeviceToDevice, s));
         }
     }
+    return FA_OK;
+}
+
+// ------------------------------------------------------------- graph cache
+// A registration is a fixed sequence of launches for given pointers, shapes
+// and parameters.  With p->graph set, the first call records that sequence
+// as a CUDA graph (stream capture on a private stream of this host thread)
+// and later calls with the same arguments replay it with one launch.
+namespace {
+
+constexpr size_t kMaxGraphs = 64;
+
+struct GraphEntry {
+    std::string key;
+    cudaGraphExec_t exec;
+    unsigned long long kernels;  // kernel launches recorded in the graph
+    int timer_count;             // event pairs recorded in the graph
+    unsigned long long last_use;
+};
+
+std::mutex g_graph_mu;
+std::vector<GraphEntry> g_graphs;
+unsigned long long g_graph_clock = 0;
+
+std::string graph_key(int dev, const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
+                      const fa_vol *u_out, const float *final_loss_dev, const void *ws,
+                      size_t ws_bytes, const fa_kernel_timer *timer) {
+    // field by field: the structs may carry uninitialised padding
+    std::string k;
+    auto add = [&](const void *b, size_t n) { k.append((const char *)b, n); };
+    auto vol = [&](const fa_vol *v) {
+        add(&v->data, sizeof(v->data));
+        const int32_t f[5] = {v->dtype, v->C, v->D, v->H, v->W};
+        add(f, sizeof(f));
+    };
+    add(&dev, sizeof(dev));
+    vol(fixed);
+    vol(moving);
+    vol(u_out);
+    static_assert(sizeof(fa_params) == 30 * 4, "fa_params holds 30 four-byte fields, no padding");
+    add(p, sizeof(*p));
+    add(&final_loss_dev, sizeof(final_loss_dev));
+    add(&ws, sizeof(ws));
+    add(&ws_bytes, sizeof(ws_bytes));
+    if (timer) {
+        const int32_t f[3] = {timer->kernel_id, timer->level, timer->capacity};
+        add(f, sizeof(f));
+        add(&timer->start_events, sizeof(timer->start_events));
+        add(&timer->stop_events, sizeof(timer->stop_events));
+        if (timer->capacity > 0) {  // the event handles themselves
+            add(timer->start_events, sizeof(void *) * (size_t)timer->capacity);
+            add(timer->stop_events, sizeof(void *) * (size_t)timer->capacity);
+        }
+    }
+    return k;
+}
+
+cudaGraphExec_t graph_find(const std::string &key, unsigned long long *kernels,
+                           int *timer_count) {
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    for (auto &e : g_graphs)
+        if (e.key == key) {
+            e.last_use = ++g_graph_clock;
+            *kernels = e.kernels;
+            *timer_count = e.timer_count;
+            return e.exec;
+        }
+    return nullptr;
+}
+
+void graph_store(const std::string &key, cudaGraphExec_t exec, unsigned long long kernels,
+                 int timer_count) {
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    if (g_graphs.size() >= kMaxGraphs) {
+        size_t old = 0;
+        for (size_t i = 1; i < g_graphs.size(); ++i)
+            if (g_graphs[i].last_use < g_graphs[old].last_use) old = i;
+        cudaGraphExecDestroy(g_graphs[old].exec);
+        g_graphs.erase(g_graphs.begin() + (long)old);
+    }
+    g_graphs.push_back(GraphEntry{key, exec, kernels, timer_count, ++g_graph_clock});
+}
+
+// A private non-blocking stream of this host thread for captures (captures
+// cannot run on the legacy default stream the caller may be using).
+cudaError_t capture_stream(cudaStream_t *out) {
+    thread_local cudaStream_t cs[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!cs[dev]) {
+        e = cudaStreamCreateWithFlags(&cs[dev], cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+    }
+    *out = cs[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+fa_status register_impl(const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
+                        fa_vol *u_out, float *final_loss_dev, float *final_loss_host, void *ws,
+                        size_t ws_bytes, cudaStream_t s, fa_kernel_timer *timer) {
+    FA_TRY(register_check(fixed, moving, p, u_out));
+    Dims full{fixed->D, fixed->H, fixed->W};
+    Plan P;
+    make_plan(P, nullptr, ~size_t(0), full, p);
+    FA_TRY(check_ws(ws, ws_bytes, P.bytes, "fa_register"));
+    if (timer) {
+        if (timer->capacity < 0 || (timer->capacity > 0 && (!timer->start_events || !timer->stop_events))) {
+            set_error("fa_register_timed: bad timer");
+            return FA_ERR_INVALID;
+        }
+        timer->count = 0;
+    }
+    if (p->graph) {
+        int dev = 0;
+        FA_CUDA_TRY(cudaGetDevice(&dev));
+        const std::string key =
+            graph_key(dev, fixed, moving, p, u_out, final_loss_dev, ws, ws_bytes, timer);
+        unsigned long long kernels = 0;
+        int timer_count = 0;
+        cudaGraphExec_t exec = graph_find(key, &kernels, &timer_count);
+        if (!exec) {
+            // record (the launch counter counts the recorded kernels once now,
+            // for this first run, and again at every later replay)
+            cudaStream_t cs;
+            FA_CUDA_TRY(capture_stream(&cs));
+            FA_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            const unsigned long long k0 = launches_so_far();
+            const fa_status st =
+                enqueue_registration(fixed, moving, p, u_out, final_loss_dev, ws, ws_bytes, cs,
+                                     timer);
+            kernels = launches_so_far() - k0;
+            cudaGraph_t graph = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+            if (st != FA_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return st;
+            }
+            FA_CUDA_TRY(ce);
+            const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            FA_CUDA_TRY(ie);
+            graph_store(key, exec, kernels, timer ? timer->count : 0);
+        } else {
+            note_launches(kernels);
+            if (timer) timer->count = timer_count;
+        }
+        FA_CUDA_TRY(cudaGraphLaunch(exec, s));
+    } else {
+        FA_TRY(enqueue_registration(fixed, moving, p, u_out, final_loss_dev, ws, ws_bytes, s,
+                                    timer));
+    }
     if (final_loss_host) {
         FA_CUDA_TRY(cudaStreamSynchronize(s));
-        FA_CUDA_TRY(cudaMemcpy(final_loss_host, &P.h->loss, sizeof(float), cudaMemcpyDeviceToHost));
+        FA_CUDA_TRY(cudaMemcpy(final_loss_host, &((const WsHeader *)ws)->loss, sizeof(float),
+                               cudaMemcpyDeviceToHost));
         return fa_ws_status(ws, s);
     }
     return FA_OK;

@@ -29,7 +29,7 @@ FA_F32, FA_BF16, FA_F16 = 0, 1, 2
 FA_LOSS_LNCC, FA_LOSS_MSE = 0, 1
 FA_MODE_FUSED, FA_MODE_PLAIN = 0, 1
 (FA_K_FUSED_WARP_LNCC, FA_K_FUSED_LNCC_GRAD, FA_K_FUSED_SMOOTH_ADAM, FA_K_FUSED_COMPOSE,
- FA_K_PLAIN_ANY) = 0, 1, 2, 3, 4
+ FA_K_PLAIN_ANY, FA_K_FUSED_ALL) = 0, 1, 2, 3, 4, 5
 
 EXPORTED = ["fa_params_default", "fa_status_str", "fa_last_error", "fa_warp",
             "fa_lncc_workspace_size", "fa_lncc_fwd_bwd", "fa_mse_fwd_bwd",
@@ -59,7 +59,7 @@ class Params(ctypes.Structure):
                 ("window", ctypes.c_int32), ("loss", ctypes.c_int32), ("beta1", ctypes.c_float),
                 ("beta2", ctypes.c_float), ("adam_eps", ctypes.c_float),
                 ("cc_eps", ctypes.c_float), ("c_lp", ctypes.c_float), ("mode", ctypes.c_int32),
-                ("storage", ctypes.c_int32)]
+                ("storage", ctypes.c_int32), ("graph", ctypes.c_int32)]
 
 
 class KernelTimer(ctypes.Structure):
@@ -170,6 +170,7 @@ class RegParams:
     cc_eps: float = 1e-5
     c_lp: float = 2.0
     mode: str = "fused"
+    graph: bool = True   # record the launch sequence once, replay it on identical calls
 
     def to_c(self) -> Params:
         p = Params()
@@ -187,6 +188,7 @@ class RegParams:
         p.cc_eps, p.c_lp = self.cc_eps, self.c_lp
         p.mode = {"fused": FA_MODE_FUSED, "plain": FA_MODE_PLAIN}[self.mode]
         p.storage = FA_F32
+        p.graph = 1 if self.graph else 0
         return p
 
 

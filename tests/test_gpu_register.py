@@ -1,6 +1,8 @@
 """End-to-end parity of fa_register with the oracle's Algorithm 1 on the
 32^3 blobs workload (final LNCC within 1e-3, mean displacement difference
 below 0.05 voxel), plus edge cases and device status reporting."""
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -141,3 +143,34 @@ def test_16bit_images_equal_fp32_of_the_rounded_images(fa, dtype):
     a = fa.fa_register(fh, mh, p)
     b = fa.fa_register(fh.float().contiguous(), mh.float().contiguous(), p)
     assert torch.equal(a["u"], b["u"]) and a["final_loss"] == b["final_loss"]
+
+
+def test_graph_replay_equals_launch_by_launch(fa):
+    """The recorded-graph path replays exactly the launches of the direct
+    path: same bits, same launch count, and the in-graph kernel timer
+    reports its events on every replay."""
+    f, m, _ = synth.voronoi_pair(shape=(24, 28, 32), seed=13)
+    fx, mv = cuda(f), cuda(m)
+    direct = fa.fa_register(fx, mv, fa.RegParams(scales=(2, 1), iters=(8, 6), graph=False))
+    pg = fa.RegParams(scales=(2, 1), iters=(8, 6), graph=True)
+    ws = fa.workspace(fa.load().fa_register_workspace_size(24, 28, 32, ctypes.byref(pg.to_c())),
+                      fx.device)
+    u = torch.empty_like(direct["u"])
+    loss = torch.empty((), device=fx.device)
+    n0 = fa.fa_launch_count()
+    fa.fa_register(fx, mv, pg, ws=ws, u_out=u, loss_out=loss)          # records the graph
+    n1 = fa.fa_launch_count()
+    u.zero_()
+    r = fa.fa_register(fx, mv, pg, ws=ws, u_out=u, loss_out=loss)      # replays it
+    n2 = fa.fa_launch_count()
+    assert torch.equal(u, direct["u"]) and r["final_loss"] == direct["final_loss"]
+    assert n2 - n1 == n1 - n0 > 0
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(4 * 6)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(4 * 6)]
+    tm = fa.make_timer(fa.FA_K_FUSED_ALL, 1, ev0, ev1)
+    for _ in range(2):
+        fa.fa_register(fx, mv, pg, ws=ws, u_out=u, loss_out=loss, timer=tm)
+        torch.cuda.synchronize()
+        assert tm.count == 24
+        assert all(a.elapsed_time(b) > 0 for a, b in zip(ev0, ev1))
+    assert torch.equal(u, direct["u"])
