@@ -278,6 +278,27 @@ fa_status fa_register_batched(int32_t n_pairs, const fa_vol *fixed, const fa_vol
                               float *final_loss_dev, uint32_t *status_dev, int32_t concurrency,
                               void *ws, size_t ws_bytes, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Tile autotuning of the fused kernels (no counterpart in the paper).
+ * fa_autotune times, for every pyramid level of a D x H x W registration
+ * with parameters p, candidate slab depths (and 32 x 16 instead of 32 x 8
+ * tiles for the Gaussian kernels) of the four fused kernels on the given
+ * workspace (fa_register_workspace_size bytes; its contents are
+ * overwritten), waits for `stream`, and keeps the fastest choice per kernel,
+ * radius and grid for every later launch in this process.  Every choice
+ * computes the same bits; only the speed changes.  It also drops the
+ * recorded graphs (they hold the previous choices).  Not during a stream
+ * capture.  fa_autotune_reset forgets all choices; fa_autotune_choices
+ * writes up to `capacity` rows of 8 int32 (kernel 0..3, radius, compose
+ * variant, D, H, W, 16-warp tiles, slab depth) and returns the number of
+ * recorded choices.  fa_autotune_set records one such row (a choice made
+ * elsewhere, or pinned by hand). */
+fa_status fa_autotune(int32_t D, int32_t H, int32_t W, const fa_params *p, void *ws,
+                      size_t ws_bytes, void *stream);
+fa_status fa_autotune_reset(void);
+int32_t fa_autotune_choices(int32_t *rows, int32_t capacity);
+fa_status fa_autotune_set(const int32_t *row);
+
 /* Waits for `stream` and returns the status word that kernels recorded in a
  * workspace used by fa_register, fa_radam_step or fa_lncc_fwd_bwd
  * (FA_OK, FA_ERR_NONFINITE or FA_ERR_TIMEOUT). */

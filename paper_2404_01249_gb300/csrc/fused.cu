@@ -38,6 +38,7 @@
 #include <cuda.h>
 #include <math.h>
 
+#include <map>
 #include <mutex>
 
 #include "register.h"
@@ -875,7 +876,7 @@ struct K3S {
 };
 
 template <int RG, int NW, int OPT, int NSTG, bool TMA>
-__global__ void __launch_bounds__(FX *NW, 1024 / (FX * NW)) k_smooth_adam(const __grid_constant__ Maps maps,
+__global__ void __launch_bounds__(FX *NW, NW >= 16 ? 2 : 1) k_smooth_adam(const __grid_constant__ Maps maps,
                                                         const float *__restrict__ g,
                                                         float *__restrict__ m,
                                                         float *__restrict__ v,
@@ -1041,7 +1042,7 @@ struct K4S {
 };
 
 template <int RG, int NW, int OPT, bool SU, int NSTG, bool TMA>
-__global__ void __launch_bounds__(FX *NW, 1024 / (FX * NW)) k_compose(const __grid_constant__ Maps maps,
+__global__ void __launch_bounds__(FX *NW, NW >= 16 ? 2 : 1) k_compose(const __grid_constant__ Maps maps,
                                                     const float *__restrict__ u,
                                                     const float *__restrict__ dir,
                                                     float *__restrict__ uo,
@@ -1318,6 +1319,37 @@ struct LaunchGeom {
     int tz;
 };
 
+// ------------------------------------------------------------- tile choices
+// Per (kernel, radius, compose variant, level grid): the slab depth TZ
+// (0: the cost model above) and, for K3/K4 on the TMA path, 32 x 16 tiles
+// of 16 warps instead of 32 x 8.  fa_autotune measures candidates and fills
+// the table; every choice computes the same bits.
+struct TileChoice {
+    int wide, tz;
+};
+struct TuneKey {
+    int kernel, radius, su, D, H, W;
+    bool operator<(const TuneKey &o) const {
+        const int a[6] = {kernel, radius, su, D, H, W}, b[6] = {o.kernel, o.radius, o.su, o.D, o.H, o.W};
+        for (int i = 0; i < 6; ++i)
+            if (a[i] != b[i]) return a[i] < b[i];
+        return false;
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TileChoice> g_tune;
+thread_local const TileChoice *g_force = nullptr;  // a candidate under measurement
+
+constexpr int kDefaultWide[4] = {0, 0, 0, 1};
+
+TileChoice tile_choice(int kernel, int radius, int su, Dims d) {
+    if (g_force) return *g_force;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(TuneKey{kernel, radius, su, d.D, d.H, d.W});
+    if (it != g_tune.end()) return it->second;
+    return TileChoice{kDefaultWide[kernel], 0};
+}
+
 // Launch with programmatic stream serialization (see pdl_wait).
 template <class... KArgs, class... Args>
 cudaError_t launch_pdl(void (*kern)(KArgs...), const LaunchGeom &g, size_t smem, cudaStream_t s,
@@ -1335,10 +1367,10 @@ cudaError_t launch_pdl(void (*kern)(KArgs...), const LaunchGeom &g, size_t smem,
     return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
-inline LaunchGeom geometry(int occ, int nw, int ty, int halo, Dims d) {
+inline LaunchGeom geometry(int occ, int nw, int ty, int halo, Dims d, int tz = 0) {
     LaunchGeom g;
     const int gx = (d.W + FX - 1) / FX, gy = (d.H + ty - 1) / ty;
-    g.tz = choose_tz(d.D, gx * gy, halo, occ);
+    g.tz = tz > 0 ? (tz < d.D ? tz : d.D) : choose_tz(d.D, gx * gy, halo, occ);
     g.grid = dim3(gx, gy, (d.D + g.tz - 1) / g.tz);
     g.block = dim3(FX, nw);
     return g;
@@ -1415,7 +1447,7 @@ bool tmap(CUtensorMap *m, const void *base, int esize, Dims d, int C, int bx, in
 constexpr int K1_NW = 8, K1_OPT = 1, K1_ST_TMA = 3, K1_ST_CP = 3;
 constexpr int K2_NW = 8, K2_OPT = 1, K2_ST_TMA = 2, K2_ST_CP = 2;
 constexpr int K3_NW = 8, K3_OPT = 1, K3_ST_TMA = 2, K3_ST_CP = 2;
-constexpr int K4_NW = 16, K4_OPT = 1, K4_ST_TMA = 2, K4_ST_CP = 2;
+constexpr int K4_NW = 8, K4_OPT = 1, K4_ST_TMA = 2, K4_ST_CP = 2;
 
 template <int R>
 cudaError_t launch_k1(const float *If, const float *J, const long long *sI, const float *varI,
@@ -1429,17 +1461,18 @@ cudaError_t launch_k1(const float *If, const float *J, const long long *sI, cons
                      tmap(&mp.b, J, 4, d, 1, ST::BXW, ST::RY, 1) &&
                      tmap(&mp.c, sI, 8, d, 1, FX, ST::TY, 1) &&
                      tmap(&mp.d, varI, 4, d, 1, FX, ST::TY, 1);
+    const TileChoice tc = tile_choice(0, R, 0, d);
     if (tma) {
         auto kern = k_lncc_fwd<R, K1_NW, K1_OPT, K1_ST_TMA, true>;
         static const int occ = prepare(kern, ST::bytes, ST::NT);
-        LaunchGeom g = geometry(occ, K1_NW, ST::TY, R, d);
+        LaunchGeom g = geometry(occ, K1_NW, ST::TY, R, d, tc.tz);
         le = launch_pdl(kern, g, ST::bytes, s, mp, If, J, sI, varI, coef, h, d.D, d.H, d.W, g.tz,
                                                 bits, cc_eps, window, wc ? 1 : 0);
     } else {
         using SC = K1S<R, K1_NW, K1_OPT, K1_ST_CP>;
         auto kern = k_lncc_fwd<R, K1_NW, K1_OPT, K1_ST_CP, false>;
         static const int occ = prepare(kern, SC::bytes, SC::NT);
-        LaunchGeom g = geometry(occ, K1_NW, SC::TY, R, d);
+        LaunchGeom g = geometry(occ, K1_NW, SC::TY, R, d, tc.tz);
         le = launch_pdl(kern, g, SC::bytes, s, mp, If, J, sI, varI, coef, h, d.D, d.H, d.W, g.tz,
                                                 bits, cc_eps, window, wc ? 1 : 0);
     }
@@ -1457,17 +1490,18 @@ cudaError_t launch_k2(const float *If, const float *Im, const float *u, const fl
     const bool tma = tmap(&mp.a, coef, 4, d, 4, ST::BXW, ST::RY, 4) &&
                      tmap(&mp.b, u, 4, d, 3, FX, ST::TY, 3) &&
                      tmap(&mp.c, If, 4, d, 1, FX, ST::TY, 1);
+    const TileChoice tc = tile_choice(1, R, 0, d);
     if (tma) {
         auto kern = k_lncc_grad<R, K2_NW, K2_OPT, K2_ST_TMA, true>;
         static const int occ = prepare(kern, ST::bytes, ST::NT);
-        LaunchGeom gg = geometry(occ, K2_NW, ST::TY, R, d);
+        LaunchGeom gg = geometry(occ, K2_NW, ST::TY, R, d, tc.tz);
         le = launch_pdl(kern, gg, ST::bytes, s, mp, If, Im, u, coef, h, g, d.D, d.H, d.W, gg.tz,
                                                   cb);
     } else {
         using SC = K2S<R, K2_NW, K2_OPT, K2_ST_CP>;
         auto kern = k_lncc_grad<R, K2_NW, K2_OPT, K2_ST_CP, false>;
         static const int occ = prepare(kern, SC::bytes, SC::NT);
-        LaunchGeom gg = geometry(occ, K2_NW, SC::TY, R, d);
+        LaunchGeom gg = geometry(occ, K2_NW, SC::TY, R, d, tc.tz);
         le = launch_pdl(kern, gg, SC::bytes, s, mp, If, Im, u, coef, h, g, d.D, d.H, d.W, gg.tz,
                                                   cb);
     }
@@ -1475,31 +1509,52 @@ cudaError_t launch_k2(const float *If, const float *Im, const float *u, const fl
     return le;
 }
 
+template <int RG, int NW>
+cudaError_t launch_k3_tma(const Maps &mp, const float *g, float *m, float *v, float *dir,
+                          WsHeader *h, Dims d, const GaussTaps &t, AdamConsts ac, int parity,
+                          int tz, cudaStream_t s) {
+    using ST = K3S<RG, NW, K3_OPT, K3_ST_TMA>;
+    auto kern = k_smooth_adam<RG, NW, K3_OPT, K3_ST_TMA, true>;
+    static const int occ = prepare(kern, ST::bytes, ST::NT);
+    LaunchGeom gg = geometry(occ, NW, ST::TY, RG, d, tz);
+    return launch_pdl(kern, gg, ST::bytes, s, mp, g, m, v, dir, h, d.D, d.H, d.W, gg.tz, t, ac,
+                      parity);
+}
+
 template <int RG>
 cudaError_t launch_k3(const float *g, float *m, float *v, float *dir, WsHeader *h, Dims d,
                       const GaussTaps &t, AdamConsts ac, int parity, cudaStream_t s) {
     Maps mp{};
     cudaError_t le;
-    using ST = K3S<RG, K3_NW, K3_OPT, K3_ST_TMA>;
-    const bool tma = tmap(&mp.a, g, 4, d, 3, ST::BXW, ST::RY, 3) &&
-                     tmap(&mp.b, m, 4, d, 3, FX, ST::TY, 3) &&
-                     tmap(&mp.c, v, 4, d, 3, FX, ST::TY, 3);
+    const TileChoice tc = tile_choice(2, RG, 0, d);
+    const int nw = tc.wide ? 16 : 8;
+    const bool tma = tmap(&mp.a, g, 4, d, 3, FX + 2 * halo4(RG), nw + 2 * RG, 3) &&
+                     tmap(&mp.b, m, 4, d, 3, FX, nw, 3) && tmap(&mp.c, v, 4, d, 3, FX, nw, 3);
     if (tma) {
-        auto kern = k_smooth_adam<RG, K3_NW, K3_OPT, K3_ST_TMA, true>;
-        static const int occ = prepare(kern, ST::bytes, ST::NT);
-        LaunchGeom gg = geometry(occ, K3_NW, ST::TY, RG, d);
-        le = launch_pdl(kern, gg, ST::bytes, s, mp, g, m, v, dir, h, d.D, d.H, d.W, gg.tz, t, ac,
-                                                  parity);
+        le = tc.wide ? launch_k3_tma<RG, 16>(mp, g, m, v, dir, h, d, t, ac, parity, tc.tz, s)
+                     : launch_k3_tma<RG, 8>(mp, g, m, v, dir, h, d, t, ac, parity, tc.tz, s);
     } else {
         using SC = K3S<RG, K3_NW, K3_OPT, K3_ST_CP>;
         auto kern = k_smooth_adam<RG, K3_NW, K3_OPT, K3_ST_CP, false>;
         static const int occ = prepare(kern, SC::bytes, SC::NT);
-        LaunchGeom gg = geometry(occ, K3_NW, SC::TY, RG, d);
+        LaunchGeom gg = geometry(occ, K3_NW, SC::TY, RG, d, tc.tz);
         le = launch_pdl(kern, gg, SC::bytes, s, mp, g, m, v, dir, h, d.D, d.H, d.W, gg.tz, t, ac,
-                                                  parity);
+                        parity);
     }
     note_launch();
     return le;
+}
+
+template <int RG, bool SU, int NW>
+cudaError_t launch_k4_tma(const Maps &mp, const float *u, const float *dir, float *uo,
+                          const float *Im, float *J, WsHeader *h, Dims d, const GaussTaps &t,
+                          float lr, float c_lp, int parity, int tz, cudaStream_t s) {
+    using ST = K4S<RG, NW, K4_OPT, SU, K4_ST_TMA>;
+    auto kern = k_compose<RG, NW, K4_OPT, SU, K4_ST_TMA, true>;
+    static const int occ = prepare(kern, ST::bytes, ST::NT);
+    LaunchGeom gg = geometry(occ, NW, ST::TY, RG, d, tz);
+    return launch_pdl(kern, gg, ST::bytes, s, mp, u, dir, uo, Im, J, h, d.D, d.H, d.W, gg.tz, t,
+                      lr, c_lp, parity);
 }
 
 template <int RG, bool SU>
@@ -1508,22 +1563,22 @@ cudaError_t launch_k4(const float *u, const float *dir, float *uo, const float *
                       cudaStream_t s) {
     Maps mp{};
     cudaError_t le;
-    using ST = K4S<RG, K4_NW, K4_OPT, SU, K4_ST_TMA>;
-    const bool tma = tmap(&mp.a, dir, 4, d, 3, ST::BXW, ST::RY, 3) &&
-                     (!SU || tmap(&mp.b, u, 4, d, 3, ST::UBXW, ST::URY, 3));
+    const TileChoice tc = tile_choice(3, RG, SU ? 1 : 0, d);
+    const int nw = tc.wide ? 16 : 8;
+    const bool tma = tmap(&mp.a, dir, 4, d, 3, FX + 2 * halo4(RG), nw + 2 * RG, 3) &&
+                     (!SU || tmap(&mp.b, u, 4, d, 3, FX + 2 * halo4(RG + 1), nw + 2 * RG + 2, 3));
     if (tma) {
-        auto kern = k_compose<RG, K4_NW, K4_OPT, SU, K4_ST_TMA, true>;
-        static const int occ = prepare(kern, ST::bytes, ST::NT);
-        LaunchGeom gg = geometry(occ, K4_NW, ST::TY, RG, d);
-        le = launch_pdl(kern, gg, ST::bytes, s, mp, u, dir, uo, Im, J, h, d.D, d.H, d.W, gg.tz,
-                                                  t, lr, c_lp, parity);
+        le = tc.wide ? launch_k4_tma<RG, SU, 16>(mp, u, dir, uo, Im, J, h, d, t, lr, c_lp, parity,
+                                                 tc.tz, s)
+                     : launch_k4_tma<RG, SU, 8>(mp, u, dir, uo, Im, J, h, d, t, lr, c_lp, parity,
+                                                tc.tz, s);
     } else {
         using SC = K4S<RG, K4_NW, K4_OPT, SU, K4_ST_CP>;
         auto kern = k_compose<RG, K4_NW, K4_OPT, SU, K4_ST_CP, false>;
         static const int occ = prepare(kern, SC::bytes, SC::NT);
-        LaunchGeom gg = geometry(occ, K4_NW, SC::TY, RG, d);
-        le = launch_pdl(kern, gg, SC::bytes, s, mp, u, dir, uo, Im, J, h, d.D, d.H, d.W, gg.tz,
-                                                  t, lr, c_lp, parity);
+        LaunchGeom gg = geometry(occ, K4_NW, SC::TY, RG, d, tc.tz);
+        le = launch_pdl(kern, gg, SC::bytes, s, mp, u, dir, uo, Im, J, h, d.D, d.H, d.W, gg.tz, t,
+                        lr, c_lp, parity);
     }
     note_launch();
     return le;
@@ -1700,6 +1755,102 @@ fa_status fused_iteration(FusedBuffers &fb, WsHeader *h, const fa_params *p, Dim
         FA_CUDA_TRY(launch_warp(it.Im, it.u_alt, fb.J, nullptr, d, s));  // J of the smoothed map
     }
     return FA_OK;
+}
+
+fa_status fused_autotune_level(FusedBuffers &fb, WsHeader *h, const fa_params *p, Dims d,
+                               const float *If, const float *Im, float *u, float *u_alt, float *m,
+                               float *v, const GaussTaps &tg, const GaussTaps &tw,
+                               cudaStream_t s) {
+    static const GaussTaps ident = [] {
+        GaussTaps t;
+        make_gauss_taps(0.0f, &t);
+        return t;
+    }();
+    const GaussTaps &g3 = tg.R > kMaxFusedRG ? ident : tg;
+    const GaussTaps &g4 = tw.R > kMaxFusedRG ? ident : tw;
+    const bool su = (double)p->lr / (double)p->c_lp < 0.999;
+    const AdamConsts ac = adam_consts(p, 1);
+    auto launch = [&](int kernel) -> cudaError_t {
+        switch (kernel) {
+            case 0:
+                return dispatch_k1(If, fb.J, fb.sI, fb.varI, fb.coef, h, d, p->window, p->cc_eps,
+                                   true, s);
+            case 1: return dispatch_k2(If, Im, u, fb.coef, h, fb.g, d, p->window, s);
+            case 2: return dispatch_k3(fb.g, m, v, fb.dir, h, d, g3, ac, 0, s);
+            default:
+                return dispatch_k4(u, fb.dir, u_alt, Im, fb.J, h, d, g4, p->lr, p->c_lp, 0, su, s);
+        }
+    };
+    cudaEvent_t e0, e1;
+    FA_CUDA_TRY(cudaEventCreate(&e0));
+    FA_CUDA_TRY(cudaEventCreate(&e1));
+    const int tzs[] = {0, 1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64};
+    fa_status result = FA_OK;
+    for (int kernel = (p->loss == FA_LOSS_LNCC ? 0 : 2); kernel < 4 && result == FA_OK; ++kernel) {
+        const int radius = kernel < 2 ? p->window / 2 : (kernel == 2 ? g3.R : g4.R);
+        const int sukey = kernel == 3 && su ? 1 : 0;
+        TileChoice best{kDefaultWide[kernel], 0};
+        float best_ms = -1.0f;
+        for (int wide = 0; wide < (kernel >= 2 ? 2 : 1) && result == FA_OK; ++wide)
+            for (int tz : tzs) {
+                if (tz > d.D) continue;
+                const TileChoice c{wide, tz};
+                g_force = &c;
+                cudaError_t e = launch(kernel);  // warm
+                if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+                for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch(kernel);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                g_force = nullptr;
+                float ms = 0.0f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) {
+                    result = cuda_fail(e, "fa_autotune");
+                    break;
+                }
+                if (best_ms < 0.0f || ms < best_ms) {
+                    best_ms = ms;
+                    best = c;
+                }
+            }
+        if (result == FA_OK) {
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            g_tune[TuneKey{kernel, radius, sukey, d.D, d.H, d.W}] = best;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return result;
+}
+
+void fused_tile_set(const int32_t *r) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[TuneKey{r[0], r[1], r[2], r[3], r[4], r[5]}] = TileChoice{r[6] ? 1 : 0, r[7]};
+}
+
+void fused_autotune_reset() {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune.clear();
+}
+
+int fused_tile_choices(int32_t *out, int capacity) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    int n = 0;
+    for (const auto &kv : g_tune) {
+        if (n < capacity && out) {
+            int32_t *r = out + 8 * n;
+            r[0] = kv.first.kernel;
+            r[1] = kv.first.radius;
+            r[2] = kv.first.su;
+            r[3] = kv.first.D;
+            r[4] = kv.first.H;
+            r[5] = kv.first.W;
+            r[6] = kv.second.wide;
+            r[7] = kv.second.tz;
+        }
+        ++n;
+    }
+    return n;
 }
 
 cudaError_t fused_lncc_forward_only(const float *If, const FusedBuffers &fb, Dims d, int window,

@@ -388,6 +388,12 @@ void graph_store(const std::string &key, cudaGraphExec_t exec, unsigned long lon
     g_graphs.push_back(GraphEntry{key, exec, kernels, timer_count, ++g_graph_clock});
 }
 
+void graph_cache_clear() {
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    for (auto &e : g_graphs) cudaGraphExecDestroy(e.exec);
+    g_graphs.clear();
+}
+
 // A private non-blocking stream of this host thread for captures (captures
 // cannot run on the legacy default stream the caller may be using).
 cudaError_t capture_stream(cudaStream_t *out) {
@@ -489,6 +495,65 @@ extern "C" fa_status fa_register(const fa_vol *fixed, const fa_vol *moving, cons
     fa::clear_error();
     return fa::register_impl(fixed, moving, p, u_out, final_loss_dev, final_loss_host, ws,
                              ws_bytes, (cudaStream_t)stream, nullptr);
+}
+
+extern "C" fa_status fa_autotune(int32_t D, int32_t H, int32_t W, const fa_params *p, void *ws,
+                                 size_t ws_bytes, void *stream) {
+    using namespace fa;
+    clear_error();
+    if (D < 1 || H < 1 || W < 1) {
+        set_error("fa_autotune: grid must be positive");
+        return FA_ERR_SHAPE;
+    }
+    FA_TRY(check_params(p));
+    if (p->mode != FA_MODE_FUSED) return FA_OK;  // the per-op kernels have no choices
+    Dims full{D, H, W};
+    Plan P;
+    make_plan(P, nullptr, ~size_t(0), full, p);
+    FA_TRY(check_ws(ws, ws_bytes, P.bytes, "fa_autotune"));
+    make_plan(P, ws, ws_bytes, full, p);
+    cudaStream_t s = (cudaStream_t)stream;
+    FA_CUDA_TRY(cudaMemsetAsync(ws, 0, P.bytes, s));
+    GaussTaps tg, tw;
+    make_gauss_taps(p->sigma_grad, &tg);
+    make_gauss_taps(p->sigma_warp, &tw);
+    for (int l = 0; l < p->n_levels; ++l) {
+        const Dims d = P.lvl[l];
+        // stand-in images (zeros): timing does not depend on the values much,
+        // and every choice computes the same bits
+        const float *If = P.If[l] ? P.If[l] : P.t1;
+        const float *Im = P.Im[l] ? P.Im[l] : P.t2;
+        FA_TRY(fused_autotune_level(P.fb, P.h, p, d, If, Im, P.u[0], P.u[1], P.m[0], P.v[0], tg,
+                                    tw, s));
+    }
+    graph_cache_clear();  // recorded graphs hold the previous choices
+    return FA_OK;
+}
+
+extern "C" fa_status fa_autotune_reset(void) {
+    fa::clear_error();
+    fa::fused_autotune_reset();
+    fa::graph_cache_clear();
+    return FA_OK;
+}
+
+extern "C" fa_status fa_autotune_set(const int32_t *row) {
+    using namespace fa;
+    clear_error();
+    if (!row || row[0] < 0 || row[0] > 3 || row[1] < 0 || row[1] > 7 || row[2] < 0 || row[2] > 1 ||
+        row[3] < 1 || row[4] < 1 || row[5] < 1 || row[6] < 0 || row[6] > 1 || row[7] < 0) {
+        set_error("fa_autotune_set: row must be (kernel 0..3, radius 0..7, variant 0..1, D, H, W "
+                  "> 0, wide 0..1, tz >= 0)");
+        return FA_ERR_INVALID;
+    }
+    fused_tile_set(row);
+    graph_cache_clear();
+    return FA_OK;
+}
+
+extern "C" int32_t fa_autotune_choices(int32_t *rows, int32_t capacity) {
+    fa::clear_error();
+    return fa::fused_tile_choices(rows, capacity);
 }
 
 extern "C" fa_status fa_register_timed(const fa_vol *fixed, const fa_vol *moving,

@@ -31,6 +31,16 @@ fa_status fused_iteration(FusedBuffers &fb, WsHeader *h, const fa_params *p, Dim
 cudaError_t fused_level_start(const float *If, const float *Im, const float *u, Dims d,
                               const fa_params *p, const WsHeader *h, FusedBuffers &fb,
                               cudaStream_t s);
+// Measures candidate tile choices of the fused kernels on grid d (any
+// buffer contents) and records the fastest for later launches.
+fa_status fused_autotune_level(FusedBuffers &fb, WsHeader *h, const fa_params *p, Dims d,
+                               const float *If, const float *Im, float *u, float *u_alt, float *m,
+                               float *v, const GaussTaps &tg, const GaussTaps &tw, cudaStream_t s);
+void fused_autotune_reset();
+void fused_tile_set(const int32_t *row);  // one row as fused_tile_choices writes it
+// Recorded choices as rows of 8 int32 (kernel, radius, compose variant, D, H,
+// W, 16-warp tiles, TZ); returns the number of rows.
+int fused_tile_choices(int32_t *out, int capacity);
 // LNCC loss accumulator only (no coefficients) for the warped image fb.J.
 cudaError_t fused_lncc_forward_only(const float *If, const FusedBuffers &fb, Dims d, int window,
                                     float cc_eps, WsHeader *h, cudaStream_t s);

@@ -38,7 +38,8 @@ EXPORTED = ["fa_params_default", "fa_status_str", "fa_last_error", "fa_warp",
             "fa_register_workspace_size", "fa_register", "fa_ws_status", "fa_register_timed",
             "fa_launch_count", "fa_lncc_fwd_bwd_noalloc", "fa_register_batched_workspace_size",
             "fa_register_batched", "fa_warp_lncc_adjoint_workspace_size",
-            "fa_warp_lncc_adjoint"]
+            "fa_warp_lncc_adjoint", "fa_autotune", "fa_autotune_reset", "fa_autotune_choices",
+            "fa_autotune_set"]
 
 
 class FAError(RuntimeError):
@@ -109,6 +110,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "fa_register_batched": (i32, [i32, V, V, i32, P, V, vp, vp, i32, vp, sz, vp]),
         "fa_warp_lncc_adjoint_workspace_size": (sz, [i32, i32, i32]),
         "fa_warp_lncc_adjoint": (i32, [V, V, V, i32, f32, vp, V, V, V, vp, sz, vp]),
+        "fa_autotune": (i32, [i32, i32, i32, P, vp, sz, vp]),
+        "fa_autotune_reset": (i32, []),
+        "fa_autotune_choices": (i32, [ctypes.POINTER(ctypes.c_int32), i32]),
+        "fa_autotune_set": (i32, [ctypes.POINTER(ctypes.c_int32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -377,6 +382,37 @@ def fa_warp_lncc_adjoint(fixed, moving, u, window: int = 5, cc_eps: float = 1e-5
                                     float(cc_eps), _ptr(loss), _vol(du, 3), _vol(dfx, 1),
                                     _vol(dmv, 1), _ptr(ws), ws.numel(), _stream()))
     return dict(loss=loss, dL_du=du, dL_dfixed=dfx, dL_dmoving=dmv)
+
+
+def fa_autotune(shape, params: RegParams, ws: Optional[torch.Tensor] = None, device=None):
+    """Tunes the fused kernels' tiles for registrations of this shape and
+    these parameters (waits for the GPU).  Returns the recorded choices."""
+    D, H, W = shape
+    p = params.to_c()
+    lib = load()
+    need = lib.fa_register_workspace_size(D, H, W, ctypes.byref(p))
+    ws = ws if ws is not None else workspace(need, device or torch.device("cuda"))
+    _check(lib.fa_autotune(D, H, W, ctypes.byref(p), _ptr(ws), ws.numel(), _stream()))
+    return fa_autotune_choices()
+
+
+def fa_autotune_choices():
+    lib = load()
+    n = lib.fa_autotune_choices(None, 0)
+    rows = (ctypes.c_int32 * (8 * max(n, 1)))()
+    n = lib.fa_autotune_choices(rows, n)
+    keys = ("kernel", "radius", "compose_variant", "D", "H", "W", "wide", "tz")
+    return [dict(zip(keys, rows[8 * i:8 * i + 8])) for i in range(n)]
+
+
+def fa_autotune_set(kernel: int, radius: int, compose_variant: int, D: int, H: int, W: int,
+                    wide: int, tz: int):
+    row = (ctypes.c_int32 * 8)(kernel, radius, compose_variant, D, H, W, wide, tz)
+    _check(load().fa_autotune_set(row))
+
+
+def fa_autotune_reset():
+    _check(load().fa_autotune_reset())
 
 
 def fa_launch_count() -> int:

@@ -174,3 +174,31 @@ def test_graph_replay_equals_launch_by_launch(fa):
         assert tm.count == 24
         assert all(a.elapsed_time(b) > 0 for a, b in zip(ev0, ev1))
     assert torch.equal(u, direct["u"])
+
+
+def test_tile_choices_change_speed_not_bits(fa):
+    """Every tile choice (slab depth, 32x8 or 32x16 tiles) of the fused
+    kernels computes the same bits: the window sums are exact integers and
+    each output's filters run in the same order; the autotuner only picks
+    the fastest."""
+    shape = (40, 48, 56)
+    f, m, _ = synth.voronoi_pair(shape=shape, seed=17)
+    fx, mv = cuda(f), cuda(m)
+    p = fa.RegParams(scales=(2, 1), iters=(6, 4), graph=False)
+    fa.fa_autotune_reset()
+    base = fa.fa_register(fx, mv, p)
+    lv = [(20, 24, 28), shape]
+    try:
+        for wide, tz in [(0, 1), (1, 3), (0, 7), (1, 64)]:
+            for (D, H, W) in lv:
+                for k, rad in [(0, 2), (1, 2), (2, 3), (3, 2)]:
+                    fa.fa_autotune_set(k, rad, 1 if k == 3 else 0, D, H, W, wide, tz)
+            r = fa.fa_register(fx, mv, p)
+            assert torch.equal(r["u"], base["u"]) and r["final_loss"] == base["final_loss"]
+        fa.fa_autotune_reset()
+        choices = fa.fa_autotune(shape, p)
+        assert len(choices) == 8 and all(c["tz"] >= 0 for c in choices)
+        r = fa.fa_register(fx, mv, p)
+        assert torch.equal(r["u"], base["u"]) and r["final_loss"] == base["final_loss"]
+    finally:
+        fa.fa_autotune_reset()
