@@ -99,3 +99,65 @@ def test_template_gradient_on_gpu_matches_oracle(fa, orc):
         ref_l += r["loss"]
     assert rel(g, ref_g / 3) < TOL
     assert abs(float(loss) - ref_l / 3) < 1e-5
+
+
+def test_adjoint_against_fp64_central_differences(fa, orc):
+    """dL/du, dL/dI_m and dL/dI_f from the GPU against FP64 central finite
+    differences (h = 1e-4) of the oracle's loss at 48^3, on voxels whose
+    warped position stays at least 10 h away from the trilinear kinks."""
+    shape = (48, 48, 48)
+    f, m, _ = synth.voronoi_pair(shape=shape, seed=48)
+    u = synth.random_field(shape, 3.0, 2.0, seed=49).astype(np.float32)
+    r = fa.fa_warp_lncc_adjoint(cuda(f), cuda(m), cuda(u), 5, 1e-5)
+    du, dm, dfx = (r[k].cpu().double().numpy() for k in ("dL_du", "dL_dmoving", "dL_dfixed"))
+    f64, m64, u64 = f.astype(np.float64), m.astype(np.float64), u.astype(np.float64)
+
+    def loss(ff, mm, uu):
+        return orc.lncc(ff, orc.warp(mm, uu, want_grad=False), 5, float(np.float32(1e-5)),
+                        want_dJ=False)["loss"]
+
+    h = 1e-4
+    rng = np.random.default_rng(7)
+    z, y, x = np.meshgrid(*[np.arange(n) for n in shape], indexing="ij")
+    pos = np.stack([z, y, x]) + u64
+    frac = np.abs(pos - np.round(pos)).min(axis=0)
+    inner = (frac > 10 * h)
+    inner[:4], inner[-4:], inner[:, :4], inner[:, -4:], inner[:, :, :4], inner[:, :, -4:] = (False,) * 6
+    cand = np.argwhere(inner & (np.abs(m64) > 0))
+    picks = cand[rng.choice(len(cand), 6, replace=False)]
+    for (a, b, c) in picks:
+        for ch in range(3):
+            up, um = u64.copy(), u64.copy()
+            up[ch, a, b, c] += h
+            um[ch, a, b, c] -= h
+            fd = (loss(f64, m64, up) - loss(f64, m64, um)) / (2 * h)
+            assert abs(du[ch, a, b, c] - fd) <= 1e-4 * np.abs(du).max(), (a, b, c, ch)
+        mp, mq = m64.copy(), m64.copy()
+        mp[a, b, c] += h
+        mq[a, b, c] -= h
+        fd = (loss(f64, mp, u64) - loss(f64, mq, u64)) / (2 * h)
+        assert abs(dm[a, b, c] - fd) <= 1e-4 * np.abs(dm).max(), (a, b, c)
+        fp, fq = f64.copy(), f64.copy()
+        fp[a, b, c] += h
+        fq[a, b, c] -= h
+        fd = (loss(fp, m64, u64) - loss(fq, m64, u64)) / (2 * h)
+        assert abs(dfx[a, b, c] - fd) <= 1e-4 * np.abs(dfx).max(), (a, b, c)
+
+
+def test_template_gradient_eight_subjects_48(fa, orc):
+    """The template step of the atlas workload: 8 subjects at 48^3, the mean
+    template gradient on the GPU against the oracle's."""
+    from paper_2404_01249_gb300.template import template_gradient
+    shape = (48, 48, 48)
+    T = synth.voronoi_pair(shape=shape, seed=400)[0]
+    subs = [synth.voronoi_pair(shape=shape, seed=401 + i)[1] for i in range(8)]
+    us = [synth.random_field(shape, 3.0, 1.5, seed=420 + i).astype(np.float32) for i in range(8)]
+    loss, g = template_gradient(cuda(T), [cuda(s) for s in subs], [cuda(u) for u in us])
+    ref_g, ref_l = np.zeros(shape), 0.0
+    for s, u in zip(subs, us):
+        J, _ = fa.fa_warp(cuda(T), cuda(u))
+        r = orc.lncc(s, J.cpu().numpy(), 5, np.float32(1e-5), want_dJ=True)
+        ref_g += orc.warp_adjoint(r["dJ"], u, shape)
+        ref_l += r["loss"]
+    assert rel(g, ref_g / 8) < TOL
+    assert abs(float(loss) - ref_l / 8) < 1e-5
