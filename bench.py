@@ -37,9 +37,9 @@ HBM_FALLBACK_GBS = 6800.0
 # field read once, every output field written once (fp32 storage, S_I int64)
 ALGO_BYTES = {
     "fused_warp_lncc": 4 + 4 + 8 + 4 + 16,      # I_f, J, S_I, var_I read; A, B, C hi/lo written
-    "fused_lncc_grad": 16 + 12 + 4 + 4 + 12,    # A, B, C hi/lo, u, I_f, I_m read; g written
+    "fused_lncc_grad": 16 + 12 + 4 + 4 + 12,    # A, B, C hi/lo, grad I_m(phi), I_f, J read; g written
     "fused_smooth_adam": 12 * 3 + 12 * 3,       # g, m, v read; m, v, d written
-    "fused_compose": 12 + 12 + 4 + 12 + 4,      # d, u, I_m read; u', J written
+    "fused_compose": 12 + 12 + 4 + 12 + 4 + 12,  # d, u, I_m read; u', J, grad I_m(phi') written
     "plain_iteration": 80,                      # whole iteration: I_f, I_m, u, m, v once
 }
 # the whole path per voxel-iteration: read I_f, I_m, u, m, v, write u, m, v

@@ -6,13 +6,15 @@
 //                       and variance come precomputed per level), cc, the
 //                       adjoint coefficients A, B, C, the loss accumulator and
 //                       the coefficient maxima.
-//   K2 k_lncc_grad      adjoint window sums of A, B, C; J and grad I_m o phi
-//                       at the output voxel; g = dL/dJ grad.
+//   K2 k_lncc_grad      adjoint window sums of A, B, C; g = dL/dJ grad I_m(phi)
+//                       with J and grad I_m(phi) as the compose kernel stored
+//                       them.
 //   K3 k_smooth_adam    Gaussian(sigma_grad) of g, Adam update of m, nu, the
 //                       direction d and the grid max |d|.
 //   K4 k_compose        delta = -eps_t d, u' = delta + u o (id + delta),
-//                       Gaussian(sigma_warp) of u', and J = I_m o (id + u) of
-//                       the new map for the next iteration's K1.
+//                       Gaussian(sigma_warp) of u', and J = I_m o (id + u')
+//                       with its gradient grad I_m(phi') for the next
+//                       iteration's K1 and K2 (one gather per iteration).
 // The grid max of K3 is a global dependency, so K4 cannot join K3; the
 // adjoint window sums need A, B, C around every output, so K2 cannot join K1
 // without recomputing a much wider halo.
@@ -201,6 +203,16 @@ struct Outs {
             const int y = y0 + wy + NW * o, x = x0 + tx;
             off[o] = (y < H && x < W) ? y * W + x : -1;
         }
+    }
+    // C channels of this thread's outputs on plane zoff / (H W), to registers
+    // (zero outside the grid)
+    template <int C, class T>
+    __device__ __forceinline__ void fetch(T (&r)[OPT][C], const T *src, long long N,
+                                          long long zoff) const {
+#pragma unroll
+        for (int o = 0; o < OPT; ++o)
+#pragma unroll
+            for (int c = 0; c < C; ++c) r[o][c] = off[o] >= 0 ? src[c * N + zoff + off[o]] : T(0);
     }
     template <int C, class T>
     __device__ __forceinline__ void load(T *dst, const T *src, long long N, long long zoff,
@@ -441,11 +453,9 @@ struct K1S {
     static constexpr int NR = BXW * RY, NS = 2 * R + 1, NOUT = NT * OPT;
     static constexpr size_t plane = al128((size_t)NR * 4);  // I_f plane, then J plane
     static constexpr size_t st_bytes = 2 * plane;
-    static constexpr size_t ost_bytes = al128((size_t)NOUT * 12);  // S_I (int64), var_I
-    static constexpr unsigned tx_plane = 2u * NR * 4, tx_out = NOUT * 12u;
+    static constexpr unsigned tx_plane = 2u * NR * 4;
     static constexpr size_t o_st = 0;
-    static constexpr size_t o_ost = o_st + st_bytes * NSTG;
-    static constexpr size_t o_ring = o_ost + ost_bytes * NSTG;           // [NS][3][NOUT] int64
+    static constexpr size_t o_ring = o_st + st_bytes * NSTG;             // [NS][3][NOUT] int64
     static constexpr size_t o_xL = o_ring + (size_t)NS * 3 * NOUT * 8;   // [3][RY][FX] int64
     static constexpr size_t o_q = o_xL + (size_t)3 * RY * FX * 8;        // [2][RY][BXW] int32
     static constexpr size_t o_bar = al128(o_q + (size_t)2 * NR * 4);
@@ -476,7 +486,6 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const __grid_constant__ Map
     __shared__ unsigned long long redu[32];
     __shared__ int flag;
     auto stage = [&](int s) { return (float *)(smem + S::o_st + S::st_bytes * s); };
-    auto ostage = [&](int s) { return (long long *)(smem + S::o_ost + S::ost_bytes * s); };
 
     const int tx = threadIdx.x, wy = threadIdx.y, tid = wy * FX + tx;
     const int x0 = blockIdx.x * FX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
@@ -507,32 +516,33 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const __grid_constant__ Map
 
     const int zs = z0 - R, np = zend - z0 + 2 * R;
     auto issue = [&](int i) {
-        const int zp = zs + i, zo = zp - R, s = i % NSTG;
-        const bool out = zo >= z0 && zo < zend;
+        const int zp = zs + i, s = i % NSTG;
         if (TMA) {
             if (tid == 0 && i < np) {
-                mbar_expect(bar + s, S::tx_plane + (out ? S::tx_out : 0u));
+                mbar_expect(bar + s, S::tx_plane);
                 tma4(stage(s), &maps.a, x0 - XB, y0 - R, zp, 0, bar + s);
                 tma4(stage(s) + CS, &maps.b, x0 - XB, y0 - R, zp, 0, bar + s);
-                if (out) {
-                    tma4(ostage(s), &maps.c, x0, y0, zo, 0, bar + s);
-                    tma4(ostage(s) + NOUT, &maps.d, x0, y0, zo, 0, bar + s);
-                }
             }
         } else {
             if (i < np) {
                 const bool zok = zp >= 0 && zp < D;
                 rg.template load<1>(stage(s), If, N, (long long)zp * HW, zok);
                 rg.template load<1>(stage(s) + CS, J, N, (long long)zp * HW, zok);
-                if (out) {
-                    ou.template load<1, long long>(ostage(s), SIg, N, (long long)zo * HW, tid);
-                    ou.template load<1, float>((float *)(ostage(s) + NOUT), varIg, N,
-                                               (long long)zo * HW, tid);
-                }
             }
             cp_commit();
         }
     };
+    // the outputs' operands S_I, var_I, loaded one plane ahead into registers
+    long long a1n[OPT][1];
+    float vIn[OPT][1];
+    auto fetch_ops = [&](int i) {
+        const int zo = zs + i - R;
+        if (i < np && zo >= z0 && zo < zend) {
+            ou.fetch(a1n, SIg, N, (long long)zo * HW);
+            ou.fetch(vIn, varIg, N, (long long)zo * HW);
+        }
+    };
+    fetch_ops(0);
 #pragma unroll
     for (int k = 0; k < NSTG - 1; ++k) issue(k);
 
@@ -543,23 +553,20 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const __grid_constant__ Map
     for (int i = 0; i < np; ++i) {
         const int zp = zs + i, z = zp - R, s = i % NSTG;
         issue(i + NSTG - 1);
+        const bool out = z >= z0 && z < zend;
+        long long a1[OPT];
+        float vI[OPT];
+#pragma unroll
+        for (int o = 0; o < OPT; ++o) {
+            a1[o] = a1n[o][0];
+            vI[o] = vIn[o][0];
+        }
+        fetch_ops(i + 1);
         bool ok = true;
         if (TMA)
             ok = mbar_wait(bar + s, (unsigned)(i / NSTG) & 1u);
         else
             cp_wait<NSTG - 1>();
-        const bool out = z >= z0 && z < zend;
-        // the outputs' operands, read before the barrier that frees the stage
-        long long a1[OPT];
-        float vI[OPT];
-        if (out) {
-            const long long *od = ostage(s);
-#pragma unroll
-            for (int o = 0; o < OPT; ++o) {
-                a1[o] = od[o * NT + tid];
-                vI[o] = ((const float *)(od + NOUT))[o * NT + tid];
-            }
-        }
         const bool zin = zp >= 0 && zp < D;
         if (zin) {
             const float *sI = stage(s), *sJ = sI + CS;
@@ -656,11 +663,9 @@ struct K2S {
     static constexpr int XB = halo4(R), BXW = FX + 2 * XB, COFF = XB - R;
     static constexpr int NR = BXW * RY, NS = 2 * R + 1, NOUT = NT * OPT;
     static constexpr size_t st_bytes = al128((size_t)4 * NR * 4);    // A, B, C hi, C lo
-    static constexpr size_t ost_bytes = al128((size_t)4 * NOUT * 4);  // u (3), I_f
-    static constexpr unsigned tx_plane = 4u * NR * 4, tx_out = 4u * NOUT * 4;
+    static constexpr unsigned tx_plane = 4u * NR * 4;
     static constexpr size_t o_st = 0;
-    static constexpr size_t o_ost = o_st + st_bytes * NSTG;
-    static constexpr size_t o_ring = o_ost + ost_bytes * NSTG;
+    static constexpr size_t o_ring = o_st + st_bytes * NSTG;
     static constexpr size_t o_xL = o_ring + (size_t)NS * 3 * NOUT * 8;
     static constexpr size_t o_q = o_xL + (size_t)3 * RY * FX * 8;
     static constexpr size_t o_bar = al128(o_q + (size_t)3 * NR * 8);
@@ -670,8 +675,8 @@ struct K2S {
 template <int R, int NW, int OPT, int NSTG, bool TMA>
 __global__ void __launch_bounds__(FX *NW) k_lncc_grad(const __grid_constant__ Maps maps,
                                                       const float *__restrict__ If,
-                                                      const float *__restrict__ Im,
-                                                      const float *__restrict__ u,
+                                                      const float *__restrict__ gJ,
+                                                      const float *__restrict__ J,
                                                       const float *__restrict__ coef,
                                                       WsHeader *__restrict__ h,
                                                       float *__restrict__ g, int D, int H, int W,
@@ -687,7 +692,6 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_grad(const __grid_constant__ Ma
     unsigned long long *bar = (unsigned long long *)(smem + S::o_bar);
     __shared__ int flag;
     auto stage = [&](int s) { return (float *)(smem + S::o_st + S::st_bytes * s); };
-    auto ostage = [&](int s) { return (float *)(smem + S::o_ost + S::ost_bytes * s); };
 
     const int tx = threadIdx.x, wy = threadIdx.y, tid = wy * FX + tx;
     const int x0 = blockIdx.x * FX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
@@ -719,29 +723,29 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_grad(const __grid_constant__ Ma
 
     const int zs = z0 - R, np = zend - z0 + 2 * R;
     auto issue = [&](int i) {
-        const int zp = zs + i, zo = zp - R, s = i % NSTG;
-        const bool out = zo >= z0 && zo < zend;
+        const int zp = zs + i, s = i % NSTG;
         if (TMA) {
             if (tid == 0 && i < np) {
-                mbar_expect(bar + s, S::tx_plane + (out ? S::tx_out : 0u));
+                mbar_expect(bar + s, S::tx_plane);
                 tma4(stage(s), &maps.a, x0 - XB, y0 - R, zp, 0, bar + s);
-                if (out) {
-                    tma4(ostage(s), &maps.b, x0, y0, zo, 0, bar + s);
-                    tma4(ostage(s) + 3 * NOUT, &maps.c, x0, y0, zo, 0, bar + s);
-                }
             }
         } else {
-            if (i < np) {
+            if (i < np)
                 rg.template load<4>(stage(s), coef, N, (long long)zp * HW, zp >= 0 && zp < D);
-                if (out) {
-                    ou.template load<3, float>(ostage(s), u, N, (long long)zo * HW, tid);
-                    ou.template load<1, float>(ostage(s) + 3 * NOUT, If, N, (long long)zo * HW,
-                                               tid);
-                }
-            }
             cp_commit();
         }
     };
+    // the outputs' operands grad I_m(phi), I_f, J, loaded one plane ahead
+    float gn[OPT][3], In[OPT][1], Jn[OPT][1];
+    auto fetch_ops = [&](int i) {
+        const int zo = zs + i - R;
+        if (i < np && zo >= z0 && zo < zend) {
+            ou.fetch(gn, gJ, N, (long long)zo * HW);
+            ou.fetch(In, If, N, (long long)zo * HW);
+            ou.fetch(Jn, J, N, (long long)zo * HW);
+        }
+    };
+    fetch_ops(0);
 #pragma unroll
     for (int k = 0; k < NSTG - 1; ++k) issue(k);
 
@@ -749,24 +753,22 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_grad(const __grid_constant__ Ma
     for (int i = 0; i < np; ++i) {
         const int zp = zs + i, zo = zp - R, s = i % NSTG;
         issue(i + NSTG - 1);
+        const bool out = zo >= z0 && zo < zend;
+        float Gz[OPT], Gy[OPT], Gx[OPT], Iv[OPT], Jv[OPT];
+#pragma unroll
+        for (int k = 0; k < OPT; ++k) {
+            Gz[k] = gn[k][0];
+            Gy[k] = gn[k][1];
+            Gx[k] = gn[k][2];
+            Iv[k] = In[k][0];
+            Jv[k] = Jn[k][0];
+        }
+        fetch_ops(i + 1);
         bool ok = true;
         if (TMA)
             ok = mbar_wait(bar + s, (unsigned)(i / NSTG) & 1u);
         else
             cp_wait<NSTG - 1>();
-        const bool out = zo >= z0 && zo < zend;
-        // gathers for this plane's outputs, consumed after the reductions
-        TriPending tp[OPT];
-        float Iv[OPT];
-        if (out && ok) {
-            const float *o = ostage(s) + tid;
-#pragma unroll
-            for (int k = 0; k < OPT; ++k) {
-                tri_issue(tp[k], Im, D, H, W, zo, y0 + wy + NW * k, x0 + tx, o[k * NT],
-                          o[NOUT + k * NT], o[2 * NOUT + k * NT]);
-                Iv[k] = o[3 * NOUT + k * NT];
-            }
-        }
         const bool zin = zp >= 0 && zp < D;
         if (zin) {
             const float *sp = stage(s);
@@ -809,21 +811,19 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_grad(const __grid_constant__ Ma
 #pragma unroll
             for (int o = 0; o < OPT; ++o) {
                 if (ou.off[o] < 0) continue;
-                float gz, gy, gx;
-                const float Jv = tri_finish<true>(tp[o], gz, gy, gx);
                 float ah, al, bh, bl, ch, cl, rh, rl, th, tl;
                 i64_to_ff(acc[o][0], ah, al);
                 i64_to_ff(acc[o][1], bh, bl);
                 i64_to_ff(acc[o][2], ch, cl);
                 ff_mul_f(Iv[o], ah * us[0], al * us[0], rh, rl);      // I SA
-                ff_mul_f(2.0f * Jv, bh * us[1], bl * us[1], th, tl);  // 2 J SB
+                ff_mul_f(2.0f * Jv[o], bh * us[1], bl * us[1], th, tl);  // 2 J SB
                 ff_add(rh, rl, th, tl);
                 ff_add(rh, rl, ch * us[2], cl * us[2]);               // + SC
                 const float dj = -(rh + rl) * inv_n;
                 float *gp = g + zoff + ou.off[o];
-                gp[0] = dj * gz;
-                gp[N] = dj * gy;
-                gp[2 * N] = dj * gx;
+                gp[0] = dj * Gz[o];
+                gp[N] = dj * Gy[o];
+                gp[2 * N] = dj * Gx[o];
             }
         }
     }
@@ -837,10 +837,11 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_grad(const __grid_constant__ Ma
     if (!TMA) cp_wait<0>();
 }
 
-// MSE: g = 2 (J - I) / N * grad I_m o phi (pointwise).
+// MSE: g = 2 (J - I) / N * grad I_m(phi) (pointwise, J and the gradient as
+// the compose kernel stored them).
 __global__ void __launch_bounds__(256) k_fused_mse_grad(const float *__restrict__ If,
-                                                        const float *__restrict__ Im,
-                                                        const float *__restrict__ u,
+                                                        const float *__restrict__ J,
+                                                        const float *__restrict__ gJ,
                                                         float *__restrict__ g, int D, int H,
                                                         int W) {
     int x = blockIdx.x * 32 + threadIdx.x;
@@ -849,13 +850,10 @@ __global__ void __launch_bounds__(256) k_fused_mse_grad(const float *__restrict_
     if (x >= W || y >= H) return;
     long long N = (long long)D * H * W;
     long long i = ((long long)z * H + y) * W + x;
-    float gz, gy, gx;
-    float Jv = tri_sample<true>(Im, D, H, W, z, y, x, __ldg(u + i), __ldg(u + N + i),
-                                __ldg(u + 2 * N + i), gz, gy, gx);
-    float dj = 2.0f * (Jv - __ldg(If + i)) / (float)N;
-    g[i] = dj * gz;
-    g[N + i] = dj * gy;
-    g[2 * N + i] = dj * gx;
+    float dj = 2.0f * (__ldg(J + i) - __ldg(If + i)) / (float)N;
+    g[i] = dj * __ldg(gJ + i);
+    g[N + i] = dj * __ldg(gJ + N + i);
+    g[2 * N + i] = dj * __ldg(gJ + 2 * N + i);
 }
 
 // ====================================================================== K3
@@ -1048,6 +1046,7 @@ __global__ void __launch_bounds__(FX *NW, NW >= 16 ? 2 : 1) k_compose(const __gr
                                                     float *__restrict__ uo,
                                                     const float *__restrict__ Im,
                                                     float *__restrict__ Jout,
+                                                    float *__restrict__ gJout,
                                                     WsHeader *__restrict__ h, int D, int H, int W,
                                                     int TZ, GaussTaps t, float lr, float c_lp,
                                                     int parity) {
@@ -1224,7 +1223,10 @@ __global__ void __launch_bounds__(FX *NW, NW >= 16 ? 2 : 1) k_compose(const __gr
                 // finish the previous plane's warped value first (its loads have landed)
                 if (jlive[o]) {
                     float gz, gy, gx;
-                    Jout[jidx[o]] = tri_finish<false>(jp[o], gz, gy, gx);
+                    Jout[jidx[o]] = tri_finish<true>(jp[o], gz, gy, gx);
+                    gJout[jidx[o]] = gz;
+                    gJout[N + jidx[o]] = gy;
+                    gJout[2 * N + jidx[o]] = gx;
                     jlive[o] = false;
                 }
                 if (ou.off[o] < 0) continue;
@@ -1253,7 +1255,10 @@ __global__ void __launch_bounds__(FX *NW, NW >= 16 ? 2 : 1) k_compose(const __gr
     for (int o = 0; o < OPT; ++o)
         if (jlive[o]) {
             float gz, gy, gx;
-            Jout[jidx[o]] = tri_finish<false>(jp[o], gz, gy, gx);
+            Jout[jidx[o]] = tri_finish<true>(jp[o], gz, gy, gx);
+            gJout[jidx[o]] = gz;
+            gJout[N + jidx[o]] = gy;
+            gJout[2 * N + jidx[o]] = gx;
         }
     if (!TMA) cp_wait<0>();
     // per-iteration header fields for the next iteration (nobody else reads them now)
@@ -1458,9 +1463,7 @@ cudaError_t launch_k1(const float *If, const float *J, const long long *sI, cons
     cudaError_t le;
     using ST = K1S<R, K1_NW, K1_OPT, K1_ST_TMA>;
     const bool tma = tmap(&mp.a, If, 4, d, 1, ST::BXW, ST::RY, 1) &&
-                     tmap(&mp.b, J, 4, d, 1, ST::BXW, ST::RY, 1) &&
-                     tmap(&mp.c, sI, 8, d, 1, FX, ST::TY, 1) &&
-                     tmap(&mp.d, varI, 4, d, 1, FX, ST::TY, 1);
+                     tmap(&mp.b, J, 4, d, 1, ST::BXW, ST::RY, 1);
     const TileChoice tc = tile_choice(0, R, 0, d);
     if (tma) {
         auto kern = k_lncc_fwd<R, K1_NW, K1_OPT, K1_ST_TMA, true>;
@@ -1481,28 +1484,26 @@ cudaError_t launch_k1(const float *If, const float *J, const long long *sI, cons
 }
 
 template <int R>
-cudaError_t launch_k2(const float *If, const float *Im, const float *u, const float *coef,
+cudaError_t launch_k2(const float *If, const float *gJ, const float *J, const float *coef,
                       WsHeader *h, float *g, Dims d, int window, cudaStream_t s) {
     const int cb = lncc_coef_bits(window);
     Maps mp{};
     cudaError_t le;
     using ST = K2S<R, K2_NW, K2_OPT, K2_ST_TMA>;
-    const bool tma = tmap(&mp.a, coef, 4, d, 4, ST::BXW, ST::RY, 4) &&
-                     tmap(&mp.b, u, 4, d, 3, FX, ST::TY, 3) &&
-                     tmap(&mp.c, If, 4, d, 1, FX, ST::TY, 1);
+    const bool tma = tmap(&mp.a, coef, 4, d, 4, ST::BXW, ST::RY, 4);
     const TileChoice tc = tile_choice(1, R, 0, d);
     if (tma) {
         auto kern = k_lncc_grad<R, K2_NW, K2_OPT, K2_ST_TMA, true>;
         static const int occ = prepare(kern, ST::bytes, ST::NT);
         LaunchGeom gg = geometry(occ, K2_NW, ST::TY, R, d, tc.tz);
-        le = launch_pdl(kern, gg, ST::bytes, s, mp, If, Im, u, coef, h, g, d.D, d.H, d.W, gg.tz,
+        le = launch_pdl(kern, gg, ST::bytes, s, mp, If, gJ, J, coef, h, g, d.D, d.H, d.W, gg.tz,
                                                   cb);
     } else {
         using SC = K2S<R, K2_NW, K2_OPT, K2_ST_CP>;
         auto kern = k_lncc_grad<R, K2_NW, K2_OPT, K2_ST_CP, false>;
         static const int occ = prepare(kern, SC::bytes, SC::NT);
         LaunchGeom gg = geometry(occ, K2_NW, SC::TY, R, d, tc.tz);
-        le = launch_pdl(kern, gg, SC::bytes, s, mp, If, Im, u, coef, h, g, d.D, d.H, d.W, gg.tz,
+        le = launch_pdl(kern, gg, SC::bytes, s, mp, If, gJ, J, coef, h, g, d.D, d.H, d.W, gg.tz,
                                                   cb);
     }
     note_launch();
@@ -1547,19 +1548,19 @@ cudaError_t launch_k3(const float *g, float *m, float *v, float *dir, WsHeader *
 
 template <int RG, bool SU, int NW>
 cudaError_t launch_k4_tma(const Maps &mp, const float *u, const float *dir, float *uo,
-                          const float *Im, float *J, WsHeader *h, Dims d, const GaussTaps &t,
+                          const float *Im, float *J, float *gJ, WsHeader *h, Dims d, const GaussTaps &t,
                           float lr, float c_lp, int parity, int tz, cudaStream_t s) {
     using ST = K4S<RG, NW, K4_OPT, SU, K4_ST_TMA>;
     auto kern = k_compose<RG, NW, K4_OPT, SU, K4_ST_TMA, true>;
     static const int occ = prepare(kern, ST::bytes, ST::NT);
     LaunchGeom gg = geometry(occ, NW, ST::TY, RG, d, tz);
-    return launch_pdl(kern, gg, ST::bytes, s, mp, u, dir, uo, Im, J, h, d.D, d.H, d.W, gg.tz, t,
+    return launch_pdl(kern, gg, ST::bytes, s, mp, u, dir, uo, Im, J, gJ, h, d.D, d.H, d.W, gg.tz, t,
                       lr, c_lp, parity);
 }
 
 template <int RG, bool SU>
 cudaError_t launch_k4(const float *u, const float *dir, float *uo, const float *Im, float *J,
-                      WsHeader *h, Dims d, const GaussTaps &t, float lr, float c_lp, int parity,
+                      float *gJ, WsHeader *h, Dims d, const GaussTaps &t, float lr, float c_lp, int parity,
                       cudaStream_t s) {
     Maps mp{};
     cudaError_t le;
@@ -1568,16 +1569,16 @@ cudaError_t launch_k4(const float *u, const float *dir, float *uo, const float *
     const bool tma = tmap(&mp.a, dir, 4, d, 3, FX + 2 * halo4(RG), nw + 2 * RG, 3) &&
                      (!SU || tmap(&mp.b, u, 4, d, 3, FX + 2 * halo4(RG + 1), nw + 2 * RG + 2, 3));
     if (tma) {
-        le = tc.wide ? launch_k4_tma<RG, SU, 16>(mp, u, dir, uo, Im, J, h, d, t, lr, c_lp, parity,
+        le = tc.wide ? launch_k4_tma<RG, SU, 16>(mp, u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity,
                                                  tc.tz, s)
-                     : launch_k4_tma<RG, SU, 8>(mp, u, dir, uo, Im, J, h, d, t, lr, c_lp, parity,
+                     : launch_k4_tma<RG, SU, 8>(mp, u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity,
                                                 tc.tz, s);
     } else {
         using SC = K4S<RG, K4_NW, K4_OPT, SU, K4_ST_CP>;
         auto kern = k_compose<RG, K4_NW, K4_OPT, SU, K4_ST_CP, false>;
         static const int occ = prepare(kern, SC::bytes, SC::NT);
         LaunchGeom gg = geometry(occ, K4_NW, SC::TY, RG, d, tc.tz);
-        le = launch_pdl(kern, gg, SC::bytes, s, mp, u, dir, uo, Im, J, h, d.D, d.H, d.W, gg.tz, t,
+        le = launch_pdl(kern, gg, SC::bytes, s, mp, u, dir, uo, Im, J, gJ, h, d.D, d.H, d.W, gg.tz, t,
                         lr, c_lp, parity);
     }
     note_launch();
@@ -1606,17 +1607,17 @@ cudaError_t dispatch_k1(const float *If, const float *J, const long long *sI, co
     return cudaErrorInvalidValue;
 }
 
-cudaError_t dispatch_k2(const float *If, const float *Im, const float *u, const float *coef,
+cudaError_t dispatch_k2(const float *If, const float *gJ, const float *J, const float *coef,
                         WsHeader *h, float *g, Dims d, int window, cudaStream_t s) {
     switch (window / 2) {
-        FA_CASE(0, (launch_k2<RR>(If, Im, u, coef, h, g, d, window, s)))
-        FA_CASE(1, (launch_k2<RR>(If, Im, u, coef, h, g, d, window, s)))
-        FA_CASE(2, (launch_k2<RR>(If, Im, u, coef, h, g, d, window, s)))
-        FA_CASE(3, (launch_k2<RR>(If, Im, u, coef, h, g, d, window, s)))
-        FA_CASE(4, (launch_k2<RR>(If, Im, u, coef, h, g, d, window, s)))
-        FA_CASE(5, (launch_k2<RR>(If, Im, u, coef, h, g, d, window, s)))
-        FA_CASE(6, (launch_k2<RR>(If, Im, u, coef, h, g, d, window, s)))
-        FA_CASE(7, (launch_k2<RR>(If, Im, u, coef, h, g, d, window, s)))
+        FA_CASE(0, (launch_k2<RR>(If, gJ, J, coef, h, g, d, window, s)))
+        FA_CASE(1, (launch_k2<RR>(If, gJ, J, coef, h, g, d, window, s)))
+        FA_CASE(2, (launch_k2<RR>(If, gJ, J, coef, h, g, d, window, s)))
+        FA_CASE(3, (launch_k2<RR>(If, gJ, J, coef, h, g, d, window, s)))
+        FA_CASE(4, (launch_k2<RR>(If, gJ, J, coef, h, g, d, window, s)))
+        FA_CASE(5, (launch_k2<RR>(If, gJ, J, coef, h, g, d, window, s)))
+        FA_CASE(6, (launch_k2<RR>(If, gJ, J, coef, h, g, d, window, s)))
+        FA_CASE(7, (launch_k2<RR>(If, gJ, J, coef, h, g, d, window, s)))
     }
     return cudaErrorInvalidValue;
 }
@@ -1638,27 +1639,28 @@ cudaError_t dispatch_k3(const float *g, float *m, float *v, float *dir, WsHeader
 }
 
 cudaError_t dispatch_k4(const float *u, const float *dir, float *uo, const float *Im, float *J,
+                        float *gJ,
                         WsHeader *h, Dims d, const GaussTaps &t, float lr, float c_lp, int parity,
                         bool su, cudaStream_t s) {
     if (su) {
         switch (t.R) {
-            FA_CASE(0, (launch_k4<RR, true>(u, dir, uo, Im, J, h, d, t, lr, c_lp, parity, s)))
-            FA_CASE(1, (launch_k4<RR, true>(u, dir, uo, Im, J, h, d, t, lr, c_lp, parity, s)))
-            FA_CASE(2, (launch_k4<RR, true>(u, dir, uo, Im, J, h, d, t, lr, c_lp, parity, s)))
-            FA_CASE(3, (launch_k4<RR, true>(u, dir, uo, Im, J, h, d, t, lr, c_lp, parity, s)))
-            FA_CASE(4, (launch_k4<RR, true>(u, dir, uo, Im, J, h, d, t, lr, c_lp, parity, s)))
-            FA_CASE(5, (launch_k4<RR, true>(u, dir, uo, Im, J, h, d, t, lr, c_lp, parity, s)))
-            FA_CASE(6, (launch_k4<RR, true>(u, dir, uo, Im, J, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(0, (launch_k4<RR, true>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(1, (launch_k4<RR, true>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(2, (launch_k4<RR, true>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(3, (launch_k4<RR, true>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(4, (launch_k4<RR, true>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(5, (launch_k4<RR, true>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(6, (launch_k4<RR, true>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
         }
     } else {
         switch (t.R) {
-            FA_CASE(0, (launch_k4<RR, false>(u, dir, uo, Im, J, h, d, t, lr, c_lp, parity, s)))
-            FA_CASE(1, (launch_k4<RR, false>(u, dir, uo, Im, J, h, d, t, lr, c_lp, parity, s)))
-            FA_CASE(2, (launch_k4<RR, false>(u, dir, uo, Im, J, h, d, t, lr, c_lp, parity, s)))
-            FA_CASE(3, (launch_k4<RR, false>(u, dir, uo, Im, J, h, d, t, lr, c_lp, parity, s)))
-            FA_CASE(4, (launch_k4<RR, false>(u, dir, uo, Im, J, h, d, t, lr, c_lp, parity, s)))
-            FA_CASE(5, (launch_k4<RR, false>(u, dir, uo, Im, J, h, d, t, lr, c_lp, parity, s)))
-            FA_CASE(6, (launch_k4<RR, false>(u, dir, uo, Im, J, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(0, (launch_k4<RR, false>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(1, (launch_k4<RR, false>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(2, (launch_k4<RR, false>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(3, (launch_k4<RR, false>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(4, (launch_k4<RR, false>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(5, (launch_k4<RR, false>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(6, (launch_k4<RR, false>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
         }
     }
     return cudaErrorInvalidValue;
@@ -1681,6 +1683,7 @@ void fused_carve(WsCarver &c, long long n, FusedBuffers *fb) {
     fb->g = c.take<float>(4 * n);     // also the second one
     fb->dir = c.take<float>(3 * n);
     fb->J = c.take<float>(n);
+    fb->gJ = c.take<float>(3 * n);
     fb->t1 = c.take<float>(3 * n);
     fb->t2 = c.take<float>(3 * n);
     fb->sI = c.take<long long>(n);
@@ -1695,7 +1698,7 @@ cudaError_t fused_level_start(const float *If, const float *Im, const float *u, 
                                            (long long *)fb.g, fb.sI, fb.varI, s);
         if (e != cudaSuccess) return e;
     }
-    return launch_warp(Im, u, fb.J, nullptr, d, s);
+    return launch_warp(Im, u, fb.J, fb.gJ, d, s);
 }
 
 fa_status fused_iteration(FusedBuffers &fb, WsHeader *h, const fa_params *p, Dims d,
@@ -1721,12 +1724,12 @@ fa_status fused_iteration(FusedBuffers &fb, WsHeader *h, const fa_params *p, Dim
                                 true, s));
         FA_CUDA_TRY(stop(FA_K_FUSED_WARP_LNCC));
         FA_CUDA_TRY(start(FA_K_FUSED_LNCC_GRAD));
-        FA_CUDA_TRY(dispatch_k2(it.If, it.Im, it.u, fb.coef, h, fb.g, d, p->window, s));
+        FA_CUDA_TRY(dispatch_k2(it.If, fb.gJ, fb.J, fb.coef, h, fb.g, d, p->window, s));
         FA_CUDA_TRY(stop(FA_K_FUSED_LNCC_GRAD));
     } else {
         VoxGrid gg(d.D, d.H, d.W);
         FA_CUDA_TRY(start(FA_K_FUSED_LNCC_GRAD));
-        k_fused_mse_grad<<<gg.grid, gg.block, 0, s>>>(it.If, it.Im, it.u, fb.g, d.D, d.H, d.W);
+        k_fused_mse_grad<<<gg.grid, gg.block, 0, s>>>(it.If, fb.J, fb.gJ, fb.g, d.D, d.H, d.W);
         note_launch();
         FA_CUDA_TRY(cudaGetLastError());
         FA_CUDA_TRY(stop(FA_K_FUSED_LNCC_GRAD));
@@ -1747,12 +1750,12 @@ fa_status fused_iteration(FusedBuffers &fb, WsHeader *h, const fa_params *p, Dim
                             adam_consts(p, it.t), parity, s));
     FA_CUDA_TRY(stop(FA_K_FUSED_SMOOTH_ADAM));
     FA_CUDA_TRY(start(FA_K_FUSED_COMPOSE));
-    FA_CUDA_TRY(dispatch_k4(it.u, fb.dir, it.u_alt, it.Im, fb.J, h, d, wide_w ? ident : tw, p->lr,
+    FA_CUDA_TRY(dispatch_k4(it.u, fb.dir, it.u_alt, it.Im, fb.J, fb.gJ, h, d, wide_w ? ident : tw, p->lr,
                             p->c_lp, parity, su, s));
     FA_CUDA_TRY(stop(FA_K_FUSED_COMPOSE));
     if (wide_w) {
         FA_CUDA_TRY(launch_gauss3(it.u_alt, it.u_alt, fb.t1, fb.t2, 3, d, tw, s));
-        FA_CUDA_TRY(launch_warp(it.Im, it.u_alt, fb.J, nullptr, d, s));  // J of the smoothed map
+        FA_CUDA_TRY(launch_warp(it.Im, it.u_alt, fb.J, fb.gJ, d, s));  // J, grad of the smoothed map
     }
     return FA_OK;
 }
@@ -1775,10 +1778,11 @@ fa_status fused_autotune_level(FusedBuffers &fb, WsHeader *h, const fa_params *p
             case 0:
                 return dispatch_k1(If, fb.J, fb.sI, fb.varI, fb.coef, h, d, p->window, p->cc_eps,
                                    true, s);
-            case 1: return dispatch_k2(If, Im, u, fb.coef, h, fb.g, d, p->window, s);
+            case 1: return dispatch_k2(If, fb.gJ, fb.J, fb.coef, h, fb.g, d, p->window, s);
             case 2: return dispatch_k3(fb.g, m, v, fb.dir, h, d, g3, ac, 0, s);
             default:
-                return dispatch_k4(u, fb.dir, u_alt, Im, fb.J, h, d, g4, p->lr, p->c_lp, 0, su, s);
+                return dispatch_k4(u, fb.dir, u_alt, Im, fb.J, fb.gJ, h, d, g4, p->lr, p->c_lp, 0,
+                                   su, s);
         }
     };
     cudaEvent_t e0, e1;

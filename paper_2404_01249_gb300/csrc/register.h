@@ -10,6 +10,7 @@ struct FusedBuffers {
     float *g;      // [3][N]: dL/dphi before smoothing
     float *dir;    // [3][N]: Adam direction d
     float *J;      // [N]    : warped image I_m o phi of the current map
+    float *gJ;     // [3][N]: grad I_m at phi (the interpolant's derivative)
     float *t1, *t2;  // [3][N]: separable passes when a Gaussian is wider than the fused kernels take
     long long *sI; // [N]    : exact window sum of the level's fixed image
     float *varI;   // [N]    : its window variance
@@ -26,8 +27,8 @@ fa_status fused_iteration(FusedBuffers &fb, WsHeader *h, const fa_params *p, Dim
                           const FusedIter &it, const GaussTaps &tg, const GaussTaps &tw,
                           fa_kernel_timer *timer, int level, cudaStream_t s);
 // Per-level set-up of the fused path: the fixed image's window statistics
-// (LNCC) and J = I_m o (id + u) for the first iteration (later iterations
-// get J from the compose kernel).  Needs the level's image maxima in h.
+// (LNCC) and J = I_m o (id + u) with its gradient for the first iteration
+// (later iterations get both from the compose kernel).  Needs the level's image maxima in h.
 cudaError_t fused_level_start(const float *If, const float *Im, const float *u, Dims d,
                               const fa_params *p, const WsHeader *h, FusedBuffers &fb,
                               cudaStream_t s);
