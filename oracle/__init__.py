@@ -50,6 +50,7 @@ class _Params(ctypes.Structure):
         ("adam_eps", ctypes.c_double),
         ("cc_eps", ctypes.c_double),
         ("c_lp", ctypes.c_double),
+        ("use_jac", ctypes.c_int),
     ]
 
 
@@ -79,6 +80,7 @@ def _L():
         lib.or_sample.argtypes = [_dp, i, i, i, d, d, d, _dp]
         lib.or_warp.argtypes = [_dp, i, i, i, _dp, _dp, _dp]
         lib.or_warp_adjoint.argtypes = [_dp, _dp, i, i, i, i, i, i, _dp]
+        lib.or_jac_direction.argtypes = [_dp, _dp, i, i, i, _dp]
         lib.or_box_sum.argtypes = [_dp, i, i, i, i, _dp]
         lib.or_lncc.argtypes = [_dp, _dp, i, i, i, i, d, _dp, _dp, _dp, _dp]
         lib.or_mse.argtypes = [_dp, _dp, i, i, i, _dp, _dp, _dp]
@@ -147,6 +149,15 @@ def warp_adjoint(dJ, u, moving_shape):
     Dm, Hm, Wm = (int(s) for s in moving_shape)
     out = np.empty((Dm, Hm, Wm))
     _check(_L().or_warp_adjoint(_p(dJ), _p(u), D, H, W, Dm, Hm, Wm, _p(out)), "warp_adjoint")
+    return out
+
+
+def jac_direction(g, u):
+    """J(phi)^T g with J(phi) = I + grad u (reading R-jac)."""
+    g, u = _f64(g), _f64(u)
+    D, H, W = g.shape[1:]
+    out = np.empty_like(g)
+    _check(_L().or_jac_direction(_p(g), _p(u), D, H, W, _p(out)), "jac_direction")
     return out
 
 
@@ -266,7 +277,7 @@ def upsample_field(src, shape, power: int):
 
 def register(If, Im, scales, iters, lr=0.5, sigma_grad=1.0, sigma_warp=0.5, window=5,
              loss="lncc", beta1=0.9, beta2=0.999, adam_eps=1e-8, cc_eps=1e-5, c_lp=2.0,
-             want_trace=False):
+             want_trace=False, use_jac=False):
     """Algorithm 1 end to end.  Returns dict(u, final_loss, trace)."""
     If, Im = _f64(If), _f64(Im)
     D, H, W = _dims(If)
@@ -284,6 +295,7 @@ def register(If, Im, scales, iters, lr=0.5, sigma_grad=1.0, sigma_warp=0.5, wind
     p.loss = {"lncc": 0, "mse": 1}[loss]
     p.beta1, p.beta2, p.adam_eps = float(beta1), float(beta2), float(adam_eps)
     p.cc_eps, p.c_lp = float(cc_eps), float(c_lp)
+    p.use_jac = 1 if use_jac else 0
     fs = level_shape((D, H, W), scales[-1])
     u = np.empty((3,) + fs)
     fl = ctypes.c_double()

@@ -21,6 +21,8 @@
  *   coordinates are voxel units of the current level; phi(x) = x + u(x).
  *
  * Readings of points the paper leaves open (each marked "reading" below):
+ *   R-jac     with use_jac, grad u by central differences inside the grid and
+ *             one-sided first differences at its ends (zero on an axis of 1).
  *   R-interp  trilinear interpolation, samples outside the grid are zero
  *             (u is extended by zero outside Omega, section Preliminaries).
  *   R-kink    at integer coordinates the interpolant's derivative is taken in
@@ -503,6 +505,41 @@ int or_upsample_field(const double *src, int Dc, int Hc, int Wc,
 
 /* Hyper-parameters of Algorithm 1 plus the smoothing widths of the grid
  * study and the Adam constants.  Plain struct, mirrored in oracle/__init__.py. */
+/* Steepest Eulerian descent direction of section "Exploiting the group
+ * structure of diffeomorphisms" (the use_jac option of Algorithm 1):
+ * out = J(phi)^T g with J(phi) = I + grad u, i.e.
+ *   out_i(x) = g_i(x) + sum_j (d u_j / d x_i)(x) g_j(x),
+ * reading R-jac: the derivatives are central differences (u[k+1] - u[k-1]) / 2
+ * inside the grid and one-sided first differences at its first and last
+ * index (zero on an axis of length 1).  out must not alias g. */
+static double dfd(const double *f, int D, int H, int W, int axis, int z, int y, int x) {
+    int n = axis == 0 ? D : (axis == 1 ? H : W);
+    int k = axis == 0 ? z : (axis == 1 ? y : x);
+    if (n < 2) return 0.0;
+    int dz = axis == 0, dy = axis == 1, dx = axis == 2;
+    if (k == 0) return f[IDX(z + dz, y + dy, x + dx)] - f[IDX(z, y, x)];
+    if (k == n - 1) return f[IDX(z, y, x)] - f[IDX(z - dz, y - dy, x - dx)];
+    return 0.5 * (f[IDX(z + dz, y + dy, x + dx)] - f[IDX(z - dz, y - dy, x - dx)]);
+}
+
+int or_jac_direction(const double *g, const double *u, int D, int H, int W, double *out) {
+    if (D <= 0 || H <= 0 || W <= 0 || out == g) return OR_EINVAL;
+    size_t N = (size_t)D * H * W;
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < D; ++z)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                size_t i = IDX(z, y, x);
+                for (int a = 0; a < 3; ++a) {          /* component of the output */
+                    double s = g[(size_t)a * N + i];
+                    for (int j = 0; j < 3; ++j)        /* J_ja = delta_ja + d u_j / d x_a */
+                        s += dfd(u + (size_t)j * N, D, H, W, a, z, y, x) * g[(size_t)j * N + i];
+                    out[(size_t)a * N + i] = s;
+                }
+            }
+    return OR_OK;
+}
+
 typedef struct {
     int n_levels;
     int scales[8];
@@ -515,6 +552,7 @@ typedef struct {
     double beta1, beta2, adam_eps;
     double cc_eps;
     double c_lp;        /* Lipschitz-bound factor of reading R-step (2) */
+    int use_jac;        /* 1: steepest Eulerian direction J(phi)^T dL/dphi (or_jac_direction) */
 } or_params;
 
 static int loss_and_grad(const or_params *p, const double *If, const double *J,
@@ -524,7 +562,8 @@ static int loss_and_grad(const or_params *p, const double *If, const double *J,
 }
 
 /* Algorithm 1 (FireANTs), Jacobian-free descent direction (section
- * "Jacobian-Free Eulerian Descent"), with the per-iteration order
+ * "Jacobian-Free Eulerian Descent"; with use_jac the steepest direction
+ * J(phi)^T dL/dphi instead), with the per-iteration order
  *   warp -> loss and dL/dphi -> Gaussian(sigma_grad) -> Adam -> step scale
  *   -> compose -> Gaussian(sigma_warp).
  * u_out receives the finest-level displacement (level size of the last
@@ -566,6 +605,10 @@ int or_register(const double *If, const double *Im, int D, int H, int W, const o
             if (loss_trace) loss_trace[trace_i++] = L;
             for (int c = 0; c < 3; ++c)          /* dL/dphi(x) = dL/dJ(x) grad I_m(phi(x)) */
                 for (size_t i = 0; i < N; ++i) g[(size_t)c * N + i] = dJ[i] * gJ[(size_t)c * N + i];
+            if (p->use_jac) {                      /* J(phi)^T dL/dphi instead */
+                or_jac_direction(g, u, d, h, w, tmp);
+                memcpy(g, tmp, 3 * N * sizeof(double));
+            }
             or_gauss_smooth(g, g, 3, d, h, w, p->sigma_grad);
             ++t;
             or_adam(g, m, v, dir, 3 * N, t, p->beta1, p->beta2, p->adam_eps);
