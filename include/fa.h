@@ -91,11 +91,15 @@ typedef struct {
                              replays it when called again with identical arguments
                              (pointers, shapes, parameters, workspace, timer); up to 64
                              graphs are kept per process.  0: launch kernel by kernel. */
+    int32_t use_jac;      /* 1: steepest Eulerian direction J(phi)^T dL/dphi (section
+                             "Exploiting the group structure of diffeomorphisms", Algorithm 1
+                             use_jac) instead of the Jacobian-free dL/dphi; see
+                             fa_jac_direction.  0 (default): Jacobian-free. */
 } fa_params;
 
 /* Fills p with: 3 levels {4,2,1} x {200,100,50}, lr 0.5, sigma_grad 1,
  * sigma_warp 0.5, window 5, LNCC, Adam (0.9, 0.999, 1e-8), cc_eps 1e-5,
- * c_lp 2, fused mode, FP32 storage, graph replay on. */
+ * c_lp 2, fused mode, FP32 storage, graph replay on, Jacobian-free direction. */
 fa_status fa_params_default(fa_params *p);
 
 const char *fa_status_str(fa_status s);
@@ -231,6 +235,15 @@ size_t fa_register_workspace_size(int32_t D, int32_t H, int32_t W, const fa_para
 fa_status fa_register(const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
                       fa_vol *u_out, float *final_loss_dev, float *final_loss_host, void *ws,
                       size_t ws_bytes, void *stream);
+
+/* Steepest Eulerian descent direction (section "Exploiting the group
+ * structure of diffeomorphisms"; Algorithm 1 with use_jac):
+ * g_out = J(phi)^T g_in with J(phi) = I + grad u, i.e.
+ * g_out_a = g_in_a + sum_j (d u_j / d x_a) g_in_j, the derivatives by central
+ * differences inside the grid and one-sided first differences at its ends
+ * (zero on an axis of length 1).  All C=3 FA_F32 on one grid; g_out may be
+ * g_in (in place) but must not otherwise overlap it.  No workspace. */
+fa_status fa_jac_direction(const fa_vol *g_in, const fa_vol *u, fa_vol *g_out, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Differentiation of the warp + LNCC loss (the Gateaux derivative of section

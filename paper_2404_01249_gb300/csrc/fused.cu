@@ -1734,6 +1734,7 @@ fa_status fused_iteration(FusedBuffers &fb, WsHeader *h, const fa_params *p, Dim
         FA_CUDA_TRY(cudaGetLastError());
         FA_CUDA_TRY(stop(FA_K_FUSED_LNCC_GRAD));
     }
+    if (p->use_jac) FA_CUDA_TRY(launch_jac_direction(fb.g, it.u, fb.g, d, s));
     // Gaussians wider than the fused kernels' rings run as separable passes
     // around the identity-width fused kernel.
     static const GaussTaps ident = [] {

@@ -48,6 +48,10 @@ static fa_status check_params(const fa_params *p) {
         set_error("sigma_grad and sigma_warp must be in [0, %g]", (double)kMaxSigma);
         return FA_ERR_INVALID;
     }
+    if (p->use_jac != 0 && p->use_jac != 1) {
+        set_error("use_jac must be 0 or 1");
+        return FA_ERR_INVALID;
+    }
     if (p->mode != FA_MODE_FUSED && p->mode != FA_MODE_PLAIN) {
         set_error("mode must be FA_MODE_FUSED or FA_MODE_PLAIN");
         return FA_ERR_INVALID;
@@ -175,6 +179,7 @@ static fa_status plain_iteration(Plan &P, const fa_params *p, int l, const float
     } else {
         FA_CUDA_TRY(launch_mse(If, P.J, P.grad, d, P.h, P.partials, nullptr, nullptr, P.g, s));
     }
+    if (p->use_jac) FA_CUDA_TRY(launch_jac_direction(P.g, u, P.g, d, s));
     FA_CUDA_TRY(launch_gauss3(P.g, P.g, P.t1, P.t2, 3, d, tg, s));
     int parity = t & 1;
     FA_CUDA_TRY(launch_adam(P.g, m, v, P.dir, N, adam_consts(p, t), P.h, parity, s));
@@ -344,7 +349,7 @@ std::string graph_key(int dev, const fa_vol *fixed, const fa_vol *moving, const 
     vol(fixed);
     vol(moving);
     vol(u_out);
-    static_assert(sizeof(fa_params) == 30 * 4, "fa_params holds 30 four-byte fields, no padding");
+    static_assert(sizeof(fa_params) == 31 * 4, "fa_params holds 31 four-byte fields, no padding");
     add(p, sizeof(*p));
     add(&final_loss_dev, sizeof(final_loss_dev));
     add(&ws, sizeof(ws));

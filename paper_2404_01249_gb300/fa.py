@@ -39,7 +39,7 @@ EXPORTED = ["fa_params_default", "fa_status_str", "fa_last_error", "fa_warp",
             "fa_launch_count", "fa_lncc_fwd_bwd_noalloc", "fa_register_batched_workspace_size",
             "fa_register_batched", "fa_warp_lncc_adjoint_workspace_size",
             "fa_warp_lncc_adjoint", "fa_autotune", "fa_autotune_reset", "fa_autotune_choices",
-            "fa_autotune_set"]
+            "fa_autotune_set", "fa_jac_direction"]
 
 
 class FAError(RuntimeError):
@@ -60,7 +60,8 @@ class Params(ctypes.Structure):
                 ("window", ctypes.c_int32), ("loss", ctypes.c_int32), ("beta1", ctypes.c_float),
                 ("beta2", ctypes.c_float), ("adam_eps", ctypes.c_float),
                 ("cc_eps", ctypes.c_float), ("c_lp", ctypes.c_float), ("mode", ctypes.c_int32),
-                ("storage", ctypes.c_int32), ("graph", ctypes.c_int32)]
+                ("storage", ctypes.c_int32), ("graph", ctypes.c_int32),
+                ("use_jac", ctypes.c_int32)]
 
 
 class KernelTimer(ctypes.Structure):
@@ -114,6 +115,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "fa_autotune_reset": (i32, []),
         "fa_autotune_choices": (i32, [ctypes.POINTER(ctypes.c_int32), i32]),
         "fa_autotune_set": (i32, [ctypes.POINTER(ctypes.c_int32)]),
+        "fa_jac_direction": (i32, [V, V, V, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -176,6 +178,7 @@ class RegParams:
     c_lp: float = 2.0
     mode: str = "fused"
     graph: bool = True   # record the launch sequence once, replay it on identical calls
+    use_jac: bool = False  # steepest Eulerian direction J(phi)^T dL/dphi
 
     def to_c(self) -> Params:
         p = Params()
@@ -194,6 +197,7 @@ class RegParams:
         p.mode = {"fused": FA_MODE_FUSED, "plain": FA_MODE_PLAIN}[self.mode]
         p.storage = FA_F32
         p.graph = 1 if self.graph else 0
+        p.use_jac = 1 if self.use_jac else 0
         return p
 
 
@@ -413,6 +417,13 @@ def fa_autotune_set(kernel: int, radius: int, compose_variant: int, D: int, H: i
 
 def fa_autotune_reset():
     _check(load().fa_autotune_reset())
+
+
+def fa_jac_direction(g: torch.Tensor, u: torch.Tensor, out: Optional[torch.Tensor] = None):
+    """J(phi)^T g with J(phi) = I + grad u (out may be g: in place)."""
+    out = out if out is not None else torch.empty_like(g)
+    _check(load().fa_jac_direction(_vol(g, 3), _vol(u, 3), _vol(out, 3), _stream()))
+    return out
 
 
 def fa_launch_count() -> int:

@@ -176,3 +176,14 @@ def test_full_size_warp_and_lncc(fa, orc):
     ref = orc.lncc(f, Jn, 5, np.float32(1e-5))
     assert abs(float(out["loss"]) - ref["loss"]) <= TOL * abs(ref["loss"])
     assert rel(out["dJ"], ref["dJ"]) < TOL
+
+
+@pytest.mark.parametrize("shape", [(19, 37, 45), (1, 9, 70), (5, 3, 2)])
+def test_jac_direction(fa, orc, shape):
+    g = np.random.default_rng(31).standard_normal((3,) + shape).astype(np.float32)
+    u = smooth_field(shape, 2.0, 32).astype(np.float32)
+    out = fa.fa_jac_direction(cuda(g), cuda(u))
+    assert rel(out, orc.jac_direction(g, u)) < TOL
+    gi = cuda(g)
+    fa.fa_jac_direction(gi, cuda(u), out=gi)          # in place
+    assert torch.equal(gi, out)

@@ -202,3 +202,25 @@ def test_tile_choices_change_speed_not_bits(fa):
         assert torch.equal(r["u"], base["u"]) and r["final_loss"] == base["final_loss"]
     finally:
         fa.fa_autotune_reset()
+
+
+@pytest.mark.parametrize("mode", ["plain", "fused"])
+def test_jacobian_direction_against_oracle(fa, orc, mode):
+    """use_jac (steepest Eulerian direction) end to end against the oracle."""
+    f, m, _ = synth.blobs_pair()
+    p = fa.RegParams(scales=(2, 1), iters=(20, 10), mode=mode, use_jac=True)
+    out = fa.fa_register(cuda(f), cuda(m), p)
+    f32 = lambda x: float(np.float32(x))  # noqa: E731
+    ref = orc.register(f, m, [2, 1], [20, 10], cc_eps=f32(1e-5), beta1=f32(0.9),
+                       beta2=f32(0.999), adam_eps=f32(1e-8), use_jac=True)
+    assert abs(out["final_loss"] - ref["final_loss"]) < 1e-3
+    assert mean_disp_diff(out["u"], ref["u"]) < 0.05
+
+
+def test_jacobian_direction_fused_equals_plain(fa):
+    f, m, _ = synth.voronoi_pair(shape=(40, 48, 56), seed=33)
+    base = dict(scales=(2, 1), iters=(10, 6), use_jac=True)
+    a = fa.fa_register(cuda(f), cuda(m), fa.RegParams(mode="plain", **base))
+    b = fa.fa_register(cuda(f), cuda(m), fa.RegParams(mode="fused", **base))
+    assert abs(a["final_loss"] - b["final_loss"]) < 1e-5
+    assert float((a["u"] - b["u"]).abs().max()) < 1e-4
