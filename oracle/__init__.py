@@ -81,6 +81,7 @@ def _L():
         lib.or_warp.argtypes = [_dp, i, i, i, _dp, _dp, _dp]
         lib.or_warp_adjoint.argtypes = [_dp, _dp, i, i, i, i, i, i, _dp]
         lib.or_jac_direction.argtypes = [_dp, _dp, i, i, i, _dp]
+        lib.or_svf_exp.argtypes = [_dp, i, i, i, i, _dp]
         lib.or_box_sum.argtypes = [_dp, i, i, i, i, _dp]
         lib.or_lncc.argtypes = [_dp, _dp, i, i, i, i, d, _dp, _dp, _dp, _dp]
         lib.or_mse.argtypes = [_dp, _dp, i, i, i, _dp, _dp, _dp]
@@ -245,6 +246,15 @@ def compose(u, delta):
     _, D, H, W = u.shape
     out = np.empty_like(u)
     _check(_L().or_compose(_p(u), _p(delta), _p(out), D, H, W), "compose")
+    return out
+
+
+def svf_exp(v, steps: int):
+    """exp(v) - id by scaling and squaring with `steps` squarings."""
+    v = _f64(v)
+    _, D, H, W = v.shape
+    out = np.empty_like(v)
+    _check(_L().or_svf_exp(_p(v), D, H, W, int(steps), _p(out)), "svf_exp")
     return out
 
 

@@ -429,6 +429,26 @@ int or_compose(const double *u, const double *delta, double *out, int D, int H, 
     return OR_OK;
 }
 
+/* Exponential of a stationary velocity field by scaling and squaring
+ * (section "Adaptive Optimization for Diffeomorphisms", Eqs. ssbasecase and
+ * scalingandsquaring): phi^(1/2^M) = id + v / 2^M, then M squarings
+ * phi <- phi o phi, i.e. u <- u + u(x + u(x)) with the zero-outside
+ * trilinear interpolation of or_compose.  out receives exp(v) - id. */
+int or_svf_exp(const double *v, int D, int H, int W, int steps, double *out) {
+    if (D <= 0 || H <= 0 || W <= 0 || steps < 0 || out == v) return OR_EINVAL;
+    size_t N = (size_t)D * H * W;
+    double *tmp = malloc(3 * N * sizeof(double));
+    if (!tmp) return OR_EINVAL;
+    double scale = ldexp(1.0, -steps);
+    for (size_t i = 0; i < 3 * N; ++i) out[i] = v[i] * scale;
+    for (int k = 0; k < steps; ++k) {
+        or_compose(out, out, tmp, D, H, W);
+        memcpy(out, tmp, 3 * N * sizeof(double));
+    }
+    free(tmp);
+    return OR_OK;
+}
+
 /* Size of a pyramid level (reading R-pyr). */
 int or_level_size(int n, int s) {
     int m = (s > 0) ? n / s : 0;

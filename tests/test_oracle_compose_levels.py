@@ -148,3 +148,33 @@ def test_upsample_preserves_positive_jacobian(orc):
     assert jac_det(u)[1:-1, 1:-1, 1:-1].min() > 0
     up = orc.upsample_field(u, (24, 24, 24), 1)
     assert jac_det(up)[1:-1, 1:-1, 1:-1].min() > 0
+
+
+def test_svf_exp_zero_and_affine_power(orc):
+    """Scaling and squaring: exp(0) = id; for an affine velocity A x the M
+    squarings give (I + A / 2^M)^(2^M) exactly wherever every intermediate
+    point stays inside the grid (trilinear is exact on affine fields)."""
+    shape = (16, 17, 18)
+    assert np.array_equal(orc.svf_exp(np.zeros((3,) + shape), 5), np.zeros((3,) + shape))
+    X = grid(shape)
+    c = np.array([(n - 1) / 2 for n in shape])[:, None, None, None]
+    A = 0.02 * rng(60).standard_normal((3, 3))
+    v = np.einsum("ab,b...->a...", A, X - c)               # zero at the centre
+    M = 4
+    out = orc.svf_exp(v, M)
+    P = np.linalg.matrix_power(np.eye(3) + A / 2 ** M, 2 ** M)
+    exact = np.einsum("ab,b...->a...", P - np.eye(3), X - c)
+    inner = (slice(4, -4),) * 3
+    assert np.allclose(out[(slice(None),) + inner], exact[(slice(None),) + inner], atol=1e-12)
+
+
+def test_svf_exp_constant_velocity_is_a_translation(orc):
+    shape = (12, 12, 12)
+    v = np.zeros((3,) + shape)
+    v[0], v[1], v[2] = 0.4, -0.3, 0.25
+    out = orc.svf_exp(v, 3)
+    # the zero outside the grid reaches one voxel further in at every
+    # squaring (each interpolation mixes in a neighbour)
+    inner = (slice(4, -4),) * 3
+    for a, val in enumerate((0.4, -0.3, 0.25)):
+        assert np.allclose(out[a][inner], val, atol=1e-14)
