@@ -236,6 +236,22 @@ fa_status fa_register(const fa_vol *fixed, const fa_vol *moving, const fa_params
                       fa_vol *u_out, float *final_loss_dev, float *final_loss_host, void *ws,
                       size_t ws_bytes, void *stream);
 
+/* Compositive update with a given step field (section "Minimizing the
+ * Eulerian differential", Algorithm 1's retraction): out = delta + u o (id +
+ * delta), trilinear with zero outside.  C=3 FA_F32 on one grid; out must not
+ * be u.  No workspace. */
+fa_status fa_compose(const fa_vol *u, const fa_vol *delta, fa_vol *out, void *stream);
+
+/* Exponential of a stationary velocity field by scaling and squaring
+ * (section "Adaptive Optimization for Diffeomorphisms", Eqs. ssbasecase and
+ * scalingandsquaring; the parametrisation the paper compares against):
+ * out = exp(v) - id after `steps` (0..30) squarings of id + v / 2^steps,
+ * each squaring a fa_compose of the field with itself.  C=3 FA_F32;
+ * workspace of fa_svf_exp_workspace_size bytes (one field). */
+size_t fa_svf_exp_workspace_size(int32_t D, int32_t H, int32_t W);
+fa_status fa_svf_exp(const fa_vol *v, int32_t steps, fa_vol *out, void *ws, size_t ws_bytes,
+                     void *stream);
+
 /* Steepest Eulerian descent direction (section "Exploiting the group
  * structure of diffeomorphisms"; Algorithm 1 with use_jac):
  * g_out = J(phi)^T g_in with J(phi) = I + grad u, i.e.

@@ -69,6 +69,43 @@ __global__ void __launch_bounds__(256) k_compose(const float *__restrict__ u,
     }
 }
 
+// u'(x) = delta(x) + u(x + delta(x)) (the compositive update with a given
+// step field; zero outside).  uo must not alias u; it may alias delta only
+// if each thread's delta is read before its writes (it is).
+__global__ void __launch_bounds__(256) k_compose_fields(const float *__restrict__ u,
+                                                        const float *delta, float *uo, int D,
+                                                        int H, int W) {
+    int x = blockIdx.x * 32 + threadIdx.x;
+    int y = blockIdx.y * 8 + threadIdx.y;
+    int z = blockIdx.z;
+    if (x >= W || y >= H) return;
+    long long N = (long long)D * H * W;
+    long long i = ((long long)z * H + y) * W + x;
+    const float dz = delta[i], dy = delta[N + i], dx = delta[2 * N + i];
+    float gz, gy, gx, r[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch)
+        r[ch] = tri_sample<false>(u + ch * N, D, H, W, z, y, x, dz, dy, dx, gz, gy, gx);
+    uo[i] = dz + r[0];
+    uo[N + i] = dy + r[1];
+    uo[2 * N + i] = dx + r[2];
+}
+
+__global__ void __launch_bounds__(256) k_scale_field(const float *__restrict__ v, float *out,
+                                                     long long n, float s) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = v[i] * s;
+}
+
+cudaError_t launch_compose_fields(const float *u, const float *delta, float *uo, Dims d,
+                                  cudaStream_t s) {
+    VoxGrid g(d.D, d.H, d.W);
+    k_compose_fields<<<g.grid, g.block, 0, s>>>(u, delta, uo, d.D, d.H, d.W);
+    note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_adam(const float *g, float *m, float *v, float *d, long long N, AdamConsts c,
                         WsHeader *h, int parity, cudaStream_t s) {
     long long blocks = (N + 255) / 256;
@@ -154,5 +191,62 @@ extern "C" fa_status fa_radam_step(const fa_vol *u_in, fa_vol *u_out, fa_vol *m,
                             adam_consts(p, t), h, parity, s));
     FA_CUDA_TRY(launch_compose((const float *)u_in->data, dir, (float *)u_out->data, d, p->lr,
                                p->c_lp, h, parity, eps_t_dev, s));
+    return FA_OK;
+}
+
+extern "C" fa_status fa_compose(const fa_vol *u, const fa_vol *delta, fa_vol *out, void *stream) {
+    using namespace fa;
+    clear_error();
+    FA_TRY(check_vol(u, "u", 3));
+    FA_TRY(check_vol(delta, "delta", 3));
+    FA_TRY(check_vol(out, "out", 3));
+    FA_TRY(same_grid(u, delta, "u", "delta"));
+    FA_TRY(same_grid(u, out, "u", "out"));
+    if (out->data == u->data) {
+        set_error("fa_compose: out must not be u");
+        return FA_ERR_INVALID;
+    }
+    Dims d{u->D, u->H, u->W};
+    FA_CUDA_TRY(launch_compose_fields((const float *)u->data, (const float *)delta->data,
+                                      (float *)out->data, d, (cudaStream_t)stream));
+    return FA_OK;
+}
+
+extern "C" size_t fa_svf_exp_workspace_size(int32_t D, int32_t H, int32_t W) {
+    fa::clear_error();
+    if (D < 1 || H < 1 || W < 1) return 0;
+    return ((size_t)3 * D * H * W * sizeof(float) + 255) & ~(size_t)255;
+}
+
+extern "C" fa_status fa_svf_exp(const fa_vol *v, int32_t steps, fa_vol *out, void *ws,
+                                size_t ws_bytes, void *stream) {
+    using namespace fa;
+    clear_error();
+    FA_TRY(check_vol(v, "v", 3));
+    FA_TRY(check_vol(out, "out", 3));
+    FA_TRY(same_grid(v, out, "v", "out"));
+    if (steps < 0 || steps > 30) {
+        set_error("fa_svf_exp: steps must be in 0..30 (got %d)", (int)steps);
+        return FA_ERR_INVALID;
+    }
+    Dims d{v->D, v->H, v->W};
+    FA_TRY(check_ws(ws, ws_bytes, fa_svf_exp_workspace_size(d.D, d.H, d.W), "fa_svf_exp"));
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long n = 3 * d.N();
+    float *a = (float *)out->data, *b = (float *)ws;
+    // an odd number of squarings starts in the workspace so the last lands in out
+    float *cur = (steps & 1) ? b : a, *nxt = (steps & 1) ? a : b;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_scale_field<<<(unsigned)blocks, 256, 0, s>>>((const float *)v->data, cur, n,
+                                                   ldexpf(1.0f, -steps));
+    note_launch();
+    FA_CUDA_TRY(cudaGetLastError());
+    for (int k = 0; k < steps; ++k) {  // phi <- phi o phi
+        FA_CUDA_TRY(launch_compose_fields(cur, cur, nxt, d, s));
+        float *t = cur;
+        cur = nxt;
+        nxt = t;
+    }
     return FA_OK;
 }

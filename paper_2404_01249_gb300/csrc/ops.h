@@ -24,6 +24,9 @@ constexpr float kMaxSigma = 10.0f;
 // ---- warp (warp.cu)
 cudaError_t launch_warp(const float *Im, const float *u, float *J, float *grad, Dims d,
                         cudaStream_t s);
+// uo = delta + u o (id + delta) (uo must not be u).
+cudaError_t launch_compose_fields(const float *u, const float *delta, float *uo, Dims d,
+                                  cudaStream_t s);
 // g_out = J(phi)^T g_in with J(phi) = I + grad u (g_out may equal g_in).
 cudaError_t launch_jac_direction(const float *gin, const float *u, float *gout, Dims d,
                                  cudaStream_t s);

@@ -39,7 +39,8 @@ EXPORTED = ["fa_params_default", "fa_status_str", "fa_last_error", "fa_warp",
             "fa_launch_count", "fa_lncc_fwd_bwd_noalloc", "fa_register_batched_workspace_size",
             "fa_register_batched", "fa_warp_lncc_adjoint_workspace_size",
             "fa_warp_lncc_adjoint", "fa_autotune", "fa_autotune_reset", "fa_autotune_choices",
-            "fa_autotune_set", "fa_jac_direction"]
+            "fa_autotune_set", "fa_jac_direction", "fa_compose", "fa_svf_exp_workspace_size",
+            "fa_svf_exp"]
 
 
 class FAError(RuntimeError):
@@ -116,6 +117,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "fa_autotune_choices": (i32, [ctypes.POINTER(ctypes.c_int32), i32]),
         "fa_autotune_set": (i32, [ctypes.POINTER(ctypes.c_int32)]),
         "fa_jac_direction": (i32, [V, V, V, vp]),
+        "fa_compose": (i32, [V, V, V, vp]),
+        "fa_svf_exp_workspace_size": (sz, [i32, i32, i32]),
+        "fa_svf_exp": (i32, [V, i32, V, vp, sz, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -423,6 +427,23 @@ def fa_jac_direction(g: torch.Tensor, u: torch.Tensor, out: Optional[torch.Tenso
     """J(phi)^T g with J(phi) = I + grad u (out may be g: in place)."""
     out = out if out is not None else torch.empty_like(g)
     _check(load().fa_jac_direction(_vol(g, 3), _vol(u, 3), _vol(out, 3), _stream()))
+    return out
+
+
+def fa_compose(u: torch.Tensor, delta: torch.Tensor, out: Optional[torch.Tensor] = None):
+    """delta + u o (id + delta)."""
+    out = out if out is not None else torch.empty_like(u)
+    _check(load().fa_compose(_vol(u, 3), _vol(delta, 3), _vol(out, 3), _stream()))
+    return out
+
+
+def fa_svf_exp(v: torch.Tensor, steps: int, out: Optional[torch.Tensor] = None):
+    """exp(v) - id by scaling and squaring."""
+    D, H, W = v.shape[-3:]
+    out = out if out is not None else torch.empty_like(v)
+    lib = load()
+    ws = workspace(lib.fa_svf_exp_workspace_size(D, H, W), v.device)
+    _check(lib.fa_svf_exp(_vol(v, 3), int(steps), _vol(out, 3), _ptr(ws), ws.numel(), _stream()))
     return out
 
 

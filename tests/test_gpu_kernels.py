@@ -187,3 +187,17 @@ def test_jac_direction(fa, orc, shape):
     gi = cuda(g)
     fa.fa_jac_direction(gi, cuda(u), out=gi)          # in place
     assert torch.equal(gi, out)
+
+
+@pytest.mark.parametrize("shape", [(19, 37, 45), (5, 3, 2)])
+def test_compose_fields(fa, orc, shape):
+    u = smooth_field(shape, 2.5, 41).astype(np.float32)
+    delta = smooth_field(shape, 1.2, 42).astype(np.float32)
+    assert rel(fa.fa_compose(cuda(u), cuda(delta)), orc.compose(u, delta)) < TOL
+
+
+@pytest.mark.parametrize("steps", [0, 1, 6])
+def test_svf_exp(fa, orc, steps):
+    shape = (24, 28, 20)
+    v = smooth_field(shape, 6.0, 43).astype(np.float32)
+    assert rel(fa.fa_svf_exp(cuda(v), steps), orc.svf_exp(v, steps)) < TOL
