@@ -82,6 +82,9 @@ def _L():
         lib.or_warp_adjoint.argtypes = [_dp, _dp, i, i, i, i, i, i, _dp]
         lib.or_jac_direction.argtypes = [_dp, _dp, i, i, i, _dp]
         lib.or_svf_exp.argtypes = [_dp, i, i, i, i, _dp]
+        lib.or_affine_field.argtypes = [_dp, i, i, i, _dp]
+        lib.or_affine_loss_grad.argtypes = [_dp, _dp, i, i, i, _dp, i, i, d, _dp, _dp]
+        lib.or_affine_register.argtypes = [_dp, _dp, i, i, i, ctypes.c_void_p, _dp, _dp]
         lib.or_box_sum.argtypes = [_dp, i, i, i, i, _dp]
         lib.or_lncc.argtypes = [_dp, _dp, i, i, i, i, d, _dp, _dp, _dp, _dp]
         lib.or_mse.argtypes = [_dp, _dp, i, i, i, _dp, _dp, _dp]
@@ -313,3 +316,48 @@ def register(If, Im, scales, iters, lr=0.5, sigma_grad=1.0, sigma_warp=0.5, wind
     _check(_L().or_register(_p(If), _p(Im), D, H, W, ctypes.byref(p), _p(u), ctypes.byref(fl),
                             _p(trace)), "register")
     return dict(u=u, final_loss=fl.value, trace=trace)
+
+
+# ------------------------------------------------------------- affine stage
+IDENTITY_AFFINE = np.array([1.0, 0, 0, 0, 1.0, 0, 0, 0, 1.0, 0, 0, 0])
+
+
+def affine_field(theta, shape):
+    """Displacement of the affine map theta (A row-major, t) on a grid (R-aff)."""
+    th = _f64(theta)
+    D, H, W = (int(n) for n in shape)
+    u = np.empty((3, D, H, W))
+    _check(_L().or_affine_field(_p(th), D, H, W, _p(u)), "affine_field")
+    return u
+
+
+def affine_loss_grad(If, Im, theta, window=5, loss="lncc", cc_eps=1e-5):
+    If, Im, th = _f64(If), _f64(Im), _f64(theta)
+    D, H, W = _dims(If)
+    L = ctypes.c_double()
+    g = np.empty(12)
+    _check(_L().or_affine_loss_grad(_p(If), _p(Im), D, H, W, _p(th), {"lncc": 0, "mse": 1}[loss],
+                                    int(window), float(cc_eps), ctypes.byref(L), _p(g)),
+           "affine_loss_grad")
+    return L.value, g
+
+
+def affine_register(If, Im, scales, iters, lr=3e-3, window=5, loss="lncc", beta1=0.9,
+                    beta2=0.999, adam_eps=1e-8, cc_eps=1e-5):
+    """Multi-scale affine pre-registration (R-aff).  Returns dict(theta, final_loss)."""
+    If, Im = _f64(If), _f64(Im)
+    D, H, W = _dims(If)
+    p = _Params()
+    p.n_levels = len(scales)
+    for k, (s, t) in enumerate(zip(scales, iters)):
+        p.scales[k] = int(s)
+        p.iters[k] = int(t)
+    p.lr, p.window = float(lr), int(window)
+    p.loss = {"lncc": 0, "mse": 1}[loss]
+    p.beta1, p.beta2, p.adam_eps, p.cc_eps = float(beta1), float(beta2), float(adam_eps), float(cc_eps)
+    th = np.empty(12)
+    fl = ctypes.c_double()
+    _check(_L().or_affine_register(_p(If), _p(Im), D, H, W, ctypes.byref(p), _p(th),
+                                   ctypes.byref(fl)), "affine_register")
+    return dict(theta=th, final_loss=fl.value)
+

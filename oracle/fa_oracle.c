@@ -21,6 +21,8 @@
  *   coordinates are voxel units of the current level; phi(x) = x + u(x).
  *
  * Readings of points the paper leaves open (each marked "reading" below):
+ *   R-aff     affine stage: p' = A p + t on align-corners normalised
+ *             coordinates, identity start, plain Adam (or_affine_register).
  *   R-jac     with use_jac, grad u by central differences inside the grid and
  *             one-sided first differences at its ends (zero on an axis of 1).
  *   R-interp  trilinear interpolation, samples outside the grid are zero
@@ -523,8 +525,6 @@ int or_upsample_field(const double *src, int Dc, int Hc, int Wc,
     return OR_OK;
 }
 
-/* Hyper-parameters of Algorithm 1 plus the smoothing widths of the grid
- * study and the Adam constants.  Plain struct, mirrored in oracle/__init__.py. */
 /* Steepest Eulerian descent direction of section "Exploiting the group
  * structure of diffeomorphisms" (the use_jac option of Algorithm 1):
  * out = J(phi)^T g with J(phi) = I + grad u, i.e.
@@ -560,6 +560,8 @@ int or_jac_direction(const double *g, const double *u, int D, int H, int W, doub
     return OR_OK;
 }
 
+/* Hyper-parameters of Algorithm 1 plus the smoothing widths of the grid
+ * study and the Adam constants.  Plain struct, mirrored in oracle/__init__.py. */
 typedef struct {
     int n_levels;
     int scales[8];
@@ -648,3 +650,112 @@ int or_register(const double *If, const double *Im, int D, int H, int W, const o
     free(u); free(m); free(v);
     return OR_OK;
 }
+
+/* ------------------------------------------------------------ affine stage
+ * Affine pre-registration (the paper aligns affinely before the
+ * diffeomorphic stage, with Adam at learning rate 3e-3 over a multi-scale
+ * schedule; section "Lung CT mapping challenges").  Reading R-aff: the map
+ * acts on align-corners normalised coordinates, p_a = 2 x_a / (n_a - 1) - 1
+ * (0 on an axis of length 1), p' = A p + t, so that theta = (A row-major, t)
+ * means the same at every pyramid level; identity start; the loss is LNCC or
+ * MSE of I_f and I_m o phi; plain Adam on the 12 parameters (no step
+ * scaling); the Adam step counter carries across levels. */
+
+/* Displacement (level voxels) of theta on a D x H x W grid:
+ * u_a(x) = (p'_a - p_a) (n_a - 1) / 2. */
+int or_affine_field(const double *theta, int D, int H, int W, double *u) {
+    if (D <= 0 || H <= 0 || W <= 0) return OR_EINVAL;
+    size_t N = (size_t)D * H * W;
+    const int n[3] = {D, H, W};
+    double half[3];
+    for (int a = 0; a < 3; ++a) half[a] = n[a] > 1 ? 0.5 * (n[a] - 1) : 0.0;
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < D; ++z)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                const int xi[3] = {z, y, x};
+                double pv[3];
+                for (int a = 0; a < 3; ++a) pv[a] = n[a] > 1 ? xi[a] / half[a] - 1.0 : 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    double q = theta[9 + a];
+                    for (int b = 0; b < 3; ++b) q += theta[3 * a + b] * pv[b];
+                    u[(size_t)a * N + IDX(z, y, x)] = (q - pv[a]) * half[a];
+                }
+            }
+    return OR_OK;
+}
+
+/* Loss of theta and its gradient: with g = dL/dJ grad I_m(phi) (dL/du),
+ * dL/dA_ab = sum_x g_a h_a p_b and dL/dt_a = sum_x g_a h_a, h_a = (n_a - 1)/2. */
+int or_affine_loss_grad(const double *If, const double *Im, int D, int H, int W,
+                        const double *theta, int loss, int window, double cc_eps, double *L,
+                        double *grad) {
+    size_t N = (size_t)D * H * W;
+    double *u = malloc(3 * N * sizeof(double)), *J = malloc(N * sizeof(double)),
+           *gJ = malloc(3 * N * sizeof(double)), *dJ = malloc(N * sizeof(double));
+    if (!u || !J || !gJ || !dJ) return OR_EINVAL;
+    or_affine_field(theta, D, H, W, u);
+    or_warp(Im, D, H, W, u, J, gJ);
+    int rc = loss == 0 ? or_lncc(If, J, D, H, W, window, cc_eps, L, NULL, grad ? dJ : NULL, NULL)
+                       : or_mse(If, J, D, H, W, L, grad ? dJ : NULL, NULL);
+    if (rc == OR_OK && grad) {
+        const int n[3] = {D, H, W};
+        double half[3];
+        for (int a = 0; a < 3; ++a) half[a] = n[a] > 1 ? 0.5 * (n[a] - 1) : 0.0;
+        for (int k = 0; k < 12; ++k) grad[k] = 0.0;
+        /* z-slices summed in order: partial sums per slice, then slice order */
+        double *part = calloc((size_t)D * 12, sizeof(double));
+        if (!part) return OR_EINVAL;
+#pragma omp parallel for schedule(static)
+        for (int z = 0; z < D; ++z) {
+            double *ps = part + (size_t)z * 12;
+            for (int y = 0; y < H; ++y)
+                for (int x = 0; x < W; ++x) {
+                    size_t i = IDX(z, y, x);
+                    const int xi[3] = {z, y, x};
+                    double pv[3];
+                    for (int a = 0; a < 3; ++a) pv[a] = n[a] > 1 ? xi[a] / half[a] - 1.0 : 0.0;
+                    for (int a = 0; a < 3; ++a) {
+                        double ga = dJ[i] * gJ[(size_t)a * N + i] * half[a];
+                        for (int b = 0; b < 3; ++b) ps[3 * a + b] += ga * pv[b];
+                        ps[9 + a] += ga;
+                    }
+                }
+        }
+        for (int z = 0; z < D; ++z)
+            for (int k = 0; k < 12; ++k) grad[k] += part[(size_t)z * 12 + k];
+        free(part);
+    }
+    free(u); free(J); free(gJ); free(dJ);
+    return rc;
+}
+
+int or_affine_register(const double *If, const double *Im, int D, int H, int W,
+                       const or_params *p, double *theta, double *final_loss) {
+    if (D <= 0 || H <= 0 || W <= 0 || !p || p->n_levels < 1 || p->n_levels > 8) return OR_EINVAL;
+    double m[12] = {0}, v[12] = {0}, g[12], dir[12];
+    for (int k = 0; k < 12; ++k) theta[k] = (k == 0 || k == 4 || k == 8) ? 1.0 : 0.0;
+    int t = 0;
+    for (int l = 0; l < p->n_levels; ++l) {
+        int s = p->scales[l];
+        int d = or_level_size(D, s), h = or_level_size(H, s), w = or_level_size(W, s);
+        size_t N = (size_t)d * h * w;
+        double *fl = malloc(N * sizeof(double)), *ml = malloc(N * sizeof(double));
+        if (!fl || !ml) return OR_EINVAL;
+        or_downsample(If, D, H, W, s, fl);
+        or_downsample(Im, D, H, W, s, ml);
+        for (int it = 0; it < p->iters[l]; ++it) {
+            double L;
+            int rc = or_affine_loss_grad(fl, ml, d, h, w, theta, p->loss, p->window, p->cc_eps, &L, g);
+            if (rc != OR_OK) return rc;
+            ++t;
+            or_adam(g, m, v, dir, 12, t, p->beta1, p->beta2, p->adam_eps);
+            for (int k = 0; k < 12; ++k) theta[k] -= p->lr * dir[k];
+        }
+        if (l == p->n_levels - 1)
+            or_affine_loss_grad(fl, ml, d, h, w, theta, p->loss, p->window, p->cc_eps, final_loss, NULL);
+        free(fl); free(ml);
+    }
+    return OR_OK;
+}
+
