@@ -84,6 +84,7 @@ def _L():
         lib.or_svf_exp.argtypes = [_dp, i, i, i, i, _dp]
         lib.or_affine_field.argtypes = [_dp, i, i, i, _dp]
         lib.or_affine_loss_grad.argtypes = [_dp, _dp, i, i, i, _dp, i, i, d, _dp, _dp]
+        lib.or_register_from.argtypes = [_dp, _dp, i, i, i, ctypes.c_void_p, _dp, _dp, _dp, _dp]
         lib.or_affine_register.argtypes = [_dp, _dp, i, i, i, ctypes.c_void_p, _dp, _dp]
         lib.or_box_sum.argtypes = [_dp, i, i, i, i, _dp]
         lib.or_lncc.argtypes = [_dp, _dp, i, i, i, i, d, _dp, _dp, _dp, _dp]
@@ -290,7 +291,7 @@ def upsample_field(src, shape, power: int):
 
 def register(If, Im, scales, iters, lr=0.5, sigma_grad=1.0, sigma_warp=0.5, window=5,
              loss="lncc", beta1=0.9, beta2=0.999, adam_eps=1e-8, cc_eps=1e-5, c_lp=2.0,
-             want_trace=False, use_jac=False):
+             want_trace=False, use_jac=False, u_init=None):
     """Algorithm 1 end to end.  Returns dict(u, final_loss, trace)."""
     If, Im = _f64(If), _f64(Im)
     D, H, W = _dims(If)
@@ -313,8 +314,11 @@ def register(If, Im, scales, iters, lr=0.5, sigma_grad=1.0, sigma_warp=0.5, wind
     u = np.empty((3,) + fs)
     fl = ctypes.c_double()
     trace = np.empty(int(sum(iters))) if want_trace else None
-    _check(_L().or_register(_p(If), _p(Im), D, H, W, ctypes.byref(p), _p(u), ctypes.byref(fl),
-                            _p(trace)), "register")
+    ui = _f64(u_init) if u_init is not None else None
+    if ui is not None and ui.shape != (3, D, H, W):
+        raise ValueError("u_init must be [3, D, H, W] on the input grid")
+    _check(_L().or_register_from(_p(If), _p(Im), D, H, W, ctypes.byref(p), _p(ui), _p(u),
+                                 ctypes.byref(fl), _p(trace)), "register")
     return dict(u=u, final_loss=fl.value, trace=trace)
 
 

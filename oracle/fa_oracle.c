@@ -592,8 +592,20 @@ static int loss_and_grad(const or_params *p, const double *If, const double *J,
  * scale); final_loss receives L(phi_final) on the last level;
  * loss_trace (nullable, sum(iters) entries) receives the loss of every
  * iteration before its update. */
+int or_register_from(const double *If, const double *Im, int D, int H, int W, const or_params *p,
+                     const double *u_init, double *u_out, double *final_loss, double *loss_trace);
+
 int or_register(const double *If, const double *Im, int D, int H, int W, const or_params *p,
                 double *u_out, double *final_loss, double *loss_trace) {
+    return or_register_from(If, Im, D, H, W, p, NULL, u_out, final_loss, loss_trace);
+}
+
+/* or_register starting from a displacement u_init given on the input grid
+ * (NULL: the identity), e.g. an affine pre-alignment: the first level starts
+ * from u_init resampled to its grid (align corners, scaled like the level
+ * hand-off), with zero Adam state. */
+int or_register_from(const double *If, const double *Im, int D, int H, int W, const or_params *p,
+                     const double *u_init, double *u_out, double *final_loss, double *loss_trace) {
     if (D <= 0 || H <= 0 || W <= 0 || !p || p->n_levels < 1 || p->n_levels > 8) return OR_EINVAL;
     for (int l = 0; l < p->n_levels; ++l)
         if (p->scales[l] < 1 || p->iters[l] < 0) return OR_EINVAL;
@@ -612,6 +624,8 @@ int or_register(const double *If, const double *Im, int D, int H, int W, const o
         if (!fl || !ml || !nu || !nm || !nv || !J || !gJ || !dJ || !g || !dir || !tmp) return OR_EINVAL;
         or_downsample(If, D, H, W, s, fl);
         or_downsample(Im, D, H, W, s, ml);
+        if (l == 0 && u_init)
+            or_upsample_field(u_init, D, H, W, nu, d, h, w, 1);
         if (l > 0) {   /* Algorithm 1: phi <- Upsample(phi), state likewise */
             or_upsample_field(u, pd, ph, pw, nu, d, h, w, 1);
             or_upsample_field(m, pd, ph, pw, nm, d, h, w, -1);

@@ -73,3 +73,17 @@ def test_recovers_a_known_affine_map(orc):
     inner = (slice(None),) + (slice(3, -3),) * 3
     assert np.sqrt((expect[inner] ** 2).sum(0)).mean() > 0.5
     assert np.sqrt((err[inner] ** 2).sum(0)).mean() < 0.15
+
+
+def test_register_from_an_affine_start_with_zero_iterations(orc):
+    """Starting the deformable stage from an affine displacement: with no
+    iterations the result is that displacement, carried through the pyramid
+    exactly (align-corners resampling is exact on affine fields)."""
+    shape = (13, 15, 17)
+    f, m, _ = synth.blobs_pair(shape=shape, sigma=2.5)
+    A = np.eye(3) + 0.03 * np.random.default_rng(7).standard_normal((3, 3))
+    u0 = orc.affine_field(theta_of(A, [0.02, -0.01, 0.03]), shape)
+    r = orc.register(f, m, [2, 1], [0, 0], u_init=u0)
+    assert np.allclose(r["u"], u0, rtol=0, atol=1e-12)
+    r1 = orc.register(f, m, [1], [0], u_init=u0)
+    assert np.array_equal(r1["u"], u0)
