@@ -328,6 +328,34 @@ fa_status fa_autotune_reset(void);
 int32_t fa_autotune_choices(int32_t *rows, int32_t capacity);
 fa_status fa_autotune_set(const int32_t *row);
 
+/* fa_register starting from a displacement u_init (C=3 FA_F32 on the input
+ * grid, e.g. an affine pre-alignment from fa_affine_field) instead of the
+ * identity: the first level starts from u_init resampled to its grid (align
+ * corners, scaled like the level hand-off) with zero Adam state.  u_init NULL
+ * is fa_register. */
+fa_status fa_register_from(const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
+                           const fa_vol *u_init, fa_vol *u_out, float *final_loss_dev,
+                           float *final_loss_host, void *ws, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Affine pre-registration (the paper's affine stage before the
+ * diffeomorphic one, Adam at learning rate 3e-3 over a multi-scale schedule;
+ * section "Lung CT mapping challenges").  The map acts on align-corners
+ * normalised coordinates p_a = 2 x_a / (n_a - 1) - 1: p' = A p + t with
+ * theta = (A row-major, t), 12 floats, identity start; loss LNCC or MSE as
+ * in fa_register; plain Adam (lr, beta1, beta2, adam_eps of p; the other
+ * smoothing and step fields are unused); the step counter carries across
+ * levels.  theta_dev (12 device floats) receives the result, u_out (C=3,
+ * last level's grid, may be NULL) its displacement, final_loss_dev (may be
+ * NULL) the loss there.  Asynchronous; no host synchronisation, so it can
+ * be recorded in a graph.  Workspace of fa_affine_workspace_size bytes. */
+size_t fa_affine_workspace_size(int32_t D, int32_t H, int32_t W, const fa_params *p);
+fa_status fa_affine_register(const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
+                             float *theta_dev, fa_vol *u_out_opt, float *final_loss_dev,
+                             void *ws, size_t ws_bytes, void *stream);
+/* Displacement (voxels of u_out's grid) of the affine map theta_dev. */
+fa_status fa_affine_field(const float *theta_dev, fa_vol *u_out, void *stream);
+
 /* Waits for `stream` and returns the status word that kernels recorded in a
  * workspace used by fa_register, fa_radam_step or fa_lncc_fwd_bwd
  * (FA_OK, FA_ERR_NONFINITE or FA_ERR_TIMEOUT). */

@@ -231,9 +231,9 @@ fa_status register_check(const fa_vol *fixed, const fa_vol *moving, const fa_par
 
 // Everything one registration enqueues on stream s (arguments checked).
 static fa_status enqueue_registration(const fa_vol *fixed, const fa_vol *moving,
-                                      const fa_params *p, fa_vol *u_out, float *final_loss_dev,
-                                      void *ws, size_t ws_bytes, cudaStream_t s,
-                                      fa_kernel_timer *timer) {
+                                      const fa_params *p, const float *u_init, fa_vol *u_out,
+                                      float *final_loss_dev, void *ws, size_t ws_bytes,
+                                      cudaStream_t s, fa_kernel_timer *timer) {
     Dims full{fixed->D, fixed->H, fixed->W};
     const int L = p->n_levels - 1;
     Plan P;
@@ -262,7 +262,13 @@ static fa_status enqueue_registration(const fa_vol *fixed, const fa_vol *moving,
         const float *Im = p->scales[l] == 1 ? Im0 : P.Im[l];
         if (l == 0) {
             size_t b = sizeof(float) * 3 * d.N();
-            FA_CUDA_TRY(cudaMemsetAsync(P.u[cur], 0, b, s));
+            if (u_init) {  // start from a given displacement of the input grid
+                float sc[3];
+                handoff_scales(full, d, 1, sc);
+                FA_CUDA_TRY(launch_resample(u_init, full, P.u[cur], d, 3, sc, s));
+            } else {
+                FA_CUDA_TRY(cudaMemsetAsync(P.u[cur], 0, b, s));
+            }
             FA_CUDA_TRY(cudaMemsetAsync(P.m[cur], 0, b, s));
             FA_CUDA_TRY(cudaMemsetAsync(P.v[cur], 0, b, s));
         } else {
@@ -335,8 +341,8 @@ std::vector<GraphEntry> g_graphs;
 unsigned long long g_graph_clock = 0;
 
 std::string graph_key(int dev, const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
-                      const fa_vol *u_out, const float *final_loss_dev, const void *ws,
-                      size_t ws_bytes, const fa_kernel_timer *timer) {
+                      const float *u_init, const fa_vol *u_out, const float *final_loss_dev,
+                      const void *ws, size_t ws_bytes, const fa_kernel_timer *timer) {
     // field by field: the structs may carry uninitialised padding
     std::string k;
     auto add = [&](const void *b, size_t n) { k.append((const char *)b, n); };
@@ -351,6 +357,7 @@ std::string graph_key(int dev, const fa_vol *fixed, const fa_vol *moving, const 
     vol(u_out);
     static_assert(sizeof(fa_params) == 31 * 4, "fa_params holds 31 four-byte fields, no padding");
     add(p, sizeof(*p));
+    add(&u_init, sizeof(u_init));
     add(&final_loss_dev, sizeof(final_loss_dev));
     add(&ws, sizeof(ws));
     add(&ws_bytes, sizeof(ws_bytes));
@@ -418,9 +425,15 @@ cudaError_t capture_stream(cudaStream_t *out) {
 }  // namespace
 
 fa_status register_impl(const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
-                        fa_vol *u_out, float *final_loss_dev, float *final_loss_host, void *ws,
-                        size_t ws_bytes, cudaStream_t s, fa_kernel_timer *timer) {
+                        const fa_vol *u_init, fa_vol *u_out, float *final_loss_dev,
+                        float *final_loss_host, void *ws, size_t ws_bytes, cudaStream_t s,
+                        fa_kernel_timer *timer) {
     FA_TRY(register_check(fixed, moving, p, u_out));
+    if (u_init) {
+        FA_TRY(check_vol(u_init, "u_init", 3));
+        FA_TRY(same_grid(fixed, u_init, "fixed", "u_init"));
+    }
+    const float *ui = u_init ? (const float *)u_init->data : nullptr;
     Dims full{fixed->D, fixed->H, fixed->W};
     Plan P;
     make_plan(P, nullptr, ~size_t(0), full, p);
@@ -436,7 +449,7 @@ fa_status register_impl(const fa_vol *fixed, const fa_vol *moving, const fa_para
         int dev = 0;
         FA_CUDA_TRY(cudaGetDevice(&dev));
         const std::string key =
-            graph_key(dev, fixed, moving, p, u_out, final_loss_dev, ws, ws_bytes, timer);
+            graph_key(dev, fixed, moving, p, ui, u_out, final_loss_dev, ws, ws_bytes, timer);
         unsigned long long kernels = 0;
         int timer_count = 0;
         cudaGraphExec_t exec = graph_find(key, &kernels, &timer_count);
@@ -448,7 +461,7 @@ fa_status register_impl(const fa_vol *fixed, const fa_vol *moving, const fa_para
             FA_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
             const unsigned long long k0 = launches_so_far();
             const fa_status st =
-                enqueue_registration(fixed, moving, p, u_out, final_loss_dev, ws, ws_bytes, cs,
+                enqueue_registration(fixed, moving, p, ui, u_out, final_loss_dev, ws, ws_bytes, cs,
                                      timer);
             kernels = launches_so_far() - k0;
             cudaGraph_t graph = nullptr;
@@ -468,7 +481,7 @@ fa_status register_impl(const fa_vol *fixed, const fa_vol *moving, const fa_para
         }
         FA_CUDA_TRY(cudaGraphLaunch(exec, s));
     } else {
-        FA_TRY(enqueue_registration(fixed, moving, p, u_out, final_loss_dev, ws, ws_bytes, s,
+        FA_TRY(enqueue_registration(fixed, moving, p, ui, u_out, final_loss_dev, ws, ws_bytes, s,
                                     timer));
     }
     if (final_loss_host) {
@@ -498,7 +511,16 @@ extern "C" fa_status fa_register(const fa_vol *fixed, const fa_vol *moving, cons
                                  fa_vol *u_out, float *final_loss_dev, float *final_loss_host,
                                  void *ws, size_t ws_bytes, void *stream) {
     fa::clear_error();
-    return fa::register_impl(fixed, moving, p, u_out, final_loss_dev, final_loss_host, ws,
+    return fa::register_impl(fixed, moving, p, nullptr, u_out, final_loss_dev, final_loss_host, ws,
+                             ws_bytes, (cudaStream_t)stream, nullptr);
+}
+
+extern "C" fa_status fa_register_from(const fa_vol *fixed, const fa_vol *moving,
+                                      const fa_params *p, const fa_vol *u_init, fa_vol *u_out,
+                                      float *final_loss_dev, float *final_loss_host, void *ws,
+                                      size_t ws_bytes, void *stream) {
+    fa::clear_error();
+    return fa::register_impl(fixed, moving, p, u_init, u_out, final_loss_dev, final_loss_host, ws,
                              ws_bytes, (cudaStream_t)stream, nullptr);
 }
 
@@ -566,6 +588,6 @@ extern "C" fa_status fa_register_timed(const fa_vol *fixed, const fa_vol *moving
                                        float *final_loss_host, void *ws, size_t ws_bytes,
                                        void *stream, fa_kernel_timer *timer) {
     fa::clear_error();
-    return fa::register_impl(fixed, moving, p, u_out, final_loss_dev, final_loss_host, ws,
+    return fa::register_impl(fixed, moving, p, nullptr, u_out, final_loss_dev, final_loss_host, ws,
                              ws_bytes, (cudaStream_t)stream, timer);
 }

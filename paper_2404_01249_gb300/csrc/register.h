@@ -52,7 +52,7 @@ fa_status register_check(const fa_vol *fixed, const fa_vol *moving, const fa_par
 size_t register_ws_bytes(int D, int H, int W, const fa_params *p);
 
 fa_status register_impl(const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
-                        fa_vol *u_out, float *final_loss_dev, float *final_loss_host, void *ws,
+                        const fa_vol *u_init, fa_vol *u_out, float *final_loss_dev, float *final_loss_host, void *ws,
                         size_t ws_bytes, cudaStream_t s, fa_kernel_timer *timer);
 
 }  // namespace fa

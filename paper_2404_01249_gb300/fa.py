@@ -40,7 +40,8 @@ EXPORTED = ["fa_params_default", "fa_status_str", "fa_last_error", "fa_warp",
             "fa_register_batched", "fa_warp_lncc_adjoint_workspace_size",
             "fa_warp_lncc_adjoint", "fa_autotune", "fa_autotune_reset", "fa_autotune_choices",
             "fa_autotune_set", "fa_jac_direction", "fa_compose", "fa_svf_exp_workspace_size",
-            "fa_svf_exp"]
+            "fa_svf_exp", "fa_register_from", "fa_affine_workspace_size", "fa_affine_register",
+            "fa_affine_field"]
 
 
 class FAError(RuntimeError):
@@ -120,6 +121,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "fa_compose": (i32, [V, V, V, vp]),
         "fa_svf_exp_workspace_size": (sz, [i32, i32, i32]),
         "fa_svf_exp": (i32, [V, i32, V, vp, sz, vp]),
+        "fa_register_from": (i32, [V, V, P, V, V, vp, fp, vp, sz, vp]),
+        "fa_affine_workspace_size": (sz, [i32, i32, i32, P]),
+        "fa_affine_register": (i32, [V, V, P, vp, V, vp, vp, sz, vp]),
+        "fa_affine_field": (i32, [vp, V, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -297,7 +302,8 @@ def fa_register_workspace_size(shape, params: RegParams) -> int:
 
 
 def fa_register(fixed, moving, params: RegParams, ws: Optional[torch.Tensor] = None,
-                sync: bool = True, u_out=None, loss_out=None, timer: Optional[KernelTimer] = None):
+                sync: bool = True, u_out=None, loss_out=None, timer: Optional[KernelTimer] = None,
+                u_init: Optional[torch.Tensor] = None):
     """Whole registration.  Returns dict(u=[3, d, h, w] tensor of the last
     level, loss=0-dim CUDA tensor, final_loss=float or None if sync=False)."""
     D, H, W = fixed.shape[-3:]
@@ -316,7 +322,11 @@ def fa_register(fixed, moving, params: RegParams, ws: Optional[torch.Tensor] = N
     host = ctypes.c_float() if sync else None
     args = (_vol(fixed, 1, True), _vol(moving, 1, True), ctypes.byref(p), _vol(u_out, 3), _ptr(loss),
             ctypes.byref(host) if sync else None, _ptr(ws), ws.numel(), _stream())
-    if timer is None:
+    if u_init is not None:
+        if timer is not None:
+            raise ValueError("u_init and timer cannot be combined")
+        _check(lib.fa_register_from(args[0], args[1], args[2], _vol(u_init, 3), *args[3:]))
+    elif timer is None:
         _check(lib.fa_register(*args))
     else:
         _check(lib.fa_register_timed(*args, ctypes.byref(timer)))
@@ -444,6 +454,35 @@ def fa_svf_exp(v: torch.Tensor, steps: int, out: Optional[torch.Tensor] = None):
     lib = load()
     ws = workspace(lib.fa_svf_exp_workspace_size(D, H, W), v.device)
     _check(lib.fa_svf_exp(_vol(v, 3), int(steps), _vol(out, 3), _ptr(ws), ws.numel(), _stream()))
+    return out
+
+
+def fa_affine_register(fixed, moving, params: RegParams, sync: bool = True):
+    """Affine pre-registration (see fa.h).  Returns dict(theta=12 floats on the
+    device, u=[3, d, h, w] of the last level, loss, final_loss)."""
+    D, H, W = fixed.shape[-3:]
+    p = params.to_c()
+    lib = load()
+    need = lib.fa_affine_workspace_size(D, H, W, ctypes.byref(p))
+    if need == 0:
+        raise FAError(FA_ERR_INVALID, lib.fa_last_error().decode())
+    ws = workspace(need, fixed.device)
+    s = params.scales[-1]
+    theta = torch.empty(12, device=fixed.device)
+    u = torch.empty((3, level_size(D, s), level_size(H, s), level_size(W, s)), device=fixed.device)
+    loss = torch.empty((), device=fixed.device)
+    _check(lib.fa_affine_register(_vol(fixed, 1), _vol(moving, 1), ctypes.byref(p), _ptr(theta),
+                                  _vol(u, 3), _ptr(loss), _ptr(ws), ws.numel(), _stream()))
+    out = dict(theta=theta, u=u, loss=loss)
+    if sync:
+        torch.cuda.current_stream().synchronize()
+        out["final_loss"] = float(loss)
+    return out
+
+
+def fa_affine_field(theta: torch.Tensor, shape, out: Optional[torch.Tensor] = None):
+    out = out if out is not None else torch.empty((3,) + tuple(shape), device=theta.device)
+    _check(load().fa_affine_field(_ptr(theta), _vol(out, 3), _stream()))
     return out
 
 
