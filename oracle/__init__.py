@@ -85,6 +85,8 @@ def _L():
         lib.or_affine_field.argtypes = [_dp, i, i, i, _dp]
         lib.or_affine_loss_grad.argtypes = [_dp, _dp, i, i, i, _dp, i, i, d, _dp, _dp]
         lib.or_register_from.argtypes = [_dp, _dp, i, i, i, ctypes.c_void_p, _dp, _dp, _dp, _dp]
+        lib.or_inverse_energy_grad.argtypes = [_dp, _dp, i, i, i, _dp, _dp]
+        lib.or_inverse.argtypes = [_dp, i, i, i, ctypes.c_void_p, _dp, _dp]
         lib.or_affine_register.argtypes = [_dp, _dp, i, i, i, ctypes.c_void_p, _dp, _dp]
         lib.or_box_sum.argtypes = [_dp, i, i, i, i, _dp]
         lib.or_lncc.argtypes = [_dp, _dp, i, i, i, i, d, _dp, _dp, _dp, _dp]
@@ -364,4 +366,34 @@ def affine_register(If, Im, scales, iters, lr=3e-3, window=5, loss="lncc", beta1
     _check(_L().or_affine_register(_p(If), _p(Im), D, H, W, ctypes.byref(p), _p(th),
                                    ctypes.byref(fl)), "affine_register")
     return dict(theta=th, final_loss=fl.value)
+
+
+# ---------------------------------------------------------------- inverse
+def inverse_energy_grad(u, w, want_grad=True):
+    u, w = _f64(u), _f64(w)
+    _, D, H, W = u.shape
+    E = ctypes.c_double()
+    g = np.empty_like(u) if want_grad else None
+    _check(_L().or_inverse_energy_grad(_p(u), _p(w), D, H, W, ctypes.byref(E), _p(g)),
+           "inverse_energy_grad")
+    return E.value, g
+
+
+def inverse(u, scales, iters, lr=0.5, sigma_grad=1.0, sigma_warp=0.5, beta1=0.9, beta2=0.999,
+            adam_eps=1e-8, c_lp=2.0):
+    """Post-hoc inverse w of phi = id + u (reading R-inv).  Returns dict(w, final_energy)."""
+    u = _f64(u)
+    _, D, H, W = u.shape
+    p = _Params()
+    p.n_levels = len(scales)
+    for k, (s, t) in enumerate(zip(scales, iters)):
+        p.scales[k] = int(s)
+        p.iters[k] = int(t)
+    p.lr, p.sigma_grad, p.sigma_warp = float(lr), float(sigma_grad), float(sigma_warp)
+    p.beta1, p.beta2, p.adam_eps, p.c_lp = float(beta1), float(beta2), float(adam_eps), float(c_lp)
+    fs = level_shape((D, H, W), scales[-1])
+    w = np.empty((3,) + fs)
+    E = ctypes.c_double()
+    _check(_L().or_inverse(_p(u), D, H, W, ctypes.byref(p), _p(w), ctypes.byref(E)), "inverse")
+    return dict(w=w, final_energy=E.value)
 

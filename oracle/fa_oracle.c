@@ -21,6 +21,8 @@
  *   coordinates are voxel units of the current level; phi(x) = x + u(x).
  *
  * Readings of points the paper leaves open (each marked "reading" below):
+ *   R-inv     post-hoc inverse: Algorithm 1's update on the
+ *             inverse-consistency energy, exact Gateaux gradient (or_inverse).
  *   R-aff     affine stage: p' = A p + t on align-corners normalised
  *             coordinates, identity start, plain Adam (or_affine_register).
  *   R-jac     with use_jac, grad u by central differences inside the grid and
@@ -770,6 +772,107 @@ int or_affine_register(const double *If, const double *Im, int D, int H, int W,
             or_affine_loss_grad(fl, ml, d, h, w, theta, p->loss, p->window, p->cc_eps, final_loss, NULL);
         free(fl); free(ml);
     }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------ inverse map
+ * Post-hoc inverse of phi = id + u (section "Alternative formulations for
+ * Eulerian differential"): psi = id + w minimises
+ *   E(w) = (1/N) sum_x |psi(phi(x)) - x|^2 + |phi(psi(x)) - x|^2
+ *        = (1/N) sum_x |u(x) + w(x + u(x))|^2 + |w(x) + u(x + w(x))|^2
+ * over a multi-scale schedule with Algorithm 1's update (reading R-inv).
+ * The gradient is the exact Gateaux derivative: the first term scatters
+ * 2 A(x) / N through the trilinear weights of w at x + u(x); the second gives
+ * 2 (I + grad u(x + w(x)))^T B(x) / N with the interpolant's derivative. */
+int or_inverse_energy_grad(const double *u, const double *w, int D, int H, int W, double *E,
+                           double *g) {
+    if (D <= 0 || H <= 0 || W <= 0) return OR_EINVAL;
+    size_t N = (size_t)D * H * W;
+    if (g) memset(g, 0, 3 * N * sizeof(double));
+    double e = 0.0;
+    for (int z = 0; z < D; ++z)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                size_t i = IDX(z, y, x);
+                double pa[3] = {z + u[i], y + u[N + i], x + u[2 * N + i]};
+                double pb[3] = {z + w[i], y + w[N + i], x + w[2 * N + i]};
+                double A[3], B[3], G[3][3];
+                for (int c = 0; c < 3; ++c) {
+                    A[c] = u[(size_t)c * N + i] +
+                           trilinear(w + (size_t)c * N, D, H, W, pa[0], pa[1], pa[2], NULL);
+                    B[c] = w[(size_t)c * N + i] +
+                           trilinear(u + (size_t)c * N, D, H, W, pb[0], pb[1], pb[2], G[c]);
+                    e += A[c] * A[c] + B[c] * B[c];
+                }
+                if (!g) continue;
+                for (int a = 0; a < 3; ++a) {       /* (I + grad u)^T B */
+                    double s = B[a];
+                    for (int j = 0; j < 3; ++j) s += G[j][a] * B[j];
+                    g[(size_t)a * N + i] += 2.0 * s / (double)N;
+                }
+                /* scatter of 2 A / N to the corners of x + u(x) */
+                if (isnan(pa[0]) || isnan(pa[1]) || isnan(pa[2])) continue;
+                if (pa[0] < -1.0 || pa[1] < -1.0 || pa[2] < -1.0 || pa[0] >= (double)D ||
+                    pa[1] >= (double)H || pa[2] >= (double)W)
+                    continue;
+                double fz = floor(pa[0]), fy = floor(pa[1]), fx = floor(pa[2]);
+                int z0 = (int)fz, y0 = (int)fy, x0 = (int)fx;
+                double tz = pa[0] - fz, ty = pa[1] - fy, tx = pa[2] - fx;
+                double wz[2] = {1.0 - tz, tz}, wy[2] = {1.0 - ty, ty}, wx[2] = {1.0 - tx, tx};
+                for (int a2 = 0; a2 < 2; ++a2)
+                    for (int b2 = 0; b2 < 2; ++b2)
+                        for (int e2 = 0; e2 < 2; ++e2) {
+                            int zz = z0 + a2, yy = y0 + b2, xx = x0 + e2;
+                            if (!in_grid(zz, yy, xx, D, H, W)) continue;
+                            double wt = wz[a2] * wy[b2] * wx[e2];
+                            for (int c = 0; c < 3; ++c)
+                                g[(size_t)c * N + IDX(zz, yy, xx)] += 2.0 * A[c] * wt / (double)N;
+                        }
+            }
+    if (E) *E = e / (double)N;
+    return OR_OK;
+}
+
+int or_inverse(const double *u, int D, int H, int W, const or_params *p, double *w_out,
+               double *final_energy) {
+    if (D <= 0 || H <= 0 || W <= 0 || !p || p->n_levels < 1 || p->n_levels > 8) return OR_EINVAL;
+    int t = 0, pd = 0, ph = 0, pw = 0;
+    double *w = NULL, *m = NULL, *v = NULL;
+    for (int l = 0; l < p->n_levels; ++l) {
+        int s = p->scales[l];
+        int d = or_level_size(D, s), h = or_level_size(H, s), wd = or_level_size(W, s);
+        size_t N = (size_t)d * h * wd;
+        double *ul = malloc(3 * N * sizeof(double));
+        double *nw = calloc(3 * N, sizeof(double)), *nm = calloc(3 * N, sizeof(double)),
+               *nv = calloc(3 * N, sizeof(double));
+        double *g = malloc(3 * N * sizeof(double)), *dir = malloc(3 * N * sizeof(double)),
+               *tmp = malloc(3 * N * sizeof(double));
+        if (!ul || !nw || !nm || !nv || !g || !dir || !tmp) return OR_EINVAL;
+        or_upsample_field(u, D, H, W, ul, d, h, wd, 1);   /* phi at this level */
+        if (l > 0) {
+            or_upsample_field(w, pd, ph, pw, nw, d, h, wd, 1);
+            or_upsample_field(m, pd, ph, pw, nm, d, h, wd, -1);
+            or_upsample_field(v, pd, ph, pw, nv, d, h, wd, -2);
+        }
+        free(w); free(m); free(v);
+        w = nw; m = nm; v = nv;
+        pd = d; ph = h; pw = wd;
+        for (int it = 0; it < p->iters[l]; ++it) {
+            or_inverse_energy_grad(ul, w, d, h, wd, NULL, g);
+            or_gauss_smooth(g, g, 3, d, h, wd, p->sigma_grad);
+            ++t;
+            or_adam(g, m, v, dir, 3 * N, t, p->beta1, p->beta2, p->adam_eps);
+            or_step_scale(dir, dir, d, h, wd, p->lr, p->c_lp);
+            or_compose(w, dir, tmp, d, h, wd);
+            or_gauss_smooth(tmp, w, 3, d, h, wd, p->sigma_warp);
+        }
+        if (l == p->n_levels - 1) {
+            or_inverse_energy_grad(ul, w, d, h, wd, final_energy, NULL);
+            memcpy(w_out, w, 3 * N * sizeof(double));
+        }
+        free(ul); free(g); free(dir); free(tmp);
+    }
+    free(w); free(m); free(v);
     return OR_OK;
 }
 
