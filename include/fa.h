@@ -356,6 +356,34 @@ fa_status fa_affine_register(const fa_vol *fixed, const fa_vol *moving, const fa
 /* Displacement (voxels of u_out's grid) of the affine map theta_dev. */
 fa_status fa_affine_field(const float *theta_dev, fa_vol *u_out, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Post-hoc inverse of a displacement (section "Alternative formulations for
+ * Eulerian differential": the inverse map is found after the registration by
+ * an optimisation of the same kind).  With phi = id + u and psi = id + w the
+ * energy is the inverse-consistency error
+ *   E(w) = (1/N) sum_x |u(x) + w(x + u(x))|^2 + |w(x) + u(x + w(x))|^2
+ * (trilinear, zero outside), minimised over the multi-scale schedule of p
+ * (scales, iters, sigma_grad, sigma_warp, lr, c_lp, Adam constants; the loss
+ * fields are unused) with the Algorithm 1 update: Gaussian(sigma_grad) of
+ * the gradient, Adam, step scaling, compose, Gaussian(sigma_warp).  Level l
+ * works on u resampled to its grid (align corners, scaled to its voxels);
+ * w, m and v are handed off between levels like fa_register's.
+ * u: C=3 FA_F32 on the input grid; w_out: C=3 FA_F32 on the last level's
+ * grid; final_energy_dev (device float, may be NULL) receives E there.
+ * Deterministic: the scatter of the first term accumulates in 64-bit fixed
+ * point (2^40 relative to the largest term) with integer atomics.
+ * Asynchronous; workspace of fa_inverse_workspace_size bytes.
+ *
+ * fa_inverse_energy_grad evaluates E(w) (energy_dev, may be NULL) and its
+ * exact Gateaux gradient g_out = dE/dw (C=3) on one grid, for checks and
+ * for callers with their own optimiser; workspace of
+ * fa_inverse_workspace_size with one level at scale 1. */
+size_t fa_inverse_workspace_size(int32_t D, int32_t H, int32_t W, const fa_params *p);
+fa_status fa_inverse(const fa_vol *u, const fa_params *p, fa_vol *w_out, float *final_energy_dev,
+                     void *ws, size_t ws_bytes, void *stream);
+fa_status fa_inverse_energy_grad(const fa_vol *u, const fa_vol *w, float *energy_dev,
+                                 fa_vol *g_out, void *ws, size_t ws_bytes, void *stream);
+
 /* Waits for `stream` and returns the status word that kernels recorded in a
  * workspace used by fa_register, fa_radam_step or fa_lncc_fwd_bwd
  * (FA_OK, FA_ERR_NONFINITE or FA_ERR_TIMEOUT). */

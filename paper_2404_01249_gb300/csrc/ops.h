@@ -75,7 +75,8 @@ struct AdamConsts {
 };
 AdamConsts adam_consts(const fa_params *p, int t);
 fa_status check_adam_params(const fa_params *p, const char *who);
-// d = Adam direction; block max of |d| into h->step_max_bits[parity].
+// d = Adam direction over N voxels of 3 channels (planar, 3N floats each);
+// block max of the voxel norm |d| into h->step_max_bits[parity].
 cudaError_t launch_adam(const float *g, float *m, float *v, float *d, long long N, AdamConsts c,
                         WsHeader *h, int parity, cudaStream_t s);
 // u_out = delta + u_in o (id + delta), delta = -lr / (c_lp max) d; resets the

@@ -41,7 +41,8 @@ EXPORTED = ["fa_params_default", "fa_status_str", "fa_last_error", "fa_warp",
             "fa_warp_lncc_adjoint", "fa_autotune", "fa_autotune_reset", "fa_autotune_choices",
             "fa_autotune_set", "fa_jac_direction", "fa_compose", "fa_svf_exp_workspace_size",
             "fa_svf_exp", "fa_register_from", "fa_affine_workspace_size", "fa_affine_register",
-            "fa_affine_field"]
+            "fa_affine_field", "fa_inverse_workspace_size", "fa_inverse",
+            "fa_inverse_energy_grad"]
 
 
 class FAError(RuntimeError):
@@ -125,6 +126,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "fa_affine_workspace_size": (sz, [i32, i32, i32, P]),
         "fa_affine_register": (i32, [V, V, P, vp, V, vp, vp, sz, vp]),
         "fa_affine_field": (i32, [vp, V, vp]),
+        "fa_inverse_workspace_size": (sz, [i32, i32, i32, P]),
+        "fa_inverse": (i32, [V, P, V, vp, vp, sz, vp]),
+        "fa_inverse_energy_grad": (i32, [V, V, vp, V, vp, sz, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -484,6 +488,41 @@ def fa_affine_field(theta: torch.Tensor, shape, out: Optional[torch.Tensor] = No
     out = out if out is not None else torch.empty((3,) + tuple(shape), device=theta.device)
     _check(load().fa_affine_field(_ptr(theta), _vol(out, 3), _stream()))
     return out
+
+
+def fa_inverse(u: torch.Tensor, params: RegParams, sync: bool = True):
+    """Post-hoc inverse w of the displacement u (see fa.h).  Returns
+    dict(w=[3, d, h, w] of the last level, energy, final_energy)."""
+    D, H, W = u.shape[-3:]
+    p = params.to_c()
+    lib = load()
+    need = lib.fa_inverse_workspace_size(D, H, W, ctypes.byref(p))
+    if need == 0:
+        raise FAError(FA_ERR_INVALID, lib.fa_last_error().decode())
+    ws = workspace(need, u.device)
+    s = params.scales[-1]
+    w = torch.empty((3, level_size(D, s), level_size(H, s), level_size(W, s)), device=u.device)
+    energy = torch.empty((), device=u.device)
+    _check(lib.fa_inverse(_vol(u, 3), ctypes.byref(p), _vol(w, 3), _ptr(energy), _ptr(ws),
+                          ws.numel(), _stream()))
+    out = dict(w=w, energy=energy)
+    if sync:
+        torch.cuda.current_stream().synchronize()
+        out["final_energy"] = float(energy)
+    return out
+
+
+def fa_inverse_energy_grad(u: torch.Tensor, w: torch.Tensor):
+    """(energy, dE/dw) of the inverse-consistency energy on one grid."""
+    D, H, W = u.shape[-3:]
+    lib = load()
+    p = RegParams(scales=(1,), iters=(0,)).to_c()
+    ws = workspace(lib.fa_inverse_workspace_size(D, H, W, ctypes.byref(p)), u.device)
+    g = torch.empty_like(w)
+    energy = torch.empty((), device=u.device)
+    _check(lib.fa_inverse_energy_grad(_vol(u, 3), _vol(w, 3), _ptr(energy), _vol(g, 3),
+                                      _ptr(ws), ws.numel(), _stream()))
+    return energy, g
 
 
 def fa_launch_count() -> int:
