@@ -87,6 +87,10 @@ def _L():
         lib.or_register_from.argtypes = [_dp, _dp, i, i, i, ctypes.c_void_p, _dp, _dp, _dp, _dp]
         lib.or_inverse_energy_grad.argtypes = [_dp, _dp, i, i, i, _dp, _dp]
         lib.or_inverse.argtypes = [_dp, i, i, i, ctypes.c_void_p, _dp, _dp]
+        lib.or_symmetric_loss_grad.argtypes = [_dp, _dp, i, i, i, ctypes.c_void_p, _dp, _dp,
+                                               _dp, _dp, _dp]
+        lib.or_register_symmetric.argtypes = [_dp, _dp, i, i, i, ctypes.c_void_p,
+                                              ctypes.c_void_p, _dp, _dp, _dp, _dp, _dp]
         lib.or_affine_register.argtypes = [_dp, _dp, i, i, i, ctypes.c_void_p, _dp, _dp]
         lib.or_box_sum.argtypes = [_dp, i, i, i, i, _dp]
         lib.or_lncc.argtypes = [_dp, _dp, i, i, i, i, d, _dp, _dp, _dp, _dp]
@@ -397,3 +401,52 @@ def inverse(u, scales, iters, lr=0.5, sigma_grad=1.0, sigma_warp=0.5, beta1=0.9,
     _check(_L().or_inverse(_p(u), D, H, W, ctypes.byref(p), _p(w), ctypes.byref(E)), "inverse")
     return dict(w=w, final_energy=E.value)
 
+
+# -------------------------------------------------------------- symmetric
+def _params(scales, iters, lr=0.5, sigma_grad=1.0, sigma_warp=0.5, window=5, loss="lncc",
+            beta1=0.9, beta2=0.999, adam_eps=1e-8, cc_eps=1e-5, c_lp=2.0, use_jac=False):
+    p = _Params()
+    p.n_levels = len(scales)
+    for k, (s, t) in enumerate(zip(scales, iters)):
+        p.scales[k] = int(s)
+        p.iters[k] = int(t)
+    p.lr, p.sigma_grad, p.sigma_warp = float(lr), float(sigma_grad), float(sigma_warp)
+    p.window = int(window)
+    p.loss = {"lncc": 0, "mse": 1}[loss]
+    p.beta1, p.beta2, p.adam_eps = float(beta1), float(beta2), float(adam_eps)
+    p.cc_eps, p.c_lp = float(cc_eps), float(c_lp)
+    p.use_jac = 1 if use_jac else 0
+    return p
+
+
+def symmetric_loss_grad(If, Im, uF, uM, window=5, loss="lncc", cc_eps=1e-5, want_grad=True):
+    """L(I_f o phi_F, I_m o phi_M) and its derivatives in u_F, u_M (R-sym)."""
+    If, Im, uF, uM = _f64(If), _f64(Im), _f64(uF), _f64(uM)
+    D, H, W = _dims(If)
+    p = _params([1], [0], window=window, loss=loss, cc_eps=cc_eps)
+    L = ctypes.c_double()
+    gF = np.empty_like(uF) if want_grad else None
+    gM = np.empty_like(uM) if want_grad else None
+    _check(_L().or_symmetric_loss_grad(_p(If), _p(Im), D, H, W, ctypes.byref(p), _p(uF), _p(uM),
+                                       ctypes.byref(L), _p(gF), _p(gM)), "symmetric_loss_grad")
+    return L.value, gF, gM
+
+
+def register_symmetric(If, Im, scales, iters, inv_scales=(1,), inv_iters=(50,), **kw):
+    """Symmetric registration (R-sym).  Returns dict(u, uF, uM, final_loss,
+    mid_loss); u = phi_M o phi_F^-1 - id on the last level's grid."""
+    If, Im = _f64(If), _f64(Im)
+    D, H, W = _dims(If)
+    if Im.shape != If.shape:
+        raise ValueError("fixed and moving must share a grid")
+    p = _params(scales, iters, **kw)
+    ikw = {k: kw[k] for k in ("lr", "sigma_grad", "sigma_warp", "beta1", "beta2", "adam_eps",
+                              "c_lp") if k in kw}
+    pi = _params(inv_scales, inv_iters, **ikw)
+    fs = level_shape((D, H, W), scales[-1])
+    u, uF, uM = (np.empty((3,) + fs) for _ in range(3))
+    fl, ml = ctypes.c_double(), ctypes.c_double()
+    _check(_L().or_register_symmetric(_p(If), _p(Im), D, H, W, ctypes.byref(p), ctypes.byref(pi),
+                                      _p(u), _p(uF), _p(uM), ctypes.byref(fl), ctypes.byref(ml)),
+           "register_symmetric")
+    return dict(u=u, uF=uF, uM=uM, final_loss=fl.value, mid_loss=ml.value)

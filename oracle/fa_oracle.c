@@ -21,6 +21,9 @@
  *   coordinates are voxel units of the current level; phi(x) = x + u(x).
  *
  * Readings of points the paper leaves open (each marked "reading" below):
+ *   R-sym     symmetric objective: L(I_f o phi_F, I_m o phi_M), Algorithm 1's
+ *             update of each map, phi = phi_M o phi_F^-1 with the post-hoc
+ *             inverse (or_register_symmetric).
  *   R-inv     post-hoc inverse: Algorithm 1's update on the
  *             inverse-consistency energy, exact Gateaux gradient (or_inverse).
  *   R-aff     affine stage: p' = A p + t on align-corners normalised
@@ -876,3 +879,126 @@ int or_inverse(const double *u, int D, int H, int W, const or_params *p, double 
     return OR_OK;
 }
 
+
+/* ------------------------------------------------------- symmetric objective
+ * Symmetric registration (section "Alternative formulations for Eulerian
+ * differential": the symmetric objective gets its final map as
+ * phi = phi_M o phi_F^-1, with phi_F^-1 from the post-hoc inverse).
+ * Reading R-sym: two maps phi_F = id + u_F and phi_M = id + u_M, both from
+ * the identity, minimise L(I_f o phi_F, I_m o phi_M), the loss of the two
+ * warped images (LNCC or MSE, symmetric in its arguments).  Each iteration
+ * takes Algorithm 1's update of each map from its own Gateaux derivative,
+ *   dL/dphi_F = dL/dJ_F grad I_f(phi_F),  dL/dphi_M = dL/dJ_M grad I_m(phi_M),
+ * with its own Adam moments and step scale (one step counter); the level
+ * hand-off treats both as or_register treats u.  On the last level w, the
+ * inverse of u_F, comes from or_inverse (schedule p_inv, scales relative to
+ * that grid, last scale 1), and u = w + u_M o (id + w) = phi_M o phi_F^-1 - id. */
+
+/* L(I_f o phi_F, I_m o phi_M) and both derivatives (gF, gM nullable). */
+int or_symmetric_loss_grad(const double *If, const double *Im, int D, int H, int W,
+                           const or_params *p, const double *uF, const double *uM, double *L,
+                           double *gF, double *gM) {
+    if (D <= 0 || H <= 0 || W <= 0 || !p) return OR_EINVAL;
+    size_t N = (size_t)D * H * W;
+    double *JF = malloc(N * sizeof(double)), *JM = malloc(N * sizeof(double));
+    double *gIF = malloc(3 * N * sizeof(double)), *gIM = malloc(3 * N * sizeof(double));
+    double *dF = malloc(N * sizeof(double)), *dM = malloc(N * sizeof(double));
+    int rc = OR_EINVAL;
+    if (!JF || !JM || !gIF || !gIM || !dF || !dM) goto done;
+    or_warp(If, D, H, W, uF, JF, gIF);
+    or_warp(Im, D, H, W, uM, JM, gIM);
+    /* J_F takes the fixed role of the loss, J_M the warped one */
+    if (p->loss == 0)
+        rc = or_lncc(JF, JM, D, H, W, p->window, p->cc_eps, L, NULL, dM, dF);
+    else
+        rc = or_mse(JF, JM, D, H, W, L, dM, dF);
+    if (rc != OR_OK) goto done;
+    for (int c = 0; c < 3; ++c)
+        for (size_t i = 0; i < N; ++i) {
+            if (gF) gF[(size_t)c * N + i] = dF[i] * gIF[(size_t)c * N + i];
+            if (gM) gM[(size_t)c * N + i] = dM[i] * gIM[(size_t)c * N + i];
+        }
+done:
+    free(JF); free(JM); free(gIF); free(gIM); free(dF); free(dM);
+    return rc;
+}
+
+/* Algorithm 1's update of one map from its derivative g (g is overwritten). */
+static void sym_update(const or_params *p, double *g, double *u, double *m, double *v, int t,
+                       int d, int h, int w, double *dir, double *tmp) {
+    size_t N = (size_t)d * h * w;
+    if (p->use_jac) {
+        or_jac_direction(g, u, d, h, w, tmp);
+        memcpy(g, tmp, 3 * N * sizeof(double));
+    }
+    or_gauss_smooth(g, g, 3, d, h, w, p->sigma_grad);
+    or_adam(g, m, v, dir, 3 * N, t, p->beta1, p->beta2, p->adam_eps);
+    or_step_scale(dir, dir, d, h, w, p->lr, p->c_lp);
+    or_compose(u, dir, tmp, d, h, w);
+    or_gauss_smooth(tmp, u, 3, d, h, w, p->sigma_warp);
+}
+
+int or_register_symmetric(const double *If, const double *Im, int D, int H, int W,
+                          const or_params *p, const or_params *p_inv, double *u_out,
+                          double *uF_out, double *uM_out, double *final_loss, double *mid_loss) {
+    if (D <= 0 || H <= 0 || W <= 0 || !p || !p_inv || p->n_levels < 1 || p->n_levels > 8 ||
+        p_inv->n_levels < 1 || p_inv->n_levels > 8 || p_inv->scales[p_inv->n_levels - 1] != 1)
+        return OR_EINVAL;
+    for (int l = 0; l < p->n_levels; ++l)
+        if (p->scales[l] < 1 || p->iters[l] < 0) return OR_EINVAL;
+    int t = 0, pd = 0, ph = 0, pw = 0;
+    double *u[2] = {NULL, NULL}, *m[2] = {NULL, NULL}, *v[2] = {NULL, NULL};
+    for (int l = 0; l < p->n_levels; ++l) {
+        int s = p->scales[l];
+        int d = or_level_size(D, s), h = or_level_size(H, s), w = or_level_size(W, s);
+        size_t N = (size_t)d * h * w;
+        double *fl = malloc(N * sizeof(double)), *ml = malloc(N * sizeof(double));
+        double *gF = malloc(3 * N * sizeof(double)), *gM = malloc(3 * N * sizeof(double));
+        double *dir = malloc(3 * N * sizeof(double)), *tmp = malloc(3 * N * sizeof(double));
+        if (!fl || !ml || !gF || !gM || !dir || !tmp) return OR_EINVAL;
+        or_downsample(If, D, H, W, s, fl);
+        or_downsample(Im, D, H, W, s, ml);
+        for (int k = 0; k < 2; ++k) {   /* k = 0: phi_F, k = 1: phi_M */
+            double *nu = calloc(3 * N, sizeof(double)), *nm = calloc(3 * N, sizeof(double)),
+                   *nv = calloc(3 * N, sizeof(double));
+            if (!nu || !nm || !nv) return OR_EINVAL;
+            if (l > 0) {
+                or_upsample_field(u[k], pd, ph, pw, nu, d, h, w, 1);
+                or_upsample_field(m[k], pd, ph, pw, nm, d, h, w, -1);
+                or_upsample_field(v[k], pd, ph, pw, nv, d, h, w, -2);
+            }
+            free(u[k]); free(m[k]); free(v[k]);
+            u[k] = nu; m[k] = nm; v[k] = nv;
+        }
+        pd = d; ph = h; pw = w;
+        for (int it = 0; it < p->iters[l]; ++it) {
+            double L;
+            or_symmetric_loss_grad(fl, ml, d, h, w, p, u[0], u[1], &L, gF, gM);
+            ++t;
+            sym_update(p, gF, u[0], m[0], v[0], t, d, h, w, dir, tmp);
+            sym_update(p, gM, u[1], m[1], v[1], t, d, h, w, dir, tmp);
+        }
+        if (l == p->n_levels - 1) {
+            double L, *winv = malloc(3 * N * sizeof(double)), *J = malloc(N * sizeof(double));
+            if (!winv || !J) return OR_EINVAL;
+            if (mid_loss) {
+                or_symmetric_loss_grad(fl, ml, d, h, w, p, u[0], u[1], &L, NULL, NULL);
+                *mid_loss = L;
+            }
+            or_inverse(u[0], d, h, w, p_inv, winv, NULL);
+            or_compose(u[1], winv, u_out, d, h, w);      /* phi_M o phi_F^-1 */
+            or_warp(ml, d, h, w, u_out, J, NULL);
+            if (p->loss == 0)
+                or_lncc(fl, J, d, h, w, p->window, p->cc_eps, &L, NULL, NULL, NULL);
+            else
+                or_mse(fl, J, d, h, w, &L, NULL, NULL);
+            *final_loss = L;
+            if (uF_out) memcpy(uF_out, u[0], 3 * N * sizeof(double));
+            if (uM_out) memcpy(uM_out, u[1], 3 * N * sizeof(double));
+            free(winv); free(J);
+        }
+        free(fl); free(ml); free(gF); free(gM); free(dir); free(tmp);
+    }
+    for (int k = 0; k < 2; ++k) { free(u[k]); free(m[k]); free(v[k]); }
+    return OR_OK;
+}
