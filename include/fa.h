@@ -384,6 +384,42 @@ fa_status fa_inverse(const fa_vol *u, const fa_params *p, fa_vol *w_out, float *
 fa_status fa_inverse_energy_grad(const fa_vol *u, const fa_vol *w, float *energy_dev,
                                  fa_vol *g_out, void *ws, size_t ws_bytes, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Symmetric registration (section "Alternative formulations for Eulerian
+ * differential": the symmetric objective obtains phi = phi_M o phi_F^-1
+ * with the post-hoc inverse).  Two maps phi_F = id + u_F and
+ * phi_M = id + u_M start at the identity and minimise
+ * L(I_f o phi_F, I_m o phi_M) (p->loss, window, cc_eps); every iteration
+ * applies Algorithm 1's update (p's Gaussians, Adam, step scaling, compose,
+ * use_jac) to each map from its own derivative
+ *   dL/dphi_F = dL/dJ_F grad I_f(phi_F),  dL/dphi_M = dL/dJ_M grad I_m(phi_M),
+ * with separate Adam moments and step scales and one step counter; both maps
+ * are handed off between levels like fa_register's.  On the last level w,
+ * the post-hoc inverse of u_F (fa_inverse with schedule p_inv, whose scales
+ * are relative to that grid and whose last scale must be 1), gives
+ *   u_out = w + u_M o (id + w)   (phi_M o phi_F^-1 - id).
+ * fixed/moving: C=1 volumes of p->storage; u_out and the optional uF_out,
+ * uM_out: C=3 FA_F32 on the last level's grid.  final_loss_dev receives
+ * L(I_f, I_m o (id + u_out)), mid_loss_dev L(I_f o phi_F, I_m o phi_M)
+ * (device floats, either may be NULL).  Per-op kernels, no graph
+ * recording (p->mode and p->graph are ignored).  Asynchronous; workspace of
+ * fa_register_symmetric_workspace_size bytes (0: invalid arguments).
+ *
+ * fa_symmetric_loss_grad evaluates L(I_f o phi_F, I_m o phi_M) and both
+ * derivatives on one grid (FA_F32 volumes; gF_out, gM_out: C=3); workspace
+ * of fa_symmetric_loss_grad_workspace_size bytes. */
+size_t fa_register_symmetric_workspace_size(int32_t D, int32_t H, int32_t W, const fa_params *p,
+                                            const fa_params *p_inv);
+fa_status fa_register_symmetric(const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
+                                const fa_params *p_inv, fa_vol *u_out, fa_vol *uF_out_opt,
+                                fa_vol *uM_out_opt, float *final_loss_dev, float *mid_loss_dev,
+                                void *ws, size_t ws_bytes, void *stream);
+size_t fa_symmetric_loss_grad_workspace_size(int32_t D, int32_t H, int32_t W);
+fa_status fa_symmetric_loss_grad(const fa_vol *fixed, const fa_vol *moving, const fa_vol *uF,
+                                 const fa_vol *uM, int32_t loss, int32_t window, float cc_eps,
+                                 float *loss_dev, fa_vol *gF_out, fa_vol *gM_out, void *ws,
+                                 size_t ws_bytes, void *stream);
+
 /* Waits for `stream` and returns the status word that kernels recorded in a
  * workspace used by fa_register, fa_radam_step or fa_lncc_fwd_bwd
  * (FA_OK, FA_ERR_NONFINITE or FA_ERR_TIMEOUT). */

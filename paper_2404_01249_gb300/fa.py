@@ -42,7 +42,9 @@ EXPORTED = ["fa_params_default", "fa_status_str", "fa_last_error", "fa_warp",
             "fa_autotune_set", "fa_jac_direction", "fa_compose", "fa_svf_exp_workspace_size",
             "fa_svf_exp", "fa_register_from", "fa_affine_workspace_size", "fa_affine_register",
             "fa_affine_field", "fa_inverse_workspace_size", "fa_inverse",
-            "fa_inverse_energy_grad"]
+            "fa_inverse_energy_grad", "fa_register_symmetric_workspace_size",
+            "fa_register_symmetric", "fa_symmetric_loss_grad_workspace_size",
+            "fa_symmetric_loss_grad"]
 
 
 class FAError(RuntimeError):
@@ -129,6 +131,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "fa_inverse_workspace_size": (sz, [i32, i32, i32, P]),
         "fa_inverse": (i32, [V, P, V, vp, vp, sz, vp]),
         "fa_inverse_energy_grad": (i32, [V, V, vp, V, vp, sz, vp]),
+        "fa_register_symmetric_workspace_size": (sz, [i32, i32, i32, P, P]),
+        "fa_register_symmetric": (i32, [V, V, P, P, V, V, V, vp, vp, vp, sz, vp]),
+        "fa_symmetric_loss_grad_workspace_size": (sz, [i32, i32, i32]),
+        "fa_symmetric_loss_grad": (i32, [V, V, V, V, i32, i32, f32, vp, V, V, vp, sz, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -523,6 +529,48 @@ def fa_inverse_energy_grad(u: torch.Tensor, w: torch.Tensor):
     _check(lib.fa_inverse_energy_grad(_vol(u, 3), _vol(w, 3), _ptr(energy), _vol(g, 3),
                                       _ptr(ws), ws.numel(), _stream()))
     return energy, g
+
+
+def fa_register_symmetric(fixed, moving, params: RegParams, inv_params: RegParams,
+                          sync: bool = True):
+    """Symmetric registration (see fa.h).  Returns dict(u, uF, uM on the last
+    level's grid, loss, mid_loss, final_loss, final_mid_loss)."""
+    D, H, W = fixed.shape[-3:]
+    p, pi = params.to_c(), inv_params.to_c()
+    p.storage = _DTYPES.get(fixed.dtype, FA_F32)  # 16-bit images are widened in the workspace
+    lib = load()
+    need = lib.fa_register_symmetric_workspace_size(D, H, W, ctypes.byref(p), ctypes.byref(pi))
+    if need == 0:
+        raise FAError(FA_ERR_INVALID, lib.fa_last_error().decode())
+    ws = workspace(need, fixed.device)
+    s = params.scales[-1]
+    shape = (3, level_size(D, s), level_size(H, s), level_size(W, s))
+    u, uF, uM = (torch.empty(shape, device=fixed.device) for _ in range(3))
+    loss, mid = torch.empty((), device=fixed.device), torch.empty((), device=fixed.device)
+    _check(lib.fa_register_symmetric(_vol(fixed, 1, half_ok=True), _vol(moving, 1, half_ok=True),
+                                     ctypes.byref(p), ctypes.byref(pi), _vol(u, 3), _vol(uF, 3),
+                                     _vol(uM, 3), _ptr(loss), _ptr(mid), _ptr(ws), ws.numel(),
+                                     _stream()))
+    out = dict(u=u, uF=uF, uM=uM, loss=loss, mid_loss=mid)
+    if sync:
+        torch.cuda.current_stream().synchronize()
+        out["final_loss"], out["final_mid_loss"] = float(loss), float(mid)
+    return out
+
+
+def fa_symmetric_loss_grad(fixed, moving, uF, uM, window: int = 5, loss: str = "lncc",
+                           cc_eps: float = 1e-5):
+    """(L, dL/du_F, dL/du_M) of L(I_f o phi_F, I_m o phi_M) on one grid."""
+    D, H, W = fixed.shape[-3:]
+    lib = load()
+    ws = workspace(lib.fa_symmetric_loss_grad_workspace_size(D, H, W), fixed.device)
+    gF, gM = torch.empty_like(uF), torch.empty_like(uM)
+    L = torch.empty((), device=fixed.device)
+    _check(lib.fa_symmetric_loss_grad(_vol(fixed, 1), _vol(moving, 1), _vol(uF, 3), _vol(uM, 3),
+                                      {"lncc": FA_LOSS_LNCC, "mse": FA_LOSS_MSE}[loss],
+                                      int(window), float(cc_eps), _ptr(L), _vol(gF, 3),
+                                      _vol(gM, 3), _ptr(ws), ws.numel(), _stream()))
+    return L, gF, gM
 
 
 def fa_launch_count() -> int:
