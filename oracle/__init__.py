@@ -51,6 +51,7 @@ class _Params(ctypes.Structure):
         ("cc_eps", ctypes.c_double),
         ("c_lp", ctypes.c_double),
         ("use_jac", ctypes.c_int),
+        ("mi_bins", ctypes.c_int),
     ]
 
 
@@ -95,6 +96,8 @@ def _L():
         lib.or_box_sum.argtypes = [_dp, i, i, i, i, _dp]
         lib.or_lncc.argtypes = [_dp, _dp, i, i, i, i, d, _dp, _dp, _dp, _dp]
         lib.or_mse.argtypes = [_dp, _dp, i, i, i, _dp, _dp, _dp]
+        lib.or_mi.argtypes = [_dp, _dp, i, i, i, i, _dp, _dp, _dp]
+        lib.or_mi_range.argtypes = [_dp, _dp, ctypes.c_size_t, _dp]
         lib.or_gauss_taps.argtypes = [d, _dp, i]
         lib.or_gauss_smooth.argtypes = [_dp, _dp, i, i, i, i, d]
         lib.or_adam.argtypes = [_dp, _dp, _dp, _dp, ctypes.c_size_t, i, d, d, d]
@@ -204,6 +207,26 @@ def mse(I, J):
     return dict(loss=loss.value, dJ=dJ, dI=dI)
 
 
+def mi_range(If, Im):
+    """[lo_f, hi_f, lo_m, hi_m]: the fixed image's range and the moving
+    image's with 0 included (reading R-mi)."""
+    If, Im = _f64(If), _f64(Im)
+    r = np.empty(4)
+    _check(_L().or_mi_range(_p(If), _p(Im), If.size, _p(r)), "mi_range")
+    return r
+
+
+def mi(I, J, bins=32, rng=None, want_dJ=True):
+    """L = -MI(I, J) (reading R-mi) and dL/dJ; rng defaults to mi_range(I, J)."""
+    I, J = _f64(I), _f64(J)
+    D, H, W = _dims(I)
+    r = _f64(rng if rng is not None else mi_range(I, J))
+    loss = ctypes.c_double()
+    dJ = np.empty_like(I) if want_dJ else None
+    _check(_L().or_mi(_p(I), _p(J), D, H, W, int(bins), _p(r), ctypes.byref(loss), _p(dJ)), "mi")
+    return dict(loss=loss.value, dJ=dJ)
+
+
 def gauss_taps(sigma: float):
     buf = np.zeros(4096)
     R = _L().or_gauss_taps(float(sigma), _p(buf), 4096)
@@ -297,7 +320,7 @@ def upsample_field(src, shape, power: int):
 
 def register(If, Im, scales, iters, lr=0.5, sigma_grad=1.0, sigma_warp=0.5, window=5,
              loss="lncc", beta1=0.9, beta2=0.999, adam_eps=1e-8, cc_eps=1e-5, c_lp=2.0,
-             want_trace=False, use_jac=False, u_init=None):
+             want_trace=False, use_jac=False, u_init=None, mi_bins=32):
     """Algorithm 1 end to end.  Returns dict(u, final_loss, trace)."""
     If, Im = _f64(If), _f64(Im)
     D, H, W = _dims(If)
@@ -312,10 +335,11 @@ def register(If, Im, scales, iters, lr=0.5, sigma_grad=1.0, sigma_warp=0.5, wind
         p.iters[k] = int(t)
     p.lr, p.sigma_grad, p.sigma_warp = float(lr), float(sigma_grad), float(sigma_warp)
     p.window = int(window)
-    p.loss = {"lncc": 0, "mse": 1}[loss]
+    p.loss = {"lncc": 0, "mse": 1, "mi": 2}[loss]
     p.beta1, p.beta2, p.adam_eps = float(beta1), float(beta2), float(adam_eps)
     p.cc_eps, p.c_lp = float(cc_eps), float(c_lp)
     p.use_jac = 1 if use_jac else 0
+    p.mi_bins = int(mi_bins)
     fs = level_shape((D, H, W), scales[-1])
     u = np.empty((3,) + fs)
     fl = ctypes.c_double()

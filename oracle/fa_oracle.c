@@ -40,6 +40,8 @@
  *               varJ = S_JJ - S_J^2 / n, cc = cross^2 / (varI varJ + eps),
  *               L = -(1/N) sum_x cc(x).
  *   R-mse     L = (1/N) sum (J - I_f)^2 (the printed sum, normalised).
+ *   R-mi      mutual information with cubic B-spline Parzen windows on B
+ *             bins, intensities mapped to [1, B - 2] (or_mi), L = -MI.
  *   R-gauss   taps exp(-k^2 / 2 sigma^2), k in [-ceil(3 sigma), ceil(3 sigma)],
  *             normalised to sum 1, zero padding; sigma == 0 is the identity.
  *   R-adam    Kingma-Ba Adam with bias correction; t carries across levels.
@@ -309,6 +311,104 @@ int or_mse(const double *I, const double *J, int D, int H, int W,
     return OR_OK;
 }
 
+/* Mutual information (the cost named with LNCC in the problem statement of
+ * section "Deformable Image Registration", with a bin-count hyper-parameter
+ * in the hyper-parameter study).  Reading R-mi: Parzen-window estimate with
+ * the cubic B-spline beta3 on B bins (B >= 6) for both images; intensity v of
+ * an image with range [lo, hi] sits at bin coordinate
+ *   xi = 1 + (v - lo) (B - 3) / (hi - lo)   (xi = 1 when hi == lo),
+ * clamped to [1, B - 2], so that the weights beta3(xi - k), k = 0..B-1, sum
+ * to one;  P(a,b) = (1/N) sum_x beta3(xi_f(x) - a) beta3(xi_m(x) - b),
+ * p_f, p_m its marginals, MI = sum P log(P / (p_f p_m)) (0 log 0 = 0),
+ * L = -MI.  The exact derivative (the marginals depend on J through P; the
+ * constant part of dMI/dP cancels because the weights sum to one):
+ *   dL/dJ(x) = -(1/N) (B - 3) / (hi_m - lo_m)
+ *              sum_{a,b} log(P / (p_f p_m)) beta3(xi_f - a) beta3'(xi_m - b).
+ * The registration takes [lo, hi] of I_f from the fixed image and of J from
+ * the moving image with 0 included (samples outside the grid are 0). */
+static double bspline3(double t) {
+    double a = fabs(t);
+    if (a < 1.0) return (4.0 - 6.0 * a * a + 3.0 * a * a * a) / 6.0;
+    if (a < 2.0) return (2.0 - a) * (2.0 - a) * (2.0 - a) / 6.0;
+    return 0.0;
+}
+
+static double bspline3_d(double t) {
+    double a = fabs(t);
+    if (a < 1.0) return -2.0 * t + 1.5 * t * a;
+    if (a < 2.0) return (t > 0.0 ? -1.0 : 1.0) * 0.5 * (2.0 - a) * (2.0 - a);
+    return 0.0;
+}
+
+static double mi_coord(double v, double lo, double hi, int B) {
+    if (!(hi > lo)) return 1.0;
+    double xi = 1.0 + (v - lo) * (double)(B - 3) / (hi - lo);
+    return xi < 1.0 ? 1.0 : (xi > (double)(B - 2) ? (double)(B - 2) : xi);
+}
+
+int or_mi(const double *I, const double *J, int D, int H, int W, int B, const double *range,
+          double *loss, double *dJ) {
+    if (D <= 0 || H <= 0 || W <= 0 || B < 6 || B > 256) return OR_EINVAL;
+    size_t N = (size_t)D * H * W;
+    double *P = calloc((size_t)B * B, sizeof(double)), *pf = calloc((size_t)B, sizeof(double)),
+           *pm = calloc((size_t)B, sizeof(double)), *T = calloc((size_t)B * B, sizeof(double));
+    if (!P || !pf || !pm || !T) { free(P); free(pf); free(pm); free(T); return OR_EINVAL; }
+    for (size_t i = 0; i < N; ++i) {
+        double xf = mi_coord(I[i], range[0], range[1], B), xm = mi_coord(J[i], range[2], range[3], B);
+        for (int a = 0; a < B; ++a) {
+            double wa = bspline3(xf - a);
+            if (wa == 0.0) continue;
+            for (int b = 0; b < B; ++b) P[(size_t)a * B + b] += wa * bspline3(xm - b);
+        }
+    }
+    for (int a = 0; a < B; ++a)
+        for (int b = 0; b < B; ++b) {
+            P[(size_t)a * B + b] /= (double)N;
+            pf[a] += P[(size_t)a * B + b];
+            pm[b] += P[(size_t)a * B + b];
+        }
+    double mi = 0.0;
+    for (int a = 0; a < B; ++a)
+        for (int b = 0; b < B; ++b) {
+            double q = P[(size_t)a * B + b];
+            if (q > 0.0) {
+                T[(size_t)a * B + b] = log(q / (pf[a] * pm[b]));
+                mi += q * T[(size_t)a * B + b];
+            }
+        }
+    *loss = -mi;
+    if (dJ) {
+        double sm = range[3] > range[2] ? (double)(B - 3) / (range[3] - range[2]) : 0.0;
+        for (size_t i = 0; i < N; ++i) {
+            double xf = mi_coord(I[i], range[0], range[1], B), xm = mi_coord(J[i], range[2], range[3], B);
+            double acc = 0.0;
+            for (int a = 0; a < B; ++a) {
+                double wa = bspline3(xf - a);
+                if (wa == 0.0) continue;
+                for (int b = 0; b < B; ++b) acc += T[(size_t)a * B + b] * wa * bspline3_d(xm - b);
+            }
+            dJ[i] = -acc * sm / (double)N;
+        }
+    }
+    free(P); free(pf); free(pm); free(T);
+    return OR_OK;
+}
+
+/* [lo, hi] of the fixed image and of the moving image with 0 included
+ * (reading R-mi). */
+int or_mi_range(const double *If, const double *Im, size_t N, double *range) {
+    if (N == 0) return OR_EINVAL;
+    range[0] = range[1] = If[0];
+    range[2] = range[3] = 0.0;
+    for (size_t i = 0; i < N; ++i) {
+        range[0] = If[i] < range[0] ? If[i] : range[0];
+        range[1] = If[i] > range[1] ? If[i] : range[1];
+        range[2] = Im[i] < range[2] ? Im[i] : range[2];
+        range[3] = Im[i] > range[3] ? Im[i] : range[3];
+    }
+    return OR_OK;
+}
+
 /* Gaussian taps (reading R-gauss).  Returns the radius R, fills taps[0..2R]
  * (taps[k + R] is the weight of offset k); -1 if cap is too small. */
 int or_gauss_taps(double sigma, double *taps, int cap) {
@@ -575,16 +675,19 @@ typedef struct {
     double sigma_grad;
     double sigma_warp;
     int window;         /* LNCC box width w (odd) */
-    int loss;           /* 0 = LNCC, 1 = MSE */
+    int loss;           /* 0 = LNCC, 1 = MSE, 2 = MI (reading R-mi) */
     double beta1, beta2, adam_eps;
     double cc_eps;
     double c_lp;        /* Lipschitz-bound factor of reading R-step (2) */
     int use_jac;        /* 1: steepest Eulerian direction J(phi)^T dL/dphi (or_jac_direction) */
+    int mi_bins;        /* MI histogram bins B (loss 2) */
 } or_params;
 
+/* range: the level's MI intensity ranges (or_mi_range), used by loss 2 only */
 static int loss_and_grad(const or_params *p, const double *If, const double *J,
-                         int D, int H, int W, double *L, double *dJ) {
+                         int D, int H, int W, const double *range, double *L, double *dJ) {
     if (p->loss == 0) return or_lncc(If, J, D, H, W, p->window, p->cc_eps, L, NULL, dJ, NULL);
+    if (p->loss == 2) return or_mi(If, J, D, H, W, p->mi_bins, range, L, dJ);
     return or_mse(If, J, D, H, W, L, dJ, NULL);
 }
 
@@ -629,6 +732,8 @@ int or_register_from(const double *If, const double *Im, int D, int H, int W, co
         if (!fl || !ml || !nu || !nm || !nv || !J || !gJ || !dJ || !g || !dir || !tmp) return OR_EINVAL;
         or_downsample(If, D, H, W, s, fl);
         or_downsample(Im, D, H, W, s, ml);
+        double range[4];
+        or_mi_range(fl, ml, N, range);
         if (l == 0 && u_init)
             or_upsample_field(u_init, D, H, W, nu, d, h, w, 1);
         if (l > 0) {   /* Algorithm 1: phi <- Upsample(phi), state likewise */
@@ -642,7 +747,7 @@ int or_register_from(const double *If, const double *Im, int D, int H, int W, co
         for (int it = 0; it < p->iters[l]; ++it) {
             double L;
             or_warp(ml, d, h, w, u, J, gJ);
-            loss_and_grad(p, fl, J, d, h, w, &L, dJ);
+            loss_and_grad(p, fl, J, d, h, w, range, &L, dJ);
             if (loss_trace) loss_trace[trace_i++] = L;
             for (int c = 0; c < 3; ++c)          /* dL/dphi(x) = dL/dJ(x) grad I_m(phi(x)) */
                 for (size_t i = 0; i < N; ++i) g[(size_t)c * N + i] = dJ[i] * gJ[(size_t)c * N + i];
@@ -660,7 +765,7 @@ int or_register_from(const double *If, const double *Im, int D, int H, int W, co
         if (l == p->n_levels - 1) {
             double L;
             or_warp(ml, d, h, w, u, J, NULL);
-            loss_and_grad(p, fl, J, d, h, w, &L, NULL);
+            loss_and_grad(p, fl, J, d, h, w, range, &L, NULL);
             *final_loss = L;
             memcpy(u_out, u, 3 * N * sizeof(double));
         }
@@ -709,6 +814,7 @@ int or_affine_field(const double *theta, int D, int H, int W, double *u) {
 int or_affine_loss_grad(const double *If, const double *Im, int D, int H, int W,
                         const double *theta, int loss, int window, double cc_eps, double *L,
                         double *grad) {
+    if (loss != 0 && loss != 1) return OR_EINVAL;
     size_t N = (size_t)D * H * W;
     double *u = malloc(3 * N * sizeof(double)), *J = malloc(N * sizeof(double)),
            *gJ = malloc(3 * N * sizeof(double)), *dJ = malloc(N * sizeof(double));
@@ -898,7 +1004,7 @@ int or_inverse(const double *u, int D, int H, int W, const or_params *p, double 
 int or_symmetric_loss_grad(const double *If, const double *Im, int D, int H, int W,
                            const or_params *p, const double *uF, const double *uM, double *L,
                            double *gF, double *gM) {
-    if (D <= 0 || H <= 0 || W <= 0 || !p) return OR_EINVAL;
+    if (D <= 0 || H <= 0 || W <= 0 || !p || (p->loss != 0 && p->loss != 1)) return OR_EINVAL;
     size_t N = (size_t)D * H * W;
     double *JF = malloc(N * sizeof(double)), *JM = malloc(N * sizeof(double));
     double *gIF = malloc(3 * N * sizeof(double)), *gIM = malloc(3 * N * sizeof(double));
@@ -942,6 +1048,7 @@ int or_register_symmetric(const double *If, const double *Im, int D, int H, int 
                           const or_params *p, const or_params *p_inv, double *u_out,
                           double *uF_out, double *uM_out, double *final_loss, double *mid_loss) {
     if (D <= 0 || H <= 0 || W <= 0 || !p || !p_inv || p->n_levels < 1 || p->n_levels > 8 ||
+        (p->loss != 0 && p->loss != 1) ||
         p_inv->n_levels < 1 || p_inv->n_levels > 8 || p_inv->scales[p_inv->n_levels - 1] != 1)
         return OR_EINVAL;
     for (int l = 0; l < p->n_levels; ++l)
