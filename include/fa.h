@@ -21,7 +21,8 @@
  *
  * Arithmetic is FP32 on the GPU.  LNCC window sums are accumulated exactly
  * in 64-bit fixed point, so the E[I^2] - E[I]^2 cancellation does not lose
- * precision.  No FP64 runs on the GPU.
+ * precision.  FP64 runs on the GPU only in the one-block table of the
+ * mutual-information loss (at most 64 x 64 entries).
  */
 #ifndef FA_H
 #define FA_H
@@ -47,7 +48,7 @@ typedef enum {
 
 typedef enum { FA_F32 = 0, FA_BF16 = 1, FA_F16 = 2 } fa_dtype;
 
-typedef enum { FA_LOSS_LNCC = 0, FA_LOSS_MSE = 1 } fa_loss;
+typedef enum { FA_LOSS_LNCC = 0, FA_LOSS_MSE = 1, FA_LOSS_MI = 2 } fa_loss;
 
 /* Kernel schedule used by fa_register: FA_MODE_FUSED (four fused kernels per
  * iteration) or FA_MODE_PLAIN (one kernel per operation, intermediates in
@@ -95,11 +96,13 @@ typedef struct {
                              "Exploiting the group structure of diffeomorphisms", Algorithm 1
                              use_jac) instead of the Jacobian-free dL/dphi; see
                              fa_jac_direction.  0 (default): Jacobian-free. */
+    int32_t mi_bins;      /* histogram bins B of FA_LOSS_MI, 6..64 (default 32) */
 } fa_params;
 
 /* Fills p with: 3 levels {4,2,1} x {200,100,50}, lr 0.5, sigma_grad 1,
  * sigma_warp 0.5, window 5, LNCC, Adam (0.9, 0.999, 1e-8), cc_eps 1e-5,
- * c_lp 2, fused mode, FP32 storage, graph replay on, Jacobian-free direction. */
+ * c_lp 2, fused mode, FP32 storage, graph replay on, Jacobian-free direction,
+ * 32 MI bins. */
 fa_status fa_params_default(fa_params *p);
 
 const char *fa_status_str(fa_status s);
@@ -168,6 +171,29 @@ fa_status fa_lncc_fwd_bwd_noalloc(const fa_vol *fixed, const fa_vol *warped, int
 fa_status fa_mse_fwd_bwd(const fa_vol *fixed, const fa_vol *warped, float *loss_dev,
                          fa_vol *dL_dwarped_opt, fa_vol *dL_dfixed_opt, void *ws,
                          size_t ws_bytes, void *stream);
+
+/* Mutual-information loss (the MI cost named with LNCC in section
+ * "Deformable Image Registration"; its bin count is a hyper-parameter of the
+ * hyper-parameter study).  Parzen-window estimate with the cubic B-spline
+ * beta3 on `bins` bins (6..64) for both images: intensity v of an image with
+ * range [lo, hi] sits at xi = 1 + (v - lo) (bins - 3) / (hi - lo), clamped
+ * to [1, bins - 2];
+ *   P(a,b) = (1/N) sum_x beta3(xi_f(x) - a) beta3(xi_J(x) - b),
+ *   L = -MI = -sum_{a,b} P log(P / (p_f(a) p_J(b))),
+ *   dL/dJ(x) = -(1/N) (bins - 3) / (hi_J - lo_J)
+ *              sum_{a,b} log(P / (p_f p_J)) beta3(xi_f - a) beta3'(xi_J - b).
+ * range_dev_opt: 4 device floats lo_f, hi_f, lo_J, hi_J; NULL takes [min, max]
+ * of `fixed` and of `warped` with 0 included (fa_register takes the moving
+ * image's range with 0 included, since samples outside the grid are 0).
+ * loss_dev (device float) receives L; dL_dwarped_opt (C=1) dL/dJ (either may
+ * be NULL).  The joint histogram is accumulated in 2^-26 fixed point with
+ * integer atomics: the result does not depend on thread order.  FA_F32,
+ * same grid; workspace of fa_mi_workspace_size(bins) bytes (0: bins out of
+ * range). */
+size_t fa_mi_workspace_size(int32_t bins);
+fa_status fa_mi_fwd_bwd(const fa_vol *fixed, const fa_vol *warped, int32_t bins,
+                        const float *range_dev_opt, float *loss_dev, fa_vol *dL_dwarped_opt,
+                        void *ws, size_t ws_bytes, void *stream);
 
 /* Bytes of workspace fa_gauss_smooth needs for C channels of D x H x W. */
 size_t fa_gauss_workspace_size(int32_t C, int32_t D, int32_t H, int32_t W);

@@ -136,6 +136,7 @@ fa_status fa_params_default(fa_params *p) {
     p->mode = FA_MODE_FUSED;
     p->storage = FA_F32;
     p->graph = 1;
+    p->mi_bins = 32;
     return FA_OK;
 }
 

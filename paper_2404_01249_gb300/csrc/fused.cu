@@ -1726,6 +1726,11 @@ fa_status fused_iteration(FusedBuffers &fb, WsHeader *h, const fa_params *p, Dim
         FA_CUDA_TRY(start(FA_K_FUSED_LNCC_GRAD));
         FA_CUDA_TRY(dispatch_k2(it.If, fb.gJ, fb.J, fb.coef, h, fb.g, d, p->window, s));
         FA_CUDA_TRY(stop(FA_K_FUSED_LNCC_GRAD));
+    } else if (p->loss == FA_LOSS_MI) {
+        FA_CUDA_TRY(start(FA_K_FUSED_LNCC_GRAD));
+        FA_CUDA_TRY(launch_mi(it.If, fb.J, fb.gJ, d, p->mi_bins, h, fb.mi, nullptr, nullptr, fb.g,
+                              s));
+        FA_CUDA_TRY(stop(FA_K_FUSED_LNCC_GRAD));
     } else {
         VoxGrid gg(d.D, d.H, d.W);
         FA_CUDA_TRY(start(FA_K_FUSED_LNCC_GRAD));

@@ -1,0 +1,345 @@
+// Mutual-information loss (named with LNCC among the costs of the problem
+// statement, section "Deformable Image Registration"; its bin count is one of
+// the hyper-parameters of the hyper-parameter study).  Parzen-window estimate
+// with the cubic B-spline beta3 on B bins for both images: an intensity v of
+// an image with range [lo, hi] sits at bin coordinate
+//   xi = 1 + (v - lo) (B - 3) / (hi - lo), clamped to [1, B - 2],
+// where the weights beta3(xi - k) of the bins k = 0..B-1 sum to one.
+//   P(a,b) = (1/N) sum_x beta3(xi_f(x) - a) beta3(xi_m(x) - b),
+//   L = -MI = -sum P log(P / (p_f p_m)),
+//   dL/dJ(x) = -(1/N) (B - 3) / (hi_m - lo_m)
+//              sum_{a,b} log(P / (p_f p_m)) beta3(xi_f - a) beta3'(xi_m - b).
+// The joint histogram is accumulated in 2^-26 fixed point with integer
+// atomics (warp-aggregated per bin), so it does not depend on thread order.
+#include "ops.h"
+#include "validate.h"
+
+namespace fa {
+
+namespace {
+
+constexpr int kMiBits = 26;  // |weight product| <= 4/9: 32 lanes sum below 2^30
+
+__device__ __forceinline__ unsigned fkey(float f) {  // order-preserving float key
+    const unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float fval(unsigned k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+struct MiMap {
+    float lo, s;  // xi = 1 + (v - lo) s
+    int B;
+    __device__ float coord(float v) const {
+        const float xi = fmaf(v - lo, s, 1.0f);
+        return fminf(fmaxf(xi, 1.0f), (float)(B - 2));
+    }
+};
+
+__device__ __forceinline__ MiMap mi_map(const unsigned *keys, int k, int B) {
+    MiMap m;
+    m.lo = fval(keys[2 * k]);
+    const float hi = fval(keys[2 * k + 1]);
+    m.s = hi > m.lo ? (float)(B - 3) / (hi - m.lo) : 0.0f;
+    m.B = B;
+    return m;
+}
+
+// cubic B-spline weights of bins floor(xi) - 1 .. floor(xi) + 2, t = xi - floor(xi)
+__device__ __forceinline__ void bspline_w(float t, float w[4]) {
+    const float t2 = t * t, t3 = t2 * t, r = 1.0f - t;
+    w[0] = r * r * r * (1.0f / 6.0f);
+    w[1] = fmaf(0.5f, t3, fmaf(-1.0f, t2, 2.0f / 3.0f));
+    w[2] = fmaf(-0.5f, t3, fmaf(0.5f, t2, fmaf(0.5f, t, 1.0f / 6.0f)));
+    w[3] = t3 * (1.0f / 6.0f);
+}
+// their derivatives with respect to xi
+__device__ __forceinline__ void bspline_dw(float t, float w[4]) {
+    const float t2 = t * t, r = 1.0f - t;
+    w[0] = -0.5f * r * r;
+    w[1] = fmaf(1.5f, t2, -2.0f * t);
+    w[2] = fmaf(-1.5f, t2, t + 0.5f);
+    w[3] = 0.5f * t2;
+}
+
+__global__ void k_mi_range_init(unsigned *keys) {
+    keys[0] = 0xffffffffu;   // lo_f: min over the fixed image
+    keys[1] = 0u;            // hi_f
+    keys[2] = fkey(0.0f);    // lo_m, hi_m: the moving image with 0 included
+    keys[3] = fkey(0.0f);
+}
+
+__global__ void k_mi_range_set(const float *range, unsigned *keys) {
+    if (threadIdx.x < 4) keys[threadIdx.x] = fkey(range[threadIdx.x]);
+}
+
+__global__ void __launch_bounds__(256) k_mi_range(const float *__restrict__ If,
+                                                  const float *__restrict__ Im, long long N,
+                                                  unsigned *keys) {
+    unsigned k[4] = {0xffffffffu, 0u, 0xffffffffu, 0u};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float a = If[i], b = Im[i];
+        if (fabsf(a) <= 3.4e38f) {
+            k[0] = min(k[0], fkey(a));
+            k[1] = max(k[1], fkey(a));
+        }
+        if (fabsf(b) <= 3.4e38f) {
+            k[2] = min(k[2], fkey(b));
+            k[3] = max(k[3], fkey(b));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        k[0] = min(k[0], __shfl_xor_sync(0xffffffffu, k[0], o));
+        k[1] = max(k[1], __shfl_xor_sync(0xffffffffu, k[1], o));
+        k[2] = min(k[2], __shfl_xor_sync(0xffffffffu, k[2], o));
+        k[3] = max(k[3], __shfl_xor_sync(0xffffffffu, k[3], o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(keys + 0, k[0]);
+        atomicMax(keys + 1, k[1]);
+        atomicMin(keys + 2, k[2]);
+        atomicMax(keys + 3, k[3]);
+    }
+}
+
+// Joint histogram: per-block shared histogram, warp-aggregated per bin.
+__global__ void __launch_bounds__(256) k_mi_hist(const float *__restrict__ I,
+                                                 const float *__restrict__ J, long long N, int B,
+                                                 const unsigned *__restrict__ keys,
+                                                 unsigned long long *ghist, WsHeader *h) {
+    extern __shared__ unsigned long long sh[];
+    const int nb = B * B, lane = threadIdx.x & 31;
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) sh[k] = 0ull;
+    __syncthreads();
+    const MiMap mf = mi_map(keys, 0, B), mm = mi_map(keys, 1, B);
+    const float scale = pow2f(kMiBits);
+    bool bad = false;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < N;
+         base += stride) {  // warp-uniform loop
+        const long long i = base + lane;
+        bool live = i < N;
+        float xf = 1.0f, xm = 1.0f;
+        if (live) {
+            const float a = I[i], b = J[i];
+            if (fabsf(a) <= 3.4e38f && fabsf(b) <= 3.4e38f) {
+                xf = mf.coord(a);
+                xm = mm.coord(b);
+            } else {
+                bad = true;
+                live = false;
+            }
+        }
+        const float ff = floorf(xf), fm = floorf(xm);
+        float wf[4], wm[4];
+        bspline_w(xf - ff, wf);
+        bspline_w(xm - fm, wm);
+        const int a0 = (int)ff - 1, b0 = (int)fm - 1;
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const unsigned v = (unsigned)quantize(wf[p] * wm[q], scale);
+                const bool use = live && v != 0u && a0 + p < B && b0 + q < B;
+                const unsigned key = use ? (unsigned)((a0 + p) * B + b0 + q) : 0xffffffffu;
+                unsigned todo = __ballot_sync(0xffffffffu, use);
+                while (todo) {
+                    const int src = __ffs(todo) - 1;
+                    const unsigned k0 = __shfl_sync(0xffffffffu, key, src);
+                    const bool mine = use && key == k0;
+                    const unsigned sum = __reduce_add_sync(0xffffffffu, mine ? v : 0u);
+                    if (lane == src) atomicAdd(sh + k0, (unsigned long long)sum);
+                    todo &= ~__ballot_sync(0xffffffffu, mine);
+                }
+            }
+    }
+    if (bad) status_set(&h->status, ST_NONFINITE);
+    __syncthreads();
+    for (int k = threadIdx.x; k < nb; k += blockDim.x)
+        if (sh[k]) atomicAdd(ghist + k, sh[k]);
+}
+
+// P, marginals, MI (FP64, fixed order) and the table log(P / (p_f p_m)).
+__global__ void __launch_bounds__(1024) k_mi_table(const unsigned long long *__restrict__ ghist,
+                                                   int B, long long N, float *T, WsHeader *h,
+                                                   float *loss_out) {
+    extern __shared__ double shd[];
+    double *P = shd, *pf = shd + B * B, *pm = pf + B, *red = pm + B;  // red: blockDim doubles
+    const int nb = B * B, tid = threadIdx.x;
+    const double inv = 1.0 / ((double)N * (double)(1ll << kMiBits));
+    for (int k = tid; k < nb; k += blockDim.x) P[k] = (double)ghist[k] * inv;
+    __syncthreads();
+    if (tid < B) {
+        double s = 0.0;
+        for (int b = 0; b < B; ++b) s += P[tid * B + b];
+        pf[tid] = s;
+    } else if (tid < 2 * B) {
+        double s = 0.0;
+        for (int a = 0; a < B; ++a) s += P[a * B + tid - B];
+        pm[tid - B] = s;
+    }
+    __syncthreads();
+    double part = 0.0;
+    for (int k = tid; k < nb; k += blockDim.x) {
+        const double q = P[k];
+        float tv = 0.0f;
+        if (q > 0.0) {
+            const double lr = log(q / (pf[k / B] * pm[k % B]));
+            part += q * lr;
+            tv = (float)lr;
+        }
+        T[k] = tv;
+    }
+    red[tid] = part;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (tid < o) red[tid] += red[tid + o];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const float L = (float)(-red[0]);
+        h->loss = L;
+        if (loss_out) *loss_out = L;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_mi_grad(const float *__restrict__ I,
+                                                 const float *__restrict__ J,
+                                                 const float *__restrict__ grad, long long N,
+                                                 int B, const unsigned *__restrict__ keys,
+                                                 const float *__restrict__ Tg, float *dJ,
+                                                 float *g) {
+    extern __shared__ float T[];
+    for (int k = threadIdx.x; k < B * B; k += blockDim.x) T[k] = Tg[k];
+    __syncthreads();
+    const MiMap mf = mi_map(keys, 0, B), mm = mi_map(keys, 1, B);
+    const float c = -mm.s / (float)N;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float xf = mf.coord(I[i]), xm = mm.coord(J[i]);
+        const float ff = floorf(xf), fm = floorf(xm);
+        float wf[4], dm[4];
+        bspline_w(xf - ff, wf);
+        bspline_dw(xm - fm, dm);
+        const int a0 = (int)ff - 1, b0 = (int)fm - 1;
+        float acc = 0.0f;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            if (a0 + p >= B) continue;
+            float r = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (b0 + q < B) r = fmaf(T[(a0 + p) * B + b0 + q], dm[q], r);
+            acc = fmaf(wf[p], r, acc);
+        }
+        const float dj = c * acc;
+        if (dJ) dJ[i] = dj;
+        if (g) {
+            g[i] = dj * grad[i];
+            g[N + i] = dj * grad[N + i];
+            g[2 * N + i] = dj * grad[2 * N + i];
+        }
+    }
+}
+
+unsigned grid_blocks(long long N) {
+    long long b = (N + 255) / 256;
+    return (unsigned)(b > 152 * 4 ? 152 * 4 : (b < 1 ? 1 : b));
+}
+
+}  // namespace
+
+MiBuffers mi_carve(WsCarver &c, int bins) {
+    MiBuffers b;
+    b.hist = c.take<unsigned long long>((size_t)bins * bins);
+    b.T = c.take<float>((size_t)bins * bins);
+    b.range = c.take<unsigned>(4);
+    return b;
+}
+
+cudaError_t launch_mi_range(const float *If, const float *Im, long long N, MiBuffers b,
+                            cudaStream_t s) {
+    k_mi_range_init<<<1, 1, 0, s>>>(b.range);
+    note_launch();
+    k_mi_range<<<grid_blocks(N), 256, 0, s>>>(If, Im, N, b.range);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mi_range_set(const float *range4, MiBuffers b, cudaStream_t s) {
+    k_mi_range_set<<<1, 32, 0, s>>>(range4, b.range);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mi(const float *I, const float *J, const float *grad, Dims d, int bins,
+                      WsHeader *h, MiBuffers b, float *loss_out, float *dJ, float *g,
+                      cudaStream_t s) {
+    const long long N = d.N();
+    const int nb = bins * bins;
+    cudaError_t e = cudaMemsetAsync(b.hist, 0, sizeof(unsigned long long) * nb, s);
+    if (e != cudaSuccess) return e;
+    const size_t hist_smem = sizeof(unsigned long long) * nb;
+    k_mi_hist<<<grid_blocks(N), 256, hist_smem, s>>>(I, J, N, bins, b.range, b.hist, h);
+    note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t tab_smem = sizeof(double) * (nb + 2 * bins + 1024);
+    k_mi_table<<<1, 1024, tab_smem, s>>>(b.hist, bins, N, b.T, h, loss_out);
+    note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (dJ || g) {
+        k_mi_grad<<<grid_blocks(N), 256, sizeof(float) * nb, s>>>(I, J, grad, N, bins, b.range,
+                                                                   b.T, dJ, g);
+        note_launch();
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace fa
+
+extern "C" size_t fa_mi_workspace_size(int32_t bins) {
+    fa::clear_error();
+    if (bins < fa::kMiMinBins || bins > fa::kMiMaxBins) return 0;
+    fa::WsCarver c(nullptr, ~size_t(0));
+    c.take<fa::WsHeader>(1);
+    fa::mi_carve(c, bins);
+    return c.off;
+}
+
+extern "C" fa_status fa_mi_fwd_bwd(const fa_vol *fixed, const fa_vol *warped, int32_t bins,
+                                   const float *range_dev_opt, float *loss_dev,
+                                   fa_vol *dL_dwarped_opt, void *ws, size_t ws_bytes,
+                                   void *stream) {
+    using namespace fa;
+    clear_error();
+    if (bins < kMiMinBins || bins > kMiMaxBins) {
+        set_error("fa_mi_fwd_bwd: bins must be in %d..%d (got %d)", kMiMinBins, kMiMaxBins,
+                  (int)bins);
+        return FA_ERR_INVALID;
+    }
+    FA_TRY(check_vol(fixed, "fixed", 1));
+    FA_TRY(check_vol(warped, "warped", 1));
+    FA_TRY(same_grid(fixed, warped, "fixed", "warped"));
+    if (dL_dwarped_opt) {
+        FA_TRY(check_vol(dL_dwarped_opt, "dL_dwarped", 1));
+        FA_TRY(same_grid(fixed, dL_dwarped_opt, "fixed", "dL_dwarped"));
+    }
+    FA_TRY(check_ws(ws, ws_bytes, fa_mi_workspace_size(bins), "fa_mi_fwd_bwd"));
+    WsCarver c(ws, ws_bytes);
+    WsHeader *h = c.take<WsHeader>(1);
+    MiBuffers b = mi_carve(c, bins);
+    cudaStream_t s = (cudaStream_t)stream;
+    const Dims d{fixed->D, fixed->H, fixed->W};
+    const float *I = (const float *)fixed->data, *J = (const float *)warped->data;
+    FA_CUDA_TRY(launch_header_reset(h, s));
+    if (range_dev_opt)
+        FA_CUDA_TRY(launch_mi_range_set(range_dev_opt, b, s));
+    else
+        FA_CUDA_TRY(launch_mi_range(I, J, d.N(), b, s));
+    FA_CUDA_TRY(launch_mi(I, J, nullptr, d, bins, h, b, loss_dev,
+                          dL_dwarped_opt ? (float *)dL_dwarped_opt->data : nullptr, nullptr, s));
+    return FA_OK;
+}

@@ -52,6 +52,23 @@ cudaError_t launch_lncc_backward(const float *I, const float *J, const float *gr
 long long mse_partials_count(Dims d);  // floats of `partials` launch_mse needs
 cudaError_t launch_mse(const float *I, const float *J, const float *grad, Dims d, WsHeader *h,
                        float *partials, float *dJ, float *dI, float *g, cudaStream_t s);
+// ---- mutual information (mi.cu)
+struct MiBuffers {
+    unsigned long long *hist;  // [B*B] joint histogram, 2^-26 fixed point
+    float *T;                  // [B*B] log(P / (p_f p_m)), 0 where P = 0
+    unsigned *range;           // [4] order-preserving keys of lo_f, hi_f, lo_m, hi_m
+};
+constexpr int kMiMinBins = 6, kMiMaxBins = 64;
+MiBuffers mi_carve(WsCarver &c, int bins);
+// [lo, hi] of I_f, and of I_m with 0 included (samples outside the grid are 0)
+cudaError_t launch_mi_range(const float *If, const float *Im, long long N, MiBuffers b,
+                            cudaStream_t s);
+cudaError_t launch_mi_range_set(const float *range4, MiBuffers b, cudaStream_t s);
+// L = -MI(I, J) into h->loss (and loss_out if not NULL); dJ = dL/dJ and
+// g = dL/dJ * grad (3 channels) when not NULL.
+cudaError_t launch_mi(const float *I, const float *J, const float *grad, Dims d, int bins,
+                      WsHeader *h, MiBuffers b, float *loss_out, float *dJ, float *g,
+                      cudaStream_t s);
 // Exact window sum S_I and rounded variance of the fixed image (p0, p1:
 // 2N int64 scratch each).
 cudaError_t launch_fixed_stats(const float *I, Dims d, int window, const WsHeader *h,

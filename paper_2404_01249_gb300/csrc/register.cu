@@ -30,8 +30,12 @@ static fa_status check_params(const fa_params *p) {
             return FA_ERR_INVALID;
         }
     }
-    if (p->loss != FA_LOSS_LNCC && p->loss != FA_LOSS_MSE) {
-        set_error("loss must be FA_LOSS_LNCC or FA_LOSS_MSE");
+    if (p->loss != FA_LOSS_LNCC && p->loss != FA_LOSS_MSE && p->loss != FA_LOSS_MI) {
+        set_error("loss must be FA_LOSS_LNCC, FA_LOSS_MSE or FA_LOSS_MI");
+        return FA_ERR_INVALID;
+    }
+    if (p->loss == FA_LOSS_MI && (p->mi_bins < kMiMinBins || p->mi_bins > kMiMaxBins)) {
+        set_error("mi_bins must be in %d..%d (got %d)", kMiMinBins, kMiMaxBins, (int)p->mi_bins);
         return FA_ERR_INVALID;
     }
     if (p->loss == FA_LOSS_LNCC &&
@@ -74,6 +78,7 @@ struct Plan {
     float *u[2], *m[2], *v[2];
     float *J, *grad, *g, *dir, *t1, *t2;
     LnccBuffers lb;
+    MiBuffers mi;
     float *partials;
     FusedBuffers fb;
     size_t bytes;
@@ -131,6 +136,8 @@ static void make_plan(Plan &P, void *base, size_t cap, Dims full, const fa_param
     } else {
         fused_carve(c, n, &P.fb);
     }
+    memset(&P.mi, 0, sizeof(P.mi));
+    if (p->loss == FA_LOSS_MI) P.mi = P.fb.mi = mi_carve(c, p->mi_bins);
     P.bytes = c.off;
     P.ok = c.ok;
 }
@@ -176,6 +183,8 @@ static fa_status plain_iteration(Plan &P, const fa_params *p, int l, const float
         FA_CUDA_TRY(launch_lncc_forward(If, P.J, d, p->window, p->cc_eps, false, P.h, P.lb, s));
         FA_CUDA_TRY(launch_lncc_backward(If, P.J, P.grad, d, p->window, P.h, P.lb, nullptr,
                                          nullptr, P.g, s));
+    } else if (p->loss == FA_LOSS_MI) {
+        FA_CUDA_TRY(launch_mi(If, P.J, P.grad, d, p->mi_bins, P.h, P.mi, nullptr, nullptr, P.g, s));
     } else {
         FA_CUDA_TRY(launch_mse(If, P.J, P.grad, d, P.h, P.partials, nullptr, nullptr, P.g, s));
     }
@@ -202,6 +211,9 @@ static fa_status final_loss(Plan &P, const fa_params *p, int l, const float *If,
             FA_CUDA_TRY(fused_lncc_forward_only(If, P.fb, d, p->window, p->cc_eps, P.h, s));
         }
         FA_CUDA_TRY(launch_loss_finalize(P.h, d.N(), -1.0f, loss_dev, s));
+    } else if (p->loss == FA_LOSS_MI) {
+        FA_CUDA_TRY(launch_mi(If, P.J, nullptr, d, p->mi_bins, P.h, P.mi, loss_dev, nullptr,
+                              nullptr, s));
     } else {
         FA_CUDA_TRY(launch_mse(If, P.J, nullptr, d, P.h, P.partials, nullptr, nullptr, nullptr, s));
         if (loss_dev)
@@ -286,6 +298,7 @@ static fa_status enqueue_registration(const fa_vol *fixed, const fa_vol *moving,
         // fixed-point scale of this level's images (max |I_f|, max |I_m|)
         FA_CUDA_TRY(cudaMemsetAsync(P.h->absmax_bits, 0, sizeof(P.h->absmax_bits), s));
         FA_CUDA_TRY(launch_absmax2(If, Im, d.N(), P.h, s));
+        if (p->loss == FA_LOSS_MI) FA_CUDA_TRY(launch_mi_range(If, Im, d.N(), P.mi, s));
         Timer tm{timer, l};
         if (p->mode == FA_MODE_FUSED)
             FA_CUDA_TRY(fused_level_start(If, Im, P.u[cur], d, p, P.h, P.fb, s));
@@ -355,7 +368,7 @@ std::string graph_key(int dev, const fa_vol *fixed, const fa_vol *moving, const 
     vol(fixed);
     vol(moving);
     vol(u_out);
-    static_assert(sizeof(fa_params) == 31 * 4, "fa_params holds 31 four-byte fields, no padding");
+    static_assert(sizeof(fa_params) == 32 * 4, "fa_params holds 32 four-byte fields, no padding");
     add(p, sizeof(*p));
     add(&u_init, sizeof(u_init));
     add(&final_loss_dev, sizeof(final_loss_dev));

@@ -14,6 +14,7 @@ struct FusedBuffers {
     float *t1, *t2;  // [3][N]: separable passes when a Gaussian is wider than the fused kernels take
     long long *sI; // [N]    : exact window sum of the level's fixed image
     float *varI;   // [N]    : its window variance
+    MiBuffers mi;  // histogram scratch of the MI loss (set by the driver)
 };
 void fused_carve(WsCarver &c, long long n, FusedBuffers *fb);
 

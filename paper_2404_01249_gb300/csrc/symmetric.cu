@@ -248,7 +248,9 @@ extern "C" size_t fa_register_symmetric_workspace_size(int32_t D, int32_t H, int
              level_size(H, p->scales[L] > 0 ? p->scales[L] : 1),
              level_size(W, p->scales[L] > 0 ? p->scales[L] : 1)};
     f.data = u.data = (void *)256;  // shape checks only
-    if (register_check(&f, &f, p, &u) != FA_OK) return 0;
+    if (register_check(&f, &f, p, &u) != FA_OK ||
+        check_loss_args(p->loss, p->window, p->cc_eps, "fa_register_symmetric") != FA_OK)
+        return 0;
     size_t inv = 0;
     if (check_inverse_schedule(Dims{D, H, W}, p, p_inv, &inv) != FA_OK) return 0;
     WsCarver c(nullptr, ~size_t(0));
@@ -265,6 +267,7 @@ extern "C" fa_status fa_register_symmetric(const fa_vol *fixed, const fa_vol *mo
     using namespace fa;
     clear_error();
     FA_TRY(register_check(fixed, moving, p, u_out));
+    FA_TRY(check_loss_args(p->loss, p->window, p->cc_eps, "fa_register_symmetric"));
     if (uF_out_opt) {
         FA_TRY(check_vol(uF_out_opt, "uF_out", 3));
         FA_TRY(same_grid(u_out, uF_out_opt, "u_out", "uF_out"));

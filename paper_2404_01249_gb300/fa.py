@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "FA_OK", 1: "FA_ERR_INVALID", 2: "FA_ERR_SHAPE", 3: "FA_ERR_D
                 4: "FA_ERR_CUDA", 5: "FA_ERR_NONFINITE", 6: "FA_ERR_TIMEOUT",
                 7: "FA_ERR_UNSUPPORTED", 8: "FA_ERR_WORKSPACE"}
 FA_F32, FA_BF16, FA_F16 = 0, 1, 2
-FA_LOSS_LNCC, FA_LOSS_MSE = 0, 1
+FA_LOSS_LNCC, FA_LOSS_MSE, FA_LOSS_MI = 0, 1, 2
 FA_MODE_FUSED, FA_MODE_PLAIN = 0, 1
 (FA_K_FUSED_WARP_LNCC, FA_K_FUSED_LNCC_GRAD, FA_K_FUSED_SMOOTH_ADAM, FA_K_FUSED_COMPOSE,
  FA_K_PLAIN_ANY, FA_K_FUSED_ALL) = 0, 1, 2, 3, 4, 5
@@ -44,7 +44,7 @@ EXPORTED = ["fa_params_default", "fa_status_str", "fa_last_error", "fa_warp",
             "fa_affine_field", "fa_inverse_workspace_size", "fa_inverse",
             "fa_inverse_energy_grad", "fa_register_symmetric_workspace_size",
             "fa_register_symmetric", "fa_symmetric_loss_grad_workspace_size",
-            "fa_symmetric_loss_grad"]
+            "fa_symmetric_loss_grad", "fa_mi_workspace_size", "fa_mi_fwd_bwd"]
 
 
 class FAError(RuntimeError):
@@ -66,7 +66,7 @@ class Params(ctypes.Structure):
                 ("beta2", ctypes.c_float), ("adam_eps", ctypes.c_float),
                 ("cc_eps", ctypes.c_float), ("c_lp", ctypes.c_float), ("mode", ctypes.c_int32),
                 ("storage", ctypes.c_int32), ("graph", ctypes.c_int32),
-                ("use_jac", ctypes.c_int32)]
+                ("use_jac", ctypes.c_int32), ("mi_bins", ctypes.c_int32)]
 
 
 class KernelTimer(ctypes.Structure):
@@ -134,6 +134,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "fa_register_symmetric_workspace_size": (sz, [i32, i32, i32, P, P]),
         "fa_register_symmetric": (i32, [V, V, P, P, V, V, V, vp, vp, vp, sz, vp]),
         "fa_symmetric_loss_grad_workspace_size": (sz, [i32, i32, i32]),
+        "fa_mi_workspace_size": (sz, [i32]),
+        "fa_mi_fwd_bwd": (i32, [V, V, i32, vp, vp, V, vp, sz, vp]),
         "fa_symmetric_loss_grad": (i32, [V, V, V, V, i32, i32, f32, vp, V, V, vp, sz, vp]),
     }
     for name, (res, args) in sig.items():
@@ -198,6 +200,7 @@ class RegParams:
     mode: str = "fused"
     graph: bool = True   # record the launch sequence once, replay it on identical calls
     use_jac: bool = False  # steepest Eulerian direction J(phi)^T dL/dphi
+    mi_bins: int = 32      # histogram bins of the MI loss
 
     def to_c(self) -> Params:
         p = Params()
@@ -210,7 +213,8 @@ class RegParams:
             p.iters[k] = int(t)
         p.lr, p.sigma_grad, p.sigma_warp = self.lr, self.sigma_grad, self.sigma_warp
         p.window = int(self.window)
-        p.loss = {"lncc": FA_LOSS_LNCC, "mse": FA_LOSS_MSE}[self.loss]
+        p.loss = {"lncc": FA_LOSS_LNCC, "mse": FA_LOSS_MSE, "mi": FA_LOSS_MI}[self.loss]
+        p.mi_bins = int(self.mi_bins)
         p.beta1, p.beta2, p.adam_eps = self.beta1, self.beta2, self.adam_eps
         p.cc_eps, p.c_lp = self.cc_eps, self.c_lp
         p.mode = {"fused": FA_MODE_FUSED, "plain": FA_MODE_PLAIN}[self.mode]
@@ -571,6 +575,23 @@ def fa_symmetric_loss_grad(fixed, moving, uF, uM, window: int = 5, loss: str = "
                                       int(window), float(cc_eps), _ptr(L), _vol(gF, 3),
                                       _vol(gM, 3), _ptr(ws), ws.numel(), _stream()))
     return L, gF, gM
+
+
+def fa_mi_fwd_bwd(fixed, warped, bins: int = 32, rng: Optional[torch.Tensor] = None,
+                  want_dJ: bool = True):
+    """L = -MI(fixed, warped) and dL/dwarped (see fa.h); rng: 4 device floats
+    (lo_f, hi_f, lo_J, hi_J) or None for the two images' own ranges."""
+    lib = load()
+    need = lib.fa_mi_workspace_size(int(bins))
+    if need == 0:
+        raise FAError(FA_ERR_INVALID, lib.fa_last_error().decode())
+    ws = workspace(need, fixed.device)
+    loss = torch.empty((), device=fixed.device)
+    dJ = torch.empty_like(warped) if want_dJ else None
+    _check(lib.fa_mi_fwd_bwd(_vol(fixed, 1), _vol(warped, 1), int(bins),
+                             _ptr(rng) if rng is not None else None, _ptr(loss), _vol(dJ, 1),
+                             _ptr(ws), ws.numel(), _stream()))
+    return dict(loss=loss, dJ=dJ)
 
 
 def fa_launch_count() -> int:
