@@ -88,6 +88,11 @@ def _L():
         lib.or_register_from.argtypes = [_dp, _dp, i, i, i, ctypes.c_void_p, _dp, _dp, _dp, _dp]
         lib.or_inverse_energy_grad.argtypes = [_dp, _dp, i, i, i, _dp, _dp]
         lib.or_inverse.argtypes = [_dp, i, i, i, ctypes.c_void_p, _dp, _dp]
+        lib.or_rodrigues.argtypes = [_dp, _dp, _dp]
+        lib.or_rodrigues.restype = None
+        lib.or_rigid_theta.argtypes = [_dp, i, i, i, _dp]
+        lib.or_rigid_loss_grad.argtypes = [_dp, _dp, i, i, i, i, i, i, _dp, i, i, d, _dp, _dp]
+        lib.or_rigid_register.argtypes = [_dp, _dp, i, i, i, ctypes.c_void_p, _dp, _dp]
         lib.or_symmetric_loss_grad.argtypes = [_dp, _dp, i, i, i, ctypes.c_void_p, _dp, _dp,
                                                _dp, _dp, _dp]
         lib.or_register_symmetric.argtypes = [_dp, _dp, i, i, i, ctypes.c_void_p,
@@ -394,6 +399,49 @@ def affine_register(If, Im, scales, iters, lr=3e-3, window=5, loss="lncc", beta1
     _check(_L().or_affine_register(_p(If), _p(Im), D, H, W, ctypes.byref(p), _p(th),
                                    ctypes.byref(fl)), "affine_register")
     return dict(theta=th, final_loss=fl.value)
+
+
+# ------------------------------------------------------------- rigid stage
+def rodrigues(w, want_grad=True):
+    """R = exp([w]x) (3 x 3) and dR/dw_k (3 x 3 x 3) (reading R-rigid)."""
+    w = _f64(w)
+    R = np.empty(9)
+    dR = np.empty(27) if want_grad else None
+    _L().or_rodrigues(_p(w), _p(R), _p(dR))
+    return R.reshape(3, 3), (dR.reshape(3, 3, 3) if want_grad else None)
+
+
+def rigid_theta(rp, shape):
+    rp = _f64(rp)
+    th = np.empty(12)
+    _check(_L().or_rigid_theta(_p(rp), *(int(n) for n in shape), _p(th)), "rigid_theta")
+    return th
+
+
+def rigid_loss_grad(If, Im, rp, full_shape=None, window=5, loss="lncc", cc_eps=1e-5):
+    If, Im, rp = _f64(If), _f64(Im), _f64(rp)
+    D, H, W = _dims(If)
+    D0, H0, W0 = full_shape if full_shape is not None else (D, H, W)
+    L = ctypes.c_double()
+    g = np.empty(6)
+    _check(_L().or_rigid_loss_grad(_p(If), _p(Im), D, H, W, D0, H0, W0, _p(rp),
+                                   {"lncc": 0, "mse": 1}[loss], int(window), float(cc_eps),
+                                   ctypes.byref(L), _p(g)), "rigid_loss_grad")
+    return L.value, g
+
+
+def rigid_register(If, Im, scales, iters, lr=3e-3, window=5, loss="lncc", beta1=0.9,
+                   beta2=0.999, adam_eps=1e-8, cc_eps=1e-5):
+    """Multi-scale rigid pre-registration (R-rigid).  Returns dict(rp, theta, final_loss)."""
+    If, Im = _f64(If), _f64(Im)
+    D, H, W = _dims(If)
+    p = _params(scales, iters, lr=lr, window=window, loss=loss, beta1=beta1, beta2=beta2,
+                adam_eps=adam_eps, cc_eps=cc_eps)
+    rp = np.empty(6)
+    fl = ctypes.c_double()
+    _check(_L().or_rigid_register(_p(If), _p(Im), D, H, W, ctypes.byref(p), _p(rp),
+                                  ctypes.byref(fl)), "rigid_register")
+    return dict(rp=rp, theta=rigid_theta(rp, (D, H, W)), final_loss=fl.value)
 
 
 # ---------------------------------------------------------------- inverse

@@ -26,6 +26,9 @@
  *             inverse (or_register_symmetric).
  *   R-inv     post-hoc inverse: Algorithm 1's update on the
  *             inverse-consistency energy, exact Gateaux gradient (or_inverse).
+ *   R-rigid   rigid stage: rotation exp([w]x) (Rodrigues) and translation in
+ *             the input grid's voxel coordinates about its centre, as the
+ *             affine map S^-1 R S, t of reading R-aff (or_rigid_register).
  *   R-aff     affine stage: p' = A p + t on align-corners normalised
  *             coordinates, identity start, plain Adam (or_affine_register).
  *   R-jac     with use_jac, grad u by central differences inside the grid and
@@ -879,6 +882,144 @@ int or_affine_register(const double *If, const double *Im, int D, int H, int W,
         }
         if (l == p->n_levels - 1)
             or_affine_loss_grad(fl, ml, d, h, w, theta, p->loss, p->window, p->cc_eps, final_loss, NULL);
+        free(fl); free(ml);
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------- rigid stage
+ * Rigid pre-registration (the rigid group among the transformation groups
+ * the paper's framework offers before the affine and deformable stages,
+ * section "Discussion": rigid -> affine -> diffeomorphism).  Reading R-rigid:
+ * the motion is rigid in the voxel coordinates of the input grid about its
+ * centre, y' = R y + tau with y = x - (n - 1) / 2; R = exp([w]x) by the
+ * Rodrigues formula (w: axis times angle, radians); the translation is kept in
+ * the normalised units of reading R-aff, t = S^-1 tau, S = diag((n_a - 1)/2)
+ * of the input grid (1 on an axis of length 1).  On normalised coordinates
+ * this is the affine map A = S^-1 R S, t, the same at every pyramid level.
+ * rp = (w, t); identity start; plain Adam on the 6 parameters; the gradient
+ * is the affine one pulled back exactly: dL/dt = dL/dt_aff and
+ * dL/dw_k = sum_ij dL/dA_ij (s_j / s_i) dR_ij/dw_k. */
+
+/* R = I + a K + b K^2 and dR/dw_k = c1 w_k K + a E_k + c2 w_k K^2 + b (E_k K + K E_k)
+ * (K = [w]x, E_k = [e_k]x, a = sin th / th, b = (1 - cos th) / th^2,
+ * c1 = a'(th) / th, c2 = b'(th) / th; power series below th = 1e-2). */
+void or_rodrigues(const double *w, double *R, double *dR /* 3 x 9, nullable */) {
+    double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2], th = sqrt(th2);
+    double a, b, c1, c2;
+    if (th < 1e-2) {
+        a = 1.0 - th2 / 6.0 + th2 * th2 / 120.0;
+        b = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
+        c1 = -1.0 / 3.0 + th2 / 30.0 - th2 * th2 / 840.0;
+        c2 = -1.0 / 12.0 + th2 / 180.0 - th2 * th2 / 6720.0;
+    } else {
+        double sn = sin(th), cs = cos(th);
+        a = sn / th;
+        b = (1.0 - cs) / th2;
+        c1 = (th * cs - sn) / (th2 * th);
+        c2 = (th * sn - 2.0 * (1.0 - cs)) / (th2 * th2);
+    }
+    double K[9] = {0.0, -w[2], w[1], w[2], 0.0, -w[0], -w[1], w[0], 0.0}, K2[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc += K[3 * i + k] * K[3 * k + j];
+            K2[3 * i + j] = acc;
+        }
+    for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0 ? 1.0 : 0.0) + a * K[i] + b * K2[i];
+    if (!dR) return;
+    for (int k = 0; k < 3; ++k) {
+        double e[3] = {0.0, 0.0, 0.0}, E[9], EK[9], KE[9];
+        e[k] = 1.0;
+        double Et[9] = {0.0, -e[2], e[1], e[2], 0.0, -e[0], -e[1], e[0], 0.0};
+        memcpy(E, Et, sizeof(E));
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double s1 = 0.0, s2 = 0.0;
+                for (int q = 0; q < 3; ++q) {
+                    s1 += E[3 * i + q] * K[3 * q + j];
+                    s2 += K[3 * i + q] * E[3 * q + j];
+                }
+                EK[3 * i + j] = s1;
+                KE[3 * i + j] = s2;
+            }
+        for (int i = 0; i < 9; ++i)
+            dR[9 * k + i] = c1 * w[k] * K[i] + a * E[i] + c2 * w[k] * K2[i] + b * (EK[i] + KE[i]);
+    }
+}
+
+static void rigid_scales(int D, int H, int W, double s[3]) {
+    const int n[3] = {D, H, W};
+    for (int a = 0; a < 3; ++a) s[a] = n[a] > 1 ? 0.5 * (n[a] - 1) : 1.0;
+}
+
+/* theta (reading R-aff) of the rigid parameters rp on a D x H x W input grid */
+int or_rigid_theta(const double *rp, int D, int H, int W, double *theta) {
+    if (D <= 0 || H <= 0 || W <= 0) return OR_EINVAL;
+    double R[9], s[3];
+    or_rodrigues(rp, R, NULL);
+    rigid_scales(D, H, W, s);
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) theta[3 * i + j] = R[3 * i + j] * s[j] / s[i];
+        theta[9 + i] = rp[3 + i];
+    }
+    return OR_OK;
+}
+
+/* the 6-parameter gradient from the affine one (gaff: 12) */
+static void rigid_pullback(const double *rp, const double s[3], const double *gaff, double *g) {
+    double R[9], dR[27];
+    or_rodrigues(rp, R, dR);
+    for (int k = 0; k < 3; ++k) {
+        double acc = 0.0;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) acc += gaff[3 * i + j] * s[j] / s[i] * dR[9 * k + 3 * i + j];
+        g[k] = acc;
+        g[3 + k] = gaff[9 + k];
+    }
+}
+
+/* loss of level images (fl, ml) at rp (input grid D0 x H0 x W0) and its
+ * 6-parameter gradient (nullable) */
+int or_rigid_loss_grad(const double *If, const double *Im, int D, int H, int W, int D0, int H0,
+                       int W0, const double *rp, int loss, int window, double cc_eps, double *L,
+                       double *grad) {
+    double theta[12], gaff[12], s[3];
+    int rc = or_rigid_theta(rp, D0, H0, W0, theta);
+    if (rc != OR_OK) return rc;
+    rc = or_affine_loss_grad(If, Im, D, H, W, theta, loss, window, cc_eps, L, grad ? gaff : NULL);
+    if (rc != OR_OK || !grad) return rc;
+    rigid_scales(D0, H0, W0, s);
+    rigid_pullback(rp, s, gaff, grad);
+    return OR_OK;
+}
+
+int or_rigid_register(const double *If, const double *Im, int D, int H, int W,
+                      const or_params *p, double *rp, double *final_loss) {
+    if (D <= 0 || H <= 0 || W <= 0 || !p || p->n_levels < 1 || p->n_levels > 8) return OR_EINVAL;
+    double m[6] = {0}, v[6] = {0}, g[6], dir[6];
+    for (int k = 0; k < 6; ++k) rp[k] = 0.0;
+    int t = 0;
+    for (int l = 0; l < p->n_levels; ++l) {
+        int s = p->scales[l];
+        int d = or_level_size(D, s), h = or_level_size(H, s), w = or_level_size(W, s);
+        size_t N = (size_t)d * h * w;
+        double *fl = malloc(N * sizeof(double)), *ml = malloc(N * sizeof(double));
+        if (!fl || !ml) return OR_EINVAL;
+        or_downsample(If, D, H, W, s, fl);
+        or_downsample(Im, D, H, W, s, ml);
+        for (int it = 0; it < p->iters[l]; ++it) {
+            double L;
+            int rc = or_rigid_loss_grad(fl, ml, d, h, w, D, H, W, rp, p->loss, p->window,
+                                        p->cc_eps, &L, g);
+            if (rc != OR_OK) return rc;
+            ++t;
+            or_adam(g, m, v, dir, 6, t, p->beta1, p->beta2, p->adam_eps);
+            for (int k = 0; k < 6; ++k) rp[k] -= p->lr * dir[k];
+        }
+        if (l == p->n_levels - 1)
+            or_rigid_loss_grad(fl, ml, d, h, w, D, H, W, rp, p->loss, p->window, p->cc_eps,
+                               final_loss, NULL);
         free(fl); free(ml);
     }
     return OR_OK;
