@@ -21,8 +21,9 @@
  *
  * Arithmetic is FP32 on the GPU.  LNCC window sums are accumulated exactly
  * in 64-bit fixed point, so the E[I^2] - E[I]^2 cancellation does not lose
- * precision.  FP64 runs on the GPU only in the one-block table of the
- * mutual-information loss (at most 64 x 64 entries).
+ * precision.  FP64 runs on the GPU only in two one-block kernels: the table
+ * of the mutual-information loss (at most 64 x 64 entries) and the 6-parameter
+ * update of the rigid stage.
  */
 #ifndef FA_H
 #define FA_H
@@ -381,6 +382,26 @@ fa_status fa_affine_register(const fa_vol *fixed, const fa_vol *moving, const fa
                              void *ws, size_t ws_bytes, void *stream);
 /* Displacement (voxels of u_out's grid) of the affine map theta_dev. */
 fa_status fa_affine_field(const float *theta_dev, fa_vol *u_out, void *stream);
+
+/* Rigid pre-registration (the rigid group, the first of the transformation
+ * groups stacked rigid -> affine -> diffeomorphism in section "Discussion").
+ * The motion is rigid in the voxel coordinates of the input grid about its
+ * centre: y' = R y + tau, y = x - (n - 1)/2, R = exp([w]x) (Rodrigues; w is
+ * the rotation axis times the angle in radians).  Parameters rp = (w, t),
+ * t = S^-1 tau in the normalised units of fa_affine_register
+ * (S = diag((n_a - 1)/2), 1 on an axis of length 1); on normalised
+ * coordinates the map is the affine theta = (S^-1 R S, t), the same at every
+ * level.  Identity start; plain Adam on the 6 parameters (lr, beta1, beta2,
+ * adam_eps of p) with the exact gradient (the 12 affine sums pulled back
+ * through dR/dw, evaluated in FP64 by one thread); loss, scales and
+ * iterations as fa_affine_register.  rp_dev (6 device floats) receives the
+ * parameters, theta_dev (12, may be NULL) the equivalent affine map, u_out
+ * (may be NULL) its displacement on the last level's grid, final_loss_dev
+ * (may be NULL) the loss there.  Workspace of fa_affine_workspace_size
+ * bytes. */
+fa_status fa_rigid_register(const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
+                            float *rp_dev, float *theta_dev, fa_vol *u_out_opt,
+                            float *final_loss_dev, void *ws, size_t ws_bytes, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Post-hoc inverse of a displacement (section "Alternative formulations for

@@ -26,6 +26,7 @@ struct AffineWs {
     Dims lvl[8];
     float *u, *J, *grad, *g, *t1, *t2, *partials;
     float *theta, *m, *v;   // 12 each
+    float *rp;              // 6 rigid parameters (rigid stage only)
     LnccBuffers lb;
 };
 
@@ -59,6 +60,7 @@ void affine_carve(WsCarver &c, Dims full, const fa_params *p, AffineWs *w) {
     w->theta = c.take<float>(12);
     w->m = c.take<float>(12);
     w->v = c.take<float>(12);
+    w->rp = c.take<float>(6);
     w->lb = lncc_carve(c, nmax);
 }
 
@@ -164,6 +166,132 @@ __global__ void k_affine_init(float *theta, float *m, float *v) {
     }
 }
 
+// ---------------------------------------------------------------- rigid
+// Rigid stage: rp = (w, t), R = exp([w]x) by the Rodrigues formula, the
+// affine map A = S^-1 R S, t on normalised coordinates (S = diag((n_a - 1)/2)
+// of the input grid, 1 on an axis of length 1), so that the motion is rigid
+// in the input grid's voxels about its centre.  The 12 affine sums are pulled
+// back exactly: dL/dt = dL/dt_aff, dL/dw_k = sum_ij dL/dA_ij (s_j / s_i)
+// dR_ij/dw_k, with
+//   R = I + a K + b K^2,  dR/dw_k = c1 w_k K + a E_k + c2 w_k K^2 + b (E_k K + K E_k)
+// (K = [w]x, E_k = [e_k]x, a = sin th / th, b = (1 - cos th) / th^2,
+// c1 = a'(th) / th, c2 = b'(th) / th; power series below th = 1e-2).
+// One thread evaluates this in FP64 (six parameters).
+__device__ void rodrigues_d(const double w[3], double R[9], double dR[27]) {
+    const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2], th = sqrt(th2);
+    double a, b, c1, c2;
+    if (th < 1e-2) {
+        a = 1.0 - th2 / 6.0 + th2 * th2 / 120.0;
+        b = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
+        c1 = -1.0 / 3.0 + th2 / 30.0 - th2 * th2 / 840.0;
+        c2 = -1.0 / 12.0 + th2 / 180.0 - th2 * th2 / 6720.0;
+    } else {
+        const double sn = sin(th), cs = cos(th);
+        a = sn / th;
+        b = (1.0 - cs) / th2;
+        c1 = (th * cs - sn) / (th2 * th);
+        c2 = (th * sn - 2.0 * (1.0 - cs)) / (th2 * th2);
+    }
+    const double K[9] = {0.0, -w[2], w[1], w[2], 0.0, -w[0], -w[1], w[0], 0.0};
+    double K2[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int q = 0; q < 3; ++q) s += K[3 * i + q] * K[3 * q + j];
+            K2[3 * i + j] = s;
+        }
+    for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0 ? 1.0 : 0.0) + a * K[i] + b * K2[i];
+    if (!dR) return;
+    for (int k = 0; k < 3; ++k) {
+        const double e0 = k == 0, e1 = k == 1, e2 = k == 2;
+        const double E[9] = {0.0, -e2, e1, e2, 0.0, -e0, -e1, e0, 0.0};
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double ek = 0.0, ke = 0.0;
+                for (int q = 0; q < 3; ++q) {
+                    ek += E[3 * i + q] * K[3 * q + j];
+                    ke += K[3 * i + q] * E[3 * q + j];
+                }
+                const int ij = 3 * i + j;
+                dR[9 * k + ij] = c1 * w[k] * K[ij] + a * E[ij] + c2 * w[k] * K2[ij] + b * (ek + ke);
+            }
+    }
+}
+
+struct RigidScales {
+    float s[3];
+};
+
+__device__ void rigid_theta_d(const float *rp, RigidScales sc, float *theta) {
+    const double w[3] = {rp[0], rp[1], rp[2]};
+    double R[9];
+    rodrigues_d(w, R, nullptr);
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j)
+            theta[3 * i + j] = (float)(R[3 * i + j] * (double)sc.s[j] / (double)sc.s[i]);
+        theta[9 + i] = rp[3 + i];
+    }
+}
+
+__global__ void k_rigid_init(float *rp, float *m, float *v, float *theta, RigidScales sc) {
+    const int k = threadIdx.x;
+    if (k < 6) {
+        rp[k] = 0.0f;
+        m[k] = 0.0f;
+        v[k] = 0.0f;
+    }
+    __syncthreads();
+    if (k == 0) rigid_theta_d(rp, sc, theta);
+}
+
+// 12 warps sum the affine partials (float-float, fixed order); thread 0 pulls
+// them back to the 6 rigid parameters, takes one Adam step and rewrites theta.
+__global__ void __launch_bounds__(384) k_rigid_adam(const float *__restrict__ partials,
+                                                    int nblocks, float *rp, float *m, float *v,
+                                                    float *theta, RigidScales sc, AdamConsts ac,
+                                                    float lr) {
+    __shared__ float gaff[12];
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float hi = 0.0f, lo = 0.0f;
+    for (int b = lane; b < nblocks; b += 32) ff_add(hi, lo, partials[(long long)b * 12 + k], 0.0f);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+        ff_add(hi, lo, oh, ol);
+    }
+    if (lane == 0) gaff[k] = hi + lo;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double w[3] = {rp[0], rp[1], rp[2]};
+    double R[9], dR[27];
+    rodrigues_d(w, R, dR);
+    float g[6];
+    for (int q = 0; q < 3; ++q) {
+        double acc = 0.0;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                acc += (double)gaff[3 * i + j] * (double)sc.s[j] / (double)sc.s[i] *
+                       dR[9 * q + 3 * i + j];
+        g[q] = (float)acc;
+        g[3 + q] = gaff[9 + q];
+    }
+    for (int q = 0; q < 6; ++q) {
+        const float mq = fmaf(ac.b1, m[q], (1.0f - ac.b1) * g[q]);
+        const float vq = fmaf(ac.b2, v[q], (1.0f - ac.b2) * g[q] * g[q]);
+        m[q] = mq;
+        v[q] = vq;
+        rp[q] -= lr * adam_dir(mq, vq, ac.rbc1, ac.rbc2, ac.eps);
+    }
+    rigid_theta_d(rp, sc, theta);
+}
+
+RigidScales rigid_scales(Dims full) {
+    RigidScales sc;
+    const int n[3] = {full.D, full.H, full.W};
+    for (int a = 0; a < 3; ++a) sc.s[a] = n[a] > 1 ? 0.5f * (float)(n[a] - 1) : 1.0f;
+    return sc;
+}
+
 fa_status check_affine_params(const fa_params *p) {
     if (!p || p->n_levels < 1 || p->n_levels > 8) {
         set_error("fa_affine_register: n_levels must be in 1..8");
@@ -234,17 +362,19 @@ extern "C" size_t fa_affine_workspace_size(int32_t D, int32_t H, int32_t W, cons
     return affine_ws_bytes(Dims{D, H, W}, p);
 }
 
-extern "C" fa_status fa_affine_register(const fa_vol *fixed, const fa_vol *moving,
-                                        const fa_params *p, float *theta_dev, fa_vol *u_out_opt,
-                                        float *final_loss_dev, void *ws, size_t ws_bytes,
-                                        void *stream) {
-    using namespace fa;
-    clear_error();
+namespace fa {
+namespace {
+
+// The affine stage, or with rp_dev the rigid one (its 6 parameters are
+// written to rp_dev, the equivalent affine map to theta_dev).
+fa_status linear_stage(const fa_vol *fixed, const fa_vol *moving, const fa_params *p, bool rigid,
+                       float *theta_dev, float *rp_dev, fa_vol *u_out_opt, float *final_loss_dev,
+                       void *ws, size_t ws_bytes, void *stream) {
     FA_TRY(check_affine_params(p));
     FA_TRY(check_vol(fixed, "fixed", 1));
     FA_TRY(check_vol(moving, "moving", 1));
     FA_TRY(same_grid(fixed, moving, "fixed", "moving"));
-    if (!theta_dev) {
+    if (!theta_dev && !rigid) {
         set_error("fa_affine_register: theta_dev must not be NULL");
         return FA_ERR_INVALID;
     }
@@ -266,7 +396,11 @@ extern "C" fa_status fa_affine_register(const fa_vol *fixed, const fa_vol *movin
     affine_carve(c, full, p, &w);
     cudaStream_t s = (cudaStream_t)stream;
     const float *If0 = (const float *)fixed->data, *Im0 = (const float *)moving->data;
-    k_affine_init<<<1, 32, 0, s>>>(w.theta, w.m, w.v);
+    const RigidScales sc = rigid_scales(full);
+    if (rigid)
+        k_rigid_init<<<1, 32, 0, s>>>(w.rp, w.m, w.v, w.theta, sc);
+    else
+        k_affine_init<<<1, 32, 0, s>>>(w.theta, w.m, w.v);
     note_launch();
     FA_CUDA_TRY(cudaGetLastError());
     for (int l = 0; l < p->n_levels; ++l) {
@@ -285,8 +419,12 @@ extern "C" fa_status fa_affine_register(const fa_vol *fixed, const fa_vol *movin
             note_launch();
             FA_CUDA_TRY(cudaGetLastError());
             ++t;
-            k_affine_adam<<<1, 384, 0, s>>>(w.partials, kRedBlocks, w.theta, w.m, w.v,
-                                            adam_consts(p, t), p->lr);
+            if (rigid)
+                k_rigid_adam<<<1, 384, 0, s>>>(w.partials, kRedBlocks, w.rp, w.m, w.v, w.theta, sc,
+                                               adam_consts(p, t), p->lr);
+            else
+                k_affine_adam<<<1, 384, 0, s>>>(w.partials, kRedBlocks, w.theta, w.m, w.v,
+                                                adam_consts(p, t), p->lr);
             note_launch();
             FA_CUDA_TRY(cudaGetLastError());
         }
@@ -303,8 +441,37 @@ extern "C" fa_status fa_affine_register(const fa_vol *fixed, const fa_vol *movin
                                             cudaMemcpyDeviceToDevice, s));
         }
     }
-    FA_CUDA_TRY(cudaMemcpyAsync(theta_dev, w.theta, 12 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    if (theta_dev)
+        FA_CUDA_TRY(
+            cudaMemcpyAsync(theta_dev, w.theta, 12 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    if (rigid)
+        FA_CUDA_TRY(cudaMemcpyAsync(rp_dev, w.rp, 6 * sizeof(float), cudaMemcpyDeviceToDevice, s));
     return FA_OK;
+}
+
+}  // namespace
+}  // namespace fa
+
+extern "C" fa_status fa_affine_register(const fa_vol *fixed, const fa_vol *moving,
+                                        const fa_params *p, float *theta_dev, fa_vol *u_out_opt,
+                                        float *final_loss_dev, void *ws, size_t ws_bytes,
+                                        void *stream) {
+    fa::clear_error();
+    return fa::linear_stage(fixed, moving, p, false, theta_dev, nullptr, u_out_opt,
+                            final_loss_dev, ws, ws_bytes, stream);
+}
+
+extern "C" fa_status fa_rigid_register(const fa_vol *fixed, const fa_vol *moving,
+                                       const fa_params *p, float *rp_dev, float *theta_dev,
+                                       fa_vol *u_out_opt, float *final_loss_dev, void *ws,
+                                       size_t ws_bytes, void *stream) {
+    fa::clear_error();
+    if (!rp_dev) {
+        fa::set_error("fa_rigid_register: rp_dev must not be NULL");
+        return FA_ERR_INVALID;
+    }
+    return fa::linear_stage(fixed, moving, p, true, theta_dev, rp_dev, u_out_opt,
+                            final_loss_dev, ws, ws_bytes, stream);
 }
 
 extern "C" fa_status fa_affine_field(const float *theta_dev, fa_vol *u_out, void *stream) {

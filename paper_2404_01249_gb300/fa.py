@@ -44,7 +44,8 @@ EXPORTED = ["fa_params_default", "fa_status_str", "fa_last_error", "fa_warp",
             "fa_affine_field", "fa_inverse_workspace_size", "fa_inverse",
             "fa_inverse_energy_grad", "fa_register_symmetric_workspace_size",
             "fa_register_symmetric", "fa_symmetric_loss_grad_workspace_size",
-            "fa_symmetric_loss_grad", "fa_mi_workspace_size", "fa_mi_fwd_bwd"]
+            "fa_symmetric_loss_grad", "fa_mi_workspace_size", "fa_mi_fwd_bwd",
+            "fa_rigid_register"]
 
 
 class FAError(RuntimeError):
@@ -128,6 +129,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "fa_affine_workspace_size": (sz, [i32, i32, i32, P]),
         "fa_affine_register": (i32, [V, V, P, vp, V, vp, vp, sz, vp]),
         "fa_affine_field": (i32, [vp, V, vp]),
+        "fa_rigid_register": (i32, [V, V, P, vp, vp, V, vp, vp, sz, vp]),
         "fa_inverse_workspace_size": (sz, [i32, i32, i32, P]),
         "fa_inverse": (i32, [V, P, V, vp, vp, sz, vp]),
         "fa_inverse_energy_grad": (i32, [V, V, vp, V, vp, sz, vp]),
@@ -488,6 +490,31 @@ def fa_affine_register(fixed, moving, params: RegParams, sync: bool = True):
     _check(lib.fa_affine_register(_vol(fixed, 1), _vol(moving, 1), ctypes.byref(p), _ptr(theta),
                                   _vol(u, 3), _ptr(loss), _ptr(ws), ws.numel(), _stream()))
     out = dict(theta=theta, u=u, loss=loss)
+    if sync:
+        torch.cuda.current_stream().synchronize()
+        out["final_loss"] = float(loss)
+    return out
+
+
+def fa_rigid_register(fixed, moving, params: RegParams, sync: bool = True):
+    """Rigid pre-registration (see fa.h).  Returns dict(rp=6 floats (w, t),
+    theta=12 floats, u=[3, d, h, w] of the last level, loss, final_loss)."""
+    D, H, W = fixed.shape[-3:]
+    p = params.to_c()
+    lib = load()
+    need = lib.fa_affine_workspace_size(D, H, W, ctypes.byref(p))
+    if need == 0:
+        raise FAError(FA_ERR_INVALID, lib.fa_last_error().decode())
+    ws = workspace(need, fixed.device)
+    s = params.scales[-1]
+    rp = torch.empty(6, device=fixed.device)
+    theta = torch.empty(12, device=fixed.device)
+    u = torch.empty((3, level_size(D, s), level_size(H, s), level_size(W, s)), device=fixed.device)
+    loss = torch.empty((), device=fixed.device)
+    _check(lib.fa_rigid_register(_vol(fixed, 1), _vol(moving, 1), ctypes.byref(p), _ptr(rp),
+                                 _ptr(theta), _vol(u, 3), _ptr(loss), _ptr(ws), ws.numel(),
+                                 _stream()))
+    out = dict(rp=rp, theta=theta, u=u, loss=loss)
     if sync:
         torch.cuda.current_stream().synchronize()
         out["final_loss"] = float(loss)

@@ -81,3 +81,33 @@ def test_deformable_from_affine_start(fa, orc, mode):
     zero = fa.fa_register(cuda(f), cuda(m), fa.RegParams(scales=(2, 1), iters=(0, 0), mode=mode),
                           u_init=cuda(u0))
     assert float((zero["u"].cpu() - torch.from_numpy(u0)).abs().max()) < 1e-5
+
+
+def rigid_pair(orc, shape=(26, 28, 30)):
+    f, _, _ = synth.blobs_pair(shape=shape, sigma=3.0, n_blobs=12, seed=1009)
+    th = orc.rigid_theta(np.array([0.04, -0.05, 0.03, 0.03, -0.04, 0.035]), shape)
+    m = orc.warp(f, orc.affine_field(th, shape), want_grad=False)
+    return f, m.astype(np.float32)
+
+
+@pytest.mark.parametrize("loss", ["mse", "lncc"])
+def test_rigid_register_against_oracle(fa, orc, loss):
+    f, m = rigid_pair(orc)
+    p = fa.RegParams(scales=(2, 1), iters=(60, 30), lr=3e-3, loss=loss)
+    out = fa.fa_rigid_register(cuda(f), cuda(m), p)
+    ref = orc.rigid_register(f, m, [2, 1], [60, 30], lr=3e-3, loss=loss,
+                             cc_eps=float(np.float32(1e-5)), beta1=float(np.float32(0.9)),
+                             beta2=float(np.float32(0.999)), adam_eps=float(np.float32(1e-8)))
+    assert abs(out["final_loss"] - ref["final_loss"]) < 1e-3
+    assert float((out["rp"].cpu().double() - torch.from_numpy(ref["rp"])).abs().max()) < 2e-3
+    assert float((out["theta"].cpu().double() - torch.from_numpy(ref["theta"])).abs().max()) < 2e-3
+    uref = orc.affine_field(ref["theta"], f.shape)
+    assert mean_disp(out["u"], uref) < 0.05
+
+
+def test_rigid_zero_iterations_is_identity(fa):
+    f = cuda(np.random.default_rng(0).random((9, 10, 11)))
+    out = fa.fa_rigid_register(f, f, fa.RegParams(scales=(1,), iters=(0,), lr=3e-3))
+    assert not out["rp"].any() and not out["u"].any()
+    assert torch.equal(out["theta"].cpu(), torch.tensor([1.0, 0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0]))
+
