@@ -88,6 +88,9 @@ def _L():
         lib.or_register_from.argtypes = [_dp, _dp, i, i, i, ctypes.c_void_p, _dp, _dp, _dp, _dp]
         lib.or_inverse_energy_grad.argtypes = [_dp, _dp, i, i, i, _dp, _dp]
         lib.or_inverse.argtypes = [_dp, i, i, i, ctypes.c_void_p, _dp, _dp]
+        lib.or_svf_loss_grad.argtypes = [_dp, _dp, i, i, i, ctypes.c_void_p, i, _dp, _dp, _dp,
+                                          _dp, _dp]
+        lib.or_register_svf.argtypes = [_dp, _dp, i, i, i, ctypes.c_void_p, i, _dp, _dp, _dp]
         lib.or_rodrigues.argtypes = [_dp, _dp, _dp]
         lib.or_rodrigues.restype = None
         lib.or_rigid_theta.argtypes = [_dp, i, i, i, _dp]
@@ -401,6 +404,37 @@ def affine_register(If, Im, scales, iters, lr=3e-3, window=5, loss="lncc", beta1
     return dict(theta=th, final_loss=fl.value)
 
 
+# ------------------------------------------------ stationary velocity field
+def svf_loss_grad(If, Im, v, steps, window=5, loss="lncc", cc_eps=1e-5, mi_bins=32,
+                  want_grad=True):
+    """(L(I_f, I_m o exp(v)), grad_v L, exp(v) - id) (reading R-svfreg)."""
+    If, Im, v = _f64(If), _f64(Im), _f64(v)
+    D, H, W = _dims(If)
+    p = _params([1], [0], window=window, loss=loss, cc_eps=cc_eps)
+    p.mi_bins = int(mi_bins)
+    rng = mi_range(If, Im)
+    L = ctypes.c_double()
+    gv = np.empty_like(v) if want_grad else None
+    u = np.empty_like(v)
+    _check(_L().or_svf_loss_grad(_p(If), _p(Im), D, H, W, ctypes.byref(p), int(steps), _p(rng),
+                                 _p(v), ctypes.byref(L), _p(gv), _p(u)), "svf_loss_grad")
+    return L.value, gv, u
+
+
+def register_svf(If, Im, scales, iters, steps=7, mi_bins=32, **kw):
+    """The Lie-algebra variant end to end (R-svfreg).  Returns dict(v, u, final_loss)."""
+    If, Im = _f64(If), _f64(Im)
+    D, H, W = _dims(If)
+    p = _params(scales, iters, **kw)
+    p.mi_bins = int(mi_bins)
+    fs = level_shape((D, H, W), scales[-1])
+    v, u = np.empty((3,) + fs), np.empty((3,) + fs)
+    fl = ctypes.c_double()
+    _check(_L().or_register_svf(_p(If), _p(Im), D, H, W, ctypes.byref(p), int(steps), _p(v),
+                                _p(u), ctypes.byref(fl)), "register_svf")
+    return dict(v=v, u=u, final_loss=fl.value)
+
+
 # ------------------------------------------------------------- rigid stage
 def rodrigues(w, want_grad=True):
     """R = exp([w]x) (3 x 3) and dR/dw_k (3 x 3 x 3) (reading R-rigid)."""
@@ -484,7 +518,7 @@ def _params(scales, iters, lr=0.5, sigma_grad=1.0, sigma_warp=0.5, window=5, los
         p.iters[k] = int(t)
     p.lr, p.sigma_grad, p.sigma_warp = float(lr), float(sigma_grad), float(sigma_warp)
     p.window = int(window)
-    p.loss = {"lncc": 0, "mse": 1}[loss]
+    p.loss = {"lncc": 0, "mse": 1, "mi": 2}[loss]
     p.beta1, p.beta2, p.adam_eps = float(beta1), float(beta2), float(adam_eps)
     p.cc_eps, p.c_lp = float(cc_eps), float(c_lp)
     p.use_jac = 1 if use_jac else 0

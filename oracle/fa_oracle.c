@@ -26,6 +26,9 @@
  *             inverse (or_register_symmetric).
  *   R-inv     post-hoc inverse: Algorithm 1's update on the
  *             inverse-consistency energy, exact Gateaux gradient (or_inverse).
+ *   R-svfreg  Lie-algebra variant: v optimised, phi = exp(v) by scaling and
+ *             squaring, exact adjoint of the squarings, additive update
+ *             (or_register_svf).
  *   R-rigid   rigid stage: rotation exp([w]x) (Rodrigues) and translation in
  *             the input grid's voxel coordinates about its centre, as the
  *             affine map S^-1 R S, t of reading R-aff (or_rigid_register).
@@ -884,6 +887,140 @@ int or_affine_register(const double *If, const double *Im, int D, int H, int W,
             or_affine_loss_grad(fl, ml, d, h, w, theta, p->loss, p->window, p->cc_eps, final_loss, NULL);
         free(fl); free(ml);
     }
+    return OR_OK;
+}
+
+/* ------------------------------------------------ stationary velocity field
+ * The Lie-algebra ("exp") variant the paper compares against (section
+ * "Euclidean gradient descent using the Lie algebra in shooting methods"): a
+ * velocity v is optimised, phi = exp(v) by scaling and squaring
+ * (or_svf_exp), and dL/dphi is pulled back into the algebra,
+ * grad_v L = (dphi/dv)^T grad_phi L.  Reading R-svfreg: the pull-back is the
+ * exact adjoint of the squarings; one squaring u' = u + u o (id + u) has the
+ * adjoint
+ *   gbar(x) = (I + grad u(x + u(x)))^T gbar'(x) + sum_y w_x(y + u(y)) gbar'(y)
+ * (w_x(p): trilinear weight of grid point x at p, zero outside), and
+ * u_0 = v / 2^M gives grad_v L = gbar_0 / 2^M.  The update is Algorithm 1's
+ * with the retraction replaced by the algebra's addition: Gaussian(sigma_grad)
+ * of grad_v L, Adam, step scaling, v <- v - eps_t d, Gaussian(sigma_warp) of
+ * v; v, m and nu are handed off between levels as u is. */
+
+/* gbar of one squaring of u from gbar' (gp); out must not alias gp. */
+static void svf_square_adjoint(const double *u, const double *gp, int D, int H, int W,
+                               double *out) {
+    size_t N = (size_t)D * H * W;
+    memset(out, 0, 3 * N * sizeof(double));
+    for (int z = 0; z < D; ++z)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                size_t i = IDX(z, y, x);
+                double pz = z + u[i], py = y + u[N + i], px = x + u[2 * N + i];
+                double G[3][3];
+                for (int c = 0; c < 3; ++c) trilinear(u + (size_t)c * N, D, H, W, pz, py, px, G[c]);
+                for (int a = 0; a < 3; ++a) {
+                    double acc = gp[(size_t)a * N + i];
+                    for (int j = 0; j < 3; ++j) acc += G[j][a] * gp[(size_t)j * N + i];
+                    out[(size_t)a * N + i] += acc;
+                }
+                if (isnan(pz) || isnan(py) || isnan(px) || pz < -1.0 || py < -1.0 || px < -1.0 ||
+                    pz >= (double)D || py >= (double)H || px >= (double)W)
+                    continue;
+                double fz = floor(pz), fy = floor(py), fx = floor(px);
+                int z0 = (int)fz, y0 = (int)fy, x0 = (int)fx;
+                double tz = pz - fz, ty = py - fy, tx = px - fx;
+                double wz[2] = {1.0 - tz, tz}, wy[2] = {1.0 - ty, ty}, wx[2] = {1.0 - tx, tx};
+                for (int a = 0; a < 2; ++a)
+                    for (int b = 0; b < 2; ++b)
+                        for (int e = 0; e < 2; ++e) {
+                            int zz = z0 + a, yy = y0 + b, xx = x0 + e;
+                            if (!in_grid(zz, yy, xx, D, H, W)) continue;
+                            double wt = wz[a] * wy[b] * wx[e];
+                            for (int c = 0; c < 3; ++c)
+                                out[(size_t)c * N + IDX(zz, yy, xx)] += wt * gp[(size_t)c * N + i];
+                        }
+            }
+}
+
+/* L(I_f, I_m o exp(v)) with loss p->loss (range: the MI ranges of the level),
+ * grad_v L (gv, nullable) and exp(v) - id (u_out, nullable). */
+int or_svf_loss_grad(const double *If, const double *Im, int D, int H, int W, const or_params *p,
+                     int steps, const double *range, const double *v, double *L, double *gv,
+                     double *u_out) {
+    if (D <= 0 || H <= 0 || W <= 0 || steps < 0 || steps > 16) return OR_EINVAL;
+    size_t N = (size_t)D * H * W;
+    double *us = malloc((size_t)(steps + 1) * 3 * N * sizeof(double));
+    double *J = malloc(N * sizeof(double)), *gJ = malloc(3 * N * sizeof(double)),
+           *dJ = malloc(N * sizeof(double)), *g = malloc(3 * N * sizeof(double)),
+           *g2 = malloc(3 * N * sizeof(double));
+    if (!us || !J || !gJ || !dJ || !g || !g2) return OR_EINVAL;
+    double sc = ldexp(1.0, -steps);
+    for (size_t i = 0; i < 3 * N; ++i) us[i] = v[i] * sc;
+    for (int k = 0; k < steps; ++k)
+        or_compose(us + (size_t)k * 3 * N, us + (size_t)k * 3 * N, us + (size_t)(k + 1) * 3 * N,
+                   D, H, W);
+    const double *uM = us + (size_t)steps * 3 * N;
+    or_warp(Im, D, H, W, uM, J, gJ);
+    int rc = loss_and_grad(p, If, J, D, H, W, range, L, gv ? dJ : NULL);
+    if (rc == OR_OK && gv) {
+        for (int c = 0; c < 3; ++c)
+            for (size_t i = 0; i < N; ++i) g[(size_t)c * N + i] = dJ[i] * gJ[(size_t)c * N + i];
+        for (int k = steps - 1; k >= 0; --k) {
+            svf_square_adjoint(us + (size_t)k * 3 * N, g, D, H, W, g2);
+            memcpy(g, g2, 3 * N * sizeof(double));
+        }
+        for (size_t i = 0; i < 3 * N; ++i) gv[i] = g[i] * sc;
+    }
+    if (u_out) memcpy(u_out, uM, 3 * N * sizeof(double));
+    free(us); free(J); free(gJ); free(dJ); free(g); free(g2);
+    return rc;
+}
+
+int or_register_svf(const double *If, const double *Im, int D, int H, int W, const or_params *p,
+                    int steps, double *v_out, double *u_out, double *final_loss) {
+    if (D <= 0 || H <= 0 || W <= 0 || !p || p->n_levels < 1 || p->n_levels > 8 || steps < 0 ||
+        steps > 16 || p->use_jac)
+        return OR_EINVAL;
+    int t = 0, pd = 0, ph = 0, pw = 0;
+    double *v = NULL, *m = NULL, *nu = NULL;
+    for (int l = 0; l < p->n_levels; ++l) {
+        int s = p->scales[l];
+        int d = or_level_size(D, s), h = or_level_size(H, s), w = or_level_size(W, s);
+        size_t N = (size_t)d * h * w;
+        double *fl = malloc(N * sizeof(double)), *ml = malloc(N * sizeof(double));
+        double *nv = calloc(3 * N, sizeof(double)), *nm = calloc(3 * N, sizeof(double)),
+               *nn = calloc(3 * N, sizeof(double));
+        double *g = malloc(3 * N * sizeof(double)), *dir = malloc(3 * N * sizeof(double));
+        if (!fl || !ml || !nv || !nm || !nn || !g || !dir) return OR_EINVAL;
+        or_downsample(If, D, H, W, s, fl);
+        or_downsample(Im, D, H, W, s, ml);
+        double range[4];
+        or_mi_range(fl, ml, N, range);
+        if (l > 0) {
+            or_upsample_field(v, pd, ph, pw, nv, d, h, w, 1);
+            or_upsample_field(m, pd, ph, pw, nm, d, h, w, -1);
+            or_upsample_field(nu, pd, ph, pw, nn, d, h, w, -2);
+        }
+        free(v); free(m); free(nu);
+        v = nv; m = nm; nu = nn;
+        pd = d; ph = h; pw = w;
+        for (int it = 0; it < p->iters[l]; ++it) {
+            double L;
+            int rc = or_svf_loss_grad(fl, ml, d, h, w, p, steps, range, v, &L, g, NULL);
+            if (rc != OR_OK) return rc;
+            or_gauss_smooth(g, g, 3, d, h, w, p->sigma_grad);
+            ++t;
+            or_adam(g, m, nu, dir, 3 * N, t, p->beta1, p->beta2, p->adam_eps);
+            or_step_scale(dir, dir, d, h, w, p->lr, p->c_lp);   /* dir <- -eps_t d */
+            for (size_t i = 0; i < 3 * N; ++i) g[i] = v[i] + dir[i];
+            or_gauss_smooth(g, v, 3, d, h, w, p->sigma_warp);
+        }
+        if (l == p->n_levels - 1) {
+            or_svf_loss_grad(fl, ml, d, h, w, p, steps, range, v, final_loss, NULL, u_out);
+            if (v_out) memcpy(v_out, v, 3 * N * sizeof(double));
+        }
+        free(fl); free(ml); free(g); free(dir);
+    }
+    free(v); free(m); free(nu);
     return OR_OK;
 }
 
