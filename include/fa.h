@@ -279,6 +279,37 @@ size_t fa_svf_exp_workspace_size(int32_t D, int32_t H, int32_t W);
 fa_status fa_svf_exp(const fa_vol *v, int32_t steps, fa_vol *out, void *ws, size_t ws_bytes,
                      void *stream);
 
+/* The Lie-algebra ("exp") registration the paper compares its method with
+ * (section "Euclidean gradient descent using the Lie algebra in shooting
+ * methods"; the exp curves of the grid study): a stationary velocity v is
+ * optimised, phi = exp(v) - id by fa_svf_exp's scaling and squaring with
+ * `steps` squarings (0..12), and dL/dphi (loss of p: LNCC, MSE or MI) is
+ * pulled back into the algebra by the exact adjoint of the squarings
+ *   gbar_k(x) = (I + grad u_k(x + u_k(x)))^T gbar_{k+1}(x)
+ *               + sum_y w_x(y + u_k(y)) gbar_{k+1}(y),   grad_v = gbar_0 / 2^M
+ * (w_x(p): trilinear weight of grid point x at p; the scatter accumulates in
+ * 64-bit fixed point, order-independent).  Each iteration: Gaussian
+ * (sigma_grad) of grad_v, Adam, the step rule eps_t = lr / (c_lp max|d|),
+ * the additive update v <- v - eps_t d, Gaussian (sigma_warp) of v; v, m, nu
+ * are handed off between levels like fa_register's u, m, nu.  p->use_jac must
+ * be 0; p->mode and p->graph are ignored (per-op kernels).  u_out (C=3,
+ * last level's grid) receives exp(v) - id, v_out_opt the velocity,
+ * final_loss_dev (may be NULL) the loss there.  Workspace of
+ * fa_register_svf_workspace_size bytes (0: invalid arguments).
+ *
+ * fa_svf_loss_grad evaluates L(I_f, I_m o exp(v)), grad_v L and optionally
+ * exp(v) - id on one grid (p gives the loss; its schedule is ignored);
+ * workspace of fa_register_svf_workspace_size for a one-level schedule at
+ * scale 1. */
+size_t fa_register_svf_workspace_size(int32_t D, int32_t H, int32_t W, const fa_params *p,
+                                      int32_t steps);
+fa_status fa_register_svf(const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
+                          int32_t steps, fa_vol *u_out, fa_vol *v_out_opt, float *final_loss_dev,
+                          void *ws, size_t ws_bytes, void *stream);
+fa_status fa_svf_loss_grad(const fa_vol *fixed, const fa_vol *moving, const fa_vol *v,
+                           const fa_params *p, int32_t steps, float *loss_dev, fa_vol *grad_v_out,
+                           fa_vol *u_out_opt, void *ws, size_t ws_bytes, void *stream);
+
 /* Steepest Eulerian descent direction (section "Exploiting the group
  * structure of diffeomorphisms"; Algorithm 1 with use_jac):
  * g_out = J(phi)^T g_in with J(phi) = I + grad u, i.e.

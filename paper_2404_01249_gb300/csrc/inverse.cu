@@ -113,20 +113,22 @@ __global__ void __launch_bounds__(256) k_inverse_terms(const float *__restrict__
     }
 }
 
-// scatter of 2 A / N to the corners of x + u(x), quantised relative to max |A|
-__global__ void __launch_bounds__(256) k_inverse_scatter(const float *__restrict__ u,
-                                                         const float *__restrict__ A,
-                                                         unsigned long long *acc, const WsHeader *h,
-                                                         int D, int H, int W) {
+// scatter of a (3 channels) to the corners of x + u(x), quantised relative
+// to max |a| (float bits in h->coef_max_bits[slot])
+__global__ void __launch_bounds__(256) k_field_scatter(const float *__restrict__ u,
+                                                       const float *__restrict__ A,
+                                                       unsigned long long *acc, const WsHeader *h,
+                                                       int slot, int D, int H, int W) {
     const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
     if (x >= W || y >= H) return;
     const long long N = (long long)D * H * W, i = ((long long)z * H + y) * W + x;
     const float uz = u[i], uy = u[N + i], ux = u[2 * N + i];
     const float LIM = 1048576.0f;
     if (!(fabsf(uz) < LIM && fabsf(uy) < LIM && fabsf(ux) < LIM)) return;
-    const int sh = fixed_shift(__uint_as_float(h->coef_max_bits[kSlotA]), kInvBits);
+    const int sh = fixed_shift(__uint_as_float(h->coef_max_bits[slot]), kInvBits);
     const float scale = pow2f(sh);
     const float a[3] = {A[i], A[N + i], A[2 * N + i]};
+    if (!(fabsf(a[0]) < 3.4e38f && fabsf(a[1]) < 3.4e38f && fabsf(a[2]) < 3.4e38f)) return;
     const float fz = floorf(uz), fy = floorf(uy), fx = floorf(ux);
     const int iz = z + (int)fz, iy = y + (int)fy, ix = x + (int)fx;
     const float tz = uz - fz, ty = uy - fy, tx = ux - fx;
@@ -155,12 +157,12 @@ __global__ void __launch_bounds__(256) k_inverse_scatter(const float *__restrict
     }
 }
 
-// g += 2 / N * (scattered A)
-__global__ void __launch_bounds__(256) k_inverse_finalize(const long long *__restrict__ acc,
-                                                          const WsHeader *h, float *g,
-                                                          long long n3, float inv_n) {
-    const int sh = fixed_shift(__uint_as_float(h->coef_max_bits[kSlotA]), kInvBits);
-    const float f = 2.0f * inv_n * pow2f(-sh);
+// g += factor * (scattered a)
+__global__ void __launch_bounds__(256) k_field_scatter_add(const long long *__restrict__ acc,
+                                                           const WsHeader *h, int slot, float *g,
+                                                           long long n3, float factor) {
+    const int sh = fixed_shift(__uint_as_float(h->coef_max_bits[slot]), kInvBits);
+    const float f = factor * pow2f(-sh);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n3;
          i += (long long)gridDim.x * blockDim.x)
         g[i] = fmaf(__ll2float_rn(acc[i]), f, g[i]);
@@ -194,14 +196,8 @@ cudaError_t inverse_gradient(InverseWs &q, const float *u, const float *w, Dims 
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if ((e = cudaMemsetAsync(q.acc, 0, sizeof(long long) * 3 * N, s)) != cudaSuccess) return e;
-    VoxGrid vg(d.D, d.H, d.W);
-    k_inverse_scatter<<<vg.grid, vg.block, 0, s>>>(u, q.A, (unsigned long long *)q.acc, q.h, d.D,
-                                                   d.H, d.W);
-    note_launch();
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_inverse_finalize<<<kEnergyBlocks, 256, 0, s>>>(q.acc, q.h, g, 3 * N, 1.0f / (float)N);
-    note_launch();
-    return cudaGetLastError();
+    if ((e = launch_field_scatter(u, q.A, q.acc, q.h, kSlotA, d, s)) != cudaSuccess) return e;
+    return launch_field_scatter_add(q.acc, q.h, kSlotA, 2.0f / (float)N, g, 3 * N, s);
 }
 
 fa_status check_inverse_params(const fa_params *p) {
@@ -231,6 +227,22 @@ size_t inverse_ws_bytes(Dims full, const fa_params *p) {
 }
 
 }  // namespace
+
+cudaError_t launch_field_scatter(const float *u, const float *a, long long *acc,
+                                 const WsHeader *h, int slot, Dims d, cudaStream_t s) {
+    VoxGrid vg(d.D, d.H, d.W);
+    k_field_scatter<<<vg.grid, vg.block, 0, s>>>(u, a, (unsigned long long *)acc, h, slot, d.D,
+                                                 d.H, d.W);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_scatter_add(const long long *acc, const WsHeader *h, int slot,
+                                     float factor, float *g, long long n3, cudaStream_t s) {
+    k_field_scatter_add<<<kEnergyBlocks, 256, 0, s>>>(acc, h, slot, g, n3, factor);
+    note_launch();
+    return cudaGetLastError();
+}
 
 }  // namespace fa
 

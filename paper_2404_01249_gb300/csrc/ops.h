@@ -52,6 +52,17 @@ cudaError_t launch_lncc_backward(const float *I, const float *J, const float *gr
 long long mse_partials_count(Dims d);  // floats of `partials` launch_mse needs
 cudaError_t launch_mse(const float *I, const float *J, const float *grad, Dims d, WsHeader *h,
                        float *partials, float *dJ, float *dI, float *g, cudaStream_t s);
+// ---- field adjoints (inverse.cu)
+// acc (3 channels, int64, zeroed by the caller) += a scattered through the
+// trilinear weights of the corners of x + u(x) (zero outside), each term
+// quantised to 2^-40 of max |a|, whose float bits the caller has put in
+// h->coef_max_bits[slot]: the sums do not depend on the order of the adds.
+cudaError_t launch_field_scatter(const float *u, const float *a, long long *acc,
+                                 const WsHeader *h, int slot, Dims d, cudaStream_t s);
+// g += factor * acc, converted back with the same scale.
+cudaError_t launch_field_scatter_add(const long long *acc, const WsHeader *h, int slot,
+                                     float factor, float *g, long long n3, cudaStream_t s);
+
 // ---- mutual information (mi.cu)
 struct MiBuffers {
     unsigned long long *hist;  // [B*B] joint histogram, 2^-26 fixed point

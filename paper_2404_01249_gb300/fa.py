@@ -45,7 +45,8 @@ EXPORTED = ["fa_params_default", "fa_status_str", "fa_last_error", "fa_warp",
             "fa_inverse_energy_grad", "fa_register_symmetric_workspace_size",
             "fa_register_symmetric", "fa_symmetric_loss_grad_workspace_size",
             "fa_symmetric_loss_grad", "fa_mi_workspace_size", "fa_mi_fwd_bwd",
-            "fa_rigid_register"]
+            "fa_rigid_register", "fa_register_svf_workspace_size", "fa_register_svf",
+            "fa_svf_loss_grad"]
 
 
 class FAError(RuntimeError):
@@ -130,6 +131,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "fa_affine_register": (i32, [V, V, P, vp, V, vp, vp, sz, vp]),
         "fa_affine_field": (i32, [vp, V, vp]),
         "fa_rigid_register": (i32, [V, V, P, vp, vp, V, vp, vp, sz, vp]),
+        "fa_register_svf_workspace_size": (sz, [i32, i32, i32, P, i32]),
+        "fa_register_svf": (i32, [V, V, P, i32, V, V, vp, vp, sz, vp]),
+        "fa_svf_loss_grad": (i32, [V, V, V, P, i32, vp, V, V, vp, sz, vp]),
         "fa_inverse_workspace_size": (sz, [i32, i32, i32, P]),
         "fa_inverse": (i32, [V, P, V, vp, vp, sz, vp]),
         "fa_inverse_energy_grad": (i32, [V, V, vp, V, vp, sz, vp]),
@@ -619,6 +623,50 @@ def fa_mi_fwd_bwd(fixed, warped, bins: int = 32, rng: Optional[torch.Tensor] = N
                              _ptr(rng) if rng is not None else None, _ptr(loss), _vol(dJ, 1),
                              _ptr(ws), ws.numel(), _stream()))
     return dict(loss=loss, dJ=dJ)
+
+
+def fa_register_svf(fixed, moving, params: RegParams, steps: int = 7, sync: bool = True):
+    """The Lie-algebra (exp) registration (see fa.h).  Returns dict(u=exp(v) -
+    id and v on the last level's grid, loss, final_loss)."""
+    D, H, W = fixed.shape[-3:]
+    p = params.to_c()
+    p.storage = _DTYPES.get(fixed.dtype, FA_F32)
+    lib = load()
+    need = lib.fa_register_svf_workspace_size(D, H, W, ctypes.byref(p), int(steps))
+    if need == 0:
+        raise FAError(FA_ERR_INVALID, lib.fa_last_error().decode())
+    ws = workspace(need, fixed.device)
+    s = params.scales[-1]
+    shape = (3, level_size(D, s), level_size(H, s), level_size(W, s))
+    u, v = torch.empty(shape, device=fixed.device), torch.empty(shape, device=fixed.device)
+    loss = torch.empty((), device=fixed.device)
+    _check(lib.fa_register_svf(_vol(fixed, 1, half_ok=True), _vol(moving, 1, half_ok=True),
+                               ctypes.byref(p), int(steps), _vol(u, 3), _vol(v, 3), _ptr(loss),
+                               _ptr(ws), ws.numel(), _stream()))
+    out = dict(u=u, v=v, loss=loss)
+    if sync:
+        torch.cuda.current_stream().synchronize()
+        out["final_loss"] = float(loss)
+    return out
+
+
+def fa_svf_loss_grad(fixed, moving, v, steps: int, params: Optional[RegParams] = None):
+    """(L(I_f, I_m o exp(v)), grad_v L, exp(v) - id) on one grid."""
+    D, H, W = fixed.shape[-3:]
+    P = params or RegParams(scales=(1,), iters=(0,))
+    p = P.to_c()
+    p.n_levels, p.scales[0], p.iters[0] = 1, 1, 0
+    lib = load()
+    need = lib.fa_register_svf_workspace_size(D, H, W, ctypes.byref(p), int(steps))
+    if need == 0:
+        raise FAError(FA_ERR_INVALID, lib.fa_last_error().decode())
+    ws = workspace(need, fixed.device)
+    g, u = torch.empty_like(v), torch.empty_like(v)
+    loss = torch.empty((), device=fixed.device)
+    _check(lib.fa_svf_loss_grad(_vol(fixed, 1), _vol(moving, 1), _vol(v, 3), ctypes.byref(p),
+                                int(steps), _ptr(loss), _vol(g, 3), _vol(u, 3), _ptr(ws),
+                                ws.numel(), _stream()))
+    return loss, g, u
 
 
 def fa_launch_count() -> int:
