@@ -437,6 +437,158 @@ def run_batched(args):
     return 0
 
 
+# ------------------------------------------------- the other paper workloads
+# Whole-path algorithmic bytes per voxel-iteration of each variant: the state
+# every iteration must read and write once (FP32), as PATH_BYTES for the main
+# path.
+VARIANT_BYTES = {
+    "symmetric": 8 + 2 * 72,  # I_f, I_m; u, m, nu of both maps read and written
+    "inverse": 12 + 72,       # u read; w, m, nu read and written
+    "svf": PATH_BYTES,        # I_f, I_m; v, m, nu
+    "mi": PATH_BYTES,
+    "use_jac": PATH_BYTES,
+    "affine": 8,              # I_f, I_m (12 parameters)
+    "rigid": 8,
+}
+INVERSE_SCHEDULE = dict(scales=(4, 2, 1), iters=(100, 50, 25))
+SYM_INVERSE_SCHEDULE = dict(scales=(2, 1), iters=(50, 25))
+SVF_STEPS = 7
+
+
+def run_variant(args):
+    """One of the paper's other workloads on the brain-shaped pair: symmetric
+    registration (with its post-hoc inverse), the post-hoc inverse of the
+    pair's generating displacement, the SVF (exp) variant, the MI loss, the
+    use_jac direction, and the affine and rigid stages.  A step is one whole
+    call; the same timing rules as the main path (L2 flushed before every
+    step, CUDA events, clocks sampled); the oracle is timed on one
+    finest-level iteration of the same workload."""
+    import torch
+    from paper_2404_01249_gb300 import build, fa, synth
+    rank, world, local = rank_env()
+    if world > 1:
+        raise SystemExit("--workload runs on one GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    fa.load()
+    w = args.workload
+    shape = WORKLOAD["shape"]
+    f, m, psi = synth.voronoi_pair(shape=shape, seed=1000)
+    fixed, moving = torch.from_numpy(f).to(dev), torch.from_numpy(m).to(dev)
+    base = dict(scales=WORKLOAD["scales"], iters=WORKLOAD["iters"], window=WORKLOAD["window"],
+                lr=WORKLOAD["lr"], sigma_grad=WORKLOAD["sigma_grad"],
+                sigma_warp=WORKLOAD["sigma_warp"], cc_eps=WORKLOAD["cc_eps"])
+    cfg = {"workload": f"{w}_voronoi_brain_160x192x224", "shape": list(shape)}
+    vi = voxel_iters(shape, WORKLOAD["scales"], WORKLOAD["iters"])
+    if w == "symmetric":
+        P, Pi = fa.RegParams(**base), fa.RegParams(**SYM_INVERSE_SCHEDULE)
+        call = lambda: fa.fa_register_symmetric(fixed, moving, P, Pi, sync=False)["loss"]  # noqa
+        cfg.update(base, inverse=SYM_INVERSE_SCHEDULE, loss="lncc")
+    elif w == "inverse":
+        u = torch.from_numpy(np.ascontiguousarray(psi, dtype=np.float32)).to(dev)
+        sched = (INVERSE_SCHEDULE if args.scales is None and args.iters is None else
+                 dict(scales=WORKLOAD["scales"], iters=WORKLOAD["iters"]))
+        P = fa.RegParams(**sched)
+        call = lambda: fa.fa_inverse(u, P, sync=False)["energy"]  # noqa
+        vi = voxel_iters(shape, sched["scales"], sched["iters"])
+        cfg.update(sched, field="the pair's generating displacement exp(v)")
+    elif w == "svf":
+        P = fa.RegParams(**base)
+        call = lambda: fa.fa_register_svf(fixed, moving, P, steps=SVF_STEPS, sync=False)["loss"]  # noqa
+        cfg.update(base, squarings=SVF_STEPS, loss="lncc")
+    elif w in ("mi", "use_jac"):
+        P = fa.RegParams(**base, loss="mi" if w == "mi" else "lncc", use_jac=(w == "use_jac"))
+        ws = fa.workspace(fa.fa_register_workspace_size(shape, P), dev)
+        if not args.no_autotune:
+            fa.fa_autotune(shape, P, ws=ws)
+        uo = torch.empty((3,) + shape, device=dev)
+        lo = torch.empty((), device=dev)
+        call = lambda: fa.fa_register(fixed, moving, P, ws=ws, sync=False, u_out=uo, loss_out=lo)["loss"]  # noqa
+        cfg.update(base, loss=P.loss, use_jac=P.use_jac, mi_bins=P.mi_bins, mode="fused")
+    else:  # affine, rigid
+        lin = dict(scales=WORKLOAD["scales"], iters=WORKLOAD["iters"], lr=3e-3,
+                   window=WORKLOAD["window"], cc_eps=WORKLOAD["cc_eps"])
+        P = fa.RegParams(**lin)
+        fn = fa.fa_affine_register if w == "affine" else fa.fa_rigid_register
+        call = lambda: fn(fixed, moving, P, sync=False)["loss"]  # noqa
+        cfg.update(lin, loss="lncc")
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(None)
+    clocks.start()
+    launches0 = fa.fa_launch_count()
+    last = None
+    for k in range(args.steps):
+        flush.zero_()
+        e0[k].record(stream)
+        last = call()
+        e1[k].record(stream)
+    torch.cuda.synchronize()
+    launches = fa.fa_launch_count() - launches0
+    clk = clocks.stop()
+    total_ms = float(sum(a.elapsed_time(b) for a, b in zip(e0, e1)))
+    value = vi * args.steps / (total_ms / 1e3)
+    peak, peak_kind = measured_peak()
+    achieved = VARIANT_BYTES[w] * vi * args.steps / (total_ms / 1e3) / 1e9
+    cfg["l2"] = "flushed between steps (256 MiB write)"
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": cfg,
+            "roofline": {"bound": "hbm", "kernel": "whole_path", "achieved": achieved,
+                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "bytes_per_voxel_iter": VARIANT_BYTES[w]},
+            "clocks": clk, "gpu_launches": int(launches), "final_value": float(last),
+            "e2e": None}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = variant_oracle_sample(w, f, m, psi)
+    print(json.dumps(line))
+    return 0
+
+
+def variant_oracle_sample(w, f, m, psi):
+    """The oracle on one finest-level iteration of the workload (plus its final
+    evaluation), as voxel-iterations per second."""
+    threads = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(threads))
+    import oracle
+    oracle.build()
+    kw = dict(lr=WORKLOAD["lr"], sigma_grad=WORKLOAD["sigma_grad"],
+              sigma_warp=WORKLOAD["sigma_warp"])
+    t0 = time.perf_counter()
+    if w == "symmetric":
+        oracle.register_symmetric(f, m, [1], [1], inv_scales=(1,), inv_iters=(1,),
+                                  window=WORKLOAD["window"], cc_eps=WORKLOAD["cc_eps"], **kw)
+    elif w == "inverse":
+        oracle.inverse(psi, [1], [1], **kw)
+    elif w == "svf":
+        oracle.register_svf(f, m, [1], [1], steps=SVF_STEPS, window=WORKLOAD["window"],
+                            cc_eps=WORKLOAD["cc_eps"], **kw)
+    elif w in ("mi", "use_jac"):
+        oracle.register(f, m, [1], [1], loss="mi" if w == "mi" else "lncc",
+                        use_jac=(w == "use_jac"), window=WORKLOAD["window"],
+                        cc_eps=WORKLOAD["cc_eps"], **kw)
+    elif w == "affine":
+        oracle.affine_register(f, m, [1], [1], lr=3e-3, window=WORKLOAD["window"],
+                               cc_eps=WORKLOAD["cc_eps"])
+    else:
+        oracle.rigid_register(f, m, [1], [1], lr=3e-3, window=WORKLOAD["window"],
+                              cc_eps=WORKLOAD["cc_eps"])
+    dt = time.perf_counter() - t0
+    n = int(np.prod(f.shape))
+    return {"value": n / dt, "unit": METRIC, "cores": int(os.environ["OMP_NUM_THREADS"]),
+            "kind": "oracle",
+            "sample": "1 finest-level iteration (scale 1, 160x192x224) of the same workload "
+                      "plus the oracle's final evaluation"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -451,6 +603,10 @@ def main():
     ap.add_argument("--batched", type=int, default=0, metavar="P",
                     help="time fa_register_batched on P uneven pairs x 9 parameter sets instead")
     ap.add_argument("--concurrency", type=int, default=8, help="streams of --batched")
+    ap.add_argument("--workload", default="brain",
+                    choices=["brain", "symmetric", "inverse", "svf", "mi", "use_jac", "affine",
+                             "rigid"],
+                    help="one of the paper's other workloads on the brain-shaped pair")
     ap.add_argument("--scales", type=int, nargs="+", default=None,
                     help="override the pyramid scales (profiling runs; changes the workload)")
     ap.add_argument("--iters", type=int, nargs="+", default=None,
@@ -468,6 +624,8 @@ def main():
         return run_reference(args)
     if args.batched:
         return run_batched(args)
+    if args.workload != "brain":
+        return run_variant(args)
     return run_gpu(args)
 
 

@@ -187,7 +187,7 @@ fa_status fa_mse_fwd_bwd(const fa_vol *fixed, const fa_vol *warped, float *loss_
  * of `fixed` and of `warped` with 0 included (fa_register takes the moving
  * image's range with 0 included, since samples outside the grid are 0).
  * loss_dev (device float) receives L; dL_dwarped_opt (C=1) dL/dJ (either may
- * be NULL).  The joint histogram is accumulated in 2^-26 fixed point with
+ * be NULL).  The joint histogram is accumulated in 2^-32 fixed point with
  * integer atomics: the result does not depend on thread order.  FA_F32,
  * same grid; workspace of fa_mi_workspace_size(bins) bytes (0: bins out of
  * range). */

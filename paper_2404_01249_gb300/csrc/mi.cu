@@ -9,8 +9,8 @@
 //   L = -MI = -sum P log(P / (p_f p_m)),
 //   dL/dJ(x) = -(1/N) (B - 3) / (hi_m - lo_m)
 //              sum_{a,b} log(P / (p_f p_m)) beta3(xi_f - a) beta3'(xi_m - b).
-// The joint histogram is accumulated in 2^-26 fixed point with integer
-// atomics (warp-aggregated per bin), so it does not depend on thread order.
+// The joint histogram is accumulated in 2^-32 fixed point with integer
+// atomics, so it does not depend on thread order.
 #include "ops.h"
 #include "validate.h"
 
@@ -18,7 +18,7 @@ namespace fa {
 
 namespace {
 
-constexpr int kMiBits = 26;  // |weight product| <= 4/9: 32 lanes sum below 2^30
+constexpr int kMiBits = 32;  // fixed-point scale of the histogram terms (< 2^31 each)
 
 __device__ __forceinline__ unsigned fkey(float f) {  // order-preserving float key
     const unsigned u = __float_as_uint(f);
@@ -105,61 +105,63 @@ __global__ void __launch_bounds__(256) k_mi_range(const float *__restrict__ If,
     }
 }
 
-// Joint histogram: per-block shared histogram, warp-aggregated per bin.
-__global__ void __launch_bounds__(256) k_mi_hist(const float *__restrict__ I,
-                                                 const float *__restrict__ J, long long N, int B,
-                                                 const unsigned *__restrict__ keys,
-                                                 unsigned long long *ghist, WsHeader *h) {
-    extern __shared__ unsigned long long sh[];
-    const int nb = B * B, lane = threadIdx.x & 31;
-    for (int k = threadIdx.x; k < nb; k += blockDim.x) sh[k] = 0ull;
+// Joint histogram.  Each weight product is quantised to 2^-32 (q < 2^31) and
+// added as two halves, q mod 2^16 and q / 2^16, with 32-bit shared atomics
+// into one of NH private copies (NH = 4 when they fit, so the block's warps
+// never share one; 1 otherwise).  A copy takes at most 4 warps x 32 lanes x
+// kHistWarpIters voxels, so each half-sum stays below 2^13 * 2^16 = 2^29;
+// the block recombines the halves exactly in 64 bits and adds its non-zero
+// bins to the global histogram.
+constexpr int kHistThreads = 128, kHistWarpIters = 64;
+
+__global__ void __launch_bounds__(kHistThreads) k_mi_hist(const float *__restrict__ I,
+                                                          const float *__restrict__ J, long long N,
+                                                          int B, int NH,
+                                                          const unsigned *__restrict__ keys,
+                                                          unsigned long long *ghist, WsHeader *h) {
+    extern __shared__ unsigned shu[];  // [NH][2][B*B]: low and high halves
+    const int nb = B * B, warp = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < 2 * nb * NH; k += blockDim.x) shu[k] = 0u;
     __syncthreads();
+    unsigned *lo_h = shu + (warp % NH) * 2 * nb, *hi_h = lo_h + nb;
     const MiMap mf = mi_map(keys, 0, B), mm = mi_map(keys, 1, B);
     const float scale = pow2f(kMiBits);
     bool bad = false;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < N;
-         base += stride) {  // warp-uniform loop
-        const long long i = base + lane;
-        bool live = i < N;
-        float xf = 1.0f, xm = 1.0f;
-        if (live) {
-            const float a = I[i], b = J[i];
-            if (fabsf(a) <= 3.4e38f && fabsf(b) <= 3.4e38f) {
-                xf = mf.coord(a);
-                xm = mm.coord(b);
-            } else {
-                bad = true;
-                live = false;
-            }
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        const float a = I[i], b = J[i];
+        if (!(fabsf(a) <= 3.4e38f && fabsf(b) <= 3.4e38f)) {
+            bad = true;
+            continue;
         }
+        const float xf = mf.coord(a), xm = mm.coord(b);
         const float ff = floorf(xf), fm = floorf(xm);
         float wf[4], wm[4];
         bspline_w(xf - ff, wf);
         bspline_w(xm - fm, wm);
         const int a0 = (int)ff - 1, b0 = (int)fm - 1;
 #pragma unroll
-        for (int p = 0; p < 4; ++p)
+        for (int p = 0; p < 4; ++p) {
+            if (a0 + p >= B) continue;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const unsigned v = (unsigned)quantize(wf[p] * wm[q], scale);
-                const bool use = live && v != 0u && a0 + p < B && b0 + q < B;
-                const unsigned key = use ? (unsigned)((a0 + p) * B + b0 + q) : 0xffffffffu;
-                unsigned todo = __ballot_sync(0xffffffffu, use);
-                while (todo) {
-                    const int src = __ffs(todo) - 1;
-                    const unsigned k0 = __shfl_sync(0xffffffffu, key, src);
-                    const bool mine = use && key == k0;
-                    const unsigned sum = __reduce_add_sync(0xffffffffu, mine ? v : 0u);
-                    if (lane == src) atomicAdd(sh + k0, (unsigned long long)sum);
-                    todo &= ~__ballot_sync(0xffffffffu, mine);
-                }
+                if (v == 0u || b0 + q >= B) continue;
+                const int k = (a0 + p) * B + b0 + q;
+                atomicAdd(lo_h + k, v & 0xffffu);
+                if (v >> 16) atomicAdd(hi_h + k, v >> 16);
             }
+        }
     }
     if (bad) status_set(&h->status, ST_NONFINITE);
     __syncthreads();
-    for (int k = threadIdx.x; k < nb; k += blockDim.x)
-        if (sh[k]) atomicAdd(ghist + k, sh[k]);
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+        unsigned long long t = 0ull;
+        for (int c = 0; c < NH; ++c)
+            t += (unsigned long long)shu[c * 2 * nb + k] +
+                 ((unsigned long long)shu[c * 2 * nb + nb + k] << 16);
+        if (t) atomicAdd(ghist + k, t);
+    }
 }
 
 // P, marginals, MI (FP64, fixed order) and the table log(P / (p_f p_m)).
@@ -282,8 +284,14 @@ cudaError_t launch_mi(const float *I, const float *J, const float *grad, Dims d,
     const int nb = bins * bins;
     cudaError_t e = cudaMemsetAsync(b.hist, 0, sizeof(unsigned long long) * nb, s);
     if (e != cudaSuccess) return e;
-    const size_t hist_smem = sizeof(unsigned long long) * nb;
-    k_mi_hist<<<grid_blocks(N), 256, hist_smem, s>>>(I, J, N, bins, b.range, b.hist, h);
+    // four private copies when they fit in 48 KB (bins <= 38), else one
+    const int nh = 2 * nb * 4 * (int)sizeof(unsigned) <= 49152 ? 4 : 1;
+    const size_t hist_smem = sizeof(unsigned) * 2 * nb * nh;
+    long long hb = (N + (long long)kHistThreads * kHistWarpIters - 1) /
+                   ((long long)kHistThreads * kHistWarpIters);
+    hb = hb < 152 * 4 ? 152 * 4 : hb;
+    k_mi_hist<<<(unsigned)hb, kHistThreads, hist_smem, s>>>(I, J, N, bins, nh, b.range, b.hist,
+                                                           h);
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const size_t tab_smem = sizeof(double) * (nb + 2 * bins + 1024);
