@@ -503,6 +503,14 @@ fa_status fa_symmetric_loss_grad(const fa_vol *fixed, const fa_vol *moving, cons
  * (FA_OK, FA_ERR_NONFINITE or FA_ERR_TIMEOUT). */
 fa_status fa_ws_status(const void *ws, void *stream);
 
+/* Failure-detection self-test (no counterpart in the paper): one kernel
+ * waits, with the bounded mbarrier wait the fused kernels use for their tile
+ * copies, on a barrier that nothing completes, gives up after limit_cycles
+ * SM cycles (0..2^31) and records FA_ERR_TIMEOUT in the workspace's status
+ * word (read it with fa_ws_status); nothing faults or hangs and the context
+ * stays usable.  ws: at least 256 bytes of device memory. */
+fa_status fa_selftest_wait_timeout(void *ws, size_t ws_bytes, int64_t limit_cycles, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Kernel timing for benchmarks.  When `timer` is not NULL, fa_register_timed
  * records a pair of CUDA events (caller-created cudaEvent_t handles) around

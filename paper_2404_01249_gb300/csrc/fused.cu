@@ -103,12 +103,14 @@ __device__ __forceinline__ bool mbar_try(unsigned long long *b, unsigned parity)
     return ok != 0;
 }
 // Waits for the phase of parity `parity` to complete; gives up after about
-// 2^28 SM cycles (0.13 s at 2 GHz; a tile copy takes microseconds).
-__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity) {
+// `limit` SM cycles (default 2^28: 0.13 s at 2 GHz; a tile copy takes
+// microseconds).
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity,
+                                          long long limit = 1ll << 28) {
     if (mbar_try(b, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try(b, parity))
-        if (clock64() - t0 > (1ll << 28)) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 // One tile copy of a rank-4 map ([C][D][H][W]) into shared memory.
@@ -1868,4 +1870,32 @@ cudaError_t fused_lncc_forward_only(const float *If, const FusedBuffers &fb, Dim
     return dispatch_k1(If, fb.J, fb.sI, fb.varI, nullptr, h, d, window, cc_eps, false, s);
 }
 
+// Self-test of the bounded wait: one thread waits on an mbarrier that no
+// thread arrives at, gives up after `limit` cycles and records ST_TIMEOUT,
+// exactly as a fused kernel does when a tile copy never lands.
+__global__ void k_wait_selftest(WsHeader *h, long long limit) {
+    __shared__ unsigned long long bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar);
+    mbar_init_fence();
+    if (!mbar_wait(&bar, 0u, limit)) status_set(&h->status, ST_TIMEOUT);
+}
+
 }  // namespace fa
+
+extern "C" fa_status fa_selftest_wait_timeout(void *ws, size_t ws_bytes, int64_t limit_cycles,
+                                              void *stream) {
+    using namespace fa;
+    clear_error();
+    FA_TRY(check_ws(ws, ws_bytes, sizeof(WsHeader), "fa_selftest_wait_timeout"));
+    if (limit_cycles < 0 || limit_cycles > (1ll << 31)) {
+        set_error("fa_selftest_wait_timeout: limit_cycles must be in 0..2^31");
+        return FA_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    FA_CUDA_TRY(launch_header_reset((WsHeader *)ws, s));
+    k_wait_selftest<<<1, 32, 0, s>>>((WsHeader *)ws, (long long)limit_cycles);
+    note_launch();
+    FA_CUDA_TRY(cudaGetLastError());
+    return FA_OK;
+}

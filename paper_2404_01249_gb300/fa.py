@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_PKG, "_build", "libfa.so")
 
 FA_OK = 0
 FA_ERR_INVALID = 1
+FA_ERR_NONFINITE, FA_ERR_TIMEOUT = 5, 6
 STATUS_NAMES = {0: "FA_OK", 1: "FA_ERR_INVALID", 2: "FA_ERR_SHAPE", 3: "FA_ERR_DTYPE",
                 4: "FA_ERR_CUDA", 5: "FA_ERR_NONFINITE", 6: "FA_ERR_TIMEOUT",
                 7: "FA_ERR_UNSUPPORTED", 8: "FA_ERR_WORKSPACE"}
@@ -46,7 +47,7 @@ EXPORTED = ["fa_params_default", "fa_status_str", "fa_last_error", "fa_warp",
             "fa_register_symmetric", "fa_symmetric_loss_grad_workspace_size",
             "fa_symmetric_loss_grad", "fa_mi_workspace_size", "fa_mi_fwd_bwd",
             "fa_rigid_register", "fa_register_svf_workspace_size", "fa_register_svf",
-            "fa_svf_loss_grad"]
+            "fa_svf_loss_grad", "fa_selftest_wait_timeout"]
 
 
 class FAError(RuntimeError):
@@ -134,6 +135,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "fa_register_svf_workspace_size": (sz, [i32, i32, i32, P, i32]),
         "fa_register_svf": (i32, [V, V, P, i32, V, V, vp, vp, sz, vp]),
         "fa_svf_loss_grad": (i32, [V, V, V, P, i32, vp, V, V, vp, sz, vp]),
+        "fa_selftest_wait_timeout": (i32, [vp, sz, ctypes.c_int64, vp]),
         "fa_inverse_workspace_size": (sz, [i32, i32, i32, P]),
         "fa_inverse": (i32, [V, P, V, vp, vp, sz, vp]),
         "fa_inverse_energy_grad": (i32, [V, V, vp, V, vp, sz, vp]),
@@ -667,6 +669,15 @@ def fa_svf_loss_grad(fixed, moving, v, steps: int, params: Optional[RegParams] =
                                 int(steps), _ptr(loss), _vol(g, 3), _vol(u, 3), _ptr(ws),
                                 ws.numel(), _stream()))
     return loss, g, u
+
+
+def fa_selftest_wait_timeout(limit_cycles: int = 1 << 20):
+    """Runs the bounded-wait self-test (see fa.h) and returns the status its
+    workspace reports (FA_ERR_TIMEOUT expected)."""
+    lib = load()
+    ws = workspace(256, torch.device("cuda", torch.cuda.current_device()))
+    _check(lib.fa_selftest_wait_timeout(_ptr(ws), ws.numel(), int(limit_cycles), _stream()))
+    return int(lib.fa_ws_status(_ptr(ws), _stream()))
 
 
 def fa_launch_count() -> int:
