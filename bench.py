@@ -381,12 +381,16 @@ def run_gpu(args):
 
 # ------------------------------------------------------- batched throughput
 def run_batched(args):
-    """Throughput of many independent registrations in one fa_register_batched
-    call: `--batched P` pairs of uneven brain-like grids (each axis uniform
-    in [96,192] x [112,224] x [96,192]) x 9 parameter sets (lr {0.25, 0.5, 1}
-    x sigma_grad {0.5, 1, 2}), scales {4,2,1} x iterations {200,100,50}.
-    A step is the whole batch.  Also times the same batch with one stream
-    (concurrency 1) once, for comparison."""
+    """Throughput of many independent registrations: `--batched P` pairs of
+    uneven brain-like grids (each axis uniform in [96,192] x [112,224] x
+    [96,192]) x 9 parameter sets (lr {0.25, 0.5, 1} x sigma_grad {0.5, 1, 2}),
+    scales {4,2,1} x iterations {200,100,50}.  A step is the whole batch.
+    `--schedule` picks the timed form: lockstep (every iteration one launch
+    per fused kernel over all jobs of a wave, fa_register_batched_lockstep),
+    streams (fused registrations on `--concurrency` forked streams,
+    fa_register_batched) or plain (the per-op schedule on forked streams).
+    The other two forms are timed once each on the same batch for
+    comparison, with the mean |final loss difference| against the timed form."""
     import torch
     from paper_2404_01249_gb300 import build, fa, synth
     torch.cuda.set_device(0)
@@ -397,45 +401,72 @@ def run_batched(args):
     pairs = [synth.voronoi_pair(shape=sh, seed=1000 + i) for i, sh in enumerate(shapes)]
     fixed = [torch.from_numpy(p[0]).to(dev) for p in pairs]
     moving = [torch.from_numpy(p[1]).to(dev) for p in pairs]
-    cfgs = [fa.RegParams(scales=WORKLOAD["scales"], iters=WORKLOAD["iters"], lr=lr, sigma_grad=sg,
-                         sigma_warp=WORKLOAD["sigma_warp"], window=WORKLOAD["window"])
-            for lr in (0.25, 0.5, 1.0) for sg in (0.5, 1.0, 2.0)]
-    vi = sum(voxel_iters(sh, WORKLOAD["scales"], WORKLOAD["iters"]) for sh in shapes) * len(cfgs)
-    n_jobs = len(shapes) * len(cfgs)
 
-    def step(conc):
-        return fa.fa_register_batched(fixed, moving, cfgs, concurrency=conc, sync=False)
+    def cfgs(mode):
+        return [fa.RegParams(scales=WORKLOAD["scales"], iters=WORKLOAD["iters"], lr=lr,
+                             sigma_grad=sg, sigma_warp=WORKLOAD["sigma_warp"],
+                             window=WORKLOAD["window"], mode=mode)
+                for lr in (0.25, 0.5, 1.0) for sg in (0.5, 1.0, 2.0)]
 
-    for _ in range(args.warmup):
-        step(args.concurrency)
-    torch.cuda.synchronize()
+    n_cfg = len(cfgs("fused"))
+    vi = sum(voxel_iters(sh, WORKLOAD["scales"], WORKLOAD["iters"]) for sh in shapes) * n_cfg
+    n_jobs = len(shapes) * n_cfg
+    waves = -(-n_jobs // 64)
+    wave = -(-n_jobs // waves)  # balanced waves of at most 64 jobs
+    forms = {
+        "lockstep": lambda: fa.fa_register_batched_lockstep(fixed, moving, cfgs("fused"),
+                                                            jobs_per_wave=wave, sync=False),
+        "streams": lambda: fa.fa_register_batched(fixed, moving, cfgs("fused"),
+                                                  concurrency=args.concurrency, sync=False),
+        "plain": lambda: fa.fa_register_batched(fixed, moving, cfgs("plain"),
+                                                concurrency=args.concurrency, sync=False),
+    }
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(form, steps):
+        e0.record(stream)
+        out = None
+        for _ in range(steps):
+            out = forms[form]()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, out
+
+    for _ in range(args.warmup):
+        forms[args.schedule]()
+    torch.cuda.synchronize()
+    n0 = fa.fa_launch_count()
     clocks = ClockSampler(None)
     clocks.start()
-    e0.record(stream)
-    for _ in range(args.steps):
-        step(args.concurrency)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms, out = timed(args.schedule, args.steps)
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    e0.record(stream)
-    step(1)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms1 = e0.elapsed_time(e1)
+    launches = (fa.fa_launch_count() - n0) // max(args.steps, 1)
+    loss = torch.stack([r["loss"] for r in out]).cpu().numpy()
+    others = {}
+    for form in forms:
+        if form == args.schedule:
+            continue
+        forms[form]()  # warm (records its graphs)
+        torch.cuda.synchronize()
+        ms_o, out_o = timed(form, 1)
+        lo = torch.stack([r["loss"] for r in out_o]).cpu().numpy()
+        others[form] = {"ms_per_step": ms_o, "speedup_of_timed_form": ms_o / ms,
+                        "mean_abs_final_loss_diff": float(np.abs(lo - loss).mean()),
+                        "max_abs_final_loss_diff": float(np.abs(lo - loss).max())}
     line = {"metric": METRIC, "value": vi / (ms / 1e3), "unit": METRIC, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": f"uneven_brain_batch_{len(shapes)}x{len(cfgs)}",
+            "config": {"workload": f"uneven_brain_batch_{len(shapes)}x{n_cfg}",
+                       "schedule": args.schedule, "jobs_per_wave": wave,
+                       "concurrency": args.concurrency,
                        "shapes": [list(x) for x in shapes], "scales": list(WORKLOAD["scales"]),
                        "iters": list(WORKLOAD["iters"]), "lr": [0.25, 0.5, 1.0],
-                       "sigma_grad": [0.5, 1.0, 2.0], "concurrency": args.concurrency,
+                       "sigma_grad": [0.5, 1.0, 2.0],
                        "l2": "inputs of the batch exceed L2"},
-            "registrations_per_s": n_jobs / (ms / 1e3),
-            "ms_per_step_concurrency_1": ms1, "clocks": clk}
+            "registrations_per_s": n_jobs / (ms / 1e3), "s_per_pair": ms / 1e3 / n_jobs,
+            "gpu_launches": int(launches), "other_schedules": others, "clocks": clk}
     print(json.dumps(line))
     return 0
 
@@ -605,7 +636,10 @@ def main():
                     help="use the default tile choices instead of fa_autotune's")
     ap.add_argument("--batched", type=int, default=0, metavar="P",
                     help="time fa_register_batched on P uneven pairs x 9 parameter sets instead")
-    ap.add_argument("--concurrency", type=int, default=8, help="streams of --batched")
+    ap.add_argument("--concurrency", type=int, default=8,
+                    help="streams of --batched's streams and plain schedules")
+    ap.add_argument("--schedule", default="lockstep", choices=["lockstep", "streams", "plain"],
+                    help="timed form of --batched")
     ap.add_argument("--workload", default="brain",
                     choices=["brain", "symmetric", "inverse", "svf", "mi", "use_jac", "affine",
                              "rigid"],

@@ -365,6 +365,39 @@ fa_status fa_register_batched(int32_t n_pairs, const fa_vol *fixed, const fa_vol
                               float *final_loss_dev, uint32_t *status_dev, int32_t concurrency,
                               void *ws, size_t ws_bytes, void *stream);
 
+/* The same jobs in lockstep (Algorithm 1 per job, as above; the lockstep
+ * schedule itself has no counterpart in the paper): the jobs of a wave
+ * advance level by level and iteration by iteration together, and every
+ * iteration is ONE launch of each fused kernel over the tiles of every job
+ * of the wave (K3 and K4: one launch per distinct Gaussian radius and
+ * compose variant among the jobs).  Per-job set-up (pyramid, level start,
+ * hand-off, final loss) runs as per-job launches between iterations.
+ * Results are those of one fa_register call per job (the kernels compute
+ * the same bits whatever the tiling).
+ *
+ * Same arguments, outputs and status words as fa_register_batched, except:
+ *  - jobs_per_wave (1..64): jobs run in waves of this many, one wave after
+ *    another on `stream` in the same workspace (fa_register_lockstep_
+ *    workspace_size bytes: one slice per job of a wave, each sized for the
+ *    largest job; 256-byte aligned);
+ *  - every job needs mode FA_MODE_FUSED, loss FA_LOSS_LNCC, use_jac 0,
+ *    sigma_grad and sigma_warp at most 2 (Gaussian radius <= 6), and the
+ *    jobs of a wave share n_levels, scales, iters, window, beta1, beta2 and
+ *    adam_eps; lr, c_lp, cc_eps, the sigmas, the storage type and the grids
+ *    may differ.  Otherwise FA_ERR_UNSUPPORTED before anything is enqueued.
+ * With graph set in every parameter set, each wave is recorded as one CUDA
+ * graph on first use and replayed by later identical calls (not during a
+ * stream capture of the caller's).  Everything runs on `stream`; the call
+ * returns after enqueueing. */
+size_t fa_register_lockstep_workspace_size(int32_t n_pairs, const fa_vol *fixed, int32_t n_cfg,
+                                           const fa_params *cfgs, int32_t jobs_per_wave);
+fa_status fa_register_batched_lockstep(int32_t n_pairs, const fa_vol *fixed,
+                                       const fa_vol *moving, int32_t n_cfg,
+                                       const fa_params *cfgs, fa_vol *u_out,
+                                       float *final_loss_dev, uint32_t *status_dev,
+                                       int32_t jobs_per_wave, void *ws, size_t ws_bytes,
+                                       void *stream);
+
 /* ---------------------------------------------------------------------------
  * Tile autotuning of the fused kernels (no counterpart in the paper).
  * fa_autotune times, for every pyramid level of a D x H x W registration

@@ -10,6 +10,7 @@
 #include <stdio.h>
 
 #include <mutex>
+#include <vector>
 
 #include "ops.h"
 #include "register.h"
@@ -154,4 +155,83 @@ extern "C" fa_status fa_register_batched(int32_t n_pairs, const fa_vol *fixed,
         if (je != cudaSuccess && result == FA_OK) result = cuda_fail(je, "fa_register_batched join");
     }
     return result;
+}
+
+// ------------------------------------------------------------------ lockstep
+// All jobs of a wave advance together: every iteration is one launch per
+// fused kernel over the tiles of every job in the wave (one per Gaussian
+// radius and compose variant for K3 and K4), so the coarse levels of many
+// registrations fill the GPU together.  Waves of `jobs_per_wave` jobs run one
+// after another in the same workspace slices.
+
+namespace fa {
+namespace {
+
+fa_status check_wave(int32_t jobs_per_wave) {
+    if (jobs_per_wave < 1 || jobs_per_wave > kMaxLockstepJobs) {
+        set_error("fa_register_batched_lockstep: jobs_per_wave must be in 1..%d (got %d)",
+                  kMaxLockstepJobs, (int)jobs_per_wave);
+        return FA_ERR_INVALID;
+    }
+    return FA_OK;
+}
+
+}  // namespace
+}  // namespace fa
+
+extern "C" size_t fa_register_lockstep_workspace_size(int32_t n_pairs, const fa_vol *fixed,
+                                                      int32_t n_cfg, const fa_params *cfgs,
+                                                      int32_t jobs_per_wave) {
+    using namespace fa;
+    clear_error();
+    if (check_counts(n_pairs, fixed, n_cfg, cfgs, 1) != FA_OK || check_wave(jobs_per_wave) != FA_OK)
+        return 0;
+    const int jobs = n_pairs * n_cfg;
+    const int wave = jobs_per_wave < jobs ? jobs_per_wave : jobs;
+    return slot_bytes(n_pairs, fixed, n_cfg, cfgs) * (size_t)wave;
+}
+
+extern "C" fa_status fa_register_batched_lockstep(int32_t n_pairs, const fa_vol *fixed,
+                                                  const fa_vol *moving, int32_t n_cfg,
+                                                  const fa_params *cfgs, fa_vol *u_out,
+                                                  float *final_loss_dev, uint32_t *status_dev,
+                                                  int32_t jobs_per_wave, void *ws,
+                                                  size_t ws_bytes, void *stream) {
+    using namespace fa;
+    clear_error();
+    FA_TRY(check_counts(n_pairs, fixed, n_cfg, cfgs, 1));
+    FA_TRY(check_wave(jobs_per_wave));
+    if (!moving || !u_out) {
+        set_error("fa_register_batched_lockstep: moving and u_out must not be NULL");
+        return FA_ERR_INVALID;
+    }
+    const int jobs = n_pairs * n_cfg;
+    std::vector<LockstepArgs> a((size_t)jobs);
+    for (int i = 0; i < n_pairs; ++i)
+        for (int c = 0; c < n_cfg; ++c) {
+            const int j = i * n_cfg + c;
+            const fa_status st = register_check(&fixed[i], &moving[i], &cfgs[c], &u_out[j]);
+            if (st != FA_OK) {
+                char msg[512];
+                snprintf(msg, sizeof(msg), "%s", fa_last_error());
+                set_error("fa_register_batched_lockstep: pair %d, parameter set %d: %s", i, c, msg);
+                return st;
+            }
+            a[(size_t)j] = LockstepArgs{&fixed[i], &moving[i], &cfgs[c], &u_out[j],
+                                        final_loss_dev ? final_loss_dev + j : nullptr,
+                                        status_dev ? status_dev + j : nullptr};
+        }
+    // every wave is checked before anything is enqueued
+    const int wave = jobs_per_wave < jobs ? jobs_per_wave : jobs;
+    for (int j0 = 0; j0 < jobs; j0 += wave) {
+        const int n = jobs - j0 < wave ? jobs - j0 : wave;
+        FA_TRY(lockstep_check(n, a.data() + j0));
+    }
+    const size_t slot = slot_bytes(n_pairs, fixed, n_cfg, cfgs);
+    FA_TRY(check_ws(ws, ws_bytes, slot * (size_t)wave, "fa_register_batched_lockstep"));
+    for (int j0 = 0; j0 < jobs; j0 += wave) {
+        const int n = jobs - j0 < wave ? jobs - j0 : wave;
+        FA_TRY(register_lockstep(n, a.data() + j0, ws, slot, (cudaStream_t)stream));
+    }
+    return FA_OK;
 }

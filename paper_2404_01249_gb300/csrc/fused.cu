@@ -240,8 +240,8 @@ struct Outs {
 // column ox + COFF; rows are read with 16-byte shared loads from column 4k.
 
 // Gaussian x pass: pl [C][RY][BXW] -> xb [C][RY][FX].
-template <int RG, int C, int RY, int BXW, int COFF, int NT>
-__device__ __forceinline__ void gauss_x4(const float *pl, float *xb, const GaussTaps &t, int tid) {
+template <int RG, int C, int RY, int BXW, int COFF, int NT, class TT>
+__device__ __forceinline__ void gauss_x4(const float *pl, float *xb, const TT &t, int tid) {
     constexpr int ITEMS = C * RY * 8, NL = (4 + COFF + 2 * RG + 3) / 4;
     static_assert(28 + 4 * NL <= BXW, "row too short for the vector loads");
 #pragma unroll
@@ -382,8 +382,8 @@ __device__ __forceinline__ void box_y3(const long long *xL, int wy, int tx, long
     }
 }
 
-template <int RG, int RY, int NW, int OPT>
-__device__ __forceinline__ void gauss_y3(const float *xb, const GaussTaps &t, int wy, int tx,
+template <int RG, int RY, int NW, int OPT, class TT>
+__device__ __forceinline__ void gauss_y3(const float *xb, const TT &t, int wy, int tx,
                                          float Q[OPT][3]) {
 #pragma unroll
     for (int o = 0; o < OPT; ++o) {
@@ -425,8 +425,8 @@ __device__ __forceinline__ void ring_put(float *ring, int newest, int tid, const
 
 // Weighted z window of all three channels of one output: tap k takes the
 // plane k - R of the window, i.e. ring slot (newest + 1 + k) mod NS.
-template <int RG, int NOUT>
-__device__ __forceinline__ void gauss_z3(const float *ring_o, int newest, const GaussTaps &t,
+template <int RG, int NOUT, class TT>
+__device__ __forceinline__ void gauss_z3(const float *ring_o, int newest, const TT &t,
                                          float out[3]) {
     constexpr int NS = 2 * RG + 1;
     out[0] = out[1] = out[2] = 0.0f;
@@ -464,16 +464,15 @@ struct K1S {
     static constexpr size_t bytes = o_bar + 8 * NSTG;
 };
 
+// The body of K1 for the CTA with tile coordinates (bx, by, bz).
 template <int R, int NW, int OPT, int NSTG, bool TMA>
-__global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const __grid_constant__ Maps maps,
-                                                     const float *__restrict__ If,
-                                                     const float *__restrict__ J,
-                                                     const long long *__restrict__ SIg,
-                                                     const float *__restrict__ varIg,
-                                                     float *__restrict__ coef,
-                                                     WsHeader *__restrict__ h, int D, int H, int W,
-                                                     int TZ, int bits, float cc_eps, int window,
-                                                     int write_coef) {
+__device__ __forceinline__ void lncc_fwd_body(const Maps *maps, const float *__restrict__ If,
+                                              const float *__restrict__ J,
+                                              const long long *__restrict__ SIg,
+                                              const float *__restrict__ varIg,
+                                              float *__restrict__ coef, WsHeader *__restrict__ h,
+                                              int D, int H, int W, int TZ, int bits, float cc_eps,
+                                              int window, int write_coef, int bx, int by, int bz) {
     using S = K1S<R, NW, OPT, NSTG>;
     constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, BXW = S::BXW, COFF = S::COFF,
                   XB = S::XB, NR = S::NR, NS = S::NS, NOUT = S::NOUT;
@@ -490,7 +489,7 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const __grid_constant__ Map
     auto stage = [&](int s) { return (float *)(smem + S::o_st + S::st_bytes * s); };
 
     const int tx = threadIdx.x, wy = threadIdx.y, tid = wy * FX + tx;
-    const int x0 = blockIdx.x * FX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+    const int x0 = bx * FX, y0 = by * TY, z0 = bz * TZ;
     const int zend = min(z0 + TZ, D);
     const long long N = (long long)D * H * W, HW = (long long)H * W;
     const long long n = (long long)window * window * window;
@@ -522,8 +521,8 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const __grid_constant__ Map
         if (TMA) {
             if (tid == 0 && i < np) {
                 mbar_expect(bar + s, S::tx_plane);
-                tma4(stage(s), &maps.a, x0 - XB, y0 - R, zp, 0, bar + s);
-                tma4(stage(s) + CS, &maps.b, x0 - XB, y0 - R, zp, 0, bar + s);
+                tma4(stage(s), &maps->a, x0 - XB, y0 - R, zp, 0, bar + s);
+                tma4(stage(s) + CS, &maps->b, x0 - XB, y0 - R, zp, 0, bar + s);
             }
         } else {
             if (i < np) {
@@ -657,6 +656,21 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const __grid_constant__ Map
     }
 }
 
+template <int R, int NW, int OPT, int NSTG, bool TMA>
+__global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const __grid_constant__ Maps maps,
+                                                     const float *__restrict__ If,
+                                                     const float *__restrict__ J,
+                                                     const long long *__restrict__ SIg,
+                                                     const float *__restrict__ varIg,
+                                                     float *__restrict__ coef,
+                                                     WsHeader *__restrict__ h, int D, int H, int W,
+                                                     int TZ, int bits, float cc_eps, int window,
+                                                     int write_coef) {
+    lncc_fwd_body<R, NW, OPT, NSTG, TMA>(&maps, If, J, SIg, varIg, coef, h, D, H, W, TZ, bits,
+                                         cc_eps, window, write_coef, blockIdx.x, blockIdx.y,
+                                         blockIdx.z);
+}
+
 // ====================================================================== K2
 // coef holds A, B and C as a float-float pair (C hi, C lo): [4][N].
 template <int R, int NW, int OPT, int NSTG>
@@ -674,15 +688,15 @@ struct K2S {
     static constexpr size_t bytes = o_bar + 8 * NSTG;
 };
 
+// The body of K2 for the CTA with tile coordinates (bx, by, bz).
 template <int R, int NW, int OPT, int NSTG, bool TMA>
-__global__ void __launch_bounds__(FX *NW) k_lncc_grad(const __grid_constant__ Maps maps,
-                                                      const float *__restrict__ If,
-                                                      const float *__restrict__ gJ,
-                                                      const float *__restrict__ J,
-                                                      const float *__restrict__ coef,
-                                                      WsHeader *__restrict__ h,
-                                                      float *__restrict__ g, int D, int H, int W,
-                                                      int TZ, int cbits) {
+__device__ __forceinline__ void lncc_grad_body(const Maps *maps, const float *__restrict__ If,
+                                               const float *__restrict__ gJ,
+                                               const float *__restrict__ J,
+                                               const float *__restrict__ coef,
+                                               WsHeader *__restrict__ h, float *__restrict__ g,
+                                               int D, int H, int W, int TZ, int cbits, int bx,
+                                               int by, int bz) {
     using S = K2S<R, NW, OPT, NSTG>;
     constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, BXW = S::BXW, COFF = S::COFF,
                   XB = S::XB, NR = S::NR, NS = S::NS, NOUT = S::NOUT;
@@ -696,7 +710,7 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_grad(const __grid_constant__ Ma
     auto stage = [&](int s) { return (float *)(smem + S::o_st + S::st_bytes * s); };
 
     const int tx = threadIdx.x, wy = threadIdx.y, tid = wy * FX + tx;
-    const int x0 = blockIdx.x * FX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+    const int x0 = bx * FX, y0 = by * TY, z0 = bz * TZ;
     const int zend = min(z0 + TZ, D);
     const long long N = (long long)D * H * W, HW = (long long)H * W;
     const float inv_n = 1.0f / (float)N;
@@ -729,7 +743,7 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_grad(const __grid_constant__ Ma
         if (TMA) {
             if (tid == 0 && i < np) {
                 mbar_expect(bar + s, S::tx_plane);
-                tma4(stage(s), &maps.a, x0 - XB, y0 - R, zp, 0, bar + s);
+                tma4(stage(s), &maps->a, x0 - XB, y0 - R, zp, 0, bar + s);
             }
         } else {
             if (i < np)
@@ -839,6 +853,19 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_grad(const __grid_constant__ Ma
     if (!TMA) cp_wait<0>();
 }
 
+template <int R, int NW, int OPT, int NSTG, bool TMA>
+__global__ void __launch_bounds__(FX *NW) k_lncc_grad(const __grid_constant__ Maps maps,
+                                                      const float *__restrict__ If,
+                                                      const float *__restrict__ gJ,
+                                                      const float *__restrict__ J,
+                                                      const float *__restrict__ coef,
+                                                      WsHeader *__restrict__ h,
+                                                      float *__restrict__ g, int D, int H, int W,
+                                                      int TZ, int cbits) {
+    lncc_grad_body<R, NW, OPT, NSTG, TMA>(&maps, If, gJ, J, coef, h, g, D, H, W, TZ, cbits,
+                                          blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 // MSE: g = 2 (J - I) / N * grad I_m(phi) (pointwise, J and the gradient as
 // the compose kernel stored them).
 __global__ void __launch_bounds__(256) k_fused_mse_grad(const float *__restrict__ If,
@@ -875,15 +902,14 @@ struct K3S {
     static constexpr size_t bytes = o_bar + 8 * NSTG;
 };
 
-template <int RG, int NW, int OPT, int NSTG, bool TMA>
-__global__ void __launch_bounds__(FX *NW, NW >= 16 ? 2 : 1) k_smooth_adam(const __grid_constant__ Maps maps,
-                                                        const float *__restrict__ g,
-                                                        float *__restrict__ m,
-                                                        float *__restrict__ v,
-                                                        float *__restrict__ dir,
-                                                        WsHeader *__restrict__ h, int D, int H,
-                                                        int W, int TZ, GaussTaps t, AdamConsts ac,
-                                                        int parity) {
+// The body of K3 for the CTA with tile coordinates (bx, by, bz).
+template <int RG, int NW, int OPT, int NSTG, bool TMA, class TT>
+__device__ __forceinline__ void smooth_adam_body(const Maps *maps, const float *__restrict__ g,
+                                                 float *__restrict__ m, float *__restrict__ v,
+                                                 float *__restrict__ dir, WsHeader *__restrict__ h,
+                                                 int D, int H, int W, int TZ, const TT t,
+                                                 const AdamConsts ac, int parity, int bx, int by,
+                                                 int bz) {
     using S = K3S<RG, NW, OPT, NSTG>;
     constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, BXW = S::BXW, COFF = S::COFF,
                   XB = S::XB, NS = S::NS, NOUT = S::NOUT;
@@ -898,7 +924,7 @@ __global__ void __launch_bounds__(FX *NW, NW >= 16 ? 2 : 1) k_smooth_adam(const 
     auto ostage = [&](int s) { return (float *)(smem + S::o_ost + S::ost_bytes * s); };
 
     const int tx = threadIdx.x, wy = threadIdx.y, tid = wy * FX + tx;
-    const int x0 = blockIdx.x * FX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+    const int x0 = bx * FX, y0 = by * TY, z0 = bz * TZ;
     const int zend = min(z0 + TZ, D);
     const long long N = (long long)D * H * W, HW = (long long)H * W;
     G rg;
@@ -919,10 +945,10 @@ __global__ void __launch_bounds__(FX *NW, NW >= 16 ? 2 : 1) k_smooth_adam(const 
         if (TMA) {
             if (tid == 0 && i < np) {
                 mbar_expect(bar + s, S::tx_plane + (out ? S::tx_out : 0u));
-                tma4(stage(s), &maps.a, x0 - XB, y0 - RG, zp, 0, bar + s);
+                tma4(stage(s), &maps->a, x0 - XB, y0 - RG, zp, 0, bar + s);
                 if (out) {
-                    tma4(ostage(s), &maps.b, x0, y0, zo, 0, bar + s);
-                    tma4(ostage(s) + 3 * NOUT, &maps.c, x0, y0, zo, 0, bar + s);
+                    tma4(ostage(s), &maps->b, x0, y0, zo, 0, bar + s);
+                    tma4(ostage(s) + 3 * NOUT, &maps->c, x0, y0, zo, 0, bar + s);
                 }
             }
         } else {
@@ -1018,6 +1044,19 @@ __global__ void __launch_bounds__(FX *NW, NW >= 16 ? 2 : 1) k_smooth_adam(const 
     block_max_to(&h->step_max_bits[parity], mx, redf);
 }
 
+template <int RG, int NW, int OPT, int NSTG, bool TMA>
+__global__ void __launch_bounds__(FX *NW, NW >= 16 ? 2 : 1) k_smooth_adam(const __grid_constant__ Maps maps,
+                                                        const float *__restrict__ g,
+                                                        float *__restrict__ m,
+                                                        float *__restrict__ v,
+                                                        float *__restrict__ dir,
+                                                        WsHeader *__restrict__ h, int D, int H,
+                                                        int W, int TZ, GaussTaps t, AdamConsts ac,
+                                                        int parity) {
+    smooth_adam_body<RG, NW, OPT, NSTG, TMA>(&maps, g, m, v, dir, h, D, H, W, TZ, t, ac, parity,
+                                             blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 // ====================================================================== K4
 // SU: u is staged in shared memory (planes z-1..z+1, halo RG + 1); valid when
 // the step is shorter than one voxel (lr / c_lp < 1).
@@ -1041,17 +1080,16 @@ struct K4S {
     static constexpr size_t bytes = o_bar + 8 * (NSTG + 1);
 };
 
-template <int RG, int NW, int OPT, bool SU, int NSTG, bool TMA>
-__global__ void __launch_bounds__(FX *NW, NW >= 16 ? 2 : 1) k_compose(const __grid_constant__ Maps maps,
-                                                    const float *__restrict__ u,
-                                                    const float *__restrict__ dir,
-                                                    float *__restrict__ uo,
-                                                    const float *__restrict__ Im,
-                                                    float *__restrict__ Jout,
-                                                    float *__restrict__ gJout,
-                                                    WsHeader *__restrict__ h, int D, int H, int W,
-                                                    int TZ, GaussTaps t, float lr, float c_lp,
-                                                    int parity) {
+// The body of K4 for the CTA with tile coordinates (bx, by, bz).
+template <int RG, int NW, int OPT, bool SU, int NSTG, bool TMA, class TT>
+__device__ __forceinline__ void compose_body(const Maps *maps, const float *__restrict__ u,
+                                             const float *__restrict__ dir,
+                                             float *__restrict__ uo,
+                                             const float *__restrict__ Im,
+                                             float *__restrict__ Jout, float *__restrict__ gJout,
+                                             WsHeader *__restrict__ h, int D, int H, int W, int TZ,
+                                             const TT t, float lr, float c_lp, int parity, int bx,
+                                             int by, int bz) {
     using S = K4S<RG, NW, OPT, SU, NSTG>;
     constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, BXW = S::BXW, COFF = S::COFF,
                   XB = S::XB, NR = S::NR, NS = S::NS, NOUT = S::NOUT, URX = S::URX,
@@ -1068,7 +1106,7 @@ __global__ void __launch_bounds__(FX *NW, NW >= 16 ? 2 : 1) k_compose(const __gr
     auto stage = [&](int s) { return (float *)(smem + S::o_st + S::st_bytes * s); };
 
     const int tx = threadIdx.x, wy = threadIdx.y, tid = wy * FX + tx;
-    const int x0 = blockIdx.x * FX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+    const int x0 = bx * FX, y0 = by * TY, z0 = bz * TZ;
     const int zend = min(z0 + TZ, D);
     const long long N = (long long)D * H * W, HW = (long long)H * W;
     G rg;
@@ -1099,8 +1137,8 @@ __global__ void __launch_bounds__(FX *NW, NW >= 16 ? 2 : 1) k_compose(const __gr
         if (TMA) {
             if (tid == 0 && i < np) {
                 mbar_expect(bar + s, S::tx_plane + (SU ? S::tx_u : 0u));
-                tma4(stage(s), &maps.a, x0 - XB, y0 - RG, zp, 0, bar + s);
-                if (SU) tma4(uslot(zp + 1), &maps.b, x0 - UXB, y0 - RG - 1, zp + 1, 0, bar + s);
+                tma4(stage(s), &maps->a, x0 - XB, y0 - RG, zp, 0, bar + s);
+                if (SU) tma4(uslot(zp + 1), &maps->b, x0 - UXB, y0 - RG - 1, zp + 1, 0, bar + s);
             }
         } else {
             if (i < np) {
@@ -1117,8 +1155,8 @@ __global__ void __launch_bounds__(FX *NW, NW >= 16 ? 2 : 1) k_compose(const __gr
         if (TMA) {
             if (tid == 0) {
                 mbar_expect(bar + NSTG, 2u * S::tx_u);
-                tma4(uslot(zs - 1), &maps.b, x0 - UXB, y0 - RG - 1, zs - 1, 0, bar + NSTG);
-                tma4(uslot(zs), &maps.b, x0 - UXB, y0 - RG - 1, zs, 0, bar + NSTG);
+                tma4(uslot(zs - 1), &maps->b, x0 - UXB, y0 - RG - 1, zs - 1, 0, bar + NSTG);
+                tma4(uslot(zs), &maps->b, x0 - UXB, y0 - RG - 1, zs, 0, bar + NSTG);
             }
         } else {
             rgu.template load<3>(uslot(zs - 1), u, N, (long long)(zs - 1) * HW,
@@ -1264,12 +1302,27 @@ __global__ void __launch_bounds__(FX *NW, NW >= 16 ? 2 : 1) k_compose(const __gr
         }
     if (!TMA) cp_wait<0>();
     // per-iteration header fields for the next iteration (nobody else reads them now)
-    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && tid == 0) {
+    if (bx == 0 && by == 0 && bz == 0 && tid == 0) {
         for (int c = 0; c < 8; ++c) h->coef_max_bits[c] = 0u;
         h->step_max_bits[parity ^ 1] = 0u;
         h->loss_acc = 0ull;
         h->eps_t = e;
     }
+}
+
+template <int RG, int NW, int OPT, bool SU, int NSTG, bool TMA>
+__global__ void __launch_bounds__(FX *NW, NW >= 16 ? 2 : 1) k_compose(const __grid_constant__ Maps maps,
+                                                    const float *__restrict__ u,
+                                                    const float *__restrict__ dir,
+                                                    float *__restrict__ uo,
+                                                    const float *__restrict__ Im,
+                                                    float *__restrict__ Jout,
+                                                    float *__restrict__ gJout,
+                                                    WsHeader *__restrict__ h, int D, int H, int W,
+                                                    int TZ, GaussTaps t, float lr, float c_lp,
+                                                    int parity) {
+    compose_body<RG, NW, OPT, SU, NSTG, TMA>(&maps, u, dir, uo, Im, Jout, gJout, h, D, H, W, TZ, t,
+                                             lr, c_lp, parity, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // ================================================================ launching
@@ -1624,7 +1677,7 @@ cudaError_t dispatch_k2(const float *If, const float *gJ, const float *J, const 
     return cudaErrorInvalidValue;
 }
 
-constexpr int kMaxFusedRG = 6;
+constexpr int kMaxFusedRG = kMaxFusedRadius;
 
 cudaError_t dispatch_k3(const float *g, float *m, float *v, float *dir, WsHeader *h, Dims d,
                         const GaussTaps &t, AdamConsts ac, int parity, cudaStream_t s) {
@@ -1663,6 +1716,316 @@ cudaError_t dispatch_k4(const float *u, const float *dir, float *uo, const float
             FA_CASE(4, (launch_k4<RR, false>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
             FA_CASE(5, (launch_k4<RR, false>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
             FA_CASE(6, (launch_k4<RR, false>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+#undef FA_CASE
+
+// ------------------------------------------------------------ lockstep batches
+// Many registrations advance together: one launch of a fused kernel covers the
+// tiles of every job in the launch's table.  CTA b belongs to the job k with
+// first[k] <= b < first[k + 1]; its tile inside that job's grid is
+// b - first[k] in x-fastest order.  The table travels in the kernel's
+// parameter space (read through the constant cache; every thread of a CTA
+// reads the same entry).  Jobs take the per-thread copy variant (cp.async):
+// their grids are mostly of uneven width, and tensor maps would not fit the
+// parameter space.
+struct BGeom {
+    int D, H, W, TZ, gx, gy;
+};
+struct BTaps {
+    float w[2 * kMaxFusedRG + 1];
+};
+struct K1Job {
+    const float *If, *J;
+    const long long *SI;
+    const float *varI;
+    float *coef;
+    WsHeader *h;
+    BGeom g;
+    float cc_eps;
+};
+struct K1Batch {
+    int n, bits, window, write_coef;
+    int first[kMaxLockstepJobs + 1];
+    K1Job j[kMaxLockstepJobs];
+};
+struct K2Job {
+    const float *If, *gJ, *J, *coef;
+    float *g;
+    WsHeader *h;
+    BGeom geo;
+};
+struct K2Batch {
+    int n, cbits;
+    int first[kMaxLockstepJobs + 1];
+    K2Job j[kMaxLockstepJobs];
+};
+struct K3Job {
+    const float *g;
+    float *m, *v, *dir;
+    WsHeader *h;
+    BGeom geo;
+    BTaps t;
+};
+struct K3Batch {
+    int n, parity;
+    AdamConsts ac;
+    int first[kMaxLockstepJobs + 1];
+    K3Job j[kMaxLockstepJobs];
+};
+struct K4Job {
+    const float *u, *dir;
+    float *uo;
+    const float *Im;
+    float *J, *gJ;
+    WsHeader *h;
+    BGeom geo;
+    BTaps t;
+    float lr, c_lp;
+};
+struct K4Batch {
+    int n, parity;
+    int first[kMaxLockstepJobs + 1];
+    K4Job j[kMaxLockstepJobs];
+};
+static_assert(sizeof(K4Batch) < 16384 && sizeof(K3Batch) < 16384 && sizeof(K1Batch) < 16384,
+              "a lockstep table must fit the kernel parameter space");
+
+// The job of CTA b: the largest k with first[k] <= b (first[0] = 0).
+__device__ __forceinline__ int batch_job(const int *first, int n, int b) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (first[mid] <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void batch_tile(const BGeom &g, int t, int &bx, int &by, int &bz) {
+    bx = t % g.gx;
+    const int r = t / g.gx;
+    by = r % g.gy;
+    bz = r / g.gy;
+}
+
+template <int R>
+__global__ void __launch_bounds__(FX *K1_NW) k_lncc_fwd_batch(const __grid_constant__ K1Batch b) {
+    const int k = batch_job(b.first, b.n, (int)blockIdx.x);
+    const K1Job &j = b.j[k];
+    int bx, by, bz;
+    batch_tile(j.g, (int)blockIdx.x - b.first[k], bx, by, bz);
+    lncc_fwd_body<R, K1_NW, K1_OPT, K1_ST_CP, false>(nullptr, j.If, j.J, j.SI, j.varI, j.coef, j.h,
+                                                     j.g.D, j.g.H, j.g.W, j.g.TZ, b.bits,
+                                                     j.cc_eps, b.window, b.write_coef, bx, by, bz);
+}
+
+template <int R>
+__global__ void __launch_bounds__(FX *K2_NW) k_lncc_grad_batch(const __grid_constant__ K2Batch b) {
+    const int k = batch_job(b.first, b.n, (int)blockIdx.x);
+    const K2Job &j = b.j[k];
+    int bx, by, bz;
+    batch_tile(j.geo, (int)blockIdx.x - b.first[k], bx, by, bz);
+    lncc_grad_body<R, K2_NW, K2_OPT, K2_ST_CP, false>(nullptr, j.If, j.gJ, j.J, j.coef, j.h, j.g,
+                                                      j.geo.D, j.geo.H, j.geo.W, j.geo.TZ, b.cbits,
+                                                      bx, by, bz);
+}
+
+template <int RG>
+__global__ void __launch_bounds__(FX *K3_NW) k_smooth_adam_batch(const __grid_constant__ K3Batch b) {
+    const int k = batch_job(b.first, b.n, (int)blockIdx.x);
+    const K3Job &j = b.j[k];
+    int bx, by, bz;
+    batch_tile(j.geo, (int)blockIdx.x - b.first[k], bx, by, bz);
+    smooth_adam_body<RG, K3_NW, K3_OPT, K3_ST_CP, false>(nullptr, j.g, j.m, j.v, j.dir, j.h,
+                                                         j.geo.D, j.geo.H, j.geo.W, j.geo.TZ, j.t,
+                                                         b.ac, b.parity, bx, by, bz);
+}
+
+template <int RG, bool SU>
+__global__ void __launch_bounds__(FX *K4_NW) k_compose_batch(const __grid_constant__ K4Batch b) {
+    const int k = batch_job(b.first, b.n, (int)blockIdx.x);
+    const K4Job &j = b.j[k];
+    int bx, by, bz;
+    batch_tile(j.geo, (int)blockIdx.x - b.first[k], bx, by, bz);
+    compose_body<RG, K4_NW, K4_OPT, SU, K4_ST_CP, false>(nullptr, j.u, j.dir, j.uo, j.Im, j.J,
+                                                         j.gJ, j.h, j.geo.D, j.geo.H, j.geo.W,
+                                                         j.geo.TZ, j.t, j.lr, j.c_lp, b.parity, bx,
+                                                         by, bz);
+}
+
+// Slab depth of one job in a lockstep launch: the job gets the share of the
+// GPU's resident CTA slots that its voxels are of the launch's voxels, and TZ
+// minimises (waves x planes per CTA) on that share.
+int batch_tz(Dims d, int tiles_xy, int halo, int occ, long long vox, long long total_vox) {
+    const long long slots = (long long)num_sms() * (occ > 0 ? occ : 1);
+    long long share = total_vox > 0 ? slots * vox / total_vox : slots;
+    if (share < 1) share = 1;
+    int best = d.D;
+    long long bestcost = -1;
+    for (int tz = 1; tz <= d.D && tz <= 64; ++tz) {
+        const long long ctas = (long long)tiles_xy * ((d.D + tz - 1) / tz);
+        const long long waves = (ctas + share - 1) / share;
+        const long long cost = waves * (tz + 2 * halo);
+        if (bestcost < 0 || cost < bestcost) {
+            bestcost = cost;
+            best = tz;
+        }
+    }
+    return best;
+}
+
+// Fills a job's tile geometry for a kernel with `ty` rows per CTA and returns
+// its CTA count.
+int batch_geom(BGeom &g, Dims d, int ty, int halo, int occ, long long total_vox) {
+    g.D = d.D;
+    g.H = d.H;
+    g.W = d.W;
+    g.gx = (d.W + FX - 1) / FX;
+    g.gy = (d.H + ty - 1) / ty;
+    g.TZ = batch_tz(d, g.gx * g.gy, halo, occ, d.N(), total_vox);
+    return g.gx * g.gy * ((d.D + g.TZ - 1) / g.TZ);
+}
+
+void batch_taps(BTaps &b, const GaussTaps &t) {
+    for (int k = 0; k < 2 * kMaxFusedRG + 1; ++k) b.w[k] = k <= 2 * t.R ? t.w[k] : 0.0f;
+}
+
+template <class K, class B>
+cudaError_t launch_batch(K kern, const B &b, int nw, size_t smem, cudaStream_t s) {
+    LaunchGeom g;
+    g.grid = dim3((unsigned)b.first[b.n]);
+    g.block = dim3(FX, nw);
+    g.tz = 0;
+    return launch_pdl(kern, g, smem, s, b);
+}
+
+template <int R>
+cudaError_t launch_k1_batch(K1Batch &b, const LockstepJob *jobs, cudaStream_t s) {
+    using SC = K1S<R, K1_NW, K1_OPT, K1_ST_CP>;
+    auto kern = k_lncc_fwd_batch<R>;
+    static const int occ = prepare(kern, SC::bytes, SC::NT);
+    long long tot = 0;
+    for (int k = 0; k < b.n; ++k) tot += jobs[k].d.N();
+    b.first[0] = 0;
+    for (int k = 0; k < b.n; ++k)
+        b.first[k + 1] = b.first[k] + batch_geom(b.j[k].g, jobs[k].d, SC::TY, R, occ, tot);
+    return launch_batch(kern, b, SC::NT / FX, SC::bytes, s);
+}
+
+template <int R>
+cudaError_t launch_k2_batch(K2Batch &b, const LockstepJob *jobs, cudaStream_t s) {
+    using SC = K2S<R, K2_NW, K2_OPT, K2_ST_CP>;
+    auto kern = k_lncc_grad_batch<R>;
+    static const int occ = prepare(kern, SC::bytes, SC::NT);
+    long long tot = 0;
+    for (int k = 0; k < b.n; ++k) tot += jobs[k].d.N();
+    b.first[0] = 0;
+    for (int k = 0; k < b.n; ++k)
+        b.first[k + 1] = b.first[k] + batch_geom(b.j[k].geo, jobs[k].d, SC::TY, R, occ, tot);
+    return launch_batch(kern, b, SC::NT / FX, SC::bytes, s);
+}
+
+// jobs[idx[0..b.n)] are the launch's jobs
+template <int RG>
+cudaError_t launch_k3_batch(K3Batch &b, const LockstepJob *jobs, const int *idx, cudaStream_t s) {
+    using SC = K3S<RG, K3_NW, K3_OPT, K3_ST_CP>;
+    auto kern = k_smooth_adam_batch<RG>;
+    static const int occ = prepare(kern, SC::bytes, SC::NT);
+    long long tot = 0;
+    for (int k = 0; k < b.n; ++k) tot += jobs[idx[k]].d.N();
+    b.first[0] = 0;
+    for (int k = 0; k < b.n; ++k)
+        b.first[k + 1] = b.first[k] + batch_geom(b.j[k].geo, jobs[idx[k]].d, SC::TY, RG, occ, tot);
+    return launch_batch(kern, b, SC::NT / FX, SC::bytes, s);
+}
+
+template <int RG, bool SU>
+cudaError_t launch_k4_batch(K4Batch &b, const LockstepJob *jobs, const int *idx, cudaStream_t s) {
+    using SC = K4S<RG, K4_NW, K4_OPT, SU, K4_ST_CP>;
+    auto kern = k_compose_batch<RG, SU>;
+    static const int occ = prepare(kern, SC::bytes, SC::NT);
+    long long tot = 0;
+    for (int k = 0; k < b.n; ++k) tot += jobs[idx[k]].d.N();
+    b.first[0] = 0;
+    for (int k = 0; k < b.n; ++k)
+        b.first[k + 1] = b.first[k] + batch_geom(b.j[k].geo, jobs[idx[k]].d, SC::TY, RG, occ, tot);
+    return launch_batch(kern, b, SC::NT / FX, SC::bytes, s);
+}
+
+#define FA_CASE(n, call)      \
+    case n: {                 \
+        constexpr int RR = n; \
+        return call;          \
+    }
+
+cudaError_t dispatch_k1_batch(int R, K1Batch &b, const LockstepJob *jobs, cudaStream_t s) {
+    switch (R) {
+        FA_CASE(0, launch_k1_batch<RR>(b, jobs, s))
+        FA_CASE(1, launch_k1_batch<RR>(b, jobs, s))
+        FA_CASE(2, launch_k1_batch<RR>(b, jobs, s))
+        FA_CASE(3, launch_k1_batch<RR>(b, jobs, s))
+        FA_CASE(4, launch_k1_batch<RR>(b, jobs, s))
+        FA_CASE(5, launch_k1_batch<RR>(b, jobs, s))
+        FA_CASE(6, launch_k1_batch<RR>(b, jobs, s))
+        FA_CASE(7, launch_k1_batch<RR>(b, jobs, s))
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t dispatch_k2_batch(int R, K2Batch &b, const LockstepJob *jobs, cudaStream_t s) {
+    switch (R) {
+        FA_CASE(0, launch_k2_batch<RR>(b, jobs, s))
+        FA_CASE(1, launch_k2_batch<RR>(b, jobs, s))
+        FA_CASE(2, launch_k2_batch<RR>(b, jobs, s))
+        FA_CASE(3, launch_k2_batch<RR>(b, jobs, s))
+        FA_CASE(4, launch_k2_batch<RR>(b, jobs, s))
+        FA_CASE(5, launch_k2_batch<RR>(b, jobs, s))
+        FA_CASE(6, launch_k2_batch<RR>(b, jobs, s))
+        FA_CASE(7, launch_k2_batch<RR>(b, jobs, s))
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t dispatch_k3_batch(int RG, K3Batch &b, const LockstepJob *jobs, const int *idx,
+                              cudaStream_t s) {
+    switch (RG) {
+        FA_CASE(0, launch_k3_batch<RR>(b, jobs, idx, s))
+        FA_CASE(1, launch_k3_batch<RR>(b, jobs, idx, s))
+        FA_CASE(2, launch_k3_batch<RR>(b, jobs, idx, s))
+        FA_CASE(3, launch_k3_batch<RR>(b, jobs, idx, s))
+        FA_CASE(4, launch_k3_batch<RR>(b, jobs, idx, s))
+        FA_CASE(5, launch_k3_batch<RR>(b, jobs, idx, s))
+        FA_CASE(6, launch_k3_batch<RR>(b, jobs, idx, s))
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t dispatch_k4_batch(int RG, bool su, K4Batch &b, const LockstepJob *jobs, const int *idx,
+                              cudaStream_t s) {
+    if (su) {
+        switch (RG) {
+            FA_CASE(0, (launch_k4_batch<RR, true>(b, jobs, idx, s)))
+            FA_CASE(1, (launch_k4_batch<RR, true>(b, jobs, idx, s)))
+            FA_CASE(2, (launch_k4_batch<RR, true>(b, jobs, idx, s)))
+            FA_CASE(3, (launch_k4_batch<RR, true>(b, jobs, idx, s)))
+            FA_CASE(4, (launch_k4_batch<RR, true>(b, jobs, idx, s)))
+            FA_CASE(5, (launch_k4_batch<RR, true>(b, jobs, idx, s)))
+            FA_CASE(6, (launch_k4_batch<RR, true>(b, jobs, idx, s)))
+        }
+    } else {
+        switch (RG) {
+            FA_CASE(0, (launch_k4_batch<RR, false>(b, jobs, idx, s)))
+            FA_CASE(1, (launch_k4_batch<RR, false>(b, jobs, idx, s)))
+            FA_CASE(2, (launch_k4_batch<RR, false>(b, jobs, idx, s)))
+            FA_CASE(3, (launch_k4_batch<RR, false>(b, jobs, idx, s)))
+            FA_CASE(4, (launch_k4_batch<RR, false>(b, jobs, idx, s)))
+            FA_CASE(5, (launch_k4_batch<RR, false>(b, jobs, idx, s)))
+            FA_CASE(6, (launch_k4_batch<RR, false>(b, jobs, idx, s)))
         }
     }
     return cudaErrorInvalidValue;
@@ -1765,6 +2128,106 @@ fa_status fused_iteration(FusedBuffers &fb, WsHeader *h, const fa_params *p, Dim
         FA_CUDA_TRY(launch_gauss3(it.u_alt, it.u_alt, fb.t1, fb.t2, 3, d, tw, s));
         FA_CUDA_TRY(launch_warp(it.Im, it.u_alt, fb.J, fb.gJ, d, s));  // J, grad of the smoothed map
     }
+    return FA_OK;
+}
+
+fa_status fused_iteration_lockstep(int n, const LockstepJob *jobs, int t, cudaStream_t s) {
+    if (n < 1 || n > kMaxLockstepJobs) {
+        set_error("lockstep iteration: 1..%d jobs per launch (got %d)", kMaxLockstepJobs, n);
+        return FA_ERR_INVALID;
+    }
+    const fa_params *p0 = jobs[0].p;
+    const int parity = t & 1, R = p0->window / 2;
+    {
+        K1Batch b;
+        b.n = n;
+        b.bits = lncc_image_bits(p0->window);
+        b.window = p0->window;
+        b.write_coef = 1;
+        for (int k = 0; k < n; ++k) {
+            const LockstepJob &q = jobs[k];
+            K1Job &j = b.j[k];
+            j.If = q.If;
+            j.J = q.fb->J;
+            j.SI = q.fb->sI;
+            j.varI = q.fb->varI;
+            j.coef = q.fb->coef;
+            j.h = q.h;
+            j.cc_eps = q.p->cc_eps;
+        }
+        FA_CUDA_TRY(dispatch_k1_batch(R, b, jobs, s));
+        note_launch();
+    }
+    {
+        K2Batch b;
+        b.n = n;
+        b.cbits = lncc_coef_bits(p0->window);
+        for (int k = 0; k < n; ++k) {
+            const LockstepJob &q = jobs[k];
+            K2Job &j = b.j[k];
+            j.If = q.If;
+            j.gJ = q.fb->gJ;
+            j.J = q.fb->J;
+            j.coef = q.fb->coef;
+            j.g = q.fb->g;
+            j.h = q.h;
+        }
+        FA_CUDA_TRY(dispatch_k2_batch(R, b, jobs, s));
+        note_launch();
+    }
+    int idx[kMaxLockstepJobs];
+    const AdamConsts ac = adam_consts(p0, t);
+    for (int rg = 0; rg <= kMaxFusedRG; ++rg) {
+        int m = 0;
+        for (int k = 0; k < n; ++k)
+            if (jobs[k].tg->R == rg) idx[m++] = k;
+        if (m == 0) continue;
+        K3Batch b;
+        b.n = m;
+        b.parity = parity;
+        b.ac = ac;
+        for (int i = 0; i < m; ++i) {
+            const LockstepJob &q = jobs[idx[i]];
+            K3Job &j = b.j[i];
+            j.g = q.fb->g;
+            j.m = q.m;
+            j.v = q.v;
+            j.dir = q.fb->dir;
+            j.h = q.h;
+            batch_taps(j.t, *q.tg);
+        }
+        FA_CUDA_TRY(dispatch_k3_batch(rg, b, jobs, idx, s));
+        note_launch();
+    }
+    for (int su = 0; su < 2; ++su)
+        for (int rg = 0; rg <= kMaxFusedRG; ++rg) {
+            int m = 0;
+            for (int k = 0; k < n; ++k) {
+                const fa_params *p = jobs[k].p;
+                const int ksu = (double)p->lr / (double)p->c_lp < 0.999 ? 1 : 0;
+                if (jobs[k].tw->R == rg && ksu == su) idx[m++] = k;
+            }
+            if (m == 0) continue;
+            K4Batch b;
+            b.n = m;
+            b.parity = parity;
+            for (int i = 0; i < m; ++i) {
+                const LockstepJob &q = jobs[idx[i]];
+                K4Job &j = b.j[i];
+                j.u = q.u;
+                j.dir = q.fb->dir;
+                j.uo = q.u_alt;
+                j.Im = q.Im;
+                j.J = q.fb->J;
+                j.gJ = q.fb->gJ;
+                j.h = q.h;
+                batch_taps(j.t, *q.tw);
+                j.lr = q.p->lr;
+                j.c_lp = q.p->c_lp;
+            }
+            FA_CUDA_TRY(dispatch_k4_batch(rg, su != 0, b, jobs, idx, s));
+            note_launch();
+        }
     return FA_OK;
 }
 

@@ -241,6 +241,83 @@ fa_status register_check(const fa_vol *fixed, const fa_vol *moving, const fa_par
     return FA_OK;
 }
 
+// Start of a registration: 16-bit images widened once (exactly) and the
+// pyramid (once per level); If0/Im0 receive the FP32 full-resolution images.
+static fa_status registration_begin(Plan &P, const fa_vol *fixed, const fa_vol *moving,
+                                    const fa_params *p, const float **If0, const float **Im0,
+                                    cudaStream_t s) {
+    const Dims full = P.full;
+    *If0 = (const float *)fixed->data;
+    *Im0 = (const float *)moving->data;
+    if (p->storage != FA_F32) {
+        FA_CUDA_TRY(launch_widen(fixed->data, p->storage, P.If0, full.N(), s));
+        FA_CUDA_TRY(launch_widen(moving->data, p->storage, P.Im0, full.N(), s));
+        *If0 = P.If0;
+        *Im0 = P.Im0;
+    }
+    FA_CUDA_TRY(launch_header_reset(P.h, s));
+    for (int l = 0; l < p->n_levels; ++l) {
+        if (p->scales[l] == 1) continue;
+        FA_CUDA_TRY(launch_pyramid_level(*If0, full, p->scales[l], P.If[l], P.lvl[l], P.t1, P.t2, s));
+        FA_CUDA_TRY(launch_pyramid_level(*Im0, full, p->scales[l], P.Im[l], P.lvl[l], P.t1, P.t2, s));
+    }
+    return FA_OK;
+}
+
+// Start of level l: the initial (or handed-off) u, m, nu in slot *cur, the
+// level's image maxima, the MI range and the fused path's set-up.
+static fa_status level_begin(Plan &P, const fa_params *p, int l, const float *u_init,
+                             const float *If, const float *Im, int *cur, cudaStream_t s) {
+    const Dims d = P.lvl[l];
+    if (l == 0) {
+        size_t b = sizeof(float) * 3 * d.N();
+        if (u_init) {  // start from a given displacement of the input grid
+            float sc[3];
+            handoff_scales(P.full, d, 1, sc);
+            FA_CUDA_TRY(launch_resample(u_init, P.full, P.u[*cur], d, 3, sc, s));
+        } else {
+            FA_CUDA_TRY(cudaMemsetAsync(P.u[*cur], 0, b, s));
+        }
+        FA_CUDA_TRY(cudaMemsetAsync(P.m[*cur], 0, b, s));
+        FA_CUDA_TRY(cudaMemsetAsync(P.v[*cur], 0, b, s));
+    } else {
+        Dims c = P.lvl[l - 1];
+        float su[3], sm[3], sv[3];
+        handoff_scales(c, d, 1, su);
+        handoff_scales(c, d, -1, sm);
+        handoff_scales(c, d, -2, sv);
+        int nx = *cur ^ 1;
+        FA_CUDA_TRY(launch_resample(P.u[*cur], c, P.u[nx], d, 3, su, s));
+        FA_CUDA_TRY(launch_resample(P.m[*cur], c, P.m[nx], d, 3, sm, s));
+        FA_CUDA_TRY(launch_resample(P.v[*cur], c, P.v[nx], d, 3, sv, s));
+        *cur = nx;
+    }
+    // fixed-point scale of this level's images (max |I_f|, max |I_m|)
+    FA_CUDA_TRY(cudaMemsetAsync(P.h->absmax_bits, 0, sizeof(P.h->absmax_bits), s));
+    FA_CUDA_TRY(launch_absmax2(If, Im, d.N(), P.h, s));
+    if (p->loss == FA_LOSS_MI) FA_CUDA_TRY(launch_mi_range(If, Im, d.N(), P.mi, s));
+    if (p->mode == FA_MODE_FUSED)
+        FA_CUDA_TRY(fused_level_start(If, Im, P.u[*cur], d, p, P.h, P.fb, s));
+    return FA_OK;
+}
+
+// After the last level's iterations: the final loss and u_out.
+static fa_status registration_end(Plan &P, const fa_params *p, const float *If, const float *Im,
+                                  const float *u, fa_vol *u_out, float *final_loss_dev,
+                                  cudaStream_t s) {
+    const int L = p->n_levels - 1;
+    FA_TRY(final_loss(P, p, L, If, Im, u, final_loss_dev, s));
+    FA_CUDA_TRY(cudaMemcpyAsync(u_out->data, u, sizeof(float) * 3 * P.lvl[L].N(),
+                                cudaMemcpyDeviceToDevice, s));
+    return FA_OK;
+}
+
+// The images of level l (scale 1 is the full-resolution input itself).
+static const float *level_image(const Plan &P, const fa_params *p, int l, const float *const *lv,
+                                const float *full) {
+    return p->scales[l] == 1 ? full : lv[l];
+}
+
 // Everything one registration enqueues on stream s (arguments checked).
 static fa_status enqueue_registration(const fa_vol *fixed, const fa_vol *moving,
                                       const fa_params *p, const float *u_init, fa_vol *u_out,
@@ -250,58 +327,17 @@ static fa_status enqueue_registration(const fa_vol *fixed, const fa_vol *moving,
     const int L = p->n_levels - 1;
     Plan P;
     make_plan(P, ws, ws_bytes, full, p);
-    const float *If0 = (const float *)fixed->data, *Im0 = (const float *)moving->data;
-    if (p->storage != FA_F32) {  // 16-bit images: widened once, exactly
-        FA_CUDA_TRY(launch_widen(fixed->data, p->storage, P.If0, full.N(), s));
-        FA_CUDA_TRY(launch_widen(moving->data, p->storage, P.Im0, full.N(), s));
-        If0 = P.If0;
-        Im0 = P.Im0;
-    }
+    const float *If0, *Im0;
+    FA_TRY(registration_begin(P, fixed, moving, p, &If0, &Im0, s));
     GaussTaps tg, tw;
     make_gauss_taps(p->sigma_grad, &tg);
     make_gauss_taps(p->sigma_warp, &tw);
-    FA_CUDA_TRY(launch_header_reset(P.h, s));
-    // pyramid (once per level)
-    for (int l = 0; l < p->n_levels; ++l) {
-        if (p->scales[l] == 1) continue;
-        FA_CUDA_TRY(launch_pyramid_level(If0, full, p->scales[l], P.If[l], P.lvl[l], P.t1, P.t2, s));
-        FA_CUDA_TRY(launch_pyramid_level(Im0, full, p->scales[l], P.Im[l], P.lvl[l], P.t1, P.t2, s));
-    }
     int cur = 0, t = 0;
     for (int l = 0; l < p->n_levels; ++l) {
-        Dims d = P.lvl[l];
-        const float *If = p->scales[l] == 1 ? If0 : P.If[l];
-        const float *Im = p->scales[l] == 1 ? Im0 : P.Im[l];
-        if (l == 0) {
-            size_t b = sizeof(float) * 3 * d.N();
-            if (u_init) {  // start from a given displacement of the input grid
-                float sc[3];
-                handoff_scales(full, d, 1, sc);
-                FA_CUDA_TRY(launch_resample(u_init, full, P.u[cur], d, 3, sc, s));
-            } else {
-                FA_CUDA_TRY(cudaMemsetAsync(P.u[cur], 0, b, s));
-            }
-            FA_CUDA_TRY(cudaMemsetAsync(P.m[cur], 0, b, s));
-            FA_CUDA_TRY(cudaMemsetAsync(P.v[cur], 0, b, s));
-        } else {
-            Dims c = P.lvl[l - 1];
-            float su[3], sm[3], sv[3];
-            handoff_scales(c, d, 1, su);
-            handoff_scales(c, d, -1, sm);
-            handoff_scales(c, d, -2, sv);
-            int nx = cur ^ 1;
-            FA_CUDA_TRY(launch_resample(P.u[cur], c, P.u[nx], d, 3, su, s));
-            FA_CUDA_TRY(launch_resample(P.m[cur], c, P.m[nx], d, 3, sm, s));
-            FA_CUDA_TRY(launch_resample(P.v[cur], c, P.v[nx], d, 3, sv, s));
-            cur = nx;
-        }
-        // fixed-point scale of this level's images (max |I_f|, max |I_m|)
-        FA_CUDA_TRY(cudaMemsetAsync(P.h->absmax_bits, 0, sizeof(P.h->absmax_bits), s));
-        FA_CUDA_TRY(launch_absmax2(If, Im, d.N(), P.h, s));
-        if (p->loss == FA_LOSS_MI) FA_CUDA_TRY(launch_mi_range(If, Im, d.N(), P.mi, s));
+        const float *If = level_image(P, p, l, P.If, If0);
+        const float *Im = level_image(P, p, l, P.Im, Im0);
+        FA_TRY(level_begin(P, p, l, l == 0 ? u_init : nullptr, If, Im, &cur, s));
         Timer tm{timer, l};
-        if (p->mode == FA_MODE_FUSED)
-            FA_CUDA_TRY(fused_level_start(If, Im, P.u[cur], d, p, P.h, P.fb, s));
         for (int it = 0; it < p->iters[l]; ++it) {
             ++t;
             if (p->mode == FA_MODE_PLAIN) {
@@ -323,11 +359,79 @@ static fa_status enqueue_registration(const fa_vol *fixed, const fa_vol *moving,
                 P.u[cur ^ 1] = tmpu;
             }
         }
-        if (l == L) {
-            FA_TRY(final_loss(P, p, l, If, Im, P.u[cur], final_loss_dev, s));
-            FA_CUDA_TRY(cudaMemcpyAsync(u_out->data, P.u[cur], sizeof(float) * 3 * d.N(),
-                                        cudaMemcpyDeviceToDevice, s));
+        if (l == L) FA_TRY(registration_end(P, p, If, Im, P.u[cur], u_out, final_loss_dev, s));
+    }
+    return FA_OK;
+}
+
+__global__ void k_status_copy(const WsHeader *h, unsigned *out) { *out = h->status; }
+
+// Lockstep: n registrations advance level by level and iteration by
+// iteration together; job k works in the workspace slice ws + k * slot.
+// Set-up, hand-off and final loss run per job; every iteration is one
+// fused_iteration_lockstep over all jobs.  The jobs were checked with
+// lockstep_check.
+static fa_status enqueue_lockstep(int n, const LockstepArgs *a, char *ws, size_t slot,
+                                  cudaStream_t s) {
+    std::vector<Plan> P((size_t)n);
+    std::vector<const float *> If0((size_t)n), Im0((size_t)n);
+    std::vector<GaussTaps> tg((size_t)n), tw((size_t)n);
+    std::vector<int> cur((size_t)n, 0);
+    std::vector<LockstepJob> jobs((size_t)n);
+    for (int k = 0; k < n; ++k) {
+        const fa_params *p = a[k].p;
+        make_plan(P[k], ws + slot * (size_t)k, slot,
+                  Dims{a[k].fixed->D, a[k].fixed->H, a[k].fixed->W}, p);
+        FA_TRY(registration_begin(P[k], a[k].fixed, a[k].moving, p, &If0[k], &Im0[k], s));
+        make_gauss_taps(p->sigma_grad, &tg[k]);
+        make_gauss_taps(p->sigma_warp, &tw[k]);
+    }
+    const fa_params *p0 = a[0].p;
+    const int L = p0->n_levels - 1;
+    int t = 0;
+    for (int l = 0; l < p0->n_levels; ++l) {
+        for (int k = 0; k < n; ++k) {
+            const fa_params *p = a[k].p;
+            LockstepJob &j = jobs[(size_t)k];
+            j.d = P[k].lvl[l];
+            j.If = level_image(P[k], p, l, P[k].If, If0[k]);
+            j.Im = level_image(P[k], p, l, P[k].Im, Im0[k]);
+            j.fb = &P[k].fb;
+            j.h = P[k].h;
+            j.p = p;
+            j.tg = &tg[k];
+            j.tw = &tw[k];
+            FA_TRY(level_begin(P[k], p, l, nullptr, j.If, j.Im, &cur[k], s));
         }
+        for (int it = 0; it < p0->iters[l]; ++it) {
+            ++t;
+            for (int k = 0; k < n; ++k) {
+                LockstepJob &j = jobs[(size_t)k];
+                const int c = cur[k];
+                j.u = P[k].u[c];
+                j.u_alt = P[k].u[c ^ 1];
+                j.m = P[k].m[c];
+                j.v = P[k].v[c];
+            }
+            FA_TRY(fused_iteration_lockstep(n, jobs.data(), t, s));
+            for (int k = 0; k < n; ++k) {  // the compose wrote u_alt: swap roles
+                const int c = cur[k];
+                float *tmpu = P[k].u[c];
+                P[k].u[c] = P[k].u[c ^ 1];
+                P[k].u[c ^ 1] = tmpu;
+            }
+        }
+        if (l == L)
+            for (int k = 0; k < n; ++k) {
+                const LockstepJob &j = jobs[(size_t)k];
+                FA_TRY(registration_end(P[k], a[k].p, j.If, j.Im, P[k].u[cur[k]], a[k].u_out,
+                                        a[k].final_loss_dev, s));
+                if (a[k].status_dev) {
+                    k_status_copy<<<1, 1, 0, s>>>(P[k].h, a[k].status_dev);
+                    note_launch();
+                    FA_CUDA_TRY(cudaGetLastError());
+                }
+            }
     }
     return FA_OK;
 }
@@ -503,6 +607,81 @@ fa_status register_impl(const fa_vol *fixed, const fa_vol *moving, const fa_para
                                cudaMemcpyDeviceToHost));
         return fa_ws_status(ws, s);
     }
+    return FA_OK;
+}
+
+fa_status lockstep_check(int n, const LockstepArgs *a) {
+    if (n < 1 || n > kMaxLockstepJobs) {
+        set_error("lockstep: 1..%d jobs at a time (got %d)", kMaxLockstepJobs, n);
+        return FA_ERR_INVALID;
+    }
+    const fa_params *p0 = a[0].p;
+    for (int k = 0; k < n; ++k) {
+        const fa_params *p = a[k].p;
+        if (p->mode != FA_MODE_FUSED || p->loss != FA_LOSS_LNCC || p->use_jac) {
+            set_error("lockstep: job %d: needs the fused LNCC path without use_jac", k);
+            return FA_ERR_UNSUPPORTED;
+        }
+        bool same = p->n_levels == p0->n_levels && p->window == p0->window &&
+                    p->beta1 == p0->beta1 && p->beta2 == p0->beta2 &&
+                    p->adam_eps == p0->adam_eps;
+        for (int l = 0; same && l < p0->n_levels; ++l)
+            same = p->scales[l] == p0->scales[l] && p->iters[l] == p0->iters[l];
+        if (!same) {
+            set_error("lockstep: job %d: every job needs the same levels, iterations, window "
+                      "and Adam constants", k);
+            return FA_ERR_UNSUPPORTED;
+        }
+        GaussTaps tg, tw;
+        make_gauss_taps(p->sigma_grad, &tg);
+        make_gauss_taps(p->sigma_warp, &tw);
+        if (tg.R > kMaxFusedRadius || tw.R > kMaxFusedRadius) {
+            set_error("lockstep: job %d: Gaussian radius above %d (sigma above %g)", k,
+                      kMaxFusedRadius, (double)kMaxFusedRadius / 3.0);
+            return FA_ERR_UNSUPPORTED;
+        }
+    }
+    return FA_OK;
+}
+
+fa_status register_lockstep(int n, const LockstepArgs *a, void *ws, size_t slot, cudaStream_t s) {
+    FA_TRY(lockstep_check(n, a));
+    bool graph = true;
+    for (int k = 0; k < n; ++k) graph = graph && a[k].p->graph;
+    if (!graph) return enqueue_lockstep(n, a, (char *)ws, slot, s);
+    int dev = 0;
+    FA_CUDA_TRY(cudaGetDevice(&dev));
+    std::string key("lockstep");
+    for (int k = 0; k < n; ++k) {
+        key += graph_key(dev, a[k].fixed, a[k].moving, a[k].p, nullptr, a[k].u_out,
+                         a[k].final_loss_dev, (char *)ws + slot * (size_t)k, slot, nullptr);
+        key.append((const char *)&a[k].status_dev, sizeof(a[k].status_dev));
+    }
+    unsigned long long kernels = 0;
+    int timer_count = 0;
+    cudaGraphExec_t exec = graph_find(key, &kernels, &timer_count);
+    if (!exec) {
+        cudaStream_t cs;
+        FA_CUDA_TRY(capture_stream(&cs));
+        FA_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        const unsigned long long k0 = launches_so_far();
+        const fa_status st = enqueue_lockstep(n, a, (char *)ws, slot, cs);
+        kernels = launches_so_far() - k0;
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(cs, &g);
+        if (st != FA_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        FA_CUDA_TRY(ce);
+        const cudaError_t ie = cudaGraphInstantiate(&exec, g, 0);
+        cudaGraphDestroy(g);
+        FA_CUDA_TRY(ie);
+        graph_store(key, exec, kernels, 0);
+    } else {
+        note_launches(kernels);
+    }
+    FA_CUDA_TRY(cudaGraphLaunch(exec, s));
     return FA_OK;
 }
 

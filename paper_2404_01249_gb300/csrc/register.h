@@ -47,6 +47,39 @@ int fused_tile_choices(int32_t *out, int capacity);
 cudaError_t fused_lncc_forward_only(const float *If, const FusedBuffers &fb, Dims d, int window,
                                     float cc_eps, WsHeader *h, cudaStream_t s);
 
+// One iteration of many registrations that advance together (lockstep): each
+// fused kernel runs as one launch over the tiles of every job (K3 and K4 one
+// launch per Gaussian radius and compose variant).  The jobs share the loss
+// (LNCC), the window, the Adam constants and the step counter t; each Gaussian
+// is at most kMaxFusedRadius wide.
+constexpr int kMaxLockstepJobs = 64;
+constexpr int kMaxFusedRadius = 6;
+struct LockstepJob {
+    Dims d;
+    const float *If, *Im;
+    float *u, *u_alt, *m, *v;  // u_alt receives the updated displacement
+    FusedBuffers *fb;
+    WsHeader *h;
+    const fa_params *p;
+    const GaussTaps *tg, *tw;
+};
+fa_status fused_iteration_lockstep(int n, const LockstepJob *jobs, int t, cudaStream_t s);
+
+// One job of a lockstep call (arguments of fa_register plus a status word).
+struct LockstepArgs {
+    const fa_vol *fixed, *moving;
+    const fa_params *p;
+    fa_vol *u_out;
+    float *final_loss_dev;  // may be NULL
+    uint32_t *status_dev;   // may be NULL
+};
+// FA_OK when the jobs (each already checked with register_check) can advance
+// together, else FA_ERR_UNSUPPORTED with the reason in fa_last_error.
+fa_status lockstep_check(int n, const LockstepArgs *a);
+// Enqueues n <= kMaxLockstepJobs checked jobs; job k works in ws + k * slot.
+// Records the call as a CUDA graph and replays it when every job asks for it.
+fa_status register_lockstep(int n, const LockstepArgs *a, void *ws, size_t slot, cudaStream_t s);
+
 // Argument checks of fa_register (no launch).
 fa_status register_check(const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
                          const fa_vol *u_out);

@@ -47,7 +47,8 @@ EXPORTED = ["fa_params_default", "fa_status_str", "fa_last_error", "fa_warp",
             "fa_register_symmetric", "fa_symmetric_loss_grad_workspace_size",
             "fa_symmetric_loss_grad", "fa_mi_workspace_size", "fa_mi_fwd_bwd",
             "fa_rigid_register", "fa_register_svf_workspace_size", "fa_register_svf",
-            "fa_svf_loss_grad", "fa_selftest_wait_timeout"]
+            "fa_svf_loss_grad", "fa_selftest_wait_timeout",
+            "fa_register_lockstep_workspace_size", "fa_register_batched_lockstep"]
 
 
 class FAError(RuntimeError):
@@ -117,6 +118,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                     ctypes.POINTER(KernelTimer)]),
         "fa_register_batched_workspace_size": (sz, [i32, V, i32, P, i32]),
         "fa_register_batched": (i32, [i32, V, V, i32, P, V, vp, vp, i32, vp, sz, vp]),
+        "fa_register_lockstep_workspace_size": (sz, [i32, V, i32, P, i32]),
+        "fa_register_batched_lockstep": (i32, [i32, V, V, i32, P, V, vp, vp, i32, vp, sz, vp]),
         "fa_warp_lncc_adjoint_workspace_size": (sz, [i32, i32, i32]),
         "fa_warp_lncc_adjoint": (i32, [V, V, V, i32, f32, vp, V, V, V, vp, sz, vp]),
         "fa_autotune": (i32, [i32, i32, i32, P, vp, sz, vp]),
@@ -361,15 +364,10 @@ def _vol_struct(t: torch.Tensor, C: int, half_ok: bool = False) -> Vol:
     return Vol(t.data_ptr(), _DTYPES[t.dtype], C, shp[1], shp[2], shp[3])
 
 
-def fa_register_batched(fixed: list, moving: list, params: list, concurrency: int = 4,
-                        ws: Optional[torch.Tensor] = None, sync: bool = True):
-    """Registers every pair under every parameter set (job = pair * len(params)
-    + set) concurrently.  Returns a list of dicts (u, loss tensor, final_loss
-    and status when sync=True), one per job."""
+def _batched_call(size_fn, run_fn, fixed, moving, params, count, ws, sync):
     n_pairs, n_cfg = len(fixed), len(params)
     if len(moving) != n_pairs:
         raise ValueError("fixed and moving need the same number of volumes")
-    lib = load()
     dev = fixed[0].device
     fv = (Vol * n_pairs)(*[_vol_struct(t, 1, True) for t in fixed])
     mv = (Vol * n_pairs)(*[_vol_struct(t, 1, True) for t in moving])
@@ -379,9 +377,9 @@ def fa_register_batched(fixed: list, moving: list, params: list, concurrency: in
     for c in cs:
         c.storage = _DTYPES[fixed[0].dtype]
     pc = (Params * n_cfg)(*cs)
-    need = lib.fa_register_batched_workspace_size(n_pairs, fv, n_cfg, pc, concurrency)
+    need = size_fn(n_pairs, fv, n_cfg, pc, count)
     if need == 0:
-        raise FAError(FA_ERR_INVALID, lib.fa_last_error().decode())
+        raise FAError(FA_ERR_INVALID, load().fa_last_error().decode())
     ws = ws if ws is not None else workspace(need, dev)
     outs = []
     for i in range(n_pairs):
@@ -393,8 +391,8 @@ def fa_register_batched(fixed: list, moving: list, params: list, concurrency: in
     uv = (Vol * len(outs))(*[_vol_struct(t, 3) for t in outs])
     loss = torch.empty(len(outs), device=dev)
     status = torch.zeros(len(outs), dtype=torch.int32, device=dev)
-    _check(lib.fa_register_batched(n_pairs, fv, mv, n_cfg, pc, uv, _ptr(loss), _ptr(status),
-                                   concurrency, _ptr(ws), ws.numel(), _stream()))
+    _check(run_fn(n_pairs, fv, mv, n_cfg, pc, uv, _ptr(loss), _ptr(status), count, _ptr(ws),
+                  ws.numel(), _stream()))
     res = [dict(u=u, loss=loss[j]) for j, u in enumerate(outs)]
     if sync:
         torch.cuda.current_stream().synchronize()
@@ -402,6 +400,28 @@ def fa_register_batched(fixed: list, moving: list, params: list, concurrency: in
         for j, r in enumerate(res):
             r["final_loss"], r["status"] = lh[j], sh[j]
     return res
+
+
+def fa_register_batched(fixed: list, moving: list, params: list, concurrency: int = 4,
+                        ws: Optional[torch.Tensor] = None, sync: bool = True):
+    """Registers every pair under every parameter set (job = pair * len(params)
+    + set) concurrently.  Returns a list of dicts (u, loss tensor, final_loss
+    and status when sync=True), one per job."""
+    lib = load()
+    return _batched_call(lib.fa_register_batched_workspace_size, lib.fa_register_batched, fixed,
+                         moving, params, concurrency, ws, sync)
+
+
+def fa_register_batched_lockstep(fixed: list, moving: list, params: list,
+                                 jobs_per_wave: int = 64, ws: Optional[torch.Tensor] = None,
+                                 sync: bool = True):
+    """The jobs of fa_register_batched advancing together: each iteration is
+    one launch of every fused kernel over all jobs of a wave of
+    `jobs_per_wave` jobs.  Same results and return value."""
+    lib = load()
+    return _batched_call(lib.fa_register_lockstep_workspace_size,
+                         lib.fa_register_batched_lockstep, fixed, moving, params, jobs_per_wave,
+                         ws, sync)
 
 
 def fa_warp_lncc_adjoint(fixed, moving, u, window: int = 5, cc_eps: float = 1e-5,

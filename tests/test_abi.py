@@ -109,3 +109,37 @@ def test_batched_validation_before_launch(lib):
     assert st == 2
     assert b"pair 1, parameter set 0" in lib.fa_last_error()
     assert lib.fa_register_batched(0, fx, fx, 1, cfgs, uo, None, None, 2, None, 0, None) == 1
+
+
+def test_lockstep_validation_before_launch(lib):
+    from paper_2404_01249_gb300 import fa
+    a = 1 << 20
+    p = fa.RegParams(scales=(2, 1), iters=(3, 2)).to_c()
+    fx = (fa.Vol * 2)(fa.Vol(a, 0, 1, 8, 9, 10), fa.Vol(a, 0, 1, 12, 6, 4))
+    uo = (fa.Vol * 2)(fa.Vol(a, 0, 3, 8, 9, 10), fa.Vol(a, 0, 3, 12, 6, 4))
+    cfgs = (fa.Params * 1)(p)
+    size = lib.fa_register_lockstep_workspace_size
+    run = lib.fa_register_batched_lockstep
+    assert size(2, fx, 1, cfgs, 0) == 0 and size(2, fx, 1, cfgs, 65) == 0
+    one = lib.fa_register_workspace_size(8, 9, 10, ctypes.byref(p))
+    two = lib.fa_register_workspace_size(12, 6, 4, ctypes.byref(p))
+    assert size(2, fx, 1, cfgs, 64) >= 2 * max(one, two)
+    assert size(2, fx, 1, cfgs, 1) < size(2, fx, 1, cfgs, 2)
+    # jobs that cannot advance together are refused before anything runs
+    for bad in (fa.RegParams(scales=(2, 1), iters=(3, 2), loss="mse"),
+                fa.RegParams(scales=(2, 1), iters=(3, 2), mode="plain"),
+                fa.RegParams(scales=(2, 1), iters=(3, 2), use_jac=True),
+                fa.RegParams(scales=(2, 1), iters=(4, 2)),
+                fa.RegParams(scales=(2, 1), iters=(3, 2), window=3),
+                fa.RegParams(scales=(2, 1), iters=(3, 2), sigma_grad=2.5)):
+        two_cfgs = (fa.Params * 2)(p, bad.to_c())
+        uo4 = (fa.Vol * 4)(*(list(uo)[:1] * 2 + list(uo)[1:] * 2))
+        assert run(2, fx, fx, 2, two_cfgs, uo4, None, None, 64, None, 0, None) == 7, bad
+    # a wave of one job is always compatible: then the missing workspace is reported
+    ok = (fa.Params * 2)(p, fa.RegParams(scales=(2, 1), iters=(3, 2), loss="mse").to_c())
+    uo4 = (fa.Vol * 4)(*(list(uo)[:1] * 2 + list(uo)[1:] * 2))
+    assert run(2, fx, fx, 2, ok, uo4, None, None, 1, None, 0, None) == 7  # MSE never in lockstep
+    same = (fa.Params * 2)(p, fa.RegParams(scales=(2, 1), iters=(3, 2), lr=0.25,
+                                           sigma_grad=2.0).to_c())
+    assert run(2, fx, fx, 2, same, uo4, None, None, 64, None, 0, None) == 8  # workspace
+    assert run(2, fx, fx, 2, same, uo4, None, None, 0, None, 0, None) == 1
