@@ -1,0 +1,421 @@
+// Lockstep batches of the fused kernels: many registrations advance together,
+// one launch of each fused kernel per iteration over the tiles of every job.
+#include "fused_kernels.cuh"
+
+namespace fa {
+
+namespace {
+
+// ------------------------------------------------------------ lockstep batches
+// Many registrations advance together: one launch of a fused kernel covers the
+// tiles of every job in the launch's table.  CTA b belongs to the job k with
+// first[k] <= b < first[k + 1]; its tile inside that job's grid is
+// b - first[k] in x-fastest order.  The table travels in the kernel's
+// parameter space (read through the constant cache; every thread of a CTA
+// reads the same entry).  Jobs take the per-thread copy variant (cp.async):
+// their grids are mostly of uneven width, and tensor maps would not fit the
+// parameter space.
+struct BGeom {
+    int D, H, W, TZ, gx, gy;
+};
+struct BTaps {
+    float w[2 * kMaxFusedRG + 1];
+};
+struct K1Job {
+    const float *If, *J;
+    const long long *SI;
+    const float *varI;
+    float *coef;
+    WsHeader *h;
+    BGeom g;
+    float cc_eps;
+};
+struct K1Batch {
+    int n, bits, window, write_coef;
+    int first[kMaxLockstepJobs + 1];
+    K1Job j[kMaxLockstepJobs];
+};
+struct K2Job {
+    const float *If, *gJ, *J, *coef;
+    float *g;
+    WsHeader *h;
+    BGeom geo;
+};
+struct K2Batch {
+    int n, cbits;
+    int first[kMaxLockstepJobs + 1];
+    K2Job j[kMaxLockstepJobs];
+};
+struct K3Job {
+    const float *g;
+    float *m, *v, *dir;
+    WsHeader *h;
+    BGeom geo;
+    BTaps t;
+};
+struct K3Batch {
+    int n, parity;
+    AdamConsts ac;
+    int first[kMaxLockstepJobs + 1];
+    K3Job j[kMaxLockstepJobs];
+};
+struct K4Job {
+    const float *u, *dir;
+    float *uo;
+    const float *Im;
+    float *J, *gJ;
+    WsHeader *h;
+    BGeom geo;
+    BTaps t;
+    float lr, c_lp;
+};
+struct K4Batch {
+    int n, parity;
+    int first[kMaxLockstepJobs + 1];
+    K4Job j[kMaxLockstepJobs];
+};
+static_assert(sizeof(K4Batch) < 16384 && sizeof(K3Batch) < 16384 && sizeof(K1Batch) < 16384,
+              "a lockstep table must fit the kernel parameter space");
+
+// The job of CTA b: the largest k with first[k] <= b (first[0] = 0).
+__device__ __forceinline__ int batch_job(const int *first, int n, int b) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (first[mid] <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void batch_tile(const BGeom &g, int t, int &bx, int &by, int &bz) {
+    bx = t % g.gx;
+    const int r = t / g.gx;
+    by = r % g.gy;
+    bz = r / g.gy;
+}
+
+template <int R>
+__global__ void __launch_bounds__(FX *K1_NW) k_lncc_fwd_batch(const __grid_constant__ K1Batch b) {
+    const int k = batch_job(b.first, b.n, (int)blockIdx.x);
+    const K1Job &j = b.j[k];
+    int bx, by, bz;
+    batch_tile(j.g, (int)blockIdx.x - b.first[k], bx, by, bz);
+    lncc_fwd_body<R, K1_NW, K1_OPT, K1_ST_CP, false>(nullptr, j.If, j.J, j.SI, j.varI, j.coef, j.h,
+                                                     j.g.D, j.g.H, j.g.W, j.g.TZ, b.bits,
+                                                     j.cc_eps, b.window, b.write_coef, bx, by, bz);
+}
+
+template <int R>
+__global__ void __launch_bounds__(FX *K2_NW) k_lncc_grad_batch(const __grid_constant__ K2Batch b) {
+    const int k = batch_job(b.first, b.n, (int)blockIdx.x);
+    const K2Job &j = b.j[k];
+    int bx, by, bz;
+    batch_tile(j.geo, (int)blockIdx.x - b.first[k], bx, by, bz);
+    lncc_grad_body<R, K2_NW, K2_OPT, K2_ST_CP, false>(nullptr, j.If, j.gJ, j.J, j.coef, j.h, j.g,
+                                                      j.geo.D, j.geo.H, j.geo.W, j.geo.TZ, b.cbits,
+                                                      bx, by, bz);
+}
+
+template <int RG>
+__global__ void __launch_bounds__(FX *K3_NW) k_smooth_adam_batch(const __grid_constant__ K3Batch b) {
+    const int k = batch_job(b.first, b.n, (int)blockIdx.x);
+    const K3Job &j = b.j[k];
+    int bx, by, bz;
+    batch_tile(j.geo, (int)blockIdx.x - b.first[k], bx, by, bz);
+    smooth_adam_body<RG, K3_NW, K3_OPT, K3_ST_CP, false>(nullptr, j.g, j.m, j.v, j.dir, j.h,
+                                                         j.geo.D, j.geo.H, j.geo.W, j.geo.TZ, j.t,
+                                                         b.ac, b.parity, bx, by, bz);
+}
+
+template <int RG, bool SU>
+__global__ void __launch_bounds__(FX *K4_NW) k_compose_batch(const __grid_constant__ K4Batch b) {
+    const int k = batch_job(b.first, b.n, (int)blockIdx.x);
+    const K4Job &j = b.j[k];
+    int bx, by, bz;
+    batch_tile(j.geo, (int)blockIdx.x - b.first[k], bx, by, bz);
+    compose_body<RG, K4_NW, K4_OPT, SU, K4_ST_CP, false>(nullptr, j.u, j.dir, j.uo, j.Im, j.J,
+                                                         j.gJ, j.h, j.geo.D, j.geo.H, j.geo.W,
+                                                         j.geo.TZ, j.t, j.lr, j.c_lp, b.parity, bx,
+                                                         by, bz);
+}
+
+// Slab depth of one job in a lockstep launch: the job gets the share of the
+// GPU's resident CTA slots that its voxels are of the launch's voxels, and TZ
+// minimises (waves x planes per CTA) on that share.
+int batch_tz(Dims d, int tiles_xy, int halo, int occ, long long vox, long long total_vox) {
+    const long long slots = (long long)num_sms() * (occ > 0 ? occ : 1);
+    long long share = total_vox > 0 ? slots * vox / total_vox : slots;
+    if (share < 1) share = 1;
+    int best = d.D;
+    long long bestcost = -1;
+    for (int tz = 1; tz <= d.D && tz <= 64; ++tz) {
+        const long long ctas = (long long)tiles_xy * ((d.D + tz - 1) / tz);
+        const long long waves = (ctas + share - 1) / share;
+        const long long cost = waves * (tz + 2 * halo);
+        if (bestcost < 0 || cost < bestcost) {
+            bestcost = cost;
+            best = tz;
+        }
+    }
+    return best;
+}
+
+// Fills a job's tile geometry for a kernel with `ty` rows per CTA and returns
+// its CTA count.
+int batch_geom(BGeom &g, Dims d, int ty, int halo, int occ, long long total_vox) {
+    g.D = d.D;
+    g.H = d.H;
+    g.W = d.W;
+    g.gx = (d.W + FX - 1) / FX;
+    g.gy = (d.H + ty - 1) / ty;
+    g.TZ = batch_tz(d, g.gx * g.gy, halo, occ, d.N(), total_vox);
+    return g.gx * g.gy * ((d.D + g.TZ - 1) / g.TZ);
+}
+
+void batch_taps(BTaps &b, const GaussTaps &t) {
+    for (int k = 0; k < 2 * kMaxFusedRG + 1; ++k) b.w[k] = k <= 2 * t.R ? t.w[k] : 0.0f;
+}
+
+template <class K, class B>
+cudaError_t launch_batch(K kern, const B &b, int nw, size_t smem, cudaStream_t s) {
+    LaunchGeom g;
+    g.grid = dim3((unsigned)b.first[b.n]);
+    g.block = dim3(FX, nw);
+    g.tz = 0;
+    return launch_pdl(kern, g, smem, s, b);
+}
+
+template <int R>
+cudaError_t launch_k1_batch(K1Batch &b, const LockstepJob *jobs, cudaStream_t s) {
+    using SC = K1S<R, K1_NW, K1_OPT, K1_ST_CP>;
+    auto kern = k_lncc_fwd_batch<R>;
+    static const int occ = prepare(kern, SC::bytes, SC::NT);
+    long long tot = 0;
+    for (int k = 0; k < b.n; ++k) tot += jobs[k].d.N();
+    b.first[0] = 0;
+    for (int k = 0; k < b.n; ++k)
+        b.first[k + 1] = b.first[k] + batch_geom(b.j[k].g, jobs[k].d, SC::TY, R, occ, tot);
+    return launch_batch(kern, b, SC::NT / FX, SC::bytes, s);
+}
+
+template <int R>
+cudaError_t launch_k2_batch(K2Batch &b, const LockstepJob *jobs, cudaStream_t s) {
+    using SC = K2S<R, K2_NW, K2_OPT, K2_ST_CP>;
+    auto kern = k_lncc_grad_batch<R>;
+    static const int occ = prepare(kern, SC::bytes, SC::NT);
+    long long tot = 0;
+    for (int k = 0; k < b.n; ++k) tot += jobs[k].d.N();
+    b.first[0] = 0;
+    for (int k = 0; k < b.n; ++k)
+        b.first[k + 1] = b.first[k] + batch_geom(b.j[k].geo, jobs[k].d, SC::TY, R, occ, tot);
+    return launch_batch(kern, b, SC::NT / FX, SC::bytes, s);
+}
+
+// jobs[idx[0..b.n)] are the launch's jobs
+template <int RG>
+cudaError_t launch_k3_batch(K3Batch &b, const LockstepJob *jobs, const int *idx, cudaStream_t s) {
+    using SC = K3S<RG, K3_NW, K3_OPT, K3_ST_CP>;
+    auto kern = k_smooth_adam_batch<RG>;
+    static const int occ = prepare(kern, SC::bytes, SC::NT);
+    long long tot = 0;
+    for (int k = 0; k < b.n; ++k) tot += jobs[idx[k]].d.N();
+    b.first[0] = 0;
+    for (int k = 0; k < b.n; ++k)
+        b.first[k + 1] = b.first[k] + batch_geom(b.j[k].geo, jobs[idx[k]].d, SC::TY, RG, occ, tot);
+    return launch_batch(kern, b, SC::NT / FX, SC::bytes, s);
+}
+
+template <int RG, bool SU>
+cudaError_t launch_k4_batch(K4Batch &b, const LockstepJob *jobs, const int *idx, cudaStream_t s) {
+    using SC = K4S<RG, K4_NW, K4_OPT, SU, K4_ST_CP>;
+    auto kern = k_compose_batch<RG, SU>;
+    static const int occ = prepare(kern, SC::bytes, SC::NT);
+    long long tot = 0;
+    for (int k = 0; k < b.n; ++k) tot += jobs[idx[k]].d.N();
+    b.first[0] = 0;
+    for (int k = 0; k < b.n; ++k)
+        b.first[k + 1] = b.first[k] + batch_geom(b.j[k].geo, jobs[idx[k]].d, SC::TY, RG, occ, tot);
+    return launch_batch(kern, b, SC::NT / FX, SC::bytes, s);
+}
+
+#define FA_CASE(n, call)      \
+    case n: {                 \
+        constexpr int RR = n; \
+        return call;          \
+    }
+
+cudaError_t dispatch_k1_batch(int R, K1Batch &b, const LockstepJob *jobs, cudaStream_t s) {
+    switch (R) {
+        FA_CASE(0, launch_k1_batch<RR>(b, jobs, s))
+        FA_CASE(1, launch_k1_batch<RR>(b, jobs, s))
+        FA_CASE(2, launch_k1_batch<RR>(b, jobs, s))
+        FA_CASE(3, launch_k1_batch<RR>(b, jobs, s))
+        FA_CASE(4, launch_k1_batch<RR>(b, jobs, s))
+        FA_CASE(5, launch_k1_batch<RR>(b, jobs, s))
+        FA_CASE(6, launch_k1_batch<RR>(b, jobs, s))
+        FA_CASE(7, launch_k1_batch<RR>(b, jobs, s))
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t dispatch_k2_batch(int R, K2Batch &b, const LockstepJob *jobs, cudaStream_t s) {
+    switch (R) {
+        FA_CASE(0, launch_k2_batch<RR>(b, jobs, s))
+        FA_CASE(1, launch_k2_batch<RR>(b, jobs, s))
+        FA_CASE(2, launch_k2_batch<RR>(b, jobs, s))
+        FA_CASE(3, launch_k2_batch<RR>(b, jobs, s))
+        FA_CASE(4, launch_k2_batch<RR>(b, jobs, s))
+        FA_CASE(5, launch_k2_batch<RR>(b, jobs, s))
+        FA_CASE(6, launch_k2_batch<RR>(b, jobs, s))
+        FA_CASE(7, launch_k2_batch<RR>(b, jobs, s))
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t dispatch_k3_batch(int RG, K3Batch &b, const LockstepJob *jobs, const int *idx,
+                              cudaStream_t s) {
+    switch (RG) {
+        FA_CASE(0, launch_k3_batch<RR>(b, jobs, idx, s))
+        FA_CASE(1, launch_k3_batch<RR>(b, jobs, idx, s))
+        FA_CASE(2, launch_k3_batch<RR>(b, jobs, idx, s))
+        FA_CASE(3, launch_k3_batch<RR>(b, jobs, idx, s))
+        FA_CASE(4, launch_k3_batch<RR>(b, jobs, idx, s))
+        FA_CASE(5, launch_k3_batch<RR>(b, jobs, idx, s))
+        FA_CASE(6, launch_k3_batch<RR>(b, jobs, idx, s))
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t dispatch_k4_batch(int RG, bool su, K4Batch &b, const LockstepJob *jobs, const int *idx,
+                              cudaStream_t s) {
+    if (su) {
+        switch (RG) {
+            FA_CASE(0, (launch_k4_batch<RR, true>(b, jobs, idx, s)))
+            FA_CASE(1, (launch_k4_batch<RR, true>(b, jobs, idx, s)))
+            FA_CASE(2, (launch_k4_batch<RR, true>(b, jobs, idx, s)))
+            FA_CASE(3, (launch_k4_batch<RR, true>(b, jobs, idx, s)))
+            FA_CASE(4, (launch_k4_batch<RR, true>(b, jobs, idx, s)))
+            FA_CASE(5, (launch_k4_batch<RR, true>(b, jobs, idx, s)))
+            FA_CASE(6, (launch_k4_batch<RR, true>(b, jobs, idx, s)))
+        }
+    } else {
+        switch (RG) {
+            FA_CASE(0, (launch_k4_batch<RR, false>(b, jobs, idx, s)))
+            FA_CASE(1, (launch_k4_batch<RR, false>(b, jobs, idx, s)))
+            FA_CASE(2, (launch_k4_batch<RR, false>(b, jobs, idx, s)))
+            FA_CASE(3, (launch_k4_batch<RR, false>(b, jobs, idx, s)))
+            FA_CASE(4, (launch_k4_batch<RR, false>(b, jobs, idx, s)))
+            FA_CASE(5, (launch_k4_batch<RR, false>(b, jobs, idx, s)))
+            FA_CASE(6, (launch_k4_batch<RR, false>(b, jobs, idx, s)))
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+#undef FA_CASE
+
+}  // namespace
+
+fa_status fused_iteration_lockstep(int n, const LockstepJob *jobs, int t, cudaStream_t s) {
+    if (n < 1 || n > kMaxLockstepJobs) {
+        set_error("lockstep iteration: 1..%d jobs per launch (got %d)", kMaxLockstepJobs, n);
+        return FA_ERR_INVALID;
+    }
+    const fa_params *p0 = jobs[0].p;
+    const int parity = t & 1, R = p0->window / 2;
+    {
+        K1Batch b;
+        b.n = n;
+        b.bits = lncc_image_bits(p0->window);
+        b.window = p0->window;
+        b.write_coef = 1;
+        for (int k = 0; k < n; ++k) {
+            const LockstepJob &q = jobs[k];
+            K1Job &j = b.j[k];
+            j.If = q.If;
+            j.J = q.fb->J;
+            j.SI = q.fb->sI;
+            j.varI = q.fb->varI;
+            j.coef = q.fb->coef;
+            j.h = q.h;
+            j.cc_eps = q.p->cc_eps;
+        }
+        FA_CUDA_TRY(dispatch_k1_batch(R, b, jobs, s));
+        note_launch();
+    }
+    {
+        K2Batch b;
+        b.n = n;
+        b.cbits = lncc_coef_bits(p0->window);
+        for (int k = 0; k < n; ++k) {
+            const LockstepJob &q = jobs[k];
+            K2Job &j = b.j[k];
+            j.If = q.If;
+            j.gJ = q.fb->gJ;
+            j.J = q.fb->J;
+            j.coef = q.fb->coef;
+            j.g = q.fb->g;
+            j.h = q.h;
+        }
+        FA_CUDA_TRY(dispatch_k2_batch(R, b, jobs, s));
+        note_launch();
+    }
+    int idx[kMaxLockstepJobs];
+    const AdamConsts ac = adam_consts(p0, t);
+    for (int rg = 0; rg <= kMaxFusedRG; ++rg) {
+        int m = 0;
+        for (int k = 0; k < n; ++k)
+            if (jobs[k].tg->R == rg) idx[m++] = k;
+        if (m == 0) continue;
+        K3Batch b;
+        b.n = m;
+        b.parity = parity;
+        b.ac = ac;
+        for (int i = 0; i < m; ++i) {
+            const LockstepJob &q = jobs[idx[i]];
+            K3Job &j = b.j[i];
+            j.g = q.fb->g;
+            j.m = q.m;
+            j.v = q.v;
+            j.dir = q.fb->dir;
+            j.h = q.h;
+            batch_taps(j.t, *q.tg);
+        }
+        FA_CUDA_TRY(dispatch_k3_batch(rg, b, jobs, idx, s));
+        note_launch();
+    }
+    for (int su = 0; su < 2; ++su)
+        for (int rg = 0; rg <= kMaxFusedRG; ++rg) {
+            int m = 0;
+            for (int k = 0; k < n; ++k) {
+                const fa_params *p = jobs[k].p;
+                const int ksu = (double)p->lr / (double)p->c_lp < 0.999 ? 1 : 0;
+                if (jobs[k].tw->R == rg && ksu == su) idx[m++] = k;
+            }
+            if (m == 0) continue;
+            K4Batch b;
+            b.n = m;
+            b.parity = parity;
+            for (int i = 0; i < m; ++i) {
+                const LockstepJob &q = jobs[idx[i]];
+                K4Job &j = b.j[i];
+                j.u = q.u;
+                j.dir = q.fb->dir;
+                j.uo = q.u_alt;
+                j.Im = q.Im;
+                j.J = q.fb->J;
+                j.gJ = q.fb->gJ;
+                j.h = q.h;
+                batch_taps(j.t, *q.tw);
+                j.lr = q.p->lr;
+                j.c_lp = q.p->c_lp;
+            }
+            FA_CUDA_TRY(dispatch_k4_batch(rg, su != 0, b, jobs, idx, s));
+            note_launch();
+        }
+    return FA_OK;
+}
+
+}  // namespace fa
