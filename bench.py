@@ -399,13 +399,14 @@ def run_batched(args):
     fa.load()
     shapes = synth.uneven_shapes(n=args.batched, seed=3000)
     pairs = [synth.voronoi_pair(shape=sh, seed=1000 + i) for i, sh in enumerate(shapes)]
-    fixed = [torch.from_numpy(p[0]).to(dev) for p in pairs]
-    moving = [torch.from_numpy(p[1]).to(dev) for p in pairs]
+    img_dtype = torch.bfloat16 if args.storage == "bf16" else torch.float32
+    fixed = [torch.from_numpy(p[0]).to(dev).to(img_dtype) for p in pairs]
+    moving = [torch.from_numpy(p[1]).to(dev).to(img_dtype) for p in pairs]
 
     def cfgs(mode):
         return [fa.RegParams(scales=WORKLOAD["scales"], iters=WORKLOAD["iters"], lr=lr,
                              sigma_grad=sg, sigma_warp=WORKLOAD["sigma_warp"],
-                             window=WORKLOAD["window"], mode=mode)
+                             window=WORKLOAD["window"], mode=mode, state=args.storage)
                 for lr in (0.25, 0.5, 1.0) for sg in (0.5, 1.0, 2.0)]
 
     n_cfg = len(cfgs("fused"))
@@ -460,6 +461,8 @@ def run_batched(args):
             "data": "synthetic",
             "config": {"workload": f"uneven_brain_batch_{len(shapes)}x{n_cfg}",
                        "schedule": args.schedule, "jobs_per_wave": wave,
+                       "storage": ("bf16 images and Adam moments, fp32 displacement and "
+                                   "arithmetic" if args.storage == "bf16" else "fp32"),
                        "concurrency": args.concurrency,
                        "shapes": [list(x) for x in shapes], "scales": list(WORKLOAD["scales"]),
                        "iters": list(WORKLOAD["iters"]), "lr": [0.25, 0.5, 1.0],
@@ -640,6 +643,8 @@ def main():
                     help="streams of --batched's streams and plain schedules")
     ap.add_argument("--schedule", default="lockstep", choices=["lockstep", "streams", "plain"],
                     help="timed form of --batched")
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16"],
+                    help="--batched: storage of the images and Adam moments")
     ap.add_argument("--workload", default="brain",
                     choices=["brain", "symmetric", "inverse", "svf", "mi", "use_jac", "affine",
                              "rigid"],

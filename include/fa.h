@@ -98,12 +98,26 @@ typedef struct {
                              use_jac) instead of the Jacobian-free dL/dphi; see
                              fa_jac_direction.  0 (default): Jacobian-free. */
     int32_t mi_bins;      /* histogram bins B of FA_LOSS_MI, 6..64 (default 32) */
+    int32_t state_storage; /* fa_dtype of the Adam moments m and nu kept between
+                             iterations (and handed off between levels) by
+                             fa_register, fa_register_from and the batched calls:
+                             FA_F32 (default) or FA_BF16.  Arithmetic stays FP32: each
+                             iteration reads the stored moments, updates them in FP32,
+                             takes the direction from the FP32 values and stores them
+                             rounded to nearest.  FA_F16 is refused
+                             (FA_ERR_UNSUPPORTED): its smallest normal value, 6.1e-5,
+                             lies far above the moments of a loss gradient that scales
+                             as 1/N, which would flush to zero.  The displacement u
+                             stays FP32 (a compositive update of a fraction of a voxel
+                             would lose its low bits in a 16-bit u of several voxels).
+                             The symmetric, SVF, inverse, affine and rigid calls take
+                             FA_F32 only (FA_ERR_UNSUPPORTED otherwise). */
 } fa_params;
 
 /* Fills p with: 3 levels {4,2,1} x {200,100,50}, lr 0.5, sigma_grad 1,
  * sigma_warp 0.5, window 5, LNCC, Adam (0.9, 0.999, 1e-8), cc_eps 1e-5,
  * c_lp 2, fused mode, FP32 storage, graph replay on, Jacobian-free direction,
- * 32 MI bins. */
+ * 32 MI bins, FP32 Adam moments. */
 fa_status fa_params_default(fa_params *p);
 
 const char *fa_status_str(fa_status s);
@@ -215,7 +229,11 @@ size_t fa_radam_workspace_size(int32_t D, int32_t H, int32_t W);
  *   d = (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + adam_eps);
  *   eps_t = lr / (c_lp max_x |d(x)|)  (0 if the max is 0);  delta = -eps_t d;
  *   u_out(x) = delta(x) + u_in(x + delta(x))   (phi <- phi o (id + delta)).
- * u_in, u_out, m, v, g: C=3, FA_F32, same grid; u_out must not alias u_in.
+ * u_in, u_out, g: C=3, FA_F32; m, v: C=3, both FA_F32, both FA_BF16 or both
+ * FA_F16 (16-bit moments are read, updated in FP32 and stored rounded to
+ * nearest, the direction coming from the FP32 values; FP16 moments must lie
+ * in its normal range to keep their precision); one grid; u_out must not
+ * alias u_in.
  * t >= 1 is the step number after increment.  Uses p->beta1, beta2,
  * adam_eps, lr, c_lp.  eps_t_dev (device float, may be NULL) receives eps_t.
  * A non-finite max|d| sets the workspace status word (see fa_ws_status). */

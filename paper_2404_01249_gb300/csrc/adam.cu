@@ -10,8 +10,9 @@
 
 namespace fa {
 
-__global__ void __launch_bounds__(256) k_adam(const float *__restrict__ g, float *__restrict__ m,
-                                              float *__restrict__ v, float *__restrict__ d,
+template <class TS>
+__global__ void __launch_bounds__(256) k_adam(const float *__restrict__ g, TS *__restrict__ m,
+                                              TS *__restrict__ v, float *__restrict__ d,
                                               long long N, AdamConsts c, WsHeader *h,
                                               int parity) {
     __shared__ float red[32];
@@ -23,10 +24,10 @@ __global__ void __launch_bounds__(256) k_adam(const float *__restrict__ g, float
         for (int ch = 0; ch < 3; ++ch) {
             long long k = ch * N + i;
             float gv = g[k];
-            float mv = fmaf(c.b1, m[k], (1.0f - c.b1) * gv);
-            float vv = fmaf(c.b2, v[k], (1.0f - c.b2) * gv * gv);
-            m[k] = mv;
-            v[k] = vv;
+            float mv = fmaf(c.b1, st_load(m[k]), (1.0f - c.b1) * gv);
+            float vv = fmaf(c.b2, st_load(v[k]), (1.0f - c.b2) * gv * gv);
+            m[k] = st_store<TS>(mv);
+            v[k] = st_store<TS>(vv);
             float dv = adam_dir(mv, vv, c.rbc1, c.rbc2, c.eps);
             d[k] = dv;
             nrm2 = fmaf(dv, dv, nrm2);
@@ -109,7 +110,21 @@ cudaError_t launch_compose_fields(const float *u, const float *delta, float *uo,
 cudaError_t launch_adam(const float *g, float *m, float *v, float *d, long long N, AdamConsts c,
                         WsHeader *h, int parity, cudaStream_t s) {
     long long blocks = (N + 255) / 256;
-    k_adam<<<(unsigned)blocks, 256, 0, s>>>(g, m, v, d, N, c, h, parity); note_launch();
+    k_adam<float><<<(unsigned)blocks, 256, 0, s>>>(g, m, v, d, N, c, h, parity); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam_state(const float *g, void *m, void *v, int state, float *d, long long N,
+                              AdamConsts c, WsHeader *h, int parity, cudaStream_t s) {
+    const unsigned blocks = (unsigned)((N + 255) / 256);
+    if (state == FA_BF16)
+        k_adam<__nv_bfloat16><<<blocks, 256, 0, s>>>(g, (__nv_bfloat16 *)m, (__nv_bfloat16 *)v, d,
+                                                     N, c, h, parity);
+    else if (state == FA_F16)
+        k_adam<__half><<<blocks, 256, 0, s>>>(g, (__half *)m, (__half *)v, d, N, c, h, parity);
+    else
+        k_adam<float><<<blocks, 256, 0, s>>>(g, (float *)m, (float *)v, d, N, c, h, parity);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -131,10 +146,14 @@ AdamConsts adam_consts(const fa_params *p, int t) {
     return c;
 }
 
-fa_status check_adam_params(const fa_params *p, const char *who) {
+fa_status check_adam_params(const fa_params *p, const char *who, bool state16_ok) {
     if (!p) {
         set_error("%s: params are NULL", who);
         return FA_ERR_INVALID;
+    }
+    if (!state16_ok && p->state_storage != FA_F32) {
+        set_error("%s: keeps its Adam moments in FP32 (state_storage must be FA_F32)", who);
+        return FA_ERR_UNSUPPORTED;
     }
     if (!(p->beta1 >= 0.0f && p->beta1 < 1.0f) || !(p->beta2 >= 0.0f && p->beta2 < 1.0f) ||
         !(p->adam_eps >= 0.0f) || !(p->lr > 0.0f && p->lr < 1e30f) ||
@@ -162,8 +181,12 @@ extern "C" fa_status fa_radam_step(const fa_vol *u_in, fa_vol *u_out, fa_vol *m,
     clear_error();
     FA_TRY(check_vol(u_in, "u_in", 3));
     FA_TRY(check_vol(u_out, "u_out", 3));
-    FA_TRY(check_vol(m, "m", 3));
-    FA_TRY(check_vol(v, "v", 3));
+    if (m && m->dtype != FA_F32 && m->dtype != FA_BF16 && m->dtype != FA_F16) {
+        set_error("fa_radam_step: m must be FA_F32, FA_BF16 or FA_F16 (got %d)", (int)m->dtype);
+        return FA_ERR_DTYPE;
+    }
+    FA_TRY(check_vol_dtype(m, "m", 3, m ? m->dtype : FA_F32));
+    FA_TRY(check_vol_dtype(v, "v", 3, m->dtype));
     FA_TRY(check_vol(g, "g", 3));
     FA_TRY(same_grid(u_in, u_out, "u_in", "u_out"));
     FA_TRY(same_grid(u_in, m, "u_in", "m"));
@@ -177,7 +200,7 @@ extern "C" fa_status fa_radam_step(const fa_vol *u_in, fa_vol *u_out, fa_vol *m,
         set_error("fa_radam_step: t must be >= 1");
         return FA_ERR_INVALID;
     }
-    FA_TRY(check_adam_params(p, "fa_radam_step"));
+    FA_TRY(check_adam_params(p, "fa_radam_step", true));  // m, v carry their own dtype
     FA_TRY(check_ws(ws, ws_bytes, fa_radam_workspace_size(u_in->D, u_in->H, u_in->W),
                     "fa_radam_step"));
     cudaStream_t s = (cudaStream_t)stream;
@@ -187,8 +210,8 @@ extern "C" fa_status fa_radam_step(const fa_vol *u_in, fa_vol *u_out, fa_vol *m,
     float *dir = c.take<float>(3 * d.N());
     int parity = t & 1;
     FA_CUDA_TRY(launch_header_reset(h, s));
-    FA_CUDA_TRY(launch_adam((const float *)g->data, (float *)m->data, (float *)v->data, dir, d.N(),
-                            adam_consts(p, t), h, parity, s));
+    FA_CUDA_TRY(launch_adam_state((const float *)g->data, m->data, v->data, m->dtype, dir, d.N(),
+                                  adam_consts(p, t), h, parity, s));
     FA_CUDA_TRY(launch_compose((const float *)u_in->data, dir, (float *)u_out->data, d, p->lr,
                                p->c_lp, h, parity, eps_t_dev, s));
     return FA_OK;

@@ -3,6 +3,8 @@
 // grid, fixed-point scaling for exact window sums, status-word bits.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -323,6 +325,33 @@ __device__ __forceinline__ void lncc_c_ff(float A, float B, long long sI, long l
 // Adam direction d = (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps) with the
 // bias corrections passed as reciprocals; square root and quotient use the
 // hardware approximations (a few ulp).
+// Storage of the Adam moments: FP32, or 16-bit values read as FP32 and
+// written rounded to nearest (all arithmetic is FP32).
+__device__ __forceinline__ float st_load(float x) { return x; }
+__device__ __forceinline__ float st_load(__nv_bfloat16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ float st_load(__half x) { return __half2float(x); }
+template <class T>
+__device__ __forceinline__ T st_store(float x);
+template <>
+__device__ __forceinline__ float st_store<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 st_store<__nv_bfloat16>(float x) {
+    return __float2bfloat16_rn(x);
+}
+template <>
+__device__ __forceinline__ __half st_store<__half>(float x) { return __float2half_rn(x); }
+// A 16-bit stored value given by its bits, as FP32 (exact).
+template <class T>
+__device__ __forceinline__ float st_bits(unsigned short b);
+template <>
+__device__ __forceinline__ float st_bits<__nv_bfloat16>(unsigned short b) {
+    return __uint_as_float((unsigned)b << 16);
+}
+template <>
+__device__ __forceinline__ float st_bits<__half>(unsigned short b) {
+    return __half2float(__ushort_as_half(b));
+}
+
 __device__ __forceinline__ float adam_dir(float m, float v, float rbc1, float rbc2, float eps) {
     const float vh = v * rbc2;
     const float sq = vh > 0.0f ? vh * rsqrtf(vh) : 0.0f;

@@ -192,33 +192,41 @@ cudaError_t launch_k2(const float *If, const float *gJ, const float *J, const fl
     return le;
 }
 
-template <int RG, int NW>
-cudaError_t launch_k3_tma(const Maps &mp, const float *g, float *m, float *v, float *dir,
-                          WsHeader *h, Dims d, const GaussTaps &t, AdamConsts ac, int parity,
-                          int tz, cudaStream_t s) {
-    using ST = K3S<RG, NW, K3_OPT, K3_ST_TMA>;
-    auto kern = k_smooth_adam<RG, NW, K3_OPT, K3_ST_TMA, true>;
+template <int RG, int NW, class TS>
+cudaError_t launch_k3_tma(const Maps &mp, const float *g, TS *m, TS *v, float *dir, WsHeader *h,
+                          Dims d, const GaussTaps &t, AdamConsts ac, int parity, int tz,
+                          cudaStream_t s) {
+    using ST = K3S<RG, NW, K3_OPT, K3_ST_TMA, sizeof(TS) == 4>;
+    auto kern = k_smooth_adam<RG, NW, K3_OPT, K3_ST_TMA, true, TS>;
     static const int occ = prepare(kern, ST::bytes, ST::NT);
     LaunchGeom gg = geometry(occ, NW, ST::TY, RG, d, tz);
     return launch_pdl(kern, gg, ST::bytes, s, mp, g, m, v, dir, h, d.D, d.H, d.W, gg.tz, t, ac,
                       parity);
 }
 
-template <int RG>
-cudaError_t launch_k3(const float *g, float *m, float *v, float *dir, WsHeader *h, Dims d,
+// TS: storage of the moments (float, __nv_bfloat16 or __half); 16-bit moments
+// take the 32 x 8 tiles only.
+template <int RG, class TS>
+cudaError_t launch_k3(const float *g, TS *m, TS *v, float *dir, WsHeader *h, Dims d,
                       const GaussTaps &t, AdamConsts ac, int parity, cudaStream_t s) {
+    constexpr bool S32 = sizeof(TS) == 4;
     Maps mp{};
     cudaError_t le;
     const TileChoice tc = tile_choice(2, RG, 0, d);
-    const int nw = tc.wide ? 16 : 8;
+    const bool wide = S32 && tc.wide;
+    const int nw = wide ? 16 : 8;
     const bool tma = tmap(&mp.a, g, 4, d, 3, FX + 2 * halo4(RG), nw + 2 * RG, 3) &&
-                     tmap(&mp.b, m, 4, d, 3, FX, nw, 3) && tmap(&mp.c, v, 4, d, 3, FX, nw, 3);
+                     (!S32 || (tmap(&mp.b, m, 4, d, 3, FX, nw, 3) &&
+                               tmap(&mp.c, v, 4, d, 3, FX, nw, 3)));
     if (tma) {
-        le = tc.wide ? launch_k3_tma<RG, 16>(mp, g, m, v, dir, h, d, t, ac, parity, tc.tz, s)
-                     : launch_k3_tma<RG, 8>(mp, g, m, v, dir, h, d, t, ac, parity, tc.tz, s);
+        if constexpr (S32)
+            le = wide ? launch_k3_tma<RG, 16, TS>(mp, g, m, v, dir, h, d, t, ac, parity, tc.tz, s)
+                      : launch_k3_tma<RG, 8, TS>(mp, g, m, v, dir, h, d, t, ac, parity, tc.tz, s);
+        else
+            le = launch_k3_tma<RG, 8, TS>(mp, g, m, v, dir, h, d, t, ac, parity, tc.tz, s);
     } else {
-        using SC = K3S<RG, K3_NW, K3_OPT, K3_ST_CP>;
-        auto kern = k_smooth_adam<RG, K3_NW, K3_OPT, K3_ST_CP, false>;
+        using SC = K3S<RG, K3_NW, K3_OPT, K3_ST_CP, S32>;
+        auto kern = k_smooth_adam<RG, K3_NW, K3_OPT, K3_ST_CP, false, TS>;
         static const int occ = prepare(kern, SC::bytes, SC::NT);
         LaunchGeom gg = geometry(occ, K3_NW, SC::TY, RG, d, tc.tz);
         le = launch_pdl(kern, gg, SC::bytes, s, mp, g, m, v, dir, h, d.D, d.H, d.W, gg.tz, t, ac,
@@ -305,18 +313,29 @@ cudaError_t dispatch_k2(const float *If, const float *gJ, const float *J, const 
 }
 
 
-cudaError_t dispatch_k3(const float *g, float *m, float *v, float *dir, WsHeader *h, Dims d,
-                        const GaussTaps &t, AdamConsts ac, int parity, cudaStream_t s) {
+template <class TS>
+cudaError_t dispatch_k3_ts(const float *g, TS *m, TS *v, float *dir, WsHeader *h, Dims d,
+                           const GaussTaps &t, AdamConsts ac, int parity, cudaStream_t s) {
     switch (t.R) {
-        FA_CASE(0, (launch_k3<RR>(g, m, v, dir, h, d, t, ac, parity, s)))
-        FA_CASE(1, (launch_k3<RR>(g, m, v, dir, h, d, t, ac, parity, s)))
-        FA_CASE(2, (launch_k3<RR>(g, m, v, dir, h, d, t, ac, parity, s)))
-        FA_CASE(3, (launch_k3<RR>(g, m, v, dir, h, d, t, ac, parity, s)))
-        FA_CASE(4, (launch_k3<RR>(g, m, v, dir, h, d, t, ac, parity, s)))
-        FA_CASE(5, (launch_k3<RR>(g, m, v, dir, h, d, t, ac, parity, s)))
-        FA_CASE(6, (launch_k3<RR>(g, m, v, dir, h, d, t, ac, parity, s)))
+        FA_CASE(0, (launch_k3<RR, TS>(g, m, v, dir, h, d, t, ac, parity, s)))
+        FA_CASE(1, (launch_k3<RR, TS>(g, m, v, dir, h, d, t, ac, parity, s)))
+        FA_CASE(2, (launch_k3<RR, TS>(g, m, v, dir, h, d, t, ac, parity, s)))
+        FA_CASE(3, (launch_k3<RR, TS>(g, m, v, dir, h, d, t, ac, parity, s)))
+        FA_CASE(4, (launch_k3<RR, TS>(g, m, v, dir, h, d, t, ac, parity, s)))
+        FA_CASE(5, (launch_k3<RR, TS>(g, m, v, dir, h, d, t, ac, parity, s)))
+        FA_CASE(6, (launch_k3<RR, TS>(g, m, v, dir, h, d, t, ac, parity, s)))
     }
     return cudaErrorInvalidValue;
+}
+
+// m, v stored as `state` (FA_F32 or FA_BF16)
+cudaError_t dispatch_k3(const float *g, void *m, void *v, int state, float *dir, WsHeader *h,
+                        Dims d, const GaussTaps &t, AdamConsts ac, int parity, cudaStream_t s) {
+    if (state == FA_BF16)
+        return dispatch_k3_ts(g, (__nv_bfloat16 *)m, (__nv_bfloat16 *)v, dir, h, d, t, ac, parity,
+                              s);
+    if (state != FA_F32) return cudaErrorInvalidValue;
+    return dispatch_k3_ts(g, (float *)m, (float *)v, dir, h, d, t, ac, parity, s);
 }
 
 cudaError_t dispatch_k4(const float *u, const float *dir, float *uo, const float *Im, float *J,
@@ -433,7 +452,7 @@ fa_status fused_iteration(FusedBuffers &fb, WsHeader *h, const fa_params *p, Dim
     const bool su = (double)p->lr / (double)p->c_lp < 0.999;
     if (wide_g) FA_CUDA_TRY(launch_gauss3(fb.g, fb.g, fb.t1, fb.t2, 3, d, tg, s));
     FA_CUDA_TRY(start(FA_K_FUSED_SMOOTH_ADAM));
-    FA_CUDA_TRY(dispatch_k3(fb.g, it.m, it.v, fb.dir, h, d, wide_g ? ident : tg,
+    FA_CUDA_TRY(dispatch_k3(fb.g, it.m, it.v, p->state_storage, fb.dir, h, d, wide_g ? ident : tg,
                             adam_consts(p, it.t), parity, s));
     FA_CUDA_TRY(stop(FA_K_FUSED_SMOOTH_ADAM));
     FA_CUDA_TRY(start(FA_K_FUSED_COMPOSE));
@@ -448,8 +467,8 @@ fa_status fused_iteration(FusedBuffers &fb, WsHeader *h, const fa_params *p, Dim
 }
 
 fa_status fused_autotune_level(FusedBuffers &fb, WsHeader *h, const fa_params *p, Dims d,
-                               const float *If, const float *Im, float *u, float *u_alt, float *m,
-                               float *v, const GaussTaps &tg, const GaussTaps &tw,
+                               const float *If, const float *Im, float *u, float *u_alt, void *m,
+                               void *v, const GaussTaps &tg, const GaussTaps &tw,
                                cudaStream_t s) {
     static const GaussTaps ident = [] {
         GaussTaps t;
@@ -466,7 +485,7 @@ fa_status fused_autotune_level(FusedBuffers &fb, WsHeader *h, const fa_params *p
                 return dispatch_k1(If, fb.J, fb.sI, fb.varI, fb.coef, h, d, p->window, p->cc_eps,
                                    true, s);
             case 1: return dispatch_k2(If, fb.gJ, fb.J, fb.coef, h, fb.g, d, p->window, s);
-            case 2: return dispatch_k3(fb.g, m, v, fb.dir, h, d, g3, ac, 0, s);
+            case 2: return dispatch_k3(fb.g, m, v, p->state_storage, fb.dir, h, d, g3, ac, 0, s);
             default:
                 return dispatch_k4(u, fb.dir, u_alt, Im, fb.J, fb.gJ, h, d, g4, p->lr, p->c_lp, 0,
                                    su, s);

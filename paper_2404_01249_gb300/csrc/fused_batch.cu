@@ -48,7 +48,8 @@ struct K2Batch {
 };
 struct K3Job {
     const float *g;
-    float *m, *v, *dir;
+    void *m, *v;  // stored as the launch's moment type
+    float *dir;
     WsHeader *h;
     BGeom geo;
     BTaps t;
@@ -119,13 +120,14 @@ __global__ void __launch_bounds__(FX *K2_NW) k_lncc_grad_batch(const __grid_cons
                                                       bx, by, bz);
 }
 
-template <int RG>
+template <int RG, class TS>
 __global__ void __launch_bounds__(FX *K3_NW) k_smooth_adam_batch(const __grid_constant__ K3Batch b) {
     const int k = batch_job(b.first, b.n, (int)blockIdx.x);
     const K3Job &j = b.j[k];
     int bx, by, bz;
     batch_tile(j.geo, (int)blockIdx.x - b.first[k], bx, by, bz);
-    smooth_adam_body<RG, K3_NW, K3_OPT, K3_ST_CP, false>(nullptr, j.g, j.m, j.v, j.dir, j.h,
+    smooth_adam_body<RG, K3_NW, K3_OPT, K3_ST_CP, false>(nullptr, j.g, (TS *)j.m, (TS *)j.v, j.dir,
+                                                         j.h,
                                                          j.geo.D, j.geo.H, j.geo.W, j.geo.TZ, j.t,
                                                          b.ac, b.parity, bx, by, bz);
 }
@@ -215,10 +217,10 @@ cudaError_t launch_k2_batch(K2Batch &b, const LockstepJob *jobs, cudaStream_t s)
 }
 
 // jobs[idx[0..b.n)] are the launch's jobs
-template <int RG>
+template <int RG, class TS>
 cudaError_t launch_k3_batch(K3Batch &b, const LockstepJob *jobs, const int *idx, cudaStream_t s) {
-    using SC = K3S<RG, K3_NW, K3_OPT, K3_ST_CP>;
-    auto kern = k_smooth_adam_batch<RG>;
+    using SC = K3S<RG, K3_NW, K3_OPT, K3_ST_CP, sizeof(TS) == 4>;
+    auto kern = k_smooth_adam_batch<RG, TS>;
     static const int occ = prepare(kern, SC::bytes, SC::NT);
     long long tot = 0;
     for (int k = 0; k < b.n; ++k) tot += jobs[idx[k]].d.N();
@@ -275,18 +277,27 @@ cudaError_t dispatch_k2_batch(int R, K2Batch &b, const LockstepJob *jobs, cudaSt
     return cudaErrorInvalidValue;
 }
 
-cudaError_t dispatch_k3_batch(int RG, K3Batch &b, const LockstepJob *jobs, const int *idx,
-                              cudaStream_t s) {
+template <class TS>
+cudaError_t dispatch_k3_batch_ts(int RG, K3Batch &b, const LockstepJob *jobs, const int *idx,
+                                 cudaStream_t s) {
     switch (RG) {
-        FA_CASE(0, launch_k3_batch<RR>(b, jobs, idx, s))
-        FA_CASE(1, launch_k3_batch<RR>(b, jobs, idx, s))
-        FA_CASE(2, launch_k3_batch<RR>(b, jobs, idx, s))
-        FA_CASE(3, launch_k3_batch<RR>(b, jobs, idx, s))
-        FA_CASE(4, launch_k3_batch<RR>(b, jobs, idx, s))
-        FA_CASE(5, launch_k3_batch<RR>(b, jobs, idx, s))
-        FA_CASE(6, launch_k3_batch<RR>(b, jobs, idx, s))
+        FA_CASE(0, (launch_k3_batch<RR, TS>(b, jobs, idx, s)))
+        FA_CASE(1, (launch_k3_batch<RR, TS>(b, jobs, idx, s)))
+        FA_CASE(2, (launch_k3_batch<RR, TS>(b, jobs, idx, s)))
+        FA_CASE(3, (launch_k3_batch<RR, TS>(b, jobs, idx, s)))
+        FA_CASE(4, (launch_k3_batch<RR, TS>(b, jobs, idx, s)))
+        FA_CASE(5, (launch_k3_batch<RR, TS>(b, jobs, idx, s)))
+        FA_CASE(6, (launch_k3_batch<RR, TS>(b, jobs, idx, s)))
     }
     return cudaErrorInvalidValue;
+}
+
+// the launch's jobs store their moments as `state`
+cudaError_t dispatch_k3_batch(int RG, int state, K3Batch &b, const LockstepJob *jobs,
+                              const int *idx, cudaStream_t s) {
+    if (state == FA_BF16) return dispatch_k3_batch_ts<__nv_bfloat16>(RG, b, jobs, idx, s);
+    if (state != FA_F32) return cudaErrorInvalidValue;
+    return dispatch_k3_batch_ts<float>(RG, b, jobs, idx, s);
 }
 
 cudaError_t dispatch_k4_batch(int RG, bool su, K4Batch &b, const LockstepJob *jobs, const int *idx,
@@ -364,27 +375,30 @@ fa_status fused_iteration_lockstep(int n, const LockstepJob *jobs, int t, cudaSt
     }
     int idx[kMaxLockstepJobs];
     const AdamConsts ac = adam_consts(p0, t);
-    for (int rg = 0; rg <= kMaxFusedRG; ++rg) {
-        int m = 0;
-        for (int k = 0; k < n; ++k)
-            if (jobs[k].tg->R == rg) idx[m++] = k;
-        if (m == 0) continue;
-        K3Batch b;
-        b.n = m;
-        b.parity = parity;
-        b.ac = ac;
-        for (int i = 0; i < m; ++i) {
-            const LockstepJob &q = jobs[idx[i]];
-            K3Job &j = b.j[i];
-            j.g = q.fb->g;
-            j.m = q.m;
-            j.v = q.v;
-            j.dir = q.fb->dir;
-            j.h = q.h;
-            batch_taps(j.t, *q.tg);
+    const int states[2] = {FA_F32, FA_BF16};
+    for (int st : states) {
+        for (int rg = 0; rg <= kMaxFusedRG; ++rg) {
+            int m = 0;
+            for (int k = 0; k < n; ++k)
+                if (jobs[k].tg->R == rg && jobs[k].p->state_storage == st) idx[m++] = k;
+            if (m == 0) continue;
+            K3Batch b;
+            b.n = m;
+            b.parity = parity;
+            b.ac = ac;
+            for (int i = 0; i < m; ++i) {
+                const LockstepJob &q = jobs[idx[i]];
+                K3Job &j = b.j[i];
+                j.g = q.fb->g;
+                j.m = q.m;
+                j.v = q.v;
+                j.dir = q.fb->dir;
+                j.h = q.h;
+                batch_taps(j.t, *q.tg);
+            }
+            FA_CUDA_TRY(dispatch_k3_batch(rg, st, b, jobs, idx, s));
+            note_launch();
         }
-        FA_CUDA_TRY(dispatch_k3_batch(rg, b, jobs, idx, s));
-        note_launch();
     }
     for (int su = 0; su < 2; ++su)
         for (int rg = 0; rg <= kMaxFusedRG; ++rg) {

@@ -889,13 +889,15 @@ __global__ void __launch_bounds__(256) k_fused_mse_grad(const float *__restrict_
 }
 
 // ====================================================================== K3
-template <int RG, int NW, int OPT, int NSTG>
+// S32: the moments m, nu are FP32 and arrive with the plane's copies; 16-bit
+// moments are loaded by each thread straight into registers one plane ahead.
+template <int RG, int NW, int OPT, int NSTG, bool S32 = true>
 struct K3S {
     static constexpr int NT = FX * NW, TY = NW * OPT, RX = FX + 2 * RG, RY = TY + 2 * RG;
     static constexpr int XB = halo4(RG), BXW = FX + 2 * XB, COFF = XB - RG;
     static constexpr int NR = BXW * RY, NS = 2 * RG + 1, NOUT = NT * OPT;
     static constexpr size_t st_bytes = al128((size_t)3 * NR * 4);    // g
-    static constexpr size_t ost_bytes = al128((size_t)6 * NOUT * 4);  // m, v
+    static constexpr size_t ost_bytes = S32 ? al128((size_t)6 * NOUT * 4) : 0;  // m, v
     static constexpr unsigned tx_plane = 3u * NR * 4, tx_out = 6u * NOUT * 4;
     static constexpr size_t o_st = 0;
     static constexpr size_t o_ost = o_st + st_bytes * NSTG;
@@ -906,14 +908,15 @@ struct K3S {
 };
 
 // The body of K3 for the CTA with tile coordinates (bx, by, bz).
-template <int RG, int NW, int OPT, int NSTG, bool TMA, class TT>
+template <int RG, int NW, int OPT, int NSTG, bool TMA, class TT, class TS>
 __device__ __forceinline__ void smooth_adam_body(const Maps *maps, const float *__restrict__ g,
-                                                 float *__restrict__ m, float *__restrict__ v,
+                                                 TS *__restrict__ m, TS *__restrict__ v,
                                                  float *__restrict__ dir, WsHeader *__restrict__ h,
                                                  int D, int H, int W, int TZ, const TT t,
                                                  const AdamConsts ac, int parity, int bx, int by,
                                                  int bz) {
-    using S = K3S<RG, NW, OPT, NSTG>;
+    constexpr bool S32 = sizeof(TS) == 4;
+    using S = K3S<RG, NW, OPT, NSTG, S32>;
     constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, BXW = S::BXW, COFF = S::COFF,
                   XB = S::XB, NS = S::NS, NOUT = S::NOUT;
     using G = Region<RY, RX, NW, BXW, COFF>;
@@ -944,7 +947,7 @@ __device__ __forceinline__ void smooth_adam_body(const Maps *maps, const float *
     const int zs = z0 - RG, np = zend - z0 + 2 * RG;
     auto issue = [&](int i) {
         const int zp = zs + i, zo = zp - RG, s = i % NSTG;
-        const bool out = zo >= z0 && zo < zend;
+        const bool out = S32 && zo >= z0 && zo < zend;
         if (TMA) {
             if (tid == 0 && i < np) {
                 mbar_expect(bar + s, S::tx_plane + (out ? S::tx_out : 0u));
@@ -957,15 +960,29 @@ __device__ __forceinline__ void smooth_adam_body(const Maps *maps, const float *
         } else {
             if (i < np) {
                 rg.template load<3>(stage(s), g, N, (long long)zp * HW, zp >= 0 && zp < D);
-                if (out) {
-                    ou.template load<3, float>(ostage(s), m, N, (long long)zo * HW, tid);
-                    ou.template load<3, float>(ostage(s) + 3 * NOUT, v, N, (long long)zo * HW,
-                                               tid);
+                if constexpr (S32) {
+                    if (out) {
+                        ou.template load<3, float>(ostage(s), m, N, (long long)zo * HW, tid);
+                        ou.template load<3, float>(ostage(s) + 3 * NOUT, v, N,
+                                                   (long long)zo * HW, tid);
+                    }
                 }
             }
             cp_commit();
         }
     };
+    // 16-bit moments of the next output plane, loaded one plane ahead
+    unsigned short mn[OPT][3], vn[OPT][3];
+    auto fetch_mv = [&](int i) {
+        if constexpr (!S32) {
+            const int zo = zs + i - RG;
+            if (i < np && zo >= z0 && zo < zend) {
+                ou.fetch(mn, (const unsigned short *)m, N, (long long)zo * HW);
+                ou.fetch(vn, (const unsigned short *)v, N, (long long)zo * HW);
+            }
+        }
+    };
+    fetch_mv(0);
 #pragma unroll
     for (int k = 0; k < NSTG - 1; ++k) issue(k);
 
@@ -983,15 +1000,26 @@ __device__ __forceinline__ void smooth_adam_body(const Maps *maps, const float *
         const bool out = zo >= z0 && zo < zend;
         float mo[OPT][3], vo[OPT][3];
         if (out) {
-            const float *od = ostage(s) + tid;
+            if constexpr (S32) {
+                const float *od = ostage(s) + tid;
 #pragma unroll
-            for (int o = 0; o < OPT; ++o)
+                for (int o = 0; o < OPT; ++o)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    mo[o][c] = od[c * NOUT + o * NT];
-                    vo[o][c] = od[(3 + c) * NOUT + o * NT];
-                }
+                    for (int c = 0; c < 3; ++c) {
+                        mo[o][c] = od[c * NOUT + o * NT];
+                        vo[o][c] = od[(3 + c) * NOUT + o * NT];
+                    }
+            } else {
+#pragma unroll
+                for (int o = 0; o < OPT; ++o)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        mo[o][c] = st_bits<TS>(mn[o][c]);
+                        vo[o][c] = st_bits<TS>(vn[o][c]);
+                    }
+            }
         }
+        fetch_mv(i + 1);
         if (__syncthreads_or(!ok)) {  // also: the x pass reads neighbours' copies
             fail = i;
             break;
@@ -1022,8 +1050,8 @@ __device__ __forceinline__ void smooth_adam_body(const Maps *maps, const float *
                     const float sg = sz[c];
                     const float mvv = fmaf(ac.b1, mo[o][c], (1.0f - ac.b1) * sg);
                     const float vvv = fmaf(ac.b2, vo[o][c], (1.0f - ac.b2) * sg * sg);
-                    m[c * N + gi] = mvv;
-                    v[c * N + gi] = vvv;
+                    m[c * N + gi] = st_store<TS>(mvv);
+                    v[c * N + gi] = st_store<TS>(vvv);
                     const float dv = adam_dir(mvv, vvv, ac.rbc1, ac.rbc2, ac.eps);
                     dir[c * N + gi] = dv;
                     nrm2 = fmaf(dv, dv, nrm2);
@@ -1047,11 +1075,11 @@ __device__ __forceinline__ void smooth_adam_body(const Maps *maps, const float *
     block_max_to(&h->step_max_bits[parity], mx, redf);
 }
 
-template <int RG, int NW, int OPT, int NSTG, bool TMA>
+template <int RG, int NW, int OPT, int NSTG, bool TMA, class TS = float>
 __global__ void __launch_bounds__(FX *NW, NW >= 16 ? 2 : 1) k_smooth_adam(const __grid_constant__ Maps maps,
                                                         const float *__restrict__ g,
-                                                        float *__restrict__ m,
-                                                        float *__restrict__ v,
+                                                        TS *__restrict__ m,
+                                                        TS *__restrict__ v,
                                                         float *__restrict__ dir,
                                                         WsHeader *__restrict__ h, int D, int H,
                                                         int W, int TZ, GaussTaps t, AdamConsts ac,

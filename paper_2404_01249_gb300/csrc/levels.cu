@@ -92,6 +92,24 @@ cudaError_t launch_widen(const void *src, int dtype, float *dst, long long n, cu
     return cudaGetLastError();
 }
 
+// FP32 values rounded to nearest into 16-bit storage (the inverse of k_widen
+// up to that rounding).
+__global__ void __launch_bounds__(256) k_narrow(const float *__restrict__ src, int dtype,
+                                                unsigned short *__restrict__ dst, long long n) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        dst[i] = dtype == FA_BF16 ? __bfloat16_as_ushort(__float2bfloat16_rn(src[i]))
+                                  : __half_as_ushort(__float2half_rn(src[i]));
+}
+
+cudaError_t launch_narrow(const float *src, int dtype, void *dst, long long n, cudaStream_t s) {
+    const long long blocks = (n + 255) / 256;
+    k_narrow<<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, s>>>(
+        src, dtype, (unsigned short *)dst, n);
+    note_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace fa
 
 extern "C" fa_status fa_pyramid_level(const fa_vol *img, int32_t s, fa_vol *out, void *ws,

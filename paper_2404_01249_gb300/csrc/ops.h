@@ -102,11 +102,18 @@ struct AdamConsts {
     float b1, b2, eps, rbc1, rbc2;  // rbc = 1 / (1 - beta^t)
 };
 AdamConsts adam_consts(const fa_params *p, int t);
-fa_status check_adam_params(const fa_params *p, const char *who);
+// state16_ok: the caller can keep its Adam moments in 16-bit storage
+// (fa_params.state_storage); otherwise only FA_F32 is accepted.
+fa_status check_adam_params(const fa_params *p, const char *who, bool state16_ok = false);
 // d = Adam direction over N voxels of 3 channels (planar, 3N floats each);
 // block max of the voxel norm |d| into h->step_max_bits[parity].
 cudaError_t launch_adam(const float *g, float *m, float *v, float *d, long long N, AdamConsts c,
                         WsHeader *h, int parity, cudaStream_t s);
+// The same with m, v stored as `state` (FA_F32, FA_BF16 or FA_F16).
+cudaError_t launch_adam_state(const float *g, void *m, void *v, int state, float *d, long long N,
+                              AdamConsts c, WsHeader *h, int parity, cudaStream_t s);
+// Bytes of one element of the Adam moments stored as `state`.
+inline size_t state_bytes(int state) { return state == FA_F32 ? 4 : 2; }
 // u_out = delta + u_in o (id + delta), delta = -lr / (c_lp max) d; resets the
 // other parity's max slot; eps_t to h->eps_t and eps_out (if not NULL).
 cudaError_t launch_compose(const float *u_in, const float *d, float *u_out, Dims dm, float lr,
@@ -124,5 +131,7 @@ cudaError_t launch_pyramid_level(const float *img, Dims d, int s, float *out, Di
 
 // dst[i] = src[i] widened to FP32 (src FA_BF16 or FA_F16; exact).
 cudaError_t launch_widen(const void *src, int dtype, float *dst, long long n, cudaStream_t s);
+// dst[i] = src[i] rounded to nearest in dtype (FA_BF16 or FA_F16).
+cudaError_t launch_narrow(const float *src, int dtype, void *dst, long long n, cudaStream_t s);
 
 }  // namespace fa

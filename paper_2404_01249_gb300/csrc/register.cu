@@ -64,7 +64,13 @@ static fa_status check_params(const fa_params *p) {
         set_error("storage must be FA_F32, FA_BF16 or FA_F16 (got %d)", (int)p->storage);
         return FA_ERR_UNSUPPORTED;
     }
-    return check_adam_params(p, "fa_register");
+    if (p->state_storage != FA_F32 && p->state_storage != FA_BF16) {
+        // FP16's smallest normal value (6.1e-5) lies far above the moments of
+        // a loss gradient that scales as 1/N: they would flush to zero
+        set_error("state_storage must be FA_F32 or FA_BF16 (got %d)", (int)p->state_storage);
+        return FA_ERR_UNSUPPORTED;
+    }
+    return check_adam_params(p, "fa_register", true);
 }
 
 // Workspace plan; with base == nullptr only sizes are computed.
@@ -75,7 +81,8 @@ struct Plan {
     WsHeader *h;
     float *If[8], *Im[8];
     float *If0, *Im0;  // FP32 copies of 16-bit input images (else nullptr)
-    float *u[2], *m[2], *v[2];
+    float *u[2];
+    void *m[2], *v[2];  // Adam moments, stored as p->state_storage
     float *J, *grad, *g, *dir, *t1, *t2;
     LnccBuffers lb;
     MiBuffers mi;
@@ -111,8 +118,13 @@ static void make_plan(Plan &P, void *base, size_t cap, Dims full, const fa_param
     }
     for (int k = 0; k < 2; ++k) {
         P.u[k] = c.take<float>(3 * n);
-        P.m[k] = c.take<float>(3 * n);
-        P.v[k] = c.take<float>(3 * n);
+        if (p->state_storage == FA_F32) {
+            P.m[k] = c.take<float>(3 * n);
+            P.v[k] = c.take<float>(3 * n);
+        } else {
+            P.m[k] = c.take<unsigned short>(3 * n);
+            P.v[k] = c.take<unsigned short>(3 * n);
+        }
     }
     long long tmp = 3 * n > full.N() ? 3 * n : full.N();
     P.t1 = c.take<float>(tmp);
@@ -171,7 +183,7 @@ struct Timer {
 
 // One plain-mode iteration: u <- G_warp(compose(u, step(Adam(G_grad(dL/du))))).
 static fa_status plain_iteration(Plan &P, const fa_params *p, int l, const float *If,
-                                 const float *Im, float *u, float *u_alt, float *m, float *v,
+                                 const float *Im, float *u, float *u_alt, void *m, void *v,
                                  int t, const GaussTaps &tg, const GaussTaps &tw, Timer &tm,
                                  cudaStream_t s) {
     Dims d = P.lvl[l];
@@ -191,7 +203,8 @@ static fa_status plain_iteration(Plan &P, const fa_params *p, int l, const float
     if (p->use_jac) FA_CUDA_TRY(launch_jac_direction(P.g, u, P.g, d, s));
     FA_CUDA_TRY(launch_gauss3(P.g, P.g, P.t1, P.t2, 3, d, tg, s));
     int parity = t & 1;
-    FA_CUDA_TRY(launch_adam(P.g, m, v, P.dir, N, adam_consts(p, t), P.h, parity, s));
+    FA_CUDA_TRY(launch_adam_state(P.g, m, v, p->state_storage, P.dir, N, adam_consts(p, t), P.h,
+                                  parity, s));
     FA_CUDA_TRY(launch_compose(u, P.dir, u_alt, d, p->lr, p->c_lp, P.h, parity, nullptr, s));
     FA_CUDA_TRY(launch_gauss3(u_alt, u, P.t1, P.t2, 3, d, tw, s));
     FA_CUDA_TRY(tm.stop(FA_K_PLAIN_ANY, s));
@@ -278,8 +291,9 @@ static fa_status level_begin(Plan &P, const fa_params *p, int l, const float *u_
         } else {
             FA_CUDA_TRY(cudaMemsetAsync(P.u[*cur], 0, b, s));
         }
-        FA_CUDA_TRY(cudaMemsetAsync(P.m[*cur], 0, b, s));
-        FA_CUDA_TRY(cudaMemsetAsync(P.v[*cur], 0, b, s));
+        const size_t bs = state_bytes(p->state_storage) * 3 * d.N();
+        FA_CUDA_TRY(cudaMemsetAsync(P.m[*cur], 0, bs, s));
+        FA_CUDA_TRY(cudaMemsetAsync(P.v[*cur], 0, bs, s));
     } else {
         Dims c = P.lvl[l - 1];
         float su[3], sm[3], sv[3];
@@ -288,8 +302,19 @@ static fa_status level_begin(Plan &P, const fa_params *p, int l, const float *u_
         handoff_scales(c, d, -2, sv);
         int nx = *cur ^ 1;
         FA_CUDA_TRY(launch_resample(P.u[*cur], c, P.u[nx], d, 3, su, s));
-        FA_CUDA_TRY(launch_resample(P.m[*cur], c, P.m[nx], d, 3, sm, s));
-        FA_CUDA_TRY(launch_resample(P.v[*cur], c, P.v[nx], d, 3, sv, s));
+        if (p->state_storage == FA_F32) {
+            FA_CUDA_TRY(launch_resample((const float *)P.m[*cur], c, (float *)P.m[nx], d, 3, sm, s));
+            FA_CUDA_TRY(launch_resample((const float *)P.v[*cur], c, (float *)P.v[nx], d, 3, sv, s));
+        } else {  // 16-bit moments: widened, resampled in FP32, rounded back
+            const int st = p->state_storage;
+            const long long nc = 3 * c.N(), nf = 3 * d.N();
+            FA_CUDA_TRY(launch_widen(P.m[*cur], st, P.t1, nc, s));
+            FA_CUDA_TRY(launch_resample(P.t1, c, P.t2, d, 3, sm, s));
+            FA_CUDA_TRY(launch_narrow(P.t2, st, P.m[nx], nf, s));
+            FA_CUDA_TRY(launch_widen(P.v[*cur], st, P.t1, nc, s));
+            FA_CUDA_TRY(launch_resample(P.t1, c, P.t2, d, 3, sv, s));
+            FA_CUDA_TRY(launch_narrow(P.t2, st, P.v[nx], nf, s));
+        }
         *cur = nx;
     }
     // fixed-point scale of this level's images (max |I_f|, max |I_m|)
@@ -472,7 +497,7 @@ std::string graph_key(int dev, const fa_vol *fixed, const fa_vol *moving, const 
     vol(fixed);
     vol(moving);
     vol(u_out);
-    static_assert(sizeof(fa_params) == 32 * 4, "fa_params holds 32 four-byte fields, no padding");
+    static_assert(sizeof(fa_params) == 33 * 4, "fa_params holds 33 four-byte fields, no padding");
     add(p, sizeof(*p));
     add(&u_init, sizeof(u_init));
     add(&final_loss_dev, sizeof(final_loss_dev));

@@ -20,7 +20,8 @@ void fused_carve(WsCarver &c, long long n, FusedBuffers *fb);
 
 struct FusedIter {
     const float *If, *Im;
-    float *u, *u_alt, *m, *v;  // u_alt receives the updated displacement
+    float *u, *u_alt;  // u_alt receives the updated displacement
+    void *m, *v;       // Adam moments, stored as fa_params.state_storage
     int t;
 };
 
@@ -36,8 +37,8 @@ cudaError_t fused_level_start(const float *If, const float *Im, const float *u, 
 // Measures candidate tile choices of the fused kernels on grid d (any
 // buffer contents) and records the fastest for later launches.
 fa_status fused_autotune_level(FusedBuffers &fb, WsHeader *h, const fa_params *p, Dims d,
-                               const float *If, const float *Im, float *u, float *u_alt, float *m,
-                               float *v, const GaussTaps &tg, const GaussTaps &tw, cudaStream_t s);
+                               const float *If, const float *Im, float *u, float *u_alt, void *m,
+                               void *v, const GaussTaps &tg, const GaussTaps &tw, cudaStream_t s);
 void fused_autotune_reset();
 void fused_tile_set(const int32_t *row);  // one row as fused_tile_choices writes it
 // Recorded choices as rows of 8 int32 (kernel, radius, compose variant, D, H,
@@ -51,13 +52,15 @@ cudaError_t fused_lncc_forward_only(const float *If, const FusedBuffers &fb, Dim
 // fused kernel runs as one launch over the tiles of every job (K3 and K4 one
 // launch per Gaussian radius and compose variant).  The jobs share the loss
 // (LNCC), the window, the Adam constants and the step counter t; each Gaussian
-// is at most kMaxFusedRadius wide.
+// is at most kMaxFusedRadius wide.  K3 runs one launch per Gaussian radius and
+// moment storage type.
 constexpr int kMaxLockstepJobs = 64;
 constexpr int kMaxFusedRadius = 6;
 struct LockstepJob {
     Dims d;
     const float *If, *Im;
-    float *u, *u_alt, *m, *v;  // u_alt receives the updated displacement
+    float *u, *u_alt;  // u_alt receives the updated displacement
+    void *m, *v;       // Adam moments, stored as p->state_storage
     FusedBuffers *fb;
     WsHeader *h;
     const fa_params *p;

@@ -203,6 +203,7 @@ fa_status check_svf(const fa_vol *fixed, const fa_vol *moving, const fa_params *
         set_error("fa_register_svf: use_jac does not apply to the velocity update");
         return FA_ERR_INVALID;
     }
+    if (p) FA_TRY(check_adam_params(p, "fa_register_svf"));
     return register_check(fixed, moving, p, u_out);
 }
 

@@ -248,7 +248,8 @@ extern "C" size_t fa_register_symmetric_workspace_size(int32_t D, int32_t H, int
              level_size(H, p->scales[L] > 0 ? p->scales[L] : 1),
              level_size(W, p->scales[L] > 0 ? p->scales[L] : 1)};
     f.data = u.data = (void *)256;  // shape checks only
-    if (register_check(&f, &f, p, &u) != FA_OK ||
+    if (check_adam_params(p, "fa_register_symmetric") != FA_OK ||
+        register_check(&f, &f, p, &u) != FA_OK ||
         check_loss_args(p->loss, p->window, p->cc_eps, "fa_register_symmetric") != FA_OK)
         return 0;
     size_t inv = 0;
@@ -266,6 +267,7 @@ extern "C" fa_status fa_register_symmetric(const fa_vol *fixed, const fa_vol *mo
                                            size_t ws_bytes, void *stream) {
     using namespace fa;
     clear_error();
+    FA_TRY(check_adam_params(p, "fa_register_symmetric"));
     FA_TRY(register_check(fixed, moving, p, u_out));
     FA_TRY(check_loss_args(p->loss, p->window, p->cc_eps, "fa_register_symmetric"));
     if (uF_out_opt) {

@@ -70,7 +70,8 @@ class Params(ctypes.Structure):
                 ("beta2", ctypes.c_float), ("adam_eps", ctypes.c_float),
                 ("cc_eps", ctypes.c_float), ("c_lp", ctypes.c_float), ("mode", ctypes.c_int32),
                 ("storage", ctypes.c_int32), ("graph", ctypes.c_int32),
-                ("use_jac", ctypes.c_int32), ("mi_bins", ctypes.c_int32)]
+                ("use_jac", ctypes.c_int32), ("mi_bins", ctypes.c_int32),
+                ("state_storage", ctypes.c_int32)]
 
 
 class KernelTimer(ctypes.Structure):
@@ -212,6 +213,7 @@ class RegParams:
     graph: bool = True   # record the launch sequence once, replay it on identical calls
     use_jac: bool = False  # steepest Eulerian direction J(phi)^T dL/dphi
     mi_bins: int = 32      # histogram bins of the MI loss
+    state: str = "f32"     # storage of the Adam moments m, nu: "f32" or "bf16"
 
     def to_c(self) -> Params:
         p = Params()
@@ -232,6 +234,7 @@ class RegParams:
         p.storage = FA_F32
         p.graph = 1 if self.graph else 0
         p.use_jac = 1 if self.use_jac else 0
+        p.state_storage = {"f32": FA_F32, "bf16": FA_BF16, "f16": FA_F16}[self.state]
         return p
 
 
@@ -298,7 +301,8 @@ def fa_radam_step(u_in, m, v, g, t: int, params: RegParams, u_out=None):
     eps_t = torch.empty((), device=u_in.device)
     ws = workspace(lib.fa_radam_workspace_size(D, H, W), u_in.device)
     p = params.to_c()
-    _check(lib.fa_radam_step(_vol(u_in, 3), _vol(u_out, 3), _vol(m, 3), _vol(v, 3), _vol(g, 3),
+    _check(lib.fa_radam_step(_vol(u_in, 3), _vol(u_out, 3), _vol(m, 3, True), _vol(v, 3, True),
+                             _vol(g, 3),
                              t, ctypes.byref(p), _ptr(eps_t), _ptr(ws), ws.numel(), _stream()))
     return u_out, eps_t
 

@@ -143,3 +143,37 @@ def test_lockstep_validation_before_launch(lib):
                                            sigma_grad=2.0).to_c())
     assert run(2, fx, fx, 2, same, uo4, None, None, 64, None, 0, None) == 8  # workspace
     assert run(2, fx, fx, 2, same, uo4, None, None, 0, None, 0, None) == 1
+
+
+def test_moment_storage_validation(lib):
+    from paper_2404_01249_gb300 import fa
+    d = fa.Params()
+    assert lib.fa_params_default(ctypes.byref(d)) == 0 and d.state_storage == 0
+    p32 = fa.RegParams().to_c()
+    p16 = fa.RegParams(state="bf16").to_c()
+    assert 0 < lib.fa_register_workspace_size(40, 48, 56, ctypes.byref(p16)) < \
+        lib.fa_register_workspace_size(40, 48, 56, ctypes.byref(p32))
+    for st in (2, 5):  # FP16 moments would flush to zero; 5 is no dtype
+        bad = fa.RegParams().to_c()
+        bad.state_storage = st
+        assert lib.fa_register_workspace_size(40, 48, 56, ctypes.byref(bad)) == 0
+    # the calls that keep their moments in FP32 refuse 16-bit moments
+    assert lib.fa_affine_workspace_size(40, 48, 56, ctypes.byref(p16)) == 0
+    assert lib.fa_affine_workspace_size(40, 48, 56, ctypes.byref(p32)) > 0
+    assert lib.fa_inverse_workspace_size(40, 48, 56, ctypes.byref(p16)) == 0
+    inv = fa.RegParams(scales=(1,), iters=(5,)).to_c()
+    assert lib.fa_register_symmetric_workspace_size(40, 48, 56, ctypes.byref(p16),
+                                                    ctypes.byref(inv)) == 0
+    assert lib.fa_register_symmetric_workspace_size(40, 48, 56, ctypes.byref(p32),
+                                                    ctypes.byref(inv)) > 0
+    assert lib.fa_register_svf_workspace_size(40, 48, 56, ctypes.byref(p16), 7) == 0
+    assert lib.fa_register_svf_workspace_size(40, 48, 56, ctypes.byref(p32), 7) > 0
+    # fa_radam_step: m and v must share a supported dtype
+    a = 1 << 20
+    V = lambda dt: ctypes.byref(fa.Vol(a, dt, 3, 4, 5, 6))
+    st = lib.fa_radam_step(V(0), ctypes.byref(fa.Vol(a + 4096, 0, 3, 4, 5, 6)), V(1), V(2), V(0),
+                           1, ctypes.byref(p32), None, None, 0, None)
+    assert st == 3
+    st = lib.fa_radam_step(V(0), ctypes.byref(fa.Vol(a + 4096, 0, 3, 4, 5, 6)), V(7), V(7), V(0),
+                           1, ctypes.byref(p32), None, None, 0, None)
+    assert st == 3
