@@ -446,7 +446,7 @@ def run_batched(args):
     loss = torch.stack([r["loss"] for r in out]).cpu().numpy()
     others = {}
     for form in forms:
-        if form == args.schedule:
+        if form == args.schedule or args.no_compare:
             continue
         forms[form]()  # warm (records its graphs)
         torch.cuda.synchronize()
@@ -645,6 +645,8 @@ def main():
                     help="timed form of --batched")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16"],
                     help="--batched: storage of the images and Adam moments")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="--batched: time only the chosen schedule (profiling runs)")
     ap.add_argument("--workload", default="brain",
                     choices=["brain", "symmetric", "inverse", "svf", "mi", "use_jac", "affine",
                              "rigid"],

@@ -15,6 +15,11 @@ namespace {
 // reads the same entry).  Jobs take the per-thread copy variant (cp.async):
 // their grids are mostly of uneven width, and tensor maps would not fit the
 // parameter space.
+// The compose kernel of a batch takes 32 x 16 tiles of 16 warps: its u' region
+// (the tile plus the sigma_warp halo) is then 1.25 instead of 1.5 times the
+// tile, the choice the single-job launches make by default.
+constexpr int K4B_NW = 16;
+
 struct BGeom {
     int D, H, W, TZ, gx, gy;
 };
@@ -133,12 +138,12 @@ __global__ void __launch_bounds__(FX *K3_NW) k_smooth_adam_batch(const __grid_co
 }
 
 template <int RG, bool SU>
-__global__ void __launch_bounds__(FX *K4_NW) k_compose_batch(const __grid_constant__ K4Batch b) {
+__global__ void __launch_bounds__(FX *K4B_NW, 2) k_compose_batch(const __grid_constant__ K4Batch b) {
     const int k = batch_job(b.first, b.n, (int)blockIdx.x);
     const K4Job &j = b.j[k];
     int bx, by, bz;
     batch_tile(j.geo, (int)blockIdx.x - b.first[k], bx, by, bz);
-    compose_body<RG, K4_NW, K4_OPT, SU, K4_ST_CP, false>(nullptr, j.u, j.dir, j.uo, j.Im, j.J,
+    compose_body<RG, K4B_NW, K4_OPT, SU, K4_ST_CP, false>(nullptr, j.u, j.dir, j.uo, j.Im, j.J,
                                                          j.gJ, j.h, j.geo.D, j.geo.H, j.geo.W,
                                                          j.geo.TZ, j.t, j.lr, j.c_lp, b.parity, bx,
                                                          by, bz);
@@ -232,7 +237,7 @@ cudaError_t launch_k3_batch(K3Batch &b, const LockstepJob *jobs, const int *idx,
 
 template <int RG, bool SU>
 cudaError_t launch_k4_batch(K4Batch &b, const LockstepJob *jobs, const int *idx, cudaStream_t s) {
-    using SC = K4S<RG, K4_NW, K4_OPT, SU, K4_ST_CP>;
+    using SC = K4S<RG, K4B_NW, K4_OPT, SU, K4_ST_CP>;
     auto kern = k_compose_batch<RG, SU>;
     static const int occ = prepare(kern, SC::bytes, SC::NT);
     long long tot = 0;
