@@ -351,6 +351,11 @@ template <>
 __device__ __forceinline__ float st_bits<__half>(unsigned short b) {
     return __half2float(__ushort_as_half(b));
 }
+// A stored moment as loaded (an FP32 value, or the bits of a 16-bit one), as FP32.
+template <class T>
+__device__ __forceinline__ float st_value(float x) { return x; }
+template <class T>
+__device__ __forceinline__ float st_value(unsigned short b) { return st_bits<T>(b); }
 
 __device__ __forceinline__ float adam_dir(float m, float v, float rbc1, float rbc2, float eps) {
     const float vh = v * rbc2;

@@ -225,7 +225,7 @@ cudaError_t launch_k3(const float *g, TS *m, TS *v, float *dir, WsHeader *h, Dim
         else
             le = launch_k3_tma<RG, 8, TS>(mp, g, m, v, dir, h, d, t, ac, parity, tc.tz, s);
     } else {
-        using SC = K3S<RG, K3_NW, K3_OPT, K3_ST_CP, S32>;
+        using SC = K3S<RG, K3_NW, K3_OPT, K3_ST_CP, false>;  // moments unstaged
         auto kern = k_smooth_adam<RG, K3_NW, K3_OPT, K3_ST_CP, false, TS>;
         static const int occ = prepare(kern, SC::bytes, SC::NT);
         LaunchGeom gg = geometry(occ, K3_NW, SC::TY, RG, d, tc.tz);

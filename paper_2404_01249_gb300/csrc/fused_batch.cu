@@ -224,7 +224,7 @@ cudaError_t launch_k2_batch(K2Batch &b, const LockstepJob *jobs, cudaStream_t s)
 // jobs[idx[0..b.n)] are the launch's jobs
 template <int RG, class TS>
 cudaError_t launch_k3_batch(K3Batch &b, const LockstepJob *jobs, const int *idx, cudaStream_t s) {
-    using SC = K3S<RG, K3_NW, K3_OPT, K3_ST_CP, sizeof(TS) == 4>;
+    using SC = K3S<RG, K3_NW, K3_OPT, K3_ST_CP, false>;  // moments unstaged
     auto kern = k_smooth_adam_batch<RG, TS>;
     static const int occ = prepare(kern, SC::bytes, SC::NT);
     long long tot = 0;

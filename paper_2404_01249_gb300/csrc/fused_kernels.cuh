@@ -40,6 +40,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <type_traits>
 #include <math.h>
 
 #include <map>
@@ -889,15 +890,16 @@ __global__ void __launch_bounds__(256) k_fused_mse_grad(const float *__restrict_
 }
 
 // ====================================================================== K3
-// S32: the moments m, nu are FP32 and arrive with the plane's copies; 16-bit
-// moments are loaded by each thread straight into registers one plane ahead.
-template <int RG, int NW, int OPT, int NSTG, bool S32 = true>
+// STAGED: the moments m, nu (FP32) arrive with the plane's TMA copies;
+// otherwise (16-bit moments, or the per-thread copy variant) each thread loads
+// its outputs' moments straight into registers one plane ahead.
+template <int RG, int NW, int OPT, int NSTG, bool STAGED = true>
 struct K3S {
     static constexpr int NT = FX * NW, TY = NW * OPT, RX = FX + 2 * RG, RY = TY + 2 * RG;
     static constexpr int XB = halo4(RG), BXW = FX + 2 * XB, COFF = XB - RG;
     static constexpr int NR = BXW * RY, NS = 2 * RG + 1, NOUT = NT * OPT;
     static constexpr size_t st_bytes = al128((size_t)3 * NR * 4);    // g
-    static constexpr size_t ost_bytes = S32 ? al128((size_t)6 * NOUT * 4) : 0;  // m, v
+    static constexpr size_t ost_bytes = STAGED ? al128((size_t)6 * NOUT * 4) : 0;  // m, v
     static constexpr unsigned tx_plane = 3u * NR * 4, tx_out = 6u * NOUT * 4;
     static constexpr size_t o_st = 0;
     static constexpr size_t o_ost = o_st + st_bytes * NSTG;
@@ -915,8 +917,10 @@ __device__ __forceinline__ void smooth_adam_body(const Maps *maps, const float *
                                                  int D, int H, int W, int TZ, const TT t,
                                                  const AdamConsts ac, int parity, int bx, int by,
                                                  int bz) {
-    constexpr bool S32 = sizeof(TS) == 4;
-    using S = K3S<RG, NW, OPT, NSTG, S32>;
+    constexpr bool S32 = sizeof(TS) == 4, STAGED = S32 && TMA;
+    using S = K3S<RG, NW, OPT, NSTG, STAGED>;
+    // moments as loaded into registers: FP32 values or 16-bit patterns
+    using FT = typename std::conditional<S32, float, unsigned short>::type;
     constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, BXW = S::BXW, COFF = S::COFF,
                   XB = S::XB, NS = S::NS, NOUT = S::NOUT;
     using G = Region<RY, RX, NW, BXW, COFF>;
@@ -947,7 +951,7 @@ __device__ __forceinline__ void smooth_adam_body(const Maps *maps, const float *
     const int zs = z0 - RG, np = zend - z0 + 2 * RG;
     auto issue = [&](int i) {
         const int zp = zs + i, zo = zp - RG, s = i % NSTG;
-        const bool out = S32 && zo >= z0 && zo < zend;
+        const bool out = STAGED && zo >= z0 && zo < zend;
         if (TMA) {
             if (tid == 0 && i < np) {
                 mbar_expect(bar + s, S::tx_plane + (out ? S::tx_out : 0u));
@@ -960,25 +964,18 @@ __device__ __forceinline__ void smooth_adam_body(const Maps *maps, const float *
         } else {
             if (i < np) {
                 rg.template load<3>(stage(s), g, N, (long long)zp * HW, zp >= 0 && zp < D);
-                if constexpr (S32) {
-                    if (out) {
-                        ou.template load<3, float>(ostage(s), m, N, (long long)zo * HW, tid);
-                        ou.template load<3, float>(ostage(s) + 3 * NOUT, v, N,
-                                                   (long long)zo * HW, tid);
-                    }
-                }
             }
             cp_commit();
         }
     };
-    // 16-bit moments of the next output plane, loaded one plane ahead
-    unsigned short mn[OPT][3], vn[OPT][3];
+    // unstaged moments of the next output plane, loaded one plane ahead
+    FT mn[OPT][3], vn[OPT][3];
     auto fetch_mv = [&](int i) {
-        if constexpr (!S32) {
+        if constexpr (!STAGED) {
             const int zo = zs + i - RG;
             if (i < np && zo >= z0 && zo < zend) {
-                ou.fetch(mn, (const unsigned short *)m, N, (long long)zo * HW);
-                ou.fetch(vn, (const unsigned short *)v, N, (long long)zo * HW);
+                ou.fetch(mn, (const FT *)m, N, (long long)zo * HW);
+                ou.fetch(vn, (const FT *)v, N, (long long)zo * HW);
             }
         }
     };
@@ -1000,7 +997,7 @@ __device__ __forceinline__ void smooth_adam_body(const Maps *maps, const float *
         const bool out = zo >= z0 && zo < zend;
         float mo[OPT][3], vo[OPT][3];
         if (out) {
-            if constexpr (S32) {
+            if constexpr (STAGED) {
                 const float *od = ostage(s) + tid;
 #pragma unroll
                 for (int o = 0; o < OPT; ++o)
@@ -1014,8 +1011,8 @@ __device__ __forceinline__ void smooth_adam_body(const Maps *maps, const float *
                 for (int o = 0; o < OPT; ++o)
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        mo[o][c] = st_bits<TS>(mn[o][c]);
-                        vo[o][c] = st_bits<TS>(vn[o][c]);
+                        mo[o][c] = st_value<TS>(mn[o][c]);
+                        vo[o][c] = st_value<TS>(vn[o][c]);
                     }
             }
         }
