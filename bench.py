@@ -486,7 +486,12 @@ VARIANT_BYTES = {
     "use_jac": PATH_BYTES,
     "affine": 8,              # I_f, I_m (12 parameters)
     "rigid": 8,
+    # BF16 storage: I_f, I_m and m, nu in 16 bits, u in 32
+    "microscopy": 2 + 2 + 12 + 6 + 6 + 12 + 6 + 6,
 }
+# the expansion-microscopy-shaped pair: 512 x 512 in-plane, 256 planes
+MICROSCOPY = dict(shape=(256, 512, 512), scales=(8, 4, 2, 1), iters=(200, 200, 100, 50),
+                  window=7)
 INVERSE_SCHEDULE = dict(scales=(4, 2, 1), iters=(100, 50, 25))
 SYM_INVERSE_SCHEDULE = dict(scales=(2, 1), iters=(50, 25))
 SVF_STEPS = 7
@@ -496,7 +501,9 @@ def run_variant(args):
     """One of the paper's other workloads on the brain-shaped pair: symmetric
     registration (with its post-hoc inverse), the post-hoc inverse of the
     pair's generating displacement, the SVF (exp) variant, the MI loss, the
-    use_jac direction, and the affine and rigid stages.  A step is one whole
+    use_jac direction, and the affine and rigid stages; or the
+    expansion-microscopy-shaped pair at 256 x 512 x 512 (window 7, scales
+    {8,4,2,1} x iterations {200,200,100,50}, BF16 images and moments).  A step is one whole
     call; the same timing rules as the main path (L2 flushed before every
     step, CUDA events, clocks sampled); the oracle is timed on one
     finest-level iteration of the same workload."""
@@ -510,14 +517,24 @@ def run_variant(args):
     build.build()
     fa.load()
     w = args.workload
-    shape = WORKLOAD["shape"]
-    f, m, psi = synth.voronoi_pair(shape=shape, seed=1000)
-    fixed, moving = torch.from_numpy(f).to(dev), torch.from_numpy(m).to(dev)
     base = dict(scales=WORKLOAD["scales"], iters=WORKLOAD["iters"], window=WORKLOAD["window"],
                 lr=WORKLOAD["lr"], sigma_grad=WORKLOAD["sigma_grad"],
                 sigma_warp=WORKLOAD["sigma_warp"], cc_eps=WORKLOAD["cc_eps"])
-    cfg = {"workload": f"{w}_voronoi_brain_160x192x224", "shape": list(shape)}
-    vi = voxel_iters(shape, WORKLOAD["scales"], WORKLOAD["iters"])
+    if w == "microscopy":
+        shape = MICROSCOPY["shape"]
+        f, m, psi = synth.microscopy_pair(shape=shape, seed=1000)
+        fixed = torch.from_numpy(f).to(dev).bfloat16()
+        moving = torch.from_numpy(m).to(dev).bfloat16()
+        base.update(scales=MICROSCOPY["scales"], iters=MICROSCOPY["iters"],
+                    window=MICROSCOPY["window"])
+        cfg = {"workload": "microscopy_cells_256x512x512", "shape": list(shape)}
+        vi = voxel_iters(shape, MICROSCOPY["scales"], MICROSCOPY["iters"])
+    else:
+        shape = WORKLOAD["shape"]
+        f, m, psi = synth.voronoi_pair(shape=shape, seed=1000)
+        fixed, moving = torch.from_numpy(f).to(dev), torch.from_numpy(m).to(dev)
+        cfg = {"workload": f"{w}_voronoi_brain_160x192x224", "shape": list(shape)}
+        vi = voxel_iters(shape, WORKLOAD["scales"], WORKLOAD["iters"])
     if w == "symmetric":
         P, Pi = fa.RegParams(**base), fa.RegParams(**SYM_INVERSE_SCHEDULE)
         call = lambda: fa.fa_register_symmetric(fixed, moving, P, Pi, sync=False)["loss"]  # noqa
@@ -534,6 +551,20 @@ def run_variant(args):
         P = fa.RegParams(**base)
         call = lambda: fa.fa_register_svf(fixed, moving, P, steps=SVF_STEPS, sync=False)["loss"]  # noqa
         cfg.update(base, squarings=SVF_STEPS, loss="lncc")
+    elif w == "microscopy":
+        import ctypes
+        P = fa.RegParams(**base, state="bf16")
+        pc = P.to_c()
+        pc.storage = fa.FA_BF16
+        ws = fa.workspace(fa.load().fa_register_workspace_size(*shape, ctypes.byref(pc)), dev)
+        if not args.no_autotune:
+            fa.fa_autotune(shape, P, ws=ws)
+        s_last = MICROSCOPY["scales"][-1]
+        uo = torch.empty((3,) + tuple(fa.level_size(a, s_last) for a in shape), device=dev)
+        lo = torch.empty((), device=dev)
+        call = lambda: fa.fa_register(fixed, moving, P, ws=ws, sync=False, u_out=uo, loss_out=lo)["loss"]  # noqa
+        cfg.update(base, storage="bf16 images and Adam moments, fp32 displacement and arithmetic",
+                   mode="fused", cells=int(round(1e-3 * np.prod(shape))))
     elif w in ("mi", "use_jac"):
         P = fa.RegParams(**base, loss="mi" if w == "mi" else "lncc", use_jac=(w == "use_jac"))
         ws = fa.workspace(fa.fa_register_workspace_size(shape, P), dev)
@@ -584,6 +615,9 @@ def run_variant(args):
                          "bytes_per_voxel_iter": VARIANT_BYTES[w]},
             "clocks": clk, "gpu_launches": int(launches), "final_value": float(last),
             "e2e": None}
+    if w == "microscopy":
+        line["dtype"] = "f32"
+        line["s_per_pair"] = total_ms / args.steps / 1e3
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = variant_oracle_sample(w, f, m, psi)
     print(json.dumps(line))
@@ -612,6 +646,9 @@ def variant_oracle_sample(w, f, m, psi):
         oracle.register(f, m, [1], [1], loss="mi" if w == "mi" else "lncc",
                         use_jac=(w == "use_jac"), window=WORKLOAD["window"],
                         cc_eps=WORKLOAD["cc_eps"], **kw)
+    elif w == "microscopy":
+        oracle.register(f, m, [1], [1], window=MICROSCOPY["window"], cc_eps=WORKLOAD["cc_eps"],
+                        **kw)
     elif w == "affine":
         oracle.affine_register(f, m, [1], [1], lr=3e-3, window=WORKLOAD["window"],
                                cc_eps=WORKLOAD["cc_eps"])
@@ -620,9 +657,10 @@ def variant_oracle_sample(w, f, m, psi):
                               cc_eps=WORKLOAD["cc_eps"])
     dt = time.perf_counter() - t0
     n = int(np.prod(f.shape))
+    grid = "x".join(str(a) for a in f.shape)
     return {"value": n / dt, "unit": METRIC, "cores": int(os.environ["OMP_NUM_THREADS"]),
             "kind": "oracle",
-            "sample": "1 finest-level iteration (scale 1, 160x192x224) of the same workload "
+            "sample": f"1 finest-level iteration (scale 1, {grid}) of the same workload "
                       "plus the oracle's final evaluation"}
 
 
@@ -649,8 +687,9 @@ def main():
                     help="--batched: time only the chosen schedule (profiling runs)")
     ap.add_argument("--workload", default="brain",
                     choices=["brain", "symmetric", "inverse", "svf", "mi", "use_jac", "affine",
-                             "rigid"],
-                    help="one of the paper's other workloads on the brain-shaped pair")
+                             "rigid", "microscopy"],
+                    help="one of the paper's other workloads on the brain-shaped pair, or "
+                         "the microscopy-shaped pair at its full size")
     ap.add_argument("--scales", type=int, nargs="+", default=None,
                     help="override the pyramid scales (profiling runs; changes the workload)")
     ap.add_argument("--iters", type=int, nargs="+", default=None,

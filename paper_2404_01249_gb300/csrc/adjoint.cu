@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(256) k_scatter_finalize(const long long *__res
     const float inv = pow2f(-sh);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
-        out[i] = __ll2float_rn(acc[i]) * inv;
+        out[i] = i64_to_float_rn(acc[i]) * inv;
 }
 
 }  // namespace

@@ -246,20 +246,37 @@ __device__ __forceinline__ long long quantize(float v, float scale) {
     return ((long long)k << 20) + l;
 }
 
-// Exact int64 value of an integer-valued float with |f| < 2^63, from its bits.
-__device__ __forceinline__ long long float_int_to_ll(float f) {
-    const unsigned b = __float_as_uint(f);
-    const int ex = (int)((b >> 23) & 0xffu) - 150;
-    const long long m = (long long)((b & 0x7fffffu) | 0x800000u);
-    long long r = ex >= 0 ? (m << (ex & 63)) : (m >> ((-ex) & 63));
-    r = (b & 0x7fffffffu) ? r : 0;
-    return (b >> 31) ? -r : r;
+// The conversions below avoid the 64-bit integer-to-float instruction, which
+// on sm_103 runs on the narrow FP64 pipe (about 2 per clock per SM) and
+// limited the exact-sum kernels; they use 32-bit conversions, integer
+// operations and FP32 adds, and give the same bits as that instruction.
+
+// uint64 -> float, rounded to nearest even: the leading 24 bits, rounded by
+// the 40 bits below them (a carry out of the mantissa raises the exponent).
+__device__ __forceinline__ float u64_to_float_rn(unsigned long long u) {
+    if (u == 0ull) return 0.0f;
+    const int lz = __clzll((long long)u);
+    const unsigned long long m = u << lz;  // bit 63 set
+    unsigned mant = (unsigned)(m >> 40);   // 24 bits, the leading one included
+    const unsigned long long rest = m & 0xFFFFFFFFFFull, half = 1ull << 39;
+    mant += (rest > half || (rest == half && (mant & 1u))) ? 1u : 0u;
+    return __uint_as_float(((unsigned)(190 - lz) << 23) + (mant - 0x800000u));
 }
 
-// int64 -> (hi, lo) floats with hi + lo == x exactly for |x| < 2^48.
+__device__ __forceinline__ float i64_to_float_rn(long long x) {
+    const float f = u64_to_float_rn(x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x);
+    return x < 0 ? -f : f;
+}
+
+// int64 -> (hi, lo) floats with hi + lo == x exactly for |x| < 2^48: hi is x
+// rounded to nearest, lo = x - hi.  x = a 2^24 + b with |a| < 2^24 and
+// 0 <= b < 2^24, both exact in FP32; hi = a 2^24 + b rounded, and lo is the
+// exact error of that sum (|a 2^24| >= b unless a = 0).
 __device__ __forceinline__ void i64_to_ff(long long x, float &hi, float &lo) {
-    hi = __ll2float_rn(x);
-    lo = __ll2float_rn(x - float_int_to_ll(hi));
+    const float fh = __int2float_rn((int)(x >> 24)) * 16777216.0f;
+    const float fl = __uint2float_rn((unsigned)x & 0xFFFFFFu);
+    hi = __fadd_rn(fh, fl);
+    lo = __fsub_rn(fl, __fsub_rn(hi, fh));
 }
 
 // n a - b c for int64 operands, formed exactly in 128 bits and rounded to
@@ -270,9 +287,10 @@ __device__ __forceinline__ float diff_i128_to_float(long long n, long long a, lo
     const __int128 r = (__int128)n * a - (__int128)b * c;
     const long long hi = (long long)(r >> 64);
     const unsigned long long lo = (unsigned long long)r;
-    if (hi == 0) return __ull2float_rn(lo);
-    if (hi == -1 && (long long)lo < 0) return __ll2float_rn((long long)lo);
-    return fmaf(__ll2float_rn(hi), 18446744073709551616.0f, __ull2float_rn(lo));
+    if (hi == 0) return u64_to_float_rn(lo);
+    if (hi == -1 && (long long)lo < 0) return i64_to_float_rn((long long)lo);
+    // |hi| < 2^24 here (|r| < 2^88), so its 32-bit conversion is exact
+    return fmaf(__int2float_rn((int)hi), 18446744073709551616.0f, u64_to_float_rn(lo));
 }
 
 // ---------------------------------------------------------- float-float
@@ -322,9 +340,6 @@ __device__ __forceinline__ void lncc_c_ff(float A, float B, long long sI, long l
     cl = -pl;
 }
 
-// Adam direction d = (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps) with the
-// bias corrections passed as reciprocals; square root and quotient use the
-// hardware approximations (a few ulp).
 // Storage of the Adam moments: FP32, or 16-bit values read as FP32 and
 // written rounded to nearest (all arithmetic is FP32).
 __device__ __forceinline__ float st_load(float x) { return x; }
@@ -357,6 +372,9 @@ __device__ __forceinline__ float st_value(float x) { return x; }
 template <class T>
 __device__ __forceinline__ float st_value(unsigned short b) { return st_bits<T>(b); }
 
+// Adam direction d = (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps) with the
+// bias corrections passed as reciprocals; square root and quotient use the
+// hardware approximations (a few ulp).
 __device__ __forceinline__ float adam_dir(float m, float v, float rbc1, float rbc2, float eps) {
     const float vh = v * rbc2;
     const float sq = vh > 0.0f ? vh * rsqrtf(vh) : 0.0f;

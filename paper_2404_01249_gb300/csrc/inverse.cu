@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(256) k_field_scatter_add(const long long *__re
     const float f = factor * pow2f(-sh);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n3;
          i += (long long)gridDim.x * blockDim.x)
-        g[i] = fmaf(__ll2float_rn(acc[i]), f, g[i]);
+        g[i] = fmaf(i64_to_float_rn(acc[i]), f, g[i]);
 }
 
 __global__ void k_energy_finalize(const float *__restrict__ partials, int nb, long long N,
