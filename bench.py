@@ -185,9 +185,10 @@ def traffic_from_profile(kernel: str, n_voxels: int):
         with open(p) as f:
             d = json.load(f)
         e = d[kernel]
-        src = os.path.join(ROOT, "paper_2404_01249_gb300", "csrc", e["source"])
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if sha != e["source_sha"]:
+        h = hashlib.sha256()
+        for name in e["sources"]:  # the kernel's code and the helpers it inlines
+            h.update(open(os.path.join(ROOT, "paper_2404_01249_gb300", "csrc", name), "rb").read())
+        if h.hexdigest()[:16] != e["sources_sha"]:
             return None
         return float(e["dram_bytes_per_voxel"]) * n_voxels
     except Exception:
