@@ -149,19 +149,22 @@ __global__ void __launch_bounds__(FX *K4B_NW, 2) k_compose_batch(const __grid_co
                                                          by, bz);
 }
 
-// Slab depth of one job in a lockstep launch: the job gets the share of the
-// GPU's resident CTA slots that its voxels are of the launch's voxels, and TZ
-// minimises (waves x planes per CTA) on that share.
-int batch_tz(Dims d, int tiles_xy, int halo, int occ, long long vox, long long total_vox) {
+// Slab depth of a lockstep launch: one TZ for all its jobs (each capped at its
+// own depth), minimising (waves x planes per CTA) over the whole launch, whose
+// CTAs fill the GPU's resident slots together.  A coarse level of many jobs
+// then takes short slabs (more CTAs), a fine level long ones (less halo).
+int launch_tz(const Dims *d, int n, int ty, int halo, int occ) {
     const long long slots = (long long)num_sms() * (occ > 0 ? occ : 1);
-    long long share = total_vox > 0 ? slots * vox / total_vox : slots;
-    if (share < 1) share = 1;
-    int best = d.D;
+    int best = 64;
     long long bestcost = -1;
-    for (int tz = 1; tz <= d.D && tz <= 64; ++tz) {
-        const long long ctas = (long long)tiles_xy * ((d.D + tz - 1) / tz);
-        const long long waves = (ctas + share - 1) / share;
-        const long long cost = waves * (tz + 2 * halo);
+    for (int tz = 1; tz <= 64; ++tz) {
+        long long ctas = 0;
+        for (int k = 0; k < n; ++k) {
+            const long long txy = (long long)((d[k].W + FX - 1) / FX) * ((d[k].H + ty - 1) / ty);
+            const int t = tz < d[k].D ? tz : d[k].D;
+            ctas += txy * ((d[k].D + t - 1) / t);
+        }
+        const long long cost = (ctas + slots - 1) / slots * (tz + 2 * halo);
         if (bestcost < 0 || cost < bestcost) {
             bestcost = cost;
             best = tz;
@@ -170,15 +173,15 @@ int batch_tz(Dims d, int tiles_xy, int halo, int occ, long long vox, long long t
     return best;
 }
 
-// Fills a job's tile geometry for a kernel with `ty` rows per CTA and returns
-// its CTA count.
-int batch_geom(BGeom &g, Dims d, int ty, int halo, int occ, long long total_vox) {
+// Fills a job's tile geometry for a kernel with `ty` rows per CTA and slab
+// depth tz (capped at the job's depth) and returns its CTA count.
+int batch_geom(BGeom &g, Dims d, int ty, int tz) {
     g.D = d.D;
     g.H = d.H;
     g.W = d.W;
     g.gx = (d.W + FX - 1) / FX;
     g.gy = (d.H + ty - 1) / ty;
-    g.TZ = batch_tz(d, g.gx * g.gy, halo, occ, d.N(), total_vox);
+    g.TZ = tz < d.D ? tz : d.D;
     return g.gx * g.gy * ((d.D + g.TZ - 1) / g.TZ);
 }
 
@@ -200,11 +203,12 @@ cudaError_t launch_k1_batch(K1Batch &b, const LockstepJob *jobs, cudaStream_t s)
     using SC = K1S<R, K1_NW, K1_OPT, K1_ST_CP>;
     auto kern = k_lncc_fwd_batch<R>;
     static const int occ = prepare(kern, SC::bytes, SC::NT);
-    long long tot = 0;
-    for (int k = 0; k < b.n; ++k) tot += jobs[k].d.N();
+    Dims dd[kMaxLockstepJobs];
+    for (int k = 0; k < b.n; ++k) dd[k] = jobs[k].d;
+    const int tz = launch_tz(dd, b.n, SC::TY, R, occ);
     b.first[0] = 0;
     for (int k = 0; k < b.n; ++k)
-        b.first[k + 1] = b.first[k] + batch_geom(b.j[k].g, jobs[k].d, SC::TY, R, occ, tot);
+        b.first[k + 1] = b.first[k] + batch_geom(b.j[k].g, dd[k], SC::TY, tz);
     return launch_batch(kern, b, SC::NT / FX, SC::bytes, s);
 }
 
@@ -213,11 +217,12 @@ cudaError_t launch_k2_batch(K2Batch &b, const LockstepJob *jobs, cudaStream_t s)
     using SC = K2S<R, K2_NW, K2_OPT, K2_ST_CP>;
     auto kern = k_lncc_grad_batch<R>;
     static const int occ = prepare(kern, SC::bytes, SC::NT);
-    long long tot = 0;
-    for (int k = 0; k < b.n; ++k) tot += jobs[k].d.N();
+    Dims dd[kMaxLockstepJobs];
+    for (int k = 0; k < b.n; ++k) dd[k] = jobs[k].d;
+    const int tz = launch_tz(dd, b.n, SC::TY, R, occ);
     b.first[0] = 0;
     for (int k = 0; k < b.n; ++k)
-        b.first[k + 1] = b.first[k] + batch_geom(b.j[k].geo, jobs[k].d, SC::TY, R, occ, tot);
+        b.first[k + 1] = b.first[k] + batch_geom(b.j[k].geo, dd[k], SC::TY, tz);
     return launch_batch(kern, b, SC::NT / FX, SC::bytes, s);
 }
 
@@ -227,11 +232,12 @@ cudaError_t launch_k3_batch(K3Batch &b, const LockstepJob *jobs, const int *idx,
     using SC = K3S<RG, K3_NW, K3_OPT, K3_ST_CP, false>;  // moments unstaged
     auto kern = k_smooth_adam_batch<RG, TS>;
     static const int occ = prepare(kern, SC::bytes, SC::NT);
-    long long tot = 0;
-    for (int k = 0; k < b.n; ++k) tot += jobs[idx[k]].d.N();
+    Dims dd[kMaxLockstepJobs];
+    for (int k = 0; k < b.n; ++k) dd[k] = jobs[idx[k]].d;
+    const int tz = launch_tz(dd, b.n, SC::TY, RG, occ);
     b.first[0] = 0;
     for (int k = 0; k < b.n; ++k)
-        b.first[k + 1] = b.first[k] + batch_geom(b.j[k].geo, jobs[idx[k]].d, SC::TY, RG, occ, tot);
+        b.first[k + 1] = b.first[k] + batch_geom(b.j[k].geo, dd[k], SC::TY, tz);
     return launch_batch(kern, b, SC::NT / FX, SC::bytes, s);
 }
 
@@ -240,11 +246,12 @@ cudaError_t launch_k4_batch(K4Batch &b, const LockstepJob *jobs, const int *idx,
     using SC = K4S<RG, K4B_NW, K4_OPT, SU, K4_ST_CP>;
     auto kern = k_compose_batch<RG, SU>;
     static const int occ = prepare(kern, SC::bytes, SC::NT);
-    long long tot = 0;
-    for (int k = 0; k < b.n; ++k) tot += jobs[idx[k]].d.N();
+    Dims dd[kMaxLockstepJobs];
+    for (int k = 0; k < b.n; ++k) dd[k] = jobs[idx[k]].d;
+    const int tz = launch_tz(dd, b.n, SC::TY, RG, occ);
     b.first[0] = 0;
     for (int k = 0; k < b.n; ++k)
-        b.first[k + 1] = b.first[k] + batch_geom(b.j[k].geo, jobs[idx[k]].d, SC::TY, RG, occ, tot);
+        b.first[k + 1] = b.first[k] + batch_geom(b.j[k].geo, dd[k], SC::TY, tz);
     return launch_batch(kern, b, SC::NT / FX, SC::bytes, s);
 }
 
