@@ -49,6 +49,22 @@ def test_adjoint_matches_oracle(fa, orc, shape, window):
     assert rel(r["dL_dmoving"], orc.warp_adjoint(ref["dJ"], u, shape)) < TOL
 
 
+def test_adjoint_full_brain_size_matches_oracle(fa, orc):
+    """The warp+LNCC adjoint at the brain workload's size (160x192x224, the
+    differentiation config's large case) against the oracle on every voxel:
+    loss and the three gradients within 1e-5 (max-norm relative)."""
+    shape = (160, 192, 224)
+    f, m, _ = synth.voronoi_pair(shape=shape, seed=1000)
+    u = synth.random_field(shape, 8.0, 4.0, seed=1001).astype(np.float32)
+    r = fa.fa_warp_lncc_adjoint(cuda(f), cuda(m), cuda(u), 5, 1e-5)
+    Jr, gr = orc.warp(m, u)
+    ref = orc.lncc(f, Jr, 5, np.float32(1e-5), want_dJ=True, want_dI=True)
+    assert abs(float(r["loss"]) - ref["loss"]) <= TOL * abs(ref["loss"])
+    assert rel(r["dL_dfixed"], ref["dI"]) < TOL
+    assert rel(r["dL_du"], ref["dJ"][None] * gr) < TOL
+    assert rel(r["dL_dmoving"], orc.warp_adjoint(ref["dJ"], u, shape)) < TOL
+
+
 def test_adjoint_outputs_are_optional_and_deterministic(fa):
     shape = (16, 20, 24)
     f, m, _ = synth.voronoi_pair(shape=shape, seed=5)
