@@ -132,6 +132,21 @@ def test_fused_brain_level_against_oracle(fa, orc):
     assert mean_disp_diff(out["u"], ref["u"]) < 0.05
 
 
+def test_brain_workload_full_size_against_oracle(fa, orc):
+    """The benchmarked workload itself, end to end at full size: the
+    160x192x224 brain-shaped pair with scales {4,2,1} x iterations
+    {200,100,50} in the fused schedule against the oracle's FP64 Algorithm 1
+    on the same pair: final LNCC within 1e-3 and mean displacement difference
+    below 0.05 voxel (the oracle takes about a minute on 16 cores)."""
+    f, m, _ = synth.voronoi_pair(shape=(160, 192, 224), seed=1000)
+    out = fa.fa_register(cuda(f), cuda(m), fa.RegParams())
+    f32 = lambda x: float(np.float32(x))
+    ref = orc.register(f, m, [4, 2, 1], [200, 100, 50], cc_eps=f32(1e-5), beta1=f32(0.9),
+                       beta2=f32(0.999), adam_eps=f32(1e-8))
+    assert abs(out["final_loss"] - ref["final_loss"]) < 1e-3
+    assert mean_disp_diff(out["u"], ref["u"]) < 0.05
+
+
 @pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
 def test_16bit_images_equal_fp32_of_the_rounded_images(fa, dtype):
     """16-bit images are widened exactly, so registering them equals
