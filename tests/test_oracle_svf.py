@@ -53,3 +53,45 @@ def test_recovers_a_subvoxel_translation(orc):
     inner = (slice(None),) + (slice(5, -5),) * 3
     est = r["u"][inner].reshape(3, -1).mean(1)
     assert np.abs(est + t).max() < 0.1   # the map that undoes the shift
+
+
+def _steps_to_diffeomorphism(orc, name, n):
+    """Smallest number of squarings M after which the oracle's exp(v) of the
+    named 1-D field, sampled on n points of [-1, 1] (velocity in units of the
+    interval, converted to voxels), is strictly increasing on the grid."""
+    x = np.linspace(-1.0, 1.0, n)
+    g = np.exp(-5.0 * x ** 2)
+    v = {"simple_gaussian": g,
+         "gaussian_sinusoid": g * (1.0 + np.sin(20.0 * np.pi * x)),
+         "complex_modulation": g * (1.0 + 0.7 * np.sin(np.pi * np.exp(np.abs(np.pi * x) ** 3)))}[name]
+    V = np.zeros((3, 1, 1, n))
+    V[2, 0, 0] = v * (n - 1) / 2.0
+    for steps in range(16):
+        phi = np.arange(n) + orc.svf_exp(V, steps)[2, 0, 0]
+        if np.all(np.diff(phi) > 0):
+            return steps
+    return None
+
+
+def test_scaling_and_squaring_steps_of_the_papers_1d_fields(orc):
+    """The paper's 1-D experiment: the printed step counts (1, 6, 10) for its
+    three fields.  Its grid is not printed, so each count is checked on a
+    grid where that field's count does not depend on the reading of the
+    boundary or of the sampling: the sinusoid needs 6 squarings on every
+    grid from 201 to 4001 points; the Gaussian needs 1 on 201 points (on
+    finer grids its value at the interval's end, e^-5 of the half-width, is
+    more than a voxel and the zero extension outside the grid folds it); the
+    complex modulation, whose slope grows with the sampling density near the
+    interval's ends, needs 10 on 4001 points.  The order of the three holds
+    on every grid."""
+    import json
+    import os
+    fx = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "svf_1d_steps.json")))
+    want = dict(zip(fx["fields"], fx["steps_printed"]))
+    assert _steps_to_diffeomorphism(orc, "simple_gaussian", 201) == want["simple_gaussian"]
+    for n in (201, 1001, 4001):
+        assert _steps_to_diffeomorphism(orc, "gaussian_sinusoid", n) == want["gaussian_sinusoid"]
+    assert _steps_to_diffeomorphism(orc, "complex_modulation", 4001) == want["complex_modulation"]
+    for n in (201, 1001):
+        m = [_steps_to_diffeomorphism(orc, f, n) for f in fx["fields"]]
+        assert m[0] <= m[1] <= m[2]
