@@ -508,7 +508,9 @@ fa_status fused_autotune_level(FusedBuffers &fb, WsHeader *h, const fa_params *p
                 g_force = &c;
                 cudaError_t e = launch(kernel);  // warm
                 if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-                for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch(kernel);
+                // 12 launches: the coarse levels' launches take 10-20 us, so
+                // fewer would leave the choice to timer noise
+                for (int r = 0; r < 12 && e == cudaSuccess; ++r) e = launch(kernel);
                 if (e == cudaSuccess) e = cudaEventRecord(e1, s);
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                 g_force = nullptr;
