@@ -61,7 +61,11 @@
  *   R-up      level hand-off: trilinear align-corners; u scaled by
  *             s_a = (Nf_a - 1)/(Nc_a - 1) per axis, m by 1/s_a and v by
  *             1/s_a^2 (state kept fixed in normalised coordinates);
- *             s_a = 1 when Nc_a == 1 or Nf_a == 1.
+ *             s_a = 1 when Nc_a == 1 or Nf_a == 1.  m and v are statistics
+ *             of dL/du, which the chain rule makes a covector (dL/du_fine =
+ *             dL/du_coarse / s_a), so these factors are the ones for which
+ *             the handed-off state equals the state of a fine-level Adam fed
+ *             the same gradient history.
  */
 #include <math.h>
 #include <stdint.h>

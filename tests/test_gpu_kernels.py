@@ -171,8 +171,10 @@ def test_full_size_warp_and_lncc(fa, orc):
     J, g = fa.fa_warp(cuda(m), cuda(u))
     Jr, gr = orc.warp(m, u)
     assert rel(J, Jr) < TOL and rel(g, gr) < TOL
-    Jn = J.cpu().numpy()
-    out = fa.fa_lncc_fwd_bwd(cuda(f), J, 5, 1e-5)
+    # the LNCC kernels take the oracle's own warped image (rounded to FP32),
+    # so no CUDA output feeds the oracle
+    Jn = Jr.astype(np.float32)
+    out = fa.fa_lncc_fwd_bwd(cuda(f), cuda(Jn), 5, 1e-5)
     ref = orc.lncc(f, Jn, 5, np.float32(1e-5))
     assert abs(float(out["loss"]) - ref["loss"]) <= TOL * abs(ref["loss"])
     assert rel(out["dJ"], ref["dJ"]) < TOL

@@ -119,7 +119,7 @@ def test_downsample_affine_image_in_interior(orc):
     assert np.allclose(out[ok], exact[ok], atol=1e-11)
 
 
-def test_upsample_affine_field_exact_and_moment_scaling(orc):
+def test_upsample_affine_field_exact(orc):
     cshape, fshape = (5, 6, 7), (10, 12, 14)
     xc = grid(cshape)
     A = 0.1 * rng(50).standard_normal((3, 3))
@@ -131,12 +131,74 @@ def test_upsample_affine_field_exact_and_moment_scaling(orc):
     xcf = xf / s[:, None, None, None]           # fine voxel -> coarse coordinate
     exact = (np.einsum("ab,b...->a...", A, xcf) + b[:, None, None, None]) * s[:, None, None, None]
     assert np.allclose(out, exact, atol=1e-12)
-    const = np.ones((3,) + cshape)
-    m = orc.upsample_field(const, fshape, -1)
-    v = orc.upsample_field(const, fshape, -2)
+
+
+def _level_fields(shape, funcs, power):
+    """Covector fields of one level from smooth functions F_a(p) of the
+    normalised coordinate p in [-1, 1]^3 (align-corners): by the chain rule
+    for u_norm,a = u_vox,a * 2 / (n_a - 1), a derivative with respect to the
+    voxel displacement is F_a(p) * (2 / (n_a - 1)), a squared one
+    F_a(p) * (2 / (n_a - 1))^2 (power 1 or 2)."""
+    p = np.stack(np.meshgrid(*[np.linspace(-1.0, 1.0, n) for n in shape], indexing="ij"))
+    return np.stack([funcs[a](p) * (2.0 / (shape[a] - 1)) ** power for a in range(3)])
+
+
+def test_moment_handoff_commutes_with_adam(orc):
+    """Reading R-up (section "Interpolation strategies", Algorithm 1's
+    upsampling of phi and the optimiser state): m and nu are running
+    statistics of dL/du, and the chain rule makes that derivative a covector
+    (the fine-level gradient at a point shared by both grids is the coarse one
+    divided by s_a, since u_fine = s_a u_coarse).  Handing off the moments is
+    therefore right exactly when the handed-off state equals the state a
+    fine-level Adam would hold after the same gradient history expressed at
+    the fine level.  Run Adam T steps on both levels from zero with the two
+    levels' chain-rule gradients of one smooth sequence, hand the coarse state
+    off with or_upsample_field(-1) and (-2), and compare on the coincident
+    grid points (where trilinear interpolation is exact); then one more step
+    on both sides gives the same direction d.  The other readings (m * s_a,
+    nu * s_a^2) and no scaling both fail the same check."""
+    cshape, fshape = (5, 7, 9), (9, 13, 25)          # s_a = 2, 2, 3
+    s = np.array([(f - 1) / (c - 1) for c, f in zip(cshape, fshape)])
+    T = 6
+    r = rng(61)
+
+    def grad_funcs(k):
+        a = r.standard_normal((3, 4))
+        return [lambda p, q=a[c]: q[0] + q[1] * np.sin(1.3 * p[0] + q[2]) * np.cos(0.7 * p[1])
+                + q[3] * p[2] * p[1] for c in range(3)]
+
+    hist = [grad_funcs(k) for k in range(T + 1)]
+    # eps = 0: with eps > 0 Adam is not scale-invariant, so the check would
+    # test eps instead of the hand-off
+    zc, zf = np.zeros((3,) + cshape), np.zeros((3,) + fshape)
+    mc, vc, mf, vf = zc, zc, zf, zf
+    for k in range(T):
+        _, mc, vc = orc.adam(_level_fields(cshape, hist[k], 1), mc, vc, k + 1, eps=0.0)
+        _, mf, vf = orc.adam(_level_fields(fshape, hist[k], 1), mf, vf, k + 1, eps=0.0)
+    co = tuple(slice(0, None, int(sa)) for sa in s)   # fine points on the coarse grid
+    assert all(len(range(n)[sl]) == c for n, sl, c in zip(fshape, co, cshape))
+    m_up = orc.upsample_field(mc, fshape, -1)
+    v_up = orc.upsample_field(vc, fshape, -2)
     for a in range(3):
-        assert np.allclose(m[a], 1.0 / s[a], rtol=1e-15)
-        assert np.allclose(v[a], 1.0 / s[a] ** 2, rtol=1e-15)
+        np.testing.assert_allclose(m_up[a][co], mf[a][co], rtol=1e-12,
+                                   atol=1e-12 * np.abs(mf[a]).max())
+        np.testing.assert_allclose(v_up[a][co], vf[a][co], rtol=1e-12)
+    # the next step's direction is the same on both sides
+    gf = _level_fields(fshape, hist[T], 1)
+    d_up, _, _ = orc.adam(gf, m_up, v_up, T + 1, eps=0.0)
+    d_ref, _, _ = orc.adam(gf, mf, vf, T + 1, eps=0.0)
+    for a in range(3):
+        np.testing.assert_allclose(d_up[a][co], d_ref[a][co], rtol=1e-10, atol=1e-12)
+    # the alternatives: m * s_a, nu * s_a^2 (power +1 on both, then once more
+    # s_a on nu), and no scaling (power +1 divided back out of the values)
+    m_alt = orc.upsample_field(mc, fshape, 1)
+    v_alt = orc.upsample_field(vc, fshape, 1) * s[:, None, None, None]
+    m_raw = m_alt / s[:, None, None, None]
+    v_raw = v_alt / s[:, None, None, None] ** 2
+    for mm, vv in ((m_alt, v_alt), (m_raw, v_raw)):
+        d_alt, _, _ = orc.adam(gf, mm, vv, T + 1, eps=0.0)
+        err = max(np.abs(d_alt[a][co] - d_ref[a][co]).max() for a in range(3))
+        assert err > 1e-2
 
 
 def test_upsample_preserves_positive_jacobian(orc):
