@@ -297,9 +297,11 @@ def run_gpu(args):
     vi = voxel_iters(shape, WORKLOAD["scales"], WORKLOAD["iters"])
     value = world * vi * args.steps / (total_ms / 1e3)
 
-    # per-kernel rooflines from the finest-level launches of the timed steps;
-    # the reported one is the kernel with the longest average launch (each
-    # runs once per iteration)
+    # Roofline of the finest-level iteration: the whole path's algorithmic
+    # bytes (read I_f, I_m, u, m, nu and write u, m, nu once: 80 B per voxel)
+    # over the summed average launch times of the iteration's kernels, timed
+    # with CUDA events inside the recorded graph.  Each kernel's own
+    # input+output bytes (its intermediates included) give kernel_io_frac.
     n_fine = int(np.prod([level_size(a, WORKLOAD["scales"][fin]) for a in shape]))
     peak, peak_kind = measured_peak()
     kernels = {}
@@ -309,17 +311,29 @@ def run_gpu(args):
         avg_ms = float(np.mean(kt))
         algo = ALGO_BYTES[kn] * n_fine
         achieved = algo / (avg_ms / 1e3) / 1e9
-        kernels[kn] = {"avg_launch_ms": avg_ms, "launches_timed": len(kt), "algo_bytes": algo,
+        kernels[kn] = {"avg_launch_ms": avg_ms, "launches_timed": len(kt), "io_bytes": algo,
                        "achieved": achieved, "frac": achieved / peak,
                        "traffic": traffic_from_profile(kn, n_fine)}
-    kname = max(kernels, key=lambda k: kernels[k]["avg_launch_ms"])
-    kd = kernels[kname]
-    roofline = {"bound": "hbm", "kernel": kname, "achieved": kd["achieved"], "peak": peak,
-                "peak_kind": peak_kind, "unit": "GB/s", "frac": kd["frac"],
-                "traffic": kd["traffic"], "algo_bytes": kd["algo_bytes"],
-                "avg_launch_ms": kd["avg_launch_ms"], "launches_timed": kd["launches_timed"],
-                "all_kernels": {k: {"avg_launch_ms": round(v["avg_launch_ms"], 4),
-                                    "frac": round(v["frac"], 4)} for k, v in kernels.items()},
+    iter_ms = float(sum(k["avg_launch_ms"] for k in kernels.values()))
+    iter_algo = PATH_BYTES * n_fine
+    iter_achieved = iter_algo / (iter_ms / 1e3) / 1e9
+    traffics = [k["traffic"] for k in kernels.values()]
+    iter_traffic = None if any(t is None for t in traffics) else float(sum(traffics))
+    dom = max(kernels, key=lambda k: kernels[k]["avg_launch_ms"])
+    roofline = {"bound": "hbm", "kernel": "finest_level_iteration",
+                "kernels": list(kernels), "achieved": iter_achieved, "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": iter_achieved / peak,
+                "traffic": iter_traffic, "algo_bytes": iter_algo,
+                "algo_bytes_per_voxel_iter": PATH_BYTES, "voxels": n_fine,
+                "iteration_ms": iter_ms,
+                "traffic_ratio": (None if iter_traffic is None else iter_traffic / iter_algo),
+                "dominant_kernel": {"name": dom,
+                                    "avg_launch_ms": kernels[dom]["avg_launch_ms"],
+                                    "launches_timed": kernels[dom]["launches_timed"]},
+                "kernel_io_frac": {k: {"avg_launch_ms": round(v["avg_launch_ms"], 4),
+                                       "io_bytes_per_voxel": ALGO_BYTES[k],
+                                       "frac": round(v["frac"], 4)}
+                                   for k, v in kernels.items()},
                 "path": {"bytes_per_voxel_iter": PATH_BYTES,
                          "achieved": PATH_BYTES * vi * args.steps / (total_ms / 1e3) / 1e9,
                          "frac": PATH_BYTES * vi * args.steps / (total_ms / 1e3) / 1e9 / peak}}

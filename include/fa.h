@@ -172,6 +172,8 @@ fa_status fa_lncc_fwd_bwd(const fa_vol *fixed, const fa_vol *warped, int32_t win
  * grid may hold at most 621,376 voxels (larger grids return FA_ERR_SHAPE
  * before any launch).  The first call on each device looks up the array's
  * address with that device current; make it before any stream capture.
+ * The address is kept per device and CUDA context: after a device reset the
+ * next call looks it up again and must likewise precede any capture.
  * All calls share the array (each clears what must start at zero); calls
  * that overlap on the GPU race and must be serialised by the caller.  No
  * counterpart in the paper: an integration convenience of this library. */
@@ -234,11 +236,17 @@ size_t fa_radam_workspace_size(int32_t D, int32_t H, int32_t W);
  * nearest, the direction coming from the FP32 values; FP16 moments must lie
  * in its normal range to keep their precision); one grid; u_out must not
  * alias u_in.
- * t >= 1 is the step number after increment.  Uses p->beta1, beta2,
- * adam_eps, lr, c_lp.  eps_t_dev (device float, may be NULL) receives eps_t.
- * A non-finite max|d| sets the workspace status word (see fa_ws_status). */
+ * t_dev is a DEVICE int32 holding the number of steps taken so far (0 before
+ * the first): the step uses t = *t_dev + 1 and the call advances *t_dev to t
+ * on the stream, so a sequence of calls can be recorded in a CUDA graph and
+ * replayed without host involvement.  The bias corrections 1 / (1 - beta^t)
+ * are formed on the device in FP32 as -1 / expm1(t log1p(beta - 1)).  A
+ * counter below 0 leaves u_out = u_in and sets FA_ERR_NONFINITE in the
+ * status word.  Uses p->beta1, beta2, adam_eps, lr, c_lp.  eps_t_dev (device
+ * float, may be NULL) receives eps_t.  A non-finite max|d| sets the
+ * workspace status word (see fa_ws_status). */
 fa_status fa_radam_step(const fa_vol *u_in, fa_vol *u_out, fa_vol *m, fa_vol *v,
-                        const fa_vol *g, int32_t t, const fa_params *p, float *eps_t_dev,
+                        const fa_vol *g, int32_t *t_dev, const fa_params *p, float *eps_t_dev,
                         void *ws, size_t ws_bytes, void *stream);
 
 /* Pyramid level (Algorithm 1 "downsample(I, s)"; section "Interpolation
@@ -248,6 +256,16 @@ fa_status fa_radam_step(const fa_vol *u_in, fa_vol *u_out, fa_vol *m, fa_vol *v,
  * img, out: C=1, FA_F32.  Workspace of fa_gauss_workspace_size(1, D, H, W). */
 fa_status fa_pyramid_level(const fa_vol *img, int32_t s, fa_vol *out, void *ws,
                            size_t ws_bytes, void *stream);
+
+/* The whole pyramid of Algorithm 1 ("downsample" for every level) in one
+ * call: levels[l] (C=1, FA_F32, max(1, floor(N_a / p->scales[l])) per axis)
+ * receives fa_pyramid_level(img, p->scales[l]) for l = 0 .. p->n_levels - 1
+ * (only n_levels and scales of p are read; scale 1 copies img).  No level
+ * may alias img.  Workspace of fa_pyramid_workspace_size bytes (two
+ * full-grid temporaries shared by the levels; 0 for invalid arguments). */
+size_t fa_pyramid_workspace_size(int32_t D, int32_t H, int32_t W, const fa_params *p);
+fa_status fa_pyramid(const fa_vol *img, const fa_params *p, fa_vol *levels, void *ws,
+                     size_t ws_bytes, void *stream);
 
 /* Level hand-off (section "Interpolation strategies": trilinear upsampling
  * of phi and of the optimiser state m, nu; Algorithm 1 "Upsample"):
@@ -266,8 +284,11 @@ fa_status fa_upsample_field(const fa_vol *coarse, fa_vol *fine, int32_t power, v
  * step counter carries across levels.
  * ------------------------------------------------------------------------- */
 
-/* Bytes of workspace fa_register needs for a D x H x W pair. */
+/* Bytes of workspace fa_register needs for a D x H x W pair (0: invalid
+ * parameters); fa_workspace_size is the same query from the fixed image's
+ * descriptor. */
 size_t fa_register_workspace_size(int32_t D, int32_t H, int32_t W, const fa_params *p);
+size_t fa_workspace_size(const fa_vol *fixed, const fa_params *p);
 
 /* fixed, moving: C=1, dtype p->storage, same D x H x W.  u_out: C=3 FA_F32 on the grid of the
  * last level (max(1, floor(N_a / s_last))).  final_loss_dev (device float,
@@ -430,12 +451,29 @@ fa_status fa_register_batched_lockstep(int32_t n_pairs, const fa_vol *fixed,
  * writes up to `capacity` rows of 8 int32 (kernel 0..3, radius, compose
  * variant, D, H, W, 16-warp tiles, slab depth) and returns the number of
  * recorded choices.  fa_autotune_set records one such row (a choice made
- * elsewhere, or pinned by hand). */
+ * elsewhere, or pinned by hand).
+ *
+ * Process-wide state.  Apart from the caller's buffers, libfa keeps three
+ * things per process, shared by every caller and every thread:
+ *  - the tile choices above (they change the speed of later fused launches,
+ *    never their results);
+ *  - the recorded graphs of fa_register / fa_register_batched_lockstep with
+ *    p->graph set: up to 64, keyed on the call's pointers, shapes and
+ *    parameters, least recently used dropped first.  A graph holds device
+ *    addresses: after freeing a buffer that a recorded call used, call
+ *    fa_graph_cache_clear (or pass graph = 0) before the memory is reused
+ *    under the same key.  Lookups are locked; a graph in use by one thread
+ *    stays valid while another thread evicts or clears it;
+ *  - internal streams (capture streams per host thread and device, and the
+ *    forked streams of fa_register_batched), created on first use.
+ * fa_graph_cache_clear drops every recorded graph (each is destroyed once no
+ * launch holds it; graphs already launched finish normally). */
 fa_status fa_autotune(int32_t D, int32_t H, int32_t W, const fa_params *p, void *ws,
                       size_t ws_bytes, void *stream);
 fa_status fa_autotune_reset(void);
 int32_t fa_autotune_choices(int32_t *rows, int32_t capacity);
 fa_status fa_autotune_set(const int32_t *row);
+fa_status fa_graph_cache_clear(void);
 
 /* fa_register starting from a displacement u_init (C=3 FA_F32 on the input
  * grid, e.g. an affine pre-alignment from fa_affine_field) instead of the

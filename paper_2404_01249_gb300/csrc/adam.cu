@@ -11,10 +11,9 @@
 namespace fa {
 
 template <class TS>
-__global__ void __launch_bounds__(256) k_adam(const float *__restrict__ g, TS *__restrict__ m,
-                                              TS *__restrict__ v, float *__restrict__ d,
-                                              long long N, AdamConsts c, WsHeader *h,
-                                              int parity) {
+__device__ __forceinline__ void adam_body(const float *__restrict__ g, TS *__restrict__ m,
+                                          TS *__restrict__ v, float *__restrict__ d, long long N,
+                                          const AdamConsts &c, WsHeader *h, int parity) {
     __shared__ float red[32];
     float nrm2 = 0.0f;
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -40,6 +39,46 @@ __global__ void __launch_bounds__(256) k_adam(const float *__restrict__ g, TS *_
     if (bad) status_set(&h->status, ST_NONFINITE);
     block_max_to(&h->step_max_bits[parity], sqrtf(nrm2), red);
 }
+
+template <class TS>
+__global__ void __launch_bounds__(256) k_adam(const float *__restrict__ g, TS *__restrict__ m,
+                                              TS *__restrict__ v, float *__restrict__ d,
+                                              long long N, AdamConsts c, WsHeader *h,
+                                              int parity) {
+    adam_body<TS>(g, m, v, d, N, c, h, parity);
+}
+
+// 1 / (1 - b^t) in FP32: 1 - b^t = -expm1(t log1p(b - 1)), with b - 1 exact
+// for b in [0.5, 1); log1p and expm1 keep their relative accuracy where b^t
+// is close to 1 (large beta2, small t), which 1 - powf(b, t) would not.
+__device__ __forceinline__ float bias_recip(float b, int t) {
+    return -1.0f / expm1f((float)t * log1pf(b - 1.0f));
+}
+
+// The same step with the step number taken from the device counter:
+// t = *t_dev + 1 (the counter itself is advanced by k_count_step after the
+// compose, so that every block here reads the same value).
+template <class TS>
+__global__ void __launch_bounds__(256) k_adam_tdev(const float *__restrict__ g,
+                                                   TS *__restrict__ m, TS *__restrict__ v,
+                                                   float *__restrict__ d, long long N, float b1,
+                                                   float b2, float eps,
+                                                   const int *__restrict__ t_dev, WsHeader *h) {
+    const int t = *t_dev + 1;
+    if (t < 1) {  // a counter below zero: uniform over the block
+        if (threadIdx.x == 0) status_set(&h->status, ST_NONFINITE);
+        return;
+    }
+    AdamConsts c;
+    c.b1 = b1;
+    c.b2 = b2;
+    c.eps = eps;
+    c.rbc1 = bias_recip(b1, t);
+    c.rbc2 = bias_recip(b2, t);
+    adam_body<TS>(g, m, v, d, N, c, h, 0);
+}
+
+__global__ void k_count_step(int *t_dev) { *t_dev += 1; }
 
 __global__ void __launch_bounds__(256) k_compose(const float *__restrict__ u,
                                                  const float *__restrict__ d,
@@ -128,6 +167,23 @@ cudaError_t launch_adam_state(const float *g, void *m, void *v, int state, float
     return cudaGetLastError();
 }
 
+cudaError_t launch_adam_tdev(const float *g, void *m, void *v, int state, float *d, long long N,
+                             const fa_params *p, const int *t_dev, WsHeader *h, cudaStream_t s) {
+    const unsigned blocks = (unsigned)((N + 255) / 256);
+    if (state == FA_BF16)
+        k_adam_tdev<__nv_bfloat16><<<blocks, 256, 0, s>>>(g, (__nv_bfloat16 *)m, (__nv_bfloat16 *)v,
+                                                          d, N, p->beta1, p->beta2, p->adam_eps,
+                                                          t_dev, h);
+    else if (state == FA_F16)
+        k_adam_tdev<__half><<<blocks, 256, 0, s>>>(g, (__half *)m, (__half *)v, d, N, p->beta1,
+                                                   p->beta2, p->adam_eps, t_dev, h);
+    else
+        k_adam_tdev<float><<<blocks, 256, 0, s>>>(g, (float *)m, (float *)v, d, N, p->beta1,
+                                                  p->beta2, p->adam_eps, t_dev, h);
+    note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_compose(const float *u_in, const float *d, float *u_out, Dims dm, float lr,
                            float c_lp, WsHeader *h, int parity, float *eps_out, cudaStream_t s) {
     VoxGrid g(dm.D, dm.H, dm.W);
@@ -175,7 +231,7 @@ extern "C" size_t fa_radam_workspace_size(int32_t D, int32_t H, int32_t W) {
 }
 
 extern "C" fa_status fa_radam_step(const fa_vol *u_in, fa_vol *u_out, fa_vol *m, fa_vol *v,
-                                   const fa_vol *g, int32_t t, const fa_params *p,
+                                   const fa_vol *g, int32_t *t_dev, const fa_params *p,
                                    float *eps_t_dev, void *ws, size_t ws_bytes, void *stream) {
     using namespace fa;
     clear_error();
@@ -196,8 +252,8 @@ extern "C" fa_status fa_radam_step(const fa_vol *u_in, fa_vol *u_out, fa_vol *m,
         set_error("fa_radam_step: u_out must not alias u_in");
         return FA_ERR_INVALID;
     }
-    if (t < 1) {
-        set_error("fa_radam_step: t must be >= 1");
+    if (!t_dev || ((uintptr_t)t_dev & 3u)) {
+        set_error("fa_radam_step: t_dev must be a 4-byte aligned device int32");
         return FA_ERR_INVALID;
     }
     FA_TRY(check_adam_params(p, "fa_radam_step", true));  // m, v carry their own dtype
@@ -208,12 +264,14 @@ extern "C" fa_status fa_radam_step(const fa_vol *u_in, fa_vol *u_out, fa_vol *m,
     WsCarver c(ws, ws_bytes);
     WsHeader *h = c.take<WsHeader>(1);
     float *dir = c.take<float>(3 * d.N());
-    int parity = t & 1;
     FA_CUDA_TRY(launch_header_reset(h, s));
-    FA_CUDA_TRY(launch_adam_state((const float *)g->data, m->data, v->data, m->dtype, dir, d.N(),
-                                  adam_consts(p, t), h, parity, s));
+    FA_CUDA_TRY(launch_adam_tdev((const float *)g->data, m->data, v->data, m->dtype, dir, d.N(), p,
+                                 t_dev, h, s));
     FA_CUDA_TRY(launch_compose((const float *)u_in->data, dir, (float *)u_out->data, d, p->lr,
-                               p->c_lp, h, parity, eps_t_dev, s));
+                               p->c_lp, h, 0, eps_t_dev, s));
+    k_count_step<<<1, 1, 0, s>>>(t_dev);
+    note_launch();
+    FA_CUDA_TRY(cudaGetLastError());
     return FA_OK;
 }
 

@@ -1,5 +1,6 @@
 // Error reporting, parameter defaults and descriptor validation of libfa.
 #include <stdarg.h>
+#include <cuda.h>
 
 #include <atomic>
 #include <stdio.h>
@@ -29,6 +30,39 @@ void clear_error() { g_err[0] = 0; }
 fa_status cuda_fail(cudaError_t e, const char *where) {
     set_error("%s: %s", where, cudaGetErrorString(e));
     return FA_ERR_CUDA;
+}
+
+cudaError_t current_context_id(unsigned long long *id) {
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static const GetCurrent get_current = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return (GetCurrent)p;
+    }();
+    static const GetId get_id = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return (GetId)p;
+    }();
+    *id = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaSetDevice(dev)) != cudaSuccess) return e;  // makes the primary context current
+    if (!get_current || !get_id) return cudaSuccess;
+    CUcontext ctx = nullptr;
+    unsigned long long v = 0;
+    if (get_current(&ctx) == CUDA_SUCCESS && ctx && get_id(ctx, &v) == CUDA_SUCCESS) *id = v;
+    return cudaSuccess;
 }
 
 fa_status check_vol(const fa_vol *v, const char *name, int C) {

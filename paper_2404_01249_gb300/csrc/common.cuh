@@ -21,6 +21,12 @@ fa_status cuda_fail(cudaError_t e, const char *where);
 void note_launch();
 void note_launches(unsigned long long n);
 unsigned long long launches_so_far();
+// Identity of the CUDA context current on the calling thread (the
+// runtime's primary context of the current device, made current first):
+// the driver's unique context id, which a new context after a device reset
+// never repeats.  0 when the driver does not provide it.  Host caches of
+// device addresses or streams key on it.
+cudaError_t current_context_id(unsigned long long *id);
 
 #define FA_CUDA_TRY(expr)                                           \
     do {                                                            \

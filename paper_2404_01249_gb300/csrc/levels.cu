@@ -163,3 +163,63 @@ extern "C" fa_status fa_upsample_field(const fa_vol *coarse, fa_vol *fine, int32
                                 (cudaStream_t)stream));
     return FA_OK;
 }
+
+extern "C" size_t fa_pyramid_workspace_size(int32_t D, int32_t H, int32_t W, const fa_params *p) {
+    using namespace fa;
+    clear_error();
+    if (D < 1 || H < 1 || W < 1 || !p || p->n_levels < 1 || p->n_levels > 8) return 0;
+    bool blur = false;
+    for (int l = 0; l < p->n_levels; ++l) {
+        if (p->scales[l] < 1 || 0.5f * (float)p->scales[l] > kMaxSigma) return 0;
+        blur = blur || p->scales[l] > 1;
+    }
+    // two full-grid temporaries shared by every blurred level (256 bytes
+    // when no level is blurred, so that a valid request never reads as 0)
+    return blur ? fa_gauss_workspace_size(1, D, H, W) : 256;
+}
+
+extern "C" fa_status fa_pyramid(const fa_vol *img, const fa_params *p, fa_vol *levels, void *ws,
+                                size_t ws_bytes, void *stream) {
+    using namespace fa;
+    clear_error();
+    FA_TRY(check_vol(img, "img", 1));
+    if (!p || !levels) {
+        set_error("fa_pyramid: params and levels must not be NULL");
+        return FA_ERR_INVALID;
+    }
+    if (p->n_levels < 1 || p->n_levels > 8) {
+        set_error("fa_pyramid: n_levels must be in 1..8 (got %d)", (int)p->n_levels);
+        return FA_ERR_INVALID;
+    }
+    const Dims d{img->D, img->H, img->W};
+    for (int l = 0; l < p->n_levels; ++l) {
+        const int sc = p->scales[l];
+        if (sc < 1 || 0.5f * (float)sc > kMaxSigma) {
+            set_error("fa_pyramid: scales[%d] must be in 1..%d (got %d)", l, (int)(2 * kMaxSigma),
+                      sc);
+            return FA_ERR_INVALID;
+        }
+        FA_TRY(check_vol(&levels[l], "levels[l]", 1));
+        const Dims dl{level_size(d.D, sc), level_size(d.H, sc), level_size(d.W, sc)};
+        if (levels[l].D != dl.D || levels[l].H != dl.H || levels[l].W != dl.W) {
+            set_error("fa_pyramid: levels[%d] must be %dx%dx%d for scale %d", l, dl.D, dl.H, dl.W,
+                      sc);
+            return FA_ERR_SHAPE;
+        }
+        if (levels[l].data == img->data) {
+            set_error("fa_pyramid: levels[%d] must not alias img", l);
+            return FA_ERR_INVALID;
+        }
+    }
+    FA_TRY(check_ws(ws, ws_bytes, fa_pyramid_workspace_size(d.D, d.H, d.W, p), "fa_pyramid"));
+    WsCarver c(ws, ws_bytes);
+    float *t1 = c.take<float>(d.N());
+    float *t2 = c.take<float>(d.N());
+    for (int l = 0; l < p->n_levels; ++l) {
+        const int sc = p->scales[l];
+        const Dims dl{level_size(d.D, sc), level_size(d.H, sc), level_size(d.W, sc)};
+        FA_CUDA_TRY(launch_pyramid_level((const float *)img->data, d, sc, (float *)levels[l].data,
+                                         dl, t1, t2, (cudaStream_t)stream));
+    }
+    return FA_OK;
+}

@@ -17,7 +17,9 @@
 //    anything is launched;
 //  * the first call on each device looks up the array's device address
 //    (cudaGetSymbolAddress, with that device current); make that first call
-//    before any stream capture;
+//    before any stream capture.  The address is kept per device and CUDA
+//    context: after a device reset the next call looks it up again (in the
+//    new context) and must likewise come before any capture;
 //  * all calls share the one array and it keeps the previous call's
 //    contents (every call clears the fields that must start at zero); calls
 //    that overlap on the GPU -- different streams, or several host threads
@@ -36,10 +38,16 @@ static constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 static std::mutex g_noalloc_mu;
-static void *g_noalloc_ptr[kMaxDevices];
+struct NoAllocSlot {
+    unsigned long long ctx;  // context id the address was looked up in
+    void *ptr;
+};
+static NoAllocSlot g_noalloc_slot[kMaxDevices];
 
-// Device address of the scratch array on the current device (looked up once
-// per device).
+// Device address of the scratch array in the current device's context,
+// looked up once per context: a device reset makes a new context (with a new
+// id) in which the array has a new address, and the next call looks it up
+// again.
 static fa_status noalloc_scratch(void **out) {
     int dev = -1;
     FA_CUDA_TRY(cudaGetDevice(&dev));
@@ -47,14 +55,18 @@ static fa_status noalloc_scratch(void **out) {
         set_error("fa_lncc_fwd_bwd_noalloc: device ordinal %d is not supported", dev);
         return FA_ERR_UNSUPPORTED;
     }
+    unsigned long long ctx = 0;
+    FA_CUDA_TRY(current_context_id(&ctx));
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    NoAllocSlot &sl = g_noalloc_slot[dev];
+    if (!sl.ptr || sl.ctx != ctx) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-        g_noalloc_ptr[dev] = p;
+        sl.ptr = p;
+        sl.ctx = ctx;
     }
-    *out = g_noalloc_ptr[dev];
+    *out = sl.ptr;
     return FA_OK;
 }
 

@@ -4,6 +4,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -470,9 +471,24 @@ namespace {
 
 constexpr size_t kMaxGraphs = 64;
 
+// An instantiated graph, destroyed when its last holder lets go: a caller
+// that found an entry keeps it alive across its cudaGraphLaunch even if
+// another thread evicts the entry or clears the cache meanwhile (a graph
+// destroyed while it runs on the GPU is freed when the run completes).
+struct ExecHolder {
+    cudaGraphExec_t exec;
+    explicit ExecHolder(cudaGraphExec_t e) : exec(e) {}
+    ~ExecHolder() {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+    ExecHolder(const ExecHolder &) = delete;
+    ExecHolder &operator=(const ExecHolder &) = delete;
+};
+using ExecRef = std::shared_ptr<ExecHolder>;
+
 struct GraphEntry {
     std::string key;
-    cudaGraphExec_t exec;
+    ExecRef exec;
     unsigned long long kernels;  // kernel launches recorded in the graph
     int timer_count;             // event pairs recorded in the graph
     unsigned long long last_use;
@@ -516,8 +532,7 @@ std::string graph_key(int dev, const fa_vol *fixed, const fa_vol *moving, const 
     return k;
 }
 
-cudaGraphExec_t graph_find(const std::string &key, unsigned long long *kernels,
-                           int *timer_count) {
+ExecRef graph_find(const std::string &key, unsigned long long *kernels, int *timer_count) {
     std::lock_guard<std::mutex> lock(g_graph_mu);
     for (auto &e : g_graphs)
         if (e.key == key) {
@@ -529,42 +544,71 @@ cudaGraphExec_t graph_find(const std::string &key, unsigned long long *kernels,
     return nullptr;
 }
 
-void graph_store(const std::string &key, cudaGraphExec_t exec, unsigned long long kernels,
+void graph_store(const std::string &key, const ExecRef &exec, unsigned long long kernels,
                  int timer_count) {
     std::lock_guard<std::mutex> lock(g_graph_mu);
     if (g_graphs.size() >= kMaxGraphs) {
         size_t old = 0;
         for (size_t i = 1; i < g_graphs.size(); ++i)
             if (g_graphs[i].last_use < g_graphs[old].last_use) old = i;
-        cudaGraphExecDestroy(g_graphs[old].exec);
         g_graphs.erase(g_graphs.begin() + (long)old);
     }
     g_graphs.push_back(GraphEntry{key, exec, kernels, timer_count, ++g_graph_clock});
 }
 
-void graph_cache_clear() {
-    std::lock_guard<std::mutex> lock(g_graph_mu);
-    for (auto &e : g_graphs) cudaGraphExecDestroy(e.exec);
-    g_graphs.clear();
-}
-
 // A private non-blocking stream of this host thread for captures (captures
 // cannot run on the legacy default stream the caller may be using).
+// The stream is kept per device and CUDA context: a stream of a context
+// that a device reset destroyed is not reused.
 cudaError_t capture_stream(cudaStream_t *out) {
     thread_local cudaStream_t cs[64] = {};
+    thread_local unsigned long long cs_ctx[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!cs[dev]) {
+    unsigned long long ctx = 0;
+    if ((e = current_context_id(&ctx)) != cudaSuccess) return e;
+    if (!cs[dev] || cs_ctx[dev] != ctx) {
         e = cudaStreamCreateWithFlags(&cs[dev], cudaStreamNonBlocking);
         if (e != cudaSuccess) return e;
+        cs_ctx[dev] = ctx;
     }
     *out = cs[dev];
     return cudaSuccess;
 }
 
+// Records what enqueue() launches on a private capture stream and
+// instantiates it; the launch counter counts the recorded kernels once now.
+template <class F>
+fa_status graph_record(F enqueue, ExecRef *out, unsigned long long *kernels) {
+    cudaStream_t cs;
+    FA_CUDA_TRY(capture_stream(&cs));
+    FA_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    const unsigned long long k0 = launches_so_far();
+    const fa_status st = enqueue(cs);
+    *kernels = launches_so_far() - k0;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+    if (st != FA_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    FA_CUDA_TRY(ce);
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    FA_CUDA_TRY(ie);
+    *out = std::make_shared<ExecHolder>(exec);
+    return FA_OK;
+}
+
 }  // namespace
+
+void graph_cache_clear() {
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    g_graphs.clear();  // each graph is destroyed once no launch holds it
+}
 
 fa_status register_impl(const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
                         const fa_vol *u_init, fa_vol *u_out, float *final_loss_dev,
@@ -594,34 +638,22 @@ fa_status register_impl(const fa_vol *fixed, const fa_vol *moving, const fa_para
             graph_key(dev, fixed, moving, p, ui, u_out, final_loss_dev, ws, ws_bytes, timer);
         unsigned long long kernels = 0;
         int timer_count = 0;
-        cudaGraphExec_t exec = graph_find(key, &kernels, &timer_count);
+        ExecRef exec = graph_find(key, &kernels, &timer_count);
         if (!exec) {
             // record (the launch counter counts the recorded kernels once now,
             // for this first run, and again at every later replay)
-            cudaStream_t cs;
-            FA_CUDA_TRY(capture_stream(&cs));
-            FA_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-            const unsigned long long k0 = launches_so_far();
-            const fa_status st =
-                enqueue_registration(fixed, moving, p, ui, u_out, final_loss_dev, ws, ws_bytes, cs,
-                                     timer);
-            kernels = launches_so_far() - k0;
-            cudaGraph_t graph = nullptr;
-            const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
-            if (st != FA_OK) {
-                if (graph) cudaGraphDestroy(graph);
-                return st;
-            }
-            FA_CUDA_TRY(ce);
-            const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
-            cudaGraphDestroy(graph);
-            FA_CUDA_TRY(ie);
+            FA_TRY(graph_record(
+                [&](cudaStream_t cs) {
+                    return enqueue_registration(fixed, moving, p, ui, u_out, final_loss_dev, ws,
+                                                ws_bytes, cs, timer);
+                },
+                &exec, &kernels));
             graph_store(key, exec, kernels, timer ? timer->count : 0);
         } else {
             note_launches(kernels);
             if (timer) timer->count = timer_count;
         }
-        FA_CUDA_TRY(cudaGraphLaunch(exec, s));
+        FA_CUDA_TRY(cudaGraphLaunch(exec->exec, s));
     } else {
         FA_TRY(enqueue_registration(fixed, moving, p, ui, u_out, final_loss_dev, ws, ws_bytes, s,
                                     timer));
@@ -684,29 +716,15 @@ fa_status register_lockstep(int n, const LockstepArgs *a, void *ws, size_t slot,
     }
     unsigned long long kernels = 0;
     int timer_count = 0;
-    cudaGraphExec_t exec = graph_find(key, &kernels, &timer_count);
+    ExecRef exec = graph_find(key, &kernels, &timer_count);
     if (!exec) {
-        cudaStream_t cs;
-        FA_CUDA_TRY(capture_stream(&cs));
-        FA_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-        const unsigned long long k0 = launches_so_far();
-        const fa_status st = enqueue_lockstep(n, a, (char *)ws, slot, cs);
-        kernels = launches_so_far() - k0;
-        cudaGraph_t g = nullptr;
-        const cudaError_t ce = cudaStreamEndCapture(cs, &g);
-        if (st != FA_OK) {
-            if (g) cudaGraphDestroy(g);
-            return st;
-        }
-        FA_CUDA_TRY(ce);
-        const cudaError_t ie = cudaGraphInstantiate(&exec, g, 0);
-        cudaGraphDestroy(g);
-        FA_CUDA_TRY(ie);
+        FA_TRY(graph_record([&](cudaStream_t cs) { return enqueue_lockstep(n, a, (char *)ws, slot, cs); },
+                            &exec, &kernels));
         graph_store(key, exec, kernels, 0);
     } else {
         note_launches(kernels);
     }
-    FA_CUDA_TRY(cudaGraphLaunch(exec, s));
+    FA_CUDA_TRY(cudaGraphLaunch(exec->exec, s));
     return FA_OK;
 }
 
@@ -722,6 +740,12 @@ size_t register_ws_bytes(int D, int H, int W, const fa_params *p) {
 extern "C" size_t fa_register_workspace_size(int32_t D, int32_t H, int32_t W, const fa_params *p) {
     fa::clear_error();
     return fa::register_ws_bytes(D, H, W, p);
+}
+
+extern "C" size_t fa_workspace_size(const fa_vol *fixed, const fa_params *p) {
+    fa::clear_error();
+    if (!fixed) return 0;
+    return fa::register_ws_bytes(fixed->D, fixed->H, fixed->W, p);
 }
 
 extern "C" fa_status fa_register(const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
@@ -771,6 +795,12 @@ extern "C" fa_status fa_autotune(int32_t D, int32_t H, int32_t W, const fa_param
                                     tw, s));
     }
     graph_cache_clear();  // recorded graphs hold the previous choices
+    return FA_OK;
+}
+
+extern "C" fa_status fa_graph_cache_clear(void) {
+    fa::clear_error();
+    fa::graph_cache_clear();
     return FA_OK;
 }
 

@@ -48,7 +48,9 @@ EXPORTED = ["fa_params_default", "fa_status_str", "fa_last_error", "fa_warp",
             "fa_symmetric_loss_grad", "fa_mi_workspace_size", "fa_mi_fwd_bwd",
             "fa_rigid_register", "fa_register_svf_workspace_size", "fa_register_svf",
             "fa_svf_loss_grad", "fa_selftest_wait_timeout",
-            "fa_register_lockstep_workspace_size", "fa_register_batched_lockstep"]
+            "fa_register_lockstep_workspace_size", "fa_register_batched_lockstep",
+            "fa_pyramid_workspace_size", "fa_pyramid", "fa_workspace_size",
+            "fa_graph_cache_clear"]
 
 
 class FAError(RuntimeError):
@@ -109,8 +111,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "fa_gauss_workspace_size": (sz, [i32, i32, i32, i32]),
         "fa_gauss_smooth": (i32, [V, V, f32, vp, sz, vp]),
         "fa_radam_workspace_size": (sz, [i32, i32, i32]),
-        "fa_radam_step": (i32, [V, V, V, V, V, i32, P, vp, vp, sz, vp]),
+        "fa_radam_step": (i32, [V, V, V, V, V, vp, P, vp, vp, sz, vp]),
         "fa_pyramid_level": (i32, [V, i32, V, vp, sz, vp]),
+        "fa_pyramid_workspace_size": (sz, [i32, i32, i32, P]),
+        "fa_pyramid": (i32, [V, P, V, vp, sz, vp]),
+        "fa_workspace_size": (sz, [V, P]),
+        "fa_graph_cache_clear": (i32, []),
         "fa_upsample_field": (i32, [V, V, i32, vp]),
         "fa_register_workspace_size": (sz, [i32, i32, i32, P]),
         "fa_register": (i32, [V, V, P, V, vp, fp, vp, sz, vp]),
@@ -293,17 +299,25 @@ def fa_gauss_smooth(x: torch.Tensor, sigma: float, out=None):
     return out4[0] if squeeze else out4
 
 
-def fa_radam_step(u_in, m, v, g, t: int, params: RegParams, u_out=None):
-    """Updates m, v in place; returns (u_out, eps_t as a 0-dim CUDA tensor)."""
+def fa_radam_step(u_in, m, v, g, t, params: RegParams, u_out=None):
+    """One Riemannian Adam step.  `t` is the device step counter (an int32
+    CUDA tensor holding the steps taken so far, advanced by the call) or a
+    Python int, the step number after increment (a counter holding t - 1 is
+    made for the call).  Updates m, v in place; returns (u_out, eps_t as a
+    0-dim CUDA tensor)."""
     D, H, W = u_in.shape[-3:]
     lib = load()
     u_out = u_out if u_out is not None else torch.empty_like(u_in)
     eps_t = torch.empty((), device=u_in.device)
+    if isinstance(t, torch.Tensor):
+        t_dev = t
+    else:
+        t_dev = torch.tensor([int(t) - 1], dtype=torch.int32, device=u_in.device)
     ws = workspace(lib.fa_radam_workspace_size(D, H, W), u_in.device)
     p = params.to_c()
     _check(lib.fa_radam_step(_vol(u_in, 3), _vol(u_out, 3), _vol(m, 3, True), _vol(v, 3, True),
-                             _vol(g, 3),
-                             t, ctypes.byref(p), _ptr(eps_t), _ptr(ws), ws.numel(), _stream()))
+                             _vol(g, 3), _ptr(t_dev), ctypes.byref(p), _ptr(eps_t), _ptr(ws),
+                             ws.numel(), _stream()))
     return u_out, eps_t
 
 
@@ -314,6 +328,27 @@ def fa_pyramid_level(img: torch.Tensor, s: int):
     ws = workspace(lib.fa_gauss_workspace_size(1, D, H, W), img.device)
     _check(lib.fa_pyramid_level(_vol(img, 1), s, _vol(out, 1), _ptr(ws), ws.numel(), _stream()))
     return out
+
+
+def fa_pyramid(img: torch.Tensor, params: RegParams):
+    """Every level of params' pyramid (Algorithm 1 "downsample") in one call;
+    returns the list of level volumes, coarsest first as params orders them."""
+    D, H, W = img.shape[-3:]
+    lib = load()
+    p = params.to_c()
+    levels = [torch.empty((level_size(D, s), level_size(H, s), level_size(W, s)),
+                          device=img.device) for s in params.scales]
+    arr = (Vol * len(levels))(*[_vol_struct(x, 1) for x in levels])
+    n = lib.fa_pyramid_workspace_size(D, H, W, ctypes.byref(p))
+    if n == 0:
+        _check(1)
+    ws = workspace(n, img.device)
+    _check(lib.fa_pyramid(_vol(img, 1), ctypes.byref(p), arr, _ptr(ws), ws.numel(), _stream()))
+    return levels
+
+
+def fa_graph_cache_clear():
+    _check(load().fa_graph_cache_clear())
 
 
 def fa_upsample_field(coarse: torch.Tensor, shape, power: int):

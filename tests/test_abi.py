@@ -79,9 +79,16 @@ def test_host_validation_rejects_before_launch(lib):
     assert lib.fa_upsample_field(_vol(a, 3, 2, 2, 2), _vol(a + 4096, 3, 4, 4, 4), 2, None) == 1
     from paper_2404_01249_gb300 import fa
     p = fa.RegParams(mode="plain").to_c()
+    t_dev = ctypes.c_void_p(a + 8192)
     assert lib.fa_radam_step(_vol(a, 3, 4, 5, 6), _vol(a, 3, 4, 5, 6), _vol(a, 3, 4, 5, 6),
-                             _vol(a, 3, 4, 5, 6), _vol(a, 3, 4, 5, 6), 1, ctypes.byref(p), None,
-                             None, 0, None) == 1   # u_out aliases u_in
+                             _vol(a, 3, 4, 5, 6), _vol(a, 3, 4, 5, 6), t_dev, ctypes.byref(p),
+                             None, None, 0, None) == 1   # u_out aliases u_in
+    # the device step counter: missing, then misaligned
+    for bad_t in (None, ctypes.c_void_p(a + 8194)):
+        assert lib.fa_radam_step(_vol(a, 3, 4, 5, 6), _vol(a + 4096, 3, 4, 5, 6),
+                                 _vol(a, 3, 4, 5, 6), _vol(a, 3, 4, 5, 6), _vol(a, 3, 4, 5, 6),
+                                 bad_t, ctypes.byref(p), None, None, 0, None) == 1
+        assert b"t_dev" in lib.fa_last_error()
     # u_out on the wrong grid, then a missing workspace
     assert lib.fa_register(ok1(), ok1(), ctypes.byref(p), _vol(a, 3, 4, 5, 7), None, None, None,
                            0, None) == 2
@@ -171,9 +178,45 @@ def test_moment_storage_validation(lib):
     # fa_radam_step: m and v must share a supported dtype
     a = 1 << 20
     V = lambda dt: ctypes.byref(fa.Vol(a, dt, 3, 4, 5, 6))
+    t_dev = ctypes.c_void_p(a + 8192)
     st = lib.fa_radam_step(V(0), ctypes.byref(fa.Vol(a + 4096, 0, 3, 4, 5, 6)), V(1), V(2), V(0),
-                           1, ctypes.byref(p32), None, None, 0, None)
+                           t_dev, ctypes.byref(p32), None, None, 0, None)
     assert st == 3
     st = lib.fa_radam_step(V(0), ctypes.byref(fa.Vol(a + 4096, 0, 3, 4, 5, 6)), V(7), V(7), V(0),
-                           1, ctypes.byref(p32), None, None, 0, None)
+                           t_dev, ctypes.byref(p32), None, None, 0, None)
     assert st == 3
+
+
+def test_pyramid_and_workspace_queries(lib):
+    """fa_pyramid (every level of Algorithm 1's downsample in one call) and
+    fa_workspace_size (the register workspace from the fixed descriptor)
+    validate on the host; the graph cache can be cleared without a GPU."""
+    from paper_2404_01249_gb300 import fa
+    a = 1 << 20
+    p = fa.RegParams(scales=(4, 2, 1), iters=(2, 2, 2)).to_c()
+    fixed = fa.Vol(a, 0, 1, 40, 48, 56)
+    assert lib.fa_workspace_size(ctypes.byref(fixed), ctypes.byref(p)) == \
+        lib.fa_register_workspace_size(40, 48, 56, ctypes.byref(p)) > 0
+    assert lib.fa_workspace_size(None, ctypes.byref(p)) == 0
+    need = lib.fa_pyramid_workspace_size(40, 48, 56, ctypes.byref(p))
+    assert need == lib.fa_gauss_workspace_size(1, 40, 48, 56)
+    one = fa.RegParams(scales=(1,), iters=(1,)).to_c()
+    assert lib.fa_pyramid_workspace_size(40, 48, 56, ctypes.byref(one)) == 256
+    bad = fa.RegParams(scales=(4, 2, 1), iters=(2, 2, 2)).to_c()
+    bad.scales[1] = 0
+    assert lib.fa_pyramid_workspace_size(40, 48, 56, ctypes.byref(bad)) == 0
+    levels = (fa.Vol * 3)(fa.Vol(a + (1 << 24), 0, 1, 10, 12, 14),
+                          fa.Vol(a + (2 << 24), 0, 1, 20, 24, 28),
+                          fa.Vol(a + (3 << 24), 0, 1, 40, 48, 56))
+    # a level of the wrong size, a level aliasing the image, a missing workspace
+    levels[1].W = 27
+    assert lib.fa_pyramid(ctypes.byref(fixed), ctypes.byref(p), levels, None, 0, None) == 2
+    assert b"levels[1]" in lib.fa_last_error()
+    levels[1].W = 28
+    levels[2].data = a
+    assert lib.fa_pyramid(ctypes.byref(fixed), ctypes.byref(p), levels, None, 0, None) == 1
+    levels[2].data = a + (3 << 24)
+    assert lib.fa_pyramid(ctypes.byref(fixed), ctypes.byref(p), levels, None, 0, None) == 8
+    assert lib.fa_pyramid(ctypes.byref(fixed), ctypes.byref(bad), levels, None, 0, None) == 1
+    assert lib.fa_pyramid(ctypes.byref(fixed), ctypes.byref(p), None, None, 0, None) == 1
+    assert lib.fa_graph_cache_clear() == 0

@@ -145,6 +145,74 @@ def test_radam_step(fa, orc):
         assert rel(u_out, ur) < TOL
 
 
+def test_radam_step_device_counter_in_a_graph(fa, orc):
+    """fa_radam_step with its device step counter, recorded in a CUDA graph:
+    two steps per replay (ping-pong of u), two replays, so t runs 1..4 on the
+    device with no host involvement; u, m, v and the counter against the
+    oracle's four Adam steps (Algorithm 1 optimiser update and retraction)."""
+    import ctypes
+    shape = (19, 37, 45)
+    r = np.random.default_rng(8)
+    u0 = smooth_field(shape, 2.0, 9)
+    gs = [(r.standard_normal((3,) + shape) * 1e-6).astype(np.float32) for _ in range(2)]
+    params = fa.RegParams(lr=0.5)
+    lib = fa.load()
+    D, H, W = shape
+    ua, ub = cuda(u0), torch.empty((3,) + shape, device="cuda")
+    m = torch.zeros((3,) + shape, device="cuda")
+    v = torch.zeros((3,) + shape, device="cuda")
+    g = [cuda(x) for x in gs]
+    t_dev = torch.zeros(1, dtype=torch.int32, device="cuda")
+    eps = torch.empty((), device="cuda")
+    ws = fa.workspace(lib.fa_radam_workspace_size(D, H, W), "cuda")
+    pc = params.to_c()
+
+    def step(src, dst, gk):
+        assert lib.fa_radam_step(fa._vol(src, 3), fa._vol(dst, 3), fa._vol(m, 3), fa._vol(v, 3),
+                                 fa._vol(gk, 3), fa._ptr(t_dev), ctypes.byref(pc), fa._ptr(eps),
+                                 fa._ptr(ws), ws.numel(), fa._stream()) == 0
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            step(ua, ub, g[0])
+            step(ub, ua, g[1])
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    assert int(t_dev.item()) == 0  # capture does not run anything
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    assert int(t_dev.item()) == 4
+    f32 = lambda x: float(np.float32(x))
+    ur, mr, vr = u0.astype(np.float64), np.zeros((3,) + shape), np.zeros((3,) + shape)
+    for t in range(1, 5):
+        d, mr, vr = orc.adam(gs[(t - 1) % 2], mr, vr, t, f32(0.9), f32(0.999), f32(1e-8))
+        delta, er = orc.step_scale(d, 0.5, 2.0)
+        ur = orc.compose(ur, delta)
+    assert rel(m, mr) < TOL and rel(v, vr) < TOL
+    assert rel(ua, ur) < TOL
+    assert abs(float(eps) - er) <= TOL * er
+
+
+def test_pyramid_all_levels(fa, orc):
+    """fa_pyramid builds every level of Algorithm 1's downsample in one call;
+    each level against the oracle's downsample (a ragged grid, four levels
+    including an odd scale and the copy at scale 1)."""
+    shape = (37, 45, 53)
+    f, _ = voronoi(shape, seed=15)
+    scales = (8, 3, 2, 1)
+    levels = fa.fa_pyramid(cuda(f), fa.RegParams(scales=scales, iters=(1, 1, 1, 1)))
+    assert len(levels) == len(scales)
+    for lv, s in zip(levels, scales):
+        ref = orc.downsample(f, s)
+        assert tuple(lv.shape) == ref.shape
+        assert rel(lv, ref) < TOL
+    assert torch.equal(levels[-1], cuda(f))
+
+
 @pytest.mark.parametrize("s", [1, 2, 3, 4])
 def test_pyramid_level(fa, orc, s):
     shape = (19, 37, 45)

@@ -55,8 +55,24 @@ def test_noalloc_matches_workspace_entry_point_twice(fa):
         assert rel(dI, ref["dI"]) <= TOL
 
 
-def test_noalloc_rejects_grids_beyond_its_scratch(fa):
-    big = torch.empty((100, 100, 100), device="cuda")
+def test_noalloc_at_its_exact_limit(fa):
+    """64 x 133 x 73 = 621,376 voxels fill the 64 MiB scratch with no slack;
+    the result still equals the workspace entry point's."""
+    shape = (64, 133, 73)
+    assert fa.load().fa_lncc_workspace_size(*shape) == 64 << 20
+    f, m, _ = synth.voronoi_pair(shape=shape, seed=23)
+    ft, mt = torch.from_numpy(f).cuda(), torch.from_numpy(m).cuda()
+    loss, dJ, dI = call_noalloc(fa, ft, mt, 5, 1e-5)
+    ref = fa.fa_lncc_fwd_bwd(ft, mt, 5, 1e-5, want_dJ=True, want_dI=True)
+    torch.cuda.synchronize()
+    assert abs(float(loss) - float(ref["loss"])) <= TOL * abs(float(ref["loss"]))
+    assert rel(dJ, ref["dJ"]) <= TOL
+    assert rel(dI, ref["dI"]) <= TOL
+
+
+@pytest.mark.parametrize("shape", [(64, 133, 74), (100, 100, 100)])
+def test_noalloc_rejects_grids_beyond_its_scratch(fa, shape):
+    big = torch.empty(shape, device="cuda")
     with pytest.raises(fa.FAError) as e:
         call_noalloc(fa, big, big, 5, 1e-5)
     assert e.value.status == 2
