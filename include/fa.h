@@ -19,11 +19,9 @@
  * read as zero (u is extended by zero outside the domain, section
  * "Preliminaries" of the paper).
  *
- * Arithmetic is FP32 on the GPU.  LNCC window sums are accumulated exactly
- * in 64-bit fixed point, so the E[I^2] - E[I]^2 cancellation does not lose
- * precision.  FP64 runs on the GPU only in two one-block kernels: the table
- * of the mutual-information loss (at most 64 x 64 entries) and the 6-parameter
- * update of the rigid stage.
+ * Arithmetic is FP32 on the GPU, and no kernel holds an FP64 instruction.
+ * LNCC window sums are accumulated exactly in 64-bit fixed point, so the
+ * E[I^2] - E[I]^2 cancellation does not lose precision.
  */
 #ifndef FA_H
 #define FA_H
@@ -51,11 +49,21 @@ typedef enum { FA_F32 = 0, FA_BF16 = 1, FA_F16 = 2 } fa_dtype;
 
 typedef enum { FA_LOSS_LNCC = 0, FA_LOSS_MSE = 1, FA_LOSS_MI = 2 } fa_loss;
 
-/* Kernel schedule used by fa_register: FA_MODE_FUSED (four fused kernels per
- * iteration) or FA_MODE_PLAIN (one kernel per operation, intermediates in
- * HBM; the baseline the fused form is measured against).  Both compute the
- * same arithmetic. */
-typedef enum { FA_MODE_FUSED = 0, FA_MODE_PLAIN = 1 } fa_mode;
+/* Kernel schedule used by fa_register:
+ *  FA_MODE_FUSED (default): four fused kernels per iteration;
+ *  FA_MODE_PLAIN: one kernel per operation, intermediates in HBM (the
+ *    baseline the fused form is measured against);
+ *  FA_MODE_PERSISTENT: as FA_MODE_FUSED, except that a level of at most
+ *    2^21 voxels (LNCC with window 3..7, no use_jac, Gaussian radii <= 6,
+ *    width <= 128) runs as ONE persistent cooperative launch for all its
+ *    iterations, with grid barriers between the phases of an iteration and
+ *    the bits of FA_MODE_FUSED.  On GB300 it is slower than FA_MODE_FUSED
+ *    (its per-voxel z gathers re-read every plane from L2 in each phase); it
+ *    is kept as an alternative schedule.  Its CTAs must be resident
+ *    together: fa_register_batched (concurrent streams) runs such jobs as
+ *    FA_MODE_FUSED.
+ * All compute the same arithmetic. */
+typedef enum { FA_MODE_FUSED = 0, FA_MODE_PLAIN = 1, FA_MODE_PERSISTENT = 2 } fa_mode;
 
 /* Descriptor of a caller-owned device buffer holding C channels of a
  * D x H x W grid, contiguous [C][D][H][W]. */
@@ -513,7 +521,7 @@ fa_status fa_affine_field(const float *theta_dev, fa_vol *u_out, void *stream);
  * coordinates the map is the affine theta = (S^-1 R S, t), the same at every
  * level.  Identity start; plain Adam on the 6 parameters (lr, beta1, beta2,
  * adam_eps of p) with the exact gradient (the 12 affine sums pulled back
- * through dR/dw, evaluated in FP64 by one thread); loss, scales and
+ * through dR/dw, evaluated in FP32 by one thread); loss, scales and
  * iterations as fa_affine_register.  rp_dev (6 device floats) receives the
  * parameters, theta_dev (12, may be NULL) the equivalent affine map, u_out
  * (may be NULL) its displacement on the last level's grid, final_loss_dev
@@ -522,6 +530,12 @@ fa_status fa_affine_field(const float *theta_dev, fa_vol *u_out, void *stream);
 fa_status fa_rigid_register(const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
                             float *rp_dev, float *theta_dev, fa_vol *u_out_opt,
                             float *final_loss_dev, void *ws, size_t ws_bytes, void *stream);
+/* The affine map theta (12 device floats, as fa_affine_register's) of the
+ * rigid parameters rp_dev = (w, t) (6 device floats) for a D x H x W input
+ * grid: (S^-1 R S, t) with R = exp([w]x), in FP32 (Rodrigues with Taylor
+ * series below |w| = 1, Cody-Waite reduced sine and cosine above). */
+fa_status fa_rigid_theta(const float *rp_dev, int32_t D, int32_t H, int32_t W, float *theta_dev,
+                         void *stream);
 
 /* ---------------------------------------------------------------------------
  * Post-hoc inverse of a displacement (section "Alternative formulations for
@@ -600,6 +614,12 @@ fa_status fa_ws_status(const void *ws, void *stream);
  * stays usable.  ws: at least 256 bytes of device memory. */
 fa_status fa_selftest_wait_timeout(void *ws, size_t ws_bytes, int64_t limit_cycles, void *stream);
 
+/* The same for the grid barrier of the persistent coarse-level launch (no
+ * counterpart in the paper): a cooperative launch of two CTAs in which one
+ * never arrives; the other's bounded wait gives up after limit_cycles
+ * (0..2^31) and records FA_ERR_TIMEOUT in the status word. */
+fa_status fa_selftest_grid_barrier(void *ws, size_t ws_bytes, int64_t limit_cycles, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Kernel timing for benchmarks.  When `timer` is not NULL, fa_register_timed
  * records a pair of CUDA events (caller-created cudaEvent_t handles) around
@@ -608,7 +628,9 @@ fa_status fa_selftest_wait_timeout(void *ws, size_t ws_bytes, int64_t limit_cycl
  * pairs recorded.  Elapsed times are then read with cudaEventElapsedTime.
  * With p->graph set, the event records are part of the recorded graph: a
  * replay records the same events again (read them before the next replay
- * of the same call), and `count` is set to the recorded number.
+ * of the same call), and `count` is set to the recorded number.  A level
+ * whose fused kernels are timed runs them (FA_MODE_PERSISTENT's launch of a
+ * coarse level has no per-kernel launches).
  * ------------------------------------------------------------------------- */
 typedef enum {
     FA_K_FUSED_WARP_LNCC = 0,   /* fused: warp + LNCC forward (coefficients, loss)    */

@@ -19,8 +19,11 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libfa.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# ptxas reports register use (-v) and any double-precision instruction in a
+# kernel (none may run on the GPU: tests/test_abi.py checks the log)
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-                     "--expt-relaxed-constexpr", "-Xptxas", "-v", "-I", INCLUDE, "-I", CSRC]
+                     "--expt-relaxed-constexpr", "-Xptxas", "-v",
+                     "-Xptxas", "--warn-on-double-precision-use", "-I", INCLUDE, "-I", CSRC]
 _lock = threading.Lock()
 
 

@@ -175,45 +175,113 @@ __global__ void k_affine_init(float *theta, float *m, float *v) {
 // dR_ij/dw_k, with
 //   R = I + a K + b K^2,  dR/dw_k = c1 w_k K + a E_k + c2 w_k K^2 + b (E_k K + K E_k)
 // (K = [w]x, E_k = [e_k]x, a = sin th / th, b = (1 - cos th) / th^2,
-// c1 = a'(th) / th, c2 = b'(th) / th; power series below th = 1e-2).
-// One thread evaluates this in FP64 (six parameters).
-__device__ void rodrigues_d(const double w[3], double R[9], double dR[27]) {
-    const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2], th = sqrt(th2);
-    double a, b, c1, c2;
-    if (th < 1e-2) {
-        a = 1.0 - th2 / 6.0 + th2 * th2 / 120.0;
-        b = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
-        c1 = -1.0 / 3.0 + th2 / 30.0 - th2 * th2 / 840.0;
-        c2 = -1.0 / 12.0 + th2 / 180.0 - th2 * th2 / 6720.0;
+// c1 = a'(th) / th, c2 = b'(th) / th).  One thread evaluates this in FP32
+// (six parameters): below th = 1 the four coefficients come from their
+// Taylor series (terms to th^14, so the truncation lies far below FP32's
+// unit roundoff there), where the closed forms for c1 and c2 would cancel;
+// from th = 1 up the closed forms, with 1 - cos th taken as 2 sin^2(th / 2).
+// sin and cos without FP64 (the library's sincosf brings FP64 instructions
+// in through its reduction of huge arguments): the Cody-Waite reduction
+// x = k pi/2 + r with pi/2 split into three floats P1 + P2 + P3 whose
+// leading two have 8 and 11 significant bits, so k P1 and k P2 are exact for
+// |k| < 2^12 (|x| below about 6400; beyond that the error grows with k), then
+// the Taylor polynomials of sin (to r^13) and cos (to r^14) on |r| <= pi/4,
+// whose truncation lies below 2^-40, and the quadrant k mod 4.
+__device__ void sincos_cw(float x, float *sn, float *cs) {
+    const float P1 = 1.5703125f, P2 = 0x1.fb4p-12f, P3 = 0x1.4442d2p-24f;
+    const float k = rintf(x * 0.636619772f);
+    float r = fmaf(-k, P1, x);
+    r = fmaf(-k, P2, r);
+    r = fmaf(-k, P3, r);
+    const float r2 = r * r;
+    float ps = 1.0f / 6227020800.0f;                 // 1/13!
+    ps = fmaf(ps, -r2, 1.0f / 39916800.0f);
+    ps = fmaf(ps, -r2, 1.0f / 362880.0f);
+    ps = fmaf(ps, -r2, 1.0f / 5040.0f);
+    ps = fmaf(ps, -r2, 1.0f / 120.0f);
+    ps = fmaf(ps, -r2, 1.0f / 6.0f);
+    const float sr = fmaf(r * r2, -ps, r);           // r - r^3 (1/6 - ...)
+    float pc = 1.0f / 87178291200.0f;                // 1/14!
+    pc = fmaf(pc, -r2, 1.0f / 479001600.0f);
+    pc = fmaf(pc, -r2, 1.0f / 3628800.0f);
+    pc = fmaf(pc, -r2, 1.0f / 40320.0f);
+    pc = fmaf(pc, -r2, 1.0f / 720.0f);
+    pc = fmaf(pc, -r2, 1.0f / 24.0f);
+    pc = fmaf(pc, -r2, 0.5f);
+    const float cr = fmaf(r2, -pc, 1.0f);             // 1 - r^2 (1/2 - ...)
+    const int q = ((int)k) & 3;
+    *sn = q == 0 ? sr : (q == 1 ? cr : (q == 2 ? -sr : -cr));
+    *cs = q == 0 ? cr : (q == 1 ? -sr : (q == 2 ? -cr : sr));
+}
+
+__device__ void rodrigues_f(const float w[3], float R[9], float dR[27]) {
+    const float th2 = fmaf(w[0], w[0], fmaf(w[1], w[1], w[2] * w[2])), th = sqrtf(th2);
+    float a, b, c1, c2;
+    if (th < 1.0f) {
+        // a = sum (-1)^k th^2k / (2k+1)!,   b = sum (-1)^k th^2k / (2k+2)!,
+        // c1 = sum_{k>=1} (-1)^k 2k th^(2k-2) / (2k+1)!,
+        // c2 = sum_{k>=1} (-1)^k 2k th^(2k-2) / (2k+2)!   (Horner in th^2)
+        a = 1.0f / 6227020800.0f;                    // 1/13!
+        a = fmaf(a, -th2, 1.0f / 39916800.0f);       // 1/11!
+        a = fmaf(a, -th2, 1.0f / 362880.0f);
+        a = fmaf(a, -th2, 1.0f / 5040.0f);
+        a = fmaf(a, -th2, 1.0f / 120.0f);
+        a = fmaf(a, -th2, 1.0f / 6.0f);
+        a = fmaf(a, -th2, 1.0f);
+        b = 1.0f / 87178291200.0f;                   // 1/14!
+        b = fmaf(b, -th2, 1.0f / 479001600.0f);      // 1/12!
+        b = fmaf(b, -th2, 1.0f / 3628800.0f);
+        b = fmaf(b, -th2, 1.0f / 40320.0f);
+        b = fmaf(b, -th2, 1.0f / 720.0f);
+        b = fmaf(b, -th2, 1.0f / 24.0f);
+        b = fmaf(b, -th2, 0.5f);
+        c1 = -14.0f / 1307674368000.0f;              // k = 7: -14/15!
+        c1 = fmaf(c1, th2, 12.0f / 6227020800.0f);   // k = 6: 12/13!
+        c1 = fmaf(c1, th2, -10.0f / 39916800.0f);
+        c1 = fmaf(c1, th2, 8.0f / 362880.0f);
+        c1 = fmaf(c1, th2, -6.0f / 5040.0f);
+        c1 = fmaf(c1, th2, 4.0f / 120.0f);
+        c1 = fmaf(c1, th2, -2.0f / 6.0f);
+        c2 = -14.0f / 20922789888000.0f;             // k = 7: -14/16!
+        c2 = fmaf(c2, th2, 12.0f / 87178291200.0f);  // k = 6: 12/14!
+        c2 = fmaf(c2, th2, -10.0f / 479001600.0f);
+        c2 = fmaf(c2, th2, 8.0f / 3628800.0f);
+        c2 = fmaf(c2, th2, -6.0f / 40320.0f);
+        c2 = fmaf(c2, th2, 4.0f / 720.0f);
+        c2 = fmaf(c2, th2, -2.0f / 24.0f);
     } else {
-        const double sn = sin(th), cs = cos(th);
+        float sn, cs, sh, ch;
+        sincos_cw(th, &sn, &cs);
+        sincos_cw(0.5f * th, &sh, &ch);
+        const float omc = 2.0f * sh * sh;  // 1 - cos th
         a = sn / th;
-        b = (1.0 - cs) / th2;
-        c1 = (th * cs - sn) / (th2 * th);
-        c2 = (th * sn - 2.0 * (1.0 - cs)) / (th2 * th2);
+        b = omc / th2;
+        c1 = fmaf(th, cs, -sn) / (th2 * th);
+        c2 = fmaf(th, sn, -2.0f * omc) / (th2 * th2);
     }
-    const double K[9] = {0.0, -w[2], w[1], w[2], 0.0, -w[0], -w[1], w[0], 0.0};
-    double K2[9];
+    const float K[9] = {0.0f, -w[2], w[1], w[2], 0.0f, -w[0], -w[1], w[0], 0.0f};
+    float K2[9];
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
-            double s = 0.0;
-            for (int q = 0; q < 3; ++q) s += K[3 * i + q] * K[3 * q + j];
+            float s = 0.0f;
+            for (int q = 0; q < 3; ++q) s = fmaf(K[3 * i + q], K[3 * q + j], s);
             K2[3 * i + j] = s;
         }
-    for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0 ? 1.0 : 0.0) + a * K[i] + b * K2[i];
+    for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0 ? 1.0f : 0.0f) + fmaf(a, K[i], b * K2[i]);
     if (!dR) return;
     for (int k = 0; k < 3; ++k) {
-        const double e0 = k == 0, e1 = k == 1, e2 = k == 2;
-        const double E[9] = {0.0, -e2, e1, e2, 0.0, -e0, -e1, e0, 0.0};
+        const float e0 = k == 0, e1 = k == 1, e2 = k == 2;
+        const float E[9] = {0.0f, -e2, e1, e2, 0.0f, -e0, -e1, e0, 0.0f};
         for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j) {
-                double ek = 0.0, ke = 0.0;
+                float ek = 0.0f, ke = 0.0f;
                 for (int q = 0; q < 3; ++q) {
-                    ek += E[3 * i + q] * K[3 * q + j];
-                    ke += K[3 * i + q] * E[3 * q + j];
+                    ek = fmaf(E[3 * i + q], K[3 * q + j], ek);
+                    ke = fmaf(K[3 * i + q], E[3 * q + j], ke);
                 }
                 const int ij = 3 * i + j;
-                dR[9 * k + ij] = c1 * w[k] * K[ij] + a * E[ij] + c2 * w[k] * K2[ij] + b * (ek + ke);
+                dR[9 * k + ij] =
+                    fmaf(c1 * w[k], K[ij], fmaf(a, E[ij], fmaf(c2 * w[k], K2[ij], b * (ek + ke))));
             }
     }
 }
@@ -222,15 +290,18 @@ struct RigidScales {
     float s[3];
 };
 
-__device__ void rigid_theta_d(const float *rp, RigidScales sc, float *theta) {
-    const double w[3] = {rp[0], rp[1], rp[2]};
-    double R[9];
-    rodrigues_d(w, R, nullptr);
+__device__ void rigid_theta_f(const float *rp, RigidScales sc, float *theta) {
+    const float w[3] = {rp[0], rp[1], rp[2]};
+    float R[9];
+    rodrigues_f(w, R, nullptr);
     for (int i = 0; i < 3; ++i) {
-        for (int j = 0; j < 3; ++j)
-            theta[3 * i + j] = (float)(R[3 * i + j] * (double)sc.s[j] / (double)sc.s[i]);
+        for (int j = 0; j < 3; ++j) theta[3 * i + j] = R[3 * i + j] * (sc.s[j] / sc.s[i]);
         theta[9 + i] = rp[3 + i];
     }
+}
+
+__global__ void k_rigid_theta(const float *rp, float *theta, RigidScales sc) {
+    if (threadIdx.x == 0) rigid_theta_f(rp, sc, theta);
 }
 
 __global__ void k_rigid_init(float *rp, float *m, float *v, float *theta, RigidScales sc) {
@@ -241,7 +312,7 @@ __global__ void k_rigid_init(float *rp, float *m, float *v, float *theta, RigidS
         v[k] = 0.0f;
     }
     __syncthreads();
-    if (k == 0) rigid_theta_d(rp, sc, theta);
+    if (k == 0) rigid_theta_f(rp, sc, theta);
 }
 
 // 12 warps sum the affine partials (float-float, fixed order); thread 0 pulls
@@ -262,17 +333,16 @@ __global__ void __launch_bounds__(384) k_rigid_adam(const float *__restrict__ pa
     if (lane == 0) gaff[k] = hi + lo;
     __syncthreads();
     if (threadIdx.x != 0) return;
-    const double w[3] = {rp[0], rp[1], rp[2]};
-    double R[9], dR[27];
-    rodrigues_d(w, R, dR);
+    const float w[3] = {rp[0], rp[1], rp[2]};
+    float R[9], dR[27];
+    rodrigues_f(w, R, dR);
     float g[6];
     for (int q = 0; q < 3; ++q) {
-        double acc = 0.0;
+        float acc = 0.0f;
         for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j)
-                acc += (double)gaff[3 * i + j] * (double)sc.s[j] / (double)sc.s[i] *
-                       dR[9 * q + 3 * i + j];
-        g[q] = (float)acc;
+                acc = fmaf(gaff[3 * i + j] * (sc.s[j] / sc.s[i]), dR[9 * q + 3 * i + j], acc);
+        g[q] = acc;
         g[3 + q] = gaff[9 + q];
     }
     for (int q = 0; q < 6; ++q) {
@@ -282,7 +352,7 @@ __global__ void __launch_bounds__(384) k_rigid_adam(const float *__restrict__ pa
         v[q] = vq;
         rp[q] -= lr * adam_dir(mq, vq, ac.rbc1, ac.rbc2, ac.eps);
     }
-    rigid_theta_d(rp, sc, theta);
+    rigid_theta_f(rp, sc, theta);
 }
 
 RigidScales rigid_scales(Dims full) {
@@ -485,6 +555,25 @@ extern "C" fa_status fa_affine_field(const float *theta_dev, fa_vol *u_out, void
     VoxGrid vg(u_out->D, u_out->H, u_out->W);
     k_affine_field<<<vg.grid, vg.block, 0, (cudaStream_t)stream>>>(
         theta_dev, (float *)u_out->data, u_out->D, u_out->H, u_out->W);
+    note_launch();
+    FA_CUDA_TRY(cudaGetLastError());
+    return FA_OK;
+}
+
+extern "C" fa_status fa_rigid_theta(const float *rp_dev, int32_t D, int32_t H, int32_t W,
+                                    float *theta_dev, void *stream) {
+    using namespace fa;
+    clear_error();
+    if (!rp_dev || !theta_dev) {
+        set_error("fa_rigid_theta: rp_dev and theta_dev must not be NULL");
+        return FA_ERR_INVALID;
+    }
+    if (D < 1 || H < 1 || W < 1) {
+        set_error("fa_rigid_theta: grid must be positive");
+        return FA_ERR_SHAPE;
+    }
+    k_rigid_theta<<<1, 32, 0, (cudaStream_t)stream>>>(rp_dev, theta_dev,
+                                                       rigid_scales(Dims{D, H, W}));
     note_launch();
     FA_CUDA_TRY(cudaGetLastError());
     return FA_OK;

@@ -134,7 +134,11 @@ extern "C" fa_status fa_register_batched(int32_t n_pairs, const fa_vol *fixed,
     for (int j = 0; j < jobs && result == FA_OK; ++j) {
         const int i = j / n_cfg, c = j % n_cfg, k = j % conc;
         char *w = (char *)ws + slot * (size_t)k;
-        result = register_impl(&fixed[i], &moving[i], &cfgs[c], nullptr, &u_out[j],
+        // jobs on concurrent streams take the four fused kernels: a
+        // persistent launch needs its CTAs resident together
+        fa_params pc = cfgs[c];
+        if (pc.mode == FA_MODE_PERSISTENT) pc.mode = FA_MODE_FUSED;
+        result = register_impl(&fixed[i], &moving[i], &pc, nullptr, &u_out[j],
                                final_loss_dev ? final_loss_dev + j : nullptr, nullptr, w, slot,
                                st[k], nullptr);
         if (result == FA_OK && status_dev) {

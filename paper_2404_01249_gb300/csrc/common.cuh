@@ -53,7 +53,9 @@ struct WsHeader {
     unsigned long long loss_acc; // sum of cc (or squared error) in 2^-32 fixed point
     float loss;                // final loss of the last reduction
     float eps_t;               // last step size
-    unsigned char pad[256 - 4 - 8 - 32 - 8 - 4 - 8 - 8];
+    unsigned pbar_count;       // grid barriers of a persistent launch: arrivals
+    unsigned pbar_abort;       // set when a persistent launch is abandoned
+    unsigned char pad[256 - 4 - 8 - 32 - 8 - 4 - 8 - 8 - 8];
 };
 static_assert(sizeof(WsHeader) == 256, "header must be 256 bytes");
 

@@ -164,45 +164,57 @@ __global__ void __launch_bounds__(kHistThreads) k_mi_hist(const float *__restric
     }
 }
 
-// P, marginals, MI (FP64, fixed order) and the table log(P / (p_f p_m)).
+// P, marginals, MI and the table log(P / (p_f p_m)), in FP32.  The
+// marginals are exact integer sums of the fixed-point histogram, so every
+// probability is one rounding of an exact count; the ratio adds two
+// roundings and logf one more.  MI = sum P log(...) is accumulated as a
+// float-float pair per thread (exact products by fmaf, two-sum additions)
+// and the pairs are combined in a fixed tree order, so the loss carries
+// about FP32's unit roundoff and does not depend on scheduling.
 __global__ void __launch_bounds__(1024) k_mi_table(const unsigned long long *__restrict__ ghist,
                                                    int B, long long N, float *T, WsHeader *h,
                                                    float *loss_out) {
-    extern __shared__ double shd[];
-    double *P = shd, *pf = shd + B * B, *pm = pf + B, *red = pm + B;  // red: blockDim doubles
+    extern __shared__ float shf[];
+    float *P = shf, *pf = shf + B * B, *pm = pf + B, *rh = pm + B, *rl = rh + blockDim.x;
     const int nb = B * B, tid = threadIdx.x;
-    const double inv = 1.0 / ((double)N * (double)(1ll << kMiBits));
-    for (int k = tid; k < nb; k += blockDim.x) P[k] = (double)ghist[k] * inv;
-    __syncthreads();
+    const float Nf = (float)N, unit = pow2f(-kMiBits);
+    for (int k = tid; k < nb; k += blockDim.x)
+        P[k] = __fdiv_rn(u64_to_float_rn(ghist[k]) * unit, Nf);
     if (tid < B) {
-        double s = 0.0;
-        for (int b = 0; b < B; ++b) s += P[tid * B + b];
-        pf[tid] = s;
+        unsigned long long s = 0ull;
+        for (int b = 0; b < B; ++b) s += ghist[tid * B + b];
+        pf[tid] = __fdiv_rn(u64_to_float_rn(s) * unit, Nf);
     } else if (tid < 2 * B) {
-        double s = 0.0;
-        for (int a = 0; a < B; ++a) s += P[a * B + tid - B];
-        pm[tid - B] = s;
+        unsigned long long s = 0ull;
+        for (int a = 0; a < B; ++a) s += ghist[a * B + tid - B];
+        pm[tid - B] = __fdiv_rn(u64_to_float_rn(s) * unit, Nf);
     }
     __syncthreads();
-    double part = 0.0;
+    float hi = 0.0f, lo = 0.0f;
     for (int k = tid; k < nb; k += blockDim.x) {
-        const double q = P[k];
+        const float q = P[k];
         float tv = 0.0f;
-        if (q > 0.0) {
-            const double lr = log(q / (pf[k / B] * pm[k % B]));
-            part += q * lr;
-            tv = (float)lr;
+        if (q > 0.0f) {
+            tv = logf(__fdiv_rn(q, pf[k / B] * pm[k % B]));
+            const float ph = q * tv, pl = fmaf(q, tv, -ph);
+            ff_add(hi, lo, ph, pl);
         }
         T[k] = tv;
     }
-    red[tid] = part;
+    rh[tid] = hi;
+    rl[tid] = lo;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (tid < o) red[tid] += red[tid + o];
+        if (tid < o) {
+            float a = rh[tid], b = rl[tid];
+            ff_add(a, b, rh[tid + o], rl[tid + o]);
+            rh[tid] = a;
+            rl[tid] = b;
+        }
         __syncthreads();
     }
     if (tid == 0) {
-        const float L = (float)(-red[0]);
+        const float L = -(rh[0] + rl[0]);
         h->loss = L;
         if (loss_out) *loss_out = L;
     }
@@ -294,7 +306,7 @@ cudaError_t launch_mi(const float *I, const float *J, const float *grad, Dims d,
                                                            h);
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const size_t tab_smem = sizeof(double) * (nb + 2 * bins + 1024);
+    const size_t tab_smem = sizeof(float) * (nb + 2 * bins + 2 * 1024);
     k_mi_table<<<1, 1024, tab_smem, s>>>(b.hist, bins, N, b.T, h, loss_out);
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -57,8 +57,8 @@ static fa_status check_params(const fa_params *p) {
         set_error("use_jac must be 0 or 1");
         return FA_ERR_INVALID;
     }
-    if (p->mode != FA_MODE_FUSED && p->mode != FA_MODE_PLAIN) {
-        set_error("mode must be FA_MODE_FUSED or FA_MODE_PLAIN");
+    if (p->mode != FA_MODE_FUSED && p->mode != FA_MODE_PLAIN && p->mode != FA_MODE_PERSISTENT) {
+        set_error("mode must be FA_MODE_FUSED, FA_MODE_PLAIN or FA_MODE_PERSISTENT");
         return FA_ERR_INVALID;
     }
     if (p->storage != FA_F32 && p->storage != FA_BF16 && p->storage != FA_F16) {
@@ -89,6 +89,7 @@ struct Plan {
     MiBuffers mi;
     float *partials;
     FusedBuffers fb;
+    long long *pxy;  // in-plane window sums of the persistent coarse levels
     size_t bytes;
     bool ok;
 };
@@ -144,10 +145,15 @@ static void make_plan(Plan &P, void *base, size_t cap, Dims full, const fa_param
     P.partials = c.take<float>(np);
     memset(&P.lb, 0, sizeof(P.lb));
     memset(&P.fb, 0, sizeof(P.fb));
+    P.pxy = nullptr;
     if (p->mode == FA_MODE_PLAIN) {
         P.lb = lncc_carve(c, n);
     } else {
         fused_carve(c, n, &P.fb);
+        long long np_ = 0;  // largest level that runs persistent
+        for (int l = 0; l < p->n_levels; ++l)
+            if (persistent_eligible(p, P.lvl[l]) && P.lvl[l].N() > np_) np_ = P.lvl[l].N();
+        if (np_ > 0) P.pxy = c.take<long long>(3 * np_);
     }
     memset(&P.mi, 0, sizeof(P.mi));
     if (p->loss == FA_LOSS_MI) P.mi = P.fb.mi = mi_carve(c, p->mi_bins);
@@ -322,7 +328,7 @@ static fa_status level_begin(Plan &P, const fa_params *p, int l, const float *u_
     FA_CUDA_TRY(cudaMemsetAsync(P.h->absmax_bits, 0, sizeof(P.h->absmax_bits), s));
     FA_CUDA_TRY(launch_absmax2(If, Im, d.N(), P.h, s));
     if (p->loss == FA_LOSS_MI) FA_CUDA_TRY(launch_mi_range(If, Im, d.N(), P.mi, s));
-    if (p->mode == FA_MODE_FUSED)
+    if (p->mode != FA_MODE_PLAIN)
         FA_CUDA_TRY(fused_level_start(If, Im, P.u[*cur], d, p, P.h, P.fb, s));
     return FA_OK;
 }
@@ -364,6 +370,22 @@ static fa_status enqueue_registration(const fa_vol *fixed, const fa_vol *moving,
         const float *Im = level_image(P, p, l, P.Im, Im0);
         FA_TRY(level_begin(P, p, l, l == 0 ? u_init : nullptr, If, Im, &cur, s));
         Timer tm{timer, l};
+        // a level whose fused kernels are timed runs them
+        const bool timed = timer && timer->kernel_id != FA_K_PLAIN_ANY &&
+                           (timer->level < 0 || timer->level == l);
+        if (!timed && persistent_eligible(p, P.lvl[l])) {  // the whole level in one launch
+            const int T = p->iters[l];
+            FA_TRY(persistent_level(P.fb, P.pxy, P.h, p, P.lvl[l], If, Im, P.u[cur], P.u[cur ^ 1],
+                                    P.m[cur], P.v[cur], t, T, tg, tw, s));
+            t += T;
+            if (T & 1) {  // the result is in the other buffer: swap roles
+                float *tmpu = P.u[cur];
+                P.u[cur] = P.u[cur ^ 1];
+                P.u[cur ^ 1] = tmpu;
+            }
+            if (l == L) FA_TRY(registration_end(P, p, If, Im, P.u[cur], u_out, final_loss_dev, s));
+            continue;
+        }
         for (int it = 0; it < p->iters[l]; ++it) {
             ++t;
             if (p->mode == FA_MODE_PLAIN) {
@@ -675,7 +697,8 @@ fa_status lockstep_check(int n, const LockstepArgs *a) {
     const fa_params *p0 = a[0].p;
     for (int k = 0; k < n; ++k) {
         const fa_params *p = a[k].p;
-        if (p->mode != FA_MODE_FUSED || p->loss != FA_LOSS_LNCC || p->use_jac) {
+        if ((p->mode != FA_MODE_FUSED && p->mode != FA_MODE_PERSISTENT) ||
+            p->loss != FA_LOSS_LNCC || p->use_jac) {
             set_error("lockstep: job %d: needs the fused LNCC path without use_jac", k);
             return FA_ERR_UNSUPPORTED;
         }
@@ -774,7 +797,7 @@ extern "C" fa_status fa_autotune(int32_t D, int32_t H, int32_t W, const fa_param
         return FA_ERR_SHAPE;
     }
     FA_TRY(check_params(p));
-    if (p->mode != FA_MODE_FUSED) return FA_OK;  // the per-op kernels have no choices
+    if (p->mode == FA_MODE_PLAIN) return FA_OK;  // the per-op kernels have no choices
     Dims full{D, H, W};
     Plan P;
     make_plan(P, nullptr, ~size_t(0), full, p);

@@ -83,6 +83,20 @@ fa_status lockstep_check(int n, const LockstepArgs *a);
 // Records the call as a CUDA graph and replays it when every job asks for it.
 fa_status register_lockstep(int n, const LockstepArgs *a, void *ws, size_t slot, cudaStream_t s);
 
+// Persistent form of a coarse level (persistent.cu): one cooperative launch
+// runs every iteration of the level with grid barriers between its phases,
+// computing the bits of fused_iteration.  Eligible: FA_MODE_PERSISTENT, LNCC
+// with window 3..7, no use_jac, Gaussian radii <= 6, width <= 128 and at
+// most kPersistMaxVoxels voxels.  xy: persistent_xy_bytes(N) of scratch.  The
+// displacement after T iterations is in u0 if T is even, else in u1.
+constexpr long long kPersistMaxVoxels = 2ll << 20;
+bool persistent_eligible(const fa_params *p, Dims d);
+size_t persistent_xy_bytes(long long n);
+fa_status persistent_level(const FusedBuffers &fb, long long *xy, WsHeader *h, const fa_params *p,
+                           Dims d, const float *If, const float *Im, float *u0, float *u1, void *m,
+                           void *v, int t0, int T, const GaussTaps &tg, const GaussTaps &tw,
+                           cudaStream_t s);
+
 // Argument checks of fa_register (no launch).
 fa_status register_check(const fa_vol *fixed, const fa_vol *moving, const fa_params *p,
                          const fa_vol *u_out);

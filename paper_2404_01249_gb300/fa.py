@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "FA_OK", 1: "FA_ERR_INVALID", 2: "FA_ERR_SHAPE", 3: "FA_ERR_D
                 7: "FA_ERR_UNSUPPORTED", 8: "FA_ERR_WORKSPACE"}
 FA_F32, FA_BF16, FA_F16 = 0, 1, 2
 FA_LOSS_LNCC, FA_LOSS_MSE, FA_LOSS_MI = 0, 1, 2
-FA_MODE_FUSED, FA_MODE_PLAIN = 0, 1
+FA_MODE_FUSED, FA_MODE_PLAIN, FA_MODE_PERSISTENT = 0, 1, 2
 (FA_K_FUSED_WARP_LNCC, FA_K_FUSED_LNCC_GRAD, FA_K_FUSED_SMOOTH_ADAM, FA_K_FUSED_COMPOSE,
  FA_K_PLAIN_ANY, FA_K_FUSED_ALL) = 0, 1, 2, 3, 4, 5
 
@@ -50,7 +50,7 @@ EXPORTED = ["fa_params_default", "fa_status_str", "fa_last_error", "fa_warp",
             "fa_svf_loss_grad", "fa_selftest_wait_timeout",
             "fa_register_lockstep_workspace_size", "fa_register_batched_lockstep",
             "fa_pyramid_workspace_size", "fa_pyramid", "fa_workspace_size",
-            "fa_graph_cache_clear"]
+            "fa_graph_cache_clear", "fa_selftest_grid_barrier", "fa_rigid_theta"]
 
 
 class FAError(RuntimeError):
@@ -117,6 +117,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "fa_pyramid": (i32, [V, P, V, vp, sz, vp]),
         "fa_workspace_size": (sz, [V, P]),
         "fa_graph_cache_clear": (i32, []),
+        "fa_selftest_grid_barrier": (i32, [vp, sz, ctypes.c_int64, vp]),
+        "fa_rigid_theta": (i32, [vp, i32, i32, i32, vp, vp]),
         "fa_upsample_field": (i32, [V, V, i32, vp]),
         "fa_register_workspace_size": (sz, [i32, i32, i32, P]),
         "fa_register": (i32, [V, V, P, V, vp, fp, vp, sz, vp]),
@@ -236,7 +238,8 @@ class RegParams:
         p.mi_bins = int(self.mi_bins)
         p.beta1, p.beta2, p.adam_eps = self.beta1, self.beta2, self.adam_eps
         p.cc_eps, p.c_lp = self.cc_eps, self.c_lp
-        p.mode = {"fused": FA_MODE_FUSED, "plain": FA_MODE_PLAIN}[self.mode]
+        p.mode = {"fused": FA_MODE_FUSED, "plain": FA_MODE_PLAIN,
+                  "persistent": FA_MODE_PERSISTENT}[self.mode]
         p.storage = FA_F32
         p.graph = 1 if self.graph else 0
         p.use_jac = 1 if self.use_jac else 0

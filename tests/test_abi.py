@@ -220,3 +220,13 @@ def test_pyramid_and_workspace_queries(lib):
     assert lib.fa_pyramid(ctypes.byref(fixed), ctypes.byref(bad), levels, None, 0, None) == 1
     assert lib.fa_pyramid(ctypes.byref(fixed), ctypes.byref(p), None, None, 0, None) == 1
     assert lib.fa_graph_cache_clear() == 0
+
+
+def test_no_fp64_instruction_in_any_kernel(lib):
+    """No kernel holds a double-precision instruction: the build passes
+    ptxas --warn-on-double-precision-use for every translation unit and
+    keeps ptxas's messages in _build/ptxas.log."""
+    from paper_2404_01249_gb300 import build
+    log = open(os.path.join(build.OUT, "ptxas.log")).read()
+    assert "ptxas info" in log                      # the log is ptxas's output
+    assert "double precision" not in log.lower()

@@ -111,3 +111,23 @@ def test_rigid_zero_iterations_is_identity(fa):
     assert not out["rp"].any() and not out["u"].any()
     assert torch.equal(out["theta"].cpu(), torch.tensor([1.0, 0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0]))
 
+
+
+@pytest.mark.parametrize("angle", [0.0, 1e-3, 0.3, 0.999, 1.0, 1.7, 3.1, 5.0, 40.0])
+def test_rigid_theta_fp32_against_oracle(fa, orc, angle):
+    """The rigid parameters' affine map in FP32 (no FP64 on the GPU): both
+    branches of the Rodrigues coefficients (Taylor series below |w| = 1,
+    closed forms with the Cody-Waite reduced sine and cosine above) against
+    the oracle's double-precision map, on an anisotropic grid."""
+    shape = (26, 41, 33)
+    axis = np.array([0.3, -0.8, 0.52])
+    rp = np.concatenate([angle * axis / np.linalg.norm(axis), [0.05, -0.02, 0.1]])
+    rp32 = rp.astype(np.float32)
+    lib = fa.load()
+    rp_dev = cuda(rp32)
+    th = torch.empty(12, device="cuda")
+    fa._check(lib.fa_rigid_theta(fa._ptr(rp_dev), *shape, fa._ptr(th), fa._stream()))
+    ref = orc.rigid_theta(rp32.astype(np.float64), shape)
+    got = th.cpu().double().numpy()
+    # FP32 rounding of O(10) operations on entries of size up to s_max/s_min
+    assert np.abs(got - ref).max() <= 2e-6 * np.abs(ref).max()
