@@ -9,10 +9,16 @@
 //   dL/dI_m(p) = sum_x dL/dJ(x) w_p(x)            (the adjoint of the warp:
 //                w_p(x) is the trilinear weight of corner p at x + u(x))
 //
-// The scatter of dL/dI_m accumulates quantised contributions in int64 with
-// integer atomics, so the result does not depend on the order in which
-// threads add (the same fixed-point scheme as the window sums).
+// Without dL/dI_f the call runs on the fused kernels of the registration
+// loop: the warp (J and grad I_m at x + u), the fixed image's window
+// statistics, K1 (exact window sums, cc, the adjoint coefficients, the loss)
+// and K2 (the adjoint window sums, dL/du, and dL/dJ for the scatter).  With
+// dL/dI_f it runs the per-op LNCC kernels, which also form the fixed image's
+// coefficients.  The scatter of dL/dI_m accumulates quantised contributions
+// in int64 with integer atomics, so the result does not depend on the order
+// in which threads add (the same fixed-point scheme as the window sums).
 #include "ops.h"
+#include "register.h"
 #include "validate.h"
 
 namespace fa {
@@ -28,6 +34,26 @@ struct AdjointBuffers {
     float *J, *grad, *dJ;
     long long *acc;
 };
+
+// The fused route (no dL/dI_f): the fused kernels' buffers, dL/dJ and the
+// scatter accumulator.
+struct AdjointFusedBuffers {
+    WsHeader *h;
+    FusedBuffers fb;
+    float *dJ;
+    long long *acc;
+};
+
+AdjointFusedBuffers adjoint_fused_carve(void *base, size_t cap, long long N, size_t *bytes) {
+    WsCarver c(base, cap);
+    AdjointFusedBuffers b;
+    b.h = c.take<WsHeader>(1);
+    fused_carve(c, N, &b.fb);
+    b.dJ = c.take<float>(N);
+    b.acc = c.take<long long>(N);
+    *bytes = c.off;
+    return b;
+}
 
 AdjointBuffers adjoint_carve(void *base, size_t cap, long long N, size_t *bytes) {
     WsCarver c(base, cap);
@@ -108,6 +134,28 @@ __global__ void __launch_bounds__(256) k_scatter_finalize(const long long *__res
         out[i] = i64_to_float_rn(acc[i]) * inv;
 }
 
+// dL/dI_m(p) = sum_x dL/dJ(x) w_p(x + u(x)): fixed point at 2^-40 of
+// max |dL/dJ| with integer atomics (order-independent), then back to float.
+fa_status scatter_to_moving(const float *dJ, const float *u, long long *acc, WsHeader *h,
+                            Dims d, float *dIm, cudaStream_t s) {
+    const long long N = d.N();
+    long long blocks = (N + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_absmax1<<<(unsigned)blocks, 256, 0, s>>>(dJ, N, &h->coef_max_bits[kSlotDJ]);
+    note_launch();
+    FA_CUDA_TRY(cudaGetLastError());
+    FA_CUDA_TRY(cudaMemsetAsync(acc, 0, sizeof(long long) * N, s));
+    VoxGrid g(d.D, d.H, d.W);
+    k_warp_adjoint_scatter<<<g.grid, g.block, 0, s>>>(dJ, u, (unsigned long long *)acc, h, d.D,
+                                                      d.H, d.W);
+    note_launch();
+    FA_CUDA_TRY(cudaGetLastError());
+    k_scatter_finalize<<<(unsigned)blocks, 256, 0, s>>>(acc, h, dIm, N);
+    note_launch();
+    FA_CUDA_TRY(cudaGetLastError());
+    return FA_OK;
+}
+
 }  // namespace
 
 }  // namespace fa
@@ -115,9 +163,10 @@ __global__ void __launch_bounds__(256) k_scatter_finalize(const long long *__res
 extern "C" size_t fa_warp_lncc_adjoint_workspace_size(int32_t D, int32_t H, int32_t W) {
     fa::clear_error();
     if (D < 1 || H < 1 || W < 1) return 0;
-    size_t bytes = 0;
-    fa::adjoint_carve(nullptr, ~size_t(0), (long long)D * H * W, &bytes);
-    return bytes;
+    size_t plain = 0, fused = 0;
+    fa::adjoint_carve(nullptr, ~size_t(0), (long long)D * H * W, &plain);
+    fa::adjoint_fused_carve(nullptr, ~size_t(0), (long long)D * H * W, &fused);
+    return plain > fused ? plain : fused;
 }
 
 extern "C" fa_status fa_warp_lncc_adjoint(const fa_vol *fixed, const fa_vol *moving,
@@ -154,16 +203,28 @@ extern "C" fa_status fa_warp_lncc_adjoint(const fa_vol *fixed, const fa_vol *mov
     }
     Dims d{fixed->D, fixed->H, fixed->W};
     const long long N = d.N();
-    size_t need = 0;
-    adjoint_carve(nullptr, ~size_t(0), N, &need);
-    FA_TRY(check_ws(ws, ws_bytes, need, "fa_warp_lncc_adjoint"));
-    AdjointBuffers b = adjoint_carve(ws, ws_bytes, N, &need);
+    FA_TRY(check_ws(ws, ws_bytes, fa_warp_lncc_adjoint_workspace_size(d.D, d.H, d.W),
+                    "fa_warp_lncc_adjoint"));
     cudaStream_t s = (cudaStream_t)stream;
     const float *I = (const float *)fixed->data, *Im = (const float *)moving->data;
     const float *uu = (const float *)u->data;
     float *du = dL_du_opt ? (float *)dL_du_opt->data : nullptr;
     float *dIf = dL_dfixed_opt ? (float *)dL_dfixed_opt->data : nullptr;
     float *dIm = dL_dmoving_opt ? (float *)dL_dmoving_opt->data : nullptr;
+
+    if (!dIf) {  // the fused kernels: warp, K1 (forward), K2 (dL/du and dL/dJ), scatter
+        size_t need = 0;
+        AdjointFusedBuffers b = adjoint_fused_carve(ws, ws_bytes, N, &need);
+        FA_CUDA_TRY(launch_header_reset(b.h, s));
+        float *g = du ? du : (dIm ? b.fb.g : nullptr);
+        FA_CUDA_TRY(fused_warp_lncc_adjoint(I, Im, uu, b.fb, d, window, cc_eps, b.h, loss_dev, g,
+                                            dIm ? b.dJ : nullptr, s));
+        if (dIm) FA_TRY(scatter_to_moving(b.dJ, uu, b.acc, b.h, d, dIm, s));
+        return FA_OK;
+    }
+
+    size_t need = 0;
+    AdjointBuffers b = adjoint_carve(ws, ws_bytes, N, &need);
 
     FA_CUDA_TRY(launch_header_reset(b.h, s));
     FA_CUDA_TRY(launch_warp(Im, uu, b.J, du ? b.grad : nullptr, d, s));
@@ -173,21 +234,6 @@ extern "C" fa_status fa_warp_lncc_adjoint(const fa_vol *fixed, const fa_vol *mov
     if (du || dIf || dIm)
         FA_CUDA_TRY(launch_lncc_backward(I, b.J, du ? b.grad : nullptr, d, window, b.h, b.lb,
                                          dIm ? b.dJ : nullptr, dIf, du, s));
-    if (dIm) {
-        long long blocks = (N + 255) / 256;
-        if (blocks > 152 * 16) blocks = 152 * 16;
-        k_absmax1<<<(unsigned)blocks, 256, 0, s>>>(b.dJ, N, &b.h->coef_max_bits[kSlotDJ]);
-        note_launch();
-        FA_CUDA_TRY(cudaGetLastError());
-        FA_CUDA_TRY(cudaMemsetAsync(b.acc, 0, sizeof(long long) * N, s));
-        VoxGrid g(d.D, d.H, d.W);
-        k_warp_adjoint_scatter<<<g.grid, g.block, 0, s>>>(b.dJ, uu, (unsigned long long *)b.acc,
-                                                          b.h, d.D, d.H, d.W);
-        note_launch();
-        FA_CUDA_TRY(cudaGetLastError());
-        k_scatter_finalize<<<(unsigned)blocks, 256, 0, s>>>(b.acc, b.h, dIm, N);
-        note_launch();
-        FA_CUDA_TRY(cudaGetLastError());
-    }
+    if (dIm) FA_TRY(scatter_to_moving(b.dJ, uu, b.acc, b.h, d, dIm, s));
     return FA_OK;
 }

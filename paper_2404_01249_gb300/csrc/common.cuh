@@ -156,11 +156,23 @@ __device__ __forceinline__ void tri_issue(TriPending &p, const float *__restrict
     p.tz = uz - fz;
     p.ty = uy - fy;
     p.tx = ux - fx;
+    // 32-bit offsets: grids hold fewer than 2^31 voxels and iz >= -1
+    if (iz >= 0 && iz + 1 < D && iy >= 0 && iy + 1 < H && ix >= 0 && ix + 1 < W) {
+        const float *q0 = v + (iz * H + iy) * W + ix, *q1 = q0 + H * W;  // the whole cell inside
+        p.c000 = __ldg(q0);
+        p.c001 = __ldg(q0 + 1);
+        p.c010 = __ldg(q0 + W);
+        p.c011 = __ldg(q0 + W + 1);
+        p.c100 = __ldg(q1);
+        p.c101 = __ldg(q1 + 1);
+        p.c110 = __ldg(q1 + W);
+        p.c111 = __ldg(q1 + W + 1);
+        return;
+    }
     if (iz < -1 || iz >= D || iy < -1 || iy >= H || ix < -1 || ix >= W) return;
     const bool z0 = iz >= 0, z1 = iz + 1 < D;
     const bool y0 = iy >= 0, y1 = iy + 1 < H;
     const bool x0 = ix >= 0, x1 = ix + 1 < W;
-    // 32-bit offsets: grids hold fewer than 2^31 voxels and iz >= -1
     const int b = (iz * H + iy) * W + ix;
     const float *q0 = v + b, *q1 = q0 + H * W;
     if (z0 && y0 && x0) p.c000 = __ldg(q0);

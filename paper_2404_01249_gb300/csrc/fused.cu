@@ -165,9 +165,11 @@ cudaError_t launch_k1(const float *If, const float *J, const long long *sI, cons
     return le;
 }
 
-template <int R>
+// WDJ: the adjoint's variant, which also writes dL/dJ to dJout.
+template <int R, bool WDJ = false>
 cudaError_t launch_k2(const float *If, const float *gJ, const float *J, const float *coef,
-                      WsHeader *h, float *g, Dims d, int window, cudaStream_t s) {
+                      WsHeader *h, float *g, Dims d, int window, cudaStream_t s,
+                      float *dJout = nullptr) {
     const int cb = lncc_coef_bits(window);
     Maps mp{};
     cudaError_t le;
@@ -175,18 +177,18 @@ cudaError_t launch_k2(const float *If, const float *gJ, const float *J, const fl
     const bool tma = tmap(&mp.a, coef, 4, d, 4, ST::BXW, ST::RY, 4);
     const TileChoice tc = tile_choice(1, R, 0, d);
     if (tma) {
-        auto kern = k_lncc_grad<R, K2_NW, K2_OPT, K2_ST_TMA, true>;
+        auto kern = k_lncc_grad<R, K2_NW, K2_OPT, K2_ST_TMA, true, WDJ>;
         static const int occ = prepare(kern, ST::bytes, ST::NT);
         LaunchGeom gg = geometry(occ, K2_NW, ST::TY, R, d, tc.tz);
         le = launch_pdl(kern, gg, ST::bytes, s, mp, If, gJ, J, coef, h, g, d.D, d.H, d.W, gg.tz,
-                                                  cb);
+                        cb, dJout);
     } else {
         using SC = K2S<R, K2_NW, K2_OPT, K2_ST_CP>;
-        auto kern = k_lncc_grad<R, K2_NW, K2_OPT, K2_ST_CP, false>;
+        auto kern = k_lncc_grad<R, K2_NW, K2_OPT, K2_ST_CP, false, WDJ>;
         static const int occ = prepare(kern, SC::bytes, SC::NT);
         LaunchGeom gg = geometry(occ, K2_NW, SC::TY, R, d, tc.tz);
         le = launch_pdl(kern, gg, SC::bytes, s, mp, If, gJ, J, coef, h, g, d.D, d.H, d.W, gg.tz,
-                                                  cb);
+                        cb, dJout);
     }
     note_launch();
     return le;
@@ -308,6 +310,22 @@ cudaError_t dispatch_k2(const float *If, const float *gJ, const float *J, const 
         FA_CASE(5, (launch_k2<RR>(If, gJ, J, coef, h, g, d, window, s)))
         FA_CASE(6, (launch_k2<RR>(If, gJ, J, coef, h, g, d, window, s)))
         FA_CASE(7, (launch_k2<RR>(If, gJ, J, coef, h, g, d, window, s)))
+    }
+    return cudaErrorInvalidValue;
+}
+
+// The adjoint's K2 (windows 1..15): g and dL/dJ.
+cudaError_t dispatch_k2_dj(const float *If, const float *gJ, const float *J, const float *coef,
+                           WsHeader *h, float *g, float *dJ, Dims d, int window, cudaStream_t s) {
+    switch (window / 2) {
+        FA_CASE(0, (launch_k2<RR, true>(If, gJ, J, coef, h, g, d, window, s, dJ)))
+        FA_CASE(1, (launch_k2<RR, true>(If, gJ, J, coef, h, g, d, window, s, dJ)))
+        FA_CASE(2, (launch_k2<RR, true>(If, gJ, J, coef, h, g, d, window, s, dJ)))
+        FA_CASE(3, (launch_k2<RR, true>(If, gJ, J, coef, h, g, d, window, s, dJ)))
+        FA_CASE(4, (launch_k2<RR, true>(If, gJ, J, coef, h, g, d, window, s, dJ)))
+        FA_CASE(5, (launch_k2<RR, true>(If, gJ, J, coef, h, g, d, window, s, dJ)))
+        FA_CASE(6, (launch_k2<RR, true>(If, gJ, J, coef, h, g, d, window, s, dJ)))
+        FA_CASE(7, (launch_k2<RR, true>(If, gJ, J, coef, h, g, d, window, s, dJ)))
     }
     return cudaErrorInvalidValue;
 }
@@ -568,6 +586,25 @@ int fused_tile_choices(int32_t *out, int capacity) {
 cudaError_t fused_lncc_forward_only(const float *If, const FusedBuffers &fb, Dims d, int window,
                                     float cc_eps, WsHeader *h, cudaStream_t s) {
     return dispatch_k1(If, fb.J, fb.sI, fb.varI, nullptr, h, d, window, cc_eps, false, s);
+}
+
+cudaError_t fused_warp_lncc_adjoint(const float *If, const float *Im, const float *u,
+                                    const FusedBuffers &fb, Dims d, int window, float cc_eps,
+                                    WsHeader *h, float *loss_dev, float *g, float *dJ,
+                                    cudaStream_t s) {
+    cudaError_t e;
+    if ((e = launch_warp(Im, u, fb.J, g ? fb.gJ : nullptr, d, s)) != cudaSuccess) return e;
+    if ((e = launch_absmax2(If, fb.J, d.N(), h, s)) != cudaSuccess) return e;
+    if ((e = launch_fixed_stats(If, d, window, h, (long long *)fb.coef, (long long *)fb.g, fb.sI,
+                                fb.varI, s)) != cudaSuccess)
+        return e;
+    if ((e = dispatch_k1(If, fb.J, fb.sI, fb.varI, fb.coef, h, d, window, cc_eps, g != nullptr,
+                         s)) != cudaSuccess)
+        return e;
+    if ((e = launch_loss_finalize(h, d.N(), -1.0f, loss_dev, s)) != cudaSuccess) return e;
+    if (!g) return cudaSuccess;
+    return dJ ? dispatch_k2_dj(If, fb.gJ, fb.J, fb.coef, h, g, dJ, d, window, s)
+              : dispatch_k2(If, fb.gJ, fb.J, fb.coef, h, g, d, window, s);
 }
 
 // Self-test of the bounded wait: one thread waits on an mbarrier that no

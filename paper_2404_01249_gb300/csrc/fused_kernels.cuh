@@ -386,19 +386,27 @@ __device__ __forceinline__ void box_y3(const long long *xL, int wy, int tx, long
     }
 }
 
+// Channels 0 and 1 of the y and z passes run as one packed FP32 pair
+// (__ffma2_rn: each component is exactly fmaf), channel 2 alone; every
+// channel's taps accumulate in the same order as a scalar loop would.
 template <int RG, int RY, int NW, int OPT, class TT>
 __device__ __forceinline__ void gauss_y3(const float *xb, const TT &t, int wy, int tx,
                                          float Q[OPT][3]) {
 #pragma unroll
     for (int o = 0; o < OPT; ++o) {
         const float *xi = xb + (wy + NW * o) * FX + tx;
+        float2 s01 = make_float2(0.0f, 0.0f);
+        float s2 = 0.0f;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            float s = 0.0f;
-#pragma unroll
-            for (int k = 0; k <= 2 * RG; ++k) s = fmaf(t.w[k], xi[c * RY * FX + k * FX], s);
-            Q[o][c] = s;
+        for (int k = 0; k <= 2 * RG; ++k) {
+            const float w = t.w[k];
+            s01 = __ffma2_rn(make_float2(w, w),
+                             make_float2(xi[k * FX], xi[RY * FX + k * FX]), s01);
+            s2 = fmaf(w, xi[2 * RY * FX + k * FX], s2);
         }
+        Q[o][0] = s01.x;
+        Q[o][1] = s01.y;
+        Q[o][2] = s2;
     }
 }
 
@@ -433,15 +441,20 @@ template <int RG, int NOUT, class TT>
 __device__ __forceinline__ void gauss_z3(const float *ring_o, int newest, const TT &t,
                                          float out[3]) {
     constexpr int NS = 2 * RG + 1;
-    out[0] = out[1] = out[2] = 0.0f;
+    float2 s01 = make_float2(0.0f, 0.0f);
+    float s2 = 0.0f;
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
         int j = newest + 1 + k;
         j = j >= NS ? j - NS : j;
         const float *r = ring_o + j * 3 * NOUT;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) out[c] = fmaf(t.w[k], r[c * NOUT], out[c]);
+        const float w = t.w[k];
+        s01 = __ffma2_rn(make_float2(w, w), make_float2(r[0], r[NOUT]), s01);
+        s2 = fmaf(w, r[2 * NOUT], s2);
     }
+    out[0] = s01.x;
+    out[1] = s01.y;
+    out[2] = s2;
 }
 
 // Bounded wait, by thread 0, for the copies of planes i .. i + NSTG - 1 that
@@ -692,15 +705,16 @@ struct K2S {
     static constexpr size_t bytes = o_bar + 8 * NSTG;
 };
 
-// The body of K2 for the CTA with tile coordinates (bx, by, bz).
-template <int R, int NW, int OPT, int NSTG, bool TMA>
+// The body of K2 for the CTA with tile coordinates (bx, by, bz).  WDJ: also
+// write dL/dJ itself to dJout (the adjoint's scatter into dL/dI_m needs it).
+template <int R, int NW, int OPT, int NSTG, bool TMA, bool WDJ = false>
 __device__ __forceinline__ void lncc_grad_body(const Maps *maps, const float *__restrict__ If,
                                                const float *__restrict__ gJ,
                                                const float *__restrict__ J,
                                                const float *__restrict__ coef,
                                                WsHeader *__restrict__ h, float *__restrict__ g,
                                                int D, int H, int W, int TZ, int cbits, int bx,
-                                               int by, int bz) {
+                                               int by, int bz, float *__restrict__ dJout = nullptr) {
     using S = K2S<R, NW, OPT, NSTG>;
     constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, BXW = S::BXW, COFF = S::COFF,
                   XB = S::XB, NR = S::NR, NS = S::NS, NOUT = S::NOUT;
@@ -844,6 +858,7 @@ __device__ __forceinline__ void lncc_grad_body(const Maps *maps, const float *__
                 gp[0] = dj * Gz[o];
                 gp[N] = dj * Gy[o];
                 gp[2 * N] = dj * Gx[o];
+                if (WDJ) dJout[zoff + ou.off[o]] = dj;
             }
         }
     }
@@ -857,7 +872,7 @@ __device__ __forceinline__ void lncc_grad_body(const Maps *maps, const float *__
     if (!TMA) cp_wait<0>();
 }
 
-template <int R, int NW, int OPT, int NSTG, bool TMA>
+template <int R, int NW, int OPT, int NSTG, bool TMA, bool WDJ = false>
 __global__ void __launch_bounds__(FX *NW) k_lncc_grad(const __grid_constant__ Maps maps,
                                                       const float *__restrict__ If,
                                                       const float *__restrict__ gJ,
@@ -865,9 +880,9 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_grad(const __grid_constant__ Ma
                                                       const float *__restrict__ coef,
                                                       WsHeader *__restrict__ h,
                                                       float *__restrict__ g, int D, int H, int W,
-                                                      int TZ, int cbits) {
-    lncc_grad_body<R, NW, OPT, NSTG, TMA>(&maps, If, gJ, J, coef, h, g, D, H, W, TZ, cbits,
-                                          blockIdx.x, blockIdx.y, blockIdx.z);
+                                                      int TZ, int cbits, float *__restrict__ dJout) {
+    lncc_grad_body<R, NW, OPT, NSTG, TMA, WDJ>(&maps, If, gJ, J, coef, h, g, D, H, W, TZ, cbits,
+                                               blockIdx.x, blockIdx.y, blockIdx.z, dJout);
 }
 
 // MSE: g = 2 (J - I) / N * grad I_m(phi) (pointwise, J and the gradient as
@@ -1203,6 +1218,22 @@ __device__ __forceinline__ void compose_body(const Maps *maps, const float *__re
 #pragma unroll
     for (int o = 0; o < OPT; ++o) jlive[o] = false;
 
+    // this thread's compose positions (fixed for every plane): plane-layout
+    // index (-1: none), inside the grid, and the u stage index of the cell
+    // (0, 0, 0) corner before the step's floor is added
+    constexpr int NP = RY * RX, NJP = (NP + NT - 1) / NT;
+    int pk[NJP], pub[NJP];
+    bool pin[NJP];
+#pragma unroll
+    for (int j = 0; j < NJP; ++j) {
+        const int pidx = tid + j * NT;
+        const int ry = pidx / RX, rx = pidx - ry * RX;
+        const int y = y0 - RG + ry, x = x0 - RG + rx;
+        pk[j] = pidx < NP ? ry * BXW + rx + COFF : -1;
+        pin[j] = pidx < NP && y >= 0 && y < H && x >= 0 && x < W;
+        pub[j] = (ry + 1) * UBXW + (rx + 1) + UCOFF;
+    }
+
     int fail = -1, slot = 0;
     for (int i = 0; i < np; ++i) {
         const int zp = zs + i, zo = zp - RG, s = i % NSTG;
@@ -1222,16 +1253,12 @@ __device__ __forceinline__ void compose_body(const Maps *maps, const float *__re
             const float *um = uslot(zp - 1), *u0 = uslot(zp), *u1 = uslot(zp + 1);
             // u' on the RY x RX region (positions spread over all threads),
             // at the plane layout's columns
-            constexpr int NP = RY * RX;
 #pragma unroll
-            for (int j = 0; j < (NP + NT - 1) / NT; ++j) {
-                const int pidx = tid + j * NT;
-                if (NP % NT != 0 && pidx >= NP) break;
-                const int ry = pidx / RX, rx = pidx - ry * RX;
-                const int y = y0 - RG + ry, x = x0 - RG + rx;
-                const int k = ry * BXW + rx + COFF;
+            for (int j = 0; j < NJP; ++j) {
+                const int k = pk[j];
+                if (NP % NT != 0 && k < 0) break;
                 float a = 0.f, b = 0.f, c = 0.f;
-                if (y >= 0 && y < H && x >= 0 && x < W) {
+                if (pin[j]) {
                     const float dz = -e * ds[k], dy = -e * ds[NR + k], dx = -e * ds[2 * NR + k];
                     if (SU) {
                         // cell corners lie within one voxel: planes zp-1..zp+1
@@ -1241,26 +1268,38 @@ __device__ __forceinline__ void compose_body(const Maps *maps, const float *__re
                             const float tz = dz - fz, ty = dy - fy, tx2 = dx - fx;
                             const float *pa = fz < 0.0f ? um : u0;
                             const float *pb = fz < 0.0f ? u0 : u1;
-                            const int b0 = (ry + 1 + (int)fy) * UBXW + (rx + 1 + (int)fx) + UCOFF;
-                            float r[3];
-#pragma unroll
-                            for (int ch = 0; ch < 3; ++ch) {
-                                const float *A = pa + ch * NRU + b0, *B = pb + ch * NRU + b0;
-                                const float c00 = fmaf(tx2, A[1] - A[0], A[0]);
-                                const float c01 = fmaf(tx2, A[UBXW + 1] - A[UBXW], A[UBXW]);
-                                const float c10 = fmaf(tx2, B[1] - B[0], B[0]);
-                                const float c11 = fmaf(tx2, B[UBXW + 1] - B[UBXW], B[UBXW]);
-                                const float c0 = fmaf(ty, c01 - c00, c00);
-                                const float c1 = fmaf(ty, c11 - c10, c10);
-                                r[ch] = fmaf(tz, c1 - c0, c0);
-                            }
-                            a = dz + r[0];
-                            b = dy + r[1];
-                            c = dx + r[2];
+                            const int b0 = pub[j] + (int)fy * UBXW + (int)fx;
+                            // channels 0 and 1 as a packed pair (each component
+                            // exactly the scalar fadd / fmaf), channel 2 alone
+                            auto pair = [&](const float *P, int o) {
+                                return make_float2(P[b0 + o], P[NRU + b0 + o]);
+                            };
+                            auto lerp2 = [](float t, float2 lo, float2 hi) {
+                                return __ffma2_rn(make_float2(t, t),
+                                                  __fadd2_rn(hi, make_float2(-lo.x, -lo.y)), lo);
+                            };
+                            const float2 c00 = lerp2(tx2, pair(pa, 0), pair(pa, 1));
+                            const float2 c01 = lerp2(tx2, pair(pa, UBXW), pair(pa, UBXW + 1));
+                            const float2 c10 = lerp2(tx2, pair(pb, 0), pair(pb, 1));
+                            const float2 c11 = lerp2(tx2, pair(pb, UBXW), pair(pb, UBXW + 1));
+                            const float2 r01 = lerp2(tz, lerp2(ty, c00, c01), lerp2(ty, c10, c11));
+                            const float *A = pa + 2 * NRU + b0, *B = pb + 2 * NRU + b0;
+                            const float e00 = fmaf(tx2, A[1] - A[0], A[0]);
+                            const float e01 = fmaf(tx2, A[UBXW + 1] - A[UBXW], A[UBXW]);
+                            const float e10 = fmaf(tx2, B[1] - B[0], B[0]);
+                            const float e11 = fmaf(tx2, B[UBXW + 1] - B[UBXW], B[UBXW]);
+                            const float e0 = fmaf(ty, e01 - e00, e00);
+                            const float e1 = fmaf(ty, e11 - e10, e10);
+                            const float2 ab = __fadd2_rn(make_float2(dz, dy), r01);
+                            a = ab.x;
+                            b = ab.y;
+                            c = dx + fmaf(tz, e1 - e0, e0);
                         } else {
                             a = b = c = __int_as_float(0x7fc00000);  // impossible step: flag it
                         }
                     } else {
+                        const int pidx = tid + j * NT, ry = pidx / RX, rx = pidx - ry * RX;
+                        const int y = y0 - RG + ry, x = x0 - RG + rx;
                         float gz, gy, gx;
                         a = dz + tri_sample<false>(u, D, H, W, zp, y, x, dz, dy, dx, gz, gy, gx);
                         b = dy + tri_sample<false>(u + N, D, H, W, zp, y, x, dz, dy, dx, gz, gy,
@@ -1272,7 +1311,7 @@ __device__ __forceinline__ void compose_body(const Maps *maps, const float *__re
                 up[k] = a;
                 up[NR + k] = b;
                 up[2 * NR + k] = c;
-                }
+            }
             __syncthreads();
             gauss_x4<RG, 3, RY, BXW, COFF, NT>(up, xb, t, tid);
             __syncthreads();

@@ -44,6 +44,14 @@ void fused_tile_set(const int32_t *row);  // one row as fused_tile_choices write
 // Recorded choices as rows of 8 int32 (kernel, radius, compose variant, D, H,
 // W, 16-warp tiles, TZ); returns the number of rows.
 int fused_tile_choices(int32_t *out, int capacity);
+// The warp + LNCC adjoint on the fused kernels: J and grad I_m at x + u
+// (fb.J, fb.gJ), the fixed image's window statistics, K1 (coefficients and
+// loss, finalised into loss_dev and h->loss), and when g is not NULL K2: g =
+// dL/du and, when dJ is not NULL, dL/dJ.  h must be reset by the caller.
+cudaError_t fused_warp_lncc_adjoint(const float *If, const float *Im, const float *u,
+                                    const FusedBuffers &fb, Dims d, int window, float cc_eps,
+                                    WsHeader *h, float *loss_dev, float *g, float *dJ,
+                                    cudaStream_t s);
 // LNCC loss accumulator only (no coefficients) for the warped image fb.J.
 cudaError_t fused_lncc_forward_only(const float *If, const FusedBuffers &fb, Dims d, int window,
                                     float cc_eps, WsHeader *h, cudaStream_t s);
