@@ -140,9 +140,11 @@ struct TriPending {
     float tz, ty, tx;
 };
 
-__device__ __forceinline__ void tri_issue(TriPending &p, const float *__restrict__ v, int D,
-                                          int H, int W, int z, int y, int x, float uz, float uy,
-                                          float ux) {
+// tri_issue_p: the same for a buffer of row pitch P (>= W; zero outside the
+// logical D x H x W grid whatever the padding holds).
+__device__ __forceinline__ void tri_issue_p(TriPending &p, const float *__restrict__ v, int D,
+                                            int H, int W, int P, int z, int y, int x, float uz,
+                                            float uy, float ux) {
     p.c000 = p.c001 = p.c010 = p.c011 = p.c100 = p.c101 = p.c110 = p.c111 = 0.0f;
     p.tz = p.ty = p.tx = 0.0f;
     const float LIM = 1048576.0f;
@@ -156,33 +158,39 @@ __device__ __forceinline__ void tri_issue(TriPending &p, const float *__restrict
     p.tz = uz - fz;
     p.ty = uy - fy;
     p.tx = ux - fx;
-    // 32-bit offsets: grids hold fewer than 2^31 voxels and iz >= -1
+    // 32-bit offsets: buffers hold fewer than 2^31 elements and iz >= -1
     if (iz >= 0 && iz + 1 < D && iy >= 0 && iy + 1 < H && ix >= 0 && ix + 1 < W) {
-        const float *q0 = v + (iz * H + iy) * W + ix, *q1 = q0 + H * W;  // the whole cell inside
+        const float *q0 = v + (iz * H + iy) * P + ix, *q1 = q0 + H * P;  // the whole cell inside
         p.c000 = __ldg(q0);
         p.c001 = __ldg(q0 + 1);
-        p.c010 = __ldg(q0 + W);
-        p.c011 = __ldg(q0 + W + 1);
+        p.c010 = __ldg(q0 + P);
+        p.c011 = __ldg(q0 + P + 1);
         p.c100 = __ldg(q1);
         p.c101 = __ldg(q1 + 1);
-        p.c110 = __ldg(q1 + W);
-        p.c111 = __ldg(q1 + W + 1);
+        p.c110 = __ldg(q1 + P);
+        p.c111 = __ldg(q1 + P + 1);
         return;
     }
     if (iz < -1 || iz >= D || iy < -1 || iy >= H || ix < -1 || ix >= W) return;
     const bool z0 = iz >= 0, z1 = iz + 1 < D;
     const bool y0 = iy >= 0, y1 = iy + 1 < H;
     const bool x0 = ix >= 0, x1 = ix + 1 < W;
-    const int b = (iz * H + iy) * W + ix;
-    const float *q0 = v + b, *q1 = q0 + H * W;
+    const int b = (iz * H + iy) * P + ix;
+    const float *q0 = v + b, *q1 = q0 + H * P;
     if (z0 && y0 && x0) p.c000 = __ldg(q0);
     if (z0 && y0 && x1) p.c001 = __ldg(q0 + 1);
-    if (z0 && y1 && x0) p.c010 = __ldg(q0 + W);
-    if (z0 && y1 && x1) p.c011 = __ldg(q0 + W + 1);
+    if (z0 && y1 && x0) p.c010 = __ldg(q0 + P);
+    if (z0 && y1 && x1) p.c011 = __ldg(q0 + P + 1);
     if (z1 && y0 && x0) p.c100 = __ldg(q1);
     if (z1 && y0 && x1) p.c101 = __ldg(q1 + 1);
-    if (z1 && y1 && x0) p.c110 = __ldg(q1 + W);
-    if (z1 && y1 && x1) p.c111 = __ldg(q1 + W + 1);
+    if (z1 && y1 && x0) p.c110 = __ldg(q1 + P);
+    if (z1 && y1 && x1) p.c111 = __ldg(q1 + P + 1);
+}
+
+__device__ __forceinline__ void tri_issue(TriPending &p, const float *__restrict__ v, int D,
+                                          int H, int W, int z, int y, int x, float uz, float uy,
+                                          float ux) {
+    tri_issue_p(p, v, D, H, W, W, z, y, x, uz, uy, ux);
 }
 
 template <bool GRAD>
@@ -213,6 +221,15 @@ __device__ __forceinline__ float tri_sample(const float *__restrict__ v, int D, 
                                             float &gz, float &gy, float &gx) {
     TriPending p;
     tri_issue(p, v, D, H, W, z, y, x, uz, uy, ux);
+    return tri_finish<GRAD>(p, gz, gy, gx);
+}
+
+template <bool GRAD>
+__device__ __forceinline__ float tri_sample_p(const float *__restrict__ v, int D, int H, int W,
+                                              int P, int z, int y, int x, float uz, float uy,
+                                              float ux, float &gz, float &gy, float &gx) {
+    TriPending p;
+    tri_issue_p(p, v, D, H, W, P, z, y, x, uz, uy, ux);
     return tri_finish<GRAD>(p, gz, gy, gx);
 }
 

@@ -5,6 +5,7 @@
 
 #include <map>
 #include <mutex>
+#include <unordered_map>
 
 namespace fa {
 
@@ -90,36 +91,45 @@ EncodeTiledFn encode_fn() {
 
 struct MapKey {
     const void *base;
-    int esize, D, H, W, C, bx, by, bc;
+    int esize, D, H, W, P, C, bx, by, bc;
     bool operator==(const MapKey &o) const {
         return base == o.base && esize == o.esize && D == o.D && H == o.H && W == o.W &&
-               C == o.C && bx == o.bx && by == o.by && bc == o.bc;
+               P == o.P && C == o.C && bx == o.bx && by == o.by && bc == o.bc;
+    }
+};
+struct MapKeyHash {
+    size_t operator()(const MapKey &k) const {
+        unsigned long long h = (unsigned long long)(uintptr_t)k.base;
+        const int f[9] = {k.esize, k.D, k.H, k.W, k.P, k.C, k.bx, k.by, k.bc};
+        for (int v : f) h = (h ^ (unsigned)v) * 0x100000001b3ull;
+        return (size_t)h;
     }
 };
 
-// Map of a [C][D][H][W] field of 4- or 8-byte elements with a {bx, by, 1, bc}
-// box, zero fill outside the field.  Encoded maps are kept per host thread
-// (a launch sequence reuses a handful of buffers).  False when the field
-// does not meet TMA's alignment rules (row pitch a multiple of 16 bytes).
+}  // namespace
+
+// Map of a [C][D][H][W] field of 4- or 8-byte elements (rows of d.pitch()
+// elements) with a {bx, by, 1, bc} box, zero fill outside the D x H x W grid
+// (so a padded row's tail is never read).  Encoded maps are kept per host
+// thread (a map is a function of its key alone; a lockstep batch reuses a
+// few hundred).  False when the field does not meet TMA's alignment rules
+// (base and row pitch multiples of 16 bytes).
 bool tmap(CUtensorMap *m, const void *base, int esize, Dims d, int C, int bx, int by, int bc) {
-    constexpr int kCache = 64;
-    thread_local MapKey keys[kCache];
-    thread_local CUtensorMap maps[kCache];
-    thread_local int used = 0, next = 0;
-    const MapKey key{base, esize, d.D, d.H, d.W, C, bx, by, bc};
-    for (int i = 0; i < used; ++i)
-        if (keys[i] == key) {
-            *m = maps[i];
-            return true;
-        }
+    thread_local std::unordered_map<MapKey, CUtensorMap, MapKeyHash> cache;
+    const MapKey key{base, esize, d.D, d.H, d.W, d.pitch(), C, bx, by, bc};
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+        *m = it->second;
+        return true;
+    }
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
-    if (((uintptr_t)base & 15u) != 0 || ((long long)d.W * esize) % 16 != 0 ||
-        (d.N() * esize) % 16 != 0)
+    const long long P = d.pitch();
+    if (((uintptr_t)base & 15u) != 0 || (P * esize) % 16 != 0 || (d.NP() * esize) % 16 != 0)
         return false;
     cuuint64_t dims[4] = {(cuuint64_t)d.W, (cuuint64_t)d.H, (cuuint64_t)d.D, (cuuint64_t)C};
-    cuuint64_t strides[3] = {(cuuint64_t)d.W * esize, (cuuint64_t)d.W * d.H * esize,
-                             (cuuint64_t)d.N() * esize};
+    cuuint64_t strides[3] = {(cuuint64_t)P * esize, (cuuint64_t)P * d.H * esize,
+                             (cuuint64_t)d.NP() * esize};
     cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1u, (cuuint32_t)bc};
     cuuint32_t es[4] = {1u, 1u, 1u, 1u};
     CUtensorMap tm;
@@ -128,12 +138,13 @@ bool tmap(CUtensorMap *m, const void *base, int esize, Dims d, int C, int bx, in
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return false;
-    const int slot = used < kCache ? used++ : (next++ % kCache);
-    keys[slot] = key;
-    maps[slot] = tm;
+    if (cache.size() >= 4096) cache.clear();
+    cache.emplace(key, tm);
     *m = tm;
     return true;
 }
+
+namespace {
 
 
 template <int R>
@@ -151,14 +162,14 @@ cudaError_t launch_k1(const float *If, const float *J, const long long *sI, cons
         auto kern = k_lncc_fwd<R, K1_NW, K1_OPT, K1_ST_TMA, true>;
         static const int occ = prepare(kern, ST::bytes, ST::NT);
         LaunchGeom g = geometry(occ, K1_NW, ST::TY, R, d, tc.tz);
-        le = launch_pdl(kern, g, ST::bytes, s, mp, If, J, sI, varI, coef, h, d.D, d.H, d.W, g.tz,
+        le = launch_pdl(kern, g, ST::bytes, s, mp, If, J, sI, varI, coef, h, d.D, d.H, d.W, d.pitch(), g.tz,
                                                 bits, cc_eps, window, wc ? 1 : 0);
     } else {
         using SC = K1S<R, K1_NW, K1_OPT, K1_ST_CP>;
         auto kern = k_lncc_fwd<R, K1_NW, K1_OPT, K1_ST_CP, false>;
         static const int occ = prepare(kern, SC::bytes, SC::NT);
         LaunchGeom g = geometry(occ, K1_NW, SC::TY, R, d, tc.tz);
-        le = launch_pdl(kern, g, SC::bytes, s, mp, If, J, sI, varI, coef, h, d.D, d.H, d.W, g.tz,
+        le = launch_pdl(kern, g, SC::bytes, s, mp, If, J, sI, varI, coef, h, d.D, d.H, d.W, d.pitch(), g.tz,
                                                 bits, cc_eps, window, wc ? 1 : 0);
     }
     note_launch();
@@ -180,14 +191,14 @@ cudaError_t launch_k2(const float *If, const float *gJ, const float *J, const fl
         auto kern = k_lncc_grad<R, K2_NW, K2_OPT, K2_ST_TMA, true, WDJ>;
         static const int occ = prepare(kern, ST::bytes, ST::NT);
         LaunchGeom gg = geometry(occ, K2_NW, ST::TY, R, d, tc.tz);
-        le = launch_pdl(kern, gg, ST::bytes, s, mp, If, gJ, J, coef, h, g, d.D, d.H, d.W, gg.tz,
+        le = launch_pdl(kern, gg, ST::bytes, s, mp, If, gJ, J, coef, h, g, d.D, d.H, d.W, d.pitch(), gg.tz,
                         cb, dJout);
     } else {
         using SC = K2S<R, K2_NW, K2_OPT, K2_ST_CP>;
         auto kern = k_lncc_grad<R, K2_NW, K2_OPT, K2_ST_CP, false, WDJ>;
         static const int occ = prepare(kern, SC::bytes, SC::NT);
         LaunchGeom gg = geometry(occ, K2_NW, SC::TY, R, d, tc.tz);
-        le = launch_pdl(kern, gg, SC::bytes, s, mp, If, gJ, J, coef, h, g, d.D, d.H, d.W, gg.tz,
+        le = launch_pdl(kern, gg, SC::bytes, s, mp, If, gJ, J, coef, h, g, d.D, d.H, d.W, d.pitch(), gg.tz,
                         cb, dJout);
     }
     note_launch();
@@ -202,7 +213,7 @@ cudaError_t launch_k3_tma(const Maps &mp, const float *g, TS *m, TS *v, float *d
     auto kern = k_smooth_adam<RG, NW, K3_OPT, K3_ST_TMA, true, TS>;
     static const int occ = prepare(kern, ST::bytes, ST::NT);
     LaunchGeom gg = geometry(occ, NW, ST::TY, RG, d, tz);
-    return launch_pdl(kern, gg, ST::bytes, s, mp, g, m, v, dir, h, d.D, d.H, d.W, gg.tz, t, ac,
+    return launch_pdl(kern, gg, ST::bytes, s, mp, g, m, v, dir, h, d.D, d.H, d.W, d.pitch(), gg.tz, t, ac,
                       parity);
 }
 
@@ -231,7 +242,7 @@ cudaError_t launch_k3(const float *g, TS *m, TS *v, float *dir, WsHeader *h, Dim
         auto kern = k_smooth_adam<RG, K3_NW, K3_OPT, K3_ST_CP, false, TS>;
         static const int occ = prepare(kern, SC::bytes, SC::NT);
         LaunchGeom gg = geometry(occ, K3_NW, SC::TY, RG, d, tc.tz);
-        le = launch_pdl(kern, gg, SC::bytes, s, mp, g, m, v, dir, h, d.D, d.H, d.W, gg.tz, t, ac,
+        le = launch_pdl(kern, gg, SC::bytes, s, mp, g, m, v, dir, h, d.D, d.H, d.W, d.pitch(), gg.tz, t, ac,
                         parity);
     }
     note_launch();
@@ -246,7 +257,7 @@ cudaError_t launch_k4_tma(const Maps &mp, const float *u, const float *dir, floa
     auto kern = k_compose<RG, NW, K4_OPT, SU, K4_ST_TMA, true>;
     static const int occ = prepare(kern, ST::bytes, ST::NT);
     LaunchGeom gg = geometry(occ, NW, ST::TY, RG, d, tz);
-    return launch_pdl(kern, gg, ST::bytes, s, mp, u, dir, uo, Im, J, gJ, h, d.D, d.H, d.W, gg.tz, t,
+    return launch_pdl(kern, gg, ST::bytes, s, mp, u, dir, uo, Im, J, gJ, h, d.D, d.H, d.W, d.pitch(), gg.tz, t,
                       lr, c_lp, parity);
 }
 
@@ -270,7 +281,7 @@ cudaError_t launch_k4(const float *u, const float *dir, float *uo, const float *
         auto kern = k_compose<RG, K4_NW, K4_OPT, SU, K4_ST_CP, false>;
         static const int occ = prepare(kern, SC::bytes, SC::NT);
         LaunchGeom gg = geometry(occ, K4_NW, SC::TY, RG, d, tc.tz);
-        le = launch_pdl(kern, gg, SC::bytes, s, mp, u, dir, uo, Im, J, gJ, h, d.D, d.H, d.W, gg.tz, t,
+        le = launch_pdl(kern, gg, SC::bytes, s, mp, u, dir, uo, Im, J, gJ, h, d.D, d.H, d.W, d.pitch(), gg.tz, t,
                         lr, c_lp, parity);
     }
     note_launch();

@@ -129,9 +129,24 @@ __device__ __forceinline__ void tma4(void *dst, const CUtensorMap *m, int x, int
 }
 
 // Tensor maps of one launch (the ones a kernel does not use stay zero).
-struct alignas(64) Maps {
+struct Maps {
     CUtensorMap a, b, c, d;
 };
+
+// The tensor maps a CTA's body loads through: generic addresses of maps in
+// the kernel's parameter space (a launch's Maps, or one job's entries of a
+// lockstep table); null where the body takes no TMA tiles.
+struct MapRef {
+    const CUtensorMap *a, *b, *c;
+};
+__device__ __forceinline__ MapRef map_ref(const Maps &m) { return MapRef{&m.a, &m.b, &m.c}; }
+
+}  // namespace
+// Map of a [C][D][H][W] field of 4- or 8-byte elements with rows of
+// d.pitch() elements, a {bx, by, 1, bc} box and zero fill outside the grid;
+// false when the field does not meet TMA's alignment rules.
+bool tmap(CUtensorMap *m, const void *base, int esize, Dims d, int C, int bx, int by, int bc);
+namespace {
 
 // Programmatic dependent launch: the fused kernels are launched so that a
 // kernel's CTAs may start while the previous kernel in the stream finishes.
@@ -162,9 +177,10 @@ template <int RY, int RX, int NW, int BXW, int COFF>
 struct Region {
     static constexpr int NJ = (RY + NW - 1) / NW;
     static constexpr int NC = (RX + 31) / 32;
-    int off[NJ * NC];  // y W + x inside the grid, -1 outside the grid, -2 outside the region
+    int off[NJ * NC];  // y P + x inside the grid, -1 outside the grid, -2 outside the region
     int sbase;
-    __device__ __forceinline__ void init(int wy, int tx, int ybase, int xbase, int H, int W) {
+    __device__ __forceinline__ void init(int wy, int tx, int ybase, int xbase, int H, int W,
+                                         int P) {
         sbase = wy * BXW + tx + COFF;
 #pragma unroll
         for (int j = 0; j < NJ; ++j)
@@ -173,7 +189,7 @@ struct Region {
                 const int ry = wy + NW * j, rx = tx + 32 * c;
                 const int y = ybase + ry, x = xbase + rx;
                 int o = -2;
-                if (ry < RY && rx < RX) o = (y >= 0 && y < H && x >= 0 && x < W) ? y * W + x : -1;
+                if (ry < RY && rx < RX) o = (y >= 0 && y < H && x >= 0 && x < W) ? y * P + x : -1;
                 off[j * NC + c] = o;
             }
     }
@@ -202,12 +218,12 @@ struct Region {
 template <int OPT, int NW>
 struct Outs {
     static constexpr int NT = 32 * NW, NOUT = OPT * NT;
-    int off[OPT];  // y W + x, -1 outside the grid
-    __device__ __forceinline__ void init(int wy, int tx, int y0, int x0, int H, int W) {
+    int off[OPT];  // y P + x (P: the row pitch), -1 outside the grid
+    __device__ __forceinline__ void init(int wy, int tx, int y0, int x0, int H, int W, int P) {
 #pragma unroll
         for (int o = 0; o < OPT; ++o) {
             const int y = y0 + wy + NW * o, x = x0 + tx;
-            off[o] = (y < H && x < W) ? y * W + x : -1;
+            off[o] = (y < H && x < W) ? y * P + x : -1;
         }
     }
     // C channels of this thread's outputs on plane zoff / (H W), to registers
@@ -483,12 +499,13 @@ struct K1S {
 
 // The body of K1 for the CTA with tile coordinates (bx, by, bz).
 template <int R, int NW, int OPT, int NSTG, bool TMA>
-__device__ __forceinline__ void lncc_fwd_body(const Maps *maps, const float *__restrict__ If,
+__device__ __forceinline__ void lncc_fwd_body(MapRef maps, const float *__restrict__ If,
                                               const float *__restrict__ J,
                                               const long long *__restrict__ SIg,
                                               const float *__restrict__ varIg,
                                               float *__restrict__ coef, WsHeader *__restrict__ h,
-                                              int D, int H, int W, int TZ, int bits, float cc_eps,
+                                              int D, int H, int W, int P, int TZ, int bits,
+                                              float cc_eps,
                                               int window, int write_coef, int bx, int by, int bz) {
     using S = K1S<R, NW, OPT, NSTG>;
     constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, BXW = S::BXW, COFF = S::COFF,
@@ -508,13 +525,13 @@ __device__ __forceinline__ void lncc_fwd_body(const Maps *maps, const float *__r
     const int tx = threadIdx.x, wy = threadIdx.y, tid = wy * FX + tx;
     const int x0 = bx * FX, y0 = by * TY, z0 = bz * TZ;
     const int zend = min(z0 + TZ, D);
-    const long long N = (long long)D * H * W, HW = (long long)H * W;
+    const long long N = (long long)D * H * P, HW = (long long)H * P;  // channel, plane strides
     const long long n = (long long)window * window * window;
     const float nf = (float)n, inv_nf = 1.0f / nf;
     G rg;
-    if (!TMA) rg.init(wy, tx, y0 - R, x0 - R, H, W);
+    if (!TMA) rg.init(wy, tx, y0 - R, x0 - R, H, W, P);
     Outs<OPT, NW> ou;
-    ou.init(wy, tx, y0, x0, H, W);
+    ou.init(wy, tx, y0, x0, H, W, P);
     if (TMA && tid == 0) {
         for (int k = 0; k < NSTG; ++k) mbar_init(bar + k);
         mbar_init_fence();
@@ -538,8 +555,8 @@ __device__ __forceinline__ void lncc_fwd_body(const Maps *maps, const float *__r
         if (TMA) {
             if (tid == 0 && i < np) {
                 mbar_expect(bar + s, S::tx_plane);
-                tma4(stage(s), &maps->a, x0 - XB, y0 - R, zp, 0, bar + s);
-                tma4(stage(s) + CS, &maps->b, x0 - XB, y0 - R, zp, 0, bar + s);
+                tma4(stage(s), maps.a, x0 - XB, y0 - R, zp, 0, bar + s);
+                tma4(stage(s) + CS, maps.b, x0 - XB, y0 - R, zp, 0, bar + s);
             }
         } else {
             if (i < np) {
@@ -681,9 +698,9 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_fwd(const __grid_constant__ Map
                                                      const float *__restrict__ varIg,
                                                      float *__restrict__ coef,
                                                      WsHeader *__restrict__ h, int D, int H, int W,
-                                                     int TZ, int bits, float cc_eps, int window,
-                                                     int write_coef) {
-    lncc_fwd_body<R, NW, OPT, NSTG, TMA>(&maps, If, J, SIg, varIg, coef, h, D, H, W, TZ, bits,
+                                                     int P, int TZ, int bits, float cc_eps,
+                                                     int window, int write_coef) {
+    lncc_fwd_body<R, NW, OPT, NSTG, TMA>(map_ref(maps), If, J, SIg, varIg, coef, h, D, H, W, P, TZ, bits,
                                          cc_eps, window, write_coef, blockIdx.x, blockIdx.y,
                                          blockIdx.z);
 }
@@ -708,12 +725,13 @@ struct K2S {
 // The body of K2 for the CTA with tile coordinates (bx, by, bz).  WDJ: also
 // write dL/dJ itself to dJout (the adjoint's scatter into dL/dI_m needs it).
 template <int R, int NW, int OPT, int NSTG, bool TMA, bool WDJ = false>
-__device__ __forceinline__ void lncc_grad_body(const Maps *maps, const float *__restrict__ If,
+__device__ __forceinline__ void lncc_grad_body(MapRef maps, const float *__restrict__ If,
                                                const float *__restrict__ gJ,
                                                const float *__restrict__ J,
                                                const float *__restrict__ coef,
                                                WsHeader *__restrict__ h, float *__restrict__ g,
-                                               int D, int H, int W, int TZ, int cbits, int bx,
+                                               int D, int H, int W, int P, int TZ, int cbits,
+                                               int bx,
                                                int by, int bz, float *__restrict__ dJout = nullptr) {
     using S = K2S<R, NW, OPT, NSTG>;
     constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, BXW = S::BXW, COFF = S::COFF,
@@ -730,12 +748,12 @@ __device__ __forceinline__ void lncc_grad_body(const Maps *maps, const float *__
     const int tx = threadIdx.x, wy = threadIdx.y, tid = wy * FX + tx;
     const int x0 = bx * FX, y0 = by * TY, z0 = bz * TZ;
     const int zend = min(z0 + TZ, D);
-    const long long N = (long long)D * H * W, HW = (long long)H * W;
-    const float inv_n = 1.0f / (float)N;
+    const long long N = (long long)D * H * P, HW = (long long)H * P;  // channel, plane strides
+    const float inv_n = 1.0f / (float)((long long)D * H * W);  // 1 / voxel count
     G rg;
-    if (!TMA) rg.init(wy, tx, y0 - R, x0 - R, H, W);
+    if (!TMA) rg.init(wy, tx, y0 - R, x0 - R, H, W, P);
     Outs<OPT, NW> ou;
-    ou.init(wy, tx, y0, x0, H, W);
+    ou.init(wy, tx, y0, x0, H, W, P);
     if (TMA && tid == 0) {
         for (int k = 0; k < NSTG; ++k) mbar_init(bar + k);
         mbar_init_fence();
@@ -761,7 +779,7 @@ __device__ __forceinline__ void lncc_grad_body(const Maps *maps, const float *__
         if (TMA) {
             if (tid == 0 && i < np) {
                 mbar_expect(bar + s, S::tx_plane);
-                tma4(stage(s), &maps->a, x0 - XB, y0 - R, zp, 0, bar + s);
+                tma4(stage(s), maps.a, x0 - XB, y0 - R, zp, 0, bar + s);
             }
         } else {
             if (i < np)
@@ -880,8 +898,9 @@ __global__ void __launch_bounds__(FX *NW) k_lncc_grad(const __grid_constant__ Ma
                                                       const float *__restrict__ coef,
                                                       WsHeader *__restrict__ h,
                                                       float *__restrict__ g, int D, int H, int W,
-                                                      int TZ, int cbits, float *__restrict__ dJout) {
-    lncc_grad_body<R, NW, OPT, NSTG, TMA, WDJ>(&maps, If, gJ, J, coef, h, g, D, H, W, TZ, cbits,
+                                                      int P, int TZ, int cbits,
+                                                      float *__restrict__ dJout) {
+    lncc_grad_body<R, NW, OPT, NSTG, TMA, WDJ>(map_ref(maps), If, gJ, J, coef, h, g, D, H, W, P, TZ, cbits,
                                                blockIdx.x, blockIdx.y, blockIdx.z, dJout);
 }
 
@@ -926,10 +945,10 @@ struct K3S {
 
 // The body of K3 for the CTA with tile coordinates (bx, by, bz).
 template <int RG, int NW, int OPT, int NSTG, bool TMA, class TT, class TS>
-__device__ __forceinline__ void smooth_adam_body(const Maps *maps, const float *__restrict__ g,
+__device__ __forceinline__ void smooth_adam_body(MapRef maps, const float *__restrict__ g,
                                                  TS *__restrict__ m, TS *__restrict__ v,
                                                  float *__restrict__ dir, WsHeader *__restrict__ h,
-                                                 int D, int H, int W, int TZ, const TT t,
+                                                 int D, int H, int W, int P, int TZ, const TT t,
                                                  const AdamConsts ac, int parity, int bx, int by,
                                                  int bz) {
     constexpr bool S32 = sizeof(TS) == 4, STAGED = S32 && TMA;
@@ -951,11 +970,11 @@ __device__ __forceinline__ void smooth_adam_body(const Maps *maps, const float *
     const int tx = threadIdx.x, wy = threadIdx.y, tid = wy * FX + tx;
     const int x0 = bx * FX, y0 = by * TY, z0 = bz * TZ;
     const int zend = min(z0 + TZ, D);
-    const long long N = (long long)D * H * W, HW = (long long)H * W;
+    const long long N = (long long)D * H * P, HW = (long long)H * P;  // channel, plane strides
     G rg;
-    if (!TMA) rg.init(wy, tx, y0 - RG, x0 - RG, H, W);
+    if (!TMA) rg.init(wy, tx, y0 - RG, x0 - RG, H, W, P);
     Outs<OPT, NW> ou;
-    ou.init(wy, tx, y0, x0, H, W);
+    ou.init(wy, tx, y0, x0, H, W, P);
     if (TMA && tid == 0) {
         for (int k = 0; k < NSTG; ++k) mbar_init(bar + k);
         mbar_init_fence();
@@ -970,10 +989,10 @@ __device__ __forceinline__ void smooth_adam_body(const Maps *maps, const float *
         if (TMA) {
             if (tid == 0 && i < np) {
                 mbar_expect(bar + s, S::tx_plane + (out ? S::tx_out : 0u));
-                tma4(stage(s), &maps->a, x0 - XB, y0 - RG, zp, 0, bar + s);
+                tma4(stage(s), maps.a, x0 - XB, y0 - RG, zp, 0, bar + s);
                 if (out) {
-                    tma4(ostage(s), &maps->b, x0, y0, zo, 0, bar + s);
-                    tma4(ostage(s) + 3 * NOUT, &maps->c, x0, y0, zo, 0, bar + s);
+                    tma4(ostage(s), maps.b, x0, y0, zo, 0, bar + s);
+                    tma4(ostage(s) + 3 * NOUT, maps.c, x0, y0, zo, 0, bar + s);
                 }
             }
         } else {
@@ -1094,9 +1113,9 @@ __global__ void __launch_bounds__(FX *NW, NW >= 16 ? 2 : 1) k_smooth_adam(const 
                                                         TS *__restrict__ v,
                                                         float *__restrict__ dir,
                                                         WsHeader *__restrict__ h, int D, int H,
-                                                        int W, int TZ, GaussTaps t, AdamConsts ac,
-                                                        int parity) {
-    smooth_adam_body<RG, NW, OPT, NSTG, TMA>(&maps, g, m, v, dir, h, D, H, W, TZ, t, ac, parity,
+                                                        int W, int P, int TZ, GaussTaps t,
+                                                        AdamConsts ac, int parity) {
+    smooth_adam_body<RG, NW, OPT, NSTG, TMA>(map_ref(maps), g, m, v, dir, h, D, H, W, P, TZ, t, ac, parity,
                                              blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
@@ -1125,12 +1144,13 @@ struct K4S {
 
 // The body of K4 for the CTA with tile coordinates (bx, by, bz).
 template <int RG, int NW, int OPT, bool SU, int NSTG, bool TMA, class TT>
-__device__ __forceinline__ void compose_body(const Maps *maps, const float *__restrict__ u,
+__device__ __forceinline__ void compose_body(MapRef maps, const float *__restrict__ u,
                                              const float *__restrict__ dir,
                                              float *__restrict__ uo,
                                              const float *__restrict__ Im,
                                              float *__restrict__ Jout, float *__restrict__ gJout,
-                                             WsHeader *__restrict__ h, int D, int H, int W, int TZ,
+                                             WsHeader *__restrict__ h, int D, int H, int W, int P,
+                                             int TZ,
                                              const TT t, float lr, float c_lp, int parity, int bx,
                                              int by, int bz) {
     using S = K4S<RG, NW, OPT, SU, NSTG>;
@@ -1151,15 +1171,15 @@ __device__ __forceinline__ void compose_body(const Maps *maps, const float *__re
     const int tx = threadIdx.x, wy = threadIdx.y, tid = wy * FX + tx;
     const int x0 = bx * FX, y0 = by * TY, z0 = bz * TZ;
     const int zend = min(z0 + TZ, D);
-    const long long N = (long long)D * H * W, HW = (long long)H * W;
+    const long long N = (long long)D * H * P, HW = (long long)H * P;  // channel, plane strides
     G rg;
     GU rgu;
     if (!TMA) {
-        rg.init(wy, tx, y0 - RG, x0 - RG, H, W);
-        if (SU) rgu.init(wy, tx, y0 - RG - 1, x0 - RG - 1, H, W);
+        rg.init(wy, tx, y0 - RG, x0 - RG, H, W, P);
+        if (SU) rgu.init(wy, tx, y0 - RG - 1, x0 - RG - 1, H, W, P);
     }
     Outs<OPT, NW> ou;
-    ou.init(wy, tx, y0, x0, H, W);
+    ou.init(wy, tx, y0, x0, H, W, P);
     if (TMA && tid == 0) {
         for (int k = 0; k <= NSTG; ++k) mbar_init(bar + k);
         mbar_init_fence();
@@ -1180,8 +1200,8 @@ __device__ __forceinline__ void compose_body(const Maps *maps, const float *__re
         if (TMA) {
             if (tid == 0 && i < np) {
                 mbar_expect(bar + s, S::tx_plane + (SU ? S::tx_u : 0u));
-                tma4(stage(s), &maps->a, x0 - XB, y0 - RG, zp, 0, bar + s);
-                if (SU) tma4(uslot(zp + 1), &maps->b, x0 - UXB, y0 - RG - 1, zp + 1, 0, bar + s);
+                tma4(stage(s), maps.a, x0 - XB, y0 - RG, zp, 0, bar + s);
+                if (SU) tma4(uslot(zp + 1), maps.b, x0 - UXB, y0 - RG - 1, zp + 1, 0, bar + s);
             }
         } else {
             if (i < np) {
@@ -1198,8 +1218,8 @@ __device__ __forceinline__ void compose_body(const Maps *maps, const float *__re
         if (TMA) {
             if (tid == 0) {
                 mbar_expect(bar + NSTG, 2u * S::tx_u);
-                tma4(uslot(zs - 1), &maps->b, x0 - UXB, y0 - RG - 1, zs - 1, 0, bar + NSTG);
-                tma4(uslot(zs), &maps->b, x0 - UXB, y0 - RG - 1, zs, 0, bar + NSTG);
+                tma4(uslot(zs - 1), maps.b, x0 - UXB, y0 - RG - 1, zs - 1, 0, bar + NSTG);
+                tma4(uslot(zs), maps.b, x0 - UXB, y0 - RG - 1, zs, 0, bar + NSTG);
             }
         } else {
             rgu.template load<3>(uslot(zs - 1), u, N, (long long)(zs - 1) * HW,
@@ -1301,11 +1321,12 @@ __device__ __forceinline__ void compose_body(const Maps *maps, const float *__re
                         const int pidx = tid + j * NT, ry = pidx / RX, rx = pidx - ry * RX;
                         const int y = y0 - RG + ry, x = x0 - RG + rx;
                         float gz, gy, gx;
-                        a = dz + tri_sample<false>(u, D, H, W, zp, y, x, dz, dy, dx, gz, gy, gx);
-                        b = dy + tri_sample<false>(u + N, D, H, W, zp, y, x, dz, dy, dx, gz, gy,
-                                                   gx);
-                        c = dx + tri_sample<false>(u + 2 * N, D, H, W, zp, y, x, dz, dy, dx, gz,
-                                                   gy, gx);
+                        a = dz + tri_sample_p<false>(u, D, H, W, P, zp, y, x, dz, dy, dx, gz, gy,
+                                                     gx);
+                        b = dy + tri_sample_p<false>(u + N, D, H, W, P, zp, y, x, dz, dy, dx, gz,
+                                                     gy, gx);
+                        c = dx + tri_sample_p<false>(u + 2 * N, D, H, W, P, zp, y, x, dz, dy, dx,
+                                                     gz, gy, gx);
                     }
                 }
                 up[k] = a;
@@ -1344,7 +1365,7 @@ __device__ __forceinline__ void compose_body(const Maps *maps, const float *__re
                 uo[gi] = a;
                 uo[N + gi] = b;
                 uo[2 * N + gi] = c;
-                tri_issue(jp[o], Im, D, H, W, zo, y0 + wy + NW * o, x0 + tx, a, b, c);
+                tri_issue_p(jp[o], Im, D, H, W, P, zo, y0 + wy + NW * o, x0 + tx, a, b, c);
                 jidx[o] = gi;
                 jlive[o] = true;
             }
@@ -1386,10 +1407,11 @@ __global__ void __launch_bounds__(FX *NW, NW >= 16 ? 2 : 1) k_compose(const __gr
                                                     float *__restrict__ Jout,
                                                     float *__restrict__ gJout,
                                                     WsHeader *__restrict__ h, int D, int H, int W,
-                                                    int TZ, GaussTaps t, float lr, float c_lp,
-                                                    int parity) {
-    compose_body<RG, NW, OPT, SU, NSTG, TMA>(&maps, u, dir, uo, Im, Jout, gJout, h, D, H, W, TZ, t,
-                                             lr, c_lp, parity, blockIdx.x, blockIdx.y, blockIdx.z);
+                                                    int P, int TZ, GaussTaps t, float lr,
+                                                    float c_lp, int parity) {
+    compose_body<RG, NW, OPT, SU, NSTG, TMA>(map_ref(maps), u, dir, uo, Im, Jout, gJout, h, D, H, W, P, TZ,
+                                             t, lr, c_lp, parity, blockIdx.x, blockIdx.y,
+                                             blockIdx.z);
 }
 
 // ================================================================ launch helpers

@@ -19,19 +19,22 @@ struct Scale3 {
     float s[3];
 };
 
+// Rows of Ps (source) and Pd (destination) elements; only x < W is read or
+// written.
 __global__ void __launch_bounds__(256) k_resample(const float *__restrict__ src, int Ds, int Hs,
-                                                  int Ws, float *__restrict__ dst, int Dd, int Hd,
-                                                  int Wd, int C, Scale3 sc) {
+                                                  int Ws, int Ps, float *__restrict__ dst, int Dd,
+                                                  int Hd, int Wd, int Pd, int C, Scale3 sc) {
     int x = blockIdx.x * 32 + threadIdx.x;
     int y = blockIdx.y * 8 + threadIdx.y;
     int z = blockIdx.z;
     if (x >= Wd || y >= Hd) return;
-    long long Ns = (long long)Ds * Hs * Ws, Nd = (long long)Dd * Hd * Wd;
-    long long i = ((long long)z * Hd + y) * Wd + x;
+    long long Ns = (long long)Ds * Hs * Ps, Nd = (long long)Dd * Hd * Pd;
+    long long i = ((long long)z * Hd + y) * Pd + x;
     float cz = ac_coord(z, Ds, Dd), cy = ac_coord(y, Hs, Hd), cx = ac_coord(x, Ws, Wd);
     float gz, gy, gx;
     for (int c = 0; c < C; ++c) {
-        float v = tri_sample<false>(src + c * Ns, Ds, Hs, Ws, 0, 0, 0, cz, cy, cx, gz, gy, gx);
+        float v = tri_sample_p<false>(src + c * Ns, Ds, Hs, Ws, Ps, 0, 0, 0, cz, cy, cx, gz, gy,
+                                      gx);
         dst[c * Nd + i] = v * sc.s[c];
     }
 }
@@ -41,7 +44,9 @@ cudaError_t launch_resample(const float *src, Dims ds, float *dst, Dims dd, int 
     Scale3 sc;
     for (int c = 0; c < 3; ++c) sc.s[c] = scale3 ? scale3[c] : 1.0f;
     VoxGrid g(dd.D, dd.H, dd.W);
-    k_resample<<<g.grid, g.block, 0, s>>>(src, ds.D, ds.H, ds.W, dst, dd.D, dd.H, dd.W, C, sc); note_launch();
+    k_resample<<<g.grid, g.block, 0, s>>>(src, ds.D, ds.H, ds.W, ds.pitch(), dst, dd.D, dd.H, dd.W,
+                                          dd.pitch(), C, sc);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -60,10 +65,14 @@ void handoff_scales(Dims c, Dims f, int power, float out[3]) {
     }
 }
 
-// Blur (sigma = s / 2) then resample; t1, t2: N floats of the input grid.
+// Blur (sigma = s / 2) then resample; t1, t2: N floats of the input grid
+// (which has no row padding); the level may have a row pitch of its own.
 cudaError_t launch_pyramid_level(const float *img, Dims d, int s, float *out, Dims dl, float *t1,
                                  float *t2, cudaStream_t st) {
-    if (s == 1) return cudaMemcpyAsync(out, img, sizeof(float) * d.N(), cudaMemcpyDeviceToDevice, st);
+    if (s == 1)
+        return cudaMemcpy2DAsync(out, sizeof(float) * dl.pitch(), img, sizeof(float) * d.pitch(),
+                                 sizeof(float) * d.W, (size_t)d.D * d.H, cudaMemcpyDeviceToDevice,
+                                 st);
     GaussTaps t;
     if (!make_gauss_taps(0.5f * (float)s, &t)) return cudaErrorInvalidValue;
     cudaError_t e;

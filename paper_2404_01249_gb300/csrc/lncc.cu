@@ -87,20 +87,21 @@ __global__ void __launch_bounds__(256) k_lncc_xpass(const float *__restrict__ I,
     p[4 * N + i] = sIJ;
 }
 
-// window sums along y (AXIS 1) or z (AXIS 2) of C int64 channels
+// window sums along y (AXIS 1) or z (AXIS 2) of C int64 channels (rows of P
+// elements, P >= W)
 template <int C, int AXIS>
 __global__ void __launch_bounds__(256) k_box_axis(const long long *__restrict__ in,
                                                   long long *__restrict__ out, int D, int H,
-                                                  int W, int R) {
+                                                  int W, int P, int R) {
     int x = blockIdx.x * 32 + threadIdx.x;
     int y = blockIdx.y * 8 + threadIdx.y;
     int z = blockIdx.z;
     if (x >= W || y >= H) return;
-    long long N = (long long)D * H * W;
-    long long i = ((long long)z * H + y) * W + x;
+    long long N = (long long)D * H * P;
+    long long i = ((long long)z * H + y) * P + x;
     const int c0 = AXIS == 1 ? y : z;
     const int n = AXIS == 1 ? H : D;
-    const long long stride = AXIS == 1 ? (long long)W : (long long)H * W;
+    const long long stride = AXIS == 1 ? (long long)P : (long long)H * P;
     int lo = max(-R, -c0), hi = min(R, n - 1 - c0);
 #pragma unroll
     for (int c = 0; c < C; ++c) {
@@ -337,18 +338,18 @@ __global__ void k_partials_finalize(const float *partials, long long nb, long lo
 
 // Window statistics of the fixed image alone (constant during a level): the
 // exact sum S_I and the rounded variance var_I, both as the LNCC kernels
-// compute them.
+// compute them.  Buffers have rows of P (>= W) elements.
 template <int R>
 __global__ void __launch_bounds__(256) k_fixed_xpass(const float *__restrict__ I,
                                                      const WsHeader *__restrict__ h,
                                                      long long *__restrict__ p, int D, int H,
-                                                     int W, int bits) {
+                                                     int W, int P, int bits) {
     int x = blockIdx.x * 32 + threadIdx.x;
     int y = blockIdx.y * 8 + threadIdx.y;
     int z = blockIdx.z;
     if (x >= W || y >= H) return;
-    long long N = (long long)D * H * W;
-    long long row = ((long long)z * H + y) * W;
+    long long N = (long long)D * H * P;
+    long long row = ((long long)z * H + y) * P;
     float sc = image_scale(h, bits);
     long long sI = 0, sII = 0;
 #pragma unroll
@@ -367,13 +368,14 @@ __global__ void __launch_bounds__(256) k_fixed_finalize(const long long *__restr
                                                         const WsHeader *__restrict__ h,
                                                         long long *__restrict__ sI_out,
                                                         float *__restrict__ varI_out, int D,
-                                                        int H, int W, int window, int bits) {
+                                                        int H, int W, int P, int window,
+                                                        int bits) {
     int x = blockIdx.x * 32 + threadIdx.x;
     int y = blockIdx.y * 8 + threadIdx.y;
     int z = blockIdx.z;
     if (x >= W || y >= H) return;
-    long long N = (long long)D * H * W;
-    long long i = ((long long)z * H + y) * W + x;
+    long long N = (long long)D * H * P;
+    long long i = ((long long)z * H + y) * P + x;
     const long long n = (long long)window * window * window;
     const float inv_nf = 1.0f / (float)n;
     float amax = fmaxf(__uint_as_float(h->absmax_bits[0]), __uint_as_float(h->absmax_bits[1]));
@@ -429,8 +431,8 @@ static void xpass_coef(const float *coef, const WsHeader *h, long long *p, Dims 
 template <int C>
 static void box_yz(long long *a, long long *b, Dims d, int R, cudaStream_t s) {
     VoxGrid g(d.D, d.H, d.W);
-    k_box_axis<C, 1><<<g.grid, g.block, 0, s>>>(a, b, d.D, d.H, d.W, R); note_launch();
-    k_box_axis<C, 2><<<g.grid, g.block, 0, s>>>(b, a, d.D, d.H, d.W, R); note_launch();
+    k_box_axis<C, 1><<<g.grid, g.block, 0, s>>>(a, b, d.D, d.H, d.W, d.pitch(), R); note_launch();
+    k_box_axis<C, 2><<<g.grid, g.block, 0, s>>>(b, a, d.D, d.H, d.W, d.pitch(), R); note_launch();
 }
 
 #define FA_DISPATCH_R(R, ...)                          \
@@ -521,11 +523,13 @@ cudaError_t launch_fixed_stats(const float *I, Dims d, int window, const WsHeade
     int R = window / 2;
     int bits = lncc_image_bits(window);
     VoxGrid g(d.D, d.H, d.W);
-    FA_DISPATCH_R(R, (k_fixed_xpass<RR><<<g.grid, g.block, 0, s>>>(I, h, p0, d.D, d.H, d.W, bits)));
+    FA_DISPATCH_R(R, (k_fixed_xpass<RR><<<g.grid, g.block, 0, s>>>(I, h, p0, d.D, d.H, d.W,
+                                                                   d.pitch(), bits)));
     note_launch();
-    k_box_axis<2, 1><<<g.grid, g.block, 0, s>>>(p0, p1, d.D, d.H, d.W, R); note_launch();
-    k_box_axis<2, 2><<<g.grid, g.block, 0, s>>>(p1, p0, d.D, d.H, d.W, R); note_launch();
-    k_fixed_finalize<<<g.grid, g.block, 0, s>>>(p0, h, sI, varI, d.D, d.H, d.W, window, bits);
+    k_box_axis<2, 1><<<g.grid, g.block, 0, s>>>(p0, p1, d.D, d.H, d.W, d.pitch(), R); note_launch();
+    k_box_axis<2, 2><<<g.grid, g.block, 0, s>>>(p1, p0, d.D, d.H, d.W, d.pitch(), R); note_launch();
+    k_fixed_finalize<<<g.grid, g.block, 0, s>>>(p0, h, sI, varI, d.D, d.H, d.W, d.pitch(), window,
+                                                bits);
     note_launch();
     return cudaGetLastError();
 }

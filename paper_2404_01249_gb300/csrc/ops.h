@@ -7,9 +7,16 @@
 
 namespace fa {
 
+// A grid of D x H x W voxels.  P, when set, is the row pitch of the buffers
+// that hold it (a multiple of 4 >= W, so that every row starts on a 16-byte
+// boundary and the fused kernels can take TMA tiles); 0 means pitch W.  N()
+// counts voxels; NP() the elements of one channel of a buffer (D H pitch).
 struct Dims {
     int D, H, W;
+    int P = 0;
     long long N() const { return (long long)D * H * W; }
+    int pitch() const { return P > 0 ? P : W; }
+    long long NP() const { return (long long)D * H * pitch(); }
 };
 
 // Gaussian taps of the method (exp(-k^2 / 2 sigma^2), |k| <= ceil(3 sigma),

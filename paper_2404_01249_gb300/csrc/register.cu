@@ -74,13 +74,31 @@ static fa_status check_params(const fa_params *p) {
     return check_adam_params(p, "fa_register", true);
 }
 
-// Workspace plan; with base == nullptr only sizes are computed.
+// Row pitch of a level's buffers: the width rounded up to a multiple of 4
+// where the four fused LNCC kernels run every step of the level, so that
+// they take TMA tiles at any width; 0 (the width itself) elsewhere.  The
+// padding is never read as data: TMA tiles describe the D x H x W grid and
+// fill beyond it with zeros, and every other access checks x < W.
+static int level_pitch(const fa_params *p, Dims d) {
+    if (p->loss != FA_LOSS_LNCC || p->use_jac || d.W % 4 == 0) return 0;
+    if (p->mode == FA_MODE_PLAIN || (p->mode == FA_MODE_PERSISTENT && persistent_eligible(p, d)))
+        return 0;
+    GaussTaps tg, tw;
+    make_gauss_taps(p->sigma_grad, &tg);
+    make_gauss_taps(p->sigma_warp, &tw);
+    if (tg.R > kMaxFusedRadius || tw.R > kMaxFusedRadius) return 0;  // separable passes, unpitched
+    return (d.W + 3) & ~3;
+}
+
+// Workspace plan; with base == nullptr only sizes are computed.  Level l's
+// images, u, m, nu and the fused buffers have rows of lvl[l].pitch()
+// elements; the full-resolution inputs and u_out have none.
 struct Plan {
     Dims full;
     Dims lvl[8];
     long long nmax;
     WsHeader *h;
-    float *If[8], *Im[8];
+    float *If[8], *Im[8];  // nullptr: the level is the unpadded input grid
     float *If0, *Im0;  // FP32 copies of 16-bit input images (else nullptr)
     float *u[2];
     void *m[2], *v[2];  // Adam moments, stored as p->state_storage
@@ -99,8 +117,10 @@ static void make_plan(Plan &P, void *base, size_t cap, Dims full, const fa_param
     P.nmax = 0;
     for (int l = 0; l < p->n_levels; ++l) {
         int s = p->scales[l];
-        P.lvl[l] = Dims{level_size(full.D, s), level_size(full.H, s), level_size(full.W, s)};
-        if (P.lvl[l].N() > P.nmax) P.nmax = P.lvl[l].N();
+        Dims d{level_size(full.D, s), level_size(full.H, s), level_size(full.W, s)};
+        d.P = level_pitch(p, d);
+        P.lvl[l] = d;
+        if (d.NP() > P.nmax) P.nmax = d.NP();
     }
     long long n = P.nmax;
     WsCarver c(base, cap);
@@ -111,11 +131,11 @@ static void make_plan(Plan &P, void *base, size_t cap, Dims full, const fa_param
         P.Im0 = c.take<float>(full.N());
     }
     for (int l = 0; l < p->n_levels; ++l) {
-        if (p->scales[l] == 1) {
+        if (p->scales[l] == 1 && P.lvl[l].pitch() == full.W) {
             P.If[l] = P.Im[l] = nullptr;  // the inputs themselves
         } else {
-            P.If[l] = c.take<float>(P.lvl[l].N());
-            P.Im[l] = c.take<float>(P.lvl[l].N());
+            P.If[l] = c.take<float>(P.lvl[l].NP());
+            P.Im[l] = c.take<float>(P.lvl[l].NP());
         }
     }
     for (int k = 0; k < 2; ++k) {
@@ -277,7 +297,12 @@ static fa_status registration_begin(Plan &P, const fa_vol *fixed, const fa_vol *
     }
     FA_CUDA_TRY(launch_header_reset(P.h, s));
     for (int l = 0; l < p->n_levels; ++l) {
-        if (p->scales[l] == 1) continue;
+        if (!P.If[l]) continue;
+        const Dims d = P.lvl[l];
+        if (d.pitch() != d.W) {  // zero padding: the level's max |I| reads whole rows
+            FA_CUDA_TRY(cudaMemsetAsync(P.If[l], 0, sizeof(float) * d.NP(), s));
+            FA_CUDA_TRY(cudaMemsetAsync(P.Im[l], 0, sizeof(float) * d.NP(), s));
+        }
         FA_CUDA_TRY(launch_pyramid_level(*If0, full, p->scales[l], P.If[l], P.lvl[l], P.t1, P.t2, s));
         FA_CUDA_TRY(launch_pyramid_level(*Im0, full, p->scales[l], P.Im[l], P.lvl[l], P.t1, P.t2, s));
     }
@@ -290,15 +315,16 @@ static fa_status level_begin(Plan &P, const fa_params *p, int l, const float *u_
                              const float *If, const float *Im, int *cur, cudaStream_t s) {
     const Dims d = P.lvl[l];
     if (l == 0) {
-        size_t b = sizeof(float) * 3 * d.N();
+        size_t b = sizeof(float) * 3 * d.NP();
         if (u_init) {  // start from a given displacement of the input grid
             float sc[3];
             handoff_scales(P.full, d, 1, sc);
+            if (d.pitch() != d.W) FA_CUDA_TRY(cudaMemsetAsync(P.u[*cur], 0, b, s));
             FA_CUDA_TRY(launch_resample(u_init, P.full, P.u[*cur], d, 3, sc, s));
         } else {
             FA_CUDA_TRY(cudaMemsetAsync(P.u[*cur], 0, b, s));
         }
-        const size_t bs = state_bytes(p->state_storage) * 3 * d.N();
+        const size_t bs = state_bytes(p->state_storage) * 3 * d.NP();
         FA_CUDA_TRY(cudaMemsetAsync(P.m[*cur], 0, bs, s));
         FA_CUDA_TRY(cudaMemsetAsync(P.v[*cur], 0, bs, s));
     } else {
@@ -314,7 +340,7 @@ static fa_status level_begin(Plan &P, const fa_params *p, int l, const float *u_
             FA_CUDA_TRY(launch_resample((const float *)P.v[*cur], c, (float *)P.v[nx], d, 3, sv, s));
         } else {  // 16-bit moments: widened, resampled in FP32, rounded back
             const int st = p->state_storage;
-            const long long nc = 3 * c.N(), nf = 3 * d.N();
+            const long long nc = 3 * c.NP(), nf = 3 * d.NP();
             FA_CUDA_TRY(launch_widen(P.m[*cur], st, P.t1, nc, s));
             FA_CUDA_TRY(launch_resample(P.t1, c, P.t2, d, 3, sm, s));
             FA_CUDA_TRY(launch_narrow(P.t2, st, P.m[nx], nf, s));
@@ -326,7 +352,7 @@ static fa_status level_begin(Plan &P, const fa_params *p, int l, const float *u_
     }
     // fixed-point scale of this level's images (max |I_f|, max |I_m|)
     FA_CUDA_TRY(cudaMemsetAsync(P.h->absmax_bits, 0, sizeof(P.h->absmax_bits), s));
-    FA_CUDA_TRY(launch_absmax2(If, Im, d.N(), P.h, s));
+    FA_CUDA_TRY(launch_absmax2(If, Im, d.NP(), P.h, s));  // padding (if any) holds zeros
     if (p->loss == FA_LOSS_MI) FA_CUDA_TRY(launch_mi_range(If, Im, d.N(), P.mi, s));
     if (p->mode != FA_MODE_PLAIN)
         FA_CUDA_TRY(fused_level_start(If, Im, P.u[*cur], d, p, P.h, P.fb, s));
@@ -339,15 +365,17 @@ static fa_status registration_end(Plan &P, const fa_params *p, const float *If, 
                                   cudaStream_t s) {
     const int L = p->n_levels - 1;
     FA_TRY(final_loss(P, p, L, If, Im, u, final_loss_dev, s));
-    FA_CUDA_TRY(cudaMemcpyAsync(u_out->data, u, sizeof(float) * 3 * P.lvl[L].N(),
-                                cudaMemcpyDeviceToDevice, s));
+    const Dims d = P.lvl[L];
+    FA_CUDA_TRY(cudaMemcpy2DAsync(u_out->data, sizeof(float) * d.W, u, sizeof(float) * d.pitch(),
+                                  sizeof(float) * d.W, (size_t)3 * d.D * d.H,
+                                  cudaMemcpyDeviceToDevice, s));
     return FA_OK;
 }
 
-// The images of level l (scale 1 is the full-resolution input itself).
-static const float *level_image(const Plan &P, const fa_params *p, int l, const float *const *lv,
-                                const float *full) {
-    return p->scales[l] == 1 ? full : lv[l];
+// The images of level l (an unpadded scale-1 level is the full-resolution
+// input itself).
+static const float *level_image(const float *const *lv, int l, const float *full) {
+    return lv[l] ? lv[l] : full;
 }
 
 // Everything one registration enqueues on stream s (arguments checked).
@@ -366,8 +394,8 @@ static fa_status enqueue_registration(const fa_vol *fixed, const fa_vol *moving,
     make_gauss_taps(p->sigma_warp, &tw);
     int cur = 0, t = 0;
     for (int l = 0; l < p->n_levels; ++l) {
-        const float *If = level_image(P, p, l, P.If, If0);
-        const float *Im = level_image(P, p, l, P.Im, Im0);
+        const float *If = level_image(P.If, l, If0);
+        const float *Im = level_image(P.Im, l, Im0);
         FA_TRY(level_begin(P, p, l, l == 0 ? u_init : nullptr, If, Im, &cur, s));
         Timer tm{timer, l};
         // a level whose fused kernels are timed runs them
@@ -442,8 +470,8 @@ static fa_status enqueue_lockstep(int n, const LockstepArgs *a, char *ws, size_t
             const fa_params *p = a[k].p;
             LockstepJob &j = jobs[(size_t)k];
             j.d = P[k].lvl[l];
-            j.If = level_image(P[k], p, l, P[k].If, If0[k]);
-            j.Im = level_image(P[k], p, l, P[k].Im, Im0[k]);
+            j.If = level_image(P[k].If, l, If0[k]);
+            j.Im = level_image(P[k].Im, l, Im0[k]);
             j.fb = &P[k].fb;
             j.h = P[k].h;
             j.p = p;

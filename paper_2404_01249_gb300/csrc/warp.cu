@@ -6,19 +6,21 @@
 
 namespace fa {
 
+// Every buffer has rows of P (>= W) elements; only x < W is read or written.
 template <bool GRAD>
 __global__ void __launch_bounds__(256) k_warp(const float *__restrict__ Im,
                                               const float *__restrict__ u, float *__restrict__ J,
-                                              float *__restrict__ grad, int D, int H, int W) {
+                                              float *__restrict__ grad, int D, int H, int W,
+                                              int P) {
     int x = blockIdx.x * 32 + threadIdx.x;
     int y = blockIdx.y * 8 + threadIdx.y;
     int z = blockIdx.z;
     if (x >= W || y >= H) return;
-    long long N = (long long)D * H * W;
-    long long i = ((long long)z * H + y) * W + x;
+    long long N = (long long)D * H * P;
+    long long i = ((long long)z * H + y) * P + x;
     float gz, gy, gx;
-    float v = tri_sample<GRAD>(Im, D, H, W, z, y, x, __ldg(u + i), __ldg(u + N + i),
-                               __ldg(u + 2 * N + i), gz, gy, gx);
+    float v = tri_sample_p<GRAD>(Im, D, H, W, P, z, y, x, __ldg(u + i), __ldg(u + N + i),
+                                 __ldg(u + 2 * N + i), gz, gy, gx);
     J[i] = v;
     if (GRAD) {
         grad[i] = gz;
@@ -31,10 +33,12 @@ cudaError_t launch_warp(const float *Im, const float *u, float *J, float *grad, 
                         cudaStream_t s) {
     VoxGrid g(d.D, d.H, d.W);
     if (grad) {
-        k_warp<true><<<g.grid, g.block, 0, s>>>(Im, u, J, grad, d.D, d.H, d.W); note_launch();
+        k_warp<true><<<g.grid, g.block, 0, s>>>(Im, u, J, grad, d.D, d.H, d.W, d.pitch());
+        note_launch();
     }
     else {
-        k_warp<false><<<g.grid, g.block, 0, s>>>(Im, u, J, nullptr, d.D, d.H, d.W); note_launch();
+        k_warp<false><<<g.grid, g.block, 0, s>>>(Im, u, J, nullptr, d.D, d.H, d.W, d.pitch());
+        note_launch();
     }
     return cudaGetLastError();
 }

@@ -100,6 +100,47 @@ def test_lockstep_equals_one_call_per_job(fa, graph):
             assert r["final_loss"] == ref["final_loss"], (i, c)
 
 
+def test_lockstep_copy_variant_equals_tma_variant(fa):
+    """The fused schedule gives a level of uneven width rows padded to a
+    multiple of 4 floats, so its kernels take TMA tiles; a job of the
+    persistent schedule keeps its small levels unpadded, and in a lockstep
+    wave those run the per-thread copy (cp.async) variant of the batch
+    kernels.  Both give the bits of one padded fa_register call per job."""
+    import dataclasses
+    fixed, moving, cfgs = _lockstep_jobs(fa)
+    for mode in ("fused", "persistent"):
+        mc = [dataclasses.replace(c, mode=mode) for c in cfgs]
+        out = fa.fa_register_batched_lockstep(fixed, moving, mc, jobs_per_wave=64)
+        for i in range(len(fixed)):
+            for c, p in enumerate(cfgs):
+                r = out[i * len(cfgs) + c]
+                ref = fa.fa_register(fixed[i], moving[i], p)
+                assert r["status"] == 0, (mode, i, c)
+                assert torch.equal(r["u"], ref["u"]), (mode, i, c)
+                assert r["final_loss"] == ref["final_loss"], (mode, i, c)
+
+
+def test_lockstep_full_wave_of_64_jobs(fa):
+    """64 jobs in one wave (the largest launch table, FP32 moments: three
+    tensor maps per job in K3's parameters) over uneven grids; sampled jobs
+    against one call each."""
+    r = np.random.default_rng(77)
+    shapes = [tuple(int(v) for v in r.integers(9, 23, size=3)) for _ in range(16)]
+    pairs = [synth.voronoi_pair(shape=s, seed=900 + i) for i, s in enumerate(shapes)]
+    fixed = [cuda(p[0]) for p in pairs]
+    moving = [cuda(p[1]) for p in pairs]
+    cfgs = [fa.RegParams(scales=(2, 1), iters=(4, 3), lr=lr, sigma_grad=sg)
+            for lr in (0.25, 1.0) for sg in (0.5, 2.0)]
+    out = fa.fa_register_batched_lockstep(fixed, moving, cfgs, jobs_per_wave=64)
+    assert len(out) == 64
+    for k in (0, 5, 22, 37, 50, 63):
+        i, c = divmod(k, len(cfgs))
+        ref = fa.fa_register(fixed[i], moving[i], cfgs[c])
+        assert out[k]["status"] == 0, k
+        assert torch.equal(out[k]["u"], ref["u"]), (k, shapes[i])
+        assert out[k]["final_loss"] == ref["final_loss"], k
+
+
 def test_lockstep_waves_and_replay_do_not_change_results(fa):
     fixed, moving, cfgs = _lockstep_jobs(fa)
     base = fa.fa_register_batched_lockstep(fixed, moving, cfgs, jobs_per_wave=64)
