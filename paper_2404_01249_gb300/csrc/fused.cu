@@ -435,14 +435,11 @@ fa_status fused_iteration(FusedBuffers &fb, WsHeader *h, const fa_params *p, Dim
                           fa_kernel_timer *timer, int level, cudaStream_t s) {
     KTimer kt{timer, level};
     auto start = [&](int id) -> cudaError_t {
-        return kt.on(id) ? cudaEventRecordWithFlags((cudaEvent_t)timer->start_events[timer->count], s,
-                                                    cudaEventRecordExternal)
-                         : cudaSuccess;
+        return kt.on(id) ? timer_record(timer->start_events[timer->count], s) : cudaSuccess;
     };
     auto stop = [&](int id) -> cudaError_t {
         if (!kt.on(id)) return cudaSuccess;
-        cudaError_t e = cudaEventRecordWithFlags((cudaEvent_t)timer->stop_events[timer->count], s,
-                                                 cudaEventRecordExternal);
+        cudaError_t e = timer_record(timer->stop_events[timer->count], s);
         timer->count++;
         return e;
     };

@@ -497,6 +497,40 @@ struct K1S {
     static constexpr size_t bytes = o_bar + 8 * NSTG;
 };
 
+// K1's output voxel from its window sums acc = (S_J, S_JJ, S_IJ) and the
+// fixed image's S_I (a1) and variance: cc into the loss sum qcc (bad when cc
+// leaves [0, 2]), and with write_coef the adjoint coefficients A, B and C
+// (float-float) at cp[0], cp[N], cp[2N], cp[3N] with their running maxima.
+__device__ __forceinline__ void lncc_fwd_output(const long long acc[3], long long a1, float varI,
+                                                long long n, float nf, float inv_nf, float inv_s,
+                                                float cc_eps, int write_coef, float *cp,
+                                                long long N, unsigned long long &qcc, bool &bad,
+                                                float &mA, float &mB, float &mC) {
+    const long long a2 = acc[0];
+    const float varJ = diff_i128_to_float(n, acc[1], a2, a2) * inv_s * inv_s * inv_nf;
+    const float cross = diff_i128_to_float(n, acc[2], a1, a2) * inv_s * inv_s * inv_nf;
+    const float den = fmaf(varI, varJ, cc_eps);
+    const float rden = __frcp_rn(den);
+    const float cc = cross * cross * rden;
+    if (cc >= 0.0f && cc <= 2.0f)
+        qcc += (unsigned long long)quantize(cc, 4294967296.0f);  // cc in [0, 2]
+    else
+        bad = true;
+    if (write_coef) {
+        const float A = 2.0f * cross * rden;
+        const float B = -cc * varI * rden;
+        float Ch, Cl;
+        lncc_c_ff(A, B, a1, a2, inv_s, nf, inv_nf, Ch, Cl);
+        cp[0] = A;
+        cp[N] = B;
+        cp[2 * N] = Ch;
+        cp[3 * N] = Cl;
+        mA = fmaxf(mA, fabsf(A));
+        mB = fmaxf(mB, fabsf(B));
+        mC = fmaxf(mC, fabsf(Ch));
+    }
+}
+
 // The body of K1 for the CTA with tile coordinates (bx, by, bz).
 template <int R, int NW, int OPT, int NSTG, bool TMA>
 __device__ __forceinline__ void lncc_fwd_body(MapRef maps, const float *__restrict__ If,
@@ -644,32 +678,8 @@ __device__ __forceinline__ void lncc_fwd_body(MapRef maps, const float *__restri
 #pragma unroll
             for (int o = 0; o < OPT; ++o) {
                 if (ou.off[o] < 0) continue;
-                const long long a2 = acc[o][0];
-                const float varI = vI[o];
-                const float varJ = diff_i128_to_float(n, acc[o][1], a2, a2) * inv_s * inv_s * inv_nf;
-                const float cross =
-                    diff_i128_to_float(n, acc[o][2], a1[o], a2) * inv_s * inv_s * inv_nf;
-                const float den = fmaf(varI, varJ, cc_eps);
-                const float rden = __frcp_rn(den);
-                const float cc = cross * cross * rden;
-                if (cc >= 0.0f && cc <= 2.0f)
-                    qcc += (unsigned long long)quantize(cc, 4294967296.0f);  // cc in [0, 2]
-                else
-                    bad = true;
-                if (write_coef) {
-                    const float A = 2.0f * cross * rden;
-                    const float B = -cc * varI * rden;
-                    float Ch, Cl;
-                    lncc_c_ff(A, B, a1[o], a2, inv_s, nf, inv_nf, Ch, Cl);
-                    float *cp = coef + zoff + ou.off[o];
-                    cp[0] = A;
-                    cp[N] = B;
-                    cp[2 * N] = Ch;
-                    cp[3 * N] = Cl;
-                    mA = fmaxf(mA, fabsf(A));
-                    mB = fmaxf(mB, fabsf(B));
-                    mC = fmaxf(mC, fabsf(Ch));
-                }
+                lncc_fwd_output(acc[o], a1[o], vI[o], n, nf, inv_nf, inv_s, cc_eps, write_coef,
+                                coef + zoff + ou.off[o], N, qcc, bad, mA, mB, mC);
             }
         }
     }

@@ -105,6 +105,17 @@ cudaError_t launch_gauss3(const float *in, float *out, float *t1, float *t2, int
                           const GaussTaps &t, cudaStream_t s);
 
 // ---- Adam, step scale, compose (adam.cu)
+// Records a kernel timer's event on s: as an external event node while s is
+// being captured into a graph (so that the replay records it), else plainly.
+inline cudaError_t timer_record(void *event, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
+    return cudaEventRecordWithFlags((cudaEvent_t)event, s,
+                                    cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal
+                                                                        : cudaEventRecordDefault);
+}
+
 struct AdamConsts {
     float b1, b2, eps, rbc1, rbc2;  // rbc = 1 / (1 - beta^t)
 };

@@ -196,13 +196,11 @@ struct Timer {
     }
     cudaError_t start(int kernel_id, cudaStream_t s) const {
         if (!on(kernel_id)) return cudaSuccess;
-        return cudaEventRecordWithFlags((cudaEvent_t)t->start_events[t->count], s,
-                                        cudaEventRecordExternal);
+        return timer_record(t->start_events[t->count], s);
     }
     cudaError_t stop(int kernel_id, cudaStream_t s) const {
         if (!on(kernel_id)) return cudaSuccess;
-        cudaError_t e = cudaEventRecordWithFlags((cudaEvent_t)t->stop_events[t->count], s,
-                                                 cudaEventRecordExternal);
+        cudaError_t e = timer_record(t->stop_events[t->count], s);
         t->count++;
         return e;
     }

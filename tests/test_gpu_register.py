@@ -2,6 +2,7 @@
 32^3 blobs workload (final LNCC within 1e-3, mean displacement difference
 below 0.05 voxel), plus edge cases and device status reporting."""
 import ctypes
+import dataclasses
 
 import numpy as np
 import pytest
@@ -188,6 +189,14 @@ def test_graph_replay_equals_launch_by_launch(fa):
         torch.cuda.synchronize()
         assert tm.count == 24
         assert all(a.elapsed_time(b) > 0 for a, b in zip(ev0, ev1))
+    assert torch.equal(u, direct["u"])
+    # without graph recording the events are recorded on the stream directly
+    tm = fa.make_timer(fa.FA_K_FUSED_ALL, 1, ev0, ev1)
+    fa.fa_register(fx, mv, dataclasses.replace(pg, graph=False), ws=ws, u_out=u, loss_out=loss,
+                   timer=tm)
+    torch.cuda.synchronize()
+    assert tm.count == 24
+    assert all(a.elapsed_time(b) > 0 for a, b in zip(ev0, ev1))
     assert torch.equal(u, direct["u"])
 
 
