@@ -159,14 +159,27 @@ __device__ __forceinline__ void pdl_trigger() {
     asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 }
 
-// Waits for the previous kernel, then exits the CTA uniformly when an earlier
-// CTA reported a timeout.
-__device__ __forceinline__ bool timed_out(const WsHeader *h, int tid, int *flag) {
-    pdl_wait();
+// For a CTA that has waited for the previous kernel (pdl_wait) and issued its
+// first copies and header loads (so that they are in flight while the status
+// word is read): true, uniformly over the CTA, when an earlier CTA reported a
+// timeout; the caller then drains its copies (drain_first) and returns.
+__device__ __forceinline__ bool status_timed_out(const WsHeader *h, int tid, int *flag) {
     if (tid == 0) *flag = (int)(*(volatile const unsigned *)&h->status & ST_TIMEOUT);
     __syncthreads();
     pdl_trigger();
     return *flag != 0;
+}
+
+// Bounded wait for the first min(n, NSTG - 1) stage copies a CTA issued
+// before it returns early (TMA), or for its copy groups (cp.async).
+template <bool TMA, int NSTG>
+__device__ __forceinline__ void drain_first(unsigned long long *bar, int n, int tid) {
+    if (TMA) {
+        if (tid == 0)
+            for (int j = 0; j < n && j < NSTG - 1; ++j) mbar_wait(bar + j, 0u);
+    } else {
+        cp_wait<0>();
+    }
 }
 
 // --------------------------------------------- cp.async position mapping
@@ -571,11 +584,6 @@ __device__ __forceinline__ void lncc_fwd_body(MapRef maps, const float *__restri
         mbar_init_fence();
     }
     for (int k = tid; k < NS * 3 * NOUT; k += NT) ring[k] = 0;
-    if (timed_out(h, tid, &flag)) return;
-    const float amax =
-        fmaxf(__uint_as_float(h->absmax_bits[0]), __uint_as_float(h->absmax_bits[1]));
-    const int sh = fixed_shift(amax, bits);
-    const float scale = pow2f(sh), inv_s = pow2f(-sh);
 
     long long acc[OPT][3];
 #pragma unroll
@@ -611,9 +619,20 @@ __device__ __forceinline__ void lncc_fwd_body(MapRef maps, const float *__restri
             ou.fetch(vIn, varIg, N, (long long)zo * HW);
         }
     };
+    // after the previous kernel: first copies, operands and header loads in
+    // flight together, then the status check
+    pdl_wait();
     fetch_ops(0);
 #pragma unroll
     for (int k = 0; k < NSTG - 1; ++k) issue(k);
+    const float amax =
+        fmaxf(__uint_as_float(h->absmax_bits[0]), __uint_as_float(h->absmax_bits[1]));
+    if (status_timed_out(h, tid, &flag)) {
+        drain_first<TMA, NSTG>(bar, np, tid);
+        return;
+    }
+    const int sh = fixed_shift(amax, bits);
+    const float scale = pow2f(sh), inv_s = pow2f(-sh);
 
     unsigned long long qcc = 0;
     float mA = 0.f, mB = 0.f, mC = 0.f;
@@ -769,14 +788,6 @@ __device__ __forceinline__ void lncc_grad_body(MapRef maps, const float *__restr
         mbar_init_fence();
     }
     for (int k = tid; k < NS * 3 * NOUT; k += NT) ring[k] = 0;
-    if (timed_out(h, tid, &flag)) return;
-    float qs[3], us[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const int e = fixed_shift(__uint_as_float(h->coef_max_bits[c]), cbits);
-        qs[c] = pow2f(e);
-        us[c] = pow2f(-e);
-    }
     long long acc[OPT][3];
 #pragma unroll
     for (int o = 0; o < OPT; ++o)
@@ -807,9 +818,26 @@ __device__ __forceinline__ void lncc_grad_body(MapRef maps, const float *__restr
             ou.fetch(Jn, J, N, (long long)zo * HW);
         }
     };
+    // after the previous kernel: first copies, operands and header loads in
+    // flight together, then the status check
+    pdl_wait();
     fetch_ops(0);
 #pragma unroll
     for (int k = 0; k < NSTG - 1; ++k) issue(k);
+    float cmax[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) cmax[c] = __uint_as_float(h->coef_max_bits[c]);
+    if (status_timed_out(h, tid, &flag)) {
+        drain_first<TMA, NSTG>(bar, np, tid);
+        return;
+    }
+    float qs[3], us[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int e = fixed_shift(cmax[c], cbits);
+        qs[c] = pow2f(e);
+        us[c] = pow2f(-e);
+    }
 
     int fail = -1, slot = 0;
     for (int i = 0; i < np; ++i) {
@@ -990,7 +1018,6 @@ __device__ __forceinline__ void smooth_adam_body(MapRef maps, const float *__res
         mbar_init_fence();
     }
     for (int k = tid; k < NS * 3 * NOUT; k += NT) ring[k] = 0.0f;
-    if (timed_out(h, tid, &flag)) return;
 
     const int zs = z0 - RG, np = zend - z0 + 2 * RG;
     auto issue = [&](int i) {
@@ -1023,9 +1050,16 @@ __device__ __forceinline__ void smooth_adam_body(MapRef maps, const float *__res
             }
         }
     };
+    // after the previous kernel: first copies and loads in flight, then the
+    // status check
+    pdl_wait();
     fetch_mv(0);
 #pragma unroll
     for (int k = 0; k < NSTG - 1; ++k) issue(k);
+    if (status_timed_out(h, tid, &flag)) {
+        drain_first<TMA, NSTG>(bar, np, tid);
+        return;
+    }
 
     float mx = 0.0f;
     bool bad = false;
@@ -1195,9 +1229,6 @@ __device__ __forceinline__ void compose_body(MapRef maps, const float *__restric
         mbar_init_fence();
     }
     for (int k = tid; k < NS * 3 * NOUT; k += NT) ring[k] = 0.0f;
-    if (timed_out(h, tid, &flag)) return;
-    const float mxd = __uint_as_float(h->step_max_bits[parity]);
-    const float e = (mxd > 0.0f) ? lr / (c_lp * mxd) : 0.0f;
 
     const int zs = z0 - RG, np = zend - z0 + 2 * RG;
     // u plane q lives in u stage (q - (zs - 1)) % NSU
@@ -1223,6 +1254,9 @@ __device__ __forceinline__ void compose_body(MapRef maps, const float *__restric
             cp_commit();
         }
     };
+    // after the previous kernel: first copies and the step maximum in flight
+    // together, then the status check
+    pdl_wait();
     // u planes zs - 1 and zs: barrier NSTG (TMA), or cp.async group 0
     if (SU) {
         if (TMA) {
@@ -1239,6 +1273,13 @@ __device__ __forceinline__ void compose_body(MapRef maps, const float *__restric
     }
 #pragma unroll
     for (int k = 0; k < NSTG - 1; ++k) issue(k);
+    const float mxd = __uint_as_float(h->step_max_bits[parity]);
+    if (status_timed_out(h, tid, &flag)) {
+        if (SU && TMA && tid == 0) mbar_wait(bar + NSTG, 0u);
+        drain_first<TMA, NSTG>(bar, np, tid);
+        return;
+    }
+    const float e = (mxd > 0.0f) ? lr / (c_lp * mxd) : 0.0f;
     bool ok0 = true;
     if (SU && TMA) ok0 = mbar_wait(bar + NSTG, 0u);
 
