@@ -1186,6 +1186,23 @@ struct K4S {
     static constexpr size_t bytes = o_bar + 8 * (NSTG + 1);
 };
 
+// Compose position of slot pidx in the RY x RX region (RX = 32 + 2 RG): the
+// first 32 RY slots are the region's first 32 columns row by row, so that a
+// warp's positions lie in one row and its shared-memory reads and writes of
+// them (d, the u cell corners, u') hit 32 consecutive words; the last 2 RG
+// columns follow.
+template <int RY, int RX>
+__device__ __forceinline__ void compose_position(int pidx, int &ry, int &rx) {
+    if (RX == 32 || pidx < 32 * RY) {
+        ry = pidx >> 5;
+        rx = pidx & 31;
+    } else {
+        const int e = pidx - 32 * RY;
+        ry = e / (RX - 32);
+        rx = 32 + e % (RX - 32);
+    }
+}
+
 // The body of K4 for the CTA with tile coordinates (bx, by, bz).
 template <int RG, int NW, int OPT, bool SU, int NSTG, bool TMA, class TT>
 __device__ __forceinline__ void compose_body(MapRef maps, const float *__restrict__ u,
@@ -1298,7 +1315,8 @@ __device__ __forceinline__ void compose_body(MapRef maps, const float *__restric
 #pragma unroll
     for (int j = 0; j < NJP; ++j) {
         const int pidx = tid + j * NT;
-        const int ry = pidx / RX, rx = pidx - ry * RX;
+        int ry, rx;
+        compose_position<RY, RX>(pidx, ry, rx);
         const int y = y0 - RG + ry, x = x0 - RG + rx;
         pk[j] = pidx < NP ? ry * BXW + rx + COFF : -1;
         pin[j] = pidx < NP && y >= 0 && y < H && x >= 0 && x < W;
@@ -1369,7 +1387,8 @@ __device__ __forceinline__ void compose_body(MapRef maps, const float *__restric
                             a = b = c = __int_as_float(0x7fc00000);  // impossible step: flag it
                         }
                     } else {
-                        const int pidx = tid + j * NT, ry = pidx / RX, rx = pidx - ry * RX;
+                        int ry, rx;
+                        compose_position<RY, RX>(tid + j * NT, ry, rx);
                         const int y = y0 - RG + ry, x = x0 - RG + rx;
                         float gz, gy, gx;
                         a = dz + tri_sample_p<false>(u, D, H, W, P, zp, y, x, dz, dy, dx, gz, gy,
