@@ -71,7 +71,8 @@ def test_batched_reports_nonfinite_job(fa):
 # order whatever the tiling, and reductions are order-independent).
 
 def _lockstep_jobs(fa, dtype=torch.float32):
-    # widths: multiples of 4 (the single-job path takes TMA there) and ragged ones
+    # widths: multiples of 4 and uneven ones (whose level rows the fused
+    # schedule pads to a multiple of 4 floats)
     shapes = [(20, 24, 28), (17, 22, 26), (24, 20, 16), (9, 13, 35)]
     pairs = [synth.voronoi_pair(shape=s, seed=700 + i) for i, s in enumerate(shapes)]
     fixed = [cuda(p[0]).to(dtype) for p in pairs]

@@ -82,8 +82,8 @@ def test_nonfinite_input_is_reported(fa, mode):
 
 @pytest.mark.parametrize("mode", ["plain", "fused"])
 def test_tiny_and_degenerate_grids(fa, orc, mode):
-    # widths that are multiples of 4 take the tile-copy (TMA) path with boxes
-    # larger than the grid; the others take the per-thread copy path
+    # the fused schedule stores every level with rows padded to a multiple of
+    # 4 floats and takes tile copies (TMA) with boxes larger than the grid
     for shape in [(1, 1, 1), (1, 4, 9), (3, 2, 5), (2, 3, 4), (5, 6, 8)]:
         r = np.random.default_rng(9)
         f = r.random(shape).astype(np.float32)
@@ -107,8 +107,8 @@ def test_tiny_and_degenerate_grids(fa, orc, mode):
 def test_fused_equals_plain(fa, kw, shape):
     """Both schedules compute the same arithmetic in the same order, so their
     results agree to float32 rounding over a whole multi-level run on a
-    brain-shaped grid: ragged (per-thread copies) and with widths that are
-    multiples of 4 (tile copies)."""
+    brain-shaped grid, of uneven width (the fused levels' rows padded) and
+    with widths that are multiples of 4."""
     f, m, _ = synth.voronoi_pair(shape=shape, seed=31)
     base = dict(scales=(2, 1), iters=(15, 8))
     base.update(kw)
@@ -116,6 +116,20 @@ def test_fused_equals_plain(fa, kw, shape):
     b = fa.fa_register(cuda(f), cuda(m), fa.RegParams(mode="fused", **base))
     assert abs(a["final_loss"] - b["final_loss"]) < 1e-5
     assert float((a["u"] - b["u"]).abs().max()) < 1e-4
+
+
+@pytest.mark.parametrize("shape", [(20, 23, 29), (17, 30, 41)])
+def test_padded_rows_against_oracle(fa, orc, shape):
+    """Uneven widths at every level (29 -> 15, 41 -> 21): the fused
+    schedule's padded level buffers (resampling, hand-off, u_out copy) give
+    the oracle's registration."""
+    f, m, _ = synth.voronoi_pair(shape=shape, seed=81)
+    out = fa.fa_register(cuda(f), cuda(m), fa.RegParams(scales=(2, 1), iters=(20, 10)))
+    f32 = lambda x: float(np.float32(x))  # noqa: E731
+    ref = orc.register(f, m, [2, 1], [20, 10], cc_eps=f32(1e-5), beta1=f32(0.9),
+                       beta2=f32(0.999), adam_eps=f32(1e-8))
+    assert abs(out["final_loss"] - ref["final_loss"]) < 1e-3
+    assert mean_disp_diff(out["u"], ref["u"]) < 0.05
 
 
 def test_fused_brain_level_against_oracle(fa, orc):
