@@ -697,13 +697,165 @@ def variant_oracle_sample(w, f, m, psi):
                       "plus the oracle's final evaluation"}
 
 
+# --------------------------------------------- PyTorch-primitives comparison
+def _torch_gauss_1d(sigma, dev):
+    """Normalised Gaussian taps exp(-k^2 / 2 sigma^2), |k| <= ceil(3 sigma)."""
+    import torch
+    if sigma <= 0:
+        return torch.ones(1, device=dev)
+    r = int(np.ceil(3 * sigma))
+    k = torch.arange(-r, r + 1, device=dev, dtype=torch.float64)
+    w = torch.exp(-k * k / (2 * sigma * sigma))
+    return (w / w.sum()).float()
+
+
+def _torch_smooth(x, w):
+    """Separable Gaussian of x [C, D, H, W] along z, y, x (zero outside)."""
+    import torch.nn.functional as F
+    c, r = x.shape[0], (w.numel() - 1) // 2
+    if r == 0:
+        return x
+    y = x.unsqueeze(0)
+    for axis in range(3):
+        shape = [1, 1, 1]
+        shape[axis] = w.numel()
+        pad = [0, 0, 0]
+        pad[axis] = r
+        y = F.conv3d(y, w.view(1, 1, *shape).expand(c, 1, *shape).contiguous(), padding=pad,
+                     groups=c)
+    return y[0]
+
+
+def _torch_grid(u):
+    """Normalised sampling grid of x + u(x) (align-corners), [1, D, H, W, 3] in x, y, z order."""
+    import torch
+    _, D, H, W = u.shape
+    z, y, x = torch.meshgrid(torch.arange(D, device=u.device), torch.arange(H, device=u.device),
+                             torch.arange(W, device=u.device), indexing="ij")
+    def norm(c, n):
+        return c * (2.0 / max(n - 1, 1)) - 1.0
+    gx = norm(x + u[2], W)
+    gy = norm(y + u[1], H)
+    gz = norm(z + u[0], D)
+    return torch.stack([gx, gy, gz], dim=-1).unsqueeze(0)
+
+
+def _torch_warp(img, u):
+    """img [C, D, H, W] sampled at x + u(x), trilinear, zero outside."""
+    import torch.nn.functional as F
+    return F.grid_sample(img.unsqueeze(0), _torch_grid(u), mode="bilinear", padding_mode="zeros",
+                         align_corners=True)[0]
+
+
+def _torch_lncc(I, J, win, eps):
+    """-mean cc of the box-window LNCC (window sums with zeros outside)."""
+    import torch.nn.functional as F
+    r = win // 2
+    n = float(win ** 3)
+    def box(v):
+        return F.avg_pool3d(v[None, None], win, stride=1, padding=r, count_include_pad=True)[0, 0] * n
+    sI, sJ, sII, sJJ, sIJ = box(I), box(J), box(I * I), box(J * J), box(I * J)
+    cross = sIJ - sI * sJ / n
+    varI = sII - sI * sI / n
+    varJ = sJJ - sJ * sJ / n
+    return -(cross * cross / (varI * varJ + eps)).mean()
+
+
+def _torch_register(If0, Im0, scales, iters, lr, sg, sw, win, eps, b1=0.9, b2=0.999,
+                    adam_eps=1e-8, c_lp=2.0):
+    """Algorithm 1 (Jacobian-free direction) written with PyTorch primitives
+    in the style of the paper's own implementation: grid_sample for the
+    warps, pooling for the LNCC window sums, autograd for dL/du, separable
+    convolutions for the Gaussians.  Returns (u, mean cc of the last level)."""
+    import torch
+    import torch.nn.functional as F
+    dev = If0.device
+    wg, ww = _torch_gauss_1d(sg, dev), _torch_gauss_1d(sw, dev)
+    u = m = v = None
+    prev = None
+    t = 0
+    for s, T in zip(scales, iters):
+        dims = tuple(level_size(a, s) for a in If0.shape)
+        def level(img):
+            x = _torch_smooth(img[None], _torch_gauss_1d(0.5 * s, dev)) if s > 1 else img[None]
+            if s > 1:
+                x = F.interpolate(x[None], size=dims, mode="trilinear", align_corners=True)[0]
+            return x[0]
+        If, Im = level(If0), level(Im0)
+        if u is None:
+            u = torch.zeros((3,) + dims, device=dev)
+            m = torch.zeros_like(u)
+            v = torch.zeros_like(u)
+        else:
+            sa = torch.tensor([(f - 1) / (c - 1) if c > 1 and f > 1 else 1.0
+                               for f, c in zip(dims, prev)], device=dev).view(3, 1, 1, 1)
+            def up(x):
+                return F.interpolate(x[None], size=dims, mode="trilinear", align_corners=True)[0]
+            u, m, v = up(u) * sa, up(m) / sa, up(v) / (sa * sa)
+        prev = dims
+        for _ in range(T):
+            t += 1
+            u_ = u.detach().requires_grad_(True)
+            L = _torch_lncc(If, _torch_warp(Im[None], u_)[0], win, eps)
+            g, = torch.autograd.grad(L, u_)
+            g = _torch_smooth(g, wg)
+            m = b1 * m + (1 - b1) * g
+            v = b2 * v + (1 - b2) * g * g
+            d = (m / (1 - b1 ** t)) / (torch.sqrt(v / (1 - b2 ** t)) + adam_eps)
+            delta = -(lr / (c_lp * d.norm(dim=0).max())) * d
+            u = _torch_smooth(delta + _torch_warp(u, delta), ww)
+    with torch.no_grad():
+        L = _torch_lncc(If, _torch_warp(Im[None], u)[0], win, eps)
+    return u, -float(L)
+
+
+def run_torch_primitives(args):
+    """The brain workload with the PyTorch-primitives form of the same
+    iteration (a comparison point in the style of the paper's own code: its
+    kernels are PyTorch's, not this library's), timed like the fused arm."""
+    import torch
+    from paper_2404_01249_gb300 import synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    shape = WORKLOAD["shape"]
+    f, m, _ = synth.voronoi_pair(shape=shape, seed=1000)
+    If0, Im0 = torch.from_numpy(f).to(dev), torch.from_numpy(m).to(dev)
+    kw = dict(scales=WORKLOAD["scales"], iters=WORKLOAD["iters"], lr=WORKLOAD["lr"],
+              sg=WORKLOAD["sigma_grad"], sw=WORKLOAD["sigma_warp"], win=WORKLOAD["window"],
+              eps=WORKLOAD["cc_eps"])
+    for _ in range(args.warmup):
+        _torch_register(If0, Im0, **kw)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        u, cc = _torch_register(If0, Im0, **kw)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    vi = voxel_iters(shape, WORKLOAD["scales"], WORKLOAD["iters"])
+    print(json.dumps({"metric": METRIC, "value": vi / (ms / 1e3), "unit": METRIC,
+                      "impl": "torch_primitives", "n_gpus": 1, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                      "dtype": "f32", "data": "synthetic", "final_lncc": cc,
+                      "config": {"workload": WORKLOAD["name"], "shape": list(shape),
+                                 "scales": list(WORKLOAD["scales"]),
+                                 "iters": list(WORKLOAD["iters"]),
+                                 "form": "PyTorch primitives (grid_sample, avg_pool3d, "
+                                         "conv3d, autograd); a comparison point, not this "
+                                         "library's path"}}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="fused", choices=["fused", "plain"])
+    ap.add_argument("--mode", default="fused", choices=["fused", "plain", "torch"],
+                    help="fused or plain: this library's schedules; torch: the same iteration "
+                         "written with PyTorch primitives (a comparison point)")
     ap.add_argument("--cpu-iters", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
@@ -742,6 +894,8 @@ def main():
         return run_batched(args)
     if args.workload != "brain":
         return run_variant(args)
+    if args.mode == "torch":
+        return run_torch_primitives(args)
     return run_gpu(args)
 
 
