@@ -22,8 +22,9 @@
 // Every kernel marches along z ("2.5-D" tiling): a CTA owns a 32 x TY tile of
 // (x, y) columns and a slab of TZ output planes.  A plane's inputs (the tile
 // plus its halo, and the operands of the plane's outputs) arrive NSTG - 1
-// planes ahead of use.  When the grid width is a multiple of 4 they come as
-// TMA tile copies issued by one thread and completed on an mbarrier (zero
+// planes ahead of use.  When the buffers' rows start on 16-byte boundaries
+// (a registration pads its levels' rows to a multiple of 4 floats) they come
+// as TMA tile copies issued by one thread and completed on an mbarrier (zero
 // fill outside the grid); otherwise each thread copies its own positions with
 // cp.async.  A plane is reduced along x (register-blocked, 16-byte shared
 // loads) and then y in shared memory; the last 2R + 1 in-plane results per
@@ -36,7 +37,8 @@
 //
 // Every wait on a TMA barrier is bounded; a wait that gives up sets
 // ST_TIMEOUT in the status word, waits (bounded again) for the CTA's copies
-// in flight and ends the CTA, and later CTAs that see the bit return at once.
+// in flight and ends the CTA, and later CTAs that see the bit drain their
+// first copies and return.
 #pragma once
 
 #include <cuda.h>
