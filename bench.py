@@ -173,7 +173,8 @@ def config_dict(args, world):
             "scales": list(WORKLOAD["scales"]), "iters": list(WORKLOAD["iters"]),
             "window": WORKLOAD["window"], "lr": WORKLOAD["lr"],
             "sigma_grad": WORKLOAD["sigma_grad"], "sigma_warp": WORKLOAD["sigma_warp"],
-            "loss": "lncc", "mode": args.mode, "pairs_per_rank": 1, "world_size": world,
+            "loss": "lncc", "mode": args.mode, "u_storage": args.field,
+            "pairs_per_rank": 1, "world_size": world,
             "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"}
 
 
@@ -213,7 +214,7 @@ def run_gpu(args):
     params = fa.RegParams(scales=WORKLOAD["scales"], iters=WORKLOAD["iters"],
                           window=WORKLOAD["window"], lr=WORKLOAD["lr"],
                           sigma_grad=WORKLOAD["sigma_grad"], sigma_warp=WORKLOAD["sigma_warp"],
-                          cc_eps=WORKLOAD["cc_eps"], mode=args.mode)
+                          cc_eps=WORKLOAD["cc_eps"], mode=args.mode, field=args.field)
     fixed = torch.from_numpy(f).to(dev)
     moving = torch.from_numpy(m).to(dev)
     ws = fa.workspace(fa.fa_register_workspace_size(shape, params), dev)
@@ -866,6 +867,8 @@ def main():
                     help="streams of --batched's streams and plain schedules")
     ap.add_argument("--schedule", default="lockstep", choices=["lockstep", "streams", "plain"],
                     help="timed form of --batched")
+    ap.add_argument("--field", default="f32", choices=["f32", "f16"],
+                    help="storage of the displacement u between iterations (fused mode)")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16"],
                     help="--batched: storage of the images and Adam moments")
     ap.add_argument("--no-compare", action="store_true",

@@ -115,13 +115,19 @@ typedef struct {
                              rounded to nearest.  FA_F16 is refused
                              (FA_ERR_UNSUPPORTED): its smallest normal value, 6.1e-5,
                              lies far above the moments of a loss gradient that scales
-                             as 1/N, which would flush to zero.  The displacement u
-                             stays FP32: rounded to BF16 after every update it moves a
-                             brain-shaped registration's result by 0.05 voxel on
-                             average, to FP16 by 0.02 voxel, and the fused kernels are
-                             not bound by its bytes.
+                             as 1/N, which would flush to zero.  The displacement u is
+                             stored as field_storage (below).
                              The symmetric, SVF, inverse, affine and rigid calls take
                              FA_F32 only (FA_ERR_UNSUPPORTED otherwise). */
+    int32_t field_storage; /* fa_dtype of the displacement u kept between iterations and
+                             levels by fa_register, fa_register_from and
+                             fa_register_batched: FA_F32 (default) or FA_F16.  With
+                             FA_F16 every update of u is rounded to FP16 when stored
+                             (arithmetic stays FP32; u_out is returned in FP32); it
+                             needs FA_MODE_FUSED, the LNCC loss, use_jac = 0 and both
+                             Gaussians within the fused kernels' radius
+                             (FA_ERR_UNSUPPORTED otherwise), and the lockstep call and
+                             every other call take FA_F32 only. */
 } fa_params;
 
 /* Fills p with: 3 levels {4,2,1} x {200,100,50}, lr 0.5, sigma_grad 1,

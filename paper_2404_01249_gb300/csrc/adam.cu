@@ -211,6 +211,10 @@ fa_status check_adam_params(const fa_params *p, const char *who, bool state16_ok
         set_error("%s: keeps its Adam moments in FP32 (state_storage must be FA_F32)", who);
         return FA_ERR_UNSUPPORTED;
     }
+    if (!state16_ok && p->field_storage != FA_F32) {
+        set_error("%s: keeps its fields in FP32 (field_storage must be FA_F32)", who);
+        return FA_ERR_UNSUPPORTED;
+    }
     if (!(p->beta1 >= 0.0f && p->beta1 < 1.0f) || !(p->beta2 >= 0.0f && p->beta2 < 1.0f) ||
         !(p->adam_eps >= 0.0f) || !(p->lr > 0.0f && p->lr < 1e30f) ||
         !(p->c_lp > 0.0f && p->c_lp < 1e30f)) {

@@ -140,9 +140,14 @@ struct TriPending {
     float tz, ty, tx;
 };
 
+// A stored field value as FP32 (FP32, or FP16 read exactly).
+__device__ __forceinline__ float ld_field(const float *q) { return __ldg(q); }
+__device__ __forceinline__ float ld_field(const __half *q) { return __half2float(__ldg(q)); }
+
 // tri_issue_p: the same for a buffer of row pitch P (>= W; zero outside the
-// logical D x H x W grid whatever the padding holds).
-__device__ __forceinline__ void tri_issue_p(TriPending &p, const float *__restrict__ v, int D,
+// logical D x H x W grid whatever the padding holds), of FP32 or FP16 values.
+template <class T>
+__device__ __forceinline__ void tri_issue_p(TriPending &p, const T *__restrict__ v, int D,
                                             int H, int W, int P, int z, int y, int x, float uz,
                                             float uy, float ux) {
     p.c000 = p.c001 = p.c010 = p.c011 = p.c100 = p.c101 = p.c110 = p.c111 = 0.0f;
@@ -160,15 +165,15 @@ __device__ __forceinline__ void tri_issue_p(TriPending &p, const float *__restri
     p.tx = ux - fx;
     // 32-bit offsets: buffers hold fewer than 2^31 elements and iz >= -1
     if (iz >= 0 && iz + 1 < D && iy >= 0 && iy + 1 < H && ix >= 0 && ix + 1 < W) {
-        const float *q0 = v + (iz * H + iy) * P + ix, *q1 = q0 + H * P;  // the whole cell inside
-        p.c000 = __ldg(q0);
-        p.c001 = __ldg(q0 + 1);
-        p.c010 = __ldg(q0 + P);
-        p.c011 = __ldg(q0 + P + 1);
-        p.c100 = __ldg(q1);
-        p.c101 = __ldg(q1 + 1);
-        p.c110 = __ldg(q1 + P);
-        p.c111 = __ldg(q1 + P + 1);
+        const T *q0 = v + (iz * H + iy) * P + ix, *q1 = q0 + H * P;  // the whole cell inside
+        p.c000 = ld_field(q0);
+        p.c001 = ld_field(q0 + 1);
+        p.c010 = ld_field(q0 + P);
+        p.c011 = ld_field(q0 + P + 1);
+        p.c100 = ld_field(q1);
+        p.c101 = ld_field(q1 + 1);
+        p.c110 = ld_field(q1 + P);
+        p.c111 = ld_field(q1 + P + 1);
         return;
     }
     if (iz < -1 || iz >= D || iy < -1 || iy >= H || ix < -1 || ix >= W) return;
@@ -176,15 +181,15 @@ __device__ __forceinline__ void tri_issue_p(TriPending &p, const float *__restri
     const bool y0 = iy >= 0, y1 = iy + 1 < H;
     const bool x0 = ix >= 0, x1 = ix + 1 < W;
     const int b = (iz * H + iy) * P + ix;
-    const float *q0 = v + b, *q1 = q0 + H * P;
-    if (z0 && y0 && x0) p.c000 = __ldg(q0);
-    if (z0 && y0 && x1) p.c001 = __ldg(q0 + 1);
-    if (z0 && y1 && x0) p.c010 = __ldg(q0 + P);
-    if (z0 && y1 && x1) p.c011 = __ldg(q0 + P + 1);
-    if (z1 && y0 && x0) p.c100 = __ldg(q1);
-    if (z1 && y0 && x1) p.c101 = __ldg(q1 + 1);
-    if (z1 && y1 && x0) p.c110 = __ldg(q1 + P);
-    if (z1 && y1 && x1) p.c111 = __ldg(q1 + P + 1);
+    const T *q0 = v + b, *q1 = q0 + H * P;
+    if (z0 && y0 && x0) p.c000 = ld_field(q0);
+    if (z0 && y0 && x1) p.c001 = ld_field(q0 + 1);
+    if (z0 && y1 && x0) p.c010 = ld_field(q0 + P);
+    if (z0 && y1 && x1) p.c011 = ld_field(q0 + P + 1);
+    if (z1 && y0 && x0) p.c100 = ld_field(q1);
+    if (z1 && y0 && x1) p.c101 = ld_field(q1 + 1);
+    if (z1 && y1 && x0) p.c110 = ld_field(q1 + P);
+    if (z1 && y1 && x1) p.c111 = ld_field(q1 + P + 1);
 }
 
 __device__ __forceinline__ void tri_issue(TriPending &p, const float *__restrict__ v, int D,
@@ -224,8 +229,8 @@ __device__ __forceinline__ float tri_sample(const float *__restrict__ v, int D, 
     return tri_finish<GRAD>(p, gz, gy, gx);
 }
 
-template <bool GRAD>
-__device__ __forceinline__ float tri_sample_p(const float *__restrict__ v, int D, int H, int W,
+template <bool GRAD, class T>
+__device__ __forceinline__ float tri_sample_p(const T *__restrict__ v, int D, int H, int W,
                                               int P, int z, int y, int x, float uz, float uy,
                                               float ux, float &gz, float &gy, float &gx) {
     TriPending p;

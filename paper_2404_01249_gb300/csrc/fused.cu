@@ -108,7 +108,7 @@ struct MapKeyHash {
 
 }  // namespace
 
-// Map of a [C][D][H][W] field of 4- or 8-byte elements (rows of d.pitch()
+// Map of a [C][D][H][W] field of 2- (FP16), 4- or 8-byte elements (rows of d.pitch()
 // elements) with a {bx, by, 1, bc} box, zero fill outside the D x H x W grid
 // (so a padded row's tail is never read).  Encoded maps are kept per host
 // thread (a map is a function of its key alone; a lockstep batch reuses a
@@ -133,7 +133,10 @@ bool tmap(CUtensorMap *m, const void *base, int esize, Dims d, int C, int bx, in
     cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1u, (cuuint32_t)bc};
     cuuint32_t es[4] = {1u, 1u, 1u, 1u};
     CUtensorMap tm;
-    CUresult r = fn(&tm, esize == 8 ? CU_TENSOR_MAP_DATA_TYPE_INT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+    const CUtensorMapDataType dt = esize == 8   ? CU_TENSOR_MAP_DATA_TYPE_INT64
+                                   : esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    CUresult r = fn(&tm, dt,
                     4, const_cast<void *>(base), dims, strides, box, es,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -249,40 +252,48 @@ cudaError_t launch_k3(const float *g, TS *m, TS *v, float *dir, WsHeader *h, Dim
     return le;
 }
 
-template <int RG, bool SU, int NW>
-cudaError_t launch_k4_tma(const Maps &mp, const float *u, const float *dir, float *uo,
+template <int RG, bool SU, int NW, class TU>
+cudaError_t launch_k4_tma(const Maps &mp, const TU *u, const float *dir, TU *uo,
                           const float *Im, float *J, float *gJ, WsHeader *h, Dims d, const GaussTaps &t,
                           float lr, float c_lp, int parity, int tz, cudaStream_t s) {
-    using ST = K4S<RG, NW, K4_OPT, SU, K4_ST_TMA>;
-    auto kern = k_compose<RG, NW, K4_OPT, SU, K4_ST_TMA, true>;
+    using ST = K4S<RG, NW, K4_OPT, SU, K4_ST_TMA, TU>;
+    auto kern = k_compose<RG, NW, K4_OPT, SU, K4_ST_TMA, true, TU>;
     static const int occ = prepare(kern, ST::bytes, ST::NT);
     LaunchGeom gg = geometry(occ, NW, ST::TY, RG, d, tz);
     return launch_pdl(kern, gg, ST::bytes, s, mp, u, dir, uo, Im, J, gJ, h, d.D, d.H, d.W, d.pitch(), gg.tz, t,
                       lr, c_lp, parity);
 }
 
-template <int RG, bool SU>
-cudaError_t launch_k4(const float *u, const float *dir, float *uo, const float *Im, float *J,
+// TU: storage of u (float, or __half: tile copies only; cudaErrorNotSupported
+// when a field does not take them).
+template <int RG, bool SU, class TU>
+cudaError_t launch_k4(const TU *u, const float *dir, TU *uo, const float *Im, float *J,
                       float *gJ, WsHeader *h, Dims d, const GaussTaps &t, float lr, float c_lp, int parity,
                       cudaStream_t s) {
+    constexpr int EU = (int)sizeof(TU);
+    using S16 = K4S<RG, 16, K4_OPT, SU, K4_ST_TMA, TU>;
+    using S8 = K4S<RG, 8, K4_OPT, SU, K4_ST_TMA, TU>;
     Maps mp{};
     cudaError_t le;
     const TileChoice tc = tile_choice(3, RG, SU ? 1 : 0, d);
     const int nw = tc.wide ? 16 : 8;
+    const int ubx = tc.wide ? S16::UBXW : S8::UBXW;
     const bool tma = tmap(&mp.a, dir, 4, d, 3, FX + 2 * halo4(RG), nw + 2 * RG, 3) &&
-                     (!SU || tmap(&mp.b, u, 4, d, 3, FX + 2 * halo4(RG + 1), nw + 2 * RG + 2, 3));
+                     (!SU || tmap(&mp.b, u, EU, d, 3, ubx, nw + 2 * RG + 2, 3));
     if (tma) {
         le = tc.wide ? launch_k4_tma<RG, SU, 16>(mp, u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity,
                                                  tc.tz, s)
                      : launch_k4_tma<RG, SU, 8>(mp, u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity,
                                                 tc.tz, s);
-    } else {
+    } else if constexpr (EU == 4) {
         using SC = K4S<RG, K4_NW, K4_OPT, SU, K4_ST_CP>;
         auto kern = k_compose<RG, K4_NW, K4_OPT, SU, K4_ST_CP, false>;
         static const int occ = prepare(kern, SC::bytes, SC::NT);
         LaunchGeom gg = geometry(occ, K4_NW, SC::TY, RG, d, tc.tz);
         le = launch_pdl(kern, gg, SC::bytes, s, mp, u, dir, uo, Im, J, gJ, h, d.D, d.H, d.W, d.pitch(), gg.tz, t,
                         lr, c_lp, parity);
+    } else {
+        return cudaErrorNotSupported;
     }
     note_launch();
     return le;
@@ -367,32 +378,42 @@ cudaError_t dispatch_k3(const float *g, void *m, void *v, int state, float *dir,
     return dispatch_k3_ts(g, (float *)m, (float *)v, dir, h, d, t, ac, parity, s);
 }
 
-cudaError_t dispatch_k4(const float *u, const float *dir, float *uo, const float *Im, float *J,
-                        float *gJ,
-                        WsHeader *h, Dims d, const GaussTaps &t, float lr, float c_lp, int parity,
-                        bool su, cudaStream_t s) {
+template <class TU>
+cudaError_t dispatch_k4_t(const TU *u, const float *dir, TU *uo, const float *Im, float *J,
+                          float *gJ, WsHeader *h, Dims d, const GaussTaps &t, float lr,
+                          float c_lp, int parity, bool su, cudaStream_t s) {
     if (su) {
         switch (t.R) {
-            FA_CASE(0, (launch_k4<RR, true>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
-            FA_CASE(1, (launch_k4<RR, true>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
-            FA_CASE(2, (launch_k4<RR, true>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
-            FA_CASE(3, (launch_k4<RR, true>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
-            FA_CASE(4, (launch_k4<RR, true>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
-            FA_CASE(5, (launch_k4<RR, true>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
-            FA_CASE(6, (launch_k4<RR, true>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(0, (launch_k4<RR, true, TU>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(1, (launch_k4<RR, true, TU>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(2, (launch_k4<RR, true, TU>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(3, (launch_k4<RR, true, TU>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(4, (launch_k4<RR, true, TU>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(5, (launch_k4<RR, true, TU>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(6, (launch_k4<RR, true, TU>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
         }
     } else {
         switch (t.R) {
-            FA_CASE(0, (launch_k4<RR, false>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
-            FA_CASE(1, (launch_k4<RR, false>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
-            FA_CASE(2, (launch_k4<RR, false>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
-            FA_CASE(3, (launch_k4<RR, false>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
-            FA_CASE(4, (launch_k4<RR, false>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
-            FA_CASE(5, (launch_k4<RR, false>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
-            FA_CASE(6, (launch_k4<RR, false>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(0, (launch_k4<RR, false, TU>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(1, (launch_k4<RR, false, TU>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(2, (launch_k4<RR, false, TU>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(3, (launch_k4<RR, false, TU>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(4, (launch_k4<RR, false, TU>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(5, (launch_k4<RR, false, TU>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
+            FA_CASE(6, (launch_k4<RR, false, TU>(u, dir, uo, Im, J, gJ, h, d, t, lr, c_lp, parity, s)))
         }
     }
     return cudaErrorInvalidValue;
+}
+// u, uo: displacements stored as `field` (FA_F32 or FA_F16)
+cudaError_t dispatch_k4(const void *u, const float *dir, void *uo, int field, const float *Im,
+                        float *J, float *gJ, WsHeader *h, Dims d, const GaussTaps &t, float lr,
+                        float c_lp, int parity, bool su, cudaStream_t s) {
+    if (field == FA_F16)
+        return dispatch_k4_t((const __half *)u, dir, (__half *)uo, Im, J, gJ, h, d, t, lr, c_lp,
+                             parity, su, s);
+    return dispatch_k4_t((const float *)u, dir, (float *)uo, Im, J, gJ, h, d, t, lr, c_lp, parity,
+                         su, s);
 }
 #undef FA_CASE
 
@@ -427,7 +448,7 @@ cudaError_t fused_level_start(const float *If, const float *Im, const float *u, 
                                            (long long *)fb.g, fb.sI, fb.varI, s);
         if (e != cudaSuccess) return e;
     }
-    return launch_warp(Im, u, fb.J, fb.gJ, d, s);
+    return launch_warp_field(Im, u, p->field_storage, fb.J, fb.gJ, d, s);
 }
 
 fa_status fused_iteration(FusedBuffers &fb, WsHeader *h, const fa_params *p, Dims d,
@@ -482,7 +503,8 @@ fa_status fused_iteration(FusedBuffers &fb, WsHeader *h, const fa_params *p, Dim
                             adam_consts(p, it.t), parity, s));
     FA_CUDA_TRY(stop(FA_K_FUSED_SMOOTH_ADAM));
     FA_CUDA_TRY(start(FA_K_FUSED_COMPOSE));
-    FA_CUDA_TRY(dispatch_k4(it.u, fb.dir, it.u_alt, it.Im, fb.J, fb.gJ, h, d, wide_w ? ident : tw, p->lr,
+    FA_CUDA_TRY(dispatch_k4(it.u, fb.dir, it.u_alt, p->field_storage, it.Im, fb.J, fb.gJ, h, d,
+                            wide_w ? ident : tw, p->lr,
                             p->c_lp, parity, su, s));
     FA_CUDA_TRY(stop(FA_K_FUSED_COMPOSE));
     if (wide_w) {
@@ -513,7 +535,8 @@ fa_status fused_autotune_level(FusedBuffers &fb, WsHeader *h, const fa_params *p
             case 1: return dispatch_k2(If, fb.gJ, fb.J, fb.coef, h, fb.g, d, p->window, s);
             case 2: return dispatch_k3(fb.g, m, v, p->state_storage, fb.dir, h, d, g3, ac, 0, s);
             default:
-                return dispatch_k4(u, fb.dir, u_alt, Im, fb.J, fb.gJ, h, d, g4, p->lr, p->c_lp, 0,
+                return dispatch_k4(u, fb.dir, u_alt, p->field_storage, Im, fb.J, fb.gJ, h, d, g4,
+                                   p->lr, p->c_lp, 0,
                                    su, s);
         }
     };

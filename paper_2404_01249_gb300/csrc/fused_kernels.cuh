@@ -1168,17 +1168,22 @@ __global__ void __launch_bounds__(FX *NW, NW >= 16 ? 2 : 1) k_smooth_adam(const 
 // ====================================================================== K4
 // SU: u is staged in shared memory (planes z-1..z+1, halo RG + 1); valid when
 // the step is shorter than one voxel (lr / c_lp < 1).
-template <int RG, int NW, int OPT, bool SU, int NSTG>
+// TU: storage of u (float, or __half for an FP16 u, whose tile rows start on
+// 8-element boundaries so that each TMA box starts on 16 bytes).
+template <int RG, int NW, int OPT, bool SU, int NSTG, class TU = float>
 struct K4S {
     static constexpr int NT = FX * NW, TY = NW * OPT, RX = FX + 2 * RG, RY = TY + 2 * RG;
     static constexpr int XB = halo4(RG), BXW = FX + 2 * XB, COFF = XB - RG;
     static constexpr int NR = BXW * RY, NS = 2 * RG + 1, NOUT = NT * OPT;
     // u planes z-1, z, z+1 in use plus NSTG - 1 in flight, halo RG + 1
-    static constexpr int URX = RX + 2, URY = RY + 2, UXB = halo4(RG + 1), UBXW = FX + 2 * UXB;
+    static constexpr int EU = (int)sizeof(TU);
+    static constexpr int URX = RX + 2, URY = RY + 2,
+                         UXB = EU == 4 ? halo4(RG + 1) : (RG + 1 + 7) / 8 * 8,
+                         UBXW = FX + 2 * UXB;
     static constexpr int UCOFF = UXB - RG - 1, NRU = UBXW * URY, NSU = NSTG + 2;
-    static constexpr size_t st_bytes = al128((size_t)3 * NR * 4);    // d
-    static constexpr size_t ust_bytes = al128((size_t)3 * NRU * 4);  // u
-    static constexpr unsigned tx_plane = 3u * NR * 4, tx_u = 3u * NRU * 4;
+    static constexpr size_t st_bytes = al128((size_t)3 * NR * 4);     // d
+    static constexpr size_t ust_bytes = al128((size_t)3 * NRU * EU);  // u
+    static constexpr unsigned tx_plane = 3u * NR * 4, tx_u = 3u * NRU * EU;
     static constexpr size_t o_st = 0;
     static constexpr size_t o_ust = o_st + st_bytes * NSTG;
     static constexpr size_t o_ring = o_ust + (SU ? ust_bytes * NSU : 0);
@@ -1206,17 +1211,18 @@ __device__ __forceinline__ void compose_position(int pidx, int &ry, int &rx) {
 }
 
 // The body of K4 for the CTA with tile coordinates (bx, by, bz).
-template <int RG, int NW, int OPT, bool SU, int NSTG, bool TMA, class TT>
-__device__ __forceinline__ void compose_body(MapRef maps, const float *__restrict__ u,
+template <int RG, int NW, int OPT, bool SU, int NSTG, bool TMA, class TT, class TU>
+__device__ __forceinline__ void compose_body(MapRef maps, const TU *__restrict__ u,
                                              const float *__restrict__ dir,
-                                             float *__restrict__ uo,
+                                             TU *__restrict__ uo,
                                              const float *__restrict__ Im,
                                              float *__restrict__ Jout, float *__restrict__ gJout,
                                              WsHeader *__restrict__ h, int D, int H, int W, int P,
                                              int TZ,
                                              const TT t, float lr, float c_lp, int parity, int bx,
                                              int by, int bz) {
-    using S = K4S<RG, NW, OPT, SU, NSTG>;
+    static_assert(TMA || sizeof(TU) == 4, "an FP16 u is staged by tile copies only");
+    using S = K4S<RG, NW, OPT, SU, NSTG, TU>;
     constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, BXW = S::BXW, COFF = S::COFF,
                   XB = S::XB, NR = S::NR, NS = S::NS, NOUT = S::NOUT, URX = S::URX,
                   URY = S::URY, UXB = S::UXB, UBXW = S::UBXW, UCOFF = S::UCOFF, NRU = S::NRU,
@@ -1252,7 +1258,7 @@ __device__ __forceinline__ void compose_body(MapRef maps, const float *__restric
     const int zs = z0 - RG, np = zend - z0 + 2 * RG;
     // u plane q lives in u stage (q - (zs - 1)) % NSU
     auto uslot = [&](int q) {
-        return (float *)(smem + S::o_ust + S::ust_bytes * ((q - (zs - 1)) % NSU));
+        return (TU *)(smem + S::o_ust + S::ust_bytes * ((q - (zs - 1)) % NSU));
     };
     // group i: d plane zs + i and u plane zs + i + 1
     auto issue = [&](int i) {
@@ -1266,7 +1272,7 @@ __device__ __forceinline__ void compose_body(MapRef maps, const float *__restric
         } else {
             if (i < np) {
                 rg.template load<3>(stage(s), dir, N, (long long)zp * HW, zp >= 0 && zp < D);
-                if (SU)
+                if constexpr (SU && sizeof(TU) == 4)
                     rgu.template load<3>(uslot(zp + 1), u, N, (long long)(zp + 1) * HW,
                                          zp + 1 >= 0 && zp + 1 < D);
             }
@@ -1284,7 +1290,7 @@ __device__ __forceinline__ void compose_body(MapRef maps, const float *__restric
                 tma4(uslot(zs - 1), maps.b, x0 - UXB, y0 - RG - 1, zs - 1, 0, bar + NSTG);
                 tma4(uslot(zs), maps.b, x0 - UXB, y0 - RG - 1, zs, 0, bar + NSTG);
             }
-        } else {
+        } else if constexpr (sizeof(TU) == 4) {
             rgu.template load<3>(uslot(zs - 1), u, N, (long long)(zs - 1) * HW,
                                  zs - 1 >= 0 && zs - 1 < D);
             rgu.template load<3>(uslot(zs), u, N, (long long)zs * HW, zs >= 0 && zs < D);
@@ -1341,7 +1347,7 @@ __device__ __forceinline__ void compose_body(MapRef maps, const float *__restric
         float Q[OPT][3];
         if (zp >= 0 && zp < D) {
             const float *ds = stage(s);
-            const float *um = uslot(zp - 1), *u0 = uslot(zp), *u1 = uslot(zp + 1);
+            const TU *um = uslot(zp - 1), *u0 = uslot(zp), *u1 = uslot(zp + 1);
             // u' on the RY x RX region (positions spread over all threads),
             // at the plane layout's columns
 #pragma unroll
@@ -1357,13 +1363,13 @@ __device__ __forceinline__ void compose_body(MapRef maps, const float *__restric
                             dx > -1.0f && dx < 1.0f) {
                             const float fz = floorf(dz), fy = floorf(dy), fx = floorf(dx);
                             const float tz = dz - fz, ty = dy - fy, tx2 = dx - fx;
-                            const float *pa = fz < 0.0f ? um : u0;
-                            const float *pb = fz < 0.0f ? u0 : u1;
+                            const TU *pa = fz < 0.0f ? um : u0;
+                            const TU *pb = fz < 0.0f ? u0 : u1;
                             const int b0 = pub[j] + (int)fy * UBXW + (int)fx;
                             // channels 0 and 1 as a packed pair (each component
                             // exactly the scalar fadd / fmaf), channel 2 alone
-                            auto pair = [&](const float *P, int o) {
-                                return make_float2(P[b0 + o], P[NRU + b0 + o]);
+                            auto pair = [&](const TU *P, int o) {
+                                return make_float2(st_load(P[b0 + o]), st_load(P[NRU + b0 + o]));
                             };
                             auto lerp2 = [](float t, float2 lo, float2 hi) {
                                 return __ffma2_rn(make_float2(t, t),
@@ -1374,11 +1380,15 @@ __device__ __forceinline__ void compose_body(MapRef maps, const float *__restric
                             const float2 c10 = lerp2(tx2, pair(pb, 0), pair(pb, 1));
                             const float2 c11 = lerp2(tx2, pair(pb, UBXW), pair(pb, UBXW + 1));
                             const float2 r01 = lerp2(tz, lerp2(ty, c00, c01), lerp2(ty, c10, c11));
-                            const float *A = pa + 2 * NRU + b0, *B = pb + 2 * NRU + b0;
+                            const TU *Ap = pa + 2 * NRU + b0, *Bp = pb + 2 * NRU + b0;
+                            const float A[2] = {st_load(Ap[0]), st_load(Ap[1])},
+                                        A2[2] = {st_load(Ap[UBXW]), st_load(Ap[UBXW + 1])},
+                                        B[2] = {st_load(Bp[0]), st_load(Bp[1])},
+                                        B2[2] = {st_load(Bp[UBXW]), st_load(Bp[UBXW + 1])};
                             const float e00 = fmaf(tx2, A[1] - A[0], A[0]);
-                            const float e01 = fmaf(tx2, A[UBXW + 1] - A[UBXW], A[UBXW]);
+                            const float e01 = fmaf(tx2, A2[1] - A2[0], A2[0]);
                             const float e10 = fmaf(tx2, B[1] - B[0], B[0]);
-                            const float e11 = fmaf(tx2, B[UBXW + 1] - B[UBXW], B[UBXW]);
+                            const float e11 = fmaf(tx2, B2[1] - B2[0], B2[0]);
                             const float e0 = fmaf(ty, e01 - e00, e00);
                             const float e1 = fmaf(ty, e11 - e10, e10);
                             const float2 ab = __fadd2_rn(make_float2(dz, dy), r01);
@@ -1434,10 +1444,13 @@ __device__ __forceinline__ void compose_body(MapRef maps, const float *__restric
                 gauss_z3<RG, NOUT>(ring + o * NT + tid, newest, t, sz);
                 const long long gi = zoff + ou.off[o];
                 const float a = sz[0], b = sz[1], c = sz[2];
-                uo[gi] = a;
-                uo[N + gi] = b;
-                uo[2 * N + gi] = c;
-                tri_issue_p(jp[o], Im, D, H, W, P, zo, y0 + wy + NW * o, x0 + tx, a, b, c);
+                // the stored (for FP16, rounded) u is the one the next steps read
+                const TU sa = st_store<TU>(a), sb = st_store<TU>(b), sc = st_store<TU>(c);
+                uo[gi] = sa;
+                uo[N + gi] = sb;
+                uo[2 * N + gi] = sc;
+                tri_issue_p(jp[o], Im, D, H, W, P, zo, y0 + wy + NW * o, x0 + tx, st_load(sa),
+                            st_load(sb), st_load(sc));
                 jidx[o] = gi;
                 jlive[o] = true;
             }
@@ -1470,11 +1483,11 @@ __device__ __forceinline__ void compose_body(MapRef maps, const float *__restric
     }
 }
 
-template <int RG, int NW, int OPT, bool SU, int NSTG, bool TMA>
+template <int RG, int NW, int OPT, bool SU, int NSTG, bool TMA, class TU = float>
 __global__ void __launch_bounds__(FX *NW, NW >= 16 ? 2 : 1) k_compose(const __grid_constant__ Maps maps,
-                                                    const float *__restrict__ u,
+                                                    const TU *__restrict__ u,
                                                     const float *__restrict__ dir,
-                                                    float *__restrict__ uo,
+                                                    TU *__restrict__ uo,
                                                     const float *__restrict__ Im,
                                                     float *__restrict__ Jout,
                                                     float *__restrict__ gJout,

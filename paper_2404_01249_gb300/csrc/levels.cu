@@ -20,9 +20,10 @@ struct Scale3 {
 };
 
 // Rows of Ps (source) and Pd (destination) elements; only x < W is read or
-// written.
-__global__ void __launch_bounds__(256) k_resample(const float *__restrict__ src, int Ds, int Hs,
-                                                  int Ws, int Ps, float *__restrict__ dst, int Dd,
+// written.  TS, TD: FP32 or FP16 (a 16-bit destination is rounded to nearest).
+template <class TS, class TD>
+__global__ void __launch_bounds__(256) k_resample(const TS *__restrict__ src, int Ds, int Hs,
+                                                  int Ws, int Ps, TD *__restrict__ dst, int Dd,
                                                   int Hd, int Wd, int Pd, int C, Scale3 sc) {
     int x = blockIdx.x * 32 + threadIdx.x;
     int y = blockIdx.y * 8 + threadIdx.y;
@@ -35,12 +36,13 @@ __global__ void __launch_bounds__(256) k_resample(const float *__restrict__ src,
     for (int c = 0; c < C; ++c) {
         float v = tri_sample_p<false>(src + c * Ns, Ds, Hs, Ws, Ps, 0, 0, 0, cz, cy, cx, gz, gy,
                                       gx);
-        dst[c * Nd + i] = v * sc.s[c];
+        dst[c * Nd + i] = st_store<TD>(v * sc.s[c]);
     }
 }
 
-cudaError_t launch_resample(const float *src, Dims ds, float *dst, Dims dd, int C,
-                            const float *scale3, cudaStream_t s) {
+template <class TS, class TD>
+static cudaError_t launch_resample_t(const TS *src, Dims ds, TD *dst, Dims dd, int C,
+                                     const float *scale3, cudaStream_t s) {
     Scale3 sc;
     for (int c = 0; c < 3; ++c) sc.s[c] = scale3 ? scale3[c] : 1.0f;
     VoxGrid g(dd.D, dd.H, dd.W);
@@ -48,6 +50,22 @@ cudaError_t launch_resample(const float *src, Dims ds, float *dst, Dims dd, int 
                                           dd.pitch(), C, sc);
     note_launch();
     return cudaGetLastError();
+}
+
+cudaError_t launch_resample(const float *src, Dims ds, float *dst, Dims dd, int C,
+                            const float *scale3, cudaStream_t s) {
+    return launch_resample_t(src, ds, dst, dd, C, scale3, s);
+}
+
+cudaError_t launch_resample_field(const void *src, int sfield, Dims ds, void *dst, int dfield,
+                                  Dims dd, int C, const float *scale3, cudaStream_t s) {
+    if (sfield == FA_F16 && dfield == FA_F16)
+        return launch_resample_t((const __half *)src, ds, (__half *)dst, dd, C, scale3, s);
+    if (sfield == FA_F16)
+        return launch_resample_t((const __half *)src, ds, (float *)dst, dd, C, scale3, s);
+    if (dfield == FA_F16)
+        return launch_resample_t((const float *)src, ds, (__half *)dst, dd, C, scale3, s);
+    return launch_resample_t((const float *)src, ds, (float *)dst, dd, C, scale3, s);
 }
 
 int level_size(int n, int s) {

@@ -31,6 +31,9 @@ constexpr float kMaxSigma = 10.0f;
 // ---- warp (warp.cu)
 cudaError_t launch_warp(const float *Im, const float *u, float *J, float *grad, Dims d,
                         cudaStream_t s);
+// The same for a displacement stored as `field` (FA_F32 or FA_F16).
+cudaError_t launch_warp_field(const float *Im, const void *u, int field, float *J, float *grad,
+                              Dims d, cudaStream_t s);
 // uo = delta + u o (id + delta) (uo must not be u).
 cudaError_t launch_compose_fields(const float *u, const float *delta, float *uo, Dims d,
                                   cudaStream_t s);
@@ -141,6 +144,9 @@ cudaError_t launch_compose(const float *u_in, const float *d, float *u_out, Dims
 // dst channel c = scale[c] * trilinear align-corners resample of src channel c
 cudaError_t launch_resample(const float *src, Dims ds, float *dst, Dims dd, int C,
                             const float *scale3, cudaStream_t s);
+// The same between fields stored as sfield and dfield (FA_F32 or FA_F16).
+cudaError_t launch_resample_field(const void *src, int sfield, Dims ds, void *dst, int dfield,
+                                  Dims dd, int C, const float *scale3, cudaStream_t s);
 
 int level_size(int n, int s);
 void handoff_scales(Dims c, Dims f, int power, float out[3]);

@@ -15,6 +15,15 @@
 
 namespace fa {
 
+// A 16-bit u is kept where the four fused kernels run every step of every
+// level (their tile copies read it; the per-op kernels keep u in FP32).
+static bool field16_ok(const fa_params *p) {
+    if (p->mode != FA_MODE_FUSED || p->loss != FA_LOSS_LNCC || p->use_jac) return false;
+    GaussTaps tg, tw;
+    if (!make_gauss_taps(p->sigma_grad, &tg) || !make_gauss_taps(p->sigma_warp, &tw)) return false;
+    return tg.R <= kMaxFusedRadius && tw.R <= kMaxFusedRadius;
+}
+
 static fa_status check_params(const fa_params *p) {
     if (!p) {
         set_error("params are NULL");
@@ -71,15 +80,27 @@ static fa_status check_params(const fa_params *p) {
         set_error("state_storage must be FA_F32 or FA_BF16 (got %d)", (int)p->state_storage);
         return FA_ERR_UNSUPPORTED;
     }
+    if (p->field_storage != FA_F32 && p->field_storage != FA_F16) {
+        set_error("field_storage must be FA_F32 or FA_F16 (got %d)", (int)p->field_storage);
+        return FA_ERR_UNSUPPORTED;
+    }
+    if (p->field_storage == FA_F16 && !field16_ok(p)) {
+        set_error("field_storage FA_F16 needs FA_MODE_FUSED, the LNCC loss, use_jac = 0 and "
+                  "Gaussian radii up to %d", kMaxFusedRadius);
+        return FA_ERR_UNSUPPORTED;
+    }
     return check_adam_params(p, "fa_register", true);
 }
 
 // Row pitch of a level's buffers: the width rounded up to a multiple of 4
-// where the four fused LNCC kernels run every step of the level, so that
-// they take TMA tiles at any width; 0 (the width itself) elsewhere.  The
-// padding is never read as data: TMA tiles describe the D x H x W grid and
-// fill beyond it with zeros, and every other access checks x < W.
+// (8 with an FP16 u) where the four fused LNCC kernels run every step of the
+// level, so that they take TMA tiles at any width; 0 (the width itself)
+// elsewhere.  The padding is never read as data: TMA tiles describe the
+// D x H x W grid and fill beyond it with zeros, and every other access
+// checks x < W.
 static int level_pitch(const fa_params *p, Dims d) {
+    // FP16 u: rows of a multiple of 8 elements (16 bytes of FP16)
+    if (p->field_storage == FA_F16) return d.W % 8 == 0 ? 0 : (d.W + 7) & ~7;
     if (p->loss != FA_LOSS_LNCC || p->use_jac || d.W % 4 == 0) return 0;
     if (p->mode == FA_MODE_PLAIN || (p->mode == FA_MODE_PERSISTENT && persistent_eligible(p, d)))
         return 0;
@@ -318,7 +339,8 @@ static fa_status level_begin(Plan &P, const fa_params *p, int l, const float *u_
             float sc[3];
             handoff_scales(P.full, d, 1, sc);
             if (d.pitch() != d.W) FA_CUDA_TRY(cudaMemsetAsync(P.u[*cur], 0, b, s));
-            FA_CUDA_TRY(launch_resample(u_init, P.full, P.u[*cur], d, 3, sc, s));
+            FA_CUDA_TRY(launch_resample_field(u_init, FA_F32, P.full, P.u[*cur],
+                                              p->field_storage, d, 3, sc, s));
         } else {
             FA_CUDA_TRY(cudaMemsetAsync(P.u[*cur], 0, b, s));
         }
@@ -332,7 +354,8 @@ static fa_status level_begin(Plan &P, const fa_params *p, int l, const float *u_
         handoff_scales(c, d, -1, sm);
         handoff_scales(c, d, -2, sv);
         int nx = *cur ^ 1;
-        FA_CUDA_TRY(launch_resample(P.u[*cur], c, P.u[nx], d, 3, su, s));
+        FA_CUDA_TRY(launch_resample_field(P.u[*cur], p->field_storage, c, P.u[nx],
+                                          p->field_storage, d, 3, su, s));
         if (p->state_storage == FA_F32) {
             FA_CUDA_TRY(launch_resample((const float *)P.m[*cur], c, (float *)P.m[nx], d, 3, sm, s));
             FA_CUDA_TRY(launch_resample((const float *)P.v[*cur], c, (float *)P.v[nx], d, 3, sv, s));
@@ -364,6 +387,11 @@ static fa_status registration_end(Plan &P, const fa_params *p, const float *If, 
     const int L = p->n_levels - 1;
     FA_TRY(final_loss(P, p, L, If, Im, u, final_loss_dev, s));
     const Dims d = P.lvl[L];
+    if (p->field_storage == FA_F16) {  // widened (exactly) into the caller's dense FP32 field
+        FA_CUDA_TRY(launch_resample_field(u, FA_F16, d, u_out->data, FA_F32,
+                                          Dims{d.D, d.H, d.W}, 3, nullptr, s));
+        return FA_OK;
+    }
     FA_CUDA_TRY(cudaMemcpy2DAsync(u_out->data, sizeof(float) * d.W, u, sizeof(float) * d.pitch(),
                                   sizeof(float) * d.W, (size_t)3 * d.D * d.H,
                                   cudaMemcpyDeviceToDevice, s));
@@ -561,7 +589,7 @@ std::string graph_key(int dev, const fa_vol *fixed, const fa_vol *moving, const 
     vol(fixed);
     vol(moving);
     vol(u_out);
-    static_assert(sizeof(fa_params) == 33 * 4, "fa_params holds 33 four-byte fields, no padding");
+    static_assert(sizeof(fa_params) == 34 * 4, "fa_params holds 34 four-byte fields, no padding");
     add(p, sizeof(*p));
     add(&u_init, sizeof(u_init));
     add(&final_loss_dev, sizeof(final_loss_dev));
@@ -726,6 +754,10 @@ fa_status lockstep_check(int n, const LockstepArgs *a) {
         if ((p->mode != FA_MODE_FUSED && p->mode != FA_MODE_PERSISTENT) ||
             p->loss != FA_LOSS_LNCC || p->use_jac) {
             set_error("lockstep: job %d: needs the fused LNCC path without use_jac", k);
+            return FA_ERR_UNSUPPORTED;
+        }
+        if (p->field_storage != FA_F32) {
+            set_error("lockstep: job %d: keeps u in FP32 (field_storage must be FA_F32)", k);
             return FA_ERR_UNSUPPORTED;
         }
         bool same = p->n_levels == p0->n_levels && p->window == p0->window &&

@@ -7,9 +7,10 @@
 namespace fa {
 
 // Every buffer has rows of P (>= W) elements; only x < W is read or written.
-template <bool GRAD>
+// u: FP32 or FP16 values.
+template <bool GRAD, class TU>
 __global__ void __launch_bounds__(256) k_warp(const float *__restrict__ Im,
-                                              const float *__restrict__ u, float *__restrict__ J,
+                                              const TU *__restrict__ u, float *__restrict__ J,
                                               float *__restrict__ grad, int D, int H, int W,
                                               int P) {
     int x = blockIdx.x * 32 + threadIdx.x;
@@ -19,8 +20,8 @@ __global__ void __launch_bounds__(256) k_warp(const float *__restrict__ Im,
     long long N = (long long)D * H * P;
     long long i = ((long long)z * H + y) * P + x;
     float gz, gy, gx;
-    float v = tri_sample_p<GRAD>(Im, D, H, W, P, z, y, x, __ldg(u + i), __ldg(u + N + i),
-                                 __ldg(u + 2 * N + i), gz, gy, gx);
+    float v = tri_sample_p<GRAD>(Im, D, H, W, P, z, y, x, ld_field(u + i), ld_field(u + N + i),
+                                 ld_field(u + 2 * N + i), gz, gy, gx);
     J[i] = v;
     if (GRAD) {
         grad[i] = gz;
@@ -29,18 +30,27 @@ __global__ void __launch_bounds__(256) k_warp(const float *__restrict__ Im,
     }
 }
 
+template <class TU>
+static cudaError_t launch_warp_t(const float *Im, const TU *u, float *J, float *grad, Dims d,
+                                 cudaStream_t s) {
+    VoxGrid g(d.D, d.H, d.W);
+    if (grad)
+        k_warp<true><<<g.grid, g.block, 0, s>>>(Im, u, J, grad, d.D, d.H, d.W, d.pitch());
+    else
+        k_warp<false><<<g.grid, g.block, 0, s>>>(Im, u, J, nullptr, d.D, d.H, d.W, d.pitch());
+    note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_warp(const float *Im, const float *u, float *J, float *grad, Dims d,
                         cudaStream_t s) {
-    VoxGrid g(d.D, d.H, d.W);
-    if (grad) {
-        k_warp<true><<<g.grid, g.block, 0, s>>>(Im, u, J, grad, d.D, d.H, d.W, d.pitch());
-        note_launch();
-    }
-    else {
-        k_warp<false><<<g.grid, g.block, 0, s>>>(Im, u, J, nullptr, d.D, d.H, d.W, d.pitch());
-        note_launch();
-    }
-    return cudaGetLastError();
+    return launch_warp_t(Im, u, J, grad, d, s);
+}
+
+cudaError_t launch_warp_field(const float *Im, const void *u, int field, float *J, float *grad,
+                              Dims d, cudaStream_t s) {
+    if (field == FA_F16) return launch_warp_t(Im, (const __half *)u, J, grad, d, s);
+    return launch_warp_t(Im, (const float *)u, J, grad, d, s);
 }
 
 

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_PKG, "_build", "libfa.so")
 
 FA_OK = 0
 FA_ERR_INVALID = 1
-FA_ERR_NONFINITE, FA_ERR_TIMEOUT = 5, 6
+FA_ERR_NONFINITE, FA_ERR_TIMEOUT, FA_ERR_UNSUPPORTED = 5, 6, 7
 STATUS_NAMES = {0: "FA_OK", 1: "FA_ERR_INVALID", 2: "FA_ERR_SHAPE", 3: "FA_ERR_DTYPE",
                 4: "FA_ERR_CUDA", 5: "FA_ERR_NONFINITE", 6: "FA_ERR_TIMEOUT",
                 7: "FA_ERR_UNSUPPORTED", 8: "FA_ERR_WORKSPACE"}
@@ -73,7 +73,8 @@ class Params(ctypes.Structure):
                 ("cc_eps", ctypes.c_float), ("c_lp", ctypes.c_float), ("mode", ctypes.c_int32),
                 ("storage", ctypes.c_int32), ("graph", ctypes.c_int32),
                 ("use_jac", ctypes.c_int32), ("mi_bins", ctypes.c_int32),
-                ("state_storage", ctypes.c_int32)]
+                ("state_storage", ctypes.c_int32),
+                ("field_storage", ctypes.c_int32)]
 
 
 class KernelTimer(ctypes.Structure):
@@ -222,6 +223,7 @@ class RegParams:
     use_jac: bool = False  # steepest Eulerian direction J(phi)^T dL/dphi
     mi_bins: int = 32      # histogram bins of the MI loss
     state: str = "f32"     # storage of the Adam moments m, nu: "f32" or "bf16"
+    field: str = "f32"     # storage of the displacement u between iterations: "f32" or "f16"
 
     def to_c(self) -> Params:
         p = Params()
@@ -244,6 +246,7 @@ class RegParams:
         p.graph = 1 if self.graph else 0
         p.use_jac = 1 if self.use_jac else 0
         p.state_storage = {"f32": FA_F32, "bf16": FA_BF16, "f16": FA_F16}[self.state]
+        p.field_storage = {"f32": FA_F32, "bf16": FA_BF16, "f16": FA_F16}[self.field]
         return p
 
 
