@@ -520,8 +520,8 @@ VARIANT_BYTES = {
     "use_jac": PATH_BYTES,
     "affine": 8,              # I_f, I_m (12 parameters)
     "rigid": 8,
-    # BF16 storage: I_f, I_m and m, nu in 16 bits, u in 32
-    "microscopy": 2 + 2 + 12 + 6 + 6 + 12 + 6 + 6,
+    # 16-bit storage: I_f, I_m, m, nu in BF16 and u in FP16
+    "microscopy": 2 + 2 + 6 + 6 + 6 + 6 + 6 + 6,
 }
 # the expansion-microscopy-shaped pair: 512 x 512 in-plane, 256 planes
 MICROSCOPY = dict(shape=(256, 512, 512), scales=(8, 4, 2, 1), iters=(200, 200, 100, 50),
@@ -587,7 +587,7 @@ def run_variant(args):
         cfg.update(base, squarings=SVF_STEPS, loss="lncc")
     elif w == "microscopy":
         import ctypes
-        P = fa.RegParams(**base, state="bf16")
+        P = fa.RegParams(**base, state="bf16", field="f16")
         pc = P.to_c()
         pc.storage = fa.FA_BF16
         ws = fa.workspace(fa.load().fa_register_workspace_size(*shape, ctypes.byref(pc)), dev)
@@ -597,7 +597,7 @@ def run_variant(args):
         uo = torch.empty((3,) + tuple(fa.level_size(a, s_last) for a in shape), device=dev)
         lo = torch.empty((), device=dev)
         call = lambda: fa.fa_register(fixed, moving, P, ws=ws, sync=False, u_out=uo, loss_out=lo)["loss"]  # noqa
-        cfg.update(base, storage="bf16 images and Adam moments, fp32 displacement and arithmetic",
+        cfg.update(base, storage="bf16 images and Adam moments, fp16 displacement, fp32 arithmetic",
                    mode="fused", cells=int(round(1e-3 * np.prod(shape))))
     elif w in ("mi", "use_jac"):
         P = fa.RegParams(**base, loss="mi" if w == "mi" else "lncc", use_jac=(w == "use_jac"))

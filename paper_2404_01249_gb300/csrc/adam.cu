@@ -103,7 +103,9 @@ __global__ void __launch_bounds__(256) k_compose(const float *__restrict__ u,
     float gz, gy, gx;
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
-        float s = tri_sample<false>(u + ch * N, D, H, W, z, y, x, dz, dy, dx, gz, gy, gx);
+        TriPending q;  // the compose's cell (the same as the fused schedule's)
+        tri_issue_step(q, u + ch * N, D, H, W, W, z, y, x, dz, dy, dx);
+        float s = tri_finish<false>(q, gz, gy, gx);
         float dc = ch == 0 ? dz : (ch == 1 ? dy : dx);
         uo[ch * N + i] = dc + s;
     }

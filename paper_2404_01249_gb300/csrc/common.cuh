@@ -192,6 +192,38 @@ __device__ __forceinline__ void tri_issue_p(TriPending &p, const T *__restrict__
     if (z1 && y1 && x1) p.c111 = ld_field(q1 + P + 1);
 }
 
+// The compose's sample u(x + delta) at a grid voxel (z, y, x): for a step
+// shorter than one voxel on every axis the cell's corners are the voxel itself
+// and its neighbours on the side of each component's sign, with the exact
+// weights |delta| (so u is sampled exactly when delta is 0 on an axis); longer
+// steps take tri_issue_p's cell.  tri_finish completes either.
+template <class T>
+__device__ __forceinline__ void tri_issue_step(TriPending &p, const T *__restrict__ v, int D,
+                                               int H, int W, int P, int z, int y, int x,
+                                               float uz, float uy, float ux) {
+    if (!(fabsf(uz) < 1.0f && fabsf(uy) < 1.0f && fabsf(ux) < 1.0f)) {
+        tri_issue_p(p, v, D, H, W, P, z, y, x, uz, uy, ux);
+        return;
+    }
+    p.tz = fabsf(uz);
+    p.ty = fabsf(uy);
+    p.tx = fabsf(ux);
+    const int sz = uz < 0.0f ? -1 : 1, sy = uy < 0.0f ? -1 : 1, sx = ux < 0.0f ? -1 : 1;
+    const bool zo = z + sz >= 0 && z + sz < D, yo = y + sy >= 0 && y + sy < H,
+               xo = x + sx >= 0 && x + sx < W;
+    // 32-bit offsets: buffers hold fewer than 2^31 elements
+    const T *q0 = v + (z * H + y) * P + x, *q1 = q0 + sz * H * P;
+    const int oy = sy * P;
+    p.c000 = ld_field(q0);
+    p.c001 = xo ? ld_field(q0 + sx) : 0.0f;
+    p.c010 = yo ? ld_field(q0 + oy) : 0.0f;
+    p.c011 = yo && xo ? ld_field(q0 + oy + sx) : 0.0f;
+    p.c100 = zo ? ld_field(q1) : 0.0f;
+    p.c101 = zo && xo ? ld_field(q1 + sx) : 0.0f;
+    p.c110 = zo && yo ? ld_field(q1 + oy) : 0.0f;
+    p.c111 = zo && yo && xo ? ld_field(q1 + oy + sx) : 0.0f;
+}
+
 __device__ __forceinline__ void tri_issue(TriPending &p, const float *__restrict__ v, int D,
                                           int H, int W, int z, int y, int x, float uz, float uy,
                                           float ux) {

@@ -91,6 +91,11 @@ __device__ __forceinline__ void mbar_init_fence() {
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
+// Orders this thread's shared-memory stores before later tile copies into the
+// same bytes (a buffer refilled by TMA after the threads wrote to it).
+__device__ __forceinline__ void proxy_fence_async() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
 // The arrival of the one expected thread, announcing `bytes` of copies.
 __device__ __forceinline__ void mbar_expect(unsigned long long *b, unsigned bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(su32(b)),
@@ -1168,8 +1173,11 @@ __global__ void __launch_bounds__(FX *NW, NW >= 16 ? 2 : 1) k_smooth_adam(const 
 // ====================================================================== K4
 // SU: u is staged in shared memory (planes z-1..z+1, halo RG + 1); valid when
 // the step is shorter than one voxel (lr / c_lp < 1).
-// TU: storage of u (float, or __half for an FP16 u, whose tile rows start on
-// 8-element boundaries so that each TMA box starts on 16 bytes).
+// TU: storage of u (float, or __half for an FP16 u).
+// The u tile's rows are 48 (or 64) elements long: an FP32 row is 16 banks
+// (mod 32) long, so that the compose's reads of a neighbour row on either side
+// of a lane's own voxel fall in the same bank, and an FP16 tile row starts on
+// 16 bytes.  Its planes are whole multiples of 32 banks apart.
 template <int RG, int NW, int OPT, bool SU, int NSTG, class TU = float>
 struct K4S {
     static constexpr int NT = FX * NW, TY = NW * OPT, RX = FX + 2 * RG, RY = TY + 2 * RG;
@@ -1177,20 +1185,20 @@ struct K4S {
     static constexpr int NR = BXW * RY, NS = 2 * RG + 1, NOUT = NT * OPT;
     // u planes z-1, z, z+1 in use plus NSTG - 1 in flight, halo RG + 1
     static constexpr int EU = (int)sizeof(TU);
-    static constexpr int URX = RX + 2, URY = RY + 2,
-                         UXB = EU == 4 ? halo4(RG + 1) : (RG + 1 + 7) / 8 * 8,
+    static constexpr int URX = RX + 2, URY = RY + 2, UXB = (RG + 1 + 7) / 8 * 8,
                          UBXW = FX + 2 * UXB;
     static constexpr int UCOFF = UXB - RG - 1, NRU = UBXW * URY, NSU = NSTG + 2;
-    static constexpr size_t st_bytes = al128((size_t)3 * NR * 4);     // d
+    static constexpr int NP = RY * RX, NJP = (NP + NT - 1) / NT;  // compose positions
+    static constexpr size_t st_bytes = al128((size_t)3 * NR * 4);     // d, then u' in place
     static constexpr size_t ust_bytes = al128((size_t)3 * NRU * EU);  // u
     static constexpr unsigned tx_plane = 3u * NR * 4, tx_u = 3u * NRU * EU;
     static constexpr size_t o_st = 0;
     static constexpr size_t o_ust = o_st + st_bytes * NSTG;
     static constexpr size_t o_ring = o_ust + (SU ? ust_bytes * NSU : 0);
     static constexpr size_t o_xb = o_ring + (size_t)NS * 3 * NOUT * 4;
-    static constexpr size_t o_up = o_xb + (size_t)3 * RY * FX * 4;
-    static constexpr size_t o_bar = al128(o_up + (size_t)3 * NR * 4);
+    static constexpr size_t o_bar = al128(o_xb + (size_t)3 * RY * FX * 4);
     static constexpr size_t bytes = o_bar + 8 * (NSTG + 1);
+    static_assert(EU == 2 || UBXW % 32 == 16 || UBXW % 32 == 0, "u rows of 16 or 32 banks");
 };
 
 // Compose position of slot pidx in the RY x RX region (RX = 32 + 2 RG): the
@@ -1226,13 +1234,12 @@ __device__ __forceinline__ void compose_body(MapRef maps, const TU *__restrict__
     constexpr int NT = S::NT, TY = S::TY, RX = S::RX, RY = S::RY, BXW = S::BXW, COFF = S::COFF,
                   XB = S::XB, NR = S::NR, NS = S::NS, NOUT = S::NOUT, URX = S::URX,
                   URY = S::URY, UXB = S::UXB, UBXW = S::UBXW, UCOFF = S::UCOFF, NRU = S::NRU,
-                  NSU = S::NSU;
+                  NSU = S::NSU, NP = S::NP, NJP = S::NJP;
     using G = Region<RY, RX, NW, BXW, COFF>;
     using GU = Region<URY, URX, NW, UBXW, UCOFF>;
     extern __shared__ __align__(128) unsigned char smem[];
     float *ring = (float *)(smem + S::o_ring);
     float *xb = (float *)(smem + S::o_xb);
-    float *up = (float *)(smem + S::o_up);
     unsigned long long *bar = (unsigned long long *)(smem + S::o_bar);
     __shared__ int flag;
     auto stage = [&](int s) { return (float *)(smem + S::o_st + S::st_bytes * s); };
@@ -1315,9 +1322,7 @@ __device__ __forceinline__ void compose_body(MapRef maps, const TU *__restrict__
     for (int o = 0; o < OPT; ++o) jlive[o] = false;
 
     // this thread's compose positions (fixed for every plane): plane-layout
-    // index (-1: none), inside the grid, and the u stage index of the cell
-    // (0, 0, 0) corner before the step's floor is added
-    constexpr int NP = RY * RX, NJP = (NP + NT - 1) / NT;
+    // index (-1: none), inside the grid, and the u stage index of the position
     int pk[NJP], pub[NJP];
     bool pin[NJP];
 #pragma unroll
@@ -1346,7 +1351,9 @@ __device__ __forceinline__ void compose_body(MapRef maps, const TU *__restrict__
         }
         float Q[OPT][3];
         if (zp >= 0 && zp < D) {
-            const float *ds = stage(s);
+            // u' replaces d in the stage, position by position (each thread
+            // reads its positions' d before it writes them)
+            float *ds = stage(s);
             const TU *um = uslot(zp - 1), *u0 = uslot(zp), *u1 = uslot(zp + 1);
             // u' on the RY x RX region (positions spread over all threads),
             // at the plane layout's columns
@@ -1361,11 +1368,13 @@ __device__ __forceinline__ void compose_body(MapRef maps, const TU *__restrict__
                         // cell corners lie within one voxel: planes zp-1..zp+1
                         if (dz > -1.0f && dz < 1.0f && dy > -1.0f && dy < 1.0f &&
                             dx > -1.0f && dx < 1.0f) {
-                            const float fz = floorf(dz), fy = floorf(dy), fx = floorf(dx);
-                            const float tz = dz - fz, ty = dy - fy, tx2 = dx - fx;
-                            const TU *pa = fz < 0.0f ? um : u0;
-                            const TU *pb = fz < 0.0f ? u0 : u1;
-                            const int b0 = pub[j] + (int)fy * UBXW + (int)fx;
+                            // the corners are this voxel and its neighbours on
+                            // the side of the step's sign, weighted by |delta|
+                            // (the cell and weights of tri_issue_step)
+                            const float tz = fabsf(dz), ty = fabsf(dy), tx2 = fabsf(dx);
+                            const TU *pa = u0, *pb = dz < 0.0f ? um : u1;
+                            const int b0 = pub[j], oy = dy < 0.0f ? -UBXW : UBXW,
+                                      ox = dx < 0.0f ? -1 : 1;
                             // channels 0 and 1 as a packed pair (each component
                             // exactly the scalar fadd / fmaf), channel 2 alone
                             auto pair = [&](const TU *P, int o) {
@@ -1375,16 +1384,16 @@ __device__ __forceinline__ void compose_body(MapRef maps, const TU *__restrict__
                                 return __ffma2_rn(make_float2(t, t),
                                                   __fadd2_rn(hi, make_float2(-lo.x, -lo.y)), lo);
                             };
-                            const float2 c00 = lerp2(tx2, pair(pa, 0), pair(pa, 1));
-                            const float2 c01 = lerp2(tx2, pair(pa, UBXW), pair(pa, UBXW + 1));
-                            const float2 c10 = lerp2(tx2, pair(pb, 0), pair(pb, 1));
-                            const float2 c11 = lerp2(tx2, pair(pb, UBXW), pair(pb, UBXW + 1));
+                            const float2 c00 = lerp2(tx2, pair(pa, 0), pair(pa, ox));
+                            const float2 c01 = lerp2(tx2, pair(pa, oy), pair(pa, oy + ox));
+                            const float2 c10 = lerp2(tx2, pair(pb, 0), pair(pb, ox));
+                            const float2 c11 = lerp2(tx2, pair(pb, oy), pair(pb, oy + ox));
                             const float2 r01 = lerp2(tz, lerp2(ty, c00, c01), lerp2(ty, c10, c11));
                             const TU *Ap = pa + 2 * NRU + b0, *Bp = pb + 2 * NRU + b0;
-                            const float A[2] = {st_load(Ap[0]), st_load(Ap[1])},
-                                        A2[2] = {st_load(Ap[UBXW]), st_load(Ap[UBXW + 1])},
-                                        B[2] = {st_load(Bp[0]), st_load(Bp[1])},
-                                        B2[2] = {st_load(Bp[UBXW]), st_load(Bp[UBXW + 1])};
+                            const float A[2] = {st_load(Ap[0]), st_load(Ap[ox])},
+                                        A2[2] = {st_load(Ap[oy]), st_load(Ap[oy + ox])},
+                                        B[2] = {st_load(Bp[0]), st_load(Bp[ox])},
+                                        B2[2] = {st_load(Bp[oy]), st_load(Bp[oy + ox])};
                             const float e00 = fmaf(tx2, A[1] - A[0], A[0]);
                             const float e01 = fmaf(tx2, A2[1] - A2[0], A2[0]);
                             const float e10 = fmaf(tx2, B[1] - B[0], B[0]);
@@ -1403,20 +1412,22 @@ __device__ __forceinline__ void compose_body(MapRef maps, const TU *__restrict__
                         compose_position<RY, RX>(tid + j * NT, ry, rx);
                         const int y = y0 - RG + ry, x = x0 - RG + rx;
                         float gz, gy, gx;
-                        a = dz + tri_sample_p<false>(u, D, H, W, P, zp, y, x, dz, dy, dx, gz, gy,
-                                                     gx);
-                        b = dy + tri_sample_p<false>(u + N, D, H, W, P, zp, y, x, dz, dy, dx, gz,
-                                                     gy, gx);
-                        c = dx + tri_sample_p<false>(u + 2 * N, D, H, W, P, zp, y, x, dz, dy, dx,
-                                                     gz, gy, gx);
+                        TriPending q;
+                        tri_issue_step(q, u, D, H, W, P, zp, y, x, dz, dy, dx);
+                        a = dz + tri_finish<false>(q, gz, gy, gx);
+                        tri_issue_step(q, u + N, D, H, W, P, zp, y, x, dz, dy, dx);
+                        b = dy + tri_finish<false>(q, gz, gy, gx);
+                        tri_issue_step(q, u + 2 * N, D, H, W, P, zp, y, x, dz, dy, dx);
+                        c = dx + tri_finish<false>(q, gz, gy, gx);
                     }
                 }
-                up[k] = a;
-                up[NR + k] = b;
-                up[2 * NR + k] = c;
+                ds[k] = a;
+                ds[NR + k] = b;
+                ds[2 * NR + k] = c;
             }
+            if (TMA) proxy_fence_async();  // the stage is refilled by a tile copy later
             __syncthreads();
-            gauss_x4<RG, 3, RY, BXW, COFF, NT>(up, xb, t, tid);
+            gauss_x4<RG, 3, RY, BXW, COFF, NT>(ds, xb, t, tid);
             __syncthreads();
             gauss_y3<RG, RY, NW, OPT>(xb, t, wy, tx, Q);
         } else {

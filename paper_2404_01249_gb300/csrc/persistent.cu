@@ -196,6 +196,35 @@ __device__ __forceinline__ void tri_issue_cg(TriPending &p, const float *v, int 
     if (z1 && y1 && x1) p.c111 = __ldcg(q1 + W + 1);
 }
 
+// The compose's sample of a field written inside this launch: the cell and
+// weights of tri_issue_step (this voxel and its neighbours on the side of the
+// step's sign for a step shorter than one voxel, tri_issue_cg's cell
+// otherwise), L2 loads.
+__device__ __forceinline__ void tri_issue_step_cg(TriPending &p, const float *v, int D, int H,
+                                                  int W, int z, int y, int x, float uz, float uy,
+                                                  float ux) {
+    if (!(fabsf(uz) < 1.0f && fabsf(uy) < 1.0f && fabsf(ux) < 1.0f)) {
+        tri_issue_cg(p, v, D, H, W, z, y, x, uz, uy, ux);
+        return;
+    }
+    p.tz = fabsf(uz);
+    p.ty = fabsf(uy);
+    p.tx = fabsf(ux);
+    const int sz = uz < 0.0f ? -1 : 1, sy = uy < 0.0f ? -1 : 1, sx = ux < 0.0f ? -1 : 1;
+    const bool zo = z + sz >= 0 && z + sz < D, yo = y + sy >= 0 && y + sy < H,
+               xo = x + sx >= 0 && x + sx < W;
+    const float *q0 = v + (z * H + y) * W + x, *q1 = q0 + sz * H * W;
+    const int oy = sy * W;
+    p.c000 = __ldcg(q0);
+    p.c001 = xo ? __ldcg(q0 + sx) : 0.0f;
+    p.c010 = yo ? __ldcg(q0 + oy) : 0.0f;
+    p.c011 = yo && xo ? __ldcg(q0 + oy + sx) : 0.0f;
+    p.c100 = zo ? __ldcg(q1) : 0.0f;
+    p.c101 = zo && xo ? __ldcg(q1 + sx) : 0.0f;
+    p.c110 = zo && yo ? __ldcg(q1 + oy) : 0.0f;
+    p.c111 = zo && yo && xo ? __ldcg(q1 + oy + sx) : 0.0f;
+}
+
 // Sliding window sums of 4 adjacent outputs from 4 + 2R values.
 template <int R, class T>
 __device__ __forceinline__ void slide4(const T *p, T s[4]) {
@@ -560,9 +589,9 @@ __global__ void __launch_bounds__(PT, 3) k_level_persistent(const __grid_constan
                         const float dx = -e * __ldcg(a.dir + 2 * N + vox);
                         float gz, gy, gx;
                         TriPending t0, t1, t2;
-                        tri_issue_cg(t0, u, D, H, W, z, y, x, dz, dy, dx);
-                        tri_issue_cg(t1, u + N, D, H, W, z, y, x, dz, dy, dx);
-                        tri_issue_cg(t2, u + 2 * N, D, H, W, z, y, x, dz, dy, dx);
+                        tri_issue_step_cg(t0, u, D, H, W, z, y, x, dz, dy, dx);
+                        tri_issue_step_cg(t1, u + N, D, H, W, z, y, x, dz, dy, dx);
+                        tri_issue_step_cg(t2, u + 2 * N, D, H, W, z, y, x, dz, dy, dx);
                         p0 = dz + tri_finish<false>(t0, gz, gy, gx);
                         p1 = dy + tri_finish<false>(t1, gz, gy, gx);
                         p2 = dx + tri_finish<false>(t2, gz, gy, gx);
