@@ -124,21 +124,30 @@ def test_gauss(fa, orc, sigma):
     assert rel(xin, orc.gauss_smooth(x, sigma)) < TOL
 
 
-def test_radam_step(fa, orc):
+@pytest.mark.parametrize("lr", [0.5, 20.0])
+def test_radam_step(fa, orc, lr):
+    """Adam, step scale and compose against the oracle.  lr 0.5 keeps every
+    step below half a voxel (the compose's sign-side cells); lr 20 allows 10
+    voxels, so one call mixes those cells with floor cells (about 1% of the
+    voxels step a voxel or more on some axis), and steps at the grid's faces
+    sample the zero outside."""
     shape = (19, 37, 45)
     r = np.random.default_rng(5)
     u = smooth_field(shape, 2.0, 6)
     m = (r.standard_normal((3,) + shape) * 1e-6).astype(np.float32)
     v = (r.random((3,) + shape) * 1e-12).astype(np.float32)
     g = (r.standard_normal((3,) + shape) * 1e-6).astype(np.float32)
-    params = fa.RegParams(lr=0.5)
+    params = fa.RegParams(lr=lr)
     mt, vt = cuda(m), cuda(v)
     for t in (1, 7):
         mt, vt = cuda(m), cuda(v)
         u_out, eps = fa.fa_radam_step(cuda(u), mt, vt, cuda(g), t, params)
         f32 = lambda x: float(np.float32(x))
         d, mr, vr = orc.adam(g, m, v, t, f32(0.9), f32(0.999), f32(1e-8))
-        delta, er = orc.step_scale(d, 0.5, 2.0)
+        delta, er = orc.step_scale(d, lr, 2.0)
+        if lr > 2.0:  # both cell rules occur
+            big = (np.abs(delta) >= 1.0).any(0)
+            assert 0 < big.sum() < big.size
         ur = orc.compose(u, delta)
         assert rel(mt, mr) < TOL and rel(vt, vr) < TOL
         assert abs(float(eps) - er) <= TOL * er

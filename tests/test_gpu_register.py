@@ -103,6 +103,7 @@ def test_tiny_and_degenerate_grids(fa, orc, mode):
     dict(window=7, sigma_grad=2.0, sigma_warp=0.0),  # wider window, no warp smoothing
     dict(window=3, sigma_grad=3.0, sigma_warp=2.5),  # Gaussians wider than the fused rings
     dict(loss="mse", sigma_grad=0.5),
+    dict(lr=2.5),  # steps up to 1.25 voxel: K4 samples u from global memory
 ])
 def test_fused_equals_plain(fa, kw, shape):
     """Both schedules compute the same arithmetic in the same order, so their
