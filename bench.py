@@ -178,9 +178,9 @@ def config_dict(args, world):
             "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"}
 
 
-def traffic_from_profile(kernel: str, n_voxels: int):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
+def profile_entry(kernel: str):
+    """The committed ncu figures of a fused kernel, if they were taken on the
+    current kernel source (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
@@ -191,9 +191,40 @@ def traffic_from_profile(kernel: str, n_voxels: int):
             h.update(open(os.path.join(ROOT, "paper_2404_01249_gb300", "csrc", name), "rb").read())
         if h.hexdigest()[:16] != e["sources_sha"]:
             return None
-        return float(e["dram_bytes_per_voxel"]) * n_voxels
+        return e
     except Exception:
         return None
+
+
+def traffic_from_profile(kernel: str, n_voxels: int):
+    """DRAM bytes per launch from the committed ncu summary (None if stale)."""
+    e = profile_entry(kernel)
+    return None if e is None else float(e["dram_bytes_per_voxel"]) * n_voxels
+
+
+# instruction issue: 4 schedulers per SM, each issuing one warp instruction
+# per clock, on every SM
+SMS = 152
+ISSUE_PER_SM_CLOCK = 4
+
+
+def issue_roofline(kernels: dict, n_voxels: int, sm_mhz):
+    """Issued warp instructions per second of each fused kernel (the committed
+    ncu count per voxel x voxels / the live average launch time) against the
+    GPU's issue rate at the SM clock sampled during the run."""
+    mhz = sm_mhz if sm_mhz else 2070.0
+    peak = SMS * ISSUE_PER_SM_CLOCK * mhz * 1e6
+    out = {}
+    for kn, k in kernels.items():
+        e = profile_entry(kn)
+        if e is None or "warp_inst_per_voxel" not in e:
+            continue
+        rate = float(e["warp_inst_per_voxel"]) * n_voxels / (k["avg_launch_ms"] / 1e3)
+        out[kn] = {"warp_inst_per_voxel": float(e["warp_inst_per_voxel"]),
+                   "achieved": rate, "frac": round(rate / peak, 4)}
+    return {"unit": "warp instructions/s", "peak": peak, "sm_mhz": mhz,
+            "peak_from": f"{SMS} SMs x {ISSUE_PER_SM_CLOCK} warp instructions per clock",
+            "kernels": out}
 
 
 # --------------------------------------------------------------- GPU leg
@@ -383,6 +414,8 @@ def run_gpu(args):
                 "wall_s": wall, "roofline": roofline,
                 "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
                 "final_lncc": -float(loss)}
+        if args.mode == "fused":
+            roofline["issue"] = issue_roofline(kernels, n_fine, (clk or {}).get("sm_mhz"))
         if world == 1 and not args.no_cpu_baseline:
             dt, units, threads = oracle_sample(f, m, args.cpu_iters)
             line["cpu_baseline"] = {
