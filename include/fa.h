@@ -247,6 +247,11 @@ size_t fa_radam_workspace_size(int32_t D, int32_t H, int32_t W);
  *   d = (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + adam_eps);
  *   eps_t = lr / (c_lp max_x |d(x)|)  (0 if the max is 0);  delta = -eps_t d;
  *   u_out(x) = delta(x) + u_in(x + delta(x))   (phi <- phi o (id + delta)).
+ * u_in(x + delta) is trilinear with zero outside the grid; where every
+ * component of delta(x) is below one voxel it is taken on the cell between x
+ * and its neighbours on delta's side (weights |delta_a|, exact), elsewhere on
+ * the floor cell: the same interpolant, rounded as fa_register's fused
+ * schedule rounds it.
  * u_in, u_out, g: C=3, FA_F32; m, v: C=3, both FA_F32, both FA_BF16 or both
  * FA_F16 (16-bit moments are read, updated in FP32 and stored rounded to
  * nearest, the direction coming from the FP32 values; FP16 moments must lie
