@@ -76,6 +76,24 @@ def test_fp16_field_close_to_fp32_and_deterministic(fa):
         assert torch.equal(o["u"], b["u"]) and o["final_loss"] == b["final_loss"]
 
 
+@pytest.mark.parametrize("field", ["f32", "f16"])
+def test_steps_above_a_voxel_against_oracle(fa, orc, field):
+    """lr 2.5 allows steps of 1.25 voxels, so the fused compose samples u
+    (FP32 or FP16) from global memory (sign-side cells below a voxel, floor
+    cells above) instead of from its staged tile; against the oracle with the
+    same bar."""
+    f, m, _ = synth.voronoi_pair(shape=(24, 28, 36), seed=87)
+    scales, iters = (2, 1), (20, 10)
+    out = fa.fa_register(cuda(f), cuda(m),
+                         fa.RegParams(scales=scales, iters=iters, lr=2.5, field=field))
+    ref = orc.register(f, m, list(scales), list(iters), lr=2.5, cc_eps=f32(1e-5),
+                       beta1=f32(0.9), beta2=f32(0.999), adam_eps=f32(1e-8))
+    assert abs(out["final_loss"] - ref["final_loss"]) < 1e-3
+    assert mean_disp_diff(out["u"], ref["u"]) < 0.05
+    if field == "f16":
+        assert torch.equal(out["u"], out["u"].half().float())
+
+
 @pytest.mark.parametrize("kw", [dict(mode="plain"), dict(mode="persistent"), dict(use_jac=True),
                                 dict(loss="mse"), dict(sigma_warp=3.0)])
 def test_fp16_field_refused_outside_the_fused_lncc_path(fa, kw):
