@@ -463,9 +463,12 @@ def run_batched(args):
     moving = [torch.from_numpy(p[1]).to(dev).to(img_dtype) for p in pairs]
 
     def cfgs(mode):
+        # an FP16 u is a fused-schedule option: the per-op form keeps u in FP32
+        field = args.field if mode == "fused" else "f32"
         return [fa.RegParams(scales=WORKLOAD["scales"], iters=WORKLOAD["iters"], lr=lr,
                              sigma_grad=sg, sigma_warp=WORKLOAD["sigma_warp"],
-                             window=WORKLOAD["window"], mode=mode, state=args.storage)
+                             window=WORKLOAD["window"], mode=mode, state=args.storage,
+                             field=field)
                 for lr in (0.25, 0.5, 1.0) for sg in (0.5, 1.0, 2.0)]
 
     n_cfg = len(cfgs("fused"))
@@ -520,8 +523,11 @@ def run_batched(args):
             "data": "synthetic",
             "config": {"workload": f"uneven_brain_batch_{len(shapes)}x{n_cfg}",
                        "schedule": args.schedule, "jobs_per_wave": wave,
-                       "storage": ("bf16 images and Adam moments, fp32 displacement and "
-                                   "arithmetic" if args.storage == "bf16" else "fp32"),
+                       "storage": (("bf16 images and Adam moments, " if args.storage == "bf16"
+                                    else "fp32 images and Adam moments, ")
+                                   + ("fp16 displacement (fp32 in the plain form), "
+                                      if args.field == "f16" else "fp32 displacement, ")
+                                   + "fp32 arithmetic"),
                        "concurrency": args.concurrency,
                        "shapes": [list(x) for x in shapes], "scales": list(WORKLOAD["scales"]),
                        "iters": list(WORKLOAD["iters"]), "lr": [0.25, 0.5, 1.0],

@@ -126,8 +126,9 @@ typedef struct {
                              (arithmetic stays FP32; u_out is returned in FP32); it
                              needs FA_MODE_FUSED, the LNCC loss, use_jac = 0 and both
                              Gaussians within the fused kernels' radius
-                             (FA_ERR_UNSUPPORTED otherwise), and the lockstep call and
-                             every other call take FA_F32 only. */
+                             (FA_ERR_UNSUPPORTED otherwise).
+                             fa_register_batched_lockstep takes FA_F16 under the same
+                             conditions; every other call takes FA_F32 only. */
 } fa_params;
 
 /* Fills p with: 3 levels {4,2,1} x {200,100,50}, lr 0.5, sigma_grad 1,
@@ -429,8 +430,9 @@ fa_status fa_register_batched(int32_t n_pairs, const fa_vol *fixed, const fa_vol
  * schedule itself has no counterpart in the paper): the jobs of a wave
  * advance level by level and iteration by iteration together, and every
  * iteration is ONE launch of each fused kernel over the tiles of every job
- * of the wave (K3 and K4: one launch per distinct Gaussian radius and
- * compose variant among the jobs).  Per-job set-up (pyramid, level start,
+ * of the wave (K3: one launch per distinct Gaussian radius and moment
+ * storage among the jobs; K4: per distinct Gaussian radius, compose variant
+ * and storage of u).  Per-job set-up (pyramid, level start,
  * hand-off, final loss) runs as per-job launches between iterations.
  * Results are those of one fa_register call per job (the kernels compute
  * the same bits whatever the tiling).
@@ -443,8 +445,8 @@ fa_status fa_register_batched(int32_t n_pairs, const fa_vol *fixed, const fa_vol
  *  - every job needs mode FA_MODE_FUSED, loss FA_LOSS_LNCC, use_jac 0,
  *    sigma_grad and sigma_warp at most 2 (Gaussian radius <= 6), and the
  *    jobs of a wave share n_levels, scales, iters, window, beta1, beta2 and
- *    adam_eps; lr, c_lp, cc_eps, the sigmas, the storage type and the grids
- *    may differ.  Otherwise FA_ERR_UNSUPPORTED before anything is enqueued.
+ *    adam_eps; lr, c_lp, cc_eps, the sigmas, the storage types (of the
+ *    moments and of u) and the grids may differ.  Otherwise FA_ERR_UNSUPPORTED before anything is enqueued.
  * With graph set in every parameter set, each wave is recorded as one CUDA
  * graph on first use and replayed by later identical calls (not during a
  * stream capture of the caller's).  Everything runs on `stream`; the call

@@ -73,8 +73,9 @@ struct K3Batch {
     K3Job j[kMaxLockstepJobs];
 };
 struct K4Job {
-    const float *u, *dir;
-    float *uo;
+    const void *u;  // stored as the launch's u type
+    const float *dir;
+    void *uo;
     const float *Im;
     float *J, *gJ;
     WsHeader *h;
@@ -167,7 +168,8 @@ __global__ void __launch_bounds__(FX *K3_NW) k_smooth_adam_batch(
         j.geo.H, j.geo.W, j.geo.P, j.geo.TZ, j.t, b.ac, b.parity, bx, by, bz);
 }
 
-template <int RG, bool SU, bool TMA>
+// TU: storage of u (float, or __half: tile copies only).
+template <int RG, bool SU, bool TMA, class TU>
 __global__ void __launch_bounds__(FX *K4B_NW, 2) k_compose_batch(
     const __grid_constant__ K4Batch<SU ? 2 : 1> b) {
     const int k = batch_job(b.first, b.n, (int)blockIdx.x);
@@ -175,8 +177,9 @@ __global__ void __launch_bounds__(FX *K4B_NW, 2) k_compose_batch(
     int bx, by, bz;
     batch_tile(j.geo, (int)blockIdx.x - b.first[k], bx, by, bz);
     compose_body<RG, K4B_NW, K4_OPT, SU, TMA ? K4_ST_TMA : K4_ST_CP, TMA>(
-        job_maps<SU ? 2 : 1, TMA>(b.tm, k), j.u, j.dir, j.uo, j.Im, j.J, j.gJ, j.h, j.geo.D,
-        j.geo.H, j.geo.W, j.geo.P, j.geo.TZ, j.t, j.lr, j.c_lp, b.parity, bx, by, bz);
+        job_maps<SU ? 2 : 1, TMA>(b.tm, k), (const TU *)j.u, j.dir, (TU *)j.uo, j.Im, j.J, j.gJ,
+        j.h, j.geo.D, j.geo.H, j.geo.W, j.geo.P, j.geo.TZ, j.t, j.lr, j.c_lp, b.parity, bx, by,
+        bz);
 }
 
 // Slab depth of a lockstep launch: one TZ for all its jobs (each capped at its
@@ -318,29 +321,35 @@ cudaError_t launch_k3_batch(K3Batch<k3_maps<TS>()> &b, const LockstepJob *jobs, 
     return launch_batch(kern, b, SC::NT / FX, SC::bytes, s);
 }
 
-template <int RG, bool SU>
+// TU: storage of u of every job of the launch (an FP16 u takes tile copies
+// only: cudaErrorNotSupported when a job's buffers do not meet their rules).
+template <int RG, bool SU, class TU>
 cudaError_t launch_k4_batch(K4Batch<SU ? 2 : 1> &b, const LockstepJob *jobs, const int *idx,
                             cudaStream_t s) {
-    constexpr int NM = SU ? 2 : 1;
-    using ST = K4S<RG, K4B_NW, K4_OPT, SU, K4_ST_TMA>;
+    constexpr int NM = SU ? 2 : 1, EU = (int)sizeof(TU);
+    using ST = K4S<RG, K4B_NW, K4_OPT, SU, K4_ST_TMA, TU>;
     bool tma = true;
     for (int k = 0; k < b.n && tma; ++k) {
         const LockstepJob &q = jobs[idx[k]];
         tma = tmap(&b.tm[NM * k], q.fb->dir, 4, q.d, 3, ST::BXW, ST::RY, 3);
         if constexpr (SU)
-            tma = tma && tmap(&b.tm[NM * k + 1], q.u, 4, q.d, 3, ST::UBXW, ST::URY, 3);
+            tma = tma && tmap(&b.tm[NM * k + 1], q.u, EU, q.d, 3, ST::UBXW, ST::URY, 3);
     }
     if (tma) {
-        auto kern = k_compose_batch<RG, SU, true>;
+        auto kern = k_compose_batch<RG, SU, true, TU>;
         static const int occ = prepare(kern, ST::bytes, ST::NT);
         batch_layout(b, jobs, idx, ST::TY, RG, occ);
         return launch_batch(kern, b, ST::NT / FX, ST::bytes, s);
     }
-    using SC = K4S<RG, K4B_NW, K4_OPT, SU, K4_ST_CP>;
-    auto kern = k_compose_batch<RG, SU, false>;
-    static const int occ = prepare(kern, SC::bytes, SC::NT);
-    batch_layout(b, jobs, idx, SC::TY, RG, occ);
-    return launch_batch(kern, b, SC::NT / FX, SC::bytes, s);
+    if constexpr (EU == 4) {
+        using SC = K4S<RG, K4B_NW, K4_OPT, SU, K4_ST_CP>;
+        auto kern = k_compose_batch<RG, SU, false, float>;
+        static const int occ = prepare(kern, SC::bytes, SC::NT);
+        batch_layout(b, jobs, idx, SC::TY, RG, occ);
+        return launch_batch(kern, b, SC::NT / FX, SC::bytes, s);
+    } else {
+        return cudaErrorNotSupported;
+    }
 }
 
 #define FA_CASE(n, call)      \
@@ -415,23 +424,23 @@ cudaError_t k3_batch(int RG, int m, const LockstepJob *jobs, const int *idx, Ada
     return dispatch_k3_batch_ts<TS>(RG, b, jobs, idx, s);
 }
 
-template <bool SU>
+template <bool SU, class TU>
 cudaError_t dispatch_k4_batch(int RG, K4Batch<SU ? 2 : 1> &b, const LockstepJob *jobs,
                               const int *idx, cudaStream_t s) {
     switch (RG) {
-        FA_CASE(0, (launch_k4_batch<RR, SU>(b, jobs, idx, s)))
-        FA_CASE(1, (launch_k4_batch<RR, SU>(b, jobs, idx, s)))
-        FA_CASE(2, (launch_k4_batch<RR, SU>(b, jobs, idx, s)))
-        FA_CASE(3, (launch_k4_batch<RR, SU>(b, jobs, idx, s)))
-        FA_CASE(4, (launch_k4_batch<RR, SU>(b, jobs, idx, s)))
-        FA_CASE(5, (launch_k4_batch<RR, SU>(b, jobs, idx, s)))
-        FA_CASE(6, (launch_k4_batch<RR, SU>(b, jobs, idx, s)))
+        FA_CASE(0, (launch_k4_batch<RR, SU, TU>(b, jobs, idx, s)))
+        FA_CASE(1, (launch_k4_batch<RR, SU, TU>(b, jobs, idx, s)))
+        FA_CASE(2, (launch_k4_batch<RR, SU, TU>(b, jobs, idx, s)))
+        FA_CASE(3, (launch_k4_batch<RR, SU, TU>(b, jobs, idx, s)))
+        FA_CASE(4, (launch_k4_batch<RR, SU, TU>(b, jobs, idx, s)))
+        FA_CASE(5, (launch_k4_batch<RR, SU, TU>(b, jobs, idx, s)))
+        FA_CASE(6, (launch_k4_batch<RR, SU, TU>(b, jobs, idx, s)))
     }
     return cudaErrorInvalidValue;
 }
 
-// One K4 launch over jobs[idx[0..m)].
-template <bool SU>
+// One K4 launch over jobs[idx[0..m)], whose u is stored as TU.
+template <bool SU, class TU>
 cudaError_t k4_batch(int RG, int m, const LockstepJob *jobs, const int *idx, int parity,
                      cudaStream_t s) {
     K4Batch<SU ? 2 : 1> b;
@@ -451,7 +460,7 @@ cudaError_t k4_batch(int RG, int m, const LockstepJob *jobs, const int *idx, int
         j.lr = q.p->lr;
         j.c_lp = q.p->c_lp;
     }
-    return dispatch_k4_batch<SU>(RG, b, jobs, idx, s);
+    return dispatch_k4_batch<SU, TU>(RG, b, jobs, idx, s);
 }
 #undef FA_CASE
 
@@ -516,19 +525,31 @@ fa_status fused_iteration_lockstep(int n, const LockstepJob *jobs, int t, cudaSt
             note_launch();
         }
     }
-    for (int su = 0; su < 2; ++su)
-        for (int rg = 0; rg <= kMaxFusedRG; ++rg) {
-            int m = 0;
-            for (int k = 0; k < n; ++k) {
-                const fa_params *p = jobs[k].p;
-                const int ksu = (double)p->lr / (double)p->c_lp < 0.999 ? 1 : 0;
-                if (jobs[k].tw->R == rg && ksu == su) idx[m++] = k;
+    const int fields[2] = {FA_F32, FA_F16};
+    for (int fs : fields)
+        for (int su = 0; su < 2; ++su)
+            for (int rg = 0; rg <= kMaxFusedRG; ++rg) {
+                int m = 0;
+                for (int k = 0; k < n; ++k) {
+                    const fa_params *p = jobs[k].p;
+                    const int ksu = (double)p->lr / (double)p->c_lp < 0.999 ? 1 : 0;
+                    if (jobs[k].tw->R == rg && ksu == su && p->field_storage == fs) idx[m++] = k;
+                }
+                if (m == 0) continue;
+                cudaError_t e;
+                if (fs == FA_F16)
+                    e = su ? k4_batch<true, __half>(rg, m, jobs, idx, parity, s)
+                           : k4_batch<false, __half>(rg, m, jobs, idx, parity, s);
+                else
+                    e = su ? k4_batch<true, float>(rg, m, jobs, idx, parity, s)
+                           : k4_batch<false, float>(rg, m, jobs, idx, parity, s);
+                if (e == cudaErrorNotSupported) {
+                    set_error("lockstep: an FP16 u needs tile copies (rows of 8 elements)");
+                    return FA_ERR_UNSUPPORTED;
+                }
+                FA_CUDA_TRY(e);
+                note_launch();
             }
-            if (m == 0) continue;
-            FA_CUDA_TRY(su ? k4_batch<true>(rg, m, jobs, idx, parity, s)
-                           : k4_batch<false>(rg, m, jobs, idx, parity, s));
-            note_launch();
-        }
     return FA_OK;
 }
 

@@ -756,10 +756,6 @@ fa_status lockstep_check(int n, const LockstepArgs *a) {
             set_error("lockstep: job %d: needs the fused LNCC path without use_jac", k);
             return FA_ERR_UNSUPPORTED;
         }
-        if (p->field_storage != FA_F32) {
-            set_error("lockstep: job %d: keeps u in FP32 (field_storage must be FA_F32)", k);
-            return FA_ERR_UNSUPPORTED;
-        }
         bool same = p->n_levels == p0->n_levels && p->window == p0->window &&
                     p->beta1 == p0->beta1 && p->beta2 == p0->beta2 &&
                     p->adam_eps == p0->adam_eps;

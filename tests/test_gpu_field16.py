@@ -3,7 +3,8 @@ stored update of u is rounded to FP16 (arithmetic stays FP32), u_out comes back
 in FP32 holding those FP16 values, and the registration stays within the
 end-to-end bar of the FP64 oracle (final LNCC within 1e-3, mean displacement
 difference below 0.05 voxel) on the C1 pair, a brain-shaped coarse level and
-grids of uneven width.  Calls outside the fused LNCC path refuse FA_F16."""
+grids of uneven width; lockstep waves may mix FP16 and FP32 u.  Calls outside
+the fused LNCC path refuse FA_F16."""
 import numpy as np
 import pytest
 import torch
@@ -104,10 +105,22 @@ def test_fp16_field_refused_outside_the_fused_lncc_path(fa, kw):
     assert "field_storage" in str(e.value)
 
 
-def test_fp16_field_refused_by_lockstep(fa):
-    f, m, _ = synth.blobs_pair(shape=(12, 14, 16), sigma=2.0)
-    with pytest.raises(fa.FAError) as e:
-        fa.fa_register_batched_lockstep([cuda(f)], [cuda(m)],
-                                        [fa.RegParams(scales=(1,), iters=(2,), field="f16")])
-    assert e.value.status in (fa.FA_ERR_INVALID, fa.FA_ERR_UNSUPPORTED)
-    assert "field_storage" in str(e.value)
+def test_fp16_field_in_lockstep_equals_one_call_per_job(fa):
+    """Jobs with FP16 and FP32 u (and BF16 moments, steps below and above a
+    voxel) in one lockstep wave: each job's u and final loss are those of its
+    own fa_register call, bit for bit (K4 runs once per u storage)."""
+    shapes = [(20, 23, 29), (17, 30, 41)]
+    pairs = [synth.voronoi_pair(shape=sh, seed=300 + i) for i, sh in enumerate(shapes)]
+    fixed = [cuda(p[0]) for p in pairs]
+    moving = [cuda(p[1]) for p in pairs]
+    cfgs = [fa.RegParams(scales=(2, 1), iters=(8, 6), field="f16"),
+            fa.RegParams(scales=(2, 1), iters=(8, 6)),
+            fa.RegParams(scales=(2, 1), iters=(8, 6), field="f16", state="bf16", lr=2.5)]
+    out = fa.fa_register_batched_lockstep(fixed, moving, cfgs)
+    for i in range(len(shapes)):
+        for c, p in enumerate(cfgs):
+            r = out[i * len(cfgs) + c]
+            ref = fa.fa_register(fixed[i], moving[i], p)
+            assert r["status"] == 0
+            assert torch.equal(r["u"], ref["u"]), (i, c)
+            assert r["final_loss"] == ref["final_loss"], (i, c)
