@@ -227,6 +227,20 @@ def issue_roofline(kernels: dict, n_voxels: int, sm_mhz):
             "kernels": out}
 
 
+def whole_job_rate(local_ms: float, units_per_rank: float, world: int, device) -> tuple:
+    """The job's time is the slowest rank's (max over ranks of the local
+    time); its rate is the units all ranks processed over that time.
+    Returns (max_ms, rate)."""
+    ms = float(local_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * units_per_rank / (ms / 1e3)
+
+
 # --------------------------------------------------------------- GPU leg
 def run_gpu(args):
     import torch
@@ -321,13 +335,8 @@ def run_gpu(args):
     clk = clocks.stop()
     fa.fa_ws_status(ws)
     step_ms = [a.elapsed_time(b) for a, b in zip(step0, step1)]
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
     vi = voxel_iters(shape, WORKLOAD["scales"], WORKLOAD["iters"])
-    value = world * vi * args.steps / (total_ms / 1e3)
+    total_ms, value = whole_job_rate(sum(step_ms), vi * args.steps, world, dev)
 
     # Roofline of the finest-level iteration: the whole path's algorithmic
     # bytes (read I_f, I_m, u, m, nu and write u, m, nu once: 80 B per voxel)
@@ -394,12 +403,8 @@ def run_gpu(args):
         lh.copy_(loss, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e = {"value": world * vi * args.steps / (e2e_ms / 1e3), "unit": METRIC,
+    _, e2e_rate = whole_job_rate(e0.elapsed_time(e1), vi * args.steps, world, dev)
+    e2e = {"value": e2e_rate, "unit": METRIC,
            "h2d_bytes_per_step": 2 * f.nbytes, "d2h_bytes_per_step": uh.numel() * 4 + 4,
            "final_lncc": -float(lh)}
 
