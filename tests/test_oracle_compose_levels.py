@@ -60,6 +60,40 @@ def test_compose_matches_scipy(orc):
         assert np.allclose(out[c], ref, atol=1e-12)
 
 
+def test_compose_sign_side_cell_gives_the_oracle_value(orc):
+    """For a step below one voxel on every axis, the trilinear sample may be
+    taken on the cell between x and its neighbours on each component's sign
+    side, with weights |delta_a| (the CUDA path's compose cell): the
+    interpolant is continuous across cell faces, so this equals the oracle's
+    floor-cell compose, including at the grid's faces (zero outside) and for
+    components that are exactly zero."""
+    shape = (6, 7, 9)
+    u = rng(46).standard_normal((3,) + shape)
+    d = rng(47).uniform(-0.999, 0.999, (3,) + shape)
+    d[0, 2] = 0.0  # a plane of zero z components
+    d[2, :, :, 4] = -0.0
+    D, H, W = shape
+
+    def at(c, z, y, x):
+        return u[c, z, y, x] if (0 <= z < D and 0 <= y < H and 0 <= x < W) else 0.0
+
+    out = np.empty_like(u)
+    for z in range(D):
+        for y in range(H):
+            for x in range(W):
+                dz, dy, dx = d[:, z, y, x]
+                sz, sy, sx = (-1 if v < 0 else 1 for v in (dz, dy, dx))
+                tz, ty, tx = abs(dz), abs(dy), abs(dx)
+                for c in range(3):
+                    v = 0.0
+                    for a, wa in ((0, 1 - tz), (sz, tz)):
+                        for b, wb in ((0, 1 - ty), (sy, ty)):
+                            for e, we in ((0, 1 - tx), (sx, tx)):
+                                v += wa * wb * we * at(c, z + a, y + b, x + e)
+                    out[c, z, y, x] = d[c, z, y, x] + v
+    assert np.allclose(out, orc.compose(u, d), rtol=0, atol=1e-13)
+
+
 def test_small_step_keeps_jacobian_positive(orc):
     """Theorem (appendix): id + eps v is a diffeomorphism for eps < 1/LP(v);
     the step scaling keeps the update inside that bound, so composing a
