@@ -150,6 +150,9 @@ def test_lockstep_validation_before_launch(lib):
                                            sigma_grad=2.0).to_c())
     assert run(2, fx, fx, 2, same, uo4, None, None, 64, None, 0, None) == 8  # workspace
     assert run(2, fx, fx, 2, same, uo4, None, None, 0, None, 0, None) == 1
+    # jobs with FP16 and FP32 u advance together (the missing workspace is reported)
+    f16 = (fa.Params * 2)(p, fa.RegParams(scales=(2, 1), iters=(3, 2), field="f16").to_c())
+    assert run(2, fx, fx, 2, f16, uo4, None, None, 64, None, 0, None) == 8
 
 
 def test_moment_storage_validation(lib):
